@@ -1,0 +1,660 @@
+"""Plain, slow, FP64 CPU oracle of the TAPS hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this module.
+The product path (the CUDA library and its Python binding) never calls it, and it
+calls nothing of the product: it shares no code, table or constant generator with
+the GPU kernels.  Inputs reach it as plain numbers built by
+``paper_2503_13933_gb300.workloads`` (seeded generators holding none of the
+method's arithmetic).
+
+Every function states the passage of the paper (Guo et al., "Tensor-decomposition-
+based A Priori Surrogate (TAPS) modeling for ultra large-scale simulations") that it
+follows.  Where the paper is silent, the reading taken is stated beside the code:
+
+* C-HiDeNN patch function (Eq. 1, Sec. 2.1): the formula is deferred to the
+  C-HiDeNN literature.  Reading: radial point interpolation with polynomial
+  reproduction on the nodal patch A_s^i = {j : |j-i| <= s} (truncated at the ends),
+  cubic-spline kernel with support a*h, monomials centred at x_i and scaled by h.
+* Quadrature (Table 1, "Gaussian integration"): 6-point Gauss-Legendre per element.
+* Solver convergence (Sec. 2.6, "relative change of all solution matrices"):
+  max_d ||U_d^new - U_d^old||_F / ||U_d^new||_F after column normalisation.
+* Residual (not defined by the paper): rho = ||F - A u||_2 / ||F||_2 on the free
+  nodal unknowns, evaluated with the Gram identity term by term.
+
+Pins (tests/test_oracle_*.py): Kronecker delta, partition of unity, polynomial
+reproduction, dilation independence, textbook special cases (linear hats,
+quadratic Lagrange), closed-form matrix integrals, dense-vs-block-banded solve,
+explicit full-grid residual, brute-force Kronecker FE solve, manufactured-solution
+convergence rates, the rank-1-in-k property of the space-parameter problem.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Operator kinds of the 1D matrices (Sec. 2.5, Eqs. 31-34): the index of each kind
+# is part of the problem description both implementations read.
+OP_K, OP_M, OP_G, OP_W, OP_BLO, OP_BHI = 0, 1, 2, 3, 4, 5
+OP_NAMES = {OP_K: "K", OP_M: "M", OP_G: "G", OP_W: "W", OP_BLO: "Blo", OP_BHI: "Bhi"}
+
+
+# ---------------------------------------------------------------------------------
+# Shape functions (Sec. 2.1, Eq. 1; Kronecker delta Eq. 3)
+# ---------------------------------------------------------------------------------
+def cubic_spline(z):
+    """Cubic-spline window phi(z), z >= 0 (the kernel of the patch function)."""
+    z = abs(z)
+    if z <= 0.5:
+        return 2.0 / 3.0 - 4.0 * z * z + 4.0 * z ** 3
+    if z <= 1.0:
+        return 4.0 / 3.0 - 4.0 * z + 4.0 * z * z - 4.0 / 3.0 * z ** 3
+    return 0.0
+
+
+def cubic_spline_dz(z):
+    """d phi / dz for z >= 0."""
+    z = abs(z)
+    if z <= 0.5:
+        return -8.0 * z + 12.0 * z * z
+    if z <= 1.0:
+        return -4.0 + 8.0 * z - 4.0 * z * z
+    return 0.0
+
+
+def patch(i, n, s):
+    """Nodal patch A_s^i: nodes within s elements of node i, truncated at the ends."""
+    return list(range(max(0, i - s), min(n - 1, i + s) + 1))
+
+
+def patch_matrix(x, i, s, a, p, h):
+    """Moment matrix G_i = [[R, P], [P^T, 0]] of node i's convolution patch (Eq. 1).
+
+    R_jk = phi(|x_j - x_k| / (a h)), P_jq = ((x_j - x_i)/h)^q, q = 0..p.
+    """
+    nodes = patch(i, len(x), s)
+    na = len(nodes)
+    if na < p + 1:
+        raise ValueError(f"patch of node {i} has {na} < p+1 = {p + 1} nodes")
+    G = np.zeros((na + p + 1, na + p + 1))
+    for r, j in enumerate(nodes):
+        for c, k in enumerate(nodes):
+            G[r, c] = cubic_spline(abs(x[j] - x[k]) / (a * h))
+        for q in range(p + 1):
+            G[r, na + q] = ((x[j] - x[i]) / h) ** q
+            G[na + q, r] = G[r, na + q]
+    return nodes, G
+
+
+def patch_function(x, i, s, a, p, h, xe):
+    """Patch function W^i_j(xe) and its derivative for every j in A_s^i (Eq. 1).
+
+    W^i(xe) = [phi(xe)^T, P(xe)^T] G_i^{-1}, first |A_s^i| entries: the RBF +
+    polynomial interpolant of unit nodal data, evaluated at xe.
+    """
+    nodes, G = patch_matrix(x, i, s, a, p, h)
+    na = len(nodes)
+    row = np.zeros(na + p + 1)
+    drow = np.zeros(na + p + 1)
+    for r, j in enumerate(nodes):
+        d = xe - x[j]
+        row[r] = cubic_spline(abs(d) / (a * h))
+        drow[r] = cubic_spline_dz(abs(d) / (a * h)) * (math.copysign(1.0, d) if d != 0 else 0.0) / (a * h)
+    for q in range(p + 1):
+        t = (xe - x[i]) / h
+        row[na + q] = t ** q
+        drow[na + q] = q * t ** (q - 1) / h if q > 0 else 0.0
+    # W solves G W = row (G symmetric) -> W = G^{-1} row.
+    W = np.linalg.solve(G, row)[:na]
+    dW = np.linalg.solve(G, drow)[:na]
+    return nodes, W, dW
+
+
+def shape_functions(x, s, a, p, e, xe):
+    """C-HiDeNN shape functions on element e at xe (Eq. 1, Eq. 31/32).
+
+    N~_k(xe) = N_e(xe) W^e_k(xe) + N_{e+1}(xe) W^{e+1}_k(xe), k in e-s .. e+1+s,
+    with N_e, N_{e+1} the linear finite-element hats of the element's two nodes.
+    Returns (global node ids, N~, dN~/dx).
+    """
+    n = len(x)
+    h = x[e + 1] - x[e]
+    lo = max(0, e - s)
+    hi = min(n - 1, e + 1 + s)
+    ids = list(range(lo, hi + 1))
+    N = np.zeros(len(ids))
+    B = np.zeros(len(ids))
+    hat = [(x[e + 1] - xe) / h, (xe - x[e]) / h]
+    dhat = [-1.0 / h, 1.0 / h]
+    for c, i in enumerate((e, e + 1)):
+        nodes, W, dW = patch_function(x, i, s, a, p, h, xe)
+        for r, j in enumerate(nodes):
+            k = j - lo
+            N[k] += hat[c] * W[r]
+            B[k] += dhat[c] * W[r] + hat[c] * dW[r]
+    return ids, N, B
+
+
+def locate(x, xe):
+    """Element containing xe on the node grid x (last element for the right end)."""
+    e = int(np.searchsorted(x, xe, side="right")) - 1
+    return min(max(e, 0), len(x) - 2)
+
+
+def gauss_legendre(nq):
+    """Gauss-Legendre points/weights on [0, 1] (Table 1: Gaussian integration)."""
+    t, w = np.polynomial.legendre.leggauss(nq)
+    return 0.5 * (t + 1.0), 0.5 * w
+
+
+# ---------------------------------------------------------------------------------
+# 1D matrices (Sec. 2.5, Eqs. 31-35: stiffness, mass, time derivative, weighted mass)
+# ---------------------------------------------------------------------------------
+@dataclass
+class Dim:
+    """One independent dimension: uniform nodes, C-HiDeNN hyperparameters, BCs."""
+    n: int
+    lo: float
+    hi: float
+    s: int = 2
+    a: float = 20.0
+    p: int = 2
+    n_quad: int = 6
+    dirichlet_lo: bool = True
+    dirichlet_hi: bool = True
+    weight_poly: tuple = (0.0, 0.0, 0.0, 0.0)
+
+    @property
+    def x(self):
+        return np.linspace(self.lo, self.hi, self.n)
+
+    @property
+    def free(self):
+        f = list(range(self.n))
+        if self.dirichlet_hi:
+            f = f[:-1]
+        if self.dirichlet_lo:
+            f = f[1:]
+        return np.array(f, dtype=int)
+
+
+def poly_eval(c, xv):
+    return sum(cj * xv ** j for j, cj in enumerate(c))
+
+
+def shape_tables(dim: Dim):
+    """Per element, per Gauss point: node ids, N~, B~, weight*|J| (Eq. 1, Table 1)."""
+    x = dim.x
+    gp, gw = gauss_legendre(dim.n_quad)
+    tab = []
+    for e in range(dim.n - 1):
+        h = x[e + 1] - x[e]
+        pts = []
+        for t, w in zip(gp, gw):
+            xe = x[e] + t * h
+            ids, N, B = shape_functions(x, dim.s, dim.a, dim.p, e, xe)
+            pts.append((xe, w * h, ids, N, B))
+        tab.append(pts)
+    return tab
+
+
+def assemble_full(dim: Dim, tab=None):
+    """Dense 1D matrices over ALL nodes (Eqs. 33-35, Sec. 2.5).
+
+    K_ij = int B~_i B~_j, M_ij = int N~_i N~_j, G_ij = int N~_i B~_j (test i, trial
+    j: the time-derivative term of Eq. 25), W_ij = int N~_i w(x) N~_j (weighted mass,
+    the k-weighted parametric term of Eq. 33), B_lo/B_hi = boundary point masses
+    (convection on a face, Eq. 21 / Eq. 25 boundary integral, by the Kronecker delta).
+    """
+    if tab is None:
+        tab = shape_tables(dim)
+    n = dim.n
+    mats = {k: np.zeros((n, n)) for k in (OP_K, OP_M, OP_G, OP_W)}
+    for pts in tab:
+        for xe, wj, ids, N, B in pts:
+            ids = np.array(ids)
+            wv = poly_eval(dim.weight_poly, xe)
+            mats[OP_K][np.ix_(ids, ids)] += wj * np.outer(B, B)
+            mats[OP_M][np.ix_(ids, ids)] += wj * np.outer(N, N)
+            mats[OP_G][np.ix_(ids, ids)] += wj * np.outer(N, B)
+            mats[OP_W][np.ix_(ids, ids)] += wj * wv * np.outer(N, N)
+    mats[OP_BLO] = np.zeros((n, n))
+    mats[OP_BLO][0, 0] = 1.0
+    mats[OP_BHI] = np.zeros((n, n))
+    mats[OP_BHI][n - 1, n - 1] = 1.0
+    return mats
+
+
+def assemble_free(dim: Dim, tab=None):
+    """1D matrices restricted to the free nodes (Dirichlet / zero-IC nodes dropped,
+    Eq. 5: the Kronecker delta makes the constrained nodal value the BC value)."""
+    full = assemble_full(dim, tab)
+    f = dim.free
+    return {k: v[np.ix_(f, f)].copy() for k, v in full.items()}
+
+
+# Source factors: g(x) on one dimension, given as plain data.
+def source_factor_values(kind, par, xv):
+    if kind == "const":
+        return np.full_like(np.asarray(xv, dtype=float), par[0])
+    if kind == "sin":          # sin(w x + phase)
+        return np.sin(par[0] * xv + par[1])
+    if kind == "gauss":        # exp(-(x-c)^2 / (2 sigma^2))
+        return np.exp(-((xv - par[0]) ** 2) / (2.0 * par[1] ** 2))
+    if kind == "poly":
+        return poly_eval(par, xv)
+    raise ValueError(kind)
+
+
+def project_source(dim: Dim, kind, par, nodal=None, tab=None):
+    """q_i = int N~_i g(x) dx on the free nodes (forcing term of Eq. 30).
+
+    kind 'nodal': g is the C-HiDeNN interpolant of nodal values -> q = M_full g.
+    """
+    n = dim.n
+    if kind == "nodal":
+        full = assemble_full(dim, tab)[OP_M] @ np.asarray(nodal, dtype=float)
+        return full[dim.free]
+    if tab is None:
+        tab = shape_tables(dim)
+    q = np.zeros(n)
+    for pts in tab:
+        for xe, wj, ids, N, B in pts:
+            q[np.array(ids)] += wj * source_factor_values(kind, par, xe) * N
+    return q[dim.free]
+
+
+# ---------------------------------------------------------------------------------
+# Problem in separated form (Sec. 2.4-2.5, Eqs. 25, 33-36, 41-42)
+# ---------------------------------------------------------------------------------
+@dataclass
+class Problem:
+    """A = sum_t alpha_t (x)_d Op[t][d];  F = sum_r beta_r (x)_d q[r][d]."""
+    dims: list
+    ops: list              # ops[d] = dict kind -> (n_free x n_free) matrix
+    terms: list            # list of (alpha, [op kind per dim])
+    sources: list          # list of (beta, [q vector per dim])
+
+    @property
+    def D(self):
+        return len(self.dims)
+
+    @property
+    def nfree(self):
+        return [len(dm.free) for dm in self.dims]
+
+
+def build_problem(dims, terms, sources):
+    """dims: list of Dim; terms: list of (alpha, [op per dim]); sources: list of
+    (beta, [(kind, par) or ('nodal', values) per dim])."""
+    tabs = [shape_tables(dm) for dm in dims]
+    ops = [assemble_free(dm, tb) for dm, tb in zip(dims, tabs)]
+    src = []
+    for beta, facs in sources:
+        qs = []
+        for dm, tb, (kind, par) in zip(dims, tabs, facs):
+            if kind == "nodal":
+                qs.append(project_source(dm, kind, None, nodal=par, tab=tb))
+            else:
+                qs.append(project_source(dm, kind, par, tab=tb))
+        src.append((float(beta), qs))
+    return Problem(dims=list(dims), ops=ops, terms=[(float(a), list(o)) for a, o in terms],
+                   sources=src)
+
+
+# ---------------------------------------------------------------------------------
+# Subspace iteration (Algorithm 1, Sec. 2.6; Eq. 43)
+# ---------------------------------------------------------------------------------
+def gram(U, Op):
+    """Gamma = U^T Op U (M x M): the coefficient integrals of Eq. 34."""
+    return U.T @ (Op @ U)
+
+
+def coefficients(prob: Problem, U, d):
+    """C_op for dim d (Eq. 34/35: Hadamard product over the other dimensions, summed
+    over the operator terms that share dim d's matrix) and the RHS F_d (Eq. 41's Q)."""
+    M = U[0].shape[1]
+    C = {}
+    for alpha, opk in prob.terms:
+        prod = np.full((M, M), alpha)
+        for e in range(prob.D):
+            if e != d:
+                prod = prod * gram(U[e], prob.ops[e][opk[e]])
+        C[opk[d]] = C.get(opk[d], np.zeros((M, M))) + prod
+    F = np.zeros((prob.nfree[d], M))
+    for beta, qs in prob.sources:
+        c = np.full(M, beta)
+        for e in range(prob.D):
+            if e != d:
+                c = c * (U[e].T @ qs[e])
+        F += np.outer(qs[d], c)
+    return C, F
+
+
+def reduced_matrix_dense(prob: Problem, d, C):
+    """The reduced operator of Eq. 36-40 reshaped with I = (node, mode), node-major:
+    A[(i,m),(j,n)] = sum_op Op[i,j] C_op[m,n] = sum_op kron(Op, C_op)."""
+    A = None
+    for op, Cop in C.items():
+        term = np.kron(prob.ops[d][op], Cop)
+        A = term if A is None else A + term
+    return A
+
+
+def solve_dense(A, F):
+    """Dense LU with partial pivoting (library solve) of the reduced system."""
+    n, M = F.shape
+    return np.linalg.solve(A, F.reshape(-1)).reshape(n, M)
+
+
+def band_halfwidth(prob: Problem, d):
+    hb = 0
+    for op in prob.ops[d].values():
+        nz = np.nonzero(op)
+        if len(nz[0]):
+            hb = max(hb, int(np.max(np.abs(nz[0] - nz[1]))))
+    return hb
+
+
+def solve_block_banded(prob: Problem, d, C, F):
+    """Block Gaussian elimination without pivoting of the node-major block-banded
+    reduced system (Eq. 43): block (i,j) = sum_op Op[i,j] C_op, half-bandwidth hb.
+
+    Forward: for each block row k, D_k = A_kk; W_kj = D_k^{-1} A_kj, z_k = D_k^{-1} F_k;
+    A_ij -= A_ik W_kj, F_i -= A_ik z_k for i, j in k+1..k+hb.
+    Backward: x_k = z_k - sum_j W_kj x_j.
+    """
+    n, M = F.shape
+    hb = band_halfwidth(prob, d)
+    blocks = {}
+    for i in range(n):
+        for j in range(max(0, i - hb), min(n, i + hb + 1)):
+            B = np.zeros((M, M))
+            for op, Cop in C.items():
+                B += prob.ops[d][op][i, j] * Cop
+            blocks[(i, j)] = B
+    rhs = [F[i].copy() for i in range(n)]
+    W = {}
+    z = [None] * n
+    for k in range(n):
+        Dk = blocks[(k, k)]
+        js = range(k + 1, min(n, k + hb + 1))
+        for j in js:
+            W[(k, j)] = np.linalg.solve(Dk, blocks[(k, j)])
+        z[k] = np.linalg.solve(Dk, rhs[k])
+        for i in js:
+            Lik = blocks[(i, k)]
+            for j in js:
+                blocks[(i, j)] = blocks[(i, j)] - Lik @ W[(k, j)]
+            rhs[i] = rhs[i] - Lik @ z[k]
+    X = np.zeros((n, M))
+    for k in range(n - 1, -1, -1):
+        xk = z[k].copy()
+        for j in range(k + 1, min(n, k + hb + 1)):
+            xk -= W[(k, j)] @ X[j]
+        X[k] = xk
+    return X
+
+
+def normalise_columns(Ud):
+    """Unit 2-norm columns; sign makes the largest-magnitude entry positive.
+    (Scale normalisation is not stated by the paper; the next dimension's solve
+    absorbs it, so the represented field is unchanged after a full sweep.)"""
+    Ud = Ud.copy()
+    for m in range(Ud.shape[1]):
+        col = Ud[:, m]
+        nrm = math.sqrt(float(np.dot(col, col)))
+        if nrm == 0.0:
+            continue
+        k = int(np.argmax(np.abs(col)))
+        sgn = 1.0 if col[k] >= 0 else -1.0
+        Ud[:, m] = col / (sgn * nrm)
+    return Ud
+
+
+def sweep(prob: Problem, U, solver="banded"):
+    """One subspace-iteration sweep (Algorithm 1 inner loop, Eq. 43).
+
+    For d = 1..D in order, with the other factors at their latest values
+    (Gauss-Seidel), solve sum_op Op_d U_d C_op^T = F_d for U_d; normalise U_d for
+    d < D.  Returns the new factors and max_d ||dU_d||_F / ||U_d||_F.
+    """
+    U = [u.copy() for u in U]
+    change = 0.0
+    for d in range(prob.D):
+        C, F = coefficients(prob, U, d)
+        if solver == "dense":
+            Ud = solve_dense(reduced_matrix_dense(prob, d, C), F)
+        else:
+            Ud = solve_block_banded(prob, d, C, F)
+        if d < prob.D - 1:
+            Ud = normalise_columns(Ud)
+        nrm = np.linalg.norm(Ud)
+        dif = np.linalg.norm(Ud - U[d])
+        change = max(change, dif / nrm if nrm > 0 else math.inf)
+        U[d] = Ud
+    return U, change
+
+
+# ---------------------------------------------------------------------------------
+# Residual (Gram identity) and explicit full-grid forms for tiny grids
+# ---------------------------------------------------------------------------------
+def residual(prob: Problem, U):
+    """rho = ||F - A u|| / ||F||, u = sum_m (x)_d U_d[:,m] (Eq. 7), expanded as
+    ||F||^2 - 2 F^T A u + ||A u||^2, each a sum of products of 1D inner products."""
+    D = prob.D
+    M = U[0].shape[1]
+    R = len(prob.terms)
+    Rf = len(prob.sources)
+    FF = np.ones((Rf, Rf))
+    FA = np.ones((Rf, R, M))
+    AA = np.ones((R, M, R, M))
+    for d in range(D):
+        Q = np.stack([qs[d] for _, qs in prob.sources], axis=1)        # n x Rf
+        Y = np.stack([prob.ops[d][opk[d]] @ U[d] for _, opk in prob.terms], axis=0)  # R x n x M
+        FF *= Q.T @ Q
+        FA *= np.einsum("ir,tim->rtm", Q, Y)
+        AA *= np.einsum("tim,sin->tmsn", Y, Y)
+    a = np.array([t[0] for t in prob.terms])
+    b = np.array([s[0] for s in prob.sources])
+    nF2 = float(b @ FF @ b)
+    fau = float(np.einsum("r,t,rtm->", b, a, FA))
+    au2 = float(np.einsum("t,s,tmsn->", a, a, AA))
+    r2 = nF2 - 2.0 * fau + au2
+    return math.sqrt(max(r2, 0.0) / nF2), nF2, fau, au2
+
+
+def kron_all(mats):
+    out = mats[0]
+    for m in mats[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+def full_operator(prob: Problem):
+    """Explicit A = sum_t alpha_t (x)_d Op_{t,d} on the free grid (tiny cases only)."""
+    A = None
+    for alpha, opk in prob.terms:
+        T = alpha * kron_all([prob.ops[d][opk[d]] for d in range(prob.D)])
+        A = T if A is None else A + T
+    return A
+
+
+def full_rhs(prob: Problem):
+    F = None
+    for beta, qs in prob.sources:
+        T = beta * kron_all([q.reshape(-1, 1) for q in qs]).reshape(-1)
+        F = T if F is None else F + T
+    return F
+
+
+def cp_full(U):
+    """Full tensor of u = sum_m prod_d U_d[:, m] (Eq. 7), C order (last dim fastest)."""
+    M = U[0].shape[1]
+    out = 0.0
+    for m in range(M):
+        out = out + kron_all([u[:, m].reshape(-1, 1) for u in U]).reshape(-1)
+    return out
+
+
+def residual_explicit(prob: Problem, U):
+    A = full_operator(prob)
+    F = full_rhs(prob)
+    u = cp_full(U)
+    return float(np.linalg.norm(F - A @ u) / np.linalg.norm(F))
+
+
+def solve_full(prob: Problem):
+    """Brute force: the full (not decomposed) C-HiDeNN Galerkin solution on the
+    tensor grid (the u^{C-HiDeNN} of Eq. 44)."""
+    return np.linalg.solve(full_operator(prob), full_rhs(prob))
+
+
+# ---------------------------------------------------------------------------------
+# Initialisation: counter-based uniform draws (SplitMix64, Steele-Lea-Flood 2014)
+# ---------------------------------------------------------------------------------
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(x):
+    """SplitMix64 output function applied to state x (published constants)."""
+    z = (x + 0x9E3779B97F4A7C15) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def uniform_pm1(seed, d, i, m):
+    """U(-1,1) draw keyed on (seed, dim, row, mode): the counter packs
+    seed (24 bits) | dim (8) | mode (12) | row (20); top 53 bits of the output."""
+    ctr = ((seed & 0xFFFFFF) << 40) | ((d & 0xFF) << 32) | ((m & 0xFFF) << 20) | (i & 0xFFFFF)
+    z = splitmix64(ctr)
+    return 2.0 * ((z >> 11) * (1.0 / 9007199254740992.0)) - 1.0
+
+
+def init_column(prob: Problem, d, m, how, seed=0):
+    """Initial column m of U_d (Algorithm 1 starts from random values).
+    'random': U(-1,1) counter-based draws; 'zero': zero in the first dimension,
+    ones elsewhere (the first solve of a sweep is dimension 1)."""
+    n = prob.nfree[d]
+    if how == "random":
+        return np.array([uniform_pm1(seed, d, i, m) for i in range(n)])
+    if how == "zero":
+        return np.zeros(n) if d == 0 else np.ones(n)
+    raise ValueError(how)
+
+
+def init_factors(prob: Problem, M, how="random", seed=0):
+    return [np.stack([init_column(prob, d, m, how, seed) for m in range(M)], axis=1)
+            for d in range(prob.D)]
+
+
+# ---------------------------------------------------------------------------------
+# Greedy mode schedule + sweeps to tolerance (Algorithm 1 with growing M)
+# ---------------------------------------------------------------------------------
+@dataclass
+class SolveResult:
+    U: list
+    history: list = field(default_factory=list)   # (M, sweep, change, rho)
+    rho: float = math.inf
+    converged: bool = False
+
+
+def solve(prob: Problem, M0=1, M_max=8, als_tol=1e-10, res_tol=1e-6, max_sweeps=200,
+          init="zero", seed=0, solver="banded", U0=None):
+    """Run Algorithm 1 for M = M0..M_max modes, adding one column per step.
+    At each M, sweep until the factor change <= als_tol or rho <= res_tol (or
+    max_sweeps); stop growing M once rho <= res_tol."""
+    if U0 is not None:
+        U = [u.copy() for u in U0]
+    else:
+        U = init_factors(prob, M0, init, seed)
+    res = SolveResult(U=U)
+    M = U[0].shape[1]
+    while True:
+        for it in range(max_sweeps):
+            U, change = sweep(prob, U, solver)
+            rho = residual(prob, U)[0]
+            res.history.append((M, it, change, rho))
+            if rho <= res_tol or change <= als_tol:
+                break
+        res.U, res.rho = U, rho
+        if rho <= res_tol:
+            res.converged = True
+            return res
+        if M >= M_max:
+            return res
+        U = [np.concatenate([U[d], init_column(prob, d, M, init, seed)[:, None]], axis=1)
+             for d in range(prob.D)]
+        M += 1
+
+
+# ---------------------------------------------------------------------------------
+# Evaluation (Eq. 13)
+# ---------------------------------------------------------------------------------
+def to_all_nodes(dim: Dim, Ud):
+    """Scatter free-node factor rows into all nodes (constrained nodes carry 0)."""
+    full = np.zeros((dim.n, Ud.shape[1]))
+    full[dim.free] = Ud
+    return full
+
+
+def eval_grid(prob: Problem, U, idx):
+    """u on the tensor grid of node indices idx[d] (all-node numbering), Eq. 7/13
+    at nodes (Kronecker delta: nodal value = factor entry).  C order output."""
+    rows = [to_all_nodes(prob.dims[d], U[d])[np.asarray(idx[d])] for d in range(prob.D)]
+    out = 0.0
+    for m in range(U[0].shape[1]):
+        out = out + kron_all([r[:, m].reshape(-1, 1) for r in rows]).reshape(-1)
+    return np.asarray(out).reshape([len(i) for i in idx])
+
+
+def eval_points(prob: Problem, U, pts):
+    """u^TD(x) = sum_m prod_d sum_I N~_I(x_d) U_d[I, m] at arbitrary points (Eq. 13)."""
+    pts = np.atleast_2d(np.asarray(pts, dtype=float))
+    out = np.zeros(len(pts))
+    full = [to_all_nodes(prob.dims[d], U[d]) for d in range(prob.D)]
+    for p_i, xp in enumerate(pts):
+        prod = np.ones(U[0].shape[1])
+        for d, dm in enumerate(prob.dims):
+            x = dm.x
+            e = locate(x, xp[d])
+            ids, N, _ = shape_functions(x, dm.s, dm.a, dm.p, e, xp[d])
+            prod = prod * (N @ full[d][ids])
+        out[p_i] = prod.sum()
+    return out
+
+
+# ---------------------------------------------------------------------------------
+# Problem descriptions (plain data from the seeded workload generators)
+# ---------------------------------------------------------------------------------
+OP_BY_NAME = {"K": OP_K, "M": OP_M, "G": OP_G, "W": OP_W, "Blo": OP_BLO, "Bhi": OP_BHI}
+
+
+def dim_from_description(dm):
+    return Dim(n=dm["n"], lo=dm["lo"], hi=dm["hi"], s=dm["s"], a=dm["a"], p=dm["p"],
+               n_quad=dm["n_quad"], dirichlet_lo=dm["dirichlet_lo"],
+               dirichlet_hi=dm["dirichlet_hi"], weight_poly=tuple(dm["weight_poly"]))
+
+
+def problem_from_description(desc):
+    dims = [dim_from_description(dm) for dm in desc["dims"]]
+    terms = [(a, [OP_BY_NAME[o] for o in ops]) for a, ops in desc["terms"]]
+    return build_problem(dims, terms, desc["sources"])
+
+
+def als_residual(prob: Problem, U):
+    """Relative residual of the coupled subspace system (Eq. 42): for every d,
+    r_d = K^[d](U_{e!=d}) U_d - Q^[d](U_{e!=d}) = sum_op Op_d U_d C_op^T - F_d,
+    evaluated with all factors at their current values; returns max_d ||r_d||/||F_d||."""
+    worst = 0.0
+    for d in range(prob.D):
+        C, F = coefficients(prob, U, d)
+        r = -F.copy()
+        for op, Cop in C.items():
+            r += prob.ops[d][op] @ U[d] @ Cop.T
+        nf = np.linalg.norm(F)
+        worst = max(worst, np.linalg.norm(r) / nf if nf > 0 else math.inf)
+    return worst

@@ -1,0 +1,144 @@
+"""Seeded synthetic workloads: problem descriptions as plain data.
+
+This module holds no arithmetic of the method.  It only draws the numbers that
+describe a problem (grid sizes, C-HiDeNN hyperparameters, operator terms, source
+parameters), so that the CUDA path and the independent CPU oracle can be fed the
+same input.  A description is a dict:
+
+    dims    : list of {kind, n, lo, hi, s, a, p, n_quad, dirichlet_lo, dirichlet_hi,
+                       weight_poly}
+    terms   : list of (alpha, [operator name per dim])      A = sum_t alpha_t (x)_d Op
+    sources : list of (beta, [(factor kind, params) per dim]) F = sum_r beta_r (x)_d q
+
+Operator names: 'K' stiffness, 'M' mass, 'G' time derivative, 'W' weighted mass
+(weight polynomial of the dim), 'Blo'/'Bhi' boundary point mass at the low/high end.
+Source factor kinds: ('const', (c,)), ('sin', (w, phase)) = sin(w x + phase),
+('gauss', (c, sigma)) = exp(-(x-c)^2/(2 sigma^2)), ('poly', (c0, c1, ...)),
+('nodal', values over all nodes).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SPACE, PARAM, TIME = 0, 1, 2
+
+
+def dim(n, lo=0.0, hi=1.0, *, kind=SPACE, s=2, a=20.0, p=2, n_quad=6,
+        dirichlet_lo=True, dirichlet_hi=True, weight_poly=(0.0, 0.0, 0.0, 0.0)):
+    w = tuple(float(c) for c in weight_poly) + (0.0,) * (4 - len(weight_poly))
+    return dict(kind=kind, n=int(n), lo=float(lo), hi=float(hi), s=int(s), a=float(a),
+                p=int(p), n_quad=int(n_quad), dirichlet_lo=bool(dirichlet_lo),
+                dirichlet_hi=bool(dirichlet_hi), weight_poly=w[:4])
+
+
+def poisson_sin(n=64, D=3, s=2, a=20.0, p=2, n_quad=6):
+    """-Laplace u = D pi^2 prod sin(pi x_d) on [0,1]^D, homogeneous Dirichlet.
+    Exact solution prod sin(pi x_d).  (3D, 64 nodes/dim, s,a,p = 2,20,2 is the plain
+    FP64 configuration; 16 nodes/dim is its brute-force case.)"""
+    dims = [dim(n, 0.0, 1.0, s=s, a=a, p=p, n_quad=n_quad) for _ in range(D)]
+    terms = [(1.0, ["K" if d == t else "M" for d in range(D)]) for t in range(D)]
+    sources = [(D * math.pi ** 2, [("sin", (math.pi, 0.0))] * D)]
+    return dict(name=f"poisson_sin_{D}d_n{n}", dims=dims, terms=terms, sources=sources)
+
+
+def gaussian_sources(rng, n_gauss, n_space):
+    """Seeded separable Gaussian bumps: amplitude U[0.5,2], width U[0.05,0.2],
+    centre U[0.2,0.8] per spatial dim."""
+    out = []
+    for _ in range(n_gauss):
+        A = rng.uniform(0.5, 2.0)
+        sig = rng.uniform(0.05, 0.2)
+        c = rng.uniform(0.2, 0.8, size=n_space)
+        out.append((float(A), float(sig), [float(ci) for ci in c]))
+    return out
+
+
+def poisson_k(n_space=256, n_k=32, seed=2000, s=2, a=20.0, p=2, n_gauss=4, k_lo=1.0,
+              k_hi=10.0):
+    """Space-parameter problem: -div(k grad u) = f on [0,1]^3 with the conductivity k in
+    [k_lo, k_hi] as a 4th independent dimension.  f = sum of n_gauss seeded separable
+    Gaussians (independent of k)."""
+    rng = np.random.default_rng(seed)
+    g = gaussian_sources(rng, n_gauss, 3)
+    dims = [dim(n_space, 0.0, 1.0, s=s, a=a, p=p) for _ in range(3)]
+    dims.append(dim(n_k, k_lo, k_hi, kind=PARAM, s=s, a=a, p=p, dirichlet_lo=False,
+                    dirichlet_hi=False, weight_poly=(0.0, 1.0)))
+    terms = [(1.0, ["K" if d == t else "M" for d in range(3)] + ["W"]) for t in range(3)]
+    sources = [(A, [("gauss", (c[d], sig)) for d in range(3)] + [("const", (1.0,))])
+               for A, sig, c in g]
+    return dict(name=f"poisson_k_{n_space}^3x{n_k}_seed{seed}", dims=dims, terms=terms,
+                sources=sources, params=g)
+
+
+def heat_transient(n_space=32, n_t=16, D_space=3, T=1.0, rho_cp=1.0, k=1.0, seed=3000,
+                   n_gauss=2, s=2, a=20.0, p=2, h_conv=0.0):
+    """rho c_p du/dt - k Laplace u = f on [0,1]^D_space x (0,T], zero initial condition,
+    homogeneous Dirichlet on the low/high faces of every spatial dim; with h_conv > 0
+    the high face of the last spatial dim is a convection (Robin) face instead.
+    f = seeded separable Gaussians in space times a linear ramp in time."""
+    rng = np.random.default_rng(seed)
+    g = gaussian_sources(rng, n_gauss, D_space)
+    dims = []
+    for d in range(D_space):
+        robin_hi = h_conv > 0 and d == D_space - 1
+        dims.append(dim(n_space, 0.0, 1.0, s=s, a=a, p=p, dirichlet_hi=not robin_hi))
+    dims.append(dim(n_t, 0.0, T, kind=TIME, s=s, a=a, p=p, dirichlet_lo=True,
+                    dirichlet_hi=False))
+    D = D_space + 1
+    terms = [(rho_cp, ["M"] * D_space + ["G"])]
+    for e in range(D_space):
+        terms.append((k, ["K" if d == e else "M" for d in range(D_space)] + ["M"]))
+    if h_conv > 0:
+        terms.append((h_conv, ["M"] * (D_space - 1) + ["Bhi", "M"]))
+    sources = [(A, [("gauss", (c[d], sig)) for d in range(D_space)] +
+                [("poly", (0.0, 1.0 / T))]) for A, sig, c in g]
+    return dict(name=f"heat_{D_space}d_n{n_space}_t{n_t}_seed{seed}", dims=dims,
+                terms=terms, sources=sources, params=g)
+
+
+def batch_instances(count=256, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32):
+    """Independent instances: D in {3..6}, n_d uniform in [n_lo, n_hi], a mode count
+    in [M_lo, M_hi], Poisson or transient (last dim time) 50/50, 1..4 separable
+    Gaussian sources.  Returns (descriptions, mode counts)."""
+    out, Ms = [], []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        D = int(rng.integers(3, 7))
+        transient = bool(rng.integers(0, 2))
+        ns = [int(v) for v in rng.integers(n_lo, n_hi + 1, size=D)]
+        M = int(rng.integers(M_lo, M_hi + 1))
+        Rf = int(rng.integers(1, 5))
+        Ds = D - 1 if transient else D
+        g = gaussian_sources(rng, Rf, Ds)
+        dims = [dim(ns[d], 0.0, 1.0) for d in range(Ds)]
+        if transient:
+            dims.append(dim(ns[-1], 0.0, 1.0, kind=TIME, dirichlet_lo=True,
+                            dirichlet_hi=False))
+            terms = [(1.0, ["M"] * Ds + ["G"])]
+            terms += [(1.0, ["K" if d == e else "M" for d in range(Ds)] + ["M"])
+                      for e in range(Ds)]
+            sources = [(A, [("gauss", (c[d], sig)) for d in range(Ds)] +
+                        [("const", (1.0,))]) for A, sig, c in g]
+        else:
+            terms = [(1.0, ["K" if d == e else "M" for d in range(D)]) for e in range(D)]
+            sources = [(A, [("gauss", (c[d], sig)) for d in range(D)]) for A, sig, c in g]
+        out.append(dict(name=f"batch_{seed + i}", dims=dims, terms=terms, sources=sources))
+        Ms.append(M)
+    return out, Ms
+
+
+def random_factors(desc, M, seed):
+    """Seeded U(-1,1) initial factors (one array per dim, free nodes x M), drawn with
+    numpy's generator; passed to both implementations as input."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for dm in desc["dims"]:
+        nf = dm["n"] - int(dm["dirichlet_lo"]) - int(dm["dirichlet_hi"])
+        out.append(rng.uniform(-1.0, 1.0, size=(nf, M)))
+    return out
+
+
+def n_free(dm):
+    return dm["n"] - int(dm["dirichlet_lo"]) - int(dm["dirichlet_hi"])
