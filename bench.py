@@ -1,0 +1,330 @@
+"""Benchmark: time to the relative residual 1e-6 of the TAPS subspace system (Eq. 42)
+on the space-parameter problem -div(k grad u) = f, 256^3 spatial nodes x 32 nodes of
+k in [1, 10], C-HiDeNN (s, a, p) = (2, 20, 2), M = 30 modes; then the full-grid
+reconstruction (256^3 x 32 values, FP32) on the device.
+
+Arms: our CUDA path (default) and `--impl reference` (the FP64 CPU oracle, on a
+bounded sample).  One JSON line on rank 0.  Under torchrun every rank solves its own
+seeded instance (replicas; weak scaling); times are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+# the CPU oracle legs run single-threaded (BLAS pinned to one thread before numpy loads)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n_space=256, n_k=32, M=30, seed=2000, res_tol=1e-6)
+METRIC = "time-to-rel.-residual 1e-6 vs plain FP64 GPU path; sweep HBM/TC roofline %"
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (recipe table); probe measured 1.20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-space", type=int, default=WORKLOAD["n_space"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as td
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        td.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def allmax(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None,
+                    sm_max_mhz=float(max(smax)) if smax else None,
+                    reasons=sorted(reasons), samples=len(self.rows))
+
+
+def oracle_sample(n_space, seed, M, sweeps_to_tol):
+    """Bounded CPU sample: the FP64 oracle (as it stands) does one subspace sweep plus
+    one Eq. 42 residual at full size from the seeded factors; the time to the
+    residual target is that per-sweep time times the sweep count of the FP64 path."""
+    from oracle import taps_oracle as O
+    from paper_2503_13933_gb300 import workloads as W
+    desc = W.poisson_k(n_space, WORKLOAD["n_k"], seed=seed)
+    P = O.problem_from_description(desc)
+    U = O.init_factors(P, M, "random", seed)
+    t0 = time.perf_counter()
+    U, _ = O.sweep(P, U)
+    O.als_residual(P, U)
+    dt = time.perf_counter() - t0
+    return dt, dt * sweeps_to_tol
+
+
+def oracle_sweeps_to_tol(n_space, seed, M):
+    """Sweeps the FP64 oracle needs from the seeded factors to the residual target."""
+    from oracle import taps_oracle as O
+    from paper_2503_13933_gb300 import workloads as W
+    P = O.problem_from_description(W.poisson_k(n_space, WORKLOAD["n_k"], seed=seed))
+    U = O.init_factors(P, M, "random", seed)
+    for it in range(60):
+        U, _ = O.sweep(P, U)
+        if O.als_residual(P, U) <= WORKLOAD["res_tol"]:
+            return it + 1
+    return 60
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    M, seed = WORKLOAD["M"], WORKLOAD["seed"]
+    steps = []
+    sweeps_to_tol = oracle_sweeps_to_tol(args.n_space, seed, M)
+    for i in range(args.warmup + args.steps):
+        dt, total = oracle_sample(args.n_space, seed, M, sweeps_to_tol)
+        if i >= args.warmup:
+            steps.append(total)
+    v = float(np.mean(steps))
+    line = dict(metric=METRIC, value=v, unit="s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=v * 1e3, higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=f"poisson_k {args.n_space}^3x{WORKLOAD['n_k']} M={M}",
+                            seed=seed, res_tol=WORKLOAD["res_tol"]),
+                cpu_baseline=dict(value=v, unit="s", cores=1, kind="oracle",
+                                  sample=f"1 FP64 oracle sweep + residual at full size per step, "
+                                         f"x{sweeps_to_tol} sweeps to the residual target"),
+                e2e=dict(value=v, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2503_13933_gb300 import taps
+    from paper_2503_13933_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    taps.lib()
+    M = WORKLOAD["M"]
+    seed = WORKLOAD["seed"] + rank
+    desc = W.poisson_k(args.n_space, WORKLOAD["n_k"], seed=seed)
+    P = taps.Problem(desc)
+    U = P.factors(M)
+    nk = WORKLOAD["n_k"]
+    count = [desc["dims"][d]["n"] for d in range(3)] + [nk]
+    total = int(np.prod(count))
+    field = torch.empty(total, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        """init (seeded SplitMix64 draws) -> sweeps to the residual target ->
+        reconstruction; returns (solve_ms, eval_ms, report)."""
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        rep = P.solve(U, M0=M, M_max=M, res_tol=WORKLOAD["res_tol"], res_kind=taps.RES_ALS,
+                      max_sweeps=60, precision=precision, polish_sweeps=30,
+                      init=taps.INIT_RANDOM, seed=seed, als_tol=0.0)
+        e1.record(stream)
+        P.eval_grid(U, [0, 0, 0, 0], count, [1, 1, 1, 1], field, dtype=taps.FP32)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), rep
+
+    paths = {"fp64": taps.FP64, "mixed": taps.FP32}
+    res = {}
+    for name, prec in paths.items():
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(prec)
+        P.profile_reset(events=True)
+        times, evals, reps = [], [], []
+        sampler = ClockSampler(local) if name == "mixed" else None
+        if sampler:
+            sampler.start()
+        for _ in range(args.steps):
+            flush.zero_()                         # L2 flush between timed steps
+            barrier(world)
+            torch.cuda.synchronize()
+            s_ms, ev_ms, rep = step(prec)
+            times.append(s_ms)
+            evals.append(ev_ms)
+            reps.append(rep)
+        clocks = sampler.stop() if sampler else None
+        prof = P.profile()
+        res[name] = dict(solve_ms=float(np.mean(times)), eval_ms=float(np.mean(evals)),
+                         sweeps=reps[-1]["sweeps"], fp64_sweeps=reps[-1]["fp64_sweeps"],
+                         rho=reps[-1]["rho"], rho_full=reps[-1]["rho_full"],
+                         converged=all(r["converged"] for r in reps), prof=prof, clocks=clocks)
+
+    # end to end through the public API with host buffers: problem set-up from the
+    # host description, seeded initial factors copied in, solve, factors copied out.
+    U0 = W.random_factors(desc, M, seed=seed)
+    h2d = sum(u.nbytes for u in U0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P2 = taps.Problem(desc)
+    U2 = P2.factors(M)
+    U2.set(U0)
+    rep2 = P2.solve(U2, M_max=M, res_tol=WORKLOAD["res_tol"], res_kind=taps.RES_ALS,
+                    max_sweeps=60, precision=taps.FP32, polish_sweeps=30, init=taps.INIT_GIVEN,
+                    als_tol=0.0)
+    Uout = U2.get()
+    e2e_s = time.perf_counter() - t0
+    d2h = sum(u.nbytes for u in Uout) + 8
+
+    best = min(res, key=lambda k: res[k]["solve_ms"])
+    value_s = allmax(res[best]["solve_ms"], world) / 1e3
+    step_ms = allmax(res[best]["solve_ms"] + res[best]["eval_ms"], world)
+    e2e_s = allmax(e2e_s, world)
+    prof = res[best]["prof"]
+    dom = max((k for k in prof if prof[k]["ms"] > 0), key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    if dom in ("eval",):
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        roof = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
+                    frac=achieved / peak, traffic=None, kernel=dom,
+                    per_launch_ms=per_launch_ms, peak_source="measured (MEASURED_PEAKS.json hbm_gbs)")
+    else:
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roof = dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=achieved / FP64_PEAK_TFLOPS, traffic=None, kernel=dom,
+                    per_launch_ms=per_launch_ms,
+                    peak_source="FP64 nominal 1.25 TFLOP/s (recipe table); DFMA probe 1.20")
+    ev = prof["eval"]
+    hbm_peak = 6780.7
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    eval_gbs = ev["bytes"] / (ev["ms"] * 1e-3) / 1e9 if ev["ms"] > 0 else None
+    launches = sum(v["launches"] for v in prof.values()) // max(args.steps, 1)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, total_s = oracle_sample(args.n_space, seed, M, res["fp64"]["sweeps"])
+        cpu = dict(value=total_s, unit="s", cores=1, kind="oracle",
+                   sample=f"1 FP64 oracle sweep + Eq. 42 residual at full size ({dt:.3f} s), "
+                          f"x{res['fp64']['sweeps']} sweeps (the FP64 path's count)")
+    if rank != 0:
+        return
+    line = dict(
+        metric=METRIC, value=value_s, unit="s", n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=step_ms, higher_is_better=False, scaling="weak",
+        vs_baseline=None, dtype="f64+f32", data="synthetic",
+        config=dict(workload=f"poisson_k {args.n_space}^3x{WORKLOAD['n_k']} M={M}, "
+                             f"time to Eq. 42 residual {WORKLOAD['res_tol']} + full-grid FP32 "
+                             f"reconstruction", seed=WORKLOAD["seed"], l2="flushed (256 MB write)",
+                    path=best, parallelism="replicas"),
+        paths={k: dict(solve_ms=v["solve_ms"], eval_ms=v["eval_ms"], sweeps=v["sweeps"],
+                       fp64_sweeps=v["fp64_sweeps"], rho=v["rho"], rho_full=v["rho_full"],
+                       converged=v["converged"]) for k, v in res.items()},
+        speedup_vs_fp64=res["fp64"]["solve_ms"] / res[best]["solve_ms"],
+        roofline=roof,
+        roofline_eval=dict(bound="hbm", achieved=eval_gbs, peak=hbm_peak, unit="GB/s",
+                           frac=(eval_gbs / hbm_peak) if eval_gbs else None,
+                           bytes_per_launch=ev["bytes"] / max(ev["launches"], 1)),
+        kernels={k: dict(launches=v["launches"] // max(args.steps, 1),
+                         ms_per_step=v["ms"] / max(args.steps, 1)) for k, v in prof.items()},
+        cpu_baseline=cpu,
+        e2e=dict(value=e2e_s, unit="s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                 converged=rep2["converged"]),
+        gpu_launches=launches,
+        clocks=res["mixed"]["clocks"],
+    )
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

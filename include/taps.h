@@ -1,0 +1,281 @@
+/*
+ * taps.h -- C ABI of the GB300 (sm_103a) TAPS hot path.
+ *
+ * TAPS (Tensor-decomposition-based A Priori Surrogate) solves a space-parameter-time
+ * PDE in CP form u(x) = sum_m prod_d sum_I N~_I(x_d) U_d[I, m] (Eq. 13) by Galerkin
+ * projection (Eq. 25) onto 1D C-HiDeNN shape functions (Eq. 1) and the subspace
+ * iteration of Algorithm 1 (Eq. 43).  This library runs every step on one GPU:
+ * 1D assembly, the per-dimension Gram contractions, the coefficient (Hadamard)
+ * combine, the n_d*M block-banded reduced solve, normalisation, residuals and
+ * reconstruction.
+ *
+ * Conventions used by every entry point
+ *   - All functions return an int status: TAPS_OK (0) or a negative TAPS_ERR_*.
+ *     No entry point aborts or traps; device-side failures (zero pivot, non-finite
+ *     value, a bounded wait that ran out) are reported through the status.
+ *   - Host pointers are read during the call only; the caller keeps ownership.
+ *   - Objects (taps_dim, taps_problem, taps_factors) are opaque, library-owned and
+ *     device-resident until their *_destroy call.  They are bound to the CUDA device
+ *     that was current at creation and to the stream given at creation; every
+ *     kernel of an object is launched on that stream.  Calls are synchronous with
+ *     respect to the host unless stated otherwise.
+ *   - Factor matrices U_d are n_free(d) x M, column-major (mode m is contiguous),
+ *     FP64, free nodes only (Dirichlet / zero-initial-condition nodes are dropped:
+ *     the Kronecker delta of Eq. 3 makes their value the boundary value, here 0).
+ *   - Band storage of a 1D matrix over the free nodes: row-major n_free x (2*hb+1),
+ *     entry (i, k) holds Op[i, i + k - hb], zero where the column is not a free node;
+ *     hb = 2*s + 1 (shape functions of nodes more than 2s+1 apart share no element).
+ */
+#ifndef TAPS_H
+#define TAPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TAPS_MAX_DIMS 8
+#define TAPS_MAX_S 4       /* patch size s <= 4 */
+#define TAPS_MAX_P 3       /* reproducing order p <= 3 */
+#define TAPS_MAX_QUAD 12   /* Gauss points per element */
+#define TAPS_MAX_M 128     /* modes per factor */
+#define TAPS_MAX_TERMS 64  /* operator terms R and source terms R_f, each */
+
+/* ---- status codes ---------------------------------------------------------- */
+#define TAPS_OK 0
+#define TAPS_ERR_INVALID_ARG (-1)   /* bad size, kind, pointer, or a patch with < p+1 nodes */
+#define TAPS_ERR_SINGULAR (-2)      /* zero / non-finite pivot in a reduced or patch solve */
+#define TAPS_ERR_NONFINITE (-3)     /* NaN or Inf in a result */
+#define TAPS_ERR_NOT_CONVERGED (-4) /* tolerance not met in the allowed sweeps (result kept) */
+#define TAPS_ERR_TIMEOUT (-5)       /* a bounded device-side wait ran out */
+#define TAPS_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define TAPS_ERR_OOM (-7)           /* device allocation failed */
+
+/* ---- dimension kinds (Eq. 11: spatial, parametric, temporal variables) ------ */
+#define TAPS_SPACE 0
+#define TAPS_PARAM 1
+#define TAPS_TIME 2
+
+/* ---- 1D operator kinds (Sec. 2.5, Eqs. 31-35) -------------------------------- */
+#define TAPS_OP_K 0    /* stiffness      K_ij = int B~_i B~_j                          */
+#define TAPS_OP_M 1    /* mass           M_ij = int N~_i N~_j                          */
+#define TAPS_OP_G 2    /* time deriv.    G_ij = int N~_i B~_j   (test i, trial j)      */
+#define TAPS_OP_W 3    /* weighted mass  W_ij = int N~_i w(x) N~_j, w = weight_poly    */
+#define TAPS_OP_BLO 4  /* point mass at the low end  (convection face, Eqs. 21/25)     */
+#define TAPS_OP_BHI 5  /* point mass at the high end                                   */
+#define TAPS_NUM_OPS 6
+
+/* ---- source factor kinds g(x) of a separable source term -------------------- */
+#define TAPS_SRC_CONST 0  /* par[0]                                       */
+#define TAPS_SRC_SIN 1    /* sin(par[0] * x + par[1])                     */
+#define TAPS_SRC_GAUSS 2  /* exp(-(x - par[0])^2 / (2 par[1]^2))          */
+#define TAPS_SRC_POLY 3   /* par[0] + par[1] x + par[2] x^2 + par[3] x^3  */
+#define TAPS_SRC_NODAL 4  /* C-HiDeNN interpolant of nodal values (all nodes) */
+
+/* ---- precisions of the Gram / SpMM contractions (reduced solves stay FP64) --- */
+#define TAPS_FP64 0
+#define TAPS_FP32 1
+
+/* ---- residual kinds ----------------------------------------------------------- */
+#define TAPS_RES_ALS 0   /* max_d ||K^[d] U_d - Q^[d]|| / ||Q^[d]|| of Eq. 42           */
+#define TAPS_RES_FULL 1  /* ||F - A u||_2 / ||F||_2 over the free tensor-grid unknowns   */
+
+/* ---- initialisation of factor columns ---------------------------------------- */
+#define TAPS_INIT_GIVEN 0   /* start from the factors as they are (taps_factors_set) */
+#define TAPS_INIT_RANDOM 1  /* U(-1,1), SplitMix64 counter-based draws (seed, d, i, m) */
+#define TAPS_INIT_ZERO 2    /* new column: 0 in the first dim, 1 elsewhere            */
+
+/* ---- reduced solvers ---------------------------------------------------------- */
+#define TAPS_SOLVER_BLOCK_LU 0   /* block-banded Gaussian elimination, FP64 */
+
+typedef struct taps_dim taps_dim;
+typedef struct taps_problem taps_problem;
+typedef struct taps_factors taps_factors;
+
+/* One independent dimension (Eq. 11) on n uniform nodes over [lo, hi] with
+ * C-HiDeNN hyperparameters s (patch size), a (dilation), p (reproducing order)
+ * of Eq. 1, n_quad Gauss points per element (Table 1: Gaussian integration).
+ * dirichlet_lo/hi = 1 drops that end node (homogeneous Dirichlet, or the zero
+ * initial condition of a time dimension).  weight_poly gives w(x) of TAPS_OP_W. */
+typedef struct {
+  int kind;
+  int n;
+  double lo, hi;
+  int s;
+  double a;
+  int p;
+  int n_quad;
+  int dirichlet_lo, dirichlet_hi;
+  double weight_poly[4];
+} taps_dim_desc;
+
+/* One operator term alpha * (x)_d Op_d of A (the separated integrals of Eq. 33). */
+typedef struct {
+  double alpha;
+  int op[TAPS_MAX_DIMS];
+} taps_term;
+
+/* One separable source term beta * (x)_d g_d; q_{r,d} = int N~ g_d (Eq. 30 forcing). */
+typedef struct {
+  double beta;
+  int kind[TAPS_MAX_DIMS];
+  double par[TAPS_MAX_DIMS][4];
+  const double* nodal[TAPS_MAX_DIMS]; /* TAPS_SRC_NODAL: host array of n values */
+} taps_source;
+
+typedef struct {
+  int precision;     /* TAPS_FP64 | TAPS_FP32 (Gram and SpMM contractions) */
+  int solver;        /* TAPS_SOLVER_* */
+  int normalize;     /* 1: unit-norm columns for d < D after each solve (default 1) */
+} taps_sweep_opts;
+
+typedef struct {
+  int sweeps;          /* sweeps performed */
+  double change;       /* max_d ||U_d^new - U_d^old||_F / ||U_d^new||_F of the last sweep */
+  double seconds;      /* wall time of the call */
+} taps_sweep_report;
+
+typedef struct {
+  int M0, M_max;       /* first and last mode count of the greedy schedule */
+  double als_tol;      /* per-M stop on the factor change (Sec. 2.6 convergence check) */
+  double res_tol;      /* stop once the residual of kind res_kind is <= res_tol */
+  int res_kind;        /* TAPS_RES_* */
+  int max_sweeps;      /* per mode count */
+  int precision;       /* TAPS_FP64 | TAPS_FP32 for the sweeps */
+  int polish_sweeps;   /* FP64 sweeps allowed after an FP32 phase stalls (refinement) */
+  int solver;          /* TAPS_SOLVER_* */
+  int init;            /* TAPS_INIT_* for the columns added by the schedule */
+  unsigned seed;       /* seed of TAPS_INIT_RANDOM */
+  int history_cap;     /* capacity of the report's history arrays (0: none) */
+} taps_solve_opts;
+
+typedef struct {
+  int M;               /* final mode count */
+  int sweeps;          /* total sweeps */
+  int fp64_sweeps;     /* of which FP64 */
+  double rho;          /* final residual of kind res_kind */
+  double rho_full;     /* final ||F - A u|| / ||F|| */
+  double change;       /* last factor change */
+  double seconds;      /* wall time of the solve */
+  int converged;       /* 1 if rho <= res_tol */
+  /* optional per-sweep history, caller-owned host arrays of history_cap entries */
+  int* hist_M;
+  double* hist_change;
+  double* hist_rho;
+  int hist_len;
+} taps_solve_report;
+
+/* ---- status ------------------------------------------------------------------- */
+const char* taps_status_string(int status);
+int taps_version(void);
+
+/* ---- 1D assembly (Eq. 1 shape functions; Eqs. 31-35 matrices; Table 1 quadrature)
+ * Builds, on the device, the C-HiDeNN patch inverses of every node, the shape
+ * function tables at the Gauss points of every element and the banded matrices of
+ * all TAPS_NUM_OPS kinds over the free nodes.  `stream` is a cudaStream_t (NULL:
+ * legacy default stream).  Errors: TAPS_ERR_INVALID_ARG for n < 2, s > TAPS_MAX_S,
+ * p > TAPS_MAX_P, n_quad outside [1, TAPS_MAX_QUAD], hi <= lo, or an end patch with
+ * fewer than p+1 nodes; TAPS_ERR_SINGULAR if a patch moment matrix is singular. */
+int taps_assemble_1d(const taps_dim_desc* desc, void* stream, taps_dim** out);
+/* Sizes of an assembled dimension: all nodes, free nodes, band half-width hb. */
+int taps_dim_info(const taps_dim* dim, int* n_all, int* n_free, int* half_band);
+/* Copy the band of operator `op` (n_free x (2hb+1), row-major, FP64) to host memory. */
+int taps_dim_copy_band(const taps_dim* dim, int op, double* host_out);
+/* Copy the shape tables (Eq. 1) to host memory: N and dN/dx at every Gauss point of
+ * every element, layout [n-1][n_quad][2s+2] with local node k <-> global e - s + k
+ * (entries of nodes outside [0, n) are 0), plus the Gauss abscissae x [n-1][n_quad]. */
+int taps_dim_copy_shape(const taps_dim* dim, double* N_out, double* B_out, double* x_out);
+void taps_dim_destroy(taps_dim* dim);
+
+/* ---- problem: A = sum_t alpha_t (x)_d Op[t][d], F = sum_r beta_r (x)_d q_{r,d}
+ * (the separated Galerkin operator and force of Eqs. 33-41).  `dims` are assembled
+ * dimensions (the problem keeps pointers: they must outlive it).  Source projections
+ * q_{r,d} are computed on the device.  Errors: TAPS_ERR_INVALID_ARG for D outside
+ * [1, TAPS_MAX_DIMS], R or Rf outside [1, TAPS_MAX_TERMS], an operator or source kind
+ * out of range, or a NULL nodal array. */
+int taps_problem_create(taps_dim* const* dims, int D, const taps_term* terms, int R,
+                        const taps_source* sources, int Rf, void* stream,
+                        taps_problem** out);
+/* Copy q_{r,d} (n_free(d) FP64 values) to host memory. */
+int taps_problem_copy_source(const taps_problem* prob, int r, int d, double* host_out);
+void taps_problem_destroy(taps_problem* prob);
+
+/* ---- factors: D device matrices U_d (n_free(d) x M, column-major, FP64; Eq. 7) --- */
+int taps_factors_create(const taps_problem* prob, int M_cap, taps_factors** out);
+/* Set M (<= M_cap) and copy host_U[d] (n_free(d) x M column-major) to the device. */
+int taps_factors_set(taps_factors* U, int M, const double* const* host_U);
+/* Copy the current factors to host_U[d] (n_free(d) x M column-major each). */
+int taps_factors_get(const taps_factors* U, double* const* host_U);
+int taps_factors_M(const taps_factors* U);
+/* Device pointer of U_d (n_free(d) x M_cap storage, leading dimension n_free(d)). */
+const double* taps_factors_device_ptr(const taps_factors* U, int d);
+void taps_factors_destroy(taps_factors* U);
+
+/* ---- sweeps (Algorithm 1 inner loop, Eq. 43) ------------------------------------
+ * Runs n_sweeps sweeps over d = 1..D: coefficient matrices C_op = Hadamard products
+ * of the other dimensions' Grams U_e^T Op U_e (Eq. 34/35), force F_d, block-banded
+ * reduced solve sum_op Op_d U_d C_op^T = F_d, normalisation of U_d (d < D), Gram
+ * refresh of dim d.  opts may be NULL (FP64, block LU, normalise).  Errors:
+ * TAPS_ERR_SINGULAR (zero or non-finite pivot; factors then undefined),
+ * TAPS_ERR_TIMEOUT, TAPS_ERR_CUDA. */
+int taps_sweep(taps_problem* prob, taps_factors* U, int n_sweeps, const taps_sweep_opts* opts,
+               taps_sweep_report* rep);
+
+/* ---- residuals (FP64) ---------------------------------------------------------
+ * kind TAPS_RES_ALS: max over d of ||sum_op Op_d U_d C_op^T - F_d||_F / ||F_d||_F
+ * with all factors at their current values (the residual of the coupled system
+ * Eq. 42).  kind TAPS_RES_FULL: ||F - A u||_2 / ||F||_2 by the Gram identity
+ * ||F||^2 - 2 F^T A u + ||A u||^2, each a sum of products of 1D inner products
+ * (cancellation limits it to about 1e-8 relative). */
+int taps_residual(taps_problem* prob, const taps_factors* U, int kind, double* rho_out);
+
+/* ---- solve: greedy mode schedule M0..M_max with sweeps to tolerance ----------------
+ * For each M: sweep until rho (kind res_kind) <= res_tol or the factor change <=
+ * als_tol or max_sweeps; then stop if rho <= res_tol, else append one column per
+ * factor (init rule) and continue.  With precision TAPS_FP32 the sweeps use FP32
+ * Grams; once the FP32 sweeps stop improving, up to polish_sweeps FP64 sweeps
+ * refine the result to FP64 accuracy.  U must have M_cap >= M_max; with init
+ * TAPS_INIT_GIVEN its current M columns are the start (M0 is then ignored), else it
+ * is reset to M0 columns drawn by the init rule.  Returns TAPS_ERR_NOT_CONVERGED if
+ * the tolerance is not met (factors and report are still valid). */
+int taps_solve(taps_problem* prob, taps_factors* U, const taps_solve_opts* opts,
+               taps_solve_report* rep);
+
+/* ---- evaluation (Eq. 13) -------------------------------------------------------
+ * Grid: u on the tensor grid of node slices idx_d = start[d] + step[d] * j,
+ * j < count[d] (all-node numbering; constrained nodes are 0).  out_dev is caller-
+ * owned device memory of prod count[d] values, C order (last dim fastest), dtype
+ * out_dtype (TAPS_FP64: double, TAPS_FP32: float).  Asynchronous on the problem's
+ * stream.  Errors: TAPS_ERR_INVALID_ARG for an index outside [0, n). */
+int taps_eval_grid(const taps_problem* prob, const taps_factors* U, const int* start,
+                   const int* count, const int* step, void* out_dev, int out_dtype);
+/* Points: u^TD(x) = sum_m prod_d sum_I N~_I(x_d) U_d[I, m] at n_pts points; pts_dev is
+ * device memory [n_pts][D] row-major (coordinates clamped to [lo, hi]); out_dev
+ * receives n_pts FP64 values.  Asynchronous on the problem's stream. */
+int taps_eval_points(const taps_problem* prob, const taps_factors* U, int n_pts,
+                     const double* pts_dev, double* out_dev);
+
+/* ---- profiling: per kernel class, CUDA events on the problem's stream ----------
+ * taps_profile_reset clears the counters; with enable_events = 1 every launch of a
+ * class is bracketed by CUDA events (read back at the library's own stream
+ * synchronisation points).  Launch counts are kept whether or not events are on.
+ * taps_profile_get returns, for one class, the launches, the summed device time in
+ * milliseconds (events only) and the algorithmic FP64/FP32 flops and DRAM bytes the
+ * launches were charged with (the roofline numerators). */
+#define TAPS_PROF_GRAM 0          /* fused banded SpMM + Gram (partial + reduce)   */
+#define TAPS_PROF_COEFF 1         /* Hadamard coefficient combine                   */
+#define TAPS_PROF_BLOCK_ASSEMBLE 2 /* reduced block band + right-hand side          */
+#define TAPS_PROF_BLOCK_LU 3      /* cooperative block-banded elimination           */
+#define TAPS_PROF_BACKSUB 4       /* block back substitution                        */
+#define TAPS_PROF_NORMALIZE 5     /* column normalisation + factor change           */
+#define TAPS_PROF_RESIDUAL 6      /* residual kernels                               */
+#define TAPS_PROF_EVAL 7          /* grid reconstruction                            */
+#define TAPS_PROF_OTHER 8         /* initialisation, copies                         */
+#define TAPS_PROF_NUM 9
+int taps_profile_reset(taps_problem* prob, int enable_events);
+int taps_profile_get(taps_problem* prob, int kernel_class, long long* launches, double* ms,
+                     double* flops, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TAPS_H */

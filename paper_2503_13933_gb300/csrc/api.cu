@@ -1,0 +1,658 @@
+// C ABI: problem and factor objects, sweeps, greedy solve (Algorithm 1 with a growing
+// mode count), residuals and grid reconstruction (Eq. 13).
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "taps_internal.cuh"
+
+int taps_project_source(const taps_dim* d, int kind, const double* par, const double* nodal_host,
+                        double* d_q_free, cudaStream_t s);
+
+int taps_sweep_setup(int dev, int num_sms, int* coop_blocks);
+
+// ---------------------------------------------------------------------------------
+// Profiling: launch counts always; CUDA events around launches when enabled.
+// ---------------------------------------------------------------------------------
+int prof_begin(taps_problem* P, int cls) {
+  ProfState* S = P->prof;
+  if (!S) return -1;
+  S->launches[cls] += 1;
+  if (!S->events) return -1;
+  if (S->npending >= 512) {
+    cudaStreamSynchronize(P->stream);
+    prof_drain(P);
+  }
+  if (S->npool < 2) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1;
+    S->pool[S->npool++] = a;
+    S->pool[S->npool++] = b;
+  }
+  ProfPending& pp = S->pending[S->npending];
+  pp.cls = cls;
+  pp.b = S->pool[--S->npool];
+  pp.a = S->pool[--S->npool];
+  cudaEventRecord(pp.a, P->stream);
+  return S->npending++;
+}
+
+void prof_end(taps_problem* P, int cls, int token, double flops, double bytes) {
+  ProfState* S = P->prof;
+  if (!S) return;
+  S->flops[cls] += flops;
+  S->bytes[cls] += bytes;
+  if (token >= 0) cudaEventRecord(S->pending[token].b, P->stream);
+}
+
+// Read back the elapsed times of all pending launches (the stream has been
+// synchronised by the caller) and return the events to the pool.
+void prof_drain(taps_problem* P) {
+  ProfState* S = P->prof;
+  if (!S) return;
+  for (int i = 0; i < S->npending; ++i) {
+    ProfPending& pp = S->pending[i];
+    float ms = 0.f;
+    if (cudaEventSynchronize(pp.b) == cudaSuccess && cudaEventElapsedTime(&ms, pp.a, pp.b) == cudaSuccess)
+      S->ms[pp.cls] += ms;
+    if (S->npool + 2 <= 1024) {
+      S->pool[S->npool++] = pp.a;
+      S->pool[S->npool++] = pp.b;
+    } else {
+      cudaEventDestroy(pp.a);
+      cudaEventDestroy(pp.b);
+    }
+  }
+  S->npending = 0;
+}
+
+extern "C" int taps_profile_reset(taps_problem* P, int enable_events) {
+  if (!P || !P->prof) return TAPS_ERR_INVALID_ARG;
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  prof_drain(P);
+  ProfState* S = P->prof;
+  for (int c = 0; c < TAPS_PROF_NUM; ++c) {
+    S->launches[c] = 0;
+    S->ms[c] = S->flops[c] = S->bytes[c] = 0.0;
+  }
+  S->events = enable_events != 0;
+  return TAPS_OK;
+}
+
+extern "C" int taps_profile_get(taps_problem* P, int cls, long long* launches, double* ms,
+                                double* flops, double* bytes) {
+  if (!P || !P->prof || cls < 0 || cls >= TAPS_PROF_NUM) return TAPS_ERR_INVALID_ARG;
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  prof_drain(P);
+  ProfState* S = P->prof;
+  if (launches) *launches = S->launches[cls];
+  if (ms) *ms = S->ms[cls];
+  if (flops) *flops = S->flops[cls];
+  if (bytes) *bytes = S->bytes[cls];
+  return TAPS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Problem
+// ---------------------------------------------------------------------------------
+static void free_ws(taps_problem* P) {
+  for (int d = 0; d < TAPS_MAX_DIMS; ++d) {
+    cudaFree(P->d_gram[d]);
+    cudaFree(P->d_h[d]);
+    P->d_gram[d] = P->d_h[d] = nullptr;
+  }
+  for (int d = 0; d < TAPS_MAX_DIMS; ++d) {
+    cudaFree(P->d_Usnap[d]);
+    P->d_Usnap[d] = nullptr;
+  }
+  cudaFree(P->d_C);
+  cudaFree(P->d_c);
+  cudaFree(P->d_F);
+  cudaFree(P->d_blocks);
+  cudaFree(P->d_lu);
+  cudaFree(P->d_Y);
+  cudaFree(P->d_Uold);
+  cudaFree(P->d_partial);
+  cudaFree(P->d_scal);
+  cudaFree(P->d_bigG);
+  if (P->h_scal) cudaFreeHost(P->h_scal);
+  P->d_C = P->d_c = P->d_F = P->d_blocks = P->d_lu = P->d_Y = P->d_Uold = nullptr;
+  P->d_partial = P->d_scal = P->d_bigG = P->h_scal = nullptr;
+  P->ws_M = 0;
+}
+
+extern "C" void taps_problem_destroy(taps_problem* P) {
+  if (!P) return;
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  free_ws(P);
+  for (int d = 0; d < TAPS_MAX_DIMS; ++d) {
+    cudaFree(P->d_q[d]);
+    cudaFree(P->d_opband[d]);
+  }
+  cudaFree(P->d_status);
+  cudaFree(P->d_bar);
+  cudaFree(P->d_evalbuf);
+  if (P->prof) {
+    for (int i = 0; i < P->prof->npending; ++i) {
+      cudaEventDestroy(P->prof->pending[i].a);
+      cudaEventDestroy(P->prof->pending[i].b);
+    }
+    for (int i = 0; i < P->prof->npool; ++i) cudaEventDestroy(P->prof->pool[i]);
+    delete P->prof;
+  }
+  delete P;
+}
+
+int taps_ws_ensure(taps_problem* P, int M) {
+  if (M <= P->ws_M) return TAPS_OK;
+  if (P->stream) TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  free_ws(P);
+  int nbmax = 0, D = P->D;
+  size_t part = 0, bigG = 0;
+  for (int d = 0; d < D; ++d) {
+    const taps_dim* dm = P->dims[d];
+    int nops = P->tt.nops[d];
+    nbmax = std::max(nbmax, dm->nb);
+    TAPS_TRY(taps_alloc((void**)&P->d_gram[d], sizeof(double) * nops * M * M));
+    TAPS_TRY(taps_alloc((void**)&P->d_h[d], sizeof(double) * P->Rf * M));
+    TAPS_TRY(taps_alloc((void**)&P->d_Usnap[d], sizeof(double) * dm->nf * M));
+    size_t gp = (size_t)((dm->nf + 15) / 16) * (nops * M * M + P->Rf * M);
+    part = std::max(part, gp);
+    size_t NC = (size_t)nops * M + P->Rf;
+    bigG += NC * NC;
+  }
+  size_t als_part = 0;
+  for (int d = 0; d < D; ++d) als_part += 2 * (((size_t)P->dims[d]->nf * M + 255) / 256);
+  part = std::max(part, als_part);
+  part = std::max(part, (size_t)3 * 64);
+  size_t MM = (size_t)M * M;
+  int nfm = P->nf_max;
+  TAPS_TRY(taps_alloc((void**)&P->d_C, sizeof(double) * TAPS_NUM_OPS * MM));
+  TAPS_TRY(taps_alloc((void**)&P->d_c, sizeof(double) * P->Rf * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_F, sizeof(double) * nfm * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_blocks, sizeof(double) * nfm * nbmax * MM));
+  TAPS_TRY(taps_alloc((void**)&P->d_lu, sizeof(double) * MM));
+  TAPS_TRY(taps_alloc((void**)&P->d_Y, sizeof(double) * TAPS_NUM_OPS * nfm * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_Uold, sizeof(double) * nfm * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_partial, sizeof(double) * part));
+  TAPS_TRY(taps_alloc((void**)&P->d_scal, sizeof(double) * 2 * M * D + 64));
+  TAPS_TRY(taps_alloc((void**)&P->d_bigG, sizeof(double) * bigG));
+  TAPS_CUDA(cudaMallocHost((void**)&P->h_scal, sizeof(double) * (2 * M * D + 64)));
+  P->partial_len = part;
+  P->bigG_len = bigG;
+  P->ws_M = M;
+  return TAPS_OK;
+}
+
+extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term* terms, int R,
+                                   const taps_source* sources, int Rf, void* stream,
+                                   taps_problem** out) {
+  if (!out) return TAPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!dims || !terms || !sources || D < 1 || D > TAPS_MAX_DIMS || R < 1 || R > TAPS_MAX_TERMS ||
+      Rf < 1 || Rf > TAPS_MAX_TERMS)
+    return TAPS_ERR_INVALID_ARG;
+  for (int d = 0; d < D; ++d)
+    if (!dims[d]) return TAPS_ERR_INVALID_ARG;
+  for (int t = 0; t < R; ++t)
+    for (int d = 0; d < D; ++d)
+      if (terms[t].op[d] < 0 || terms[t].op[d] >= TAPS_NUM_OPS) return TAPS_ERR_INVALID_ARG;
+  for (int r = 0; r < Rf; ++r)
+    for (int d = 0; d < D; ++d) {
+      int k = sources[r].kind[d];
+      if (k < TAPS_SRC_CONST || k > TAPS_SRC_NODAL) return TAPS_ERR_INVALID_ARG;
+      if (k == TAPS_SRC_NODAL && !sources[r].nodal[d]) return TAPS_ERR_INVALID_ARG;
+    }
+  taps_problem* P = new taps_problem();
+  memset((void*)P, 0, sizeof(taps_problem));
+  P->D = D;
+  P->R = R;
+  P->Rf = Rf;
+  P->stream = (cudaStream_t)stream;
+  P->prof = new ProfState();
+  memset((void*)P->prof, 0, sizeof(ProfState));
+  P->tt.D = D;
+  P->tt.R = R;
+  P->tt.Rf = Rf;
+  // Distinct operator slots per dim, in order of first appearance in the terms.
+  for (int d = 0; d < D; ++d) {
+    P->dims[d] = dims[d];
+    P->nf_max = std::max(P->nf_max, dims[d]->nf);
+    int n = 0;
+    for (int t = 0; t < R; ++t) {
+      int op = terms[t].op[d], slot = -1;
+      for (int j = 0; j < n; ++j)
+        if (P->ops[d][j] == op) slot = j;
+      if (slot < 0) {
+        slot = n;
+        P->ops[d][n++] = op;
+      }
+      P->tt.oi[t][d] = (signed char)slot;
+    }
+    P->tt.nops[d] = n;
+  }
+  for (int t = 0; t < R; ++t) P->tt.alpha[t] = terms[t].alpha;
+  for (int r = 0; r < Rf; ++r) P->tt.beta[r] = sources[r].beta;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  int st = TAPS_OK;
+  do {
+    if ((st = taps_alloc((void**)&P->d_status, sizeof(int))) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&P->d_bar, 2 * sizeof(unsigned))) != TAPS_OK) break;
+    if (cudaMemsetAsync(P->d_status, 0, sizeof(int), P->stream) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+    for (int d = 0; d < D && st == TAPS_OK; ++d) {
+      const taps_dim* dm = dims[d];
+      int nops = P->tt.nops[d];
+      size_t bandsz = (size_t)dm->nf * dm->nb;
+      if ((st = taps_alloc((void**)&P->d_opband[d], sizeof(double) * nops * bandsz)) != TAPS_OK) break;
+      for (int j = 0; j < nops; ++j)
+        if (cudaMemcpyAsync(P->d_opband[d] + j * bandsz, dm->d_band + (size_t)P->ops[d][j] * bandsz,
+                            sizeof(double) * bandsz, cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess)
+          st = TAPS_ERR_CUDA;
+      if (st != TAPS_OK) break;
+      if ((st = taps_alloc((void**)&P->d_q[d], sizeof(double) * Rf * dm->nf)) != TAPS_OK) break;
+      for (int r = 0; r < Rf && st == TAPS_OK; ++r)
+        st = taps_project_source(dm, sources[r].kind[d], sources[r].par[d], sources[r].nodal[d],
+                                 P->d_q[d] + (size_t)r * dm->nf, P->stream);
+    }
+    if (st != TAPS_OK) break;
+    if ((st = taps_sweep_setup(dev, P->num_sms, &P->coop_blocks)) != TAPS_OK) break;
+    st = taps_check_status(P->d_status, P->stream);
+  } while (0);
+  if (st != TAPS_OK) {
+    taps_problem_destroy(P);
+    return st;
+  }
+  *out = P;
+  return TAPS_OK;
+}
+
+extern "C" int taps_problem_copy_source(const taps_problem* P, int r, int d, double* host_out) {
+  if (!P || !host_out || r < 0 || r >= P->Rf || d < 0 || d >= P->D) return TAPS_ERR_INVALID_ARG;
+  int nf = P->dims[d]->nf;
+  TAPS_CUDA(cudaMemcpyAsync(host_out, P->d_q[d] + (size_t)r * nf, sizeof(double) * nf,
+                            cudaMemcpyDeviceToHost, P->stream));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  return TAPS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Factors
+// ---------------------------------------------------------------------------------
+extern "C" void taps_factors_destroy(taps_factors* U) {
+  if (!U) return;
+  for (int d = 0; d < TAPS_MAX_DIMS; ++d) cudaFree(U->d_U[d]);
+  delete U;
+}
+
+extern "C" int taps_factors_create(const taps_problem* P, int M_cap, taps_factors** out) {
+  if (!P || !out || M_cap < 1 || M_cap > TAPS_MAX_M) return TAPS_ERR_INVALID_ARG;
+  taps_factors* U = new taps_factors();
+  memset((void*)U, 0, sizeof(taps_factors));
+  U->prob = P;
+  U->M_cap = M_cap;
+  for (int d = 0; d < P->D; ++d) {
+    int st = taps_alloc((void**)&U->d_U[d], sizeof(double) * P->dims[d]->nf * M_cap);
+    if (st != TAPS_OK) {
+      taps_factors_destroy(U);
+      return st;
+    }
+    cudaMemsetAsync(U->d_U[d], 0, sizeof(double) * P->dims[d]->nf * M_cap, P->stream);
+  }
+  *out = U;
+  return TAPS_OK;
+}
+
+extern "C" int taps_factors_set(taps_factors* U, int M, const double* const* host_U) {
+  if (!U || M < 0 || M > U->M_cap || (M > 0 && !host_U)) return TAPS_ERR_INVALID_ARG;
+  const taps_problem* P = U->prob;
+  for (int d = 0; d < P->D && M > 0; ++d) {
+    if (!host_U[d]) return TAPS_ERR_INVALID_ARG;
+    TAPS_CUDA(cudaMemcpyAsync(U->d_U[d], host_U[d], sizeof(double) * P->dims[d]->nf * M,
+                              cudaMemcpyHostToDevice, P->stream));
+  }
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  U->M = M;
+  return TAPS_OK;
+}
+
+extern "C" int taps_factors_get(const taps_factors* U, double* const* host_U) {
+  if (!U || !host_U) return TAPS_ERR_INVALID_ARG;
+  const taps_problem* P = U->prob;
+  for (int d = 0; d < P->D && U->M > 0; ++d) {
+    if (!host_U[d]) return TAPS_ERR_INVALID_ARG;
+    TAPS_CUDA(cudaMemcpyAsync(host_U[d], U->d_U[d], sizeof(double) * P->dims[d]->nf * U->M,
+                              cudaMemcpyDeviceToHost, P->stream));
+  }
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  return TAPS_OK;
+}
+
+extern "C" int taps_factors_M(const taps_factors* U) { return U ? U->M : -1; }
+
+extern "C" const double* taps_factors_device_ptr(const taps_factors* U, int d) {
+  if (!U || d < 0 || d >= U->prob->D) return nullptr;
+  return U->d_U[d];
+}
+
+// Columns [m0, m1) of U_d by the init rule (SplitMix64 draws or zero/one).
+__global__ void init_cols_kernel(double* U, int nf, int m0, int m1, int d, int kind, unsigned seed) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tot = (long long)nf * (m1 - m0);
+  if (idx >= tot) return;
+  int i = idx % nf, m = m0 + (int)(idx / nf);
+  double v;
+  if (kind == TAPS_INIT_RANDOM) v = taps_uniform_pm1(seed, d, i, m);
+  else v = (d == 0) ? 0.0 : 1.0;
+  U[(size_t)m * nf + i] = v;
+}
+
+static int init_columns(taps_problem* P, taps_factors* U, int m0, int m1, int kind, unsigned seed) {
+  if (m1 <= m0) return TAPS_OK;
+  for (int d = 0; d < P->D; ++d) {
+    int nf = P->dims[d]->nf;
+    long long tot = (long long)nf * (m1 - m0);
+    int tk = prof_begin(P, TAPS_PROF_OTHER);
+    init_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, P->stream>>>(U->d_U[d], nf, m0, m1, d,
+                                                                           kind, seed);
+    prof_end(P, TAPS_PROF_OTHER, tk, 0.0, 8.0 * tot);
+    TAPS_CUDA(cudaGetLastError());
+  }
+  return TAPS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Sweeps, residuals, solve
+// ---------------------------------------------------------------------------------
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const taps_sweep_opts* opts,
+                          taps_sweep_report* rep) {
+  if (!P || !U || U->prob != P || n_sweeps < 0 || U->M < 1) return TAPS_ERR_INVALID_ARG;
+  int precision = opts ? opts->precision : TAPS_FP64;
+  int solver = opts ? opts->solver : TAPS_SOLVER_BLOCK_LU;
+  int normalize = opts ? opts->normalize : 1;
+  if (precision != TAPS_FP64 && precision != TAPS_FP32) return TAPS_ERR_INVALID_ARG;
+  if (solver != TAPS_SOLVER_BLOCK_LU) return TAPS_ERR_INVALID_ARG;
+  double t0 = now_s();
+  TAPS_TRY(taps_ws_ensure(P, U->M));
+  TAPS_TRY(taps_refresh_grams(P, U, precision));
+  double change = 0.0;
+  for (int it = 0; it < n_sweeps; ++it) TAPS_TRY(taps_sweep_impl(P, U, precision, solver, normalize, &change));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  prof_drain(P);
+  if (rep) {
+    rep->sweeps = n_sweeps;
+    rep->change = change;
+    rep->seconds = now_s() - t0;
+  }
+  return TAPS_OK;
+}
+
+extern "C" int taps_residual(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
+  if (!P || !U || !rho_out || U->prob != P || U->M < 1) return TAPS_ERR_INVALID_ARG;
+  return taps_residual_impl(P, U, kind, rho_out);
+}
+
+extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opts* o,
+                          taps_solve_report* rep) {
+  if (!P || !U || !o || U->prob != P) return TAPS_ERR_INVALID_ARG;
+  if (o->M_max < 1 || o->M_max > U->M_cap || o->max_sweeps < 1 ||
+      (o->precision != TAPS_FP64 && o->precision != TAPS_FP32) ||
+      (o->res_kind != TAPS_RES_ALS && o->res_kind != TAPS_RES_FULL) ||
+      o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO || o->solver != TAPS_SOLVER_BLOCK_LU)
+    return TAPS_ERR_INVALID_ARG;
+  double t0 = now_s();
+  if (o->init != TAPS_INIT_GIVEN) {
+    if (o->M0 < 1 || o->M0 > o->M_max) return TAPS_ERR_INVALID_ARG;
+    TAPS_TRY(init_columns(P, U, 0, o->M0, o->init, o->seed));
+    U->M = o->M0;
+  } else if (U->M < 1) {
+    return TAPS_ERR_INVALID_ARG;
+  }
+  int add_kind = (o->init == TAPS_INIT_GIVEN) ? TAPS_INIT_RANDOM : o->init;
+  int M = U->M;
+  TAPS_TRY(taps_ws_ensure(P, o->M_max));
+  int precision = o->precision;
+  TAPS_TRY(taps_refresh_grams(P, U, precision));
+  int sweeps = 0, fp64_sweeps = 0, polish_left = o->polish_sweeps, hist = 0;
+  double rho = INFINITY, change = INFINITY;
+  bool converged = false;
+  while (true) {
+    double prev_rho = INFINITY;
+    int prec = precision;
+    for (int it = 0; it < o->max_sweeps; ++it) {
+      if (prec == TAPS_FP32) {
+        for (int d = 0; d < P->D; ++d)
+          TAPS_CUDA(cudaMemcpyAsync(P->d_Usnap[d], U->d_U[d], sizeof(double) * P->dims[d]->nf * M,
+                                    cudaMemcpyDeviceToDevice, P->stream));
+      }
+      int sst = taps_sweep_impl(P, U, prec, TAPS_SOLVER_BLOCK_LU, 1, &change);
+      if (prec == TAPS_FP32 && (sst == TAPS_ERR_SINGULAR || sst == TAPS_ERR_NONFINITE)) {
+        // FP32 Grams cannot separate modes that agree to ~1e-8 (a Gram entry rounds to
+        // an exact duplicate): restore the factors and redo the sweep in FP64.
+        for (int d = 0; d < P->D; ++d)
+          TAPS_CUDA(cudaMemcpyAsync(U->d_U[d], P->d_Usnap[d], sizeof(double) * P->dims[d]->nf * M,
+                                    cudaMemcpyDeviceToDevice, P->stream));
+        prec = TAPS_FP64;
+        TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
+        sst = taps_sweep_impl(P, U, prec, TAPS_SOLVER_BLOCK_LU, 1, &change);
+      }
+      TAPS_TRY(sst);
+      ++sweeps;
+      if (prec == TAPS_FP64) ++fp64_sweeps;
+      TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho));
+      if (o->history_cap > 0 && rep && hist < o->history_cap) {
+        if (rep->hist_M) rep->hist_M[hist] = M;
+        if (rep->hist_change) rep->hist_change[hist] = change;
+        if (rep->hist_rho) rep->hist_rho[hist] = rho;
+        ++hist;
+      }
+      if (rho <= o->res_tol) { converged = true; break; }
+      if (change <= o->als_tol) break;
+      if (prec == TAPS_FP32) {
+        // FP32 Grams stop helping once the residual no longer falls: refine in FP64.
+        if (rho > 0.5 * prev_rho) {
+          if (polish_left <= 0) break;
+          prec = TAPS_FP64;
+        }
+      } else if (precision == TAPS_FP32) {
+        if (--polish_left <= 0) break;
+      }
+      prev_rho = rho;
+    }
+    if (converged || M >= o->M_max) break;
+    TAPS_TRY(init_columns(P, U, M, M + 1, add_kind, o->seed));
+    U->M = ++M;
+    TAPS_TRY(taps_refresh_grams(P, U, precision));
+  }
+  double rho_full = rho;
+  if (o->res_kind != TAPS_RES_FULL) TAPS_TRY(taps_residual_impl(P, U, TAPS_RES_FULL, &rho_full));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  prof_drain(P);
+  if (rep) {
+    rep->M = M;
+    rep->sweeps = sweeps;
+    rep->fp64_sweeps = fp64_sweeps;
+    rep->rho = rho;
+    rep->rho_full = rho_full;
+    rep->change = change;
+    rep->seconds = now_s() - t0;
+    rep->converged = converged ? 1 : 0;
+    rep->hist_len = hist;
+  }
+  return converged ? TAPS_OK : TAPS_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------------
+// Grid reconstruction (Eq. 13 at nodes): u[i_1..i_D] = sum_m prod_d U_d[i_d, m].
+// Rows of the gathered factors G_d [count_d][M] carry 0 at constrained nodes.  A CTA
+// owns ER prefix rows (indices of dims 0..D-2) and all `last` entries of dim D-1.
+// ---------------------------------------------------------------------------------
+struct GridSpec {
+  int D;
+  int count[TAPS_MAX_DIMS];
+  long long goff[TAPS_MAX_DIMS];  // offsets of G_d in the gathered buffer
+};
+
+template <typename T>
+__global__ void gather_rows_kernel(const double* U, int nf, int off, int start, int step, int count,
+                                   int M, T* G) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count * M) return;
+  int j = idx / M, m = idx % M;
+  int node = start + step * j;
+  int fj = node - off;
+  G[idx] = (fj >= 0 && fj < nf) ? (T)U[(size_t)m * nf + fj] : (T)0;
+}
+
+// A CTA owns ER prefix rows and a tile of up to ECT entries of the last dim.  The
+// prefix products P[r][m] and the transposed last-dim rows GLt[m][j] are staged in
+// shared memory; each thread produces 4 consecutive outputs of one row (vector
+// store when the row start is 16-byte aligned), so the kernel streams the output.
+#define ER 32
+#define ECT 256
+
+template <typename T>
+__global__ void __launch_bounds__(256) eval_grid_kernel(const T* __restrict__ G, GridSpec gs, int M,
+                                                        long long rows, int ect, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int last = gs.count[gs.D - 1];
+  const int j0 = blockIdx.y * ect;
+  const int ct = min(ect, last - j0);
+  T* Pr = reinterpret_cast<T*>(smraw);  // [ER][M]
+  T* GLt = Pr + ER * M;                 // [M][ct]
+  const long long r0 = (long long)blockIdx.x * ER;
+  const int nr = (int)min((long long)ER, rows - r0);
+  // prefix products of dims 0..D-2 (one 64-bit decomposition per row)
+  for (int idx = threadIdx.x; idx < nr * M; idx += blockDim.x) {
+    int rr = idx / M, m = idx - rr * M;
+    long long row = r0 + rr;
+    T v = (T)1;
+    for (int d = gs.D - 2; d >= 0; --d) {
+      long long q = row / gs.count[d];
+      int id = (int)(row - q * gs.count[d]);
+      row = q;
+      v *= G[gs.goff[d] + (long long)id * M + m];
+    }
+    Pr[rr * M + m] = v;
+  }
+  const T* GL = G + gs.goff[gs.D - 1];
+  for (int idx = threadIdx.x; idx < ct * M; idx += blockDim.x) {
+    int j = idx / M, m = idx - j * M;
+    GLt[m * ct + j] = GL[(long long)(j0 + j) * M + m];
+  }
+  __syncthreads();
+  const int groups = (ct + 3) >> 2;           // 4-wide column groups per row
+  const int ntask = nr * groups;
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    int rr = t / groups, g4 = (t - rr * groups) << 2;
+    const T* p = Pr + rr * M;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    if (g4 + 3 < ct) {
+      for (int m = 0; m < M; ++m) {
+        T pv = p[m];
+        const T* g = GLt + m * ct + g4;
+        a0 += pv * g[0];
+        a1 += pv * g[1];
+        a2 += pv * g[2];
+        a3 += pv * g[3];
+      }
+    } else {
+      for (int m = 0; m < M; ++m) {
+        T pv = p[m];
+        const T* g = GLt + m * ct + g4;
+        a0 += pv * g[0];
+        if (g4 + 1 < ct) a1 += pv * g[1];
+        if (g4 + 2 < ct) a2 += pv * g[2];
+      }
+    }
+    T* o = out + (r0 + rr) * (long long)last + j0 + g4;
+    bool full = g4 + 3 < ct;
+    if (full && sizeof(T) == 4 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+      float4 v = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+      *reinterpret_cast<float4*>(o) = v;
+    } else {
+      o[0] = a0;
+      if (g4 + 1 < ct) o[1] = a1;
+      if (g4 + 2 < ct) o[2] = a2;
+      if (full) o[3] = a3;
+    }
+  }
+}
+
+extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, const int* start,
+                              const int* count, const int* step, void* out_dev, int out_dtype) {
+  taps_problem* P = const_cast<taps_problem*>(Pc);
+  if (!P || !U || !start || !count || !step || U->M < 1) return TAPS_ERR_INVALID_ARG;
+  if (out_dtype != TAPS_FP64 && out_dtype != TAPS_FP32) return TAPS_ERR_INVALID_ARG;
+  GridSpec gs;
+  memset(&gs, 0, sizeof(gs));
+  gs.D = P->D;
+  long long total = 1, goff = 0;
+  int M = U->M;
+  for (int d = 0; d < P->D; ++d) {
+    const taps_dim* dm = P->dims[d];
+    if (count[d] < 1) return TAPS_ERR_INVALID_ARG;
+    long long first = start[d], lastn = start[d] + (long long)step[d] * (count[d] - 1);
+    if (first < 0 || first >= dm->n || lastn < 0 || lastn >= dm->n) return TAPS_ERR_INVALID_ARG;
+    gs.count[d] = count[d];
+    gs.goff[d] = goff;
+    goff += (long long)count[d] * M;
+    total *= count[d];
+  }
+  if (!out_dev) return TAPS_ERR_INVALID_ARG;
+  cudaStream_t s = P->stream;
+  size_t esz = out_dtype == TAPS_FP64 ? sizeof(double) : sizeof(float);
+  if (esz * goff > P->evalbuf_len) {
+    TAPS_CUDA(cudaStreamSynchronize(s));
+    cudaFree(P->d_evalbuf);
+    P->d_evalbuf = nullptr;
+    P->evalbuf_len = 0;
+    TAPS_TRY(taps_alloc(&P->d_evalbuf, esz * goff));
+    P->evalbuf_len = esz * goff;
+  }
+  void* G = P->d_evalbuf;
+  int st = TAPS_OK;
+  for (int d = 0; d < P->D; ++d) {
+    const taps_dim* dm = P->dims[d];
+    int n = count[d] * M;
+    if (out_dtype == TAPS_FP64)
+      gather_rows_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(U->d_U[d], dm->nf, dm->off, start[d],
+                                                                 step[d], count[d], M,
+                                                                 (double*)G + gs.goff[d]);
+    else
+      gather_rows_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(U->d_U[d], dm->nf, dm->off, start[d],
+                                                                step[d], count[d], M,
+                                                                (float*)G + gs.goff[d]);
+  }
+  long long rows = total / count[P->D - 1];
+  int last = count[P->D - 1];
+  int ect = ECT;
+  while (ect > 4 && (size_t)(ER * M + M * std::min(last, ect)) * esz > 96 * 1024) ect >>= 1;
+  dim3 egrid((unsigned)((rows + ER - 1) / ER), (unsigned)((last + ect - 1) / ect));
+  size_t esm = (size_t)(ER * M + M * std::min(last, ect)) * esz;
+  if (!P->eval_attr_set) {
+    cudaFuncSetAttribute((const void*)eval_grid_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute((const void*)eval_grid_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    P->eval_attr_set = 1;
+  }
+  int tk = prof_begin(P, TAPS_PROF_EVAL);
+  if (out_dtype == TAPS_FP64)
+    eval_grid_kernel<double><<<egrid, 256, esm, s>>>((const double*)G, gs, M, rows, ect, (double*)out_dev);
+  else
+    eval_grid_kernel<float><<<egrid, 256, esm, s>>>((const float*)G, gs, M, rows, ect, (float*)out_dev);
+  prof_end(P, TAPS_PROF_EVAL, tk, 2.0 * M * (double)total + (double)rows * M * (P->D - 1),
+           (double)esz * total + (double)esz * goff);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    taps_note_cuda_error(e, "eval_grid_kernel", __FILE__, __LINE__);
+    st = TAPS_ERR_CUDA;
+  }
+  return st;
+}

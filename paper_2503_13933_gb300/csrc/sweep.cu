@@ -1,0 +1,756 @@
+// Subspace-iteration sweep (Algorithm 1, Eq. 43) on the device: Gram refresh (fused
+// banded SpMM + U^T Y, Eq. 34), coefficient combine (Hadamard products over the other
+// dimensions, Eq. 35), block-banded reduced system (Eqs. 36-40) and its solve,
+// column normalisation and factor change; residuals of Eq. 42 and of the full system.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "taps_internal.cuh"
+
+// ---------------------------------------------------------------------------------
+// Gram refresh of one dimension: Gamma_o = U^T Op_o U for each distinct op o and
+// h_r = U^T q_r.  CTA (chunk, mtile) handles GR rows and MT rows of Gamma; partial
+// sums are reduced in a fixed order by gram_reduce_kernel.
+// ---------------------------------------------------------------------------------
+#define GR 16
+#define GMT 8
+
+template <typename T>
+__global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M, int hb,
+                                    const double* __restrict__ opband, int nops,
+                                    const double* __restrict__ q, int Rf,
+                                    double* __restrict__ partial, int stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = 2 * hb + 1;
+  const int rows_h = GR + 2 * hb;
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [rows_h][M]
+  T* Ys = Us + rows_h * M;                 // [GR][M]
+  const int r0 = blockIdx.x * GR;
+  const int m0 = blockIdx.y * GMT;
+  const int mt = min(GMT, M - m0);
+  for (int idx = threadIdx.x; idx < rows_h * M; idx += blockDim.x) {
+    int m = idx / rows_h, rr = idx % rows_h;
+    int gi = r0 - hb + rr;
+    Us[rr * M + m] = (gi >= 0 && gi < nf) ? (T)U[(size_t)m * nf + gi] : (T)0;
+  }
+  __syncthreads();
+  double* out = partial + ((size_t)blockIdx.x) * stride;
+  for (int o = 0; o < nops; ++o) {
+    const double* band = opband + (size_t)o * nf * nb;
+    for (int idx = threadIdx.x; idx < GR * M; idx += blockDim.x) {
+      int i = idx / M, n = idx % M;
+      int gi = r0 + i;
+      T acc = 0;
+      if (gi < nf) {
+        const double* brow = band + (size_t)gi * nb;
+        for (int k = 0; k < nb; ++k) acc += (T)brow[k] * Us[(i + k) * M + n];
+      }
+      Ys[i * M + n] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < mt * M; idx += blockDim.x) {
+      int m = m0 + idx / M, n = idx % M;
+      T acc = 0;
+      for (int i = 0; i < GR; ++i) acc += Us[(i + hb) * M + m] * Ys[i * M + n];
+      out[((size_t)o * M + m) * M + n] = (double)acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < Rf * mt; idx += blockDim.x) {
+    int r = idx / mt, m = m0 + idx % mt;
+    T acc = 0;
+    for (int i = 0; i < GR; ++i) {
+      int gi = r0 + i;
+      if (gi < nf) acc += (T)q[(size_t)r * nf + gi] * Us[(i + hb) * M + m];
+    }
+    out[(size_t)nops * M * M + (size_t)r * M + m] = (double)acc;
+  }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ partial, int nchunk, int stride,
+                                   int nops, int M, int Rf, double* gram, double* h) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int ng = nops * M * M;
+  if (j >= ng + Rf * M) return;
+  double acc = 0.0;
+  for (int c = 0; c < nchunk; ++c) acc += partial[(size_t)c * stride + j];
+  if (j < ng) gram[j] = acc;
+  else h[j - ng] = acc;
+}
+
+int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision) {
+  const taps_dim* dm = P->dims[d];
+  int M = U->M, nf = dm->nf, hb = dm->hb, nops = P->tt.nops[d], Rf = P->Rf;
+  if (M == 0) return TAPS_OK;
+  int nchunk = (nf + GR - 1) / GR;
+  int stride = nops * M * M + Rf * M;
+  dim3 grid(nchunk, (M + GMT - 1) / GMT);
+  size_t elems = (size_t)(GR + 2 * hb) * M + (size_t)GR * M;
+  const int nb = 2 * hb + 1;
+  const double gflops = nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
+  const double gbytes = 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf +
+                               (double)nops * M * M + (double)Rf * M);
+  int tk = prof_begin(P, TAPS_PROF_GRAM);
+  if (precision == TAPS_FP32) {
+    gram_partial_kernel<float><<<grid, 256, elems * sizeof(float), P->stream>>>(
+        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride);
+  } else {
+    gram_partial_kernel<double><<<grid, 256, elems * sizeof(double), P->stream>>>(
+        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride);
+  }
+  TAPS_CUDA(cudaGetLastError());
+  gram_reduce_kernel<<<(stride + 255) / 256, 256, 0, P->stream>>>(P->d_partial, nchunk, stride, nops,
+                                                                  M, Rf, P->d_gram[d], P->d_h[d]);
+  prof_end(P, TAPS_PROF_GRAM, tk, gflops, gbytes);
+  P->prof->launches[TAPS_PROF_GRAM] += 1;  // the reduce kernel is a second launch
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision) {
+  for (int d = 0; d < P->D; ++d) TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision));
+  return TAPS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Coefficients of dim d: C_o = sum_{t: op(t,d) = o} alpha_t prod_{e != d} Gamma_{op(t,e),e}
+// and c_r = beta_r prod_{e != d} h_{r,e}.
+// ---------------------------------------------------------------------------------
+__global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int MM = M * M;
+  if (idx < MM) {
+    double acc[TAPS_NUM_OPS];
+    for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
+    for (int t = 0; t < tt.R; ++t) {
+      double prod = tt.alpha[t];
+      for (int e = 0; e < tt.D; ++e)
+        if (e != d) prod *= gp.gram[e][(size_t)tt.oi[t][e] * MM + idx];
+      acc[tt.oi[t][d]] += prod;
+    }
+    for (int o = 0; o < tt.nops[d]; ++o) C[(size_t)o * MM + idx] = acc[o];
+  }
+  if (idx < M) {
+    for (int r = 0; r < tt.Rf; ++r) {
+      double v = tt.beta[r];
+      for (int e = 0; e < tt.D; ++e)
+        if (e != d) v *= gp.h[e][(size_t)r * M + idx];
+      c[(size_t)r * M + idx] = v;
+    }
+  }
+}
+
+// Block band of the reduced matrix (node-major, I = (i, m)):
+// block(i, i+k-hb)[m][n] = sum_o Op_o[i, i+k-hb] C_o[m][n]; and F[i][m] = sum_r q_r[i] c_r[m].
+__global__ void block_assemble_kernel(const double* __restrict__ opband, int nops, int nf, int nb,
+                                      int M, const double* __restrict__ C,
+                                      const double* __restrict__ q, const double* __restrict__ c,
+                                      int Rf, double* __restrict__ blocks, double* __restrict__ F) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long MM = (long long)M * M;
+  long long nblk = (long long)nf * nb * MM;
+  if (idx < nblk) {
+    long long ik = idx / MM;
+    int mn = idx % MM;
+    int i = ik / nb, k = ik % nb;
+    double v = 0.0;
+    for (int o = 0; o < nops; ++o)
+      v += opband[((size_t)o * nf + i) * nb + k] * C[(size_t)o * MM + mn];
+    blocks[idx] = v;
+  } else if (idx < nblk + (long long)nf * M) {
+    long long j = idx - nblk;
+    int i = j / M, m = j % M;
+    double v = 0.0;
+    for (int r = 0; r < Rf; ++r) v += q[(size_t)r * nf + i] * c[(size_t)r * M + m];
+    F[j] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Block-banded Gaussian elimination without pivoting (one cooperative launch).
+// For each block row k: LU of the diagonal block (CTA 0, shared memory) -> W_kj =
+// D_k^{-1} A_kj and z_k = D_k^{-1} F_k (one warp per column, triangular solves) ->
+// Schur updates A_ij -= A_ik W_kj, F_i -= A_ik z_k (all threads).  Three grid
+// barriers per block row.  The symmetric part of every reduced matrix is positive
+// definite (Hadamard products of Gram matrices, Kronecker products with SPD 1D
+// matrices), so elimination without pivoting exists; a zero or non-finite pivot is
+// reported as TAPS_DEV_SINGULAR.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double slot_get(const double v[4], int s) {
+  return s == 0 ? v[0] : (s == 1 ? v[1] : (s == 2 ? v[2] : v[3]));
+}
+__device__ __forceinline__ void slot_set(double v[4], int s, double x) {
+  if (s == 0) v[0] = x;
+  else if (s == 1) v[1] = x;
+  else if (s == 2) v[2] = x;
+  else v[3] = x;
+}
+
+__global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ blocks,
+                                                       double* __restrict__ F,
+                                                       double* __restrict__ lu_g, int nf, int hb,
+                                                       int M, int* status, unsigned* bar) {
+  extern __shared__ __align__(16) double sm[];  // LU of the diagonal block, stride M+1
+  const int nb = 2 * hb + 1;
+  const int ld = M + 1;
+  const size_t MM = (size_t)M * M;
+  const unsigned nblk = gridDim.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  const long long gtid = (long long)blockIdx.x * nthr + tid;
+  const long long gthreads = (long long)nblk * nthr;
+#define BLK(i, j) (blocks + ((size_t)(i) * nb + ((j) - (i) + hb)) * MM)
+
+  for (int k = 0; k < nf; ++k) {
+    // ---- LU of the diagonal block A(k,k), CTA 0
+    if (blockIdx.x == 0) {
+      const double* Akk = BLK(k, k);
+      for (int idx = tid; idx < (int)MM; idx += nthr) sm[(idx / M) * ld + idx % M] = Akk[idx];
+      __syncthreads();
+      for (int p = 0; p < M; ++p) {
+        double piv = sm[p * ld + p];
+        bool bad = !(fabs(piv) > 0.0) || !isfinite(piv);
+        if (bad && tid == 0) taps_flag(status, TAPS_DEV_SINGULAR);
+        double inv = bad ? 1.0 : 1.0 / piv;
+        for (int r = p + 1 + tid; r < M; r += nthr) sm[r * ld + p] *= inv;
+        __syncthreads();
+        int w = M - p - 1;
+        for (int idx = tid; idx < w * w; idx += nthr) {
+          int r = p + 1 + idx / w, c = p + 1 + idx % w;
+          sm[r * ld + c] -= sm[r * ld + p] * sm[p * ld + c];
+        }
+        __syncthreads();
+      }
+      for (int idx = tid; idx < (int)MM; idx += nthr) lu_g[idx] = sm[(idx / M) * ld + idx % M];
+    }
+    grid_barrier(bar, status, nblk);
+
+    // ---- W(k, k+jj) = LU^{-1} A(k, k+jj), z_k = LU^{-1} F_k : one warp per column
+    const int nj = min(hb, nf - 1 - k);
+    const int ntask = nj * M + 1;
+    const int cta_needed = (ntask + nwarps - 1) / nwarps;
+    if ((int)blockIdx.x < cta_needed) {
+      if (blockIdx.x != 0) {
+        for (int idx = tid; idx < (int)MM; idx += nthr) sm[(idx / M) * ld + idx % M] = lu_g[idx];
+      }
+      __syncthreads();
+      int task = blockIdx.x * nwarps + warp;
+      if (task < ntask) {
+        double* col;
+        int cstride;
+        if (task < nj * M) {
+          int jj = task / M + 1, cc = task % M;
+          col = BLK(k, k + jj) + cc;
+          cstride = M;
+        } else {
+          col = F + (size_t)k * M;
+          cstride = 1;
+        }
+        double v[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          int r = lane + 32 * s;
+          v[s] = (r < M) ? col[(size_t)r * cstride] : 0.0;
+        }
+        // forward: unit lower L
+        for (int c = 0; c < M; ++c) {
+          double yc = __shfl_sync(0xffffffffu, slot_get(v, c >> 5), c & 31);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            int r = lane + 32 * s;
+            if (r > c && r < M) v[s] -= sm[r * ld + c] * yc;
+          }
+        }
+        // backward: upper U
+        for (int c = M - 1; c >= 0; --c) {
+          int sc = c >> 5;
+          double own = slot_get(v, sc);
+          if (lane == (c & 31)) {
+            own /= sm[c * ld + c];
+            slot_set(v, sc, own);
+          }
+          double yc = __shfl_sync(0xffffffffu, own, c & 31);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            int r = lane + 32 * s;
+            if (r < c) v[s] -= sm[r * ld + c] * yc;
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          int r = lane + 32 * s;
+          if (r < M) col[(size_t)r * cstride] = v[s];
+        }
+      }
+    }
+    grid_barrier(bar, status, nblk);
+
+    // ---- Schur updates of the trailing window
+    const long long nupd = (long long)nj * nj * MM;
+    const long long total = nupd + (long long)nj * M;
+    for (long long o = gtid; o < total; o += gthreads) {
+      if (o < nupd) {
+        int pair = (int)(o / MM);
+        int rem = (int)(o % MM);
+        int ii = pair / nj + 1, jj = pair % nj + 1;
+        int m = rem / M, n = rem % M;
+        const double* L = BLK(k + ii, k) + (size_t)m * M;
+        const double* W = BLK(k, k + jj) + n;
+        double s = 0.0;
+        for (int l = 0; l < M; ++l) s += L[l] * W[(size_t)l * M];
+        BLK(k + ii, k + jj)[(size_t)m * M + n] -= s;
+      } else {
+        int o2 = (int)(o - nupd);
+        int ii = o2 / M + 1, m = o2 % M;
+        const double* L = BLK(k + ii, k) + (size_t)m * M;
+        const double* z = F + (size_t)k * M;
+        double s = 0.0;
+        for (int l = 0; l < M; ++l) s += L[l] * z[l];
+        F[(size_t)(k + ii) * M + m] -= s;
+      }
+    }
+    grid_barrier(bar, status, nblk);
+  }
+#undef BLK
+}
+
+// Back substitution x_k = z_k - sum_j W_kj x_j (k = nf-1 .. 0), written into the
+// column-major factor U_d.  One CTA; each output is split over 8 partial dots.
+__global__ void __launch_bounds__(256) block_backsub_kernel(const double* __restrict__ blocks,
+                                                            const double* __restrict__ F, int nf,
+                                                            int hb, int M, double* __restrict__ X,
+                                                            int* status) {
+  extern __shared__ __align__(16) double xs[];  // [(hb+1)][M] ring + [8][M] partials
+  const int nb = 2 * hb + 1;
+  const size_t MM = (size_t)M * M;
+  double* part = xs + (size_t)(hb + 1) * M;
+  const int tid = threadIdx.x;
+  const int nparts = 8;
+  for (int k = nf - 1; k >= 0; --k) {
+    const int nj = min(hb, nf - 1 - k);
+    const int work = nj * M;  // dot length per output
+    for (int idx = tid; idx < nparts * M; idx += blockDim.x) {
+      int m = idx % M, pp = idx / M;
+      double s = 0.0;
+      for (int w = pp; w < work; w += nparts) {
+        int jj = w / M + 1, n = w % M;
+        const double* W = blocks + ((size_t)k * nb + (jj + hb)) * MM;
+        s += W[(size_t)m * M + n] * xs[((k + jj) % (hb + 1)) * M + n];
+      }
+      part[pp * M + m] = s;
+    }
+    __syncthreads();
+    for (int m = tid; m < M; m += blockDim.x) {
+      double s = F[(size_t)k * M + m];
+      for (int pp = 0; pp < nparts; ++pp) s -= part[pp * M + m];
+      if (!isfinite(s)) taps_flag(status, TAPS_DEV_NONFINITE);
+      xs[(k % (hb + 1)) * M + m] = s;
+      X[(size_t)m * nf + k] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Column normalisation (unit 2-norm, largest-magnitude entry positive) and the
+// squared change / norm of every column against the pre-solve copy.
+// ---------------------------------------------------------------------------------
+__global__ void normalize_change_kernel(double* U, const double* Uold, int nf, int M, int normalize,
+                                        double* out, int* status) {
+  __shared__ double red[32];
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  int m = blockIdx.x;
+  double* col = U + (size_t)m * nf;
+  const double* old = Uold + (size_t)m * nf;
+  double s2 = 0.0, best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    double v = col[i];
+    s2 += v * v;
+    double a = fabs(v);
+    if (a > best) { best = a; bi = i; }
+  }
+  s2 = block_sum(s2, red);
+  // argmax with ties to the smallest index
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { redv[w] = best; redi[w] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int j = 1; j < nw; ++j)
+      if (redv[j] > redv[0] || (redv[j] == redv[0] && redi[j] < redi[0])) { redv[0] = redv[j]; redi[0] = redi[j]; }
+  }
+  __syncthreads();
+  int imax = redi[0];
+  double nrm = sqrt(s2);
+  if (!isfinite(nrm)) taps_flag(status, TAPS_DEV_NONFINITE);
+  if (normalize && nrm > 0.0) {
+    double sgn = (col[imax] >= 0.0) ? 1.0 : -1.0;
+    double den = sgn * nrm;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) col[i] = col[i] / den;
+    __syncthreads();
+  }
+  double dif = 0.0, n2 = 0.0;
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    double v = col[i];
+    double dv = v - old[i];
+    dif += dv * dv;
+    n2 += v * v;
+  }
+  dif = block_sum(dif, red);
+  n2 = block_sum(n2, red);
+  if (threadIdx.x == 0) {
+    out[2 * m] = dif;
+    out[2 * m + 1] = n2;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Reduced solve of dim d with the coefficients already in P->d_C / P->d_c.
+// ---------------------------------------------------------------------------------
+static int reduced_solve_block_lu(taps_problem* P, taps_factors* U, int d) {
+  const taps_dim* dm = P->dims[d];
+  int M = U->M, nf = dm->nf, hb = dm->hb, nb = dm->nb, nops = P->tt.nops[d];
+  cudaStream_t s = P->stream;
+  long long nblk = (long long)nf * nb * M * M + (long long)nf * M;
+  int tk = prof_begin(P, TAPS_PROF_BLOCK_ASSEMBLE);
+  block_assemble_kernel<<<(unsigned)((nblk + 255) / 256), 256, 0, s>>>(
+      P->d_opband[d], nops, nf, nb, M, P->d_C, P->d_q[d], P->d_c, P->Rf, P->d_blocks, P->d_F);
+  prof_end(P, TAPS_PROF_BLOCK_ASSEMBLE, tk, 2.0 * nops * (double)nf * nb * M * M + 2.0 * P->Rf * nf * M,
+           8.0 * ((double)nf * nb * M * M + (double)nf * M + (double)nops * nf * nb + (double)P->Rf * nf));
+  TAPS_CUDA(cudaGetLastError());
+  // algorithmic flops of the elimination and of the back substitution
+  double lu_flops = 0.0, bs_flops = 0.0;
+  const double Md = M;
+  for (int k = 0; k < nf; ++k) {
+    int nj = std::min(hb, nf - 1 - k);
+    lu_flops += (2.0 / 3.0) * Md * Md * Md + (nj * Md + 1) * 2.0 * Md * Md +
+                nj * (double)nj * 2.0 * Md * Md * Md + nj * 2.0 * Md * Md;
+    bs_flops += nj * 2.0 * Md * Md;
+  }
+  const double band_bytes = 8.0 * (double)nf * nb * M * M;
+  // cooperative elimination
+  size_t smem = sizeof(double) * (size_t)M * (M + 1);
+  int want = (int)std::min<long long>((long long)hb * hb * M * M / 256 + 1, P->num_sms);
+  int want_a = (hb * M + 1 + 7) / 8;
+  int grid = std::max(1, std::max(want, want_a));
+  grid = std::min(grid, P->coop_blocks);
+  TAPS_CUDA(cudaMemsetAsync(P->d_bar, 0, 2 * sizeof(unsigned), s));
+  double* blocks = P->d_blocks;
+  double* Fp = P->d_F;
+  double* lu = P->d_lu;
+  int* st = P->d_status;
+  unsigned* bar = P->d_bar;
+  void* args[] = {&blocks, &Fp, &lu, &nf, &hb, &M, &st, &bar};
+  tk = prof_begin(P, TAPS_PROF_BLOCK_LU);
+  TAPS_CUDA(cudaLaunchCooperativeKernel((const void*)block_lu_kernel, dim3(grid), dim3(256), args,
+                                        smem, s));
+  prof_end(P, TAPS_PROF_BLOCK_LU, tk, lu_flops, 2.0 * band_bytes + 16.0 * nf * M);
+  size_t smem_b = sizeof(double) * ((size_t)(hb + 1) * M + 8 * (size_t)M);
+  tk = prof_begin(P, TAPS_PROF_BACKSUB);
+  block_backsub_kernel<<<1, 256, smem_b, s>>>(P->d_blocks, P->d_F, nf, hb, M, U->d_U[d],
+                                              P->d_status);
+  prof_end(P, TAPS_PROF_BACKSUB, tk, bs_flops, 8.0 * (double)nf * hb * M * M + 16.0 * nf * M);
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+// Shared-memory opt-in of the kernels whose footprint grows with M, and the number
+// of CTAs a cooperative block-LU launch may use (co-residency at the largest M).
+int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
+  int maxsm = 0;
+  TAPS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  TAPS_CUDA(cudaFuncSetAttribute((const void*)block_lu_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  TAPS_CUDA(cudaFuncSetAttribute((const void*)gram_partial_kernel<double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  TAPS_CUDA(cudaFuncSetAttribute((const void*)gram_partial_kernel<float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  int bps = 0;
+  size_t smem_max = sizeof(double) * TAPS_MAX_M * (TAPS_MAX_M + 1);
+  TAPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, block_lu_kernel, 256, smem_max));
+  *coop_blocks = std::max(bps, 1) * num_sms;
+  return TAPS_OK;
+}
+
+static GramPtrs gram_ptrs(const taps_problem* P) {
+  GramPtrs gp;
+  memset(&gp, 0, sizeof(gp));
+  for (int d = 0; d < P->D; ++d) {
+    gp.gram[d] = P->d_gram[d];
+    gp.h[d] = P->d_h[d];
+  }
+  return gp;
+}
+
+static int coefficients(taps_problem* P, int d, int M) {
+  int tk = prof_begin(P, TAPS_PROF_COEFF);
+  coeff_kernel<<<(M * M + 127) / 128, 128, 0, P->stream>>>(P->tt, gram_ptrs(P), d, M, P->d_C, P->d_c);
+  prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D + (double)P->Rf * M * P->D,
+           8.0 * ((double)P->R * M * M * P->D));
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
+                    double* change_out) {
+  (void)solver;
+  int M = U->M;
+  if (M < 1) return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_ws_ensure(P, M));
+  cudaStream_t s = P->stream;
+  for (int d = 0; d < P->D; ++d) {
+    const taps_dim* dm = P->dims[d];
+    TAPS_TRY(coefficients(P, d, M));
+    TAPS_CUDA(cudaMemcpyAsync(P->d_Uold, U->d_U[d], sizeof(double) * dm->nf * M,
+                              cudaMemcpyDeviceToDevice, s));
+    TAPS_TRY(reduced_solve_block_lu(P, U, d));
+    int norm_d = (normalize && d < P->D - 1) ? 1 : 0;
+    int tk = prof_begin(P, TAPS_PROF_NORMALIZE);
+    normalize_change_kernel<<<M, 256, 0, s>>>(U->d_U[d], P->d_Uold, dm->nf, M, norm_d,
+                                              P->d_scal + (size_t)d * 2 * M, P->d_status);
+    prof_end(P, TAPS_PROF_NORMALIZE, tk, 7.0 * dm->nf * M, 8.0 * 3.0 * dm->nf * M);
+    TAPS_CUDA(cudaGetLastError());
+    TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision));
+  }
+  TAPS_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, sizeof(double) * 2 * M * P->D,
+                            cudaMemcpyDeviceToHost, s));
+  TAPS_TRY(taps_check_status(P->d_status, s));
+  prof_drain(P);
+  double change = 0.0;
+  for (int d = 0; d < P->D; ++d) {
+    double dif = 0.0, n2 = 0.0;
+    for (int m = 0; m < M; ++m) {
+      dif += P->h_scal[(size_t)d * 2 * M + 2 * m];
+      n2 += P->h_scal[(size_t)d * 2 * M + 2 * m + 1];
+    }
+    double ch = n2 > 0.0 ? sqrt(dif / n2) : INFINITY;
+    change = std::max(change, ch);
+  }
+  if (!std::isfinite(change)) return TAPS_ERR_NONFINITE;
+  if (change_out) *change_out = change;
+  return TAPS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Residuals
+// ---------------------------------------------------------------------------------
+// Y_o = Op_o U for every distinct op of dim d; Y layout [nops][nf][M] (row-major).
+__global__ void spmm_kernel(const double* __restrict__ U, int nf, int M, int hb,
+                            const double* __restrict__ opband, int nops, double* __restrict__ Y) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tot = (long long)nops * nf * M;
+  if (idx >= tot) return;
+  int m = idx % M;
+  int i = (idx / M) % nf;
+  int o = idx / ((long long)M * nf);
+  int nb = 2 * hb + 1;
+  const double* brow = opband + ((size_t)o * nf + i) * nb;
+  double acc = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    int j = i + k - hb;
+    if (j >= 0 && j < nf) acc += brow[k] * U[(size_t)m * nf + j];
+  }
+  Y[idx] = acc;
+}
+
+// Residual of dim d's reduced system: r[i][m] = sum_o sum_n Y_o[i][n] C_o[m][n] - F[i][m].
+// Per-block partial sums of ||r||^2 and ||F||^2.
+__global__ void als_residual_kernel(const double* __restrict__ Y, int nops, int nf, int M,
+                                    const double* __restrict__ C, const double* __restrict__ q,
+                                    const double* __restrict__ c, int Rf, double* partial) {
+  __shared__ double red[32];
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0, f2 = 0.0;
+  if (idx < (long long)nf * M) {
+    int i = idx / M, m = idx % M;
+    double f = 0.0;
+    for (int r = 0; r < Rf; ++r) f += q[(size_t)r * nf + i] * c[(size_t)r * M + m];
+    double a = 0.0;
+    for (int o = 0; o < nops; ++o) {
+      const double* y = Y + ((size_t)o * nf + i) * M;
+      const double* cc = C + ((size_t)o * M + m) * M;
+      for (int n = 0; n < M; ++n) a += y[n] * cc[n];
+    }
+    double rr = a - f;
+    r2 = rr * rr;
+    f2 = f * f;
+  }
+  r2 = block_sum(r2, red);
+  f2 = block_sum(f2, red);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = r2;
+    partial[2 * blockIdx.x + 1] = f2;
+  }
+}
+
+// Per-dim Gram of the columns [Y_0 | Y_1 | ... | q_0 .. q_{Rf-1}] (NC = nops*M + Rf).
+__global__ void big_gram_kernel(const double* __restrict__ Y, int nops, int nf, int M,
+                                const double* __restrict__ q, int Rf, double* __restrict__ G) {
+  int NC = nops * M + Rf;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)NC * NC) return;
+  int a = idx / NC, b = idx % NC;
+  double acc = 0.0;
+  for (int i = 0; i < nf; ++i) {
+    double va = (a < nops * M) ? Y[((size_t)(a / M) * nf + i) * M + (a % M)] : q[(size_t)(a - nops * M) * nf + i];
+    double vb = (b < nops * M) ? Y[((size_t)(b / M) * nf + i) * M + (b % M)] : q[(size_t)(b - nops * M) * nf + i];
+    acc += va * vb;
+  }
+  G[idx] = acc;
+}
+
+struct BigGramPtrs {
+  const double* G[TAPS_MAX_DIMS];
+  int NC[TAPS_MAX_DIMS];
+};
+
+// Gram-identity combination: partial sums of ||F||^2, F^T A u and ||A u||^2.
+__global__ void full_residual_combine_kernel(TermTable tt, BigGramPtrs bg, int M, double* partial) {
+  __shared__ double red[32];
+  const long long nAA = (long long)tt.R * M * tt.R * M;
+  const long long nFA = (long long)tt.Rf * tt.R * M;
+  const long long nFF = (long long)tt.Rf * tt.Rf;
+  const long long tot = nAA + nFA + nFF;
+  double sAA = 0.0, sFA = 0.0, sFF = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (idx < nAA) {
+      int tm = idx / ((long long)tt.R * M), sn = idx % ((long long)tt.R * M);
+      int t = tm / M, m = tm % M, t2 = sn / M, n = sn % M;
+      double v = tt.alpha[t] * tt.alpha[t2];
+      for (int d = 0; d < tt.D; ++d)
+        v *= bg.G[d][(size_t)(tt.oi[t][d] * M + m) * bg.NC[d] + tt.oi[t2][d] * M + n];
+      sAA += v;
+    } else if (idx < nAA + nFA) {
+      long long j = idx - nAA;
+      int r = j / ((long long)tt.R * M), tm = j % ((long long)tt.R * M);
+      int t = tm / M, m = tm % M;
+      double v = tt.beta[r] * tt.alpha[t];
+      for (int d = 0; d < tt.D; ++d) {
+        int qa = tt.nops[d] * M + r;
+        v *= bg.G[d][(size_t)qa * bg.NC[d] + tt.oi[t][d] * M + m];
+      }
+      sFA += v;
+    } else {
+      long long j = idx - nAA - nFA;
+      int r = j / tt.Rf, r2 = j % tt.Rf;
+      double v = tt.beta[r] * tt.beta[r2];
+      for (int d = 0; d < tt.D; ++d) {
+        int qa = tt.nops[d] * M + r, qb = tt.nops[d] * M + r2;
+        v *= bg.G[d][(size_t)qa * bg.NC[d] + qb];
+      }
+      sFF += v;
+    }
+  }
+  sAA = block_sum(sAA, red);
+  sFA = block_sum(sFA, red);
+  sFF = block_sum(sFF, red);
+  if (threadIdx.x == 0) {
+    partial[3 * blockIdx.x] = sFF;
+    partial[3 * blockIdx.x + 1] = sFA;
+    partial[3 * blockIdx.x + 2] = sAA;
+  }
+}
+
+int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
+  int M = U->M;
+  if (M < 1) return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_ws_ensure(P, M));
+  cudaStream_t s = P->stream;
+  if (kind == TAPS_RES_ALS) {
+    // FP64 Grams of every dim at the current factors, then each dim's residual.
+    TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
+    std::vector<int> nblocks(P->D);
+    size_t off = 0;
+    for (int d = 0; d < P->D; ++d) {
+      const taps_dim* dm = P->dims[d];
+      int nops = P->tt.nops[d];
+      TAPS_TRY(coefficients(P, d, M));
+      long long ny = (long long)nops * dm->nf * M;
+      int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
+      spmm_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(U->d_U[d], dm->nf, M, dm->hb,
+                                                               P->d_opband[d], nops, P->d_Y);
+      TAPS_CUDA(cudaGetLastError());
+      long long nr = (long long)dm->nf * M;
+      nblocks[d] = (int)((nr + 255) / 256);
+      als_residual_kernel<<<nblocks[d], 256, 0, s>>>(P->d_Y, nops, dm->nf, M, P->d_C, P->d_q[d],
+                                                     P->d_c, P->Rf, P->d_partial + off);
+      prof_end(P, TAPS_PROF_RESIDUAL, tk, 2.0 * ny * dm->nb + 2.0 * nops * (double)nr * M + 2.0 * P->Rf * nr,
+               8.0 * (2.0 * ny + (double)nr * (nops + 1)));
+      P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
+      TAPS_CUDA(cudaGetLastError());
+      off += 2 * (size_t)nblocks[d];
+    }
+    std::vector<double> h(off);
+    TAPS_CUDA(cudaMemcpyAsync(h.data(), P->d_partial, off * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TAPS_CUDA(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    off = 0;
+    for (int d = 0; d < P->D; ++d) {
+      double r2 = 0.0, f2 = 0.0;
+      for (int b = 0; b < nblocks[d]; ++b) {
+        r2 += h[off + 2 * b];
+        f2 += h[off + 2 * b + 1];
+      }
+      off += 2 * (size_t)nblocks[d];
+      double v = f2 > 0.0 ? sqrt(r2 / f2) : INFINITY;
+      worst = std::max(worst, v);
+    }
+    if (!std::isfinite(worst)) return TAPS_ERR_NONFINITE;
+    *rho_out = worst;
+    prof_drain(P);
+    return taps_check_status(P->d_status, s);
+  }
+  if (kind != TAPS_RES_FULL) return TAPS_ERR_INVALID_ARG;
+  BigGramPtrs bg;
+  memset(&bg, 0, sizeof(bg));
+  size_t goff = 0;
+  for (int d = 0; d < P->D; ++d) {
+    const taps_dim* dm = P->dims[d];
+    int nops = P->tt.nops[d];
+    int NC = nops * M + P->Rf;
+    long long ny = (long long)nops * dm->nf * M;
+    int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
+    spmm_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(U->d_U[d], dm->nf, M, dm->hb,
+                                                             P->d_opband[d], nops, P->d_Y);
+    TAPS_CUDA(cudaGetLastError());
+    P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
+    prof_end(P, TAPS_PROF_RESIDUAL, tk, 2.0 * ny * dm->nb + 2.0 * (double)NC * NC * dm->nf, 8.0 * 2.0 * ny);
+    big_gram_kernel<<<(unsigned)(((long long)NC * NC + 127) / 128), 128, 0, s>>>(
+        P->d_Y, nops, dm->nf, M, P->d_q[d], P->Rf, P->d_bigG + goff);
+    TAPS_CUDA(cudaGetLastError());
+    bg.G[d] = P->d_bigG + goff;
+    bg.NC[d] = NC;
+    goff += (size_t)NC * NC;
+  }
+  const int nblk = 64;
+  int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
+  full_residual_combine_kernel<<<nblk, 256, 0, s>>>(P->tt, bg, M, P->d_partial);
+  prof_end(P, TAPS_PROF_RESIDUAL, tk, (double)P->R * M * P->R * M * (P->D + 1), 8.0 * (double)goff);
+  TAPS_CUDA(cudaGetLastError());
+  double h[3 * nblk];
+  TAPS_CUDA(cudaMemcpyAsync(h, P->d_partial, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TAPS_CUDA(cudaStreamSynchronize(s));
+  double FF = 0.0, FA = 0.0, AA = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    FF += h[3 * b];
+    FA += h[3 * b + 1];
+    AA += h[3 * b + 2];
+  }
+  double r2 = FF - 2.0 * FA + AA;
+  double rho = sqrt(std::max(r2, 0.0) / FF);
+  if (!std::isfinite(rho)) return TAPS_ERR_NONFINITE;
+  *rho_out = rho;
+  prof_drain(P);
+  return taps_check_status(P->d_status, s);
+}

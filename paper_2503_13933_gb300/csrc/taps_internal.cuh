@@ -1,0 +1,236 @@
+// Internal declarations shared by the TAPS CUDA translation units (GPU path only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "taps.h"
+
+#define TAPS_WARP 32
+
+// Record a CUDA error and return TAPS_ERR_CUDA from the calling entry point.
+#define TAPS_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) {                             \
+      taps_note_cuda_error(e_, #call, __FILE__, __LINE__); \
+      return TAPS_ERR_CUDA;                              \
+    }                                                    \
+  } while (0)
+
+#define TAPS_TRY(expr)          \
+  do {                          \
+    int s_ = (expr);            \
+    if (s_ != TAPS_OK) return s_; \
+  } while (0)
+
+void taps_note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+int taps_alloc(void** p, size_t bytes);
+
+// Device status word values (set with atomicCAS so the first error wins).
+#define TAPS_DEV_OK 0
+#define TAPS_DEV_SINGULAR 1
+#define TAPS_DEV_NONFINITE 2
+#define TAPS_DEV_TIMEOUT 3
+int taps_status_from_device(int dev);
+
+// ---------------------------------------------------------------------------------
+// Assembled dimension: C-HiDeNN tables and banded 1D matrices on the device.
+// ---------------------------------------------------------------------------------
+struct taps_dim {
+  taps_dim_desc desc;
+  int n;        // all nodes
+  int nf;       // free nodes
+  int off;      // index of the first free node (1 with a Dirichlet low end)
+  int hb;       // band half-width 2s+1
+  int nb;       // band width 2hb+1
+  int amax;     // max patch size 2s+1
+  int pmax;     // moment-matrix size 2s+1+p+1
+  int nloc;     // nodes touching one element 2s+2
+  int nq;       // Gauss points per element
+  double h;     // element size
+  double gq_t[TAPS_MAX_QUAD];  // Gauss abscissae on [0,1]
+  double gq_w[TAPS_MAX_QUAD];  // Gauss weights on [0,1]
+  cudaStream_t stream;
+  double* d_ginv;       // [n][amax][pmax]: first |A| rows of each patch's G_i^{-1}
+  double* d_N;          // [n-1][nq][nloc]
+  double* d_B;          // [n-1][nq][nloc]
+  double* d_xq;         // [n-1][nq]
+  double* d_band_full;  // [TAPS_NUM_OPS][n][nb]
+  double* d_band;       // [TAPS_NUM_OPS][nf][nb] restricted to the free nodes
+  int* d_status;
+};
+
+// Term table passed by value to the kernels that combine dimensions.
+struct TermTable {
+  int D, R, Rf;
+  double alpha[TAPS_MAX_TERMS];
+  double beta[TAPS_MAX_TERMS];
+  signed char oi[TAPS_MAX_TERMS][TAPS_MAX_DIMS];  // distinct-op index of term t in dim d
+  int nops[TAPS_MAX_DIMS];
+};
+
+struct GramPtrs {
+  const double* gram[TAPS_MAX_DIMS];  // [nops_d][M][M]
+  const double* h[TAPS_MAX_DIMS];     // [Rf][M]
+};
+
+struct ProfPending {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+struct ProfState {
+  bool events;
+  long long launches[TAPS_PROF_NUM];
+  double ms[TAPS_PROF_NUM];
+  double flops[TAPS_PROF_NUM];
+  double bytes[TAPS_PROF_NUM];
+  ProfPending pending[512];
+  int npending;
+  cudaEvent_t pool[1024];
+  int npool;
+};
+
+struct taps_problem {
+  int D, R, Rf;
+  taps_dim* dims[TAPS_MAX_DIMS];
+  cudaStream_t stream;
+  TermTable tt;
+  int ops[TAPS_MAX_DIMS][TAPS_NUM_OPS];  // op kind of each distinct-op slot
+  int nf_max;
+  double* d_q[TAPS_MAX_DIMS];            // [Rf][nf_d] source projections
+  double* d_opband[TAPS_MAX_DIMS];       // [nops_d][nf_d][nb] bands of the distinct ops
+  // Workspace, grown to the largest mode count seen (ws_M).
+  int ws_M;
+  double* d_gram[TAPS_MAX_DIMS];  // [nops_d][M][M]
+  double* d_h[TAPS_MAX_DIMS];     // [Rf][M]
+  double* d_C;        // [TAPS_NUM_OPS][M][M] coefficient matrices of the current dim
+  double* d_c;        // [Rf][M]
+  double* d_F;        // [nf_max][M] reduced right-hand side (node-major)
+  double* d_blocks;   // [nf_max][nb][M][M] block band of the reduced matrix
+  double* d_lu;       // [M][M] LU of the current diagonal block
+  double* d_Y;        // [TAPS_NUM_OPS][nf_max][M] SpMM products
+  double* d_Uold;     // [nf_max][M]
+  double* d_partial;  // partial sums of the Gram and residual kernels
+  size_t partial_len;
+  double* d_scal;     // small scalar scratch
+  double* d_bigG;     // [D][NC][NC] residual Grams
+  size_t bigG_len;
+  int* d_status;
+  unsigned* d_bar;    // grid barrier words (count, generation)
+  double* h_scal;     // pinned host mirror of d_scal
+  double* d_Usnap[TAPS_MAX_DIMS];  // factor snapshot for the FP32 -> FP64 retry
+  void* d_evalbuf;    // grow-only gathered rows of taps_eval_grid
+  size_t evalbuf_len;
+  int eval_attr_set;  // shared-memory opt-in of the reconstruction kernels done
+  int coop_blocks;    // CTAs of the cooperative block solve
+  int num_sms;
+  ProfState* prof;
+};
+
+// Profiling helpers: prof_begin returns a token passed to prof_end.
+int prof_begin(taps_problem* P, int cls);
+void prof_end(taps_problem* P, int cls, int token, double flops, double bytes);
+void prof_drain(taps_problem* P);
+
+struct taps_factors {
+  const taps_problem* prob;
+  int M, M_cap;
+  double* d_U[TAPS_MAX_DIMS];  // [nf_d][M_cap] column-major, leading dim nf_d
+};
+
+// ---------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void taps_flag(int* status, int code) {
+  atomicCAS(status, TAPS_DEV_OK, code);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum for blockDim.x <= 1024; `red` holds >= 32 T in shared memory.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  T r = (threadIdx.x < nw) ? red[threadIdx.x] : T(0);
+  if (w == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) red[0] = r;
+  __syncthreads();
+  r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Grid barrier for a cooperative launch (all CTAs co-resident).  Sense-reversal on
+// a generation counter; every wait is bounded: after `limit` polls the barrier
+// records TAPS_DEV_TIMEOUT and stops waiting, and later barriers return at once, so
+// the kernel always runs to its end and the host reads the status.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* vstat = status;
+    if (*vstat != TAPS_DEV_TIMEOUT) {
+      unsigned gen = *vgen;
+      __threadfence();
+      unsigned arrived = atomicAdd(bar, 1u);
+      if (arrived == nblocks - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        long long polls = 0;
+        while (*vgen == gen) {
+          if (++polls > (1ll << 26)) {  // ~seconds: far above any legitimate wait
+            taps_flag(status, TAPS_DEV_TIMEOUT);
+            break;
+          }
+          if (*vstat == TAPS_DEV_TIMEOUT) break;
+          __nanosleep(20);
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): state += golden gamma, then the output mix.
+__host__ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Counter = seed (24 bits) | dim (8) | mode (12) | row (20); top 53 bits -> U(-1,1).
+__host__ __device__ __forceinline__ double taps_uniform_pm1(unsigned seed, int d, int i, int m) {
+  uint64_t ctr = ((uint64_t)(seed & 0xFFFFFFu) << 40) | ((uint64_t)(d & 0xFF) << 32) |
+                 ((uint64_t)(m & 0xFFF) << 20) | (uint64_t)(i & 0xFFFFF);
+  uint64_t z = splitmix64_mix(ctr);
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// ---------------------------------------------------------------------------------
+// Entry points between translation units
+// ---------------------------------------------------------------------------------
+int taps_ws_ensure(taps_problem* P, int M);
+int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision);
+int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision);
+int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
+                    double* change_out);
+int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
+int taps_check_status(int* d_status, cudaStream_t s);

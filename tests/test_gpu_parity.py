@@ -1,0 +1,305 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 path <= 1e-10 relative (assembly <= 1e-12); fields are compared,
+not raw factors, except for runs from the same seeded factors over a few sweeps,
+where the normalised factors themselves must agree."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import taps_oracle as O
+from paper_2503_13933_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_13933_gb300 import build, taps
+    build.build()
+    taps.lib()
+    return taps
+
+
+def to_band(A, hb):
+    n = A.shape[0]
+    out = np.zeros((n, 2 * hb + 1))
+    for i in range(n):
+        for k in range(2 * hb + 1):
+            j = i + k - hb
+            if 0 <= j < n:
+                out[i, k] = A[i, j]
+    return out
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+DIMS = [
+    W.dim(16, 0.0, 1.0),
+    W.dim(23, -0.5, 2.0, s=1, p=1),
+    W.dim(19, 1.0, 10.0, kind=W.PARAM, dirichlet_lo=False, dirichlet_hi=False,
+          weight_poly=(0.5, 1.0, 0.25, 0.1)),
+    W.dim(13, 0.0, 2.0, kind=W.TIME, dirichlet_hi=False),
+    W.dim(21, 0.0, 1.0, s=3, p=3, n_quad=8),
+    W.dim(40, 0.0, 3.0, s=4, p=2, dirichlet_lo=False),
+]
+
+
+@pytest.mark.parametrize("dm", DIMS, ids=lambda d: f"n{d['n']}s{d['s']}p{d['p']}")
+def test_assembly_parity(T, dm):
+    """A1/A2: shape tables and every banded 1D matrix vs the oracle (<= 1e-12)."""
+    g = T.Dim(dm)
+    od = O.dim_from_description(dm)
+    mats = O.assemble_free(od)
+    for name, op in O.OP_BY_NAME.items():
+        assert rel(g.band(name), to_band(mats[op], g.hb)) < 5e-12, name
+    N, B, X = g.shape_tables()
+    tab = O.shape_tables(od)
+    s = dm["s"]
+    for e in (0, 1, dm["n"] // 2, dm["n"] - 2):
+        for q, (xe, wj, ids, Nv, Bv) in enumerate(tab[e]):
+            assert abs(X[e, q] - xe) < 1e-14
+            for c, k in enumerate(ids):
+                assert abs(N[e, q, k - (e - s)] - Nv[c]) < 5e-12
+                assert abs(B[e, q, k - (e - s)] - Bv[c]) < 1e-10 * max(1, np.max(np.abs(Bv)))
+
+
+def test_assembly_rejects_bad_patches(T):
+    bad = W.dim(8, 0.0, 1.0, s=1, p=2)     # end patch of 2 nodes < p+1
+    with pytest.raises(T.TapsError) as e:
+        T.Dim(bad)
+    assert e.value.status == T.ERR_INVALID_ARG
+    with pytest.raises(T.TapsError):
+        T.Dim(W.dim(8, 0.0, 1.0, s=5, p=1))   # s beyond the supported maximum
+
+
+def _pair(desc):
+    return O.problem_from_description(desc), None
+
+
+def _poisson_nodal(n, nsrc, seed):
+    """3D Poisson with random separable nodal sources (a solution of CP rank > 1, so
+    that a few modes are well posed; the sine source gives a nearly rank-1 solution)."""
+    desc = W.poisson_sin(n)
+    rng = np.random.default_rng(seed)
+    desc["sources"] = [(1.0, [("nodal", rng.uniform(-1, 1, n)) for _ in range(3)])
+                       for _ in range(nsrc)]
+    return desc
+
+
+CASES = {
+    "poisson3d_n12": _poisson_nodal(12, 4, seed=31),
+    "poisson_k_7x9": W.poisson_k(n_space=11, n_k=9, seed=2002),
+    "heat2d_robin": W.heat_transient(n_space=10, n_t=9, D_space=2, h_conv=3.0),
+    "heat3d_ragged": W.heat_transient(n_space=19, n_t=7, D_space=3, seed=3001),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_sources_parity(T, name):
+    desc = CASES[name]
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    for r, (beta, qs) in enumerate(Po.sources):
+        for d in range(Po.D):
+            assert rel(P.source(r, d), qs[d]) < 1e-12
+
+
+@pytest.mark.parametrize("name,M,nsw", [("poisson3d_n12", 3, 3), ("poisson_k_7x9", 4, 2),
+                                        ("heat2d_robin", 5, 3), ("heat3d_ragged", 2, 2),
+                                        ("poisson3d_n12", 1, 2)])
+def test_sweep_parity_same_seed(T, name, M, nsw):
+    """A3-A8: from the same seeded factors, k sweeps give the same normalised factors
+    (<= 1e-10) and the same factor change."""
+    desc = CASES[name]
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=17 + M)
+    Ug = P.factors(max(M, 4))
+    Ug.set(U0)
+    rep = P.sweep(Ug, nsw)
+    Uo = [u.copy() for u in U0]
+    for _ in range(nsw):
+        Uo, ch = O.sweep(Po, Uo)
+    Ugot = Ug.get()
+    for d in range(Po.D):
+        assert rel(Ugot[d], Uo[d]) < 1e-10, (d, rel(Ugot[d], Uo[d]))
+    assert abs(rep["change"] - ch) <= 1e-9 * max(1.0, ch)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_residual_parity(T, name):
+    """A9: the residual of Eq. 42 and the full-system residual vs the oracle."""
+    desc = CASES[name]
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, 3, seed=5)
+    Ug = P.factors(3)
+    Ug.set(U0)
+    r_als = P.residual(Ug, T.RES_ALS)
+    r_full = P.residual(Ug, T.RES_FULL)
+    assert abs(r_als - O.als_residual(Po, U0)) < 1e-10 * max(1.0, r_als)
+    ro = O.residual(Po, U0)[0]
+    assert abs(r_full - ro) < 1e-7 + 1e-9 * ro
+    assert abs(r_full - O.residual_explicit(Po, U0)) < 1e-7 + 1e-9 * ro
+
+
+def test_solve_poisson_16cubed_vs_brute_force(T):
+    """Greedy solve on 16^3 vs the oracle's greedy solve and the full Kronecker FE
+    solution: reconstructed fields agree (FP64 <= 1e-10 against the oracle)."""
+    desc = W.poisson_sin(16)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    Ug = P.factors(4)
+    # res_tol < 0: never stop on the residual (it can reach its cancellation floor 0)
+    rep = P.solve(Ug, M0=1, M_max=3, als_tol=1e-12, res_tol=-1.0, res_kind=T.RES_FULL,
+                  max_sweeps=100, init=T.INIT_ZERO)
+    ro = O.solve(Po, M0=1, M_max=3, als_tol=1e-12, res_tol=-1.0, max_sweeps=100, init="zero")
+    ug = O.cp_full(Ug.get())
+    uo = O.cp_full(ro.U)
+    assert rep["M"] == 3
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-10
+    u_full = O.solve_full(Po)
+    assert np.linalg.norm(ug - u_full) / np.linalg.norm(u_full) < 1e-6
+    assert abs(rep["rho_full"] - O.residual(Po, ro.U)[0]) < 1e-7
+
+
+def test_solve_random_init_matches_oracle_counter_rng(T):
+    """TAPS_INIT_RANDOM draws the same SplitMix64 values as the oracle."""
+    desc = W.poisson_k(n_space=9, n_k=7, seed=2004)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    Ug = P.factors(3)
+    P.solve(Ug, M0=3, M_max=3, max_sweeps=1, res_tol=-1.0, als_tol=0.0, init=T.INIT_RANDOM, seed=99)
+    Uo = O.init_factors(Po, 3, "random", 99)
+    Uo, _ = O.sweep(Po, Uo)
+    got = Ug.get()
+    for d in range(Po.D):
+        assert rel(got[d], Uo[d]) < 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_eval_grid_parity(T, dtype):
+    """A10: grid reconstruction on strided node slices (constrained nodes = 0)."""
+    desc = W.heat_transient(n_space=14, n_t=11, D_space=2, h_conv=1.0)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, 7, seed=3)
+    Ug = P.factors(7)
+    Ug.set(U0)
+    start, count, step = [0, 1, 0], [14, 5, 11], [1, 3, 1]
+    idx = [list(range(s, s + c * st, st)) for s, c, st in zip(start, count, step)]
+    ref = O.eval_grid(Po, U0, idx)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    out = torch.empty(int(np.prod(count)), dtype=tdt, device="cuda")
+    P.eval_grid(Ug, start, count, step, out, dtype=T.FP64 if dtype == "f64" else T.FP32)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy().reshape(count)
+    tol = 1e-13 if dtype == "f64" else 2e-6
+    assert rel(got, ref) < tol
+
+
+def test_eval_points_parity(T):
+    """Point evaluation with the C-HiDeNN shape functions (Eq. 13)."""
+    desc = W.poisson_k(n_space=12, n_k=8, seed=2005)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, 4, seed=8)
+    Ug = P.factors(4)
+    Ug.set(U0)
+    rng = np.random.default_rng(0)
+    pts = np.stack([rng.uniform(0, 1, 50), rng.uniform(0, 1, 50), rng.uniform(0, 1, 50),
+                    rng.uniform(1, 10, 50)], axis=1)
+    pts[0] = [0.0, 1.0, 0.5, 1.0]
+    ref = O.eval_points(Po, U0, pts)
+    out = torch.empty(50, dtype=torch.float64, device="cuda")
+    P.eval_points(Ug, torch.tensor(pts, device="cuda"), out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) < 1e-12
+
+
+def _full_rank_2d(n, nsrc, seed):
+    """D = 2 Poisson with nsrc random separable nodal sources: with M = n_free modes
+    the CP space holds every grid function, so one sweep from full-rank factors gives
+    the full Galerkin solution."""
+    desc = W.poisson_sin(n, D=2)
+    rng = np.random.default_rng(seed)
+    desc["sources"] = [(1.0, [("nodal", rng.uniform(-1, 1, n)) for _ in range(2)])
+                       for _ in range(nsrc)]
+    return desc
+
+
+def test_full_rank_2d_more_than_32_modes(T):
+    """M = 34 > 32 (several rows per lane in the block triangular solves): one sweep
+    reaches the brute-force Kronecker solution, and matches the oracle's sweep."""
+    desc = _full_rank_2d(36, 40, seed=21)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, 34, seed=4)
+    Ug = P.factors(34)
+    Ug.set(U0)
+    P.sweep(Ug, 1)
+    u_full = O.solve_full(Po)
+    ug = O.cp_full(Ug.get())
+    assert np.linalg.norm(ug - u_full) / np.linalg.norm(u_full) < 1e-9
+    Uo, _ = O.sweep(Po, U0)
+    # 34 modes from random factors: the reduced systems carry kappa ~ 1e5, so two
+    # FP64 eliminations (no pivoting vs LAPACK partial pivoting) agree to ~kappa*eps
+    assert np.linalg.norm(ug - O.cp_full(Uo)) / np.linalg.norm(u_full) < 1e-8
+
+
+def test_fp32_grams_then_fp64_polish(T):
+    """Mixed precision: FP32 Gram sweeps, then FP64 polishing, reach the full-rank
+    solution to FP64 accuracy; FP32 alone stays near single precision."""
+    desc = _full_rank_2d(20, 20, seed=22)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    u_full = O.solve_full(Po)
+    U32 = P.factors(18)
+    U32.set(W.random_factors(desc, 18, seed=6))
+    P.sweep(U32, 2, precision=T.FP32)
+    e32 = np.linalg.norm(O.cp_full(U32.get()) - u_full) / np.linalg.norm(u_full)
+    # FP32 Grams of 18 random modes carry kappa-amplified single-precision error
+    assert 1e-9 < e32 < 0.5
+    r = P.solve(U32, M_max=18, res_tol=1e-11, max_sweeps=20, init=T.INIT_GIVEN,
+                precision=T.FP32, polish_sweeps=5)
+    assert r["converged"] and r["fp64_sweeps"] >= 1
+    e = np.linalg.norm(O.cp_full(U32.get()) - u_full) / np.linalg.norm(u_full)
+    assert e < 1e-10
+
+
+def test_fp32_solve_poisson_matches_fp64(T):
+    """3D Poisson, greedy to a full-residual target: the mixed-precision solve and the
+    FP64 solve reconstruct the same field within the mixed-path bound 1e-6."""
+    desc = W.poisson_sin(20)
+    P = T.Problem(desc)
+    U64, U32 = P.factors(3), P.factors(3)
+    r64 = P.solve(U64, M0=1, M_max=3, res_tol=1e-7, res_kind=T.RES_FULL, max_sweeps=50)
+    r32 = P.solve(U32, M0=1, M_max=3, res_tol=1e-7, res_kind=T.RES_FULL, max_sweeps=50,
+                  precision=T.FP32, polish_sweeps=10)
+    assert r64["converged"] and r32["converged"]
+    a, b = O.cp_full(U64.get()), O.cp_full(U32.get())
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-6
+
+
+def test_degenerate_inputs(T):
+    """Edge cases: one free node per dim... and bad arguments come back as statuses."""
+    desc = W.poisson_sin(3, D=2, s=1, p=1)     # one free node per dim
+    P = T.Problem(desc)
+    Ug = P.factors(2)
+    rep = P.solve(Ug, M0=1, M_max=1, res_tol=1e-12, max_sweeps=5, init=T.INIT_ZERO)
+    Po = O.problem_from_description(desc)
+    u_full = O.solve_full(Po)
+    assert abs(O.cp_full(Ug.get())[0] - u_full[0]) < 1e-12 * abs(u_full[0])
+    with pytest.raises(T.TapsError):
+        P.factors(0)
+    with pytest.raises(T.TapsError):
+        P.solve(Ug, M0=1, M_max=3)       # M_max > M_cap
