@@ -457,7 +457,16 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       if (change <= o->als_tol) break;
       if (prec == TAPS_FP32) {
         // FP32 Grams stop helping once the residual no longer falls: refine in FP64.
+        // If the FP32 sweep made the residual grow (an ill-conditioned factor set
+        // amplifies single-precision Gram errors), go back to the pre-sweep factors.
         if (rho > 0.5 * prev_rho) {
+          if (rho > prev_rho && std::isfinite(prev_rho)) {
+            for (int d = 0; d < P->D; ++d)
+              TAPS_CUDA(cudaMemcpyAsync(U->d_U[d], P->d_Usnap[d], sizeof(double) * P->dims[d]->nf * M,
+                                        cudaMemcpyDeviceToDevice, P->stream));
+            TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
+            rho = prev_rho;
+          }
           if (polish_left <= 0) break;
           prec = TAPS_FP64;
         }
@@ -491,13 +500,16 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
 
 // ---------------------------------------------------------------------------------
 // Grid reconstruction (Eq. 13 at nodes): u[i_1..i_D] = sum_m prod_d U_d[i_d, m].
-// Rows of the gathered factors G_d [count_d][M] carry 0 at constrained nodes.  A CTA
-// owns ER prefix rows (indices of dims 0..D-2) and all `last` entries of dim D-1.
+// The dims are split into leading "row" dims and trailing "column" dims (at least
+// 128 columns when the grid allows), so the output is the rank-M product
+// out[r][c] = sum_m A[r][m] B[c][m] with A = row-wise products of the leading dims'
+// factor rows and B = those of the trailing dims.  A and B are built by
+// eval_factor_kernel; eval_gemm_kernel streams the output with register tiles.
 // ---------------------------------------------------------------------------------
 struct GridSpec {
   int D;
   int count[TAPS_MAX_DIMS];
-  long long goff[TAPS_MAX_DIMS];  // offsets of G_d in the gathered buffer
+  long long goff[TAPS_MAX_DIMS];  // offsets of the gathered rows G_d [count_d][M]
 };
 
 template <typename T>
@@ -511,77 +523,136 @@ __global__ void gather_rows_kernel(const double* U, int nf, int off, int start, 
   G[idx] = (fj >= 0 && fj < nf) ? (T)U[(size_t)m * nf + fj] : (T)0;
 }
 
-// A CTA owns ER prefix rows and a tile of up to ECT entries of the last dim.  The
-// prefix products P[r][m] and the transposed last-dim rows GLt[m][j] are staged in
-// shared memory; each thread produces 4 consecutive outputs of one row (vector
-// store when the row start is 16-byte aligned), so the kernel streams the output.
-#define ER 32
-#define ECT 256
+// X[x][m] = prod_{d in [d0, d1)} G_d[i_d(x)][m], x in C order over dims d0..d1-1.
+template <typename T>
+__global__ void eval_factor_kernel(const T* __restrict__ G, GridSpec gs, int d0, int d1, int M,
+                                   long long nx, T* __restrict__ X) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nx * M) return;
+  long long x = idx / M;
+  int m = (int)(idx - x * M);
+  T v = (T)1;
+  for (int d = d1 - 1; d >= d0; --d) {
+    long long q = x / gs.count[d];
+    int id = (int)(x - q * gs.count[d]);
+    x = q;
+    v *= G[gs.goff[d] + (long long)id * M + m];
+  }
+  X[idx] = v;
+}
+
+// out[r][c] = sum_m A[r][m] B[c][m].  CTA tile 128 x 128 (256 threads), thread tile
+// 8 x 8 with rows ty + 16a and columns tx + 16b, so that shared-memory reads are
+// broadcasts / conflict-free and every warp store covers two 64-byte row segments.
+// The tiles are stored transposed ([m][row]) with a padded stride (129) so that the
+// transposing fill is conflict-free.  The FP32 product uses packed fma.rn.f32x2.
+#define EB 128
+#define EBP 129
+
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
 
 template <typename T>
-__global__ void __launch_bounds__(256) eval_grid_kernel(const T* __restrict__ G, GridSpec gs, int M,
-                                                        long long rows, int ect, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int last = gs.count[gs.D - 1];
-  const int j0 = blockIdx.y * ect;
-  const int ct = min(ect, last - j0);
-  T* Pr = reinterpret_cast<T*>(smraw);  // [ER][M]
-  T* GLt = Pr + ER * M;                 // [M][ct]
-  const long long r0 = (long long)blockIdx.x * ER;
-  const int nr = (int)min((long long)ER, rows - r0);
-  // prefix products of dims 0..D-2 (one 64-bit decomposition per row)
-  for (int idx = threadIdx.x; idx < nr * M; idx += blockDim.x) {
-    int rr = idx / M, m = idx - rr * M;
-    long long row = r0 + rr;
-    T v = (T)1;
-    for (int d = gs.D - 2; d >= 0; --d) {
-      long long q = row / gs.count[d];
-      int id = (int)(row - q * gs.count[d]);
-      row = q;
-      v *= G[gs.goff[d] + (long long)id * M + m];
-    }
-    Pr[rr * M + m] = v;
+__device__ __forceinline__ void eval_fill(const T* __restrict__ A, const T* __restrict__ B, long long r0,
+                                          int c0, int nr, int nc, int M, T* As, T* Bs) {
+  for (int idx = threadIdx.x; idx < EB * M; idx += blockDim.x) {
+    int r = idx / M, m = idx - r * M;
+    As[m * EBP + r] = (r < nr) ? A[(r0 + r) * M + m] : (T)0;
+    Bs[m * EBP + r] = (r < nc) ? B[(long long)(c0 + r) * M + m] : (T)0;
   }
-  const T* GL = G + gs.goff[gs.D - 1];
-  for (int idx = threadIdx.x; idx < ct * M; idx += blockDim.x) {
-    int j = idx / M, m = idx - j * M;
-    GLt[m * ct + j] = GL[(long long)(j0 + j) * M + m];
-  }
+}
+
+__global__ void __launch_bounds__(256) eval_gemm_f32_kernel(const float* __restrict__ A,
+                                                            const float* __restrict__ B, long long R,
+                                                            int C, int M, float* __restrict__ out) {
+  extern __shared__ __align__(16) float smf[];
+  float* As = smf;              // [M][EBP]
+  float* Bs = smf + M * EBP;    // [M][EBP]
+  const long long r0 = (long long)blockIdx.x * EB;
+  const int c0 = blockIdx.y * EB;
+  const int nr = (int)min((long long)EB, R - r0);
+  const int nc = min(EB, C - c0);
+  eval_fill<float>(A, B, r0, c0, nr, nc, M, As, Bs);
   __syncthreads();
-  const int groups = (ct + 3) >> 2;           // 4-wide column groups per row
-  const int ntask = nr * groups;
-  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-    int rr = t / groups, g4 = (t - rr * groups) << 2;
-    const T* p = Pr + rr * M;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    if (g4 + 3 < ct) {
-      for (int m = 0; m < M; ++m) {
-        T pv = p[m];
-        const T* g = GLt + m * ct + g4;
-        a0 += pv * g[0];
-        a1 += pv * g[1];
-        a2 += pv * g[2];
-        a3 += pv * g[3];
-      }
-    } else {
-      for (int m = 0; m < M; ++m) {
-        T pv = p[m];
-        const T* g = GLt + m * ct + g4;
-        a0 += pv * g[0];
-        if (g4 + 1 < ct) a1 += pv * g[1];
-        if (g4 + 2 < ct) a2 += pv * g[2];
-      }
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  unsigned long long acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0ull;
+  for (int m = 0; m < M; ++m) {
+    const float* ar = As + m * EBP + ty;
+    const float* br = Bs + m * EBP + tx;
+    unsigned long long bv[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = pack2(br[32 * b], br[32 * b + 16]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      float av = ar[16 * a];
+      unsigned long long aa = pack2(av, av);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[a][b]) : "l"(aa), "l"(bv[b]));
     }
-    T* o = out + (r0 + rr) * (long long)last + j0 + g4;
-    bool full = g4 + 3 < ct;
-    if (full && sizeof(T) == 4 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
-      float4 v = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
-      *reinterpret_cast<float4*>(o) = v;
-    } else {
-      o[0] = a0;
-      if (g4 + 1 < ct) o[1] = a1;
-      if (g4 + 2 < ct) o[2] = a2;
-      if (full) o[3] = a3;
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    int r = ty + 16 * a;
+    if (r >= nr) continue;
+    float* o = out + (r0 + r) * (long long)C + c0 + tx;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float lo, hi;
+      unpack2(acc[a][b], lo, hi);
+      if (tx + 32 * b < nc) __stcs(o + 32 * b, lo);
+      if (tx + 32 * b + 16 < nc) __stcs(o + 32 * b + 16, hi);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) eval_gemm_f64_kernel(const double* __restrict__ A,
+                                                            const double* __restrict__ B, long long R,
+                                                            int C, int M, double* __restrict__ out) {
+  extern __shared__ __align__(16) double smd[];
+  double* As = smd;
+  double* Bs = smd + M * EBP;
+  const long long r0 = (long long)blockIdx.x * EB;
+  const int c0 = blockIdx.y * EB;
+  const int nr = (int)min((long long)EB, R - r0);
+  const int nc = min(EB, C - c0);
+  eval_fill<double>(A, B, r0, c0, nr, nc, M, As, Bs);
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  for (int half = 0; half < 2; ++half) {  // 4 of the 8 rows per pass keeps registers bounded
+    double acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+    for (int m = 0; m < M; ++m) {
+      double av[4], bv[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[m * EBP + ty + 16 * (4 * half + a)];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) bv[b] = Bs[m * EBP + tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] += av[a] * bv[b];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int r = ty + 16 * (4 * half + a);
+      if (r >= nr) continue;
+      double* o = out + (r0 + r) * (long long)C + c0 + tx;
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        if (tx + 16 * b < nc) o[16 * b] = acc[a][b];
     }
   }
 }
@@ -609,16 +680,33 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
   if (!out_dev) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
   size_t esz = out_dtype == TAPS_FP64 ? sizeof(double) : sizeof(float);
-  if (esz * goff > P->evalbuf_len) {
+  int st = TAPS_OK;
+  int split = P->D - 1;
+  long long cols = count[P->D - 1];
+  while (split > 1 && cols < 128) cols *= count[--split];
+  if (cols > (1ll << 30)) return TAPS_ERR_INVALID_ARG;
+  long long rows = total / cols;
+  size_t need = esz * (goff + (size_t)(rows + cols) * M);
+  if (need > P->evalbuf_len) {
     TAPS_CUDA(cudaStreamSynchronize(s));
     cudaFree(P->d_evalbuf);
     P->d_evalbuf = nullptr;
     P->evalbuf_len = 0;
-    TAPS_TRY(taps_alloc(&P->d_evalbuf, esz * goff));
-    P->evalbuf_len = esz * goff;
+    TAPS_TRY(taps_alloc(&P->d_evalbuf, need));
+    P->evalbuf_len = need;
   }
   void* G = P->d_evalbuf;
-  int st = TAPS_OK;
+  if (!P->eval_attr_set) {
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    TAPS_CUDA(cudaFuncSetAttribute((const void*)eval_gemm_f64_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    TAPS_CUDA(cudaFuncSetAttribute((const void*)eval_gemm_f32_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    P->eval_attr_set = 1;
+  }
+  int tk = prof_begin(P, TAPS_PROF_EVAL);
   for (int d = 0; d < P->D; ++d) {
     const taps_dim* dm = P->dims[d];
     int n = count[d] * M;
@@ -631,24 +719,24 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
                                                                 step[d], count[d], M,
                                                                 (float*)G + gs.goff[d]);
   }
-  long long rows = total / count[P->D - 1];
-  int last = count[P->D - 1];
-  int ect = ECT;
-  while (ect > 4 && (size_t)(ER * M + M * std::min(last, ect)) * esz > 96 * 1024) ect >>= 1;
-  dim3 egrid((unsigned)((rows + ER - 1) / ER), (unsigned)((last + ect - 1) / ect));
-  size_t esm = (size_t)(ER * M + M * std::min(last, ect)) * esz;
-  if (!P->eval_attr_set) {
-    cudaFuncSetAttribute((const void*)eval_grid_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute((const void*)eval_grid_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    P->eval_attr_set = 1;
+  if (out_dtype == TAPS_FP64) {
+    double* A = (double*)G + goff;
+    double* B = A + rows * M;
+    eval_factor_kernel<double><<<(unsigned)((rows * M + 255) / 256), 256, 0, s>>>((const double*)G, gs, 0, split, M, rows, A);
+    eval_factor_kernel<double><<<(unsigned)((cols * M + 255) / 256), 256, 0, s>>>((const double*)G, gs, split, P->D, M, cols, B);
+    dim3 eg((unsigned)((rows + EB - 1) / EB), (unsigned)((cols + EB - 1) / EB));
+    eval_gemm_f64_kernel<<<eg, 256, (size_t)M * 2 * EBP * sizeof(double), s>>>(A, B, rows, (int)cols, M, (double*)out_dev);
+  } else {
+    float* A = (float*)G + goff;
+    float* B = A + rows * M;
+    eval_factor_kernel<float><<<(unsigned)((rows * M + 255) / 256), 256, 0, s>>>((const float*)G, gs, 0, split, M, rows, A);
+    eval_factor_kernel<float><<<(unsigned)((cols * M + 255) / 256), 256, 0, s>>>((const float*)G, gs, split, P->D, M, cols, B);
+    dim3 eg((unsigned)((rows + EB - 1) / EB), (unsigned)((cols + EB - 1) / EB));
+    eval_gemm_f32_kernel<<<eg, 256, (size_t)M * 2 * EBP * sizeof(float), s>>>(A, B, rows, (int)cols, M, (float*)out_dev);
   }
-  int tk = prof_begin(P, TAPS_PROF_EVAL);
-  if (out_dtype == TAPS_FP64)
-    eval_grid_kernel<double><<<egrid, 256, esm, s>>>((const double*)G, gs, M, rows, ect, (double*)out_dev);
-  else
-    eval_grid_kernel<float><<<egrid, 256, esm, s>>>((const float*)G, gs, M, rows, ect, (float*)out_dev);
-  prof_end(P, TAPS_PROF_EVAL, tk, 2.0 * M * (double)total + (double)rows * M * (P->D - 1),
-           (double)esz * total + (double)esz * goff);
+  P->prof->launches[TAPS_PROF_EVAL] += P->D + 2;  // gathers, two factor products, product
+  prof_end(P, TAPS_PROF_EVAL, tk, 2.0 * M * (double)total + (double)(rows + cols) * M * (P->D - 1),
+           (double)esz * total);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     taps_note_cuda_error(e, "eval_grid_kernel", __FILE__, __LINE__);
