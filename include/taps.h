@@ -49,6 +49,7 @@ extern "C" {
 #define TAPS_ERR_TIMEOUT (-5)       /* a bounded device-side wait ran out */
 #define TAPS_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define TAPS_ERR_OOM (-7)           /* device allocation failed */
+#define TAPS_ERR_SCRATCH_LIMIT (-8) /* request larger than the fixed scratch of taps_eval_grid_noalloc */
 
 /* ---- dimension kinds (Eq. 11: spatial, parametric, temporal variables) ------ */
 #define TAPS_SPACE 0
@@ -248,6 +249,27 @@ int taps_solve(taps_problem* prob, taps_factors* U, const taps_solve_opts* opts,
  * stream.  Errors: TAPS_ERR_INVALID_ARG for an index outside [0, n). */
 int taps_eval_grid(const taps_problem* prob, const taps_factors* U, const int* start,
                    const int* count, const int* step, void* out_dev, int out_dtype);
+/* Allocation-free variant of taps_eval_grid (the paper has no counterpart: this is a
+ * service for callers of this library).  Same arguments, same values (up to the
+ * order of the FP sums) and the same C-order output, but it allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  It is meant for callers
+ * that cannot allocate device memory when they need a field -- code that runs
+ * under a fixed, fully reserved memory budget, or inside a host framework whose hot
+ * path forbids allocation and the synchronisation an allocation may imply.  Its
+ * working memory (the gathered factor rows, sum_d count[d] * M values of the
+ * output type) lives in one fixed array of TAPS_NOALLOC_SCRATCH_BYTES in device
+ * global memory, which every GPU that loads this library holds until the process
+ * exits.  Requests that need more return TAPS_ERR_SCRATCH_LIMIT and touch nothing.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call on a device shares the one array and it keeps the last
+ * call's contents (each call overwrites all it reads, so nothing needs clearing);
+ * calls whose kernels overlap on the GPU -- on different streams, or different
+ * problems launched concurrently -- race on it and must be serialised by the
+ * caller.  Asynchronous on the problem's stream. */
+#define TAPS_NOALLOC_SCRATCH_BYTES (4u << 20)
+int taps_eval_grid_noalloc(const taps_problem* prob, const taps_factors* U, const int* start,
+                           const int* count, const int* step, void* out_dev, int out_dtype);
 /* Points: u^TD(x) = sum_m prod_d sum_I N~_I(x_d) U_d[I, m] at n_pts points; pts_dev is
  * device memory [n_pts][D] row-major (coordinates clamped to [lo, hi]); out_dev
  * receives n_pts FP64 values.  Asynchronous on the problem's stream. */

@@ -65,6 +65,8 @@ extern "C" const char* taps_status_string(int status) {
     case TAPS_ERR_TIMEOUT: return "device wait timed out";
     case TAPS_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
     case TAPS_ERR_OOM: return "out of device memory";
+    case TAPS_ERR_SCRATCH_LIMIT:
+      return "request exceeds the fixed scratch of taps_eval_grid_noalloc (TAPS_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown status";
   }
 }

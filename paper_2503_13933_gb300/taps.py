@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libtaps.so")
 MAX_DIMS = 8
 MAX_TERMS = 64
 OK, ERR_INVALID_ARG, ERR_SINGULAR, ERR_NONFINITE, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4
-ERR_TIMEOUT, ERR_CUDA, ERR_OOM = -5, -6, -7
+ERR_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SCRATCH_LIMIT = -5, -6, -7, -8
+NOALLOC_SCRATCH_BYTES = 4 << 20
 SPACE, PARAM, TIME = 0, 1, 2
 OP = {"K": 0, "M": 1, "G": 2, "W": 3, "Blo": 4, "Bhi": 5}
 NUM_OPS = 6
@@ -101,6 +102,7 @@ SIGNATURES = {
     "taps_solve": (_i, [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)]),
     "taps_eval_grid": (_i, [_vp, _vp, _pi, _pi, _pi, _vp, _i]),
     "taps_eval_points": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "taps_eval_grid_noalloc": (_i, [_vp, _vp, _pi, _pi, _pi, _vp, _i]),
     "taps_profile_reset": (_i, [_vp, _i]),
     "taps_profile_get": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong), _pd, _pd, _pd]),
 }
@@ -275,6 +277,17 @@ class Problem:
         s = (ctypes.c_int * D)(*step)
         check(lib().taps_eval_grid(self.handle, U.handle, a, c, s, ctypes.c_void_p(out.data_ptr()),
                                    dtype), "taps_eval_grid")
+        return out
+
+    def eval_grid_noalloc(self, U, start, count, step, out, dtype=FP32):
+        """Allocation-free reconstruction (fixed library scratch; see include/taps.h)."""
+        D = self.D
+        a = (ctypes.c_int * D)(*start)
+        c = (ctypes.c_int * D)(*count)
+        s = (ctypes.c_int * D)(*step)
+        check(lib().taps_eval_grid_noalloc(self.handle, U.handle, a, c, s,
+                                           ctypes.c_void_p(out.data_ptr()), dtype),
+              "taps_eval_grid_noalloc")
         return out
 
     def eval_points(self, U, pts, out):
