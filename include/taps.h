@@ -87,6 +87,9 @@ extern "C" {
 
 /* ---- reduced solvers ---------------------------------------------------------- */
 #define TAPS_SOLVER_BLOCK_LU 0   /* block-banded Gaussian elimination, FP64 */
+#define TAPS_SOLVER_FASTDIAG 1   /* fast diagonalisation (Sec. 2.6) for every dimension whose
+                                    operators form a symmetric pencil with a mass-like partner
+                                    (K/M, W, ...); block LU for the others (e.g. time) */
 
 typedef struct taps_dim taps_dim;
 typedef struct taps_problem taps_problem;
@@ -291,8 +294,9 @@ int taps_eval_points(const taps_problem* prob, const taps_factors* U, int n_pts,
 #define TAPS_PROF_NORMALIZE 5     /* column normalisation + factor change           */
 #define TAPS_PROF_RESIDUAL 6      /* residual kernels                               */
 #define TAPS_PROF_EVAL 7          /* grid reconstruction                            */
-#define TAPS_PROF_OTHER 8         /* initialisation, copies                         */
-#define TAPS_PROF_NUM 9
+#define TAPS_PROF_OTHER 8         /* initialisation, pencil set-up, copies           */
+#define TAPS_PROF_FASTDIAG 9      /* fast-diagonalisation reduced solve              */
+#define TAPS_PROF_NUM 10
 int taps_profile_reset(taps_problem* prob, int enable_events);
 int taps_profile_get(taps_problem* prob, int kernel_class, long long* launches, double* ms,
                      double* flops, double* bytes);

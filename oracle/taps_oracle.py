@@ -398,6 +398,43 @@ def solve_block_banded(prob: Problem, d, C, F):
     return X
 
 
+def fast_diag_pencil(prob: Problem, d, C):
+    """Operator pencil of dim d for fast diagonalisation (Sec. 2.6): returns (opA, opB)
+    with opB mass-like (M or W) and both symmetric, opA None for a single operator;
+    None if the dim's operators do not form such a pencil."""
+    ops = list(C.keys())
+    if any(o == OP_G for o in ops) or not 1 <= len(ops) <= 2:
+        return None
+    if len(ops) == 1:
+        return None, ops[0]
+    mass = [o for o in ops if o in (OP_M, OP_W)]
+    if not mass:
+        return None
+    b = mass[0]
+    return [o for o in ops if o != b][0], b
+
+
+def solve_fast_diag(prob: Problem, d, C, F):
+    """Fast diagonalisation of sum_op Op U C_op^T = F (Sec. 2.6): with the generalised
+    eigenpairs A phi = mu B phi (Phi^T B Phi = I; library symmetric-definite eigensolver),
+    U = Phi Y and (mu_i C_A + C_B) Y[i]^T = (Phi^T F)[i]^T for each i."""
+    import scipy.linalg
+    opA, opB = fast_diag_pencil(prob, d, C)
+    B = prob.ops[d][opB]
+    if opA is None:
+        Phi = np.linalg.inv(np.linalg.cholesky(B)).T
+        mu = np.zeros(B.shape[0])
+    else:
+        mu, Phi = scipy.linalg.eigh(prob.ops[d][opA], B)
+    G = Phi.T @ F
+    M = F.shape[1]
+    Y = np.zeros_like(G)
+    for i in range(G.shape[0]):
+        T = C[opB] + (mu[i] * C[opA] if opA is not None else 0.0)
+        Y[i] = np.linalg.solve(T, G[i])
+    return Phi @ Y
+
+
 def normalise_columns(Ud):
     """Unit 2-norm columns; sign makes the largest-magnitude entry positive.
     (Scale normalisation is not stated by the paper; the next dimension's solve
@@ -427,6 +464,8 @@ def sweep(prob: Problem, U, solver="banded"):
         C, F = coefficients(prob, U, d)
         if solver == "dense":
             Ud = solve_dense(reduced_matrix_dense(prob, d, C), F)
+        elif solver == "fastdiag" and fast_diag_pencil(prob, d, C) is not None:
+            Ud = solve_fast_diag(prob, d, C, F)
         else:
             Ud = solve_block_banded(prob, d, C, F)
         if d < prob.D - 1:

@@ -378,7 +378,7 @@ extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const 
   int solver = opts ? opts->solver : TAPS_SOLVER_BLOCK_LU;
   int normalize = opts ? opts->normalize : 1;
   if (precision != TAPS_FP64 && precision != TAPS_FP32) return TAPS_ERR_INVALID_ARG;
-  if (solver != TAPS_SOLVER_BLOCK_LU) return TAPS_ERR_INVALID_ARG;
+  if (solver != TAPS_SOLVER_BLOCK_LU && solver != TAPS_SOLVER_FASTDIAG) return TAPS_ERR_INVALID_ARG;
   double t0 = now_s();
   TAPS_TRY(taps_ws_ensure(P, U->M));
   TAPS_TRY(taps_refresh_grams(P, U, precision));
@@ -405,7 +405,8 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
   if (o->M_max < 1 || o->M_max > U->M_cap || o->max_sweeps < 1 ||
       (o->precision != TAPS_FP64 && o->precision != TAPS_FP32) ||
       (o->res_kind != TAPS_RES_ALS && o->res_kind != TAPS_RES_FULL) ||
-      o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO || o->solver != TAPS_SOLVER_BLOCK_LU)
+      o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO ||
+      (o->solver != TAPS_SOLVER_BLOCK_LU && o->solver != TAPS_SOLVER_FASTDIAG))
     return TAPS_ERR_INVALID_ARG;
   double t0 = now_s();
   if (o->init != TAPS_INIT_GIVEN) {
@@ -432,7 +433,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
           TAPS_CUDA(cudaMemcpyAsync(P->d_Usnap[d], U->d_U[d], sizeof(double) * P->dims[d]->nf * M,
                                     cudaMemcpyDeviceToDevice, P->stream));
       }
-      int sst = taps_sweep_impl(P, U, prec, TAPS_SOLVER_BLOCK_LU, 1, &change);
+      int sst = taps_sweep_impl(P, U, prec, o->solver, 1, &change);
       if (prec == TAPS_FP32 && (sst == TAPS_ERR_SINGULAR || sst == TAPS_ERR_NONFINITE)) {
         // FP32 Grams cannot separate modes that agree to ~1e-8 (a Gram entry rounds to
         // an exact duplicate): restore the factors and redo the sweep in FP64.
@@ -441,7 +442,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
                                     cudaMemcpyDeviceToDevice, P->stream));
         prec = TAPS_FP64;
         TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
-        sst = taps_sweep_impl(P, U, prec, TAPS_SOLVER_BLOCK_LU, 1, &change);
+        sst = taps_sweep_impl(P, U, prec, o->solver, 1, &change);
       }
       TAPS_TRY(sst);
       ++sweeps;

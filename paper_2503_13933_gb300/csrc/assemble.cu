@@ -367,6 +367,8 @@ static DimParams make_params(const taps_dim* d) {
 
 extern "C" void taps_dim_destroy(taps_dim* d) {
   if (!d) return;
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  taps_fd_release(d);
   cudaFree(d->d_ginv);
   cudaFree(d->d_N);
   cudaFree(d->d_B);

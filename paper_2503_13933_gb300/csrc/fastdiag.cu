@@ -1,0 +1,495 @@
+// Fast-diagonalisation reduced solver (Sec. 2.6: the subspace system of one dimension
+// is a generalised Sylvester equation, solved by fast diagonalisation).
+//
+// For a dimension whose distinct operators form a symmetric-definite pencil (A, B)
+// (e.g. stiffness K and mass M; or a single SPD operator B, A = 0), the pencil is
+// diagonalised once: Phi^T B Phi = I, Phi^T A Phi = diag(mu).  The reduced system
+//     A U C_A^T + B U C_B^T = F        (U: n x M, C: M x M, possibly nonsymmetric)
+// becomes, with U = Phi Y and G = Phi^T F, n independent M x M systems
+//     (mu_i C_A + C_B) Y[i,:]^T = G[i,:]^T,
+// so a solve costs two n x n x M products and n small LU solves instead of a
+// sequential block elimination over the n block rows.
+//
+// The one-off pencil decomposition runs in one CTA in FP64: banded Cholesky
+// B = L L^T, S = L^{-1} A L^{-T}, Householder tridiagonalisation of S with the
+// reflectors accumulated, the implicit QL iteration with Wilkinson shifts on the
+// tridiagonal (rotations applied to the accumulated basis), and Phi = L^{-T} Z.
+#include <string.h>
+
+#include <algorithm>
+
+#include "taps_internal.cuh"
+
+#define FD_THREADS 1024
+
+__global__ void fd_dense_kernel(const double* __restrict__ bandA, const double* __restrict__ bandB, int n,
+                                int hb, double* __restrict__ A, double* __restrict__ B) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  int i = idx / n, j = idx % n, k = j - i + hb, nb = 2 * hb + 1;
+  bool in = (k >= 0 && k < nb);
+  A[idx] = (bandA && in) ? bandA[(size_t)i * nb + k] : 0.0;
+  B[idx] = in ? bandB[(size_t)i * nb + k] : 0.0;
+}
+
+// Single-CTA pencil decomposition.  A (n x n, row-major) is overwritten (S, then the
+// eigenvector basis Z); B holds the banded Cholesky factor L (lower) on exit.  V and
+// tmp are n x n and 2n scratch; Phi / PhiT receive L^{-T} Z and its transpose.
+__global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double* B, double* V, double* tmp,
+                                                              double* beta, double* d, double* e, int n,
+                                                              int hb, int hasA, double* Phi, double* PhiT,
+                                                              double* mu, int* status) {
+  __shared__ double red[32];
+  __shared__ double sh[8];
+  __shared__ int shi[8];
+  extern __shared__ double rot[];  // [2][n]: QL rotations (c, s) of one sweep
+  const int tid = threadIdx.x, nt = blockDim.x;
+#define AT(M_, i, j) M_[(size_t)(i) * n + (j)]
+
+  // ---- 1. banded Cholesky of B (lower factor in place; band half-width hb)
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      double piv = AT(B, k, k);
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        taps_flag(status, TAPS_DEV_SINGULAR);
+        piv = 1.0;
+      }
+      AT(B, k, k) = sqrt(piv);
+    }
+    __syncthreads();
+    double lkk = AT(B, k, k);
+    int top = min(n - 1, k + hb);
+    for (int i = k + 1 + tid; i <= top; i += nt) AT(B, i, k) /= lkk;
+    __syncthreads();
+    int w = top - k;
+    for (int idx = tid; idx < w * w; idx += nt) {
+      int i = k + 1 + idx / w, j = k + 1 + idx % w;
+      if (j <= i) AT(B, i, j) -= AT(B, i, k) * AT(B, j, k);
+    }
+    __syncthreads();
+  }
+
+  if (hasA) {
+    // ---- 2. X = L^{-1} A (column by column), then S = L^{-1} X^T (A symmetric)
+    for (int c = tid; c < n; c += nt) {
+      for (int i = 0; i < n; ++i) {
+        double s = AT(A, i, c);
+        for (int j = max(0, i - hb); j < i; ++j) s -= AT(B, i, j) * AT(A, j, c);
+        AT(A, i, c) = s / AT(B, i, i);
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt) {   // column r of S into V (row-major V[i][r])
+      for (int i = 0; i < n; ++i) {
+        double s = AT(A, r, i);
+        for (int j = max(0, i - hb); j < i; ++j) s -= AT(B, i, j) * AT(V, j, r);
+        AT(V, i, r) = s / AT(B, i, i);
+      }
+    }
+    __syncthreads();
+    for (long long idx = tid; idx < (long long)n * n; idx += nt) {
+      int i = idx / n, j = idx % n;
+      A[idx] = 0.5 * (AT(V, i, j) + AT(V, j, i));
+    }
+    __syncthreads();
+
+    // ---- 3. Householder tridiagonalisation of S (stored in A)
+    for (int k = 0; k + 2 < n; ++k) {
+      const int len = n - k - 1;
+      double s2 = 0.0;
+      for (int t = tid; t < len; t += nt) {
+        double x = AT(A, k + 1 + t, k);
+        s2 += x * x;
+      }
+      s2 = block_sum(s2, red);
+      if (s2 == 0.0) {
+        if (tid == 0) {
+          beta[k] = 0.0;
+          d[k] = AT(A, k, k);
+          e[k] = 0.0;
+        }
+        __syncthreads();
+        continue;
+      }
+      double x0 = AT(A, k + 1, k);
+      double alpha = -copysign(sqrt(s2), x0);
+      double v0 = x0 - alpha;
+      double vn2 = s2 - x0 * x0 + v0 * v0;
+      double bk = 2.0 / vn2;
+      for (int t = tid; t < len; t += nt) AT(V, k, k + 1 + t) = (t == 0) ? v0 : AT(A, k + 1 + t, k);
+      __syncthreads();
+      // p = beta S22 v (column access: S symmetric)
+      double pv = 0.0;
+      for (int i = tid; i < len; i += nt) {
+        double acc = 0.0;
+        for (int j = 0; j < len; ++j) acc += AT(A, k + 1 + j, k + 1 + i) * AT(V, k, k + 1 + j);
+        acc *= bk;
+        tmp[i] = acc;
+        pv += acc * AT(V, k, k + 1 + i);
+      }
+      pv = block_sum(pv, red);
+      double Kc = 0.5 * bk * pv;
+      for (int i = tid; i < len; i += nt) tmp[n + i] = tmp[i] - Kc * AT(V, k, k + 1 + i);  // w
+      __syncthreads();
+      for (long long idx = tid; idx < (long long)len * len; idx += nt) {
+        int i = idx / len, j = idx % len;
+        double vi = AT(V, k, k + 1 + i), vj = AT(V, k, k + 1 + j);
+        AT(A, k + 1 + i, k + 1 + j) -= vi * tmp[n + j] + tmp[n + i] * vj;
+      }
+      if (tid == 0) {
+        beta[k] = bk;
+        d[k] = AT(A, k, k);
+        e[k] = alpha;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (n >= 2) {
+        d[n - 2] = AT(A, n - 2, n - 2);
+        e[n - 2] = AT(A, n - 1, n - 2);
+      }
+      d[n - 1] = AT(A, n - 1, n - 1);
+      e[n - 1] = 0.0;
+      for (int k = max(0, n - 2); k < n; ++k) beta[k] = 0.0;
+    }
+    __syncthreads();
+
+    // ---- 4. accumulate Q = H_0 ... H_{n-3} into A (backward: Q <- H_k Q)
+    for (long long idx = tid; idx < (long long)n * n; idx += nt) A[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = n - 3; k >= 0; --k) {
+      double bk = beta[k];
+      if (bk == 0.0) continue;
+      const int len = n - k - 1;
+      for (int c = k + 1 + tid; c < n; c += nt) {
+        double z = 0.0;
+        for (int i = 0; i < len; ++i) z += AT(V, k, k + 1 + i) * AT(A, k + 1 + i, c);
+        z *= bk;
+        for (int i = 0; i < len; ++i) AT(A, k + 1 + i, c) -= AT(V, k, k + 1 + i) * z;
+      }
+      __syncthreads();
+    }
+
+    // ---- 5. implicit QL with Wilkinson shifts on (d, e); rotations -> columns of A
+    double* rc = rot;
+    double* rs = rot + n;
+    for (int l = 0; l < n; ++l) {
+      int iter = 0;
+      while (true) {
+        if (tid == 0) {
+          int m = l;
+          for (; m < n - 1; ++m) {
+            double dd = fabs(d[m]) + fabs(d[m + 1]);
+            if (fabs(e[m]) <= 2.220446049250313e-16 * dd) break;
+          }
+          int lo = m;   // rotations run i = m-1 .. stop (inclusive); none if m == l
+          int stop = m;
+          if (m != l) {
+            if (++iter > 60) taps_flag(status, TAPS_DEV_NONFINITE);
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = m - 1;
+            bool underflow = false;
+            for (; i >= l; --i) {
+              double f = s * e[i], b = c * e[i];
+              r = hypot(f, g);
+              e[i + 1] = r;
+              if (r == 0.0) {
+                d[i + 1] -= p;
+                e[m] = 0.0;
+                underflow = true;
+                break;
+              }
+              s = f / r;
+              c = g / r;
+              g = d[i + 1] - p;
+              r = (d[i] - g) * s + 2.0 * c * b;
+              p = s * r;
+              d[i + 1] = g + p;
+              g = c * r - b;
+              rc[i] = c;
+              rs[i] = s;
+            }
+            stop = underflow ? i + 1 : l;
+            if (!underflow) {
+              d[l] -= p;
+              e[l] = g;
+              e[m] = 0.0;
+            }
+            if (iter > 60) { lo = l; stop = l; }
+          }
+          shi[0] = (m == l || iter > 60) ? 1 : 0;  // l converged
+          shi[1] = lo;                              // first rotation index + 1
+          shi[2] = stop;                            // last rotation index
+        }
+        __syncthreads();
+        const int done = shi[0], lo = shi[1], stop = shi[2];
+        // rows of the basis are independent under column rotations
+        for (int row = tid; row < n; row += nt) {
+          for (int i = lo - 1; i >= stop; --i) {
+            double c = rc[i], s = rs[i];
+            double f = AT(A, row, i + 1);
+            AT(A, row, i + 1) = s * AT(A, row, i) + c * f;
+            AT(A, row, i) = c * AT(A, row, i) - s * f;
+          }
+        }
+        __syncthreads();
+        if (done) break;
+      }
+    }
+  } else {
+    for (long long idx = tid; idx < (long long)n * n; idx += nt) A[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+    for (int i = tid; i < n; i += nt) d[i] = 0.0;
+    __syncthreads();
+  }
+
+  // ---- 6. Phi = L^{-T} Z, column by column
+  for (int c = tid; c < n; c += nt) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = AT(A, i, c);
+      for (int j = i + 1; j <= min(n - 1, i + hb); ++j) s -= AT(B, j, i) * AT(Phi, j, c);
+      double v = s / AT(B, i, i);
+      AT(Phi, i, c) = v;
+      AT(PhiT, c, i) = v;
+    }
+    mu[c] = d[c];
+    if (!isfinite(mu[c])) taps_flag(status, TAPS_DEV_NONFINITE);
+  }
+#undef AT
+}
+
+// ---------------------------------------------------------------------------------
+// Per-solve kernels
+// ---------------------------------------------------------------------------------
+// F[i][m] = sum_r q_r[i] c_r[m]
+__global__ void fd_rhs_kernel(const double* __restrict__ q, const double* __restrict__ c, int Rf, int nf,
+                              int M, double* __restrict__ F) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nf * M) return;
+  int i = idx / M, m = idx % M;
+  double v = 0.0;
+  for (int r = 0; r < Rf; ++r) v += q[(size_t)r * nf + i] * c[(size_t)r * M + m];
+  F[idx] = v;
+}
+
+// Out[i][m] = sum_j Mat[i][j] In[j][m]  (Mat n x n row-major, In/Out n x M row-major)
+__global__ void fd_gemm_kernel(const double* __restrict__ Mat, const double* __restrict__ In, int n, int M,
+                               double* __restrict__ Out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * M) return;
+  int i = idx / M, m = idx % M;
+  const double* row = Mat + (size_t)i * n;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) acc += row[j] * In[(size_t)j * M + m];
+  Out[idx] = acc;
+}
+
+// U_d[j + m nf] = sum_i Phi[j][i] Y[i][m]  (column-major factor output)
+__global__ void fd_back_kernel(const double* __restrict__ Phi, const double* __restrict__ Y, int n, int M,
+                               double* __restrict__ U) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * M) return;
+  int j = idx / M, m = idx % M;
+  const double* row = Phi + (size_t)j * n;
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) acc += row[i] * Y[(size_t)i * M + m];
+  U[(size_t)m * n + j] = acc;
+}
+
+// One CTA per node i: solve (mu_i C_A + C_B) y = g_i by LU with partial pivoting.
+__global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __restrict__ CA,
+                                                             const double* __restrict__ CB,
+                                                             const double* __restrict__ mu,
+                                                             const double* __restrict__ G, int M,
+                                                             double* __restrict__ Y, int* status) {
+  extern __shared__ double T[];   // [M][M+1]: matrix | rhs
+  __shared__ int piv_row;
+  const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int ld = M + 1;
+  const double mi = mu ? mu[i] : 0.0;
+  for (int idx = tid; idx < M * M; idx += nt) {
+    int r = idx / M, c = idx % M;
+    T[r * ld + c] = (CA ? mi * CA[idx] : 0.0) + CB[idx];
+  }
+  for (int r = tid; r < M; r += nt) T[r * ld + M] = G[(size_t)i * M + r];
+  __syncthreads();
+  for (int p = 0; p < M; ++p) {
+    if (tid < 32) {   // argmax |T[r][p]|, r >= p (ties to the smaller r)
+      double best = -1.0;
+      int br = p;
+      for (int r = p + tid; r < M; r += 32) {
+        double a = fabs(T[r * ld + p]);
+        if (a > best) { best = a; br = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+      }
+      if (tid == 0) {
+        piv_row = br;
+        if (!(best > 0.0) || !isfinite(best)) taps_flag(status, TAPS_DEV_SINGULAR);
+      }
+    }
+    __syncthreads();
+    int pr = piv_row;
+    if (pr != p)
+      for (int c = tid; c <= M; c += nt) {
+        double t = T[p * ld + c];
+        T[p * ld + c] = T[pr * ld + c];
+        T[pr * ld + c] = t;
+      }
+    __syncthreads();
+    double pv = T[p * ld + p];
+    double inv = (pv != 0.0 && isfinite(pv)) ? 1.0 / pv : 0.0;
+    int w = M - p - 1;
+    for (int idx = tid; idx < w * (w + 1); idx += nt) {
+      int r = p + 1 + idx / (w + 1), c = p + 1 + idx % (w + 1);
+      T[r * ld + c] -= T[r * ld + p] * inv * T[p * ld + c];
+    }
+    __syncthreads();
+  }
+  // back substitution (one warp)
+  if (tid < 32) {
+    for (int r = M - 1; r >= 0; --r) {
+      double s = 0.0;
+      for (int c = r + 1 + tid; c < M; c += 32) s += T[r * ld + c] * T[c * ld + M];
+      s = warp_sum(s);
+      if (tid == 0) {
+        double pv = T[r * ld + r];
+        T[r * ld + M] = (pv != 0.0) ? (T[r * ld + M] - s) / pv : 0.0;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < M; r += nt) Y[(size_t)i * M + r] = T[r * ld + M];
+}
+
+// ---------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------
+static bool op_symmetric(int op) { return op != TAPS_OP_G; }
+static bool op_mass_like(int op) { return op == TAPS_OP_M || op == TAPS_OP_W; }
+
+// Slot choice of dim d: returns 1 with (slotA, slotB) (slotA = -1 when the dim has a
+// single operator) if the dim's distinct operators form a symmetric pencil with a
+// mass-like (positive definite) partner.
+int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB) {
+  int n = P->tt.nops[d];
+  if (n < 1 || n > 2) return 0;
+  for (int s = 0; s < n; ++s)
+    if (!op_symmetric(P->ops[d][s])) return 0;
+  if (n == 1) {
+    *slotA = -1;
+    *slotB = 0;
+    return 1;
+  }
+  int b = op_mass_like(P->ops[d][0]) ? 0 : (op_mass_like(P->ops[d][1]) ? 1 : -1);
+  if (b < 0) return 0;
+  *slotB = b;
+  *slotA = 1 - b;
+  return 1;
+}
+
+static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, FdEntry** out) {
+  for (int k = 0; k < dm->nfd; ++k)
+    if (dm->fd[k].opA == opA && dm->fd[k].opB == opB) {
+      *out = &dm->fd[k];
+      return dm->fd[k].status;
+    }
+  if (dm->nfd >= 4) return TAPS_ERR_INVALID_ARG;
+  FdEntry& E = dm->fd[dm->nfd];
+  memset(&E, 0, sizeof(E));
+  E.opA = opA;
+  E.opB = opB;
+  int n = dm->nf;
+  size_t nn = (size_t)n * n;
+  cudaStream_t s = P->stream;
+  double *A = nullptr, *B = nullptr, *V = nullptr, *tmp = nullptr, *bt = nullptr, *dd = nullptr, *ee = nullptr;
+  int st = TAPS_OK;
+  do {
+    if ((st = taps_alloc((void**)&E.Phi, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&E.PhiT, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&E.mu, sizeof(double) * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&A, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&B, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&V, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&tmp, sizeof(double) * 2 * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&bt, sizeof(double) * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&dd, sizeof(double) * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&ee, sizeof(double) * n)) != TAPS_OK) break;
+    const size_t bsz = (size_t)n * dm->nb;
+    const double* bandA = opA >= 0 ? dm->d_band + (size_t)opA * bsz : nullptr;
+    const double* bandB = dm->d_band + (size_t)opB * bsz;
+    fd_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(bandA, bandB, n, dm->hb, A, B);
+    if (cudaMemsetAsync(V, 0, sizeof(double) * nn, s) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+    size_t smem = sizeof(double) * 2 * (size_t)n;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute((const void*)fd_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int tk = prof_begin(P, TAPS_PROF_OTHER);
+    fd_setup_kernel<<<1, FD_THREADS, smem, s>>>(A, B, V, tmp, bt, dd, ee, n, dm->hb, opA >= 0 ? 1 : 0, E.Phi,
+                                                E.PhiT, E.mu, P->d_status);
+    prof_end(P, TAPS_PROF_OTHER, tk, 6.0 * (double)nn * n, 8.0 * 4.0 * nn);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+      taps_note_cuda_error(ce, "fd_setup_kernel", __FILE__, __LINE__);
+      st = TAPS_ERR_CUDA;
+      break;
+    }
+    st = taps_check_status(P->d_status, s);
+  } while (0);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(V);
+  cudaFree(tmp);
+  cudaFree(bt);
+  cudaFree(dd);
+  cudaFree(ee);
+  E.status = st;
+  dm->nfd++;
+  *out = &E;
+  return st;
+}
+
+// Reduced solve of dim d by fast diagonalisation, coefficients in P->d_C / P->d_c.
+int taps_fd_solve(taps_problem* P, taps_factors* U, int d) {
+  int slotA, slotB;
+  if (!taps_fd_eligible(P, d, &slotA, &slotB)) return TAPS_ERR_INVALID_ARG;
+  taps_dim* dm = P->dims[d];
+  FdEntry* E = nullptr;
+  int opA = slotA >= 0 ? P->ops[d][slotA] : -1;
+  TAPS_TRY(fd_prepare(P, d, dm, opA, P->ops[d][slotB], &E));
+  const int n = dm->nf, M = U->M;
+  const size_t MM = (size_t)M * M;
+  cudaStream_t s = P->stream;
+  const int nM = n * M;
+  double* F = P->d_F;
+  double* G = P->d_Y;
+  double* Y = P->d_Y + (size_t)n * M;
+  int tk = prof_begin(P, TAPS_PROF_FASTDIAG);
+  fd_rhs_kernel<<<(nM + 255) / 256, 256, 0, s>>>(P->d_q[d], P->d_c, P->Rf, n, M, F);
+  fd_gemm_kernel<<<(nM + 127) / 128, 128, 0, s>>>(E->PhiT, F, n, M, G);
+  const double* CA = slotA >= 0 ? P->d_C + (size_t)slotA * MM : nullptr;
+  const double* CB = P->d_C + (size_t)slotB * MM;
+  fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr,
+                                                                             G, M, Y, P->d_status);
+  fd_back_kernel<<<(nM + 127) / 128, 128, 0, s>>>(E->Phi, Y, n, M, U->d_U[d]);
+  P->prof->launches[TAPS_PROF_FASTDIAG] += 3;
+  prof_end(P, TAPS_PROF_FASTDIAG, tk,
+           2.0 * P->Rf * nM + 4.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),
+           8.0 * (2.0 * (double)n * n + 4.0 * nM + (double)P->Rf * n + 2.0 * MM));
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+void taps_fd_release(taps_dim* dm) {
+  for (int k = 0; k < dm->nfd; ++k) {
+    cudaFree(dm->fd[k].Phi);
+    cudaFree(dm->fd[k].PhiT);
+    cudaFree(dm->fd[k].mu);
+  }
+  dm->nfd = 0;
+}

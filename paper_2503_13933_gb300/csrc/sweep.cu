@@ -503,7 +503,6 @@ static int coefficients(taps_problem* P, int d, int M) {
 
 int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
                     double* change_out) {
-  (void)solver;
   int M = U->M;
   if (M < 1) return TAPS_ERR_INVALID_ARG;
   TAPS_TRY(taps_ws_ensure(P, M));
@@ -513,7 +512,11 @@ int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver,
     TAPS_TRY(coefficients(P, d, M));
     TAPS_CUDA(cudaMemcpyAsync(P->d_Uold, U->d_U[d], sizeof(double) * dm->nf * M,
                               cudaMemcpyDeviceToDevice, s));
-    TAPS_TRY(reduced_solve_block_lu(P, U, d));
+    int sa, sb;
+    if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb))
+      TAPS_TRY(taps_fd_solve(P, U, d));
+    else
+      TAPS_TRY(reduced_solve_block_lu(P, U, d));
     int norm_d = (normalize && d < P->D - 1) ? 1 : 0;
     int tk = prof_begin(P, TAPS_PROF_NORMALIZE);
     normalize_change_kernel<<<M, 256, 0, s>>>(U->d_U[d], P->d_Uold, dm->nf, M, norm_d,

@@ -36,6 +36,16 @@ int taps_alloc(void** p, size_t bytes);
 #define TAPS_DEV_TIMEOUT 3
 int taps_status_from_device(int dev);
 
+// Fast-diagonalisation data of one operator pencil (A, B) of a dimension:
+// Phi^T B Phi = I, Phi^T A Phi = diag(mu) over the free nodes (A absent: opA = -1).
+struct FdEntry {
+  int opA, opB;
+  int status;
+  double* Phi;   // [nf][nf] row-major
+  double* PhiT;  // [nf][nf] row-major (transpose)
+  double* mu;    // [nf]
+};
+
 // ---------------------------------------------------------------------------------
 // Assembled dimension: C-HiDeNN tables and banded 1D matrices on the device.
 // ---------------------------------------------------------------------------------
@@ -61,6 +71,8 @@ struct taps_dim {
   double* d_band_full;  // [TAPS_NUM_OPS][n][nb]
   double* d_band;       // [TAPS_NUM_OPS][nf][nb] restricted to the free nodes
   int* d_status;
+  FdEntry fd[4];        // cached pencil decompositions
+  int nfd;
 };
 
 // Term table passed by value to the kernels that combine dimensions.
@@ -234,3 +246,6 @@ int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver,
                     double* change_out);
 int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
 int taps_check_status(int* d_status, cudaStream_t s);
+int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB);
+int taps_fd_solve(taps_problem* P, taps_factors* U, int d);
+void taps_fd_release(taps_dim* dm);

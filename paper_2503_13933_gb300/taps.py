@@ -27,7 +27,7 @@ SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4}
 FP64, FP32 = 0, 1
 RES_ALS, RES_FULL = 0, 1
 INIT_GIVEN, INIT_RANDOM, INIT_ZERO = 0, 1, 2
-SOLVER_BLOCK_LU = 0
+SOLVER_BLOCK_LU, SOLVER_FASTDIAG = 0, 1
 
 
 class DimDesc(ctypes.Structure):
@@ -108,7 +108,7 @@ SIGNATURES = {
 }
 
 PROF_CLASSES = ["gram", "coeff", "block_assemble", "block_lu", "backsub", "normalize",
-                "residual", "eval", "other"]
+                "residual", "eval", "other", "fastdiag"]
 
 _LIB = None
 
@@ -239,6 +239,7 @@ class Problem:
         return Factors(self, M_cap)
 
     def sweep(self, U, n=1, precision=FP64, normalize=True, solver=SOLVER_BLOCK_LU):
+        """Run n sweeps (Algorithm 1 inner loop)."""
         o = SweepOpts(precision=precision, solver=solver, normalize=int(normalize))
         rep = SweepReport()
         check(lib().taps_sweep(self.handle, U.handle, n, ctypes.byref(o), ctypes.byref(rep)),
@@ -252,10 +253,10 @@ class Problem:
 
     def solve(self, U, M0=1, M_max=8, als_tol=1e-10, res_tol=1e-6, res_kind=RES_ALS,
               max_sweeps=200, precision=FP64, polish_sweeps=20, init=INIT_ZERO, seed=0,
-              history_cap=4096, raise_not_converged=False):
+              history_cap=4096, raise_not_converged=False, solver=SOLVER_BLOCK_LU):
         o = SolveOpts(M0=M0, M_max=M_max, als_tol=als_tol, res_tol=res_tol, res_kind=res_kind,
                       max_sweeps=max_sweeps, precision=precision, polish_sweeps=polish_sweeps,
-                      solver=SOLVER_BLOCK_LU, init=init, seed=seed, history_cap=history_cap)
+                      solver=solver, init=init, seed=seed, history_cap=history_cap)
         hM = (ctypes.c_int * max(history_cap, 1))()
         hc = (ctypes.c_double * max(history_cap, 1))()
         hr = (ctypes.c_double * max(history_cap, 1))()

