@@ -150,6 +150,9 @@ typedef struct {
   int init;            /* TAPS_INIT_* for the columns added by the schedule */
   unsigned seed;       /* seed of TAPS_INIT_RANDOM */
   int history_cap;     /* capacity of the report's history arrays (0: none) */
+  int graphs;          /* 1: replay each sweep + residual as a captured CUDA graph
+                          (captured on first use per factors / M / precision / solver;
+                          falls back to direct launches if capture is unavailable) */
 } taps_solve_opts;
 
 typedef struct {

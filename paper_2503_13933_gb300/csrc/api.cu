@@ -20,7 +20,8 @@ int prof_begin(taps_problem* P, int cls) {
   ProfState* S = P->prof;
   if (!S) return -1;
   S->launches[cls] += 1;
-  if (!S->events) return -1;
+  if (!S->events && !S->capturing) return -1;
+  if (S->capturing && (S->npool < 2 || S->npending >= 512)) return -1;  // no allocation / sync while capturing
   if (S->npending >= 512) {
     cudaStreamSynchronize(P->stream);
     prof_drain(P);
@@ -35,7 +36,9 @@ int prof_begin(taps_problem* P, int cls) {
   pp.cls = cls;
   pp.b = S->pool[--S->npool];
   pp.a = S->pool[--S->npool];
-  cudaEventRecord(pp.a, P->stream);
+  // inside a capture the record must become an event-record node of the graph
+  if (S->capturing) cudaEventRecordWithFlags(pp.a, P->stream, cudaEventRecordExternal);
+  else cudaEventRecord(pp.a, P->stream);
   return S->npending++;
 }
 
@@ -44,7 +47,10 @@ void prof_end(taps_problem* P, int cls, int token, double flops, double bytes) {
   if (!S) return;
   S->flops[cls] += flops;
   S->bytes[cls] += bytes;
-  if (token >= 0) cudaEventRecord(S->pending[token].b, P->stream);
+  if (token >= 0) {
+    if (S->capturing) cudaEventRecordWithFlags(S->pending[token].b, P->stream, cudaEventRecordExternal);
+    else cudaEventRecord(S->pending[token].b, P->stream);
+  }
 }
 
 // Read back the elapsed times of all pending launches (the stream has been
@@ -66,6 +72,130 @@ void prof_drain(taps_problem* P) {
     }
   }
   S->npending = 0;
+}
+
+// ---------------------------------------------------------------------------------
+// Sweep graphs: one sweep plus one residual evaluation, captured once per
+// (factors, M, precision, solver, residual kind, workspace) and replayed.
+// ---------------------------------------------------------------------------------
+struct SweepGraph {
+  const taps_factors* U;
+  int M, precision, solver, res_kind, ws_M;
+  bool failed;
+  cudaGraph_t g;
+  cudaGraphExec_t exec;
+  long long dl[TAPS_PROF_NUM];   // per-replay profiling increments
+  double dfl[TAPS_PROF_NUM], dby[TAPS_PROF_NUM];
+  int nrec;
+  ProfPending recs[512];         // events recorded by the graph's own event nodes
+};
+
+static void graph_destroy(taps_problem* P) {
+  SweepGraph* G = (SweepGraph*)P->graph;
+  if (!G) return;
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->g) cudaGraphDestroy(G->g);
+  for (int i = 0; i < G->nrec; ++i) {
+    cudaEventDestroy(G->recs[i].a);
+    cudaEventDestroy(G->recs[i].b);
+  }
+  delete G;
+  P->graph = nullptr;
+}
+
+static int graph_build(taps_problem* P, taps_factors* U, int prec, int solver, int res_kind) {
+  graph_destroy(P);
+  SweepGraph* G = new SweepGraph();
+  memset((void*)G, 0, sizeof(SweepGraph));
+  G->U = U;
+  G->M = U->M;
+  G->precision = prec;
+  G->solver = solver;
+  G->res_kind = res_kind;
+  G->ws_M = P->ws_M;
+  P->graph = G;
+  ProfState* S = P->prof;
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  prof_drain(P);
+  long long l0[TAPS_PROF_NUM];
+  double f0[TAPS_PROF_NUM], b0[TAPS_PROF_NUM];
+  for (int c = 0; c < TAPS_PROF_NUM; ++c) { l0[c] = S->launches[c]; f0[c] = S->flops[c]; b0[c] = S->bytes[c]; }
+  while (S->npool < 512) {   // events for the graph's event nodes, created before capture
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) break;
+    S->pool[S->npool++] = ev;
+  }
+  cudaStream_t saved = P->stream;
+  P->stream = P->cap_stream;
+  int st = TAPS_OK;
+  S->capturing = true;
+  if (cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    st = TAPS_ERR_CUDA;
+  } else {
+    st = taps_sweep_enqueue(P, U, prec, solver, 1);
+    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
+    if (ce != cudaSuccess || g == nullptr) st = (st == TAPS_OK) ? TAPS_ERR_CUDA : st;
+    G->g = g;
+  }
+  P->stream = saved;
+  S->capturing = false;
+  cudaGetLastError();
+  for (int c = 0; c < TAPS_PROF_NUM; ++c) {
+    G->dl[c] = S->launches[c] - l0[c];
+    G->dfl[c] = S->flops[c] - f0[c];
+    G->dby[c] = S->bytes[c] - b0[c];
+    S->launches[c] = l0[c];
+    S->flops[c] = f0[c];
+    S->bytes[c] = b0[c];
+  }
+  for (int i = 0; i < S->npending; ++i) G->recs[G->nrec++] = S->pending[i];
+  S->npending = 0;
+  if (st == TAPS_OK && cudaGraphInstantiate(&G->exec, G->g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    st = TAPS_ERR_CUDA;
+  }
+  if (st != TAPS_OK) G->failed = true;
+  return st;
+}
+
+// One sweep + residual through the cached graph (built on first use).  Returns
+// TAPS_ERR_CUDA with *fallback = 1 if capture is unavailable (caller runs eagerly).
+static int graph_sweep(taps_problem* P, taps_factors* U, int prec, int solver, int res_kind,
+                       double* change, double* rho, int* fallback) {
+  *fallback = 0;
+  SweepGraph* G = (SweepGraph*)P->graph;
+  bool match = G && G->U == U && G->M == U->M && G->precision == prec && G->solver == solver &&
+               G->res_kind == res_kind && G->ws_M == P->ws_M;
+  if (match && G->failed) {
+    *fallback = 1;
+    return TAPS_ERR_CUDA;
+  }
+  if (!match) {
+    TAPS_TRY(taps_fd_prepare_all(P, solver));
+    if (graph_build(P, U, prec, solver, res_kind) != TAPS_OK) {
+      *fallback = 1;
+      return TAPS_ERR_CUDA;
+    }
+    G = (SweepGraph*)P->graph;
+  }
+  TAPS_CUDA(cudaGraphLaunch(G->exec, P->stream));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  ProfState* S = P->prof;
+  for (int c = 0; c < TAPS_PROF_NUM; ++c) {
+    S->launches[c] += G->dl[c];
+    S->flops[c] += G->dfl[c];
+    S->bytes[c] += G->dby[c];
+  }
+  if (S->events)
+    for (int i = 0; i < G->nrec; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, G->recs[i].a, G->recs[i].b) == cudaSuccess) S->ms[G->recs[i].cls] += ms;
+    }
+  cudaGetLastError();
+  TAPS_TRY(taps_sweep_finish(P, U, change));
+  return taps_residual_finish(P, U, res_kind, rho);
 }
 
 extern "C" int taps_profile_reset(taps_problem* P, int enable_events) {
@@ -118,6 +248,9 @@ static void free_ws(taps_problem* P) {
   cudaFree(P->d_scal);
   cudaFree(P->d_bigG);
   if (P->h_scal) cudaFreeHost(P->h_scal);
+  if (P->h_part) cudaFreeHost(P->h_part);
+  P->h_part = nullptr;
+  graph_destroy(P);
   P->d_C = P->d_c = P->d_F = P->d_blocks = P->d_lu = P->d_Y = P->d_Uold = nullptr;
   P->d_partial = P->d_scal = P->d_bigG = P->h_scal = nullptr;
   P->ws_M = 0;
@@ -134,6 +267,8 @@ extern "C" void taps_problem_destroy(taps_problem* P) {
   cudaFree(P->d_status);
   cudaFree(P->d_bar);
   cudaFree(P->d_evalbuf);
+  if (P->h_status) cudaFreeHost(P->h_status);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->prof) {
     for (int i = 0; i < P->prof->npending; ++i) {
       cudaEventDestroy(P->prof->pending[i].a);
@@ -158,7 +293,7 @@ int taps_ws_ensure(taps_problem* P, int M) {
     TAPS_TRY(taps_alloc((void**)&P->d_gram[d], sizeof(double) * nops * M * M));
     TAPS_TRY(taps_alloc((void**)&P->d_h[d], sizeof(double) * P->Rf * M));
     TAPS_TRY(taps_alloc((void**)&P->d_Usnap[d], sizeof(double) * dm->nf * M));
-    size_t gp = (size_t)((dm->nf + 15) / 16) * (nops * M * M + P->Rf * M);
+    size_t gp = (size_t)((dm->nf + 7) / 8) * (nops * M * M + P->Rf * M);
     part = std::max(part, gp);
     size_t NC = (size_t)nops * M + P->Rf;
     bigG += NC * NC;
@@ -180,6 +315,7 @@ int taps_ws_ensure(taps_problem* P, int M) {
   TAPS_TRY(taps_alloc((void**)&P->d_scal, sizeof(double) * 2 * M * D + 64));
   TAPS_TRY(taps_alloc((void**)&P->d_bigG, sizeof(double) * bigG));
   TAPS_CUDA(cudaMallocHost((void**)&P->h_scal, sizeof(double) * (2 * M * D + 64)));
+  TAPS_CUDA(cudaMallocHost((void**)&P->h_part, sizeof(double) * part));
   P->partial_len = part;
   P->bigG_len = bigG;
   P->ws_M = M;
@@ -242,6 +378,9 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   do {
     if ((st = taps_alloc((void**)&P->d_status, sizeof(int))) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&P->d_bar, 2 * sizeof(unsigned))) != TAPS_OK) break;
+    if (cudaMallocHost((void**)&P->h_status, sizeof(int)) != cudaSuccess) { st = TAPS_ERR_OOM; break; }
+    *P->h_status = 0;
+    if (cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
     if (cudaMemsetAsync(P->d_status, 0, sizeof(int), P->stream) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
     for (int d = 0; d < D && st == TAPS_OK; ++d) {
       const taps_dim* dm = dims[d];
@@ -433,7 +572,13 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
           TAPS_CUDA(cudaMemcpyAsync(P->d_Usnap[d], U->d_U[d], sizeof(double) * P->dims[d]->nf * M,
                                     cudaMemcpyDeviceToDevice, P->stream));
       }
-      int sst = taps_sweep_impl(P, U, prec, o->solver, 1, &change);
+      int sst = TAPS_ERR_CUDA, fallback = 1;
+      bool rho_done = false;
+      if (o->graphs) {
+        sst = graph_sweep(P, U, prec, o->solver, o->res_kind, &change, &rho, &fallback);
+        rho_done = (sst == TAPS_OK);
+      }
+      if (fallback) sst = taps_sweep_impl(P, U, prec, o->solver, 1, &change);
       if (prec == TAPS_FP32 && (sst == TAPS_ERR_SINGULAR || sst == TAPS_ERR_NONFINITE)) {
         // FP32 Grams cannot separate modes that agree to ~1e-8 (a Gram entry rounds to
         // an exact duplicate): restore the factors and redo the sweep in FP64.
@@ -443,11 +588,12 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
         prec = TAPS_FP64;
         TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
         sst = taps_sweep_impl(P, U, prec, o->solver, 1, &change);
+        rho_done = false;
       }
       TAPS_TRY(sst);
       ++sweeps;
       if (prec == TAPS_FP64) ++fp64_sweeps;
-      TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho));
+      if (!rho_done) TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho));
       if (o->history_cap > 0 && rep && hist < o->history_cap) {
         if (rep->hist_M) rep->hist_M[hist] = M;
         if (rep->hist_change) rep->hist_change[hist] = change;

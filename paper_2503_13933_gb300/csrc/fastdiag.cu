@@ -274,28 +274,95 @@ __global__ void fd_rhs_kernel(const double* __restrict__ q, const double* __rest
   F[idx] = v;
 }
 
-// Out[i][m] = sum_j Mat[i][j] In[j][m]  (Mat n x n row-major, In/Out n x M row-major)
-__global__ void fd_gemm_kernel(const double* __restrict__ Mat, const double* __restrict__ In, int n, int M,
-                               double* __restrict__ Out) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * M) return;
-  int i = idx / M, m = idx % M;
+// Out[i][m] = sum_j Mat[i][j] In[j][m] (Mat n x n row-major, In n x M row-major).
+// One warp per output row i: lanes split the sum over j, each lane keeps 32 mode
+// accumulators, and the per-lane partials are combined through shared memory.
+// Out is n x M row-major, or (colmajor) the factor layout Out[m * n + i].
+#define RG_WARPS 4
+__global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double* __restrict__ Mat,
+                                                                   const double* __restrict__ In, int n,
+                                                                   int M, double* __restrict__ Out,
+                                                                   int colmajor) {
+  __shared__ double part[RG_WARPS][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * RG_WARPS + warp;
+  if (i >= n) return;   // whole warps only: no block-wide barrier below
   const double* row = Mat + (size_t)i * n;
-  double acc = 0.0;
-  for (int j = 0; j < n; ++j) acc += row[j] * In[(size_t)j * M + m];
-  Out[idx] = acc;
+  for (int m0 = 0; m0 < M; m0 += 32) {
+    const int mc = min(32, M - m0);
+    double acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double a = row[j];
+      const double* in = In + (size_t)j * M + m0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < mc) acc[c] += a * in[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) part[warp][lane][c] = acc[c];
+    __syncwarp();
+    if (lane < mc) {
+      double sum = 0.0;
+      for (int l = 0; l < 32; ++l) sum += part[warp][l][lane];
+      if (colmajor) Out[(size_t)(m0 + lane) * n + i] = sum;
+      else Out[(size_t)i * M + m0 + lane] = sum;
+    }
+    __syncwarp();
+  }
 }
 
-// U_d[j + m nf] = sum_i Phi[j][i] Y[i][m]  (column-major factor output)
-__global__ void fd_back_kernel(const double* __restrict__ Phi, const double* __restrict__ Y, int n, int M,
-                               double* __restrict__ U) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * M) return;
-  int j = idx / M, m = idx % M;
-  const double* row = Phi + (size_t)j * n;
-  double acc = 0.0;
-  for (int i = 0; i < n; ++i) acc += row[i] * Y[(size_t)i * M + m];
-  U[(size_t)m * n + j] = acc;
+// One warp per node i, M <= 32: lane r holds row r of (mu_i C_A + C_B | g_i) in
+// registers; LU without pivoting (the systems are mu_i C_A + C_B with positive
+// definite symmetric part) and back substitution by shuffles.  A zero or
+// non-finite pivot is reported as TAPS_DEV_SINGULAR.
+__global__ void __launch_bounds__(128) fd_small_solve_warp_kernel(const double* __restrict__ CA,
+                                                                  const double* __restrict__ CB,
+                                                                  const double* __restrict__ mu,
+                                                                  const double* __restrict__ G, int n,
+                                                                  int M, double* __restrict__ Y,
+                                                                  int* status) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const double mi = (CA && mu) ? mu[i] : 0.0;
+  double row[33];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    double v = 0.0;
+    if (lane < M && c < M) v = (CA ? mi * CA[lane * M + c] : 0.0) + CB[lane * M + c];
+    row[c] = v;
+  }
+  row[32] = (lane < M) ? G[(size_t)i * M + lane] : 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < 32; ++p) {
+    if (p < M) {
+      double piv = __shfl_sync(0xffffffffu, row[p], p);
+      bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
+      double l = (lane > p && lane < M && piv != 0.0) ? row[p] / piv : 0.0;
+#pragma unroll
+      for (int c = 0; c < 33; ++c) {
+        if (c > p && (c < M || c == 32)) {
+          double pc = __shfl_sync(0xffffffffu, row[c], p);
+          row[c] -= l * pc;
+        }
+      }
+    }
+  }
+  if (bad && lane == 0) taps_flag(status, TAPS_DEV_SINGULAR);
+  double x = 0.0;
+#pragma unroll
+  for (int c = 31; c >= 0; --c) {
+    if (c < M) {
+      double xc = (lane == c && row[c] != 0.0) ? row[32] / row[c] : 0.0;
+      xc = __shfl_sync(0xffffffffu, xc, c);
+      if (lane == c) x = xc;
+      if (lane < c) row[32] -= row[c] * xc;
+    }
+  }
+  if (lane < M) Y[(size_t)i * M + lane] = x;
 }
 
 // One CTA per node i: solve (mu_i C_A + C_B) y = g_i by LU with partial pivoting.
@@ -471,17 +538,35 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d) {
   double* Y = P->d_Y + (size_t)n * M;
   int tk = prof_begin(P, TAPS_PROF_FASTDIAG);
   fd_rhs_kernel<<<(nM + 255) / 256, 256, 0, s>>>(P->d_q[d], P->d_c, P->Rf, n, M, F);
-  fd_gemm_kernel<<<(nM + 127) / 128, 128, 0, s>>>(E->PhiT, F, n, M, G);
+  const unsigned rg = (unsigned)((n + RG_WARPS - 1) / RG_WARPS);
+  fd_rowgemm_kernel<<<rg, RG_WARPS * 32, 0, s>>>(E->PhiT, F, n, M, G, 0);
   const double* CA = slotA >= 0 ? P->d_C + (size_t)slotA * MM : nullptr;
   const double* CB = P->d_C + (size_t)slotB * MM;
-  fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr,
-                                                                             G, M, Y, P->d_status);
-  fd_back_kernel<<<(nM + 127) / 128, 128, 0, s>>>(E->Phi, Y, n, M, U->d_U[d]);
+  if (M <= 32)
+    fd_small_solve_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
+                                                           P->d_status);
+  else
+    fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
+        CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
+  fd_rowgemm_kernel<<<rg, RG_WARPS * 32, 0, s>>>(E->Phi, Y, n, M, U->d_U[d], 1);
   P->prof->launches[TAPS_PROF_FASTDIAG] += 3;
   prof_end(P, TAPS_PROF_FASTDIAG, tk,
            2.0 * P->Rf * nM + 4.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),
            8.0 * (2.0 * (double)n * n + 4.0 * nM + (double)P->Rf * n + 2.0 * MM));
   TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+// Pencil decompositions of every eligible dim, done before any capture (they
+// allocate and synchronise).
+int taps_fd_prepare_all(taps_problem* P, int solver) {
+  if (solver != TAPS_SOLVER_FASTDIAG) return TAPS_OK;
+  for (int d = 0; d < P->D; ++d) {
+    int sa, sb;
+    if (!taps_fd_eligible(P, d, &sa, &sb)) continue;
+    FdEntry* E = nullptr;
+    TAPS_TRY(fd_prepare(P, d, P->dims[d], sa >= 0 ? P->ops[d][sa] : -1, P->ops[d][sb], &E));
+  }
   return TAPS_OK;
 }
 

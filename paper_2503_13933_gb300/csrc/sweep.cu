@@ -14,7 +14,7 @@
 // h_r = U^T q_r.  CTA (chunk, mtile) handles GR rows and MT rows of Gamma; partial
 // sums are reduced in a fixed order by gram_reduce_kernel.
 // ---------------------------------------------------------------------------------
-#define GR 16
+#define GR 8
 #define GMT 8
 
 template <typename T>
@@ -501,11 +501,12 @@ static int coefficients(taps_problem* P, int d, int M) {
   return TAPS_OK;
 }
 
-int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
-                    double* change_out) {
+// Kernels of one sweep (no host synchronisation: capturable in a CUDA graph).  The
+// per-column change / norm partials and the status word are copied to pinned host
+// memory at the end; taps_sweep_finish reads them after the stream has drained.
+int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize) {
   int M = U->M;
-  if (M < 1) return TAPS_ERR_INVALID_ARG;
-  TAPS_TRY(taps_ws_ensure(P, M));
+  if (M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
   for (int d = 0; d < P->D; ++d) {
     const taps_dim* dm = P->dims[d];
@@ -527,7 +528,21 @@ int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver,
   }
   TAPS_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, sizeof(double) * 2 * M * P->D,
                             cudaMemcpyDeviceToHost, s));
-  TAPS_TRY(taps_check_status(P->d_status, s));
+  TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return TAPS_OK;
+}
+
+// Reads the device status and the change partials copied by taps_sweep_enqueue (the
+// caller has synchronised the stream).
+int taps_sweep_finish(taps_problem* P, taps_factors* U, double* change_out) {
+  int M = U->M;
+  if (*P->h_status != TAPS_DEV_OK) {
+    int dev = *P->h_status;
+    *P->h_status = TAPS_DEV_OK;
+    TAPS_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), P->stream));
+    TAPS_CUDA(cudaStreamSynchronize(P->stream));
+    return taps_status_from_device(dev);
+  }
   prof_drain(P);
   double change = 0.0;
   for (int d = 0; d < P->D; ++d) {
@@ -542,6 +557,17 @@ int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver,
   if (!std::isfinite(change)) return TAPS_ERR_NONFINITE;
   if (change_out) *change_out = change;
   return TAPS_OK;
+}
+
+int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
+                    double* change_out) {
+  int M = U->M;
+  if (M < 1) return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_ws_ensure(P, M));
+  TAPS_TRY(taps_fd_prepare_all(P, solver));
+  TAPS_TRY(taps_sweep_enqueue(P, U, precision, solver, normalize));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  return taps_sweep_finish(P, U, change_out);
 }
 
 // ---------------------------------------------------------------------------------
@@ -665,15 +691,15 @@ __global__ void full_residual_combine_kernel(TermTable tt, BigGramPtrs bg, int M
   }
 }
 
-int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
+// Residual kernels (no host synchronisation); the partial sums land in pinned host
+// memory (P->h_part) for taps_residual_finish.  Returns the number of partials.
+int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind) {
   int M = U->M;
-  if (M < 1) return TAPS_ERR_INVALID_ARG;
-  TAPS_TRY(taps_ws_ensure(P, M));
+  if (M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
   if (kind == TAPS_RES_ALS) {
     // FP64 Grams of every dim at the current factors, then each dim's residual.
     TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
-    std::vector<int> nblocks(P->D);
     size_t off = 0;
     for (int d = 0; d < P->D; ++d) {
       const taps_dim* dm = P->dims[d];
@@ -685,34 +711,18 @@ int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double*
                                                                P->d_opband[d], nops, P->d_Y);
       TAPS_CUDA(cudaGetLastError());
       long long nr = (long long)dm->nf * M;
-      nblocks[d] = (int)((nr + 255) / 256);
-      als_residual_kernel<<<nblocks[d], 256, 0, s>>>(P->d_Y, nops, dm->nf, M, P->d_C, P->d_q[d],
-                                                     P->d_c, P->Rf, P->d_partial + off);
+      int nblocks = (int)((nr + 255) / 256);
+      als_residual_kernel<<<nblocks, 256, 0, s>>>(P->d_Y, nops, dm->nf, M, P->d_C, P->d_q[d],
+                                                  P->d_c, P->Rf, P->d_partial + off);
       prof_end(P, TAPS_PROF_RESIDUAL, tk, 2.0 * ny * dm->nb + 2.0 * nops * (double)nr * M + 2.0 * P->Rf * nr,
                8.0 * (2.0 * ny + (double)nr * (nops + 1)));
       P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
       TAPS_CUDA(cudaGetLastError());
-      off += 2 * (size_t)nblocks[d];
+      off += 2 * (size_t)nblocks;
     }
-    std::vector<double> h(off);
-    TAPS_CUDA(cudaMemcpyAsync(h.data(), P->d_partial, off * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TAPS_CUDA(cudaStreamSynchronize(s));
-    double worst = 0.0;
-    off = 0;
-    for (int d = 0; d < P->D; ++d) {
-      double r2 = 0.0, f2 = 0.0;
-      for (int b = 0; b < nblocks[d]; ++b) {
-        r2 += h[off + 2 * b];
-        f2 += h[off + 2 * b + 1];
-      }
-      off += 2 * (size_t)nblocks[d];
-      double v = f2 > 0.0 ? sqrt(r2 / f2) : INFINITY;
-      worst = std::max(worst, v);
-    }
-    if (!std::isfinite(worst)) return TAPS_ERR_NONFINITE;
-    *rho_out = worst;
-    prof_drain(P);
-    return taps_check_status(P->d_status, s);
+    TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, off * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return TAPS_OK;
   }
   if (kind != TAPS_RES_FULL) return TAPS_ERR_INVALID_ARG;
   BigGramPtrs bg;
@@ -741,19 +751,58 @@ int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double*
   full_residual_combine_kernel<<<nblk, 256, 0, s>>>(P->tt, bg, M, P->d_partial);
   prof_end(P, TAPS_PROF_RESIDUAL, tk, (double)P->R * M * P->R * M * (P->D + 1), 8.0 * (double)goff);
   TAPS_CUDA(cudaGetLastError());
-  double h[3 * nblk];
-  TAPS_CUDA(cudaMemcpyAsync(h, P->d_partial, sizeof(h), cudaMemcpyDeviceToHost, s));
-  TAPS_CUDA(cudaStreamSynchronize(s));
+  TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, 3 * nblk * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return TAPS_OK;
+}
+
+int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
+  int M = U->M;
+  if (*P->h_status != TAPS_DEV_OK) {
+    int dev = *P->h_status;
+    *P->h_status = TAPS_DEV_OK;
+    TAPS_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), P->stream));
+    TAPS_CUDA(cudaStreamSynchronize(P->stream));
+    return taps_status_from_device(dev);
+  }
+  prof_drain(P);
+  if (kind == TAPS_RES_ALS) {
+    double worst = 0.0;
+    size_t off = 0;
+    for (int d = 0; d < P->D; ++d) {
+      long long nr = (long long)P->dims[d]->nf * M;
+      int nblocks = (int)((nr + 255) / 256);
+      double r2 = 0.0, f2 = 0.0;
+      for (int b = 0; b < nblocks; ++b) {
+        r2 += P->h_part[off + 2 * b];
+        f2 += P->h_part[off + 2 * b + 1];
+      }
+      off += 2 * (size_t)nblocks;
+      double v = f2 > 0.0 ? sqrt(r2 / f2) : INFINITY;
+      worst = std::max(worst, v);
+    }
+    if (!std::isfinite(worst)) return TAPS_ERR_NONFINITE;
+    *rho_out = worst;
+    return TAPS_OK;
+  }
   double FF = 0.0, FA = 0.0, AA = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    FF += h[3 * b];
-    FA += h[3 * b + 1];
-    AA += h[3 * b + 2];
+  for (int b = 0; b < 64; ++b) {
+    FF += P->h_part[3 * b];
+    FA += P->h_part[3 * b + 1];
+    AA += P->h_part[3 * b + 2];
   }
   double r2 = FF - 2.0 * FA + AA;
   double rho = sqrt(std::max(r2, 0.0) / FF);
   if (!std::isfinite(rho)) return TAPS_ERR_NONFINITE;
   *rho_out = rho;
-  prof_drain(P);
-  return taps_check_status(P->d_status, s);
+  return TAPS_OK;
+}
+
+int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
+  int M = U->M;
+  if (M < 1) return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_ws_ensure(P, M));
+  TAPS_TRY(taps_residual_enqueue(P, U, kind));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  return taps_residual_finish(P, U, kind, rho_out);
 }

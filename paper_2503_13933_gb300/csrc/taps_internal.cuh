@@ -96,6 +96,7 @@ struct ProfPending {
 
 struct ProfState {
   bool events;
+  bool capturing;   // a sweep graph is being captured: record event nodes
   long long launches[TAPS_PROF_NUM];
   double ms[TAPS_PROF_NUM];
   double flops[TAPS_PROF_NUM];
@@ -134,6 +135,10 @@ struct taps_problem {
   int* d_status;
   unsigned* d_bar;    // grid barrier words (count, generation)
   double* h_scal;     // pinned host mirror of d_scal
+  double* h_part;     // pinned host mirror of the residual partial sums
+  int* h_status;      // pinned host mirror of the device status word
+  cudaStream_t cap_stream;  // private stream used to capture sweep graphs
+  void* graph;        // cached sweep graph (SweepGraph, api.cu)
   double* d_Usnap[TAPS_MAX_DIMS];  // factor snapshot for the FP32 -> FP64 retry
   void* d_evalbuf;    // grow-only gathered rows of taps_eval_grid
   size_t evalbuf_len;
@@ -245,6 +250,11 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
 int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
                     double* change_out);
 int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
+int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize);
+int taps_sweep_finish(taps_problem* P, taps_factors* U, double* change_out);
+int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind);
+int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
+int taps_fd_prepare_all(taps_problem* P, int solver);
 int taps_check_status(int* d_status, cudaStream_t s);
 int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB);
 int taps_fd_solve(taps_problem* P, taps_factors* U, int d);

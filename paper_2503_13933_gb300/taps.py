@@ -60,7 +60,7 @@ class SolveOpts(ctypes.Structure):
                 ("res_tol", ctypes.c_double), ("res_kind", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("precision", ctypes.c_int),
                 ("polish_sweeps", ctypes.c_int), ("solver", ctypes.c_int), ("init", ctypes.c_int),
-                ("seed", ctypes.c_uint), ("history_cap", ctypes.c_int)]
+                ("seed", ctypes.c_uint), ("history_cap", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -199,7 +199,16 @@ class Problem:
     def __init__(self, desc, stream=None):
         self.desc = desc
         self.stream = stream if stream is not None else current_stream()
-        self.dims = [Dim(dm, self.stream) for dm in desc["dims"]]
+        # identical dimension descriptions share one assembled dimension (and its
+        # cached pencil decomposition)
+        uniq = {}
+        self.dims = []
+        for dm in desc["dims"]:
+            key = tuple(sorted((k, tuple(v) if isinstance(v, (list, tuple)) else v)
+                               for k, v in dm.items()))
+            if key not in uniq:
+                uniq[key] = Dim(dm, self.stream)
+            self.dims.append(uniq[key])
         D = len(self.dims)
         self.D = D
         terms = (Term * len(desc["terms"]))()
@@ -253,10 +262,11 @@ class Problem:
 
     def solve(self, U, M0=1, M_max=8, als_tol=1e-10, res_tol=1e-6, res_kind=RES_ALS,
               max_sweeps=200, precision=FP64, polish_sweeps=20, init=INIT_ZERO, seed=0,
-              history_cap=4096, raise_not_converged=False, solver=SOLVER_BLOCK_LU):
+              history_cap=4096, raise_not_converged=False, solver=SOLVER_BLOCK_LU, graphs=True):
         o = SolveOpts(M0=M0, M_max=M_max, als_tol=als_tol, res_tol=res_tol, res_kind=res_kind,
                       max_sweeps=max_sweeps, precision=precision, polish_sweeps=polish_sweeps,
-                      solver=solver, init=init, seed=seed, history_cap=history_cap)
+                      solver=solver, init=init, seed=seed, history_cap=history_cap,
+                      graphs=int(graphs))
         hM = (ctypes.c_int * max(history_cap, 1))()
         hc = (ctypes.c_double * max(history_cap, 1))()
         hr = (ctypes.c_double * max(history_cap, 1))()
