@@ -282,6 +282,41 @@ int taps_eval_grid_noalloc(const taps_problem* prob, const taps_factors* U, cons
 int taps_eval_points(const taps_problem* prob, const taps_factors* U, int n_pts,
                      const double* pts_dev, double* out_dev);
 
+/* ---- learned warm start (the paper's Algorithm 1 starts from random values) ------
+ * A fully connected FP32 network n_in -> H (x hidden_layers, tanh) -> n_out (linear)
+ * with hand-written forward, backward (mean squared error) and Adam kernels.  It maps
+ * an instance's parameter vector and a mode index to that mode's factor profiles;
+ * taps_factors_from_profiles turns predictions into initial factors.  Parameters are
+ * one flat FP32 array: per layer W [out][in] row-major, then b [out].  Weights start
+ * Xavier-uniform from SplitMix64 draws of `seed`.  All device pointers are
+ * caller-owned; calls run on `stream` (taps_mlp_train and the _get/_set calls
+ * synchronise it). */
+#define TAPS_MLP_MAX_LAYERS 8
+typedef struct taps_mlp taps_mlp;
+int taps_mlp_create(int n_in, int n_hidden, int hidden_layers, int n_out, unsigned seed, void* stream,
+                    taps_mlp** out);
+long long taps_mlp_num_params(const taps_mlp* net);
+int taps_mlp_get_params(const taps_mlp* net, float* host, long long n);
+int taps_mlp_set_params(taps_mlp* net, const float* host, long long n);  /* also resets Adam */
+/* y_dev[batch][n_out] = net(x_dev[batch][n_in]) */
+int taps_mlp_forward(taps_mlp* net, const float* x_dev, int batch, float* y_dev);
+/* loss = mean (net(x) - t)^2 over batch x n_out; parameter gradients kept on the device
+ * (and copied to grad_host, nparams floats, when it is not NULL). */
+int taps_mlp_grad(taps_mlp* net, const float* x_dev, const float* t_dev, int batch, float* loss_out,
+                  float* grad_host);
+/* one Adam step with the last gradients (bias-corrected moments) */
+int taps_mlp_adam(taps_mlp* net, float lr, float beta1, float beta2, float eps);
+/* `steps` full-batch gradient + Adam(0.9, 0.999, 1e-8) steps; loss of the last step */
+int taps_mlp_train(taps_mlp* net, const float* x_dev, const float* t_dev, int batch, int steps, float lr,
+                   float* loss_out);
+void taps_mlp_destroy(taps_mlp* net);
+/* Initial factors from predicted profiles: prof_dev [M][D * n_ref + 1] (FP32), per
+ * dim d a profile at n_ref uniform points of [lo_d, hi_d] (all-node coordinates),
+ * then the mode weight.  U_d[:, m] = the profile interpolated linearly at the free
+ * nodes; the last dim is multiplied by weight_scale * weight.  Sets the factors' M. */
+int taps_factors_from_profiles(const taps_problem* prob, taps_factors* U, int M, const float* prof_dev,
+                               int n_ref, double weight_scale);
+
 /* ---- profiling: per kernel class, CUDA events on the problem's stream ----------
  * taps_profile_reset clears the counters; with enable_events = 1 every launch of a
  * class is bracketed by CUDA events (read back at the library's own stream

@@ -697,3 +697,57 @@ def als_residual(prob: Problem, U):
         nf = np.linalg.norm(F)
         worst = max(worst, np.linalg.norm(r) / nf if nf > 0 else math.inf)
     return worst
+
+
+# ---------------------------------------------------------------------------------
+# Warm-start network (not in the paper: the learned initialisation that replaces the
+# random start of Algorithm 1).  FP64, written from the chain rule.
+# Layout of the flat parameter vector: per layer W [out][in] row-major, then b [out].
+# ---------------------------------------------------------------------------------
+def mlp_unpack(p, dims):
+    out, off = [], 0
+    for i, o in zip(dims[:-1], dims[1:]):
+        W = p[off:off + i * o].reshape(o, i)
+        off += i * o
+        b = p[off:off + o]
+        off += o
+        out.append((W, b))
+    return out
+
+
+def mlp_forward(p, dims, X):
+    """Activations A_0 = X, A_{l+1} = tanh(A_l W_l^T + b_l) (linear last layer)."""
+    acts = [np.asarray(X, dtype=float)]
+    layers = mlp_unpack(np.asarray(p, dtype=float), dims)
+    for l, (W, b) in enumerate(layers):
+        Z = acts[-1] @ W.T + b
+        acts.append(np.tanh(Z) if l < len(layers) - 1 else Z)
+    return acts
+
+
+def mlp_loss_grad(p, dims, X, T):
+    """Mean squared error over all outputs and its gradient (same flat layout)."""
+    layers = mlp_unpack(np.asarray(p, dtype=float), dims)
+    acts = mlp_forward(p, dims, X)
+    Y = acts[-1]
+    n = Y.size
+    loss = float(np.sum((Y - T) ** 2) / n)
+    G = 2.0 * (Y - T) / n
+    grads = [None] * len(layers)
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        A = acts[l]
+        grads[l] = (G.T @ A, G.sum(axis=0))
+        if l > 0:
+            G = (G @ W) * (1.0 - A ** 2)
+    flat = np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
+    return loss, flat
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """Adam (Kingma & Ba 2015) with bias-corrected moments; returns new p, m, v."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -104,6 +104,17 @@ SIGNATURES = {
     "taps_eval_points": (_i, [_vp, _vp, _i, _vp, _vp]),
     "taps_eval_grid_noalloc": (_i, [_vp, _vp, _pi, _pi, _pi, _vp, _i]),
     "taps_profile_reset": (_i, [_vp, _i]),
+    "taps_mlp_create": (_i, [_i, _i, _i, _i, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
+    "taps_mlp_num_params": (ctypes.c_longlong, [_vp]),
+    "taps_mlp_get_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
+    "taps_mlp_set_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
+    "taps_mlp_forward": (_i, [_vp, _vp, _i, _vp]),
+    "taps_mlp_grad": (_i, [_vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(ctypes.c_float)]),
+    "taps_mlp_adam": (_i, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "taps_mlp_train": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "taps_mlp_destroy": (None, [_vp]),
+    "taps_factors_from_profiles": (_i, [_vp, _vp, _i, _vp, _i, _d]),
     "taps_profile_get": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong), _pd, _pd, _pd]),
 }
 
@@ -328,6 +339,59 @@ class Problem:
             self.handle = None
 
 
+class MLP:
+    """The warm-start network (taps_mlp_*): FP32, tanh hidden layers, linear output."""
+
+    def __init__(self, n_in, n_hidden, hidden_layers, n_out, seed=0, stream=None):
+        self.stream = stream if stream is not None else current_stream()
+        h = ctypes.c_void_p()
+        check(lib().taps_mlp_create(n_in, n_hidden, hidden_layers, n_out, seed, self.stream,
+                                    ctypes.byref(h)), "taps_mlp_create")
+        self.handle = h
+        self.n_in, self.n_out = n_in, n_out
+        self.nparams = lib().taps_mlp_num_params(h)
+
+    def params(self):
+        out = np.zeros(self.nparams, dtype=np.float32)
+        check(lib().taps_mlp_get_params(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        self.nparams), "taps_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(lib().taps_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        self.nparams), "taps_mlp_set_params")
+
+    def forward(self, x, y):
+        """x, y: CUDA float32 tensors [batch, n_in], [batch, n_out]."""
+        check(lib().taps_mlp_forward(self.handle, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                     ctypes.c_void_p(y.data_ptr())), "taps_mlp_forward")
+        return y
+
+    def grad(self, x, t, want_grad=True):
+        loss = ctypes.c_float()
+        g = np.zeros(self.nparams, dtype=np.float32) if want_grad else None
+        check(lib().taps_mlp_grad(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                  int(x.shape[0]), ctypes.byref(loss),
+                                  g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None),
+              "taps_mlp_grad")
+        return loss.value, g
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        check(lib().taps_mlp_adam(self.handle, lr, b1, b2, eps), "taps_mlp_adam")
+
+    def train(self, x, t, steps, lr=1e-3):
+        loss = ctypes.c_float()
+        check(lib().taps_mlp_train(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                   int(x.shape[0]), steps, lr, ctypes.byref(loss)), "taps_mlp_train")
+        return loss.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.taps_mlp_destroy(self.handle)
+            self.handle = None
+
+
 class Factors:
     """CP factor matrices U_d (n_free x M, column-major on the device)."""
 
@@ -347,6 +411,13 @@ class Factors:
         cols = [np.asfortranarray(u, dtype=np.float64) for u in Us]
         ptrs = (_pd * len(cols))(*[c.ctypes.data_as(_pd) for c in cols])
         check(lib().taps_factors_set(self.handle, M, ptrs), "taps_factors_set")
+
+    def from_profiles(self, prof, M, n_ref, weight_scale=1.0):
+        """Initial factors from predicted profiles (CUDA float32 [M, D*n_ref + 1])."""
+        check(lib().taps_factors_from_profiles(self.prob.handle, self.handle, M,
+                                               ctypes.c_void_p(prof.data_ptr()), n_ref,
+                                               float(weight_scale)),
+              "taps_factors_from_profiles")
 
     def get(self):
         M = self.M

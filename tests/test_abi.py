@@ -13,7 +13,7 @@ def _declared():
     src = open(os.path.join(ROOT, "include", "taps.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(
-        r"^\s*(?:const\s+)?(?:int|void|char|double)\s*\*?\s*(taps_\w+)\s*\(", src, flags=re.M)))
+        r"^\s*(?:const\s+)?(?:int|void|char|double|long long)\s*\*?\s*(taps_\w+)\s*\(", src, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
