@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-space", type=int, default=WORKLOAD["n_space"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--paths", default="fp64,fp64_fastdiag,mixed_fastdiag,fp64_fastdiag_mlp",
+    ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp32gram_fastdiag,mixed_fastdiag,mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
     return ap.parse_args()
 
@@ -220,7 +220,7 @@ def run_ours(args, rank, world, local):
     # for other seeded instances; its inference is part of the timed step of its path
     ws_info = None
     ws = None
-    if "fp64_fastdiag_mlp" in args.paths.split(","):
+    if any(p.endswith("_mlp") for p in args.paths.split(",")):
         from paper_2503_13933_gb300 import warmstart as WS
         t0 = time.perf_counter()
         Xw, Tw, _ = WS.training_set(range(WORKLOAD["seed"] + 1, WORKLOAD["seed"] + 17),
@@ -233,8 +233,9 @@ def run_ours(args, rank, world, local):
     # plain FP64 path (block-banded elimination) and the fast paths
     paths = {"fp64": (taps.FP64, taps.SOLVER_BLOCK_LU),
              "fp64_fastdiag": (taps.FP64, taps.SOLVER_FASTDIAG),
-             "mixed_fastdiag": (taps.FP32, taps.SOLVER_FASTDIAG),
-             "fp64_fastdiag_mlp": (taps.FP64, taps.SOLVER_FASTDIAG, "mlp")}
+             "fp32gram_fastdiag": (taps.FP32, taps.SOLVER_FASTDIAG),
+             "mixed_fastdiag": (taps.MIXED, taps.SOLVER_FASTDIAG),
+             "mixed_fastdiag_mlp": (taps.MIXED, taps.SOLVER_FASTDIAG, "mlp")}
     paths = {k: v for k, v in paths.items() if k in args.paths.split(",")}
     res = {}
     for name, prec in paths.items():

@@ -74,7 +74,10 @@ extern "C" {
 
 /* ---- precisions of the Gram / SpMM contractions (reduced solves stay FP64) --- */
 #define TAPS_FP64 0
-#define TAPS_FP32 1
+#define TAPS_FP32 1   /* FP32 Gram / SpMM contractions; FP64 solves and residuals */
+#define TAPS_MIXED 2  /* FP64 Grams; the n small M x M systems of the fast-diagonalisation
+                         solve factorised in FP32 and refined in FP64 to FP64 backward
+                         accuracy (FP64 LU fallback per system) */
 
 /* ---- residual kinds ----------------------------------------------------------- */
 #define TAPS_RES_ALS 0   /* max_d ||K^[d] U_d - Q^[d]|| / ||Q^[d]|| of Eq. 42           */

@@ -516,7 +516,7 @@ extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const 
   int precision = opts ? opts->precision : TAPS_FP64;
   int solver = opts ? opts->solver : TAPS_SOLVER_BLOCK_LU;
   int normalize = opts ? opts->normalize : 1;
-  if (precision != TAPS_FP64 && precision != TAPS_FP32) return TAPS_ERR_INVALID_ARG;
+  if (precision != TAPS_FP64 && precision != TAPS_FP32 && precision != TAPS_MIXED) return TAPS_ERR_INVALID_ARG;
   if (solver != TAPS_SOLVER_BLOCK_LU && solver != TAPS_SOLVER_FASTDIAG) return TAPS_ERR_INVALID_ARG;
   double t0 = now_s();
   TAPS_TRY(taps_ws_ensure(P, U->M));
@@ -542,7 +542,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
                           taps_solve_report* rep) {
   if (!P || !U || !o || U->prob != P) return TAPS_ERR_INVALID_ARG;
   if (o->M_max < 1 || o->M_max > U->M_cap || o->max_sweeps < 1 ||
-      (o->precision != TAPS_FP64 && o->precision != TAPS_FP32) ||
+      (o->precision != TAPS_FP64 && o->precision != TAPS_FP32 && o->precision != TAPS_MIXED) ||
       (o->res_kind != TAPS_RES_ALS && o->res_kind != TAPS_RES_FULL) ||
       o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO ||
       (o->solver != TAPS_SOLVER_BLOCK_LU && o->solver != TAPS_SOLVER_FASTDIAG))

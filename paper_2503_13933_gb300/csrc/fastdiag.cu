@@ -275,25 +275,27 @@ __global__ void fd_rhs_kernel(const double* __restrict__ q, const double* __rest
 }
 
 // Out[i][m] = sum_j Mat[i][j] In[j][m] (Mat n x n row-major, In n x M row-major).
-// One warp per output row i: lanes split the sum over j, each lane keeps 32 mode
-// accumulators, and the per-lane partials are combined through shared memory.
+// One CTA per output row i.  Its RG_WARPS warps (one per SM sub-partition) split the
+// sum over j; within a warp the lanes split it again, each lane keeping 32 mode
+// accumulators.  The partials are combined through shared memory.  FP64 on this GPU
+// is issue-bound per sub-partition, so spreading one row over all four pipes matters.
 // Out is n x M row-major, or (colmajor) the factor layout Out[m * n + i].
 #define RG_WARPS 4
 __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double* __restrict__ Mat,
                                                                    const double* __restrict__ In, int n,
                                                                    int M, double* __restrict__ Out,
                                                                    int colmajor) {
-  __shared__ double part[RG_WARPS][32][33];
+  __shared__ double part[RG_WARPS * 32][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * RG_WARPS + warp;
-  if (i >= n) return;   // whole warps only: no block-wide barrier below
+  const int i = blockIdx.x;
   const double* row = Mat + (size_t)i * n;
+  const int step = RG_WARPS * 32;
   for (int m0 = 0; m0 < M; m0 += 32) {
     const int mc = min(32, M - m0);
     double acc[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-    for (int j = lane; j < n; j += 32) {
+    for (int j = warp * 32 + lane; j < n; j += step) {
       const double a = row[j];
       const double* in = In + (size_t)j * M + m0;
 #pragma unroll
@@ -301,30 +303,82 @@ __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double*
         if (c < mc) acc[c] += a * in[c];
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c) part[warp][lane][c] = acc[c];
-    __syncwarp();
-    if (lane < mc) {
+    for (int c = 0; c < 32; ++c) part[threadIdx.x][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < mc) {
       double sum = 0.0;
-      for (int l = 0; l < 32; ++l) sum += part[warp][l][lane];
-      if (colmajor) Out[(size_t)(m0 + lane) * n + i] = sum;
-      else Out[(size_t)i * M + m0 + lane] = sum;
+      for (int l = 0; l < step; ++l) sum += part[l][threadIdx.x];
+      if (colmajor) Out[(size_t)(m0 + threadIdx.x) * n + i] = sum;
+      else Out[(size_t)i * M + m0 + threadIdx.x] = sum;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
 // One warp per node i, M <= 32: lane r holds row r of (mu_i C_A + C_B | g_i) in
-// registers; LU without pivoting (the systems are mu_i C_A + C_B with positive
-// definite symmetric part) and back substitution by shuffles.  A zero or
-// non-finite pivot is reported as TAPS_DEV_SINGULAR.
-__global__ void __launch_bounds__(128) fd_small_solve_warp_kernel(const double* __restrict__ CA,
-                                                                  const double* __restrict__ CB,
-                                                                  const double* __restrict__ mu,
-                                                                  const double* __restrict__ G, int n,
-                                                                  int M, double* __restrict__ Y,
-                                                                  int* status) {
+// registers.  Without refinement: LU without pivoting in FP64 (the systems have a
+// positive definite symmetric part) and back substitution by shuffles.  With
+// refinement: the LU runs in FP32 and the solution is refined in FP64
+// (y += T^{-1}_32 (g - T y)) until the FP64 residual is at the level of FP64
+// rounding; a system that does not get there in 4 steps is solved again by the FP64
+// LU.  A zero or non-finite pivot is reported as TAPS_DEV_SINGULAR.
+template <typename R>
+__device__ __forceinline__ void warp_lu_inplace(R row[33], int lane, int M, bool& bad) {
+#pragma unroll
+  for (int p = 0; p < 32; ++p) {
+    if (p < M) {
+      R piv = __shfl_sync(0xffffffffu, row[p], p);
+      bad |= !(fabs((double)piv) > 0.0) || !isfinite((double)piv);
+      R l = (lane > p && lane < M && piv != (R)0) ? row[p] / piv : (R)0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c > p && c < M) {
+          R pc = __shfl_sync(0xffffffffu, row[c], p);
+          row[c] -= l * pc;
+        }
+      }
+      if (lane > p && lane < M) row[p] = l;   // keep the multiplier (unit lower L)
+    }
+  }
+}
+
+// Solve L U x = b with the factors of warp_lu_inplace; b and x are lane-distributed.
+template <typename R>
+__device__ __forceinline__ R warp_lu_solve(const R row[33], R b, int lane, int M) {
+#pragma unroll
+  for (int p = 0; p < 32; ++p) {
+    if (p < M) {
+      R bp = __shfl_sync(0xffffffffu, b, p);
+      if (lane > p && lane < M) b -= row[p] * bp;
+    }
+  }
+  R x = (R)0;
+#pragma unroll
+  for (int c = 31; c >= 0; --c) {
+    if (c < M) {
+      R xc = (lane == c && row[c] != (R)0) ? b / row[c] : (R)0;
+      xc = __shfl_sync(0xffffffffu, xc, c);
+      if (lane == c) x = xc;
+      if (lane < c) b -= row[c] * xc;
+    }
+  }
+  return x;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* __restrict__ CA,
+                                                                 const double* __restrict__ CB,
+                                                                 const double* __restrict__ mu,
+                                                                 const double* __restrict__ G, int n,
+                                                                 int M, double* __restrict__ Y,
+                                                                 int* status, int refine) {
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int i = blockIdx.x;   // one warp per CTA: the n systems spread over every SM
   if (i >= n) return;
   const double mi = (CA && mu) ? mu[i] : 0.0;
   double row[33];
@@ -334,38 +388,47 @@ __global__ void __launch_bounds__(128) fd_small_solve_warp_kernel(const double* 
     if (lane < M && c < M) v = (CA ? mi * CA[lane * M + c] : 0.0) + CB[lane * M + c];
     row[c] = v;
   }
-  row[32] = (lane < M) ? G[(size_t)i * M + lane] : 0.0;
+  const double g = (lane < M) ? G[(size_t)i * M + lane] : 0.0;
   bool bad = false;
+  double x = 0.0;
+  bool done = false;
+  if (refine) {
+    float rf[33];
 #pragma unroll
-  for (int p = 0; p < 32; ++p) {
-    if (p < M) {
-      double piv = __shfl_sync(0xffffffffu, row[p], p);
-      bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
-      double l = (lane > p && lane < M && piv != 0.0) ? row[p] / piv : 0.0;
+    for (int c = 0; c < 33; ++c) rf[c] = (float)row[c];
+    bool bad32 = false;
+    warp_lu_inplace<float>(rf, lane, M, bad32);
+    if (!bad32) {
+      double tnorm = 0.0;
 #pragma unroll
-      for (int c = 0; c < 33; ++c) {
-        if (c > p && (c < M || c == 32)) {
-          double pc = __shfl_sync(0xffffffffu, row[c], p);
-          row[c] -= l * pc;
+      for (int c = 0; c < 32; ++c) tnorm += fabs(row[c]);
+      tnorm = warp_max(tnorm);
+      double r = g;
+      for (int it = 0; it < 4 && !done; ++it) {
+        x += (double)warp_lu_solve<float>(rf, (float)r, lane, M);
+        // r = g - T x in FP64
+        double acc = g;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          if (c < M) acc -= row[c] * __shfl_sync(0xffffffffu, x, c);
         }
+        r = (lane < M) ? acc : 0.0;
+        double rmax = warp_max(fabs(r)), xmax = warp_max(fabs(x)), gmax = warp_max(fabs(g));
+        done = rmax <= 8.0 * 2.220446049250313e-16 * (tnorm * xmax + gmax);
+        if (!isfinite(rmax)) break;
       }
     }
   }
-  if (bad && lane == 0) taps_flag(status, TAPS_DEV_SINGULAR);
-  double x = 0.0;
-#pragma unroll
-  for (int c = 31; c >= 0; --c) {
-    if (c < M) {
-      double xc = (lane == c && row[c] != 0.0) ? row[32] / row[c] : 0.0;
-      xc = __shfl_sync(0xffffffffu, xc, c);
-      if (lane == c) x = xc;
-      if (lane < c) row[32] -= row[c] * xc;
-    }
+  if (!done) {   // FP64 LU (also the fallback of the refined path)
+    warp_lu_inplace<double>(row, lane, M, bad);
+    x = warp_lu_solve<double>(row, g, lane, M);
+    if (bad && lane == 0) taps_flag(status, TAPS_DEV_SINGULAR);
   }
   if (lane < M) Y[(size_t)i * M + lane] = x;
 }
 
-// One CTA per node i: solve (mu_i C_A + C_B) y = g_i by LU with partial pivoting.
+// One CTA per node i (M > 32): solve (mu_i C_A + C_B) y = g_i by LU with partial
+// pivoting in shared memory.
 __global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __restrict__ CA,
                                                              const double* __restrict__ CB,
                                                              const double* __restrict__ mu,
@@ -418,8 +481,7 @@ __global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __res
     }
     __syncthreads();
   }
-  // back substitution (one warp)
-  if (tid < 32) {
+  if (tid < 32) {   // back substitution (one warp)
     for (int r = M - 1; r >= 0; --r) {
       double s = 0.0;
       for (int c = r + 1 + tid; c < M; c += 32) s += T[r * ld + c] * T[c * ld + M];
@@ -522,7 +584,7 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
 }
 
 // Reduced solve of dim d by fast diagonalisation, coefficients in P->d_C / P->d_c.
-int taps_fd_solve(taps_problem* P, taps_factors* U, int d) {
+int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
   int slotA, slotB;
   if (!taps_fd_eligible(P, d, &slotA, &slotB)) return TAPS_ERR_INVALID_ARG;
   taps_dim* dm = P->dims[d];
@@ -538,17 +600,16 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d) {
   double* Y = P->d_Y + (size_t)n * M;
   int tk = prof_begin(P, TAPS_PROF_FASTDIAG);
   fd_rhs_kernel<<<(nM + 255) / 256, 256, 0, s>>>(P->d_q[d], P->d_c, P->Rf, n, M, F);
-  const unsigned rg = (unsigned)((n + RG_WARPS - 1) / RG_WARPS);
-  fd_rowgemm_kernel<<<rg, RG_WARPS * 32, 0, s>>>(E->PhiT, F, n, M, G, 0);
+  fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->PhiT, F, n, M, G, 0);
   const double* CA = slotA >= 0 ? P->d_C + (size_t)slotA * MM : nullptr;
   const double* CB = P->d_C + (size_t)slotB * MM;
   if (M <= 32)
-    fd_small_solve_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
-                                                           P->d_status);
+    fd_small_solve_warp_kernel<<<n, 32, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
+                                                P->d_status, precision == TAPS_MIXED ? 1 : 0);
   else
     fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
         CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
-  fd_rowgemm_kernel<<<rg, RG_WARPS * 32, 0, s>>>(E->Phi, Y, n, M, U->d_U[d], 1);
+  fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->Phi, Y, n, M, U->d_U[d], 1);
   P->prof->launches[TAPS_PROF_FASTDIAG] += 3;
   prof_end(P, TAPS_PROF_FASTDIAG, tk,
            2.0 * P->Rf * nM + 4.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),

@@ -93,7 +93,7 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
   const double gbytes = 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf +
                                (double)nops * M * M + (double)Rf * M);
   int tk = prof_begin(P, TAPS_PROF_GRAM);
-  if (precision == TAPS_FP32) {
+  if (precision == TAPS_FP32) {   // TAPS_MIXED keeps FP64 Grams
     gram_partial_kernel<float><<<grid, 256, elems * sizeof(float), P->stream>>>(
         U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride);
   } else {
@@ -515,7 +515,7 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
                               cudaMemcpyDeviceToDevice, s));
     int sa, sb;
     if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb))
-      TAPS_TRY(taps_fd_solve(P, U, d));
+      TAPS_TRY(taps_fd_solve(P, U, d, precision));
     else
       TAPS_TRY(reduced_solve_block_lu(P, U, d));
     int norm_d = (normalize && d < P->D - 1) ? 1 : 0;

@@ -257,5 +257,5 @@ int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, doubl
 int taps_fd_prepare_all(taps_problem* P, int solver);
 int taps_check_status(int* d_status, cudaStream_t s);
 int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB);
-int taps_fd_solve(taps_problem* P, taps_factors* U, int d);
+int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision);
 void taps_fd_release(taps_dim* dm);

@@ -24,7 +24,7 @@ SPACE, PARAM, TIME = 0, 1, 2
 OP = {"K": 0, "M": 1, "G": 2, "W": 3, "Blo": 4, "Bhi": 5}
 NUM_OPS = 6
 SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4}
-FP64, FP32 = 0, 1
+FP64, FP32, MIXED = 0, 1, 2
 RES_ALS, RES_FULL = 0, 1
 INIT_GIVEN, INIT_RANDOM, INIT_ZERO = 0, 1, 2
 SOLVER_BLOCK_LU, SOLVER_FASTDIAG = 0, 1

@@ -178,6 +178,26 @@ def test_graph_replay_matches_direct_launches(T, solver):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("name,M,nsw", [("poisson3d_n12", 3, 3), ("poisson_k_7x9", 4, 2),
+                                        ("heat2d_robin", 5, 3)])
+def test_mixed_refined_small_solves_parity(T, name, M, nsw):
+    """TAPS_MIXED: the small systems of the fast-diagonalisation solve are factorised in
+    FP32 and refined in FP64 to FP64 backward accuracy: same factors as the oracle."""
+    desc = CASES[name]
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=77 + M)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    P.sweep(Ug, nsw, solver=T.SOLVER_FASTDIAG, precision=T.MIXED)
+    Uo = [u.copy() for u in U0]
+    for _ in range(nsw):
+        Uo, _ = O.sweep(Po, Uo, solver="fastdiag")
+    Ugot = Ug.get()
+    for d in range(Po.D):
+        assert rel(Ugot[d], Uo[d]) < 1e-9, (d, rel(Ugot[d], Uo[d]))
+
+
 def test_fastdiag_large_dim_matches_block_lu(T):
     """n = 254 free nodes, M = 12: one fast-diagonalisation sweep and one block-LU
     sweep from the same factors give the same field."""
