@@ -38,7 +38,8 @@ extern "C" {
 #define TAPS_MAX_P 3       /* reproducing order p <= 3 */
 #define TAPS_MAX_QUAD 12   /* Gauss points per element */
 #define TAPS_MAX_M 128     /* modes per factor */
-#define TAPS_MAX_TERMS 64  /* operator terms R and source terms R_f, each */
+#define TAPS_MAX_TERMS 64     /* operator terms R */
+#define TAPS_MAX_SOURCES 1024 /* source terms R_f (slab chaining adds M per term and slab) */
 
 /* ---- status codes ---------------------------------------------------------- */
 #define TAPS_OK 0
@@ -71,6 +72,9 @@ extern "C" {
 #define TAPS_SRC_GAUSS 2  /* exp(-(x - par[0])^2 / (2 par[1]^2))          */
 #define TAPS_SRC_POLY 3   /* par[0] + par[1] x + par[2] x^2 + par[3] x^3  */
 #define TAPS_SRC_NODAL 4  /* C-HiDeNN interpolant of nodal values (all nodes) */
+#define TAPS_SRC_OPVEC 5  /* q = Op v over the free nodes: par[0] = operator kind, nodal = v
+                             (n_free values); the projection of a field already in the
+                             C-HiDeNN space, e.g. the end state of a previous time slab */
 
 /* ---- precisions of the Gram / SpMM contractions (reduced solves stay FP64) --- */
 #define TAPS_FP64 0
@@ -126,7 +130,8 @@ typedef struct {
   double beta;
   int kind[TAPS_MAX_DIMS];
   double par[TAPS_MAX_DIMS][4];
-  const double* nodal[TAPS_MAX_DIMS]; /* TAPS_SRC_NODAL: host array of n values */
+  const double* nodal[TAPS_MAX_DIMS]; /* TAPS_SRC_NODAL: host array of n values;
+                                         TAPS_SRC_OPVEC: host array of n_free values */
 } taps_source;
 
 typedef struct {
@@ -200,7 +205,7 @@ void taps_dim_destroy(taps_dim* dim);
  * (the separated Galerkin operator and force of Eqs. 33-41).  `dims` are assembled
  * dimensions (the problem keeps pointers: they must outlive it).  Source projections
  * q_{r,d} are computed on the device.  Errors: TAPS_ERR_INVALID_ARG for D outside
- * [1, TAPS_MAX_DIMS], R or Rf outside [1, TAPS_MAX_TERMS], an operator or source kind
+ * [1, TAPS_MAX_DIMS], R outside [1, TAPS_MAX_TERMS], Rf outside [1, TAPS_MAX_SOURCES], an operator or source kind
  * out of range, or a NULL nodal array. */
 int taps_problem_create(taps_dim* const* dims, int D, const taps_term* terms, int R,
                         const taps_source* sources, int Rf, void* stream,

@@ -294,9 +294,12 @@ def build_problem(dims, terms, sources):
     src = []
     for beta, facs in sources:
         qs = []
-        for dm, tb, (kind, par) in zip(dims, tabs, facs):
+        for d, (dm, tb, (kind, par)) in enumerate(zip(dims, tabs, facs)):
             if kind == "nodal":
                 qs.append(project_source(dm, kind, None, nodal=par, tab=tb))
+            elif kind == "opvec":
+                # the projection of a field already in the C-HiDeNN space: q = Op v
+                qs.append(ops[d][OP_BY_NAME[par[0]]] @ np.asarray(par[1], dtype=float))
             else:
                 qs.append(project_source(dm, kind, par, tab=tb))
         src.append((float(beta), qs))
@@ -751,3 +754,39 @@ def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------------------------
+# Time slabs (Sec. 2.4, Eq. 16; App. B Eq. 56): initial condition by lifting.
+# ---------------------------------------------------------------------------------
+def slab_end_state(U, time_dim, prev=None):
+    """(spatial/parametric factors, weights) of u(., t_max): the time factors' last rows
+    weight the modes; the previous slab's lifting modes are kept in front."""
+    facs = [None if d == time_dim else np.array(u) for d, u in enumerate(U)]
+    wts = np.array(U[time_dim][-1, :])
+    if prev is not None:
+        pf, pw = prev
+        facs = [None if d == time_dim else np.concatenate([pf[d], facs[d]], axis=1)
+                for d in range(len(U))]
+        wts = np.concatenate([pw, wts])
+    return facs, wts
+
+
+def slab_next_description(desc, state, time_dim, t_shift):
+    """Next slab: time window shifted; force += -alpha_t w_m (x)_d (Op_{t,d} U_d[:,m]) (x) M_t 1
+    for each term without time derivative (d/dt of the constant lifting is zero)."""
+    facs, wts = state
+    nd = dict(desc)
+    nd["dims"] = [dict(dm) for dm in desc["dims"]]
+    nd["dims"][time_dim]["lo"] += t_shift
+    nd["dims"][time_dim]["hi"] += t_shift
+    extra = []
+    for alpha, ops in desc["terms"]:
+        if ops[time_dim] == "G":
+            continue
+        for m in range(len(wts)):
+            extra.append((-alpha * wts[m],
+                          [("const", (1.0,)) if d == time_dim else ("opvec", (ops[d], facs[d][:, m]))
+                           for d in range(len(ops))]))
+    nd["sources"] = list(desc["sources"]) + extra
+    return nd

@@ -266,6 +266,7 @@ extern "C" void taps_problem_destroy(taps_problem* P) {
   }
   cudaFree(P->d_status);
   cudaFree(P->d_bar);
+  cudaFree(P->d_beta);
   cudaFree(P->d_evalbuf);
   if (P->h_status) cudaFreeHost(P->h_status);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
@@ -328,7 +329,7 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   if (!out) return TAPS_ERR_INVALID_ARG;
   *out = nullptr;
   if (!dims || !terms || !sources || D < 1 || D > TAPS_MAX_DIMS || R < 1 || R > TAPS_MAX_TERMS ||
-      Rf < 1 || Rf > TAPS_MAX_TERMS)
+      Rf < 1 || Rf > TAPS_MAX_SOURCES)
     return TAPS_ERR_INVALID_ARG;
   for (int d = 0; d < D; ++d)
     if (!dims[d]) return TAPS_ERR_INVALID_ARG;
@@ -338,8 +339,10 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   for (int r = 0; r < Rf; ++r)
     for (int d = 0; d < D; ++d) {
       int k = sources[r].kind[d];
-      if (k < TAPS_SRC_CONST || k > TAPS_SRC_NODAL) return TAPS_ERR_INVALID_ARG;
-      if (k == TAPS_SRC_NODAL && !sources[r].nodal[d]) return TAPS_ERR_INVALID_ARG;
+      if (k < TAPS_SRC_CONST || k > TAPS_SRC_OPVEC) return TAPS_ERR_INVALID_ARG;
+      if ((k == TAPS_SRC_NODAL || k == TAPS_SRC_OPVEC) && !sources[r].nodal[d]) return TAPS_ERR_INVALID_ARG;
+      if (k == TAPS_SRC_OPVEC && (sources[r].par[d][0] < 0 || sources[r].par[d][0] >= TAPS_NUM_OPS))
+        return TAPS_ERR_INVALID_ARG;
     }
   taps_problem* P = new taps_problem();
   memset((void*)P, 0, sizeof(taps_problem));
@@ -370,7 +373,8 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
     P->tt.nops[d] = n;
   }
   for (int t = 0; t < R; ++t) P->tt.alpha[t] = terms[t].alpha;
-  for (int r = 0; r < Rf; ++r) P->tt.beta[r] = sources[r].beta;
+  std::vector<double> hbeta(Rf);
+  for (int r = 0; r < Rf; ++r) hbeta[r] = sources[r].beta;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -378,6 +382,12 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   do {
     if ((st = taps_alloc((void**)&P->d_status, sizeof(int))) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&P->d_bar, 2 * sizeof(unsigned))) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&P->d_beta, sizeof(double) * Rf)) != TAPS_OK) break;
+    if (cudaMemcpy(P->d_beta, hbeta.data(), sizeof(double) * Rf, cudaMemcpyHostToDevice) != cudaSuccess) {
+      st = TAPS_ERR_CUDA;
+      break;
+    }
+    P->tt.beta = P->d_beta;
     if (cudaMallocHost((void**)&P->h_status, sizeof(int)) != cudaSuccess) { st = TAPS_ERR_OOM; break; }
     *P->h_status = 0;
     if (cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }

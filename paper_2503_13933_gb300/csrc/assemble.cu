@@ -312,14 +312,20 @@ __device__ __forceinline__ double source_factor(int kind, const double* par, dou
 // q_i = int N~_i g (Gauss sums over the elements touching node i), or for nodal
 // data q = M_full g; written for the free nodes only.
 __global__ void source_kernel(DimParams P, const double* Nt, const double* xq,
-                              const double* band_full, int kind, double p0, double p1,
-                              double p2, double p3, const double* nodal, double* q_free) {
+                              const double* band_full, const double* band_free, int kind, double p0,
+                              double p1, double p2, double p3, const double* nodal, double* q_free) {
   int fi = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= P.nf) return;
   int i = fi + P.off;
   double par[4] = {p0, p1, p2, p3};
   double v = 0.0;
-  if (kind == TAPS_SRC_NODAL) {
+  if (kind == TAPS_SRC_OPVEC) {   // q = Op v on the free nodes
+    const double* row = band_free + ((size_t)(int)p0 * P.nf + fi) * P.nb;
+    for (int k = 0; k < P.nb; ++k) {
+      int fj = fi + k - P.hb;
+      if (fj >= 0 && fj < P.nf) v += row[k] * nodal[fj];
+    }
+  } else if (kind == TAPS_SRC_NODAL) {
     const double* Mrow = band_full + ((size_t)TAPS_OP_M * P.n + i) * P.nb;
     for (int k = 0; k < P.nb; ++k) {
       int j = i + k - P.hb;
@@ -476,16 +482,17 @@ extern "C" int taps_dim_copy_shape(const taps_dim* d, double* N_out, double* B_o
 // Source projection of one factor onto the free nodes of an assembled dimension.
 int taps_project_source(const taps_dim* d, int kind, const double* par, const double* nodal_host,
                         double* d_q_free, cudaStream_t s) {
-  if (kind < TAPS_SRC_CONST || kind > TAPS_SRC_NODAL) return TAPS_ERR_INVALID_ARG;
+  if (kind < TAPS_SRC_CONST || kind > TAPS_SRC_OPVEC) return TAPS_ERR_INVALID_ARG;
   DimParams P = make_params(d);
   double* d_nodal = nullptr;
-  if (kind == TAPS_SRC_NODAL) {
+  if (kind == TAPS_SRC_NODAL || kind == TAPS_SRC_OPVEC) {
     if (!nodal_host) return TAPS_ERR_INVALID_ARG;
-    TAPS_TRY(taps_alloc((void**)&d_nodal, sizeof(double) * d->n));
-    TAPS_CUDA(cudaMemcpyAsync(d_nodal, nodal_host, sizeof(double) * d->n, cudaMemcpyHostToDevice, s));
+    size_t len = kind == TAPS_SRC_NODAL ? d->n : d->nf;
+    TAPS_TRY(taps_alloc((void**)&d_nodal, sizeof(double) * len));
+    TAPS_CUDA(cudaMemcpyAsync(d_nodal, nodal_host, sizeof(double) * len, cudaMemcpyHostToDevice, s));
   }
-  source_kernel<<<(d->nf + 127) / 128, 128, 0, s>>>(P, d->d_N, d->d_xq, d->d_band_full, kind, par[0],
-                                                     par[1], par[2], par[3], d_nodal, d_q_free);
+  source_kernel<<<(d->nf + 127) / 128, 128, 0, s>>>(P, d->d_N, d->d_xq, d->d_band_full, d->d_band, kind,
+                                                     par[0], par[1], par[2], par[3], d_nodal, d_q_free);
   cudaError_t e = cudaGetLastError();
   if (d_nodal) {
     cudaStreamSynchronize(s);

@@ -79,7 +79,7 @@ struct taps_dim {
 struct TermTable {
   int D, R, Rf;
   double alpha[TAPS_MAX_TERMS];
-  double beta[TAPS_MAX_TERMS];
+  const double* beta;   // device array [Rf] (source amplitudes)
   signed char oi[TAPS_MAX_TERMS][TAPS_MAX_DIMS];  // distinct-op index of term t in dim d
   int nops[TAPS_MAX_DIMS];
 };
@@ -115,6 +115,7 @@ struct taps_problem {
   int ops[TAPS_MAX_DIMS][TAPS_NUM_OPS];  // op kind of each distinct-op slot
   int nf_max;
   double* d_q[TAPS_MAX_DIMS];            // [Rf][nf_d] source projections
+  double* d_beta;                        // [Rf] source amplitudes
   double* d_opband[TAPS_MAX_DIMS];       // [nops_d][nf_d][nb] bands of the distinct ops
   // Workspace, grown to the largest mode count seen (ws_M).
   int ws_M;

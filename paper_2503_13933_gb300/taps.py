@@ -17,13 +17,14 @@ LIB_PATH = os.path.join(HERE, "libtaps.so")
 
 MAX_DIMS = 8
 MAX_TERMS = 64
+MAX_SOURCES = 1024
 OK, ERR_INVALID_ARG, ERR_SINGULAR, ERR_NONFINITE, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4
 ERR_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SCRATCH_LIMIT = -5, -6, -7, -8
 NOALLOC_SCRATCH_BYTES = 4 << 20
 SPACE, PARAM, TIME = 0, 1, 2
 OP = {"K": 0, "M": 1, "G": 2, "W": 3, "Blo": 4, "Bhi": 5}
 NUM_OPS = 6
-SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4}
+SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4, "opvec": 5}
 FP64, FP32, MIXED = 0, 1, 2
 RES_ALS, RES_FULL = 0, 1
 INIT_GIVEN, INIT_RANDOM, INIT_ZERO = 0, 1, 2
@@ -237,6 +238,11 @@ class Problem:
                     arr = np.ascontiguousarray(par, dtype=np.float64)
                     self._keep.append(arr)
                     srcs[r].nodal[d] = arr.ctypes.data_as(_pd)
+                elif kind == "opvec":        # (operator name, free-node vector)
+                    arr = np.ascontiguousarray(par[1], dtype=np.float64)
+                    self._keep.append(arr)
+                    srcs[r].nodal[d] = arr.ctypes.data_as(_pd)
+                    srcs[r].par[d][0] = float(OP[par[0]])
                 else:
                     vals = [float(v) for v in par] + [0.0] * (4 - len(par))
                     for j in range(4):
