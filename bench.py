@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-space", type=int, default=WORKLOAD["n_space"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=32, help="instances of the batched measurement (0: off)")
     ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp32gram_fastdiag,mixed_fastdiag,mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
     return ap.parse_args()
@@ -323,6 +324,42 @@ def run_ours(args, rank, world, local):
     eval_gbs = ev["bytes"] / (ev["ms"] * 1e-3) / 1e9 if ev["ms"] > 0 else None
     launches = sum(v["launches"] for v in prof.values()) // max(args.steps, 1)
 
+    batched = None
+    if args.batch > 0:
+        # independent seeded instances (D 3..6, n_d 32..128, M 4..16, Poisson/transient):
+        # 10 sweeps each, all instances as one graph per sweep vs one launch sequence
+        # per instance in turn
+        descs, Ms = W.batch_instances(count=args.batch, seed=4000 + 1000 * rank, n_lo=32, n_hi=128,
+                                      M_lo=4, M_hi=16)
+        bp, bu, b0 = [], [], []
+        for i, (dsc, Mi) in enumerate(zip(descs, Ms)):
+            Pi = taps.Problem(dsc, stream=taps.ctypes.c_void_p(torch.cuda.Stream().cuda_stream))
+            Ui = Pi.factors(Mi)
+            U0i = W.random_factors(dsc, Mi, seed=100 + i)
+            Ui.set(U0i)
+            bp.append(Pi)
+            bu.append(Ui)
+            b0.append(U0i)
+        times = {}
+        for mode in ("graph", "per_instance"):
+            Bt = taps.Batch(bp, bu, solver=taps.SOLVER_FASTDIAG)
+            for _ in range(2):
+                for Ui, U0i in zip(bu, b0):
+                    Ui.set(U0i)
+                Bt.sweep(10, graphs=(mode == "graph"))
+            for Ui, U0i in zip(bu, b0):
+                Ui.set(U0i)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Bt.sweep(10, graphs=(mode == "graph"))
+            torch.cuda.synchronize()
+            times[mode] = time.perf_counter() - t0
+        batched = dict(instances=args.batch, sweeps=10, dims=[len(d["dims"]) for d in descs][:8],
+                       graph_s=times["graph"], per_instance_s=times["per_instance"],
+                       instances_per_s=args.batch / times["graph"],
+                       instances_per_s_per_instance_launches=args.batch / times["per_instance"],
+                       speedup=times["per_instance"] / times["graph"])
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nsw = res[best]["sweeps"]
@@ -356,6 +393,7 @@ def run_ours(args, rank, world, local):
                  converged=rep2["converged"]),
         gpu_launches=launches,
         warm_start=ws_info,
+        batched=batched,
         clocks=res[list(paths)[-1]]["clocks"],
     )
     print(json.dumps(line))

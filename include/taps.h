@@ -290,6 +290,21 @@ int taps_eval_grid_noalloc(const taps_problem* prob, const taps_factors* U, cons
 int taps_eval_points(const taps_problem* prob, const taps_factors* U, int n_pts,
                      const double* pts_dev, double* out_dev);
 
+/* ---- batched independent instances ------------------------------------------------
+ * A batch holds `count` (problem, factors) pairs -- distinct problems, each created on
+ * its own stream -- and sweeps them together (Algorithm 1 inner loop per instance).
+ * With graphs = 1, one sweep of every instance is captured once as one CUDA graph
+ * (instances on their own streams, forked from and joined to the batch's stream)
+ * and replayed n_sweeps times; otherwise each instance runs its own launch sequence
+ * in turn.  changes_out (count values, optional) receives each instance's factor
+ * change of its last sweep.  The pointers must outlive the batch.  Errors as
+ * taps_sweep, TAPS_ERR_INVALID_ARG for a shared problem or empty factors. */
+typedef struct taps_batch taps_batch;
+int taps_batch_create(taps_problem* const* probs, taps_factors* const* Us, int count, int precision,
+                      int solver, taps_batch** out);
+int taps_batch_sweep(taps_batch* batch, int n_sweeps, int graphs, double* changes_out);
+void taps_batch_destroy(taps_batch* batch);
+
 /* ---- learned warm start (the paper's Algorithm 1 starts from random values) ------
  * A fully connected FP32 network n_in -> H (x hidden_layers, tanh) -> n_out (linear)
  * with hand-written forward, backward (mean squared error) and Adam kernels.  It maps

@@ -901,3 +901,141 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
   }
   return st;
 }
+
+
+// ---------------------------------------------------------------------------------
+// Batched independent instances: one sweep of every instance captured as one CUDA
+// graph (each instance on its own stream, forked from and joined to a master stream),
+// replayed n_sweeps times back to back.  Without graphs each instance runs its own
+// launch sequence in turn (the one-launch-sequence-per-instance baseline).
+// ---------------------------------------------------------------------------------
+struct taps_batch {
+  int count, precision, solver;
+  taps_problem** P;
+  taps_factors** U;
+  cudaStream_t master;
+  cudaEvent_t fork;
+  cudaEvent_t* join;
+  cudaGraph_t g;
+  cudaGraphExec_t exec;
+};
+
+extern "C" void taps_batch_destroy(taps_batch* B) {
+  if (!B) return;
+  if (B->master) cudaStreamSynchronize(B->master);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->g) cudaGraphDestroy(B->g);
+  if (B->join) {
+    for (int i = 0; i < B->count; ++i) cudaEventDestroy(B->join[i]);
+    delete[] B->join;
+  }
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->master) cudaStreamDestroy(B->master);
+  delete[] B->P;
+  delete[] B->U;
+  delete B;
+}
+
+extern "C" int taps_batch_create(taps_problem* const* probs, taps_factors* const* Us, int count, int precision,
+                                 int solver, taps_batch** out) {
+  if (!probs || !Us || !out || count < 1 || (precision != TAPS_FP64 && precision != TAPS_MIXED) ||
+      (solver != TAPS_SOLVER_BLOCK_LU && solver != TAPS_SOLVER_FASTDIAG))
+    return TAPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i] || !Us[i] || Us[i]->prob != probs[i] || Us[i]->M < 1) return TAPS_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == probs[i]) return TAPS_ERR_INVALID_ARG;   // instances must not share workspaces
+  }
+  taps_batch* B = new taps_batch();
+  memset((void*)B, 0, sizeof(taps_batch));
+  B->count = count;
+  B->precision = precision;
+  B->solver = solver;
+  B->P = new taps_problem*[count];
+  B->U = new taps_factors*[count];
+  for (int i = 0; i < count; ++i) { B->P[i] = probs[i]; B->U[i] = Us[i]; }
+  int st = TAPS_OK;
+  do {
+    if (cudaStreamCreateWithFlags(&B->master, cudaStreamNonBlocking) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+    B->join = new cudaEvent_t[count];
+    memset(B->join, 0, sizeof(cudaEvent_t) * count);
+    for (int i = 0; i < count && st == TAPS_OK; ++i)
+      if (cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) != cudaSuccess) st = TAPS_ERR_CUDA;
+    for (int i = 0; i < count && st == TAPS_OK; ++i) {
+      taps_problem* P = B->P[i];
+      if ((st = taps_ws_ensure(P, B->U[i]->M)) != TAPS_OK) break;
+      if ((st = taps_fd_prepare_all(P, solver)) != TAPS_OK) break;
+      if ((st = taps_refresh_grams(P, B->U[i], TAPS_FP64)) != TAPS_OK) break;
+      if (cudaStreamSynchronize(P->stream) != cudaSuccess) st = TAPS_ERR_CUDA;
+    }
+  } while (0);
+  if (st != TAPS_OK) {
+    taps_batch_destroy(B);
+    return st;
+  }
+  *out = B;
+  return TAPS_OK;
+}
+
+static int batch_capture(taps_batch* B) {
+  if (B->exec) return TAPS_OK;
+  if (cudaStreamBeginCapture(B->master, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TAPS_ERR_CUDA;
+  int st = TAPS_OK;
+  cudaEventRecord(B->fork, B->master);
+  cudaStream_t* saved = new cudaStream_t[B->count];
+  for (int i = 0; i < B->count; ++i) {
+    taps_problem* P = B->P[i];
+    saved[i] = P->stream;
+    P->stream = P->cap_stream;
+    bool cap = P->prof->capturing;
+    P->prof->capturing = true;    // no event-pool growth or synchronisation inside capture
+    cudaStreamWaitEvent(P->cap_stream, B->fork, 0);
+    if (st == TAPS_OK) st = taps_sweep_enqueue(P, B->U[i], B->precision, B->solver, 1);
+    cudaEventRecord(B->join[i], P->cap_stream);
+    cudaStreamWaitEvent(B->master, B->join[i], 0);
+    P->prof->capturing = cap;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(B->master, &g);
+  for (int i = 0; i < B->count; ++i) {
+    B->P[i]->stream = saved[i];
+    // events recorded inside the batch graph stay owned by the graph's lifetime; the
+    // instances' pending lists are cleared (their timing is not read for batches)
+    B->P[i]->prof->npending = 0;
+  }
+  delete[] saved;
+  if (ce != cudaSuccess || !g) {
+    cudaGetLastError();
+    return st != TAPS_OK ? st : TAPS_ERR_CUDA;
+  }
+  B->g = g;
+  if (st == TAPS_OK && cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    st = TAPS_ERR_CUDA;
+  }
+  return st;
+}
+
+extern "C" int taps_batch_sweep(taps_batch* B, int n_sweeps, int graphs, double* changes_out) {
+  if (!B || n_sweeps < 1) return TAPS_ERR_INVALID_ARG;
+  if (graphs) {
+    TAPS_TRY(batch_capture(B));
+    for (int it = 0; it < n_sweeps; ++it) TAPS_CUDA(cudaGraphLaunch(B->exec, B->master));
+    TAPS_CUDA(cudaStreamSynchronize(B->master));
+    for (int i = 0; i < B->count; ++i) {
+      double ch = 0.0;
+      TAPS_TRY(taps_sweep_finish(B->P[i], B->U[i], &ch));
+      if (changes_out) changes_out[i] = ch;
+    }
+    return TAPS_OK;
+  }
+  for (int i = 0; i < B->count; ++i) {
+    double ch = 0.0;
+    for (int it = 0; it < n_sweeps; ++it)
+      TAPS_TRY(taps_sweep_impl(B->P[i], B->U[i], B->precision, B->solver, 1, &ch));
+    if (changes_out) changes_out[i] = ch;
+  }
+  return TAPS_OK;
+}

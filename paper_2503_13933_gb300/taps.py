@@ -105,6 +105,9 @@ SIGNATURES = {
     "taps_eval_points": (_i, [_vp, _vp, _i, _vp, _vp]),
     "taps_eval_grid_noalloc": (_i, [_vp, _vp, _pi, _pi, _pi, _vp, _i]),
     "taps_profile_reset": (_i, [_vp, _i]),
+    "taps_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_vp)]),
+    "taps_batch_sweep": (_i, [_vp, _i, _i, _pd]),
+    "taps_batch_destroy": (None, [_vp]),
     "taps_mlp_create": (_i, [_i, _i, _i, _i, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
     "taps_mlp_num_params": (ctypes.c_longlong, [_vp]),
     "taps_mlp_get_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
@@ -342,6 +345,30 @@ class Problem:
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.taps_problem_destroy(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """Independent instances swept together (taps_batch_*)."""
+
+    def __init__(self, problems, factors, precision=FP64, solver=SOLVER_FASTDIAG):
+        self.problems, self.factors = list(problems), list(factors)
+        n = len(self.problems)
+        ph = (ctypes.c_void_p * n)(*[p.handle.value for p in self.problems])
+        uh = (ctypes.c_void_p * n)(*[u.handle.value for u in self.factors])
+        h = ctypes.c_void_p()
+        check(lib().taps_batch_create(ph, uh, n, precision, solver, ctypes.byref(h)), "taps_batch_create")
+        self.handle = h
+
+    def sweep(self, n_sweeps, graphs=True):
+        ch = np.zeros(len(self.problems))
+        check(lib().taps_batch_sweep(self.handle, n_sweeps, int(graphs), ch.ctypes.data_as(_pd)),
+              "taps_batch_sweep")
+        return ch
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.taps_batch_destroy(self.handle)
             self.handle = None
 
 

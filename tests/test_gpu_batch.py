@@ -1,0 +1,60 @@
+"""Batched independent instances: one CUDA graph sweeping all instances gives exactly the
+per-instance results, and an instance agrees with the oracle."""
+import numpy as np
+import pytest
+
+from oracle import taps_oracle as O
+from paper_2503_13933_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_13933_gb300 import build, taps
+    import os
+    if not os.path.exists(taps.LIB_PATH):
+        build.build()
+    taps.lib()
+    return taps
+
+
+def _instances(T, count, seed):
+    descs, Ms = W.batch_instances(count=count, seed=seed, n_lo=10, n_hi=24, M_lo=2, M_hi=5)
+    probs, facs, inits = [], [], []
+    for i, (dsc, M) in enumerate(zip(descs, Ms)):
+        P = T.Problem(dsc, stream=T.ctypes.c_void_p(torch.cuda.Stream().cuda_stream))
+        U = P.factors(M)
+        U0 = W.random_factors(dsc, M, seed=100 + i)
+        U.set(U0)
+        probs.append(P)
+        facs.append(U)
+        inits.append(U0)
+    return descs, probs, facs, inits
+
+
+@pytest.mark.parametrize("solver", ["fastdiag", "block_lu"])
+def test_batched_graph_equals_per_instance(T, solver):
+    sv = T.SOLVER_FASTDIAG if solver == "fastdiag" else T.SOLVER_BLOCK_LU
+    descs, probs, facs, inits = _instances(T, 6, 4100)
+    B = T.Batch(probs, facs, solver=sv)
+    chg = B.sweep(3, graphs=True)
+    got = [u.get() for u in facs]
+    for P, U, U0 in zip(probs, facs, inits):
+        U.set(U0)
+    chg2 = T.Batch(probs, facs, solver=sv).sweep(3, graphs=False)
+    ref = [u.get() for u in facs]
+    for a, b in zip(got, ref):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(chg, chg2)
+    # one instance against the oracle
+    Po = O.problem_from_description(descs[0])
+    Uo = [u.copy() for u in inits[0]]
+    for _ in range(3):
+        Uo, _ = O.sweep(Po, Uo, solver="fastdiag" if solver == "fastdiag" else "banded")
+    a, b = O.cp_full(got[0]), O.cp_full(Uo)
+    assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
