@@ -172,6 +172,10 @@ static int graph_sweep(taps_problem* P, taps_factors* U, int prec, int solver, i
     *fallback = 1;
     return TAPS_ERR_CUDA;
   }
+  if (!match && taps_lu_needs_tuning(P, solver, U->M)) {
+    *fallback = 1;   // run this sweep directly: the block-elimination tuner needs it
+    return TAPS_ERR_CUDA;
+  }
   if (!match) {
     TAPS_TRY(taps_fd_prepare_all(P, solver));
     if (graph_build(P, U, prec, solver, res_kind) != TAPS_OK) {

@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double*
 // One warp per node i, M <= 32: lane r holds row r of (mu_i C_A + C_B | g_i) in
 // registers.  Without refinement: LU without pivoting in FP64 (the systems have a
 // positive definite symmetric part) and back substitution by shuffles.  With
-// refinement: the LU runs in FP32 and the solution is refined in FP64
+// refinement: the LU runs in FP32 (whose dependent-instruction latency is a small
+// fraction of FP64's on this GPU) and the solution is refined in FP64
 // (y += T^{-1}_32 (g - T y)) until the FP64 residual is at the level of FP64
 // rounding; a system that does not get there in 4 steps is solved again by the FP64
 // LU.  A zero or non-finite pivot is reported as TAPS_DEV_SINGULAR.
@@ -406,14 +407,21 @@ __global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* _
       double r = g;
       for (int it = 0; it < 4 && !done; ++it) {
         x += (double)warp_lu_solve<float>(rf, (float)r, lane, M);
-        // r = g - T x in FP64
-        double acc = g;
+        // r = g - T x in FP64, as four independent partial sums (FP64 latency is long)
+        double a0 = g, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          if (c < M) acc -= row[c] * __shfl_sync(0xffffffffu, x, c);
+        for (int c = 0; c < 32; c += 4) {
+          double x0 = __shfl_sync(0xffffffffu, x, c), x1 = __shfl_sync(0xffffffffu, x, c + 1);
+          double x2 = __shfl_sync(0xffffffffu, x, c + 2), x3 = __shfl_sync(0xffffffffu, x, c + 3);
+          if (c < M) a0 -= row[c] * x0;
+          if (c + 1 < M) a1 -= row[c + 1] * x1;
+          if (c + 2 < M) a2 -= row[c + 2] * x2;
+          if (c + 3 < M) a3 -= row[c + 3] * x3;
         }
-        r = (lane < M) ? acc : 0.0;
+        r = (lane < M) ? (a0 + a1) + (a2 + a3) : 0.0;
         double rmax = warp_max(fabs(r)), xmax = warp_max(fabs(x)), gmax = warp_max(fabs(g));
+        // FP64 backward accuracy (a few eps), so that the refined path gives the
+        // FP64 path's factors; the FP64 LU below is the fallback
         done = rmax <= 8.0 * 2.220446049250313e-16 * (tnorm * xmax + gmax);
         if (!isfinite(rmax)) break;
       }

@@ -2,6 +2,7 @@
 // banded SpMM + U^T Y, Eq. 34), coefficient combine (Hadamard products over the other
 // dimensions, Eq. 35), block-banded reduced system (Eqs. 36-40) and its solve,
 // column normalisation and factor change; residuals of Eq. 42 and of the full system.
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -236,8 +237,8 @@ __global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ bloc
         for (int idx = tid; idx < (int)MM; idx += nthr) sm[(idx / M) * ld + idx % M] = lu_g[idx];
       }
       __syncthreads();
-      int task = blockIdx.x * nwarps + warp;
-      if (task < ntask) {
+      // grid-stride over the columns: any CTA count covers all of them
+      for (int task = blockIdx.x * nwarps + warp; task < ntask; task += (int)nblk * nwarps) {
         double* col;
         int cstride;
         if (task < nj * M) {
@@ -417,6 +418,92 @@ __global__ void normalize_change_kernel(double* U, const double* Uold, int nf, i
 // ---------------------------------------------------------------------------------
 // Reduced solve of dim d with the coefficients already in P->d_C / P->d_c.
 // ---------------------------------------------------------------------------------
+// Tile-shape tuner of the block elimination: the number of co-resident CTAs trades
+// parallel work per block row against the cost of the three grid barriers per row.
+// On first use for a (n, M) pair, outside any graph capture, each candidate runs the
+// elimination on the current block band (re-assembled before every trial, so every
+// trial computes the same thing) and the fastest is cached for the problem.
+static int lu_grid_default(const taps_problem* P, int hb, int M) {
+  int want = (int)std::min<long long>((long long)hb * hb * M * M / 256 + 1, P->num_sms);
+  int want_a = (hb * M + 1 + 7) / 8;
+  return std::min(std::max(1, std::max(want, want_a)), P->coop_blocks);
+}
+
+int taps_lu_grid(taps_problem* P, int d, taps_factors* U, int nf, int M) {
+  const int hb = P->dims[d]->hb;
+  for (int k = 0; k < P->n_lu_tuned; ++k)
+    if (P->lu_tuned[k][0] == nf && P->lu_tuned[k][1] == M) return P->lu_tuned[k][2];
+  int fallback = lu_grid_default(P, hb, M);
+  if (P->prof->capturing || P->n_lu_tuned >= 16 || getenv("TAPS_NO_TUNE")) return fallback;
+  const int cands[] = {8, 16, 32, 64, 96, 152};
+  cudaStream_t s = P->stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fallback;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fallback; }
+  // keep the assembled band: trials work on a copy
+  const size_t band = sizeof(double) * ((size_t)nf * P->dims[d]->nb * M * M);
+  const size_t rhs = sizeof(double) * (size_t)nf * M;
+  double* keep = nullptr;
+  if (taps_alloc((void**)&keep, band + rhs + sizeof(double)) != TAPS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return fallback; }
+  cudaMemcpyAsync(keep, P->d_blocks, band, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync((char*)keep + band, P->d_F, rhs, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync((char*)keep + band + rhs, P->d_status, sizeof(int), cudaMemcpyDeviceToDevice, s);
+  int best = fallback;
+  float best_ms = 1e30f;
+  size_t smem = sizeof(double) * (size_t)M * (M + 1);
+  int hbv = hb, nfv = nf, Mv = M;
+  for (int c : cands) {
+    int g = std::min(c, P->coop_blocks);
+    cudaMemcpyAsync(P->d_blocks, keep, band, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(P->d_F, (char*)keep + band, rhs, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(P->d_bar, 0, 2 * sizeof(unsigned), s);
+    double* blocks = P->d_blocks;
+    double* Fp = P->d_F;
+    double* lu = P->d_lu;
+    int* st = P->d_status;
+    unsigned* bar = P->d_bar;
+    void* args[] = {&blocks, &Fp, &lu, &nfv, &hbv, &Mv, &st, &bar};
+    cudaEventRecord(e0, s);
+    if (cudaLaunchCooperativeKernel((const void*)block_lu_kernel, dim3(g), dim3(256), args, smem, s) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = g; }
+  }
+  // restore the assembled band and the status word for the real elimination
+  cudaMemcpyAsync(P->d_blocks, keep, band, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(P->d_F, (char*)keep + band, rhs, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(P->d_status, (char*)keep + band + rhs, sizeof(int), cudaMemcpyDeviceToDevice, s);
+  cudaStreamSynchronize(s);
+  cudaFree(keep);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->lu_tuned[P->n_lu_tuned][0] = nf;
+  P->lu_tuned[P->n_lu_tuned][1] = M;
+  P->lu_tuned[P->n_lu_tuned][2] = best;
+  P->n_lu_tuned++;
+  (void)U;
+  return best;
+}
+
+// 1 if some dim of the sweep would use block elimination with an untuned (n, M).
+int taps_lu_needs_tuning(const taps_problem* P, int solver, int M) {
+  if (getenv("TAPS_NO_TUNE")) return 0;
+  for (int d = 0; d < P->D; ++d) {
+    int sa, sb;
+    if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb)) continue;
+    bool found = false;
+    for (int k = 0; k < P->n_lu_tuned; ++k)
+      if (P->lu_tuned[k][0] == P->dims[d]->nf && P->lu_tuned[k][1] == M) found = true;
+    if (!found && P->n_lu_tuned < 16) return 1;
+  }
+  return 0;
+}
+
 static int reduced_solve_block_lu(taps_problem* P, taps_factors* U, int d) {
   const taps_dim* dm = P->dims[d];
   int M = U->M, nf = dm->nf, hb = dm->hb, nb = dm->nb, nops = P->tt.nops[d];
@@ -438,12 +525,9 @@ static int reduced_solve_block_lu(taps_problem* P, taps_factors* U, int d) {
     bs_flops += nj * 2.0 * Md * Md;
   }
   const double band_bytes = 8.0 * (double)nf * nb * M * M;
-  // cooperative elimination
+  // cooperative elimination; the CTA count comes from the tuner (first use per (n, M))
   size_t smem = sizeof(double) * (size_t)M * (M + 1);
-  int want = (int)std::min<long long>((long long)hb * hb * M * M / 256 + 1, P->num_sms);
-  int want_a = (hb * M + 1 + 7) / 8;
-  int grid = std::max(1, std::max(want, want_a));
-  grid = std::min(grid, P->coop_blocks);
+  int grid = taps_lu_grid(P, d, U, nf, M);
   TAPS_CUDA(cudaMemsetAsync(P->d_bar, 0, 2 * sizeof(unsigned), s));
   double* blocks = P->d_blocks;
   double* Fp = P->d_F;

@@ -144,6 +144,8 @@ struct taps_problem {
   void* d_evalbuf;    // grow-only gathered rows of taps_eval_grid
   size_t evalbuf_len;
   int eval_attr_set;  // shared-memory opt-in of the reconstruction kernels done
+  int lu_tuned[16][3];  // tuned block-elimination CTA counts: (n, M, CTAs)
+  int n_lu_tuned;
   int coop_blocks;    // CTAs of the cooperative block solve
   int num_sms;
   ProfState* prof;
@@ -256,6 +258,7 @@ int taps_sweep_finish(taps_problem* P, taps_factors* U, double* change_out);
 int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind);
 int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
 int taps_fd_prepare_all(taps_problem* P, int solver);
+int taps_lu_needs_tuning(const taps_problem* P, int solver, int M);
 int taps_check_status(int* d_status, cudaStream_t s);
 int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB);
 int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision);
