@@ -435,6 +435,98 @@ __global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* _
   if (lane < M) Y[(size_t)i * M + lane] = x;
 }
 
+// One CTA of four warps per node i, M <= 32, FP64.  FP64 instructions issue at a
+// fraction of a lane per clock per SM sub-partition on this GPU, so the elimination
+// of one system is spread over the four sub-partitions: warp w holds the columns
+// c = w, w+4, w+8, ... of T = mu_i C_A + C_B (lane r = row r) and warp 0 also the
+// right-hand side.  At step p every warp updates its columns c > p with the
+// multipliers l_r = T[r][p] / T[p][p] of that step, which the owner of column p has
+// published in shared memory (one reciprocal of the pivot, kept for the back
+// substitution).  The owner of column p+1 updates that column first and publishes
+// the next multipliers before its other columns, so the chain of pivots is not held
+// up by the bulk of the updates.  No pivoting, as in the one-warp solve.  The upper
+// factor then goes to shared memory and warp 0 back-substitutes.
+__global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* __restrict__ CA,
+                                                                  const double* __restrict__ CB,
+                                                                  const double* __restrict__ mu,
+                                                                  const double* __restrict__ G, int n,
+                                                                  int M, double* __restrict__ Y,
+                                                                  int* status) {
+  __shared__ double lbuf[2][32];
+  __shared__ double invd[32];
+  __shared__ double Ush[32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const double mi = (CA && mu) ? mu[i] : 0.0;
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int c = 4 * k + w;
+    double x = 0.0;
+    if (lane < M && c < M) x = (CA ? mi * CA[lane * M + c] : 0.0) + CB[lane * M + c];
+    v[k] = x;
+  }
+  double b = (w == 0 && lane < M) ? G[(size_t)i * M + lane] : 0.0;
+  bool bad = false;
+  // multipliers of step 0 (column 0 belongs to warp 0)
+  if (w == 0) {
+    const double piv = __shfl_sync(0xffffffffu, v[0], 0);
+    bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
+    const double inv = bad ? 0.0 : 1.0 / piv;
+    lbuf[0][lane] = (lane > 0 && lane < M) ? v[0] * inv : 0.0;
+    if (lane == 0) invd[0] = inv;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 32; ++p) {
+    if (p < M) {
+      const double l = lbuf[p & 1][lane];
+      const int q = p + 1;   // next pivot column, owned by warp q & 3 in slot q >> 2
+      if (q < 32 && q < M && w == (q & 3)) {
+        const double pc = __shfl_sync(0xffffffffu, v[q >> 2], p);
+        v[q >> 2] -= l * pc;
+        const double piv = __shfl_sync(0xffffffffu, v[q >> 2], q);
+        const bool badq = !(fabs(piv) > 0.0) || !isfinite(piv);
+        bad |= badq;
+        const double inv = badq ? 0.0 : 1.0 / piv;
+        lbuf[q & 1][lane] = (lane > q && lane < M) ? v[q >> 2] * inv : 0.0;
+        if (lane == 0) invd[q] = inv;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (4 * k + 3 <= p) continue;              // every column of this slot is <= p
+        if (q < 32 && k == (q >> 2) && w == (q & 3)) continue;   // column q, done above
+        if (4 * k <= p && w <= p - 4 * k) continue;   // column 4k + w <= p
+        const double pc = __shfl_sync(0xffffffffu, v[k], p);
+        v[k] -= l * pc;
+      }
+      if (w == 0) b -= l * __shfl_sync(0xffffffffu, b, p);
+      __syncthreads();
+    }
+  }
+  // upper factor to shared memory; warp 0 back-substitutes with the kept reciprocals
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int c = 4 * k + w;
+    Ush[lane][c] = v[k];
+  }
+  __syncthreads();
+  if (w == 0) {
+    double x = 0.0;
+#pragma unroll
+    for (int c = 31; c >= 0; --c) {
+      if (c < M) {
+        const double xc = __shfl_sync(0xffffffffu, b, c) * invd[c];
+        if (lane == c) x = xc;
+        if (lane < c) b -= Ush[lane][c] * xc;
+      }
+    }
+    if (lane < M) Y[(size_t)i * M + lane] = x;
+  }
+  if (bad && lane == 0) taps_flag(status, TAPS_DEV_SINGULAR);
+}
+
 // One CTA per node i (M > 32): solve (mu_i C_A + C_B) y = g_i by LU with partial
 // pivoting in shared memory.
 __global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __restrict__ CA,
@@ -611,9 +703,12 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
   fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->PhiT, F, n, M, G, 0);
   const double* CA = slotA >= 0 ? P->d_C + (size_t)slotA * MM : nullptr;
   const double* CB = P->d_C + (size_t)slotB * MM;
-  if (M <= 32)
+  if (M <= 32 && precision == TAPS_MIXED)
     fd_small_solve_warp_kernel<<<n, 32, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
-                                                P->d_status, precision == TAPS_MIXED ? 1 : 0);
+                                                P->d_status, 1);
+  else if (M <= 32)
+    fd_small_solve_quad_kernel<<<n, 128, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
+                                                 P->d_status);
   else
     fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
         CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);

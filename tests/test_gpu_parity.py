@@ -335,6 +335,35 @@ def test_full_rank_2d_more_than_32_modes(T):
     assert np.linalg.norm(ug - O.cp_full(Uo)) / np.linalg.norm(u_full) < 1e-8
 
 
+@pytest.mark.parametrize("nodes,M", [(7, 1), (19, 17), (31, 29), (34, 32)])
+def test_fastdiag_full_rank_2d_reaches_kronecker_solution(T, nodes, M):
+    """Fast-diagonalisation small solves with the columns of each M x M system spread
+    over four warps (ragged when 4 does not divide M, one column at M = 1): with
+    M = n_free modes one sweep gives the brute-force Kronecker solution, and the same
+    field as the oracle's fast-diagonalisation sweep."""
+    desc = _full_rank_2d(nodes, M + 2, seed=30 + M)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=11 + M)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    P.sweep(Ug, 1, solver=T.SOLVER_FASTDIAG)
+    assert P.profile()["fastdiag"]["launches"] > 0
+    u_full = O.solve_full(Po)
+    ug = O.cp_full(Ug.get())
+    Uo, _ = O.sweep(Po, U0, solver="fastdiag")
+    Ub, _ = O.sweep(Po, U0)
+    # the reduced systems of M random modes are ill-conditioned; the spread between
+    # the oracle's own two FP64 solvers (fast diagonalisation, dense LU) measures
+    # kappa * eps for this case and sets the bound
+    uo = O.cp_full(Uo)
+    spread = np.linalg.norm(uo - O.cp_full(Ub)) / np.linalg.norm(u_full)
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(u_full) < max(1e-10, 10 * spread)
+    if M == nodes - 2:   # as many modes as free nodes
+        reach = np.linalg.norm(uo - u_full) / np.linalg.norm(u_full)
+        assert np.linalg.norm(ug - u_full) / np.linalg.norm(u_full) < max(1e-10, 10 * reach)
+
+
 def test_fp32_grams_then_fp64_polish(T):
     """Mixed precision: FP32 Gram sweeps, then FP64 polishing, reach the full-rank
     solution within the mixed-path bound 1e-6."""
