@@ -133,7 +133,7 @@ static int graph_build(taps_problem* P, taps_factors* U, int prec, int solver, i
     st = TAPS_ERR_CUDA;
   } else {
     st = taps_sweep_enqueue(P, U, prec, solver, 1);
-    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind);
+    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind, prec != TAPS_FP32);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
     if (ce != cudaSuccess || g == nullptr) st = (st == TAPS_OK) ? TAPS_ERR_CUDA : st;
@@ -266,6 +266,7 @@ extern "C" void taps_problem_destroy(taps_problem* P) {
   free_ws(P);
   for (int d = 0; d < TAPS_MAX_DIMS; ++d) {
     cudaFree(P->d_q[d]);
+    cudaFree(P->d_pq[d]);
     cudaFree(P->d_opband[d]);
   }
   cudaFree(P->d_status);
@@ -607,7 +608,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       TAPS_TRY(sst);
       ++sweeps;
       if (prec == TAPS_FP64) ++fp64_sweeps;
-      if (!rho_done) TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho));
+      if (!rho_done) TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho, prec != TAPS_FP32));
       if (o->history_cap > 0 && rep && hist < o->history_cap) {
         if (rep->hist_M) rep->hist_M[hist] = M;
         if (rep->hist_change) rep->hist_change[hist] = change;

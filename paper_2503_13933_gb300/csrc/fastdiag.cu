@@ -274,20 +274,39 @@ __global__ void fd_rhs_kernel(const double* __restrict__ q, const double* __rest
   F[idx] = v;
 }
 
+// PQ[r][i] = sum_j PhiT[i][j] q[r][j]: the source vectors of dim d in the eigenbasis
+// of its pencil.  The reduced right-hand side of dim d is F = Q c (c from the other
+// dims), so its transform Phi^T F = (Phi^T Q) c needs only this fixed n x Rf matrix.
+__global__ void fd_pq_kernel(const double* __restrict__ PhiT, const double* __restrict__ q, int n,
+                             int Rf, double* __restrict__ PQ) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * Rf) return;
+  const int r = (int)(idx / n), i = (int)(idx % n);
+  const double* row = PhiT + (size_t)i * n;
+  const double* qr = q + (size_t)r * n;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) acc += row[j] * qr[j];
+  PQ[idx] = acc;
+}
+
 // Out[i][m] = sum_j Mat[i][j] In[j][m] (Mat n x n row-major, In n x M row-major).
 // One CTA per output row i.  Its RG_WARPS warps (one per SM sub-partition) split the
 // sum over j; within a warp the lanes split it again, each lane keeping 32 mode
 // accumulators.  The partials are combined through shared memory.  FP64 on this GPU
 // is issue-bound per sub-partition, so spreading one row over all four pipes matters.
-// Out is n x M row-major, or (colmajor) the factor layout Out[m * n + i].
+// Out is n x M row-major, or (colmajor) the factor layout Out[m * n + i]; in the
+// factor layout a non-null Save receives the row's previous values first.
 #define RG_WARPS 4
 __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double* __restrict__ Mat,
                                                                    const double* __restrict__ In, int n,
                                                                    int M, double* __restrict__ Out,
-                                                                   int colmajor) {
+                                                                   int colmajor,
+                                                                   double* __restrict__ Save) {
   __shared__ double part[RG_WARPS * 32][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x;
+  if (colmajor && Save)   // the writes below come after a barrier
+    for (int m = threadIdx.x; m < M; m += blockDim.x) Save[(size_t)m * n + i] = Out[(size_t)m * n + i];
   const double* row = Mat + (size_t)i * n;
   const int step = RG_WARPS * 32;
   for (int m0 = 0; m0 < M; m0 += 32) {
@@ -439,7 +458,8 @@ __global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* _
 // fraction of a lane per clock per SM sub-partition on this GPU, so the elimination
 // of one system is spread over the four sub-partitions: warp w holds the columns
 // c = w, w+4, w+8, ... of T = mu_i C_A + C_B (lane r = row r) and warp 0 also the
-// right-hand side.  At step p every warp updates its columns c > p with the
+// right-hand side g_i = sum_r PQ[r][i] c_r, formed here from the transformed source
+// vectors (the warps split the sum over r).  At step p every warp updates its columns c > p with the
 // multipliers l_r = T[r][p] / T[p][p] of that step, which the owner of column p has
 // published in shared memory (one reciprocal of the pivot, kept for the back
 // substitution).  The owner of column p+1 updates that column first and publishes
@@ -449,9 +469,11 @@ __global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* _
 __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* __restrict__ CA,
                                                                   const double* __restrict__ CB,
                                                                   const double* __restrict__ mu,
-                                                                  const double* __restrict__ G, int n,
-                                                                  int M, double* __restrict__ Y,
+                                                                  const double* __restrict__ PQ,
+                                                                  const double* __restrict__ cf, int Rf,
+                                                                  int n, int M, double* __restrict__ Y,
                                                                   int* status) {
+  __shared__ double gpart[4][32];
   __shared__ double lbuf[2][32];
   __shared__ double invd[32];
   __shared__ double Ush[32][33];
@@ -467,7 +489,10 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
     if (lane < M && c < M) x = (CA ? mi * CA[lane * M + c] : 0.0) + CB[lane * M + c];
     v[k] = x;
   }
-  double b = (w == 0 && lane < M) ? G[(size_t)i * M + lane] : 0.0;
+  double gp = 0.0;
+  if (lane < M)
+    for (int r = w; r < Rf; r += 4) gp += PQ[(size_t)r * n + i] * cf[(size_t)r * M + lane];
+  gpart[w][lane] = gp;
   bool bad = false;
   // multipliers of step 0 (column 0 belongs to warp 0)
   if (w == 0) {
@@ -478,6 +503,7 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
     if (lane == 0) invd[0] = inv;
   }
   __syncthreads();
+  double b = (w == 0) ? (gpart[0][lane] + gpart[1][lane]) + (gpart[2][lane] + gpart[3][lane]) : 0.0;
 #pragma unroll
   for (int p = 0; p < 32; ++p) {
     if (p < M) {
@@ -691,32 +717,36 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
   FdEntry* E = nullptr;
   int opA = slotA >= 0 ? P->ops[d][slotA] : -1;
   TAPS_TRY(fd_prepare(P, d, dm, opA, P->ops[d][slotB], &E));
+  if (!P->d_pq[d]) return TAPS_ERR_INVALID_ARG;   // taps_fd_prepare_all comes first
   const int n = dm->nf, M = U->M;
   const size_t MM = (size_t)M * M;
   cudaStream_t s = P->stream;
   const int nM = n * M;
-  double* F = P->d_F;
   double* G = P->d_Y;
   double* Y = P->d_Y + (size_t)n * M;
   int tk = prof_begin(P, TAPS_PROF_FASTDIAG);
-  fd_rhs_kernel<<<(nM + 255) / 256, 256, 0, s>>>(P->d_q[d], P->d_c, P->Rf, n, M, F);
-  fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->PhiT, F, n, M, G, 0);
   const double* CA = slotA >= 0 ? P->d_C + (size_t)slotA * MM : nullptr;
   const double* CB = P->d_C + (size_t)slotB * MM;
-  if (M <= 32 && precision == TAPS_MIXED)
-    fd_small_solve_warp_kernel<<<n, 32, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
-                                                P->d_status, 1);
-  else if (M <= 32)
-    fd_small_solve_quad_kernel<<<n, 128, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
-                                                 P->d_status);
-  else
-    fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
-        CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
-  fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->Phi, Y, n, M, U->d_U[d], 1);
-  P->prof->launches[TAPS_PROF_FASTDIAG] += 3;
+  int launches = 2;
+  if (M <= 32 && precision != TAPS_MIXED) {
+    fd_small_solve_quad_kernel<<<n, 128, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, P->d_pq[d],
+                                                 P->d_c, P->Rf, n, M, Y, P->d_status);
+  } else {
+    fd_rhs_kernel<<<(nM + 255) / 256, 256, 0, s>>>(P->d_pq[d], P->d_c, P->Rf, n, M, G);
+    if (M <= 32)
+      fd_small_solve_warp_kernel<<<n, 32, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
+                                                  P->d_status, 1);
+    else
+      fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
+          CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
+    ++launches;
+  }
+  // back to the nodal basis; the previous factor goes to d_Uold for the change norm
+  fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->Phi, Y, n, M, U->d_U[d], 1, P->d_Uold);
+  P->prof->launches[TAPS_PROF_FASTDIAG] += launches - 1;
   prof_end(P, TAPS_PROF_FASTDIAG, tk,
-           2.0 * P->Rf * nM + 4.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),
-           8.0 * (2.0 * (double)n * n + 4.0 * nM + (double)P->Rf * n + 2.0 * MM));
+           2.0 * P->Rf * nM + 2.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),
+           8.0 * ((double)n * n + 4.0 * nM + (double)P->Rf * n + 2.0 * MM));
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }
@@ -730,6 +760,15 @@ int taps_fd_prepare_all(taps_problem* P, int solver) {
     if (!taps_fd_eligible(P, d, &sa, &sb)) continue;
     FdEntry* E = nullptr;
     TAPS_TRY(fd_prepare(P, d, P->dims[d], sa >= 0 ? P->ops[d][sa] : -1, P->ops[d][sb], &E));
+    if (!P->d_pq[d]) {   // the problem's source vectors in the pencil's eigenbasis
+      const int n = P->dims[d]->nf;
+      const long long tot = (long long)n * P->Rf;
+      TAPS_TRY(taps_alloc((void**)&P->d_pq[d], sizeof(double) * (size_t)std::max(tot, 1LL)));
+      if (tot > 0)
+        fd_pq_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, P->stream>>>(E->PhiT, P->d_q[d], n, P->Rf,
+                                                                           P->d_pq[d]);
+      TAPS_CUDA(cudaGetLastError());
+    }
   }
   return TAPS_OK;
 }

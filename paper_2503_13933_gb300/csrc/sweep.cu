@@ -595,13 +595,14 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
   for (int d = 0; d < P->D; ++d) {
     const taps_dim* dm = P->dims[d];
     TAPS_TRY(coefficients(P, d, M));
-    TAPS_CUDA(cudaMemcpyAsync(P->d_Uold, U->d_U[d], sizeof(double) * dm->nf * M,
-                              cudaMemcpyDeviceToDevice, s));
     int sa, sb;
-    if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb))
-      TAPS_TRY(taps_fd_solve(P, U, d, precision));
-    else
+    if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb)) {
+      TAPS_TRY(taps_fd_solve(P, U, d, precision));   // keeps the old factor in d_Uold
+    } else {
+      TAPS_CUDA(cudaMemcpyAsync(P->d_Uold, U->d_U[d], sizeof(double) * dm->nf * M,
+                                cudaMemcpyDeviceToDevice, s));
       TAPS_TRY(reduced_solve_block_lu(P, U, d));
+    }
     int norm_d = (normalize && d < P->D - 1) ? 1 : 0;
     int tk = prof_begin(P, TAPS_PROF_NORMALIZE);
     normalize_change_kernel<<<M, 256, 0, s>>>(U->d_U[d], P->d_Uold, dm->nf, M, norm_d,
@@ -777,13 +778,13 @@ __global__ void full_residual_combine_kernel(TermTable tt, BigGramPtrs bg, int M
 
 // Residual kernels (no host synchronisation); the partial sums land in pinned host
 // memory (P->h_part) for taps_residual_finish.  Returns the number of partials.
-int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind) {
+int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current) {
   int M = U->M;
   if (M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
   if (kind == TAPS_RES_ALS) {
     // FP64 Grams of every dim at the current factors, then each dim's residual.
-    TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
+    if (!grams_current) TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
     size_t off = 0;
     for (int d = 0; d < P->D; ++d) {
       const taps_dim* dm = P->dims[d];
@@ -882,11 +883,12 @@ int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, doubl
   return TAPS_OK;
 }
 
-int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
+int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out,
+                       int grams_current) {
   int M = U->M;
   if (M < 1) return TAPS_ERR_INVALID_ARG;
   TAPS_TRY(taps_ws_ensure(P, M));
-  TAPS_TRY(taps_residual_enqueue(P, U, kind));
+  TAPS_TRY(taps_residual_enqueue(P, U, kind, grams_current));
   TAPS_CUDA(cudaStreamSynchronize(P->stream));
   return taps_residual_finish(P, U, kind, rho_out);
 }

@@ -115,6 +115,7 @@ struct taps_problem {
   int ops[TAPS_MAX_DIMS][TAPS_NUM_OPS];  // op kind of each distinct-op slot
   int nf_max;
   double* d_q[TAPS_MAX_DIMS];            // [Rf][nf_d] source projections
+  double* d_pq[TAPS_MAX_DIMS];           // [Rf][nf_d] Phi_d^T q_r (fast diagonalisation)
   double* d_beta;                        // [Rf] source amplitudes
   double* d_opband[TAPS_MAX_DIMS];       // [nops_d][nf_d][nb] bands of the distinct ops
   // Workspace, grown to the largest mode count seen (ws_M).
@@ -252,10 +253,13 @@ int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision);
 int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision);
 int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
                     double* change_out);
-int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
+int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out,
+                       int grams_current = 0);
 int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize);
 int taps_sweep_finish(taps_problem* P, taps_factors* U, double* change_out);
-int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind);
+// grams_current: the FP64 Grams and source projections of every dim already belong to
+// U (true right after an FP64 or MIXED sweep), so the ALS residual does not refresh them.
+int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current = 0);
 int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
 int taps_fd_prepare_all(taps_problem* P, int solver);
 int taps_lu_needs_tuning(const taps_problem* P, int solver, int M);
