@@ -243,6 +243,11 @@ static void free_ws(taps_problem* P) {
   }
   cudaFree(P->d_C);
   cudaFree(P->d_c);
+  cudaFree(P->d_Call);
+  cudaFree(P->d_call);
+  cudaFree(P->d_ticket);
+  P->d_Call = P->d_call = nullptr;
+  P->d_ticket = nullptr;
   cudaFree(P->d_F);
   cudaFree(P->d_blocks);
   cudaFree(P->d_lu);
@@ -305,13 +310,17 @@ int taps_ws_ensure(taps_problem* P, int M) {
     bigG += NC * NC;
   }
   size_t als_part = 0;
-  for (int d = 0; d < D; ++d) als_part += 2 * (((size_t)P->dims[d]->nf * M + 255) / 256);
+  for (int d = 0; d < D; ++d) als_part += 2 * (((size_t)P->dims[d]->nf + 7) / 8);   // 8 rows per CTA
   part = std::max(part, als_part);
   part = std::max(part, (size_t)3 * 64);
   size_t MM = (size_t)M * M;
   int nfm = P->nf_max;
   TAPS_TRY(taps_alloc((void**)&P->d_C, sizeof(double) * TAPS_NUM_OPS * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_c, sizeof(double) * P->Rf * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_Call, sizeof(double) * D * TAPS_NUM_OPS * MM));
+  TAPS_TRY(taps_alloc((void**)&P->d_call, sizeof(double) * D * P->Rf * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_ticket, sizeof(unsigned) * 64));   // >= M / 8 + 1
+  TAPS_CUDA(cudaMemsetAsync(P->d_ticket, 0, sizeof(unsigned) * 64, P->stream));
   TAPS_TRY(taps_alloc((void**)&P->d_F, sizeof(double) * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_blocks, sizeof(double) * nfm * nbmax * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_lu, sizeof(double) * MM));

@@ -40,7 +40,6 @@ __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double*
                                                               int hb, int hasA, double* Phi, double* PhiT,
                                                               double* mu, int* status) {
   __shared__ double red[32];
-  __shared__ double sh[8];
   __shared__ int shi[8];
   extern __shared__ double rot[];  // [2][n]: QL rotations (c, s) of one sweep
   const int tid = threadIdx.x, nt = blockDim.x;

@@ -11,9 +11,51 @@
 #include "taps_internal.cuh"
 
 // ---------------------------------------------------------------------------------
+// Coefficients of dim d: C_o = sum_{t: op(t,d) = o} alpha_t prod_{e != d} Gamma_{op(t,e),e}
+// and c_r = beta_r prod_{e != d} h_{r,e} (Eq. 35), entry idx of the M x M matrices.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void coeff_entry(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
+                                            double* C, double* c) {
+  const int MM = M * M;
+  if (idx < MM) {
+    double acc[TAPS_NUM_OPS];
+    for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
+    for (int t = 0; t < tt.R; ++t) {
+      double prod = tt.alpha[t];
+      for (int e = 0; e < tt.D; ++e)
+        if (e != d) prod *= __ldcg(gp.gram[e] + (size_t)tt.oi[t][e] * MM + idx);
+      acc[tt.oi[t][d]] += prod;
+    }
+    for (int o = 0; o < tt.nops[d]; ++o) C[(size_t)o * MM + idx] = acc[o];
+  }
+  if (idx < M) {
+    for (int r = 0; r < tt.Rf; ++r) {
+      double v = tt.beta[r];
+      for (int e = 0; e < tt.D; ++e)
+        if (e != d) v *= __ldcg(gp.h[e] + (size_t)r * M + idx);
+      c[(size_t)r * M + idx] = v;
+    }
+  }
+}
+
+__global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
+  coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x, C, c);
+}
+
+// Coefficients of every dim at once (blockIdx.y = dim), into [D][TAPS_NUM_OPS][M][M]
+// and [D][Rf][M].
+__global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call, double* call) {
+  const int d = blockIdx.y;
+  coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x,
+              Call + (size_t)d * TAPS_NUM_OPS * M * M, call + (size_t)d * tt.Rf * M);
+}
+
+// ---------------------------------------------------------------------------------
 // Gram refresh of one dimension: Gamma_o = U^T Op_o U for each distinct op o and
-// h_r = U^T q_r.  CTA (chunk, mtile) handles GR rows and MT rows of Gamma; partial
-// sums are reduced in a fixed order by gram_reduce_kernel.
+// h_r = U^T q_r (Eq. 34).  CTA (chunk, mtile) handles GR rows and MT rows of Gamma and
+// writes its partial sums; the last CTA to finish (a ticket counter, no waiting)
+// sums the partials in a fixed chunk order and, when asked, forms the coefficients
+// of the next dimension from the fresh Grams, so one launch does all three steps.
 // ---------------------------------------------------------------------------------
 #define GR 8
 #define GMT 8
@@ -22,8 +64,11 @@ template <typename T>
 __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M, int hb,
                                     const double* __restrict__ opband, int nops,
                                     const double* __restrict__ q, int Rf,
-                                    double* __restrict__ partial, int stride) {
+                                    double* __restrict__ partial, int stride, unsigned* ticket,
+                                    double* gram, double* h, TermTable tt, GramPtrs gp, int cd,
+                                    double* C, double* c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int is_last;
   const int nb = 2 * hb + 1;
   const int rows_h = GR + 2 * hb;
   T* Us = reinterpret_cast<T*>(smem_raw);  // [rows_h][M]
@@ -68,20 +113,56 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
     }
     out[(size_t)nops * M * M + (size_t)r * M + m] = (double)acc;
   }
+  // ---- per mode tile, the last chunk CTA reduces the tile's slice of the partials;
+  // the last tile to finish forms the coefficients of dim cd.  Tickets: [0, gridDim.y)
+  // per tile, gridDim.y for the tiles.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket + blockIdx.y, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int nchunk = gridDim.x;
+  const int ng = nops * M * M;
+  const int nslice = nops * mt * M + Rf * mt;   // this tile's rows of every Gamma_o, then of h
+  for (int e = threadIdx.x; e < nslice; e += blockDim.x) {
+    int j;
+    if (e < nops * mt * M) {
+      const int o = e / (mt * M), rem = e % (mt * M);
+      j = (o * M + m0 + rem / M) * M + rem % M;
+    } else {
+      const int rem = e - nops * mt * M;
+      j = ng + (rem / mt) * M + m0 + rem % mt;
+    }
+    double acc = 0.0;
+#pragma unroll 8
+    for (int ch = 0; ch < nchunk; ++ch) acc += __ldcg(partial + (size_t)ch * stride + j);
+    if (j < ng) gram[j] = acc;
+    else h[j - ng] = acc;
+  }
+  if (threadIdx.x == 0) ticket[blockIdx.y] = 0u;   // ready for the next launch on this stream
+  if (cd < 0) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket + gridDim.y, 1u) == gridDim.y - 1) ? 1 : 0;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) coeff_entry(tt, gp, cd, M, idx, C, c);
+  if (threadIdx.x == 0) ticket[gridDim.y] = 0u;
 }
 
-__global__ void gram_reduce_kernel(const double* __restrict__ partial, int nchunk, int stride,
-                                   int nops, int M, int Rf, double* gram, double* h) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int ng = nops * M * M;
-  if (j >= ng + Rf * M) return;
-  double acc = 0.0;
-  for (int c = 0; c < nchunk; ++c) acc += partial[(size_t)c * stride + j];
-  if (j < ng) gram[j] = acc;
-  else h[j - ng] = acc;
+static GramPtrs gram_ptrs(const taps_problem* P) {
+  GramPtrs gp;
+  memset(&gp, 0, sizeof(gp));
+  for (int d = 0; d < P->D; ++d) {
+    gp.gram[d] = P->d_gram[d];
+    gp.h[d] = P->d_h[d];
+  }
+  return gp;
 }
 
-int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision) {
+int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision, int coeff_dim) {
   const taps_dim* dm = P->dims[d];
   int M = U->M, nf = dm->nf, hb = dm->hb, nops = P->tt.nops[d], Rf = P->Rf;
   if (M == 0) return TAPS_OK;
@@ -90,57 +171,32 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
   dim3 grid(nchunk, (M + GMT - 1) / GMT);
   size_t elems = (size_t)(GR + 2 * hb) * M + (size_t)GR * M;
   const int nb = 2 * hb + 1;
-  const double gflops = nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
-  const double gbytes = 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf +
-                               (double)nops * M * M + (double)Rf * M);
+  double gflops = nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
+  double gbytes = 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf +
+                         (double)nops * M * M + (double)Rf * M);
+  if (coeff_dim >= 0) {
+    gflops += (double)P->R * M * M * P->D + (double)P->Rf * M * P->D;
+    gbytes += 8.0 * ((double)P->R * M * M * P->D);
+  }
+  GramPtrs gp = gram_ptrs(P);
   int tk = prof_begin(P, TAPS_PROF_GRAM);
   if (precision == TAPS_FP32) {   // TAPS_MIXED keeps FP64 Grams
     gram_partial_kernel<float><<<grid, 256, elems * sizeof(float), P->stream>>>(
-        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride);
+        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
+        P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c);
   } else {
     gram_partial_kernel<double><<<grid, 256, elems * sizeof(double), P->stream>>>(
-        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride);
+        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
+        P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c);
   }
-  TAPS_CUDA(cudaGetLastError());
-  gram_reduce_kernel<<<(stride + 255) / 256, 256, 0, P->stream>>>(P->d_partial, nchunk, stride, nops,
-                                                                  M, Rf, P->d_gram[d], P->d_h[d]);
   prof_end(P, TAPS_PROF_GRAM, tk, gflops, gbytes);
-  P->prof->launches[TAPS_PROF_GRAM] += 1;  // the reduce kernel is a second launch
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }
 
 int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision) {
-  for (int d = 0; d < P->D; ++d) TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision));
+  for (int d = 0; d < P->D; ++d) TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, -1));
   return TAPS_OK;
-}
-
-// ---------------------------------------------------------------------------------
-// Coefficients of dim d: C_o = sum_{t: op(t,d) = o} alpha_t prod_{e != d} Gamma_{op(t,e),e}
-// and c_r = beta_r prod_{e != d} h_{r,e}.
-// ---------------------------------------------------------------------------------
-__global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int MM = M * M;
-  if (idx < MM) {
-    double acc[TAPS_NUM_OPS];
-    for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
-    for (int t = 0; t < tt.R; ++t) {
-      double prod = tt.alpha[t];
-      for (int e = 0; e < tt.D; ++e)
-        if (e != d) prod *= gp.gram[e][(size_t)tt.oi[t][e] * MM + idx];
-      acc[tt.oi[t][d]] += prod;
-    }
-    for (int o = 0; o < tt.nops[d]; ++o) C[(size_t)o * MM + idx] = acc[o];
-  }
-  if (idx < M) {
-    for (int r = 0; r < tt.Rf; ++r) {
-      double v = tt.beta[r];
-      for (int e = 0; e < tt.D; ++e)
-        if (e != d) v *= gp.h[e][(size_t)r * M + idx];
-      c[(size_t)r * M + idx] = v;
-    }
-  }
 }
 
 // Block band of the reduced matrix (node-major, I = (i, m)):
@@ -548,32 +604,32 @@ static int reduced_solve_block_lu(taps_problem* P, taps_factors* U, int d) {
   return TAPS_OK;
 }
 
+static int residual_setup(int maxsm);
+
+// Largest dynamic shared memory a launch of `fn` may ask for: the opt-in limit less
+// the kernel's static shared memory.
+int taps_allow_dyn_smem(const void* fn, int maxsm) {
+  cudaFuncAttributes fa;
+  TAPS_CUDA(cudaFuncGetAttributes(&fa, fn));
+  TAPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 maxsm - (int)fa.sharedSizeBytes));
+  return TAPS_OK;
+}
+
 // Shared-memory opt-in of the kernels whose footprint grows with M, and the number
 // of CTAs a cooperative block-LU launch may use (co-residency at the largest M).
 int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
   int maxsm = 0;
   TAPS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  TAPS_CUDA(cudaFuncSetAttribute((const void*)block_lu_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-  TAPS_CUDA(cudaFuncSetAttribute((const void*)gram_partial_kernel<double>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-  TAPS_CUDA(cudaFuncSetAttribute((const void*)gram_partial_kernel<float>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)block_lu_kernel, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<double>, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float>, maxsm));
+  TAPS_TRY(residual_setup(maxsm));
   int bps = 0;
   size_t smem_max = sizeof(double) * TAPS_MAX_M * (TAPS_MAX_M + 1);
   TAPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, block_lu_kernel, 256, smem_max));
   *coop_blocks = std::max(bps, 1) * num_sms;
   return TAPS_OK;
-}
-
-static GramPtrs gram_ptrs(const taps_problem* P) {
-  GramPtrs gp;
-  memset(&gp, 0, sizeof(gp));
-  for (int d = 0; d < P->D; ++d) {
-    gp.gram[d] = P->d_gram[d];
-    gp.h[d] = P->d_h[d];
-  }
-  return gp;
 }
 
 static int coefficients(taps_problem* P, int d, int M) {
@@ -594,7 +650,8 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
   cudaStream_t s = P->stream;
   for (int d = 0; d < P->D; ++d) {
     const taps_dim* dm = P->dims[d];
-    TAPS_TRY(coefficients(P, d, M));
+    // the coefficients of the later dims come with the previous dim's Gram refresh
+    if (d == 0) TAPS_TRY(coefficients(P, 0, M));
     int sa, sb;
     if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb)) {
       TAPS_TRY(taps_fd_solve(P, U, d, precision));   // keeps the old factor in d_Uold
@@ -609,7 +666,7 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
                                               P->d_scal + (size_t)d * 2 * M, P->d_status);
     prof_end(P, TAPS_PROF_NORMALIZE, tk, 7.0 * dm->nf * M, 8.0 * 3.0 * dm->nf * M);
     TAPS_CUDA(cudaGetLastError());
-    TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision));
+    TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, d + 1 < P->D ? d + 1 : -1));
   }
   TAPS_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, sizeof(double) * 2 * M * P->D,
                             cudaMemcpyDeviceToHost, s));
@@ -707,6 +764,91 @@ __global__ void als_residual_kernel(const double* __restrict__ Y, int nops, int 
   }
 }
 
+// Residual of every dim's reduced system at the current factors (Eq. 42):
+// r_d[i][m] = sum_o (Op_o U_d)[i][:] . C_{d,o}[m][:] - sum_r q_{d,r}[i] c_{d,r}[m].
+// One launch for all dims: CTA b belongs to the dim whose range [cta0[d], cta0[d+1])
+// holds b and covers RR rows of it.  The CTA stages the factor rows with their band
+// halo and Y_o = Op_o U on those rows in shared memory, then writes its partial sums
+// of ||r||^2 and ||F||^2 (summed per dim in a fixed order on the host).
+#define RR 8
+struct ResDims {
+  const double* U[TAPS_MAX_DIMS];
+  const double* band[TAPS_MAX_DIMS];   // [nops][nf][nb]
+  const double* q[TAPS_MAX_DIMS];      // [Rf][nf]
+  int nf[TAPS_MAX_DIMS], hb[TAPS_MAX_DIMS], nops[TAPS_MAX_DIMS];
+  int cta0[TAPS_MAX_DIMS + 1];
+  int D;
+};
+
+__global__ void __launch_bounds__(256) als_residual_all_kernel(ResDims rd, int M, int Rf,
+                                                               const double* __restrict__ Call,
+                                                               const double* __restrict__ call,
+                                                               double* __restrict__ partial) {
+  extern __shared__ __align__(16) double rsm[];
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  int d = 0;
+  while (d + 1 < rd.D && b >= rd.cta0[d + 1]) ++d;
+  const int r0 = (b - rd.cta0[d]) * RR;
+  const int nf = rd.nf[d], hb = rd.hb[d], nops = rd.nops[d], nb = 2 * hb + 1;
+  const int rows_h = RR + 2 * hb;
+  double* Us = rsm;                 // [rows_h][M]
+  double* Ys = Us + rows_h * M;     // [nops][RR][M]
+  const double* U = rd.U[d];
+  for (int idx = threadIdx.x; idx < rows_h * M; idx += blockDim.x) {
+    const int m = idx / rows_h, rr = idx % rows_h;
+    const int gi = r0 - hb + rr;
+    Us[rr * M + m] = (gi >= 0 && gi < nf) ? U[(size_t)m * nf + gi] : 0.0;
+  }
+  __syncthreads();
+  for (int o = 0; o < nops; ++o) {
+    const double* band = rd.band[d] + (size_t)o * nf * nb;
+    for (int idx = threadIdx.x; idx < RR * M; idx += blockDim.x) {
+      const int i = idx / M, n = idx % M;
+      const int gi = r0 + i;
+      double acc = 0.0;
+      if (gi < nf) {
+        const double* brow = band + (size_t)gi * nb;
+        for (int k = 0; k < nb; ++k) acc += brow[k] * Us[(i + k) * M + n];
+      }
+      Ys[(o * RR + i) * M + n] = acc;
+    }
+  }
+  __syncthreads();
+  const double* C = Call + (size_t)d * TAPS_NUM_OPS * M * M;
+  const double* c = call + (size_t)d * Rf * M;
+  const double* q = rd.q[d];
+  double r2 = 0.0, f2 = 0.0;
+  for (int idx = threadIdx.x; idx < RR * M; idx += blockDim.x) {
+    const int i = idx / M, m = idx % M;
+    const int gi = r0 + i;
+    if (gi < nf) {
+      double f = 0.0;
+      for (int r = 0; r < Rf; ++r) f += q[(size_t)r * nf + gi] * c[(size_t)r * M + m];
+      double a = 0.0;
+      for (int o = 0; o < nops; ++o) {
+        const double* y = Ys + (o * RR + i) * M;
+        const double* cc = C + ((size_t)o * M + m) * M;
+        for (int n = 0; n < M; ++n) a += y[n] * cc[n];
+      }
+      const double rr = a - f;
+      r2 += rr * rr;
+      f2 += f * f;
+    }
+  }
+  r2 = block_sum(r2, red);
+  f2 = block_sum(f2, red);
+  if (threadIdx.x == 0) {
+    partial[2 * b] = r2;
+    partial[2 * b + 1] = f2;
+  }
+}
+
+static int residual_setup(int maxsm) {
+  TAPS_TRY(taps_allow_dyn_smem((const void*)als_residual_all_kernel, maxsm));
+  return TAPS_OK;
+}
+
 // Per-dim Gram of the columns [Y_0 | Y_1 | ... | q_0 .. q_{Rf-1}] (NC = nops*M + Rf).
 __global__ void big_gram_kernel(const double* __restrict__ Y, int nops, int nf, int M,
                                 const double* __restrict__ q, int Rf, double* __restrict__ G) {
@@ -783,28 +925,40 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
   if (M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
   if (kind == TAPS_RES_ALS) {
-    // FP64 Grams of every dim at the current factors, then each dim's residual.
+    // FP64 Grams of every dim at the current factors, the coefficients of every dim,
+    // then every dim's residual in one launch.
     if (!grams_current) TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
-    size_t off = 0;
+    int tk = prof_begin(P, TAPS_PROF_COEFF);
+    coeff_all_kernel<<<dim3((M * M + 127) / 128, P->D), 128, 0, s>>>(P->tt, gram_ptrs(P), M, P->d_Call,
+                                                                   P->d_call);
+    prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D * P->D,
+             8.0 * ((double)P->R * M * M * P->D * P->D));
+    TAPS_CUDA(cudaGetLastError());
+    ResDims rd;
+    memset(&rd, 0, sizeof(rd));
+    rd.D = P->D;
+    double fl = 0.0, by = 0.0;
+    int rows_max = 0;
     for (int d = 0; d < P->D; ++d) {
       const taps_dim* dm = P->dims[d];
-      int nops = P->tt.nops[d];
-      TAPS_TRY(coefficients(P, d, M));
-      long long ny = (long long)nops * dm->nf * M;
-      int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
-      spmm_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(U->d_U[d], dm->nf, M, dm->hb,
-                                                               P->d_opband[d], nops, P->d_Y);
-      TAPS_CUDA(cudaGetLastError());
-      long long nr = (long long)dm->nf * M;
-      int nblocks = (int)((nr + 255) / 256);
-      als_residual_kernel<<<nblocks, 256, 0, s>>>(P->d_Y, nops, dm->nf, M, P->d_C, P->d_q[d],
-                                                  P->d_c, P->Rf, P->d_partial + off);
-      prof_end(P, TAPS_PROF_RESIDUAL, tk, 2.0 * ny * dm->nb + 2.0 * nops * (double)nr * M + 2.0 * P->Rf * nr,
-               8.0 * (2.0 * ny + (double)nr * (nops + 1)));
-      P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
-      TAPS_CUDA(cudaGetLastError());
-      off += 2 * (size_t)nblocks;
+      rd.U[d] = U->d_U[d];
+      rd.band[d] = P->d_opband[d];
+      rd.q[d] = P->d_q[d];
+      rd.nf[d] = dm->nf;
+      rd.hb[d] = dm->hb;
+      rd.nops[d] = P->tt.nops[d];
+      rd.cta0[d + 1] = rd.cta0[d] + (dm->nf + RR - 1) / RR;
+      rows_max = std::max(rows_max, RR + 2 * dm->hb + P->tt.nops[d] * RR);
+      const double ny = (double)rd.nops[d] * dm->nf * M, nr = (double)dm->nf * M;
+      fl += 2.0 * ny * dm->nb + 2.0 * rd.nops[d] * nr * M + 2.0 * P->Rf * nr;
+      by += 8.0 * (nr + (double)rd.nops[d] * dm->nf * dm->nb + (double)P->Rf * dm->nf);
     }
+    tk = prof_begin(P, TAPS_PROF_RESIDUAL);
+    als_residual_all_kernel<<<rd.cta0[P->D], 256, sizeof(double) * (size_t)rows_max * M, s>>>(
+        rd, M, P->Rf, P->d_Call, P->d_call, P->d_partial);
+    prof_end(P, TAPS_PROF_RESIDUAL, tk, fl, by);
+    TAPS_CUDA(cudaGetLastError());
+    size_t off = 2 * (size_t)rd.cta0[P->D];
     TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, off * sizeof(double), cudaMemcpyDeviceToHost, s));
     TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     return TAPS_OK;
@@ -842,7 +996,7 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
 }
 
 int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
-  int M = U->M;
+  (void)U;
   if (*P->h_status != TAPS_DEV_OK) {
     int dev = *P->h_status;
     *P->h_status = TAPS_DEV_OK;
@@ -855,8 +1009,7 @@ int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, doubl
     double worst = 0.0;
     size_t off = 0;
     for (int d = 0; d < P->D; ++d) {
-      long long nr = (long long)P->dims[d]->nf * M;
-      int nblocks = (int)((nr + 255) / 256);
+      int nblocks = (P->dims[d]->nf + RR - 1) / RR;
       double r2 = 0.0, f2 = 0.0;
       for (int b = 0; b < nblocks; ++b) {
         r2 += P->h_part[off + 2 * b];

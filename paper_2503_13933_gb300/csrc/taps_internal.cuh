@@ -124,6 +124,9 @@ struct taps_problem {
   double* d_h[TAPS_MAX_DIMS];     // [Rf][M]
   double* d_C;        // [TAPS_NUM_OPS][M][M] coefficient matrices of the current dim
   double* d_c;        // [Rf][M]
+  double* d_Call;     // [D][TAPS_NUM_OPS][M][M] coefficients of every dim (residual)
+  double* d_call;     // [D][Rf][M]
+  unsigned* d_ticket; // CTA tickets of the kernels whose last CTA finishes a reduction
   double* d_F;        // [nf_max][M] reduced right-hand side (node-major)
   double* d_blocks;   // [nf_max][nb][M][M] block band of the reduced matrix
   double* d_lu;       // [M][M] LU of the current diagonal block
@@ -250,7 +253,10 @@ __host__ __device__ __forceinline__ double taps_uniform_pm1(unsigned seed, int d
 // ---------------------------------------------------------------------------------
 int taps_ws_ensure(taps_problem* P, int M);
 int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision);
-int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision);
+// Gram refresh of dim d; with coeff_dim >= 0 the same launch then forms the
+// coefficients of dim coeff_dim in P->d_C / P->d_c.
+int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision,
+                          int coeff_dim);
 int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
                     double* change_out);
 int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out,
