@@ -14,28 +14,49 @@
 // Coefficients of dim d: C_o = sum_{t: op(t,d) = o} alpha_t prod_{e != d} Gamma_{op(t,e),e}
 // and c_r = beta_r prod_{e != d} h_{r,e} (Eq. 35), entry idx of the M x M matrices.
 // ---------------------------------------------------------------------------------
+// The loads of one product are issued together (unrolled over TAPS_MAX_DIMS with a
+// factor 1 for the skipped dims, an exact no-op) so that their latencies overlap.
+__device__ __forceinline__ void coeff_C(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
+                                        double* C) {
+  const int MM = M * M;
+  double acc[TAPS_NUM_OPS];
+#pragma unroll
+  for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
+  for (int t = 0; t < tt.R; ++t) {
+    double f[TAPS_MAX_DIMS];
+#pragma unroll
+    for (int e = 0; e < TAPS_MAX_DIMS; ++e)
+      f[e] = (e < tt.D && e != d) ? __ldcg(gp.gram[e] + (size_t)tt.oi[t][e] * MM + idx) : 1.0;
+    double prod = tt.alpha[t];
+#pragma unroll
+    for (int e = 0; e < TAPS_MAX_DIMS; ++e) prod *= f[e];
+    const int od = tt.oi[t][d];
+#pragma unroll
+    for (int o = 0; o < TAPS_NUM_OPS; ++o)
+      if (o == od) acc[o] += prod;
+  }
+#pragma unroll
+  for (int o = 0; o < TAPS_NUM_OPS; ++o)
+    if (o < tt.nops[d]) C[(size_t)o * MM + idx] = acc[o];
+}
+
+__device__ __forceinline__ void coeff_c(const TermTable& tt, const GramPtrs& gp, int d, int M, int r, int m,
+                                        double* c) {
+  double f[TAPS_MAX_DIMS];
+#pragma unroll
+  for (int e = 0; e < TAPS_MAX_DIMS; ++e)
+    f[e] = (e < tt.D && e != d) ? __ldcg(gp.h[e] + (size_t)r * M + m) : 1.0;
+  double v = tt.beta[r];
+#pragma unroll
+  for (int e = 0; e < TAPS_MAX_DIMS; ++e) v *= f[e];
+  c[(size_t)r * M + m] = v;
+}
+
 __device__ __forceinline__ void coeff_entry(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
                                             double* C, double* c) {
-  const int MM = M * M;
-  if (idx < MM) {
-    double acc[TAPS_NUM_OPS];
-    for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
-    for (int t = 0; t < tt.R; ++t) {
-      double prod = tt.alpha[t];
-      for (int e = 0; e < tt.D; ++e)
-        if (e != d) prod *= __ldcg(gp.gram[e] + (size_t)tt.oi[t][e] * MM + idx);
-      acc[tt.oi[t][d]] += prod;
-    }
-    for (int o = 0; o < tt.nops[d]; ++o) C[(size_t)o * MM + idx] = acc[o];
-  }
-  if (idx < M) {
-    for (int r = 0; r < tt.Rf; ++r) {
-      double v = tt.beta[r];
-      for (int e = 0; e < tt.D; ++e)
-        if (e != d) v *= __ldcg(gp.h[e] + (size_t)r * M + idx);
-      c[(size_t)r * M + idx] = v;
-    }
-  }
+  if (idx < M * M) coeff_C(tt, gp, d, M, idx, C);
+  if (idx < M)
+    for (int r = 0; r < tt.Rf; ++r) coeff_c(tt, gp, d, M, r, idx, c);
 }
 
 __global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
@@ -53,9 +74,10 @@ __global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call,
 // ---------------------------------------------------------------------------------
 // Gram refresh of one dimension: Gamma_o = U^T Op_o U for each distinct op o and
 // h_r = U^T q_r (Eq. 34).  CTA (chunk, mtile) handles GR rows and MT rows of Gamma and
-// writes its partial sums; the last CTA to finish (a ticket counter, no waiting)
-// sums the partials in a fixed chunk order and, when asked, forms the coefficients
-// of the next dimension from the fresh Grams, so one launch does all three steps.
+// writes its partial sums; per mode tile the last CTA to finish (a ticket counter, no
+// waiting) sums the tile's partials in a fixed chunk order and, when asked, forms
+// the tile's rows of the next dimension's coefficients from the fresh Grams, so one
+// launch does all three steps.
 // ---------------------------------------------------------------------------------
 #define GR 8
 #define GMT 8
@@ -113,9 +135,9 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
     }
     out[(size_t)nops * M * M + (size_t)r * M + m] = (double)acc;
   }
-  // ---- per mode tile, the last chunk CTA reduces the tile's slice of the partials;
-  // the last tile to finish forms the coefficients of dim cd.  Tickets: [0, gridDim.y)
-  // per tile, gridDim.y for the tiles.
+  // ---- per mode tile, the last chunk CTA reduces the tile's slice of the partials
+  // and forms the tile's rows of the coefficients of dim cd.  Ticket y counts the
+  // CTAs of tile y.
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(ticket + blockIdx.y, 1u) == gridDim.x - 1) ? 1 : 0;
@@ -142,14 +164,12 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
   }
   if (threadIdx.x == 0) ticket[blockIdx.y] = 0u;   // ready for the next launch on this stream
   if (cd < 0) return;
+  // entry (m, n) of the coefficients needs entry (m, n) of each dim's Gram only, so
+  // this CTA forms the rows m of its tile
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(ticket + gridDim.y, 1u) == gridDim.y - 1) ? 1 : 0;
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) coeff_entry(tt, gp, cd, M, idx, C, c);
-  if (threadIdx.x == 0) ticket[gridDim.y] = 0u;
+  for (int e = threadIdx.x; e < mt * M; e += blockDim.x) coeff_C(tt, gp, cd, M, m0 * M + e, C);
+  for (int e = threadIdx.x; e < Rf * mt; e += blockDim.x) coeff_c(tt, gp, cd, M, e / mt, m0 + e % mt, c);
 }
 
 static GramPtrs gram_ptrs(const taps_problem* P) {
@@ -732,36 +752,6 @@ __global__ void spmm_kernel(const double* __restrict__ U, int nf, int M, int hb,
     if (j >= 0 && j < nf) acc += brow[k] * U[(size_t)m * nf + j];
   }
   Y[idx] = acc;
-}
-
-// Residual of dim d's reduced system: r[i][m] = sum_o sum_n Y_o[i][n] C_o[m][n] - F[i][m].
-// Per-block partial sums of ||r||^2 and ||F||^2.
-__global__ void als_residual_kernel(const double* __restrict__ Y, int nops, int nf, int M,
-                                    const double* __restrict__ C, const double* __restrict__ q,
-                                    const double* __restrict__ c, int Rf, double* partial) {
-  __shared__ double red[32];
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0, f2 = 0.0;
-  if (idx < (long long)nf * M) {
-    int i = idx / M, m = idx % M;
-    double f = 0.0;
-    for (int r = 0; r < Rf; ++r) f += q[(size_t)r * nf + i] * c[(size_t)r * M + m];
-    double a = 0.0;
-    for (int o = 0; o < nops; ++o) {
-      const double* y = Y + ((size_t)o * nf + i) * M;
-      const double* cc = C + ((size_t)o * M + m) * M;
-      for (int n = 0; n < M; ++n) a += y[n] * cc[n];
-    }
-    double rr = a - f;
-    r2 = rr * rr;
-    f2 = f * f;
-  }
-  r2 = block_sum(r2, red);
-  f2 = block_sum(f2, red);
-  if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = r2;
-    partial[2 * blockIdx.x + 1] = f2;
-  }
 }
 
 // Residual of every dim's reduced system at the current factors (Eq. 42):
