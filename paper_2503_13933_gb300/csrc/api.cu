@@ -677,11 +677,6 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
 // factor rows and B = those of the trailing dims.  A and B are built by
 // eval_factor_kernel; eval_gemm_kernel streams the output with register tiles.
 // ---------------------------------------------------------------------------------
-struct GridSpec {
-  int D;
-  int count[TAPS_MAX_DIMS];
-  long long goff[TAPS_MAX_DIMS];  // offsets of the gathered rows G_d [count_d][M]
-};
 
 template <typename T>
 __global__ void gather_rows_kernel(const double* U, int nf, int off, int start, int step, int count,
@@ -857,7 +852,9 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
   while (split > 1 && cols < 128) cols *= count[--split];
   if (cols > (1ll << 30)) return TAPS_ERR_INVALID_ARG;
   long long rows = total / cols;
-  size_t need = esz * (goff + (size_t)(rows + cols) * M);
+  const bool use_tc = out_dtype == TAPS_FP32 && taps_eval_tc_usable(rows, cols, M);
+  const size_t gbytes = (esz * (size_t)goff + 255) / 256 * 256;
+  size_t need = use_tc ? gbytes + taps_eval_tc_scratch(rows, cols, M) : esz * (goff + (size_t)(rows + cols) * M);
   if (need > P->evalbuf_len) {
     TAPS_CUDA(cudaStreamSynchronize(s));
     cudaFree(P->d_evalbuf);
@@ -875,6 +872,7 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     TAPS_CUDA(cudaFuncSetAttribute((const void*)eval_gemm_f32_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    TAPS_TRY(taps_eval_tc_setup(maxsm));
     P->eval_attr_set = 1;
   }
   int tk = prof_begin(P, TAPS_PROF_EVAL);
@@ -890,7 +888,10 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
                                                                 step[d], count[d], M,
                                                                 (float*)G + gs.goff[d]);
   }
-  if (out_dtype == TAPS_FP64) {
+  if (use_tc) {
+    st = taps_eval_tc(P, (const float*)G, gs, split, M, rows, cols, (char*)G + gbytes, (float*)out_dev);
+    if (st != TAPS_OK) return st;
+  } else if (out_dtype == TAPS_FP64) {
     double* A = (double*)G + goff;
     double* B = A + rows * M;
     eval_factor_kernel<double><<<(unsigned)((rows * M + 255) / 256), 256, 0, s>>>((const double*)G, gs, 0, split, M, rows, A);
@@ -905,7 +906,7 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
     dim3 eg((unsigned)((rows + EB - 1) / EB), (unsigned)((cols + EB - 1) / EB));
     eval_gemm_f32_kernel<<<eg, 256, (size_t)M * 2 * EBP * sizeof(float), s>>>(A, B, rows, (int)cols, M, (float*)out_dev);
   }
-  P->prof->launches[TAPS_PROF_EVAL] += P->D + 2;  // gathers, two factor products, product
+  P->prof->launches[TAPS_PROF_EVAL] += P->D + 2;  // gathers, two factor products / images, product
   prof_end(P, TAPS_PROF_EVAL, tk, 2.0 * M * (double)total + (double)(rows + cols) * M * (P->D - 1),
            (double)esz * total);
   cudaError_t e = cudaGetLastError();

@@ -253,6 +253,24 @@ __host__ __device__ __forceinline__ double taps_uniform_pm1(unsigned seed, int d
 // ---------------------------------------------------------------------------------
 int taps_ws_ensure(taps_problem* P, int M);
 int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision);
+// Largest dynamic shared memory a launch of `fn` may ask for (opt-in limit less the
+// kernel's static shared memory).
+int taps_allow_dyn_smem(const void* fn, int maxsm);
+
+// Grid of a reconstruction: per dim the number of nodes and the offset of its
+// gathered factor rows [count][M].
+struct GridSpec {
+  int D;
+  int count[TAPS_MAX_DIMS];
+  long long goff[TAPS_MAX_DIMS];
+};
+// Tensor-core reconstruction of an FP32 grid (rank-M product of the leading dims'
+// and the trailing dims' row products).
+int taps_eval_tc_usable(long long rows, long long cols, int M);
+size_t taps_eval_tc_scratch(long long rows, long long cols, int M);
+int taps_eval_tc_setup(int maxsm);
+int taps_eval_tc(taps_problem* P, const float* G, const GridSpec& gs, int split, int M, long long rows,
+                 long long cols, void* scratch, float* out);
 // Gram refresh of dim d; with coeff_dim >= 0 the same launch then forms the
 // coefficients of dim coeff_dim in P->d_C / P->d_c.
 int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision,

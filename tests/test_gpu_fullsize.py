@@ -1,0 +1,125 @@
+"""GPU parity at the benchmark's full size (space-parameter Poisson, 256^3 nodes x 32
+conductivity nodes, M = 30, the fast-diagonalisation FP64 path with CUDA graphs, FP32
+reconstruction on the tensor cores), and element-wise parity of the tensor-core
+reconstruction on ragged tiles.
+
+At full size the oracle cannot form the 5e8-point field, so it checks what it can
+compute exactly: one subspace sweep from the same factors (every reduced system of
+every dim), the Eq. 42 residual of the GPU's factors, and sampled grid points of the
+reconstruction, each summed in FP64 from the GPU's own factors."""
+import numpy as np
+import pytest
+
+from oracle import taps_oracle as O
+from paper_2503_13933_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_13933_gb300 import build, taps
+    build.build()
+    taps.lib()
+    return taps
+
+
+@pytest.fixture(scope="module")
+def full(T):
+    """The benchmark workload solved as the benchmark solves it."""
+    desc = W.poisson_k(256, 32, seed=2000)
+    P = T.Problem(desc)
+    U = P.factors(30)
+    rep = P.solve(U, M0=30, M_max=30, res_tol=1e-6, res_kind=T.RES_ALS, max_sweeps=60,
+                  precision=T.FP64, init=T.INIT_RANDOM, seed=2000, als_tol=0.0,
+                  solver=T.SOLVER_FASTDIAG)
+    return desc, P, U, rep
+
+
+def test_full_size_solve_reaches_target_and_residual_matches_oracle(T, full):
+    desc, P, U, rep = full
+    assert rep["converged"] and rep["rho"] <= 1e-6
+    Po = O.problem_from_description(desc)
+    rho_oracle = O.als_residual(Po, U.get())
+    # the GPU's Eq. 42 residual of its own factors, recomputed by the oracle
+    assert abs(P.residual(U, T.RES_ALS) - rho_oracle) <= 1e-3 * rho_oracle
+
+
+def test_full_size_sweep_matches_oracle(T, full):
+    """One fast-diagonalisation sweep on the GPU and in the oracle from the same
+    converged factors: same normalised factors."""
+    desc, P, U, _ = full
+    Po = O.problem_from_description(desc)
+    U0 = U.get()
+    V = P.factors(30)
+    V.set(U0)
+    P.sweep(V, 1, solver=T.SOLVER_FASTDIAG)
+    Uo, _ = O.sweep(Po, [u.copy() for u in U0], solver="fastdiag")
+    Ub, _ = O.sweep(Po, [u.copy() for u in U0], solver="banded")
+    got = V.get()
+    for d in range(Po.D):
+        # converged M = 30 modes make the reduced systems ill-conditioned; the spread
+        # between the oracle's two FP64 solvers (fast diagonalisation, banded LU)
+        # measures kappa * eps of this case and sets the bound
+        spread = np.linalg.norm(Ub[d] - Uo[d]) / np.linalg.norm(Uo[d])
+        err = np.linalg.norm(got[d] - Uo[d]) / np.linalg.norm(Uo[d])
+        assert err < max(1e-10, 10 * spread), (d, err, spread)
+
+
+def test_full_size_reconstruction_sampled(T, full):
+    """The 256^3 x 32 FP32 grid (tensor-core path) at 4096 seeded sample points
+    against FP64 sums of the GPU's factors."""
+    desc, P, U, _ = full
+    count = [desc["dims"][d]["n"] for d in range(4)]
+    field = torch.empty(int(np.prod(count)), dtype=torch.float32, device="cuda")
+    P.eval_grid(U, [0, 0, 0, 0], count, [1, 1, 1, 1], field, dtype=T.FP32)
+    torch.cuda.synchronize()
+    Po = O.problem_from_description(desc)
+    rows = [O.to_all_nodes(Po.dims[d], u) for d, u in enumerate(U.get())]
+    rng = np.random.default_rng(7)
+    idx = np.stack([rng.integers(0, c, 4096) for c in count], axis=1)
+    terms = np.ones((4096, rows[0].shape[1]))
+    for d in range(4):
+        terms *= rows[d][idx[:, d]]
+    ref = terms.sum(axis=1)
+    flat = np.ravel_multi_index(idx.T, count)
+    got = field[torch.as_tensor(flat, device="cuda")].double().cpu().numpy()
+    # converged CP terms cancel: the bound is FP32's worst-case accumulation error of
+    # M = 30 terms, M * 2^-24 ~ 1.8e-6, times sum_m |term_m|
+    bound = 2e-6 * np.abs(terms).sum(axis=1)
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+    assert np.isfinite(field.sum().item())
+
+
+@pytest.mark.parametrize("M", [5, 30, 32])
+def test_tensor_core_reconstruction_ragged_tiles(T, M):
+    """Grid 24^3 x 10 split as 576 rows x 240 columns: 4.5 row tiles of 128 and one
+    partial column tile of 256; M = 5 (one K step, mostly padding), 30 (ragged K), 32
+    (full K).  Element-wise against the oracle's FP64 grid."""
+    desc = W.poisson_k(24, 10, seed=2003)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=40 + M)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    count = [24, 24, 24, 10]
+    ref = O.eval_grid(Po, U0, [list(range(c)) for c in count])
+    out = torch.empty(int(np.prod(count)), dtype=torch.float32, device="cuda")
+    P.eval_grid(Ug, [0, 0, 0, 0], count, [1, 1, 1, 1], out, dtype=T.FP32)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy().reshape(count)
+    # per element: FP32's worst-case accumulation error of M terms (M * 2^-24 <= 2e-6)
+    # times sum_m |a_m b_m|
+    bound = np.zeros(count)
+    rows = [O.to_all_nodes(Po.dims[d], u) for d, u in enumerate(U0)]
+    for m in range(M):
+        t = np.abs(rows[0][:, m])
+        for d in range(1, 4):
+            t = np.multiply.outer(t, np.abs(rows[d][:, m]))
+        bound += t
+    assert np.all(np.abs(got - ref) <= 2e-6 * bound + 1e-30)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-6
