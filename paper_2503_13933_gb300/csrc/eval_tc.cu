@@ -14,13 +14,15 @@
 // as hi*hi + hi*lo + lo*hi (the lo*lo term is below 2^-22 relative).  This keeps the
 // FP32 reconstruction within a few 1e-7 of the FP32-operand product.
 //
-// Roles in one persistent CTA per SM (192 threads):
+// Roles in one persistent CTA per SM (320 threads):
 //   warp 0       : bulk-copy producer (one elected lane) and TMEM allocation
 //   warp 1       : MMA issuer (one elected lane)
-//   warps 2 - 5  : epilogue; warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
-// Two shared-memory stages (operands of one tile each) and two TMEM accumulators
-// (256 columns each, 512 in all) let the copies, the MMAs of the next tile and the
-// output stream of the previous tile overlap.  Every wait on an mbarrier is bounded;
+//   warps 2 - 9  : epilogue; warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 and
+//                  the column half (w - 2) / 4 of the tile
+// Two TMEM accumulators (256 columns each, 512 in all) let the operand copy and the
+// MMAs of the next tile run while the previous tile streams out; the copy and the
+// MMAs are short next to a tile's 128 KB output, so one operand stage suffices and
+// the shared memory goes to the epilogue's staging blocks.  Every wait on an mbarrier is bounded;
 // a wait that runs out sets TAPS_DEV_TIMEOUT, the other roles see the abort flag, the
 // MMA issuer waits (bounded) for its outstanding MMAs, and TMEM is freed on exit.
 #include <stdint.h>
@@ -35,9 +37,10 @@
 #define TC_MAXK 32                   // largest padded K handled here (M <= 32)
 #define TC_A_KBLK (TC_BM * TC_KSTEP) // floats of one A K-step block (4 KB)
 #define TC_B_KBLK (TC_BN * TC_KSTEP) // floats of one B K-step block (8 KB)
-#define TC_STAGES 2
-#define TC_ACC 2
-#define TC_THREADS 192
+#define TC_STAGES 1                  // operand stages (the output stream dominates)
+#define TC_ACC 2                     // TMEM accumulators
+#define TC_EPI_WARPS 8               // two per TMEM lane quarter, one per column half
+#define TC_THREADS (64 + 32 * TC_EPI_WARPS)
 #define TC_SPIN (1u << 24)
 
 // ---------------------------------------------------------------------------------
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
     }
     for (int b = 0; b < TC_ACC; ++b) {
       tc_mbar_init(&acc_full[b], 1);
-      tc_mbar_init(&acc_empty[b], 4);
+      tc_mbar_init(&acc_empty[b], TC_EPI_WARPS);
     }
     tc_mbar_init(&drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -297,9 +300,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
       volatile int never = 0;
       if (!tc_mbar_wait(&drain_bar, 0u, (volatile int*)&never)) taps_flag(status, TAPS_DEV_TIMEOUT);
     }
-  } else {   // ---- epilogue: warps 2..5
-    const int q = warp & 3;   // TMEM lane quarter of this warp
-    const int row_in_tile = 32 * q + lane;
+  } else {   // ---- epilogue: warps 2..9
+    const int q = warp & 3;             // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;   // column half of the tile
+    // 32 x 32 block of this warp, row stride 36 floats: the row-wise float4 writes and
+    // the column-wise float4 reads of 8 lanes at a time fall in distinct banks
+    float* tb = reinterpret_cast<float*>(base + (size_t)TC_STAGES * stage_bytes) + (warp - 2) * (32 * 36);
+    const int rr = lane >> 3, c4 = (lane & 7) * 4;   // store pattern: 4 rows x 8 float4
     long long i = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = (int)(i % TC_ACC);
@@ -311,26 +318,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
       }
       tc_fence_after();
       const long long rb = t % nrb, cb = t / nrb;
-      const long long row = rb * TC_BM + row_in_tile;
-      const int c0 = (int)(cb * TC_BN);
-      float* orow = out + row * (long long)C;
-      const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * TC_BN);
+      const long long row0 = rb * TC_BM + 32 * q;
+      const int c0 = (int)(cb * TC_BN) + half * (TC_BN / 2);
+      const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * TC_BN + half * (TC_BN / 2));
 #pragma unroll 1
-      for (int ch = 0; ch < TC_BN / 32; ++ch) {
+      for (int ch = 0; ch < TC_BN / 64; ++ch) {
         float v[32];
-        tc_ld32(tbase + (uint32_t)(32 * ch), v);
-        const int cc = c0 + 32 * ch;
-        if (row < R && cc < C) {
-          if (vec_ok && cc + 32 <= C) {
+        tc_ld32(tbase + (uint32_t)(32 * ch), v);   // lane = row, 32 consecutive columns
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              __stcs(reinterpret_cast<float4*>(orow + cc + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
-          } else {
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4*>(tb + lane * 36 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        __syncwarp();
+        const int cc = c0 + 32 * ch + c4;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (cc + j < C) __stcs(orow + cc + j, v[j]);
+        for (int k = 0; k < 8; ++k) {   // rows rr, rr + 4, ..., each by 8 lanes x 16 bytes
+          const int r = rr + 4 * k;
+          const long long row = row0 + r;
+          const float4 w = *reinterpret_cast<const float4*>(tb + r * 36 + c4);
+          if (row < R) {
+            float* o = out + row * (long long)C + cc;
+            if (vec_ok && cc + 4 <= C) {
+              __stcs(reinterpret_cast<float4*>(o), w);
+            } else {
+              if (cc < C) __stcs(o, w.x);
+              if (cc + 1 < C) __stcs(o + 1, w.y);
+              if (cc + 2 < C) __stcs(o + 2, w.z);
+              if (cc + 3 < C) __stcs(o + 3, w.w);
+            }
           }
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -373,7 +390,7 @@ int taps_eval_tc(taps_problem* P, const float* G, const GridSpec& gs, int split,
   tc_image_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(G, gs, split, gs.D, M, ksteps, cols, TC_BN,
                                                               Bimg);
   const size_t stage = (size_t)2 * ksteps * (TC_A_KBLK + TC_B_KBLK) * sizeof(float);
-  const size_t smem = TC_STAGES * stage + 1024;
+  const size_t smem = TC_STAGES * stage + TC_EPI_WARPS * 32 * 36 * sizeof(float) + 1024;
   const long long ntiles = nrb * ncb;
   const int grid = (int)std::min<long long>(ntiles, P->num_sms);
   const int vec_ok = ((cols & 3) == 0 && (((uintptr_t)out) & 15) == 0) ? 1 : 0;
