@@ -240,10 +240,10 @@ def run_ours(args, rank, world, local):
     paths = {k: v for k, v in paths.items() if k in args.paths.split(",")}
     res = {}
     for name, prec in paths.items():
+        P.profile_reset(events=False)   # timed steps: no timing-event nodes in the graphs
         for _ in range(args.warmup):
             flush.zero_()
             step(prec)
-        P.profile_reset(events=True)
         times, evals, reps = [], [], []
         sampler = ClockSampler(local) if name == list(paths)[-1] else None
         if sampler:
@@ -257,6 +257,15 @@ def run_ours(args, rank, world, local):
             evals.append(ev_ms)
             reps.append(rep)
         clocks = sampler.stop() if sampler else None
+        # per-kernel-class breakdown: the same steps again with CUDA events around every
+        # class of launches (on the library's stream), after one untimed step that
+        # captures the graphs with their event nodes
+        flush.zero_()
+        step(prec)
+        P.profile_reset(events=True)
+        for _ in range(args.steps):
+            flush.zero_()
+            step(prec)
         prof = P.profile()
         res[name] = dict(solve_ms=float(np.mean(times)), eval_ms=float(np.mean(evals)),
                          sweeps=reps[-1]["sweeps"], fp64_sweeps=reps[-1]["fp64_sweeps"],

@@ -20,7 +20,9 @@ int prof_begin(taps_problem* P, int cls) {
   ProfState* S = P->prof;
   if (!S) return -1;
   S->launches[cls] += 1;
-  if (!S->events && !S->capturing) return -1;
+  // without timing events a captured graph gets no event-record nodes between its
+  // kernels (they would add a dependency hop per class)
+  if (!S->events) return -1;
   if (S->capturing && (S->npool < 2 || S->npending >= 512)) return -1;  // no allocation / sync while capturing
   if (S->npending >= 512) {
     cudaStreamSynchronize(P->stream);
@@ -81,6 +83,7 @@ void prof_drain(taps_problem* P) {
 struct SweepGraph {
   const taps_factors* U;
   int M, precision, solver, res_kind, ws_M;
+  bool events;                   // captured with timing-event nodes
   bool failed;
   cudaGraph_t g;
   cudaGraphExec_t exec;
@@ -113,6 +116,7 @@ static int graph_build(taps_problem* P, taps_factors* U, int prec, int solver, i
   G->solver = solver;
   G->res_kind = res_kind;
   G->ws_M = P->ws_M;
+  G->events = P->prof->events;
   P->graph = G;
   ProfState* S = P->prof;
   TAPS_CUDA(cudaStreamSynchronize(P->stream));
@@ -167,7 +171,7 @@ static int graph_sweep(taps_problem* P, taps_factors* U, int prec, int solver, i
   *fallback = 0;
   SweepGraph* G = (SweepGraph*)P->graph;
   bool match = G && G->U == U && G->M == U->M && G->precision == prec && G->solver == solver &&
-               G->res_kind == res_kind && G->ws_M == P->ws_M;
+               G->res_kind == res_kind && G->ws_M == P->ws_M && G->events == P->prof->events;
   if (match && G->failed) {
     *fallback = 1;
     return TAPS_ERR_CUDA;

@@ -291,8 +291,10 @@ __global__ void fd_pq_kernel(const double* __restrict__ PhiT, const double* __re
 // Out[i][m] = sum_j Mat[i][j] In[j][m] (Mat n x n row-major, In n x M row-major).
 // One CTA per output row i.  Its RG_WARPS warps (one per SM sub-partition) split the
 // sum over j; within a warp the lanes split it again, each lane keeping 32 mode
-// accumulators.  The partials are combined through shared memory.  FP64 on this GPU
-// is issue-bound per sub-partition, so spreading one row over all four pipes matters.
+// accumulators.  A butterfly reduce-scatter then leaves lane l of each warp with the
+// warp's sum for mode l (31 additions per lane instead of a chain of 32), and the
+// warps' sums are combined through shared memory.  FP64 on this GPU is issue-bound
+// per sub-partition, so spreading one row over all four pipes matters.
 // Out is n x M row-major, or (colmajor) the factor layout Out[m * n + i]; in the
 // factor layout a non-null Save receives the row's previous values first.
 #define RG_WARPS 4
@@ -301,9 +303,10 @@ __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double*
                                                                    int M, double* __restrict__ Out,
                                                                    int colmajor,
                                                                    double* __restrict__ Save) {
-  __shared__ double part[RG_WARPS * 32][33];
+  __shared__ double part[RG_WARPS][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x;
+  taps_pdl_wait_then_release();
   if (colmajor && Save)   // the writes below come after a barrier
     for (int m = threadIdx.x; m < M; m += blockDim.x) Save[(size_t)m * n + i] = Out[(size_t)m * n + i];
   const double* row = Mat + (size_t)i * n;
@@ -320,12 +323,23 @@ __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double*
       for (int c = 0; c < 32; ++c)
         if (c < mc) acc[c] += a * in[c];
     }
+    // reduce-scatter: at offset o a lane keeps the half of its current modes selected
+    // by lane bit o and receives its partner's values of that half
 #pragma unroll
-    for (int c = 0; c < 32; ++c) part[threadIdx.x][c] = acc[c];
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int c = 0; c < o; ++c) {
+        const double send = up ? acc[c] : acc[c + o];
+        const double keep = up ? acc[c + o] : acc[c];
+        acc[c] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    part[warp][lane] = acc[0];   // the warp's sum for mode m0 + lane
     __syncthreads();
     if (threadIdx.x < mc) {
-      double sum = 0.0;
-      for (int l = 0; l < step; ++l) sum += part[l][threadIdx.x];
+      const double sum = (part[0][threadIdx.x] + part[1][threadIdx.x]) +
+                         (part[2][threadIdx.x] + part[3][threadIdx.x]);
       if (colmajor) Out[(size_t)(m0 + threadIdx.x) * n + i] = sum;
       else Out[(size_t)i * M + m0 + threadIdx.x] = sum;
     }
@@ -479,6 +493,7 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x;
   if (i >= n) return;
+  taps_pdl_wait_then_release();
   const double mi = (CA && mu) ? mu[i] : 0.0;
   double v[8];
 #pragma unroll
@@ -728,8 +743,9 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
   const double* CB = P->d_C + (size_t)slotB * MM;
   int launches = 2;
   if (M <= 32 && precision != TAPS_MIXED) {
-    fd_small_solve_quad_kernel<<<n, 128, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, P->d_pq[d],
-                                                 P->d_c, P->Rf, n, M, Y, P->d_status);
+    TAPS_CUDA(taps_launch_pdl(fd_small_solve_quad_kernel, dim3(n), dim3(128), 0, s, CA, CB,
+                              slotA >= 0 ? (const double*)E->mu : nullptr, (const double*)P->d_pq[d],
+                              (const double*)P->d_c, P->Rf, n, M, Y, P->d_status));
   } else {
     fd_rhs_kernel<<<(nM + 255) / 256, 256, 0, s>>>(P->d_pq[d], P->d_c, P->Rf, n, M, G);
     if (M <= 32)
@@ -741,7 +757,8 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
     ++launches;
   }
   // back to the nodal basis; the previous factor goes to d_Uold for the change norm
-  fd_rowgemm_kernel<<<n, RG_WARPS * 32, 0, s>>>(E->Phi, Y, n, M, U->d_U[d], 1, P->d_Uold);
+  TAPS_CUDA(taps_launch_pdl(fd_rowgemm_kernel, dim3(n), dim3(RG_WARPS * 32), 0, s, (const double*)E->Phi,
+                            (const double*)Y, n, M, U->d_U[d], 1, P->d_Uold));
   P->prof->launches[TAPS_PROF_FASTDIAG] += launches - 1;
   prof_end(P, TAPS_PROF_FASTDIAG, tk,
            2.0 * P->Rf * nM + 2.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),

@@ -60,12 +60,14 @@ __device__ __forceinline__ void coeff_entry(const TermTable& tt, const GramPtrs&
 }
 
 __global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
+  taps_pdl_wait_then_release();
   coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x, C, c);
 }
 
 // Coefficients of every dim at once (blockIdx.y = dim), into [D][TAPS_NUM_OPS][M][M]
 // and [D][Rf][M].
 __global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call, double* call) {
+  taps_pdl_wait_then_release();
   const int d = blockIdx.y;
   coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x,
               Call + (size_t)d * TAPS_NUM_OPS * M * M, call + (size_t)d * tt.Rf * M);
@@ -98,6 +100,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
   const int r0 = blockIdx.x * GR;
   const int m0 = blockIdx.y * GMT;
   const int mt = min(GMT, M - m0);
+  taps_pdl_wait_then_release();
   for (int idx = threadIdx.x; idx < rows_h * M; idx += blockDim.x) {
     int m = idx / rows_h, rr = idx % rows_h;
     int gi = r0 - hb + rr;
@@ -201,13 +204,15 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
   GramPtrs gp = gram_ptrs(P);
   int tk = prof_begin(P, TAPS_PROF_GRAM);
   if (precision == TAPS_FP32) {   // TAPS_MIXED keeps FP64 Grams
-    gram_partial_kernel<float><<<grid, 256, elems * sizeof(float), P->stream>>>(
-        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
-        P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c);
+    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float>, grid, dim3(256), elems * sizeof(float), P->stream,
+                              (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
+                              (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
+                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
   } else {
-    gram_partial_kernel<double><<<grid, 256, elems * sizeof(double), P->stream>>>(
-        U->d_U[d], nf, M, hb, P->d_opband[d], nops, P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
-        P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c);
+    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<double>, grid, dim3(256), elems * sizeof(double),
+                              P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d],
+                              nops, (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
+                              P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
   }
   prof_end(P, TAPS_PROF_GRAM, tk, gflops, gbytes);
   TAPS_CUDA(cudaGetLastError());
@@ -436,6 +441,7 @@ __global__ void __launch_bounds__(256) block_backsub_kernel(const double* __rest
 // ---------------------------------------------------------------------------------
 __global__ void normalize_change_kernel(double* U, const double* Uold, int nf, int M, int normalize,
                                         double* out, int* status) {
+  taps_pdl_wait_then_release();
   __shared__ double red[32];
   __shared__ double redv[32];
   __shared__ int redi[32];
@@ -654,7 +660,8 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
 
 static int coefficients(taps_problem* P, int d, int M) {
   int tk = prof_begin(P, TAPS_PROF_COEFF);
-  coeff_kernel<<<(M * M + 127) / 128, 128, 0, P->stream>>>(P->tt, gram_ptrs(P), d, M, P->d_C, P->d_c);
+  TAPS_CUDA(taps_launch_pdl(coeff_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+                            gram_ptrs(P), d, M, P->d_C, P->d_c));
   prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D + (double)P->Rf * M * P->D,
            8.0 * ((double)P->R * M * M * P->D));
   TAPS_CUDA(cudaGetLastError());
@@ -682,8 +689,9 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
     }
     int norm_d = (normalize && d < P->D - 1) ? 1 : 0;
     int tk = prof_begin(P, TAPS_PROF_NORMALIZE);
-    normalize_change_kernel<<<M, 256, 0, s>>>(U->d_U[d], P->d_Uold, dm->nf, M, norm_d,
-                                              P->d_scal + (size_t)d * 2 * M, P->d_status);
+    TAPS_CUDA(taps_launch_pdl(normalize_change_kernel, dim3(M), dim3(256), 0, s, U->d_U[d],
+                              (const double*)P->d_Uold, dm->nf, M, norm_d, P->d_scal + (size_t)d * 2 * M,
+                              P->d_status));
     prof_end(P, TAPS_PROF_NORMALIZE, tk, 7.0 * dm->nf * M, 8.0 * 3.0 * dm->nf * M);
     TAPS_CUDA(cudaGetLastError());
     TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, d + 1 < P->D ? d + 1 : -1));
@@ -777,6 +785,7 @@ __global__ void __launch_bounds__(256) als_residual_all_kernel(ResDims rd, int M
   extern __shared__ __align__(16) double rsm[];
   __shared__ double red[32];
   const int b = blockIdx.x;
+  taps_pdl_wait_then_release();
   int d = 0;
   while (d + 1 < rd.D && b >= rd.cta0[d + 1]) ++d;
   const int r0 = (b - rd.cta0[d]) * RR;
@@ -919,8 +928,8 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     // then every dim's residual in one launch.
     if (!grams_current) TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
     int tk = prof_begin(P, TAPS_PROF_COEFF);
-    coeff_all_kernel<<<dim3((M * M + 127) / 128, P->D), 128, 0, s>>>(P->tt, gram_ptrs(P), M, P->d_Call,
-                                                                   P->d_call);
+    TAPS_CUDA(taps_launch_pdl(coeff_all_kernel, dim3((M * M + 127) / 128, P->D), dim3(128), 0, s, P->tt,
+                              gram_ptrs(P), M, P->d_Call, P->d_call));
     prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D * P->D,
              8.0 * ((double)P->R * M * M * P->D * P->D));
     TAPS_CUDA(cudaGetLastError());
@@ -944,8 +953,9 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
       by += 8.0 * (nr + (double)rd.nops[d] * dm->nf * dm->nb + (double)P->Rf * dm->nf);
     }
     tk = prof_begin(P, TAPS_PROF_RESIDUAL);
-    als_residual_all_kernel<<<rd.cta0[P->D], 256, sizeof(double) * (size_t)rows_max * M, s>>>(
-        rd, M, P->Rf, P->d_Call, P->d_call, P->d_partial);
+    TAPS_CUDA(taps_launch_pdl(als_residual_all_kernel, dim3(rd.cta0[P->D]), dim3(256),
+                              sizeof(double) * (size_t)rows_max * M, s, rd, M, P->Rf,
+                              (const double*)P->d_Call, (const double*)P->d_call, P->d_partial));
     prof_end(P, TAPS_PROF_RESIDUAL, tk, fl, by);
     TAPS_CUDA(cudaGetLastError());
     size_t off = 2 * (size_t)rd.cta0[P->D];
