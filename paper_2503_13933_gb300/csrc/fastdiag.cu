@@ -472,13 +472,15 @@ __global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* _
 // of one system is spread over the four sub-partitions: warp w holds the columns
 // c = w, w+4, w+8, ... of T = mu_i C_A + C_B (lane r = row r) and warp 0 also the
 // right-hand side g_i = sum_r PQ[r][i] c_r, formed here from the transformed source
-// vectors (the warps split the sum over r).  At step p every warp updates its columns c > p with the
-// multipliers l_r = T[r][p] / T[p][p] of that step, which the owner of column p has
-// published in shared memory (one reciprocal of the pivot, kept for the back
-// substitution).  The owner of column p+1 updates that column first and publishes
-// the next multipliers before its other columns, so the chain of pivots is not held
-// up by the bulk of the updates.  No pivoting, as in the one-warp solve.  The upper
-// factor then goes to shared memory and warp 0 back-substitutes.
+// vectors (the warps split the sum over r).  At step p every warp updates its
+// columns c > p with the multipliers l_r = T[r][p] / T[p][p] of that step, which the
+// owner of column p has published in shared memory (one reciprocal of the pivot,
+// kept for the back substitution).  The owner of column p+1 updates only that column
+// at step p and publishes the next multipliers; its other updates of step p run at
+// step p+1, when another warp carries the chain of pivots, so that chain is held up
+// by neither the bulk of the updates nor the barrier waiting for them.  No pivoting,
+// as in the one-warp solve.  The upper factor then goes to shared memory and warp 0
+// back-substitutes.
 __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* __restrict__ CA,
                                                                   const double* __restrict__ CB,
                                                                   const double* __restrict__ mu,
@@ -518,12 +520,22 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
   }
   __syncthreads();
   double b = (w == 0) ? (gpart[0][lane] + gpart[1][lane]) + (gpart[2][lane] + gpart[3][lane]) : 0.0;
+  double lprev = 0.0;   // multipliers of the step whose other updates this warp deferred
 #pragma unroll
   for (int p = 0; p < 32; ++p) {
     if (p < M) {
       const double l = lbuf[p & 1][lane];
       const int q = p + 1;   // next pivot column, owned by warp q & 3 in slot q >> 2
-      if (q < 32 && q < M && w == (q & 3)) {
+      // (1) the owner of column p published the multipliers of step p before its
+      // other updates of step p - 1; it applies them now (rows p - 1 of its columns
+      // are final, so the pivot-row values are the same as then)
+      if (p >= 1 && w == (p & 3)) {
+#pragma unroll
+        for (int k = (p >> 2) + 1; k < 8; ++k) v[k] -= lprev * __shfl_sync(0xffffffffu, v[k], p - 1);
+      }
+      if (q < M && w == (q & 3)) {
+        // (2) the owner of column q: that column first, then the next multipliers;
+        // its other updates of this step wait for the next step
         const double pc = __shfl_sync(0xffffffffu, v[q >> 2], p);
         v[q >> 2] -= l * pc;
         const double piv = __shfl_sync(0xffffffffu, v[q >> 2], q);
@@ -532,14 +544,15 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
         const double inv = badq ? 0.0 : 1.0 / piv;
         lbuf[q & 1][lane] = (lane > q && lane < M) ? v[q >> 2] * inv : 0.0;
         if (lane == 0) invd[q] = inv;
-      }
+        lprev = l;
+      } else {
+        // (3) every other warp: its columns c > p
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (4 * k + 3 <= p) continue;              // every column of this slot is <= p
-        if (q < 32 && k == (q >> 2) && w == (q & 3)) continue;   // column q, done above
-        if (4 * k <= p && w <= p - 4 * k) continue;   // column 4k + w <= p
-        const double pc = __shfl_sync(0xffffffffu, v[k], p);
-        v[k] -= l * pc;
+        for (int k = 0; k < 8; ++k) {
+          if (4 * k + 3 <= p) continue;                 // every column of this slot is <= p
+          if (4 * k <= p && w <= p - 4 * k) continue;   // column 4k + w <= p
+          v[k] -= l * __shfl_sync(0xffffffffu, v[k], p);
+        }
       }
       if (w == 0) b -= l * __shfl_sync(0xffffffffu, b, p);
       __syncthreads();

@@ -849,19 +849,36 @@ static int residual_setup(int maxsm) {
 }
 
 // Per-dim Gram of the columns [Y_0 | Y_1 | ... | q_0 .. q_{Rf-1}] (NC = nops*M + Rf).
-__global__ void big_gram_kernel(const double* __restrict__ Y, int nops, int nf, int M,
-                                const double* __restrict__ q, int Rf, double* __restrict__ G) {
-  int NC = nops * M + Rf;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)NC * NC) return;
-  int a = idx / NC, b = idx % NC;
-  double acc = 0.0;
-  for (int i = 0; i < nf; ++i) {
-    double va = (a < nops * M) ? Y[((size_t)(a / M) * nf + i) * M + (a % M)] : q[(size_t)(a - nops * M) * nf + i];
-    double vb = (b < nops * M) ? Y[((size_t)(b / M) * nf + i) * M + (b % M)] : q[(size_t)(b - nops * M) * nf + i];
-    acc += va * vb;
+// CTA a forms row a: its threads split the columns b (BG_COLS at a time) and the
+// rows i (BG_SPLIT ways, so that each thread's chain of products is short and its
+// loads overlap); the row splits are summed in a fixed order through shared memory.
+#define BG_COLS 64
+#define BG_SPLIT 4
+__device__ __forceinline__ double big_gram_col(const double* Y, const double* q, int nops, int nf, int M,
+                                               int a, int i) {
+  return (a < nops * M) ? Y[((size_t)(a / M) * nf + i) * M + (a % M)] : q[(size_t)(a - nops * M) * nf + i];
+}
+
+__global__ void __launch_bounds__(BG_COLS * BG_SPLIT) big_gram_kernel(const double* __restrict__ Y, int nops,
+                                                                       int nf, int M,
+                                                                       const double* __restrict__ q, int Rf,
+                                                                       double* __restrict__ G) {
+  __shared__ double part[BG_SPLIT][BG_COLS];
+  const int NC = nops * M + Rf;
+  const int a = blockIdx.x;
+  const int col = threadIdx.x % BG_COLS, sp = threadIdx.x / BG_COLS;
+  const int i0 = (int)((long long)nf * sp / BG_SPLIT), i1 = (int)((long long)nf * (sp + 1) / BG_SPLIT);
+  for (int b0 = 0; b0 < NC; b0 += BG_COLS) {
+    const int b = b0 + col;
+    double acc = 0.0;
+    if (b < NC)
+      for (int i = i0; i < i1; ++i)
+        acc += big_gram_col(Y, q, nops, nf, M, a, i) * big_gram_col(Y, q, nops, nf, M, b, i);
+    part[sp][col] = acc;
+    __syncthreads();
+    if (sp == 0 && b < NC) G[(size_t)a * NC + b] = (part[0][col] + part[1][col]) + (part[2][col] + part[3][col]);
+    __syncthreads();
   }
-  G[idx] = acc;
 }
 
 struct BigGramPtrs {
@@ -978,8 +995,8 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     TAPS_CUDA(cudaGetLastError());
     P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
     prof_end(P, TAPS_PROF_RESIDUAL, tk, 2.0 * ny * dm->nb + 2.0 * (double)NC * NC * dm->nf, 8.0 * 2.0 * ny);
-    big_gram_kernel<<<(unsigned)(((long long)NC * NC + 127) / 128), 128, 0, s>>>(
-        P->d_Y, nops, dm->nf, M, P->d_q[d], P->Rf, P->d_bigG + goff);
+    big_gram_kernel<<<NC, BG_COLS * BG_SPLIT, 0, s>>>(P->d_Y, nops, dm->nf, M, P->d_q[d], P->Rf,
+                                                      P->d_bigG + goff);
     TAPS_CUDA(cudaGetLastError());
     bg.G[d] = P->d_bigG + goff;
     bg.NC[d] = NC;
