@@ -362,6 +362,15 @@ int taps_profile_reset(taps_problem* prob, int enable_events);
 int taps_profile_get(taps_problem* prob, int kernel_class, long long* launches, double* ms,
                      double* flops, double* bytes);
 
+/* ---- the FP64 reciprocal of the small reduced solves (no counterpart in the method;
+ * exposed so that its accuracy can be checked against IEEE division) ---------------
+ * y[i] = 1 / x[i] for n device doubles, from the hardware's approximate reciprocal
+ * refined by one step of the series 1/x = y0 (1 + e + e^2), e = 1 - x y0; within one
+ * unit in the last place of 1.0 / x for normal x whose reciprocal is normal.  x_dev and
+ * y_dev are device pointers (they may alias); stream is a cudaStream_t or NULL.
+ * Asynchronous; TAPS_ERR_INVALID_ARG for n < 0 or null pointers with n > 0. */
+int taps_util_rcp(const double* x_dev, double* y_dev, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

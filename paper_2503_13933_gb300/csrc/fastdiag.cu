@@ -514,10 +514,12 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
   if (w == 0) {
     const double piv = __shfl_sync(0xffffffffu, v[0], 0);
     bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
-    const double inv = bad ? 0.0 : 1.0 / piv;
+    const double inv = taps_rcp(piv);
     lbuf[0][lane] = (lane > 0 && lane < M) ? v[0] * inv : 0.0;
     if (lane == 0) invd[0] = inv;
   }
+  // row 0 of column 1, for the owner of the next pivot
+  double pc_next = (w == 1) ? __shfl_sync(0xffffffffu, v[0], 0) : 0.0;
   __syncthreads();
   double b = (w == 0) ? (gpart[0][lane] + gpart[1][lane]) + (gpart[2][lane] + gpart[3][lane]) : 0.0;
   double lprev = 0.0;   // multipliers of the step whose other updates this warp deferred
@@ -534,16 +536,15 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
         for (int k = (p >> 2) + 1; k < 8; ++k) v[k] -= lprev * __shfl_sync(0xffffffffu, v[k], p - 1);
       }
       if (q < M && w == (q & 3)) {
-        // (2) the owner of column q: that column first, then the next multipliers;
-        // its other updates of this step wait for the next step
-        const double pc = __shfl_sync(0xffffffffu, v[q >> 2], p);
-        v[q >> 2] -= l * pc;
+        // (2) the owner of column q: that column first (its row p was shuffled at
+        // the end of the previous step), then the next multipliers; its other
+        // updates of this step wait for the next step
+        v[q >> 2] -= l * pc_next;
         const double piv = __shfl_sync(0xffffffffu, v[q >> 2], q);
-        const bool badq = !(fabs(piv) > 0.0) || !isfinite(piv);
-        bad |= badq;
-        const double inv = badq ? 0.0 : 1.0 / piv;
+        const double inv = taps_rcp(piv);
         lbuf[q & 1][lane] = (lane > q && lane < M) ? v[q >> 2] * inv : 0.0;
         if (lane == 0) invd[q] = inv;
+        bad |= !(fabs(piv) > 0.0) || !isfinite(piv);   // off the chain of pivots
         lprev = l;
       } else {
         // (3) every other warp: its columns c > p
@@ -555,6 +556,8 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
         }
       }
       if (w == 0) b -= l * __shfl_sync(0xffffffffu, b, p);
+      // row q of column q + 1 is final now: the next owner fetches it before the barrier
+      if (q + 1 < M && w == ((q + 1) & 3)) pc_next = __shfl_sync(0xffffffffu, v[(q + 1) >> 2], q);
       __syncthreads();
     }
   }
@@ -809,4 +812,21 @@ void taps_fd_release(taps_dim* dm) {
     cudaFree(dm->fd[k].mu);
   }
   dm->nfd = 0;
+}
+
+// ---------------------------------------------------------------------------------
+// The small solves' reciprocal on a device array (for checking it against IEEE
+// division).
+// ---------------------------------------------------------------------------------
+__global__ void rcp_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = taps_rcp(x[i]);
+}
+
+extern "C" int taps_util_rcp(const double* x_dev, double* y_dev, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x_dev || !y_dev))) return TAPS_ERR_INVALID_ARG;
+  if (n == 0) return TAPS_OK;
+  rcp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x_dev, y_dev, n);
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
 }

@@ -209,6 +209,18 @@ inline cudaError_t taps_launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// FP64 reciprocal: the hardware's approximate reciprocal y0 refined by one step of
+// the series 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...), e = 1 - x y0 (the quadratic
+// Newton-Raphson / series refinement of a reciprocal seed).  One approximate op and
+// three dependent FMAs: within one ulp of 1.0 / x for normal x (the seed flushes
+// subnormals), at about 60% of the IEEE division's dependent latency.
+__device__ __forceinline__ double taps_rcp(double x) {
+  double y0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+
 // Block-wide sum for blockDim.x <= 1024; `red` holds >= 32 T in shared memory.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {

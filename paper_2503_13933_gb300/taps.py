@@ -120,6 +120,7 @@ SIGNATURES = {
     "taps_mlp_destroy": (None, [_vp]),
     "taps_factors_from_profiles": (_i, [_vp, _vp, _i, _vp, _i, _d]),
     "taps_profile_get": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong), _pd, _pd, _pd]),
+    "taps_util_rcp": (_i, [_vp, _vp, ctypes.c_longlong, _vp]),
 }
 
 PROF_CLASSES = ["gram", "coeff", "block_assemble", "block_lu", "backsub", "normalize",
@@ -162,6 +163,12 @@ def current_stream():
     if torch.cuda.is_available():
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     return ctypes.c_void_p(0)
+
+
+def rcp(x, y):
+    """y = 1 / x with the small solves' reciprocal (x, y: CUDA float64 tensors)."""
+    check(lib().taps_util_rcp(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                              x.numel(), current_stream()), "taps_util_rcp")
 
 
 def dim_desc(dm):
