@@ -356,8 +356,9 @@ int taps_factors_from_profiles(const taps_problem* prob, taps_factors* U, int M,
 #define TAPS_PROF_RESIDUAL 6      /* residual kernels                               */
 #define TAPS_PROF_EVAL 7          /* grid reconstruction                            */
 #define TAPS_PROF_OTHER 8         /* initialisation, pencil set-up, copies           */
-#define TAPS_PROF_FASTDIAG 9      /* fast-diagonalisation reduced solve              */
-#define TAPS_PROF_NUM 10
+#define TAPS_PROF_FASTDIAG 9      /* fast diagonalisation: the n small M x M solves  */
+#define TAPS_PROF_FD_TRANSFORM 10 /* fast diagonalisation: back to the nodal basis   */
+#define TAPS_PROF_NUM 11
 int taps_profile_reset(taps_problem* prob, int enable_events);
 int taps_profile_get(taps_problem* prob, int kernel_class, long long* launches, double* ms,
                      double* flops, double* bytes);

@@ -772,13 +772,14 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
           CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
     ++launches;
   }
+  P->prof->launches[TAPS_PROF_FASTDIAG] += launches - 2;
+  prof_end(P, TAPS_PROF_FASTDIAG, tk, 2.0 * P->Rf * nM + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),
+           8.0 * ((double)P->Rf * n + 2.0 * MM + (double)nM));
   // back to the nodal basis; the previous factor goes to d_Uold for the change norm
+  tk = prof_begin(P, TAPS_PROF_FD_TRANSFORM);
   TAPS_CUDA(taps_launch_pdl(fd_rowgemm_kernel, dim3(n), dim3(RG_WARPS * 32), 0, s, (const double*)E->Phi,
                             (const double*)Y, n, M, U->d_U[d], 1, P->d_Uold));
-  P->prof->launches[TAPS_PROF_FASTDIAG] += launches - 1;
-  prof_end(P, TAPS_PROF_FASTDIAG, tk,
-           2.0 * P->Rf * nM + 2.0 * (double)n * n * M + n * ((2.0 / 3.0) * M * MM + 2.0 * MM),
-           8.0 * ((double)n * n + 4.0 * nM + (double)P->Rf * n + 2.0 * MM));
+  prof_end(P, TAPS_PROF_FD_TRANSFORM, tk, 2.0 * (double)n * n * M, 8.0 * ((double)n * n + 3.0 * nM));
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }

@@ -124,7 +124,7 @@ SIGNATURES = {
 }
 
 PROF_CLASSES = ["gram", "coeff", "block_assemble", "block_lu", "backsub", "normalize",
-                "residual", "eval", "other", "fastdiag"]
+                "residual", "eval", "other", "fastdiag", "fd_transform"]
 
 _LIB = None
 
