@@ -10,10 +10,13 @@
 // so a solve costs two n x n x M products and n small LU solves instead of a
 // sequential block elimination over the n block rows.
 //
-// The one-off pencil decomposition runs in one CTA in FP64: banded Cholesky
-// B = L L^T, S = L^{-1} A L^{-T}, Householder tridiagonalisation of S with the
-// reflectors accumulated, the implicit QL iteration with Wilkinson shifts on the
-// tridiagonal (rotations applied to the accumulated basis), and Phi = L^{-T} Z.
+// The one-off pencil decomposition, in FP64: banded Cholesky B = L L^T,
+// S = L^{-1} A L^{-T} and Householder tridiagonalisation S = Q T Q^T in one CTA; then,
+// in parallel, the eigenvalues of T by Sturm-count multisection (one warp per
+// eigenvalue), its eigenvectors by inverse iteration (one thread per eigenvector, one
+// per cluster of nearly equal eigenvalues), one step of symmetric orthogonalisation,
+// the back-transform Z = Q Z_T (one warp per column), and Phi = L^{-T} Z (one thread per
+// column).
 #include <string.h>
 
 #include <algorithm>
@@ -32,16 +35,15 @@ __global__ void fd_dense_kernel(const double* __restrict__ bandA, const double* 
   B[idx] = in ? bandB[(size_t)i * nb + k] : 0.0;
 }
 
-// Single-CTA pencil decomposition.  A (n x n, row-major) is overwritten (S, then the
-// eigenvector basis Z); B holds the banded Cholesky factor L (lower) on exit.  V and
-// tmp are n x n and 2n scratch; Phi / PhiT receive L^{-T} Z and its transpose.
+// Single-CTA part of the pencil decomposition.  On exit B holds the banded Cholesky
+// factor L (lower) and, when the pencil has an A, (d, e) hold the tridiagonal T of
+// S = L^{-1} A L^{-T} = Q T Q^T (e[i] couples i and i+1) with the Householder vectors of
+// Q in the rows of V (row k: entries k+1 .. n-1) and their factors in beta.  A is
+// overwritten; tmp is 2n scratch.
 __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double* B, double* V, double* tmp,
                                                               double* beta, double* d, double* e, int n,
-                                                              int hb, int hasA, double* Phi, double* PhiT,
-                                                              double* mu, int* status) {
+                                                              int hb, int hasA, int* status) {
   __shared__ double red[32];
-  __shared__ int shi[8];
-  extern __shared__ double rot[];  // [2][n]: QL rotations (c, s) of one sweep
   const int tid = threadIdx.x, nt = blockDim.x;
 #define AT(M_, i, j) M_[(size_t)(i) * n + (j)]
 
@@ -153,110 +155,248 @@ __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double*
     }
     __syncthreads();
 
-    // ---- 4. accumulate Q = H_0 ... H_{n-3} into A (backward: Q <- H_k Q)
-    for (long long idx = tid; idx < (long long)n * n; idx += nt) A[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int k = n - 3; k >= 0; --k) {
-      double bk = beta[k];
-      if (bk == 0.0) continue;
-      const int len = n - k - 1;
-      for (int c = k + 1 + tid; c < n; c += nt) {
-        double z = 0.0;
-        for (int i = 0; i < len; ++i) z += AT(V, k, k + 1 + i) * AT(A, k + 1 + i, c);
-        z *= bk;
-        for (int i = 0; i < len; ++i) AT(A, k + 1 + i, c) -= AT(V, k, k + 1 + i) * z;
-      }
-      __syncthreads();
-    }
-
-    // ---- 5. implicit QL with Wilkinson shifts on (d, e); rotations -> columns of A
-    double* rc = rot;
-    double* rs = rot + n;
-    for (int l = 0; l < n; ++l) {
-      int iter = 0;
-      while (true) {
-        if (tid == 0) {
-          int m = l;
-          for (; m < n - 1; ++m) {
-            double dd = fabs(d[m]) + fabs(d[m + 1]);
-            if (fabs(e[m]) <= 2.220446049250313e-16 * dd) break;
-          }
-          int lo = m;   // rotations run i = m-1 .. stop (inclusive); none if m == l
-          int stop = m;
-          if (m != l) {
-            if (++iter > 60) taps_flag(status, TAPS_DEV_NONFINITE);
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int i = m - 1;
-            bool underflow = false;
-            for (; i >= l; --i) {
-              double f = s * e[i], b = c * e[i];
-              r = hypot(f, g);
-              e[i + 1] = r;
-              if (r == 0.0) {
-                d[i + 1] -= p;
-                e[m] = 0.0;
-                underflow = true;
-                break;
-              }
-              s = f / r;
-              c = g / r;
-              g = d[i + 1] - p;
-              r = (d[i] - g) * s + 2.0 * c * b;
-              p = s * r;
-              d[i + 1] = g + p;
-              g = c * r - b;
-              rc[i] = c;
-              rs[i] = s;
-            }
-            stop = underflow ? i + 1 : l;
-            if (!underflow) {
-              d[l] -= p;
-              e[l] = g;
-              e[m] = 0.0;
-            }
-            if (iter > 60) { lo = l; stop = l; }
-          }
-          shi[0] = (m == l || iter > 60) ? 1 : 0;  // l converged
-          shi[1] = lo;                              // first rotation index + 1
-          shi[2] = stop;                            // last rotation index
-        }
-        __syncthreads();
-        const int done = shi[0], lo = shi[1], stop = shi[2];
-        // rows of the basis are independent under column rotations
-        for (int row = tid; row < n; row += nt) {
-          for (int i = lo - 1; i >= stop; --i) {
-            double c = rc[i], s = rs[i];
-            double f = AT(A, row, i + 1);
-            AT(A, row, i + 1) = s * AT(A, row, i) + c * f;
-            AT(A, row, i) = c * AT(A, row, i) - s * f;
-          }
-        }
-        __syncthreads();
-        if (done) break;
-      }
-    }
-  } else {
-    for (long long idx = tid; idx < (long long)n * n; idx += nt) A[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
-    for (int i = tid; i < n; i += nt) d[i] = 0.0;
-    __syncthreads();
-  }
-
-  // ---- 6. Phi = L^{-T} Z, column by column
-  for (int c = tid; c < n; c += nt) {
-    for (int i = n - 1; i >= 0; --i) {
-      double s = AT(A, i, c);
-      for (int j = i + 1; j <= min(n - 1, i + hb); ++j) s -= AT(B, j, i) * AT(Phi, j, c);
-      double v = s / AT(B, i, i);
-      AT(Phi, i, c) = v;
-      AT(PhiT, c, i) = v;
-    }
-    mu[c] = d[c];
-    if (!isfinite(mu[c])) taps_flag(status, TAPS_DEV_NONFINITE);
   }
 #undef AT
+}
+
+// ---------------------------------------------------------------------------------
+// Eigenvalues of the symmetric tridiagonal T (diagonal d, off-diagonal e) by Sturm-count
+// multisection: warp k finds the k-th smallest eigenvalue.  Each lane counts the
+// eigenvalues below one of 32 interior points of the current interval (the signs of
+// the pivots of T - x I); the first point whose count exceeds k bounds the eigenvalue
+// from above, its left neighbour from below, so each round shrinks the interval 33x.
+// The start interval is Gershgorin's; a pivot smaller than pivmin counts as -pivmin.
+// The interval is refined until its width is 4 eps of the eigenvalue's magnitude.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ int fd_sturm_count(const double* __restrict__ d, const double* __restrict__ e,
+                                              int n, double x, double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.0 ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    const double ei = e[i - 1];
+    q = (d[i] - x) - (ei * ei) * taps_rcp(q);
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0 ? 1 : 0;
+  }
+  return cnt;
+}
+
+__global__ void fd_bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                 double* __restrict__ lam) {
+  const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;   // whole warps
+  double lo = INFINITY, hi = -INFINITY, e2max = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < n - 1) e2max = fmax(e2max, e[i] * e[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    e2max = fmax(e2max, __shfl_xor_sync(0xffffffffu, e2max, o));
+  }
+  const double eps = 2.220446049250313e-16;
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  // underflow guard for the Sturm pivots (the smallest normal double times the largest
+  // squared off-diagonal), small enough not to limit the eigenvalues' accuracy
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, e2max);
+  lo -= 4.0 * eps * tnorm + pivmin;
+  hi += 4.0 * eps * tnorm + pivmin;
+  for (int it = 0; it < 40; ++it) {
+    const double w = hi - lo;
+    if (w <= 4.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const double x = lo + w * (double)(lane + 1) / 33.0;
+    const unsigned above = __ballot_sync(0xffffffffu, fd_sturm_count(d, e, n, x, pivmin) > k);
+    const int j = above ? __ffs(above) - 1 : 32;
+    const double nhi = (j < 32) ? lo + w * (double)(j + 1) / 33.0 : hi;
+    const double nlo = (j > 0) ? lo + w * (double)j / 33.0 : lo;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) lam[k] = 0.5 * (lo + hi);
+}
+
+// ---------------------------------------------------------------------------------
+// Eigenvectors of T by inverse iteration: thread k factors T - lam_k I by Gaussian
+// elimination with partial pivoting (U has two super-diagonals) and solves three times
+// from a fixed start vector, normalising after each solve.  Eigenvalues closer than
+// 1e-5 ||T|| form a cluster, handled in order by the thread of its first member, each
+// iterate orthogonalised against the members already done (modified Gram-Schmidt).
+// Z is n x n row-major (column k = eigenvector k); W holds five n x n arrays laid out
+// [array][row][k] so that neighbouring threads touch neighbouring words.
+// ---------------------------------------------------------------------------------
+__global__ void fd_invit_kernel(const double* __restrict__ d, const double* __restrict__ e,
+                                const double* __restrict__ lam, int n, double* __restrict__ Z,
+                                double* __restrict__ W) {
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n) return;
+  double tnorm = 0.0;   // Gershgorin bound of ||T||
+  for (int i = 0; i < n; ++i)
+    tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0));
+  if (!(tnorm > 0.0)) tnorm = 1.0;
+  const double ctol = 1e-5 * tnorm;
+  if (k0 > 0 && lam[k0] - lam[k0 - 1] <= ctol) return;   // not the first member of its cluster
+  int k1 = k0;
+  while (k1 + 1 < n && lam[k1 + 1] - lam[k1] <= ctol) ++k1;
+  const double tiny = 2.220446049250313e-16 * tnorm;
+  const size_t nn = (size_t)n * n;
+#define WA(a, i) W[(size_t)(a) * nn + (size_t)(i) * n + k]
+#define ZC(i) Z[(size_t)(i) * n + k]
+  for (int k = k0; k <= k1; ++k) {
+    const double lk = lam[k];
+    // ---- factor T - lk I: arrays 0: 1/U0, 1: U1, 2: U2, 3: multiplier, 4: row swap
+    double ai = d[0] - lk, bi = n > 1 ? e[0] : 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+      const double ci = e[i], an = d[i + 1] - lk, bn = (i + 2 < n) ? e[i + 1] : 0.0;
+      if (fabs(ai) >= fabs(ci)) {
+        if (ai == 0.0) ai = tiny;
+        const double m = ci / ai;
+        WA(0, i) = 1.0 / ai;
+        WA(1, i) = bi;
+        WA(2, i) = 0.0;
+        WA(3, i) = m;
+        WA(4, i) = 0.0;
+        ai = an - m * bi;
+        bi = bn;
+      } else {
+        const double m = ai / ci;
+        WA(0, i) = 1.0 / ci;
+        WA(1, i) = an;
+        WA(2, i) = bn;
+        WA(3, i) = m;
+        WA(4, i) = 1.0;
+        ai = bi - m * an;
+        bi = -m * bn;
+      }
+    }
+    if (ai == 0.0) ai = tiny;
+    WA(0, n - 1) = 1.0 / ai;
+    // ---- start vector (fixed, different per k), then three solves
+    for (int i = 0; i < n; ++i) ZC(i) = 1.0 + 0.5 * sin(0.7 * i + 1.3 * k);
+    for (int it = 0; it < 3; ++it) {
+      for (int i = 0; i + 1 < n; ++i) {   // forward: row swaps and multipliers
+        double yi = ZC(i), yn = ZC(i + 1);
+        if (WA(4, i) != 0.0) {
+          const double t = yi;
+          yi = yn;
+          yn = t;
+        }
+        ZC(i) = yi;
+        ZC(i + 1) = yn - WA(3, i) * yi;
+      }
+      for (int i = n - 1; i >= 0; --i) {   // backward with the two super-diagonals
+        double sacc = ZC(i);
+        if (i + 1 < n) sacc -= WA(1, i) * ZC(i + 1);
+        if (i + 2 < n) sacc -= WA(2, i) * ZC(i + 2);
+        ZC(i) = sacc * WA(0, i);
+      }
+      for (int j = k0; j < k; ++j) {   // against the cluster's earlier members
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot += Z[(size_t)i * n + j] * ZC(i);
+        for (int i = 0; i < n; ++i) ZC(i) -= dot * Z[(size_t)i * n + j];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) nrm += ZC(i) * ZC(i);
+      const double inv = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
+      for (int i = 0; i < n; ++i) ZC(i) *= inv;
+    }
+  }
+#undef WA
+#undef ZC
+}
+
+// ---------------------------------------------------------------------------------
+// Symmetric orthogonalisation of the inverse-iteration vectors, first order:
+// Z <- Z - Z E / 2 with E = Z^T Z - I.  Independently computed eigenvectors are
+// orthogonal only to ~eps ||T|| / gap (1e-11 for the lowest eigenvalues of a stiffness
+// pencil); one step squares that, and Z^T T Z stays diagonal to ~eps ||T|| because the
+// correction of entry (j, k) is scaled by lam_j + lam_k.  E[j][k]: one thread each;
+// four partial sums shorten the dependent FP64 chain.
+// ---------------------------------------------------------------------------------
+__global__ void fd_gram_minus_identity_kernel(const double* __restrict__ Z, int n, double* __restrict__ E) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int j = (int)(idx / n), k = (int)(idx % n);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = 0;
+  for (; i + 3 < n; i += 4) {
+    a0 += Z[(size_t)i * n + j] * Z[(size_t)i * n + k];
+    a1 += Z[(size_t)(i + 1) * n + j] * Z[(size_t)(i + 1) * n + k];
+    a2 += Z[(size_t)(i + 2) * n + j] * Z[(size_t)(i + 2) * n + k];
+    a3 += Z[(size_t)(i + 3) * n + j] * Z[(size_t)(i + 3) * n + k];
+  }
+  for (; i < n; ++i) a0 += Z[(size_t)i * n + j] * Z[(size_t)i * n + k];
+  E[idx] = ((a0 + a1) + (a2 + a3)) - (j == k ? 1.0 : 0.0);
+}
+
+__global__ void fd_orth_update_kernel(const double* __restrict__ Z, const double* __restrict__ E, int n,
+                                      double* __restrict__ Zout) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx / n), k = (int)(idx % n);
+  const double* zi = Z + (size_t)i * n;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int j = 0;
+  for (; j + 3 < n; j += 4) {
+    a0 += zi[j] * E[(size_t)j * n + k];
+    a1 += zi[j + 1] * E[(size_t)(j + 1) * n + k];
+    a2 += zi[j + 2] * E[(size_t)(j + 2) * n + k];
+    a3 += zi[j + 3] * E[(size_t)(j + 3) * n + k];
+  }
+  for (; j < n; ++j) a0 += zi[j] * E[(size_t)j * n + k];
+  Zout[idx] = zi[k] - 0.5 * ((a0 + a1) + (a2 + a3));
+}
+
+// ---------------------------------------------------------------------------------
+// Back-transform Z <- Q Z with Q = H_0 H_1 ... H_{n-3}, H_r = I - beta_r v_r v_r^T acting
+// on rows r+1 .. n-1 (v_r in row r of V): warp c takes column c through the reflections
+// from the last to the first, the column held in shared memory.
+// ---------------------------------------------------------------------------------
+__global__ void fd_backtransform_kernel(const double* __restrict__ V, const double* __restrict__ beta, int n,
+                                        double* __restrict__ Z) {
+  extern __shared__ double zs[];   // [warps per CTA][n]
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + wl;
+  if (c >= n) return;   // whole warps
+  double* z = zs + (size_t)wl * n;
+  for (int i = lane; i < n; i += 32) z[i] = Z[(size_t)i * n + c];
+  __syncwarp();
+  for (int r = n - 3; r >= 0; --r) {
+    const double br = beta[r];
+    if (br == 0.0) continue;
+    const double* v = V + (size_t)r * n;
+    double dot = 0.0;
+    for (int i = r + 1 + lane; i < n; i += 32) dot += v[i] * z[i];
+    dot = warp_sum(dot) * br;
+    for (int i = r + 1 + lane; i < n; i += 32) z[i] -= dot * v[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) Z[(size_t)i * n + c] = z[i];
+}
+
+// Phi = L^{-T} Z (L: the banded Cholesky factor in B, lower, half-width hb), Phi^T, and
+// mu = the eigenvalues; one thread per column.  Without an A (single-operator pencil)
+// Z = I and mu = 0.
+__global__ void fd_phi_kernel(const double* __restrict__ L, const double* __restrict__ Z,
+                              const double* __restrict__ lam, int n, int hb, double* __restrict__ Phi,
+                              double* __restrict__ PhiT, double* __restrict__ mu, int* status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = n - 1; i >= 0; --i) {
+    double sacc = Z ? Z[(size_t)i * n + c] : (i == c ? 1.0 : 0.0);
+    for (int j = i + 1; j <= min(n - 1, i + hb); ++j) sacc -= L[(size_t)j * n + i] * Phi[(size_t)j * n + c];
+    const double v = sacc / L[(size_t)i * n + i];
+    Phi[(size_t)i * n + c] = v;
+    PhiT[(size_t)c * n + i] = v;
+  }
+  const double m = lam ? lam[c] : 0.0;
+  mu[c] = m;
+  if (!isfinite(m)) taps_flag(status, TAPS_DEV_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------------
@@ -694,8 +834,12 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
   size_t nn = (size_t)n * n;
   cudaStream_t s = P->stream;
   double *A = nullptr, *B = nullptr, *V = nullptr, *tmp = nullptr, *bt = nullptr, *dd = nullptr, *ee = nullptr;
+  double *lam = nullptr, *W = nullptr;
+  const int hasA = opA >= 0 ? 1 : 0;
   int st = TAPS_OK;
   do {
+    // the back-transform keeps one column per warp in shared memory (n <= 6144)
+    if (sizeof(double) * (size_t)n > 48 * 1024) { st = TAPS_ERR_INVALID_ARG; break; }
     if ((st = taps_alloc((void**)&E.Phi, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.PhiT, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.mu, sizeof(double) * n)) != TAPS_OK) break;
@@ -706,21 +850,41 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
     if ((st = taps_alloc((void**)&bt, sizeof(double) * n)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&dd, sizeof(double) * n)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&ee, sizeof(double) * n)) != TAPS_OK) break;
+    if (hasA) {
+      if ((st = taps_alloc((void**)&lam, sizeof(double) * n)) != TAPS_OK) break;
+      if ((st = taps_alloc((void**)&W, sizeof(double) * 5 * nn)) != TAPS_OK) break;
+    }
     const size_t bsz = (size_t)n * dm->nb;
-    const double* bandA = opA >= 0 ? dm->d_band + (size_t)opA * bsz : nullptr;
+    const double* bandA = hasA ? dm->d_band + (size_t)opA * bsz : nullptr;
     const double* bandB = dm->d_band + (size_t)opB * bsz;
+    int tk = prof_begin(P, TAPS_PROF_OTHER);
     fd_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(bandA, bandB, n, dm->hb, A, B);
     if (cudaMemsetAsync(V, 0, sizeof(double) * nn, s) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
-    size_t smem = sizeof(double) * 2 * (size_t)n;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute((const void*)fd_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int tk = prof_begin(P, TAPS_PROF_OTHER);
-    fd_setup_kernel<<<1, FD_THREADS, smem, s>>>(A, B, V, tmp, bt, dd, ee, n, dm->hb, opA >= 0 ? 1 : 0, E.Phi,
-                                                E.PhiT, E.mu, P->d_status);
-    prof_end(P, TAPS_PROF_OTHER, tk, 6.0 * (double)nn * n, 8.0 * 4.0 * nn);
+    // banded Cholesky and tridiagonalisation (one CTA)
+    fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(A, B, V, tmp, bt, dd, ee, n, dm->hb, hasA, P->d_status);
+    if (hasA) {
+      // eigenvalues (warp each), eigenvectors (thread each), back-transform (warp each),
+      // all into A, which the tridiagonalisation no longer needs
+      fd_bisect_kernel<<<(unsigned)((32LL * n + 255) / 256), 256, 0, s>>>(dd, ee, n, lam);
+      fd_invit_kernel<<<(n + 127) / 128, 128, 0, s>>>(dd, ee, lam, n, A, W);
+      // symmetric orthogonalisation: E in W, the corrected vectors back into A
+      const unsigned gnn = (unsigned)((nn + 255) / 256);
+      fd_gram_minus_identity_kernel<<<gnn, 256, 0, s>>>(A, n, W);
+      fd_orth_update_kernel<<<gnn, 256, 0, s>>>(A, W, n, W + nn);
+      if (cudaMemcpyAsync(A, W + nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        st = TAPS_ERR_CUDA;
+        break;
+      }
+      const int wpc = std::max(1, std::min(8, (int)(48 * 1024 / (sizeof(double) * (size_t)n))));
+      fd_backtransform_kernel<<<(n + wpc - 1) / wpc, 32 * wpc, sizeof(double) * (size_t)n * wpc, s>>>(V, bt, n,
+                                                                                                      A);
+    }
+    fd_phi_kernel<<<(n + 127) / 128, 128, 0, s>>>(B, hasA ? A : nullptr, hasA ? lam : nullptr, n, dm->hb, E.Phi,
+                                                  E.PhiT, E.mu, P->d_status);
+    prof_end(P, TAPS_PROF_OTHER, tk, (10.0 / 3.0) * (double)nn * n, 8.0 * 4.0 * nn);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
-      taps_note_cuda_error(ce, "fd_setup_kernel", __FILE__, __LINE__);
+      taps_note_cuda_error(ce, "pencil decomposition", __FILE__, __LINE__);
       st = TAPS_ERR_CUDA;
       break;
     }
@@ -733,6 +897,8 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
   cudaFree(bt);
   cudaFree(dd);
   cudaFree(ee);
+  cudaFree(lam);
+  cudaFree(W);
   E.status = st;
   dm->nfd++;
   *out = &E;
