@@ -615,12 +615,11 @@ __global__ void __launch_bounds__(32) fd_small_solve_warp_kernel(const double* _
 // vectors (the warps split the sum over r).  At step p every warp updates its
 // columns c > p with the multipliers l_r = T[r][p] / T[p][p] of that step, which the
 // owner of column p has published in shared memory (one reciprocal of the pivot,
-// kept for the back substitution).  The owner of column p+1 updates only that column
-// at step p and publishes the next multipliers; its other updates of step p run at
-// step p+1, when another warp carries the chain of pivots, so that chain is held up
-// by neither the bulk of the updates nor the barrier waiting for them.  No pivoting,
-// as in the one-warp solve.  The upper factor then goes to shared memory and warp 0
-// back-substitutes.
+// kept for the back substitution).  The chain of pivots is the bound: the owner of
+// column p+1 updates that column first (its row-p value fetched before the barrier),
+// takes the pivot's reciprocal (approximate seed + series refinement) and issues its
+// other updates while the reciprocal completes.  No pivoting, as in the one-warp
+// solve.  The upper factor then goes to shared memory and warp 0 back-substitutes.
 __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* __restrict__ CA,
                                                                   const double* __restrict__ CB,
                                                                   const double* __restrict__ mu,
@@ -662,34 +661,26 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
   double pc_next = (w == 1) ? __shfl_sync(0xffffffffu, v[0], 0) : 0.0;
   __syncthreads();
   double b = (w == 0) ? (gpart[0][lane] + gpart[1][lane]) + (gpart[2][lane] + gpart[3][lane]) : 0.0;
-  double lprev = 0.0;   // multipliers of the step whose other updates this warp deferred
 #pragma unroll
   for (int p = 0; p < 32; ++p) {
     if (p < M) {
       const double l = lbuf[p & 1][lane];
       const int q = p + 1;   // next pivot column, owned by warp q & 3 in slot q >> 2
-      // (1) the owner of column p published the multipliers of step p before its
-      // other updates of step p - 1; it applies them now (rows p - 1 of its columns
-      // are final, so the pivot-row values are the same as then)
-      if (p >= 1 && w == (p & 3)) {
-#pragma unroll
-        for (int k = (p >> 2) + 1; k < 8; ++k) v[k] -= lprev * __shfl_sync(0xffffffffu, v[k], p - 1);
-      }
       if (q < M && w == (q & 3)) {
-        // (2) the owner of column q: that column first (its row p was shuffled at
-        // the end of the previous step), then the next multipliers; its other
-        // updates of this step wait for the next step
+        // owner of column q: that column (its row p was fetched before the barrier),
+        // the pivot's reciprocal, then its other columns in the same block so that
+        // their FP64 issue fills the reciprocal's latency, then the next multipliers
         v[q >> 2] -= l * pc_next;
         const double piv = __shfl_sync(0xffffffffu, v[q >> 2], q);
         const double inv = taps_rcp(piv);
+#pragma unroll
+        for (int k = (q >> 2) + 1; k < 8; ++k) v[k] -= l * __shfl_sync(0xffffffffu, v[k], p);
         lbuf[q & 1][lane] = (lane > q && lane < M) ? v[q >> 2] * inv : 0.0;
         if (lane == 0) invd[q] = inv;
-        bad |= !(fabs(piv) > 0.0) || !isfinite(piv);   // off the chain of pivots
-        lprev = l;
+        bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
       } else {
-        // (3) every other warp: its columns c > p
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 8; ++k) {   // this warp's columns c > p
           if (4 * k + 3 <= p) continue;                 // every column of this slot is <= p
           if (4 * k <= p && w <= p - 4 * k) continue;   // column 4k + w <= p
           v[k] -= l * __shfl_sync(0xffffffffu, v[k], p);

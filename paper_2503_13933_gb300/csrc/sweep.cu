@@ -22,6 +22,7 @@ __device__ __forceinline__ void coeff_C(const TermTable& tt, const GramPtrs& gp,
   double acc[TAPS_NUM_OPS];
 #pragma unroll
   for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
+#pragma unroll 4
   for (int t = 0; t < tt.R; ++t) {
     double f[TAPS_MAX_DIMS];
 #pragma unroll
@@ -160,7 +161,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
       j = ng + (rem / mt) * M + m0 + rem % mt;
     }
     double acc = 0.0;
-#pragma unroll 8
+#pragma unroll 16
     for (int ch = 0; ch < nchunk; ++ch) acc += __ldcg(partial + (size_t)ch * stride + j);
     if (j < ng) gram[j] = acc;
     else h[j - ng] = acc;
