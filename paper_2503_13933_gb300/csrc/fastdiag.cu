@@ -10,9 +10,9 @@
 // so a solve costs two n x n x M products and n small LU solves instead of a
 // sequential block elimination over the n block rows.
 //
-// The one-off pencil decomposition, in FP64: banded Cholesky B = L L^T,
-// S = L^{-1} A L^{-T} and Householder tridiagonalisation S = Q T Q^T in one CTA; then,
-// in parallel, the eigenvalues of T by Sturm-count multisection (one warp per
+// The one-off pencil decomposition, in FP64: banded Cholesky B = L L^T and
+// S = L^{-1} A L^{-T} in one CTA, Householder tridiagonalisation S = Q T Q^T on one
+// thread-block cluster; then, in parallel, the eigenvalues of T by Sturm-count multisection (one warp per
 // eigenvalue), its eigenvectors by inverse iteration (one thread per eigenvector, one
 // per cluster of nearly equal eigenvalues), one step of symmetric orthogonalisation,
 // the back-transform Z = Q Z_T (one warp per column), and Phi = L^{-T} Z (one thread per
@@ -36,14 +36,10 @@ __global__ void fd_dense_kernel(const double* __restrict__ bandA, const double* 
 }
 
 // Single-CTA part of the pencil decomposition.  On exit B holds the banded Cholesky
-// factor L (lower) and, when the pencil has an A, (d, e) hold the tridiagonal T of
-// S = L^{-1} A L^{-T} = Q T Q^T (e[i] couples i and i+1) with the Householder vectors of
-// Q in the rows of V (row k: entries k+1 .. n-1) and their factors in beta.  A is
-// overwritten; tmp is 2n scratch.
-__global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double* B, double* V, double* tmp,
-                                                              double* beta, double* d, double* e, int n,
-                                                              int hb, int hasA, int* status) {
-  __shared__ double red[32];
+// factor L (lower) and, when the pencil has an A, A holds S = L^{-1} A L^{-T}
+// (symmetrised); V is n x n scratch.
+__global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double* B, double* V, int n, int hb,
+                                                              int hasA, int* status) {
   const int tid = threadIdx.x, nt = blockDim.x;
 #define AT(M_, i, j) M_[(size_t)(i) * n + (j)]
 
@@ -94,67 +90,108 @@ __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double*
     }
     __syncthreads();
 
-    // ---- 3. Householder tridiagonalisation of S (stored in A)
-    for (int k = 0; k + 2 < n; ++k) {
-      const int len = n - k - 1;
-      double s2 = 0.0;
-      for (int t = tid; t < len; t += nt) {
-        double x = AT(A, k + 1 + t, k);
-        s2 += x * x;
+  }
+#undef AT
+}
+
+// ---------------------------------------------------------------------------------
+// Householder tridiagonalisation S = Q T Q^T of the symmetric S held in A (n x n,
+// row-major), on one cluster of TD_CTAS CTAs with hardware cluster barriers between
+// the phases of a step.  Step k: every CTA stages column k below the diagonal in
+// shared memory and forms the same reflector v (beta = 2 / v.v); one warp per row of
+// the cluster computes p = beta S22 v; after a cluster barrier every CTA forms
+// w = p - (beta v.p / 2) v and its warps update their rows of S22 -= v w^T + w v^T;
+// a second barrier ends the step.  Values written by other CTAs are read through L2.
+// On exit (d, e) hold T (e[i] couples i and i+1), the rows of V the reflectors
+// (row k: entries k+1 .. n-1) and beta their factors.
+// ---------------------------------------------------------------------------------
+#define TD_CTAS 8
+#define TD_THREADS 1024
+__device__ __forceinline__ void td_cluster_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
+    fd_tridiag_kernel(double* __restrict__ A, double* __restrict__ V, double* __restrict__ p,
+                      double* __restrict__ beta, double* __restrict__ d, double* __restrict__ e, int n) {
+  extern __shared__ double tds[];   // v [n], p [n], w [n]
+  __shared__ double red[32];
+  double* vs = tds;
+  double* ps = tds + n;
+  double* ws = tds + 2 * n;
+  const int rank = blockIdx.x;   // the grid is one cluster
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gwarp = rank * (TD_THREADS / 32) + (tid >> 5);
+  const int nwarps = TD_CTAS * (TD_THREADS / 32);
+#define AT(i, j) A[(size_t)(i) * n + (j)]
+  for (int k = 0; k + 2 < n; ++k) {
+    const int len = n - k - 1;
+    double s2 = 0.0;
+    for (int t = tid; t < len; t += TD_THREADS) {
+      const double x = __ldcg(&AT(k + 1 + t, k));
+      vs[t] = x;
+      s2 += x * x;
+    }
+    s2 = block_sum(s2, red);   // also orders the vs writes
+    if (s2 == 0.0) {           // the same in every CTA: nothing to reflect
+      if (rank == 0 && tid == 0) {
+        beta[k] = 0.0;
+        d[k] = __ldcg(&AT(k, k));
+        e[k] = 0.0;
       }
-      s2 = block_sum(s2, red);
-      if (s2 == 0.0) {
-        if (tid == 0) {
-          beta[k] = 0.0;
-          d[k] = AT(A, k, k);
-          e[k] = 0.0;
-        }
-        __syncthreads();
-        continue;
-      }
-      double x0 = AT(A, k + 1, k);
-      double alpha = -copysign(sqrt(s2), x0);
-      double v0 = x0 - alpha;
-      double vn2 = s2 - x0 * x0 + v0 * v0;
-      double bk = 2.0 / vn2;
-      for (int t = tid; t < len; t += nt) AT(V, k, k + 1 + t) = (t == 0) ? v0 : AT(A, k + 1 + t, k);
-      __syncthreads();
-      // p = beta S22 v (column access: S symmetric)
-      double pv = 0.0;
-      for (int i = tid; i < len; i += nt) {
-        double acc = 0.0;
-        for (int j = 0; j < len; ++j) acc += AT(A, k + 1 + j, k + 1 + i) * AT(V, k, k + 1 + j);
-        acc *= bk;
-        tmp[i] = acc;
-        pv += acc * AT(V, k, k + 1 + i);
-      }
-      pv = block_sum(pv, red);
-      double Kc = 0.5 * bk * pv;
-      for (int i = tid; i < len; i += nt) tmp[n + i] = tmp[i] - Kc * AT(V, k, k + 1 + i);  // w
-      __syncthreads();
-      for (long long idx = tid; idx < (long long)len * len; idx += nt) {
-        int i = idx / len, j = idx % len;
-        double vi = AT(V, k, k + 1 + i), vj = AT(V, k, k + 1 + j);
-        AT(A, k + 1 + i, k + 1 + j) -= vi * tmp[n + j] + tmp[n + i] * vj;
-      }
+      continue;
+    }
+    const double x0 = vs[0];
+    const double alpha = -copysign(sqrt(s2), x0);
+    const double v0 = x0 - alpha;
+    const double bk = 2.0 / (s2 - x0 * x0 + v0 * v0);
+    __syncthreads();
+    if (tid == 0) vs[0] = v0;
+    __syncthreads();
+    // p = beta S22 v, one warp per row
+    for (int i = gwarp; i < len; i += nwarps) {
+      const double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+      double acc = 0.0;
+      for (int t = lane; t < len; t += 32) acc += __ldcg(row + t) * vs[t];
+      acc = warp_sum(acc);
+      if (lane == 0) p[i] = bk * acc;
+    }
+    td_cluster_sync();
+    double pv = 0.0;
+    for (int t = tid; t < len; t += TD_THREADS) {
+      const double pt = __ldcg(p + t);
+      ps[t] = pt;
+      pv += pt * vs[t];
+    }
+    pv = block_sum(pv, red);
+    const double Kc = 0.5 * bk * pv;
+    for (int t = tid; t < len; t += TD_THREADS) ws[t] = ps[t] - Kc * vs[t];
+    __syncthreads();
+    for (int i = gwarp; i < len; i += nwarps) {
+      double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+      const double vi = vs[i], wi = ws[i];
+      for (int t = lane; t < len; t += 32) row[t] = __ldcg(row + t) - (vi * ws[t] + wi * vs[t]);
+    }
+    if (rank == 0) {
+      for (int t = tid; t < len; t += TD_THREADS) V[(size_t)k * n + k + 1 + t] = vs[t];
       if (tid == 0) {
         beta[k] = bk;
-        d[k] = AT(A, k, k);
+        d[k] = __ldcg(&AT(k, k));
         e[k] = alpha;
       }
-      __syncthreads();
     }
-    if (tid == 0) {
-      if (n >= 2) {
-        d[n - 2] = AT(A, n - 2, n - 2);
-        e[n - 2] = AT(A, n - 1, n - 2);
-      }
-      d[n - 1] = AT(A, n - 1, n - 1);
-      e[n - 1] = 0.0;
-      for (int k = max(0, n - 2); k < n; ++k) beta[k] = 0.0;
+    td_cluster_sync();
+  }
+  if (rank == 0 && tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = __ldcg(&AT(n - 2, n - 2));
+      e[n - 2] = __ldcg(&AT(n - 1, n - 2));
     }
-    __syncthreads();
-
+    d[n - 1] = __ldcg(&AT(n - 1, n - 1));
+    e[n - 1] = 0.0;
+    for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) beta[k] = 0.0;
   }
 #undef AT
 }
@@ -829,8 +866,15 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
   const int hasA = opA >= 0 ? 1 : 0;
   int st = TAPS_OK;
   do {
-    // the back-transform keeps one column per warp in shared memory (n <= 6144)
+    // the back-transform keeps one column per warp in shared memory (n <= 6144); the
+    // tridiagonalisation stages three vectors (3n doubles)
     if (sizeof(double) * (size_t)n > 48 * 1024) { st = TAPS_ERR_INVALID_ARG; break; }
+    if (sizeof(double) * 3 * (size_t)n > 48 * 1024) {
+      int dev = 0, maxsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if ((st = taps_allow_dyn_smem((const void*)fd_tridiag_kernel, maxsm)) != TAPS_OK) break;
+    }
     if ((st = taps_alloc((void**)&E.Phi, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.PhiT, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.mu, sizeof(double) * n)) != TAPS_OK) break;
@@ -851,9 +895,10 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
     int tk = prof_begin(P, TAPS_PROF_OTHER);
     fd_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(bandA, bandB, n, dm->hb, A, B);
     if (cudaMemsetAsync(V, 0, sizeof(double) * nn, s) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
-    // banded Cholesky and tridiagonalisation (one CTA)
-    fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(A, B, V, tmp, bt, dd, ee, n, dm->hb, hasA, P->d_status);
+    // banded Cholesky and S (one CTA), then the tridiagonalisation (one cluster)
+    fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(A, B, V, n, dm->hb, hasA, P->d_status);
     if (hasA) {
+      fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, tmp, bt, dd, ee, n);
       // eigenvalues (warp each), eigenvectors (thread each), back-transform (warp each),
       // all into A, which the tridiagonalisation no longer needs
       fd_bisect_kernel<<<(unsigned)((32LL * n + 255) / 256), 256, 0, s>>>(dd, ee, n, lam);
