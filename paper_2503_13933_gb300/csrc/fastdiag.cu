@@ -199,17 +199,20 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
 // ---------------------------------------------------------------------------------
 // Eigenvalues of the symmetric tridiagonal T (diagonal d, off-diagonal e) by Sturm-count
 // multisection: warp k finds the k-th smallest eigenvalue.  Each lane counts the
-// eigenvalues below one of 32 interior points of the current interval (the signs of
-// the pivots of T - x I); the first point whose count exceeds k bounds the eigenvalue
-// from above, its left neighbour from below, so each round shrinks the interval 33x.
-// The start interval is Gershgorin's; a pivot smaller than pivmin counts as -pivmin.
-// The interval is refined until its width is 4 eps of the eigenvalue's magnitude.
+// eigenvalues below one of 32 interior points of the current interval (Sturm count);
+// the first point whose count exceeds k bounds the eigenvalue from above, its left
+// neighbour from below, so each round shrinks the interval 33x.  The start interval is
+// Gershgorin's; it is refined to a width of 4 eps ||T|| (what Sturm counts resolve),
+// about 11 rounds, or until rounding stops it shrinking.
 // ---------------------------------------------------------------------------------
+// Number of eigenvalues of T below x: the negative pivots of T - x I,
+// q_i = (d_i - x) - e_{i-1}^2 / q_{i-1}; a pivot smaller than pivmin counts as -pivmin.
 __device__ __forceinline__ int fd_sturm_count(const double* __restrict__ d, const double* __restrict__ e,
                                               int n, double x, double pivmin) {
   double q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   int cnt = q < 0.0 ? 1 : 0;
+#pragma unroll 4
   for (int i = 1; i < n; ++i) {
     const double ei = e[i - 1];
     q = (d[i] - x) - (ei * ei) * taps_rcp(q);
@@ -244,9 +247,13 @@ __global__ void fd_bisect_kernel(const double* __restrict__ d, const double* __r
   const double pivmin = 2.2250738585072014e-308 * fmax(1.0, e2max);
   lo -= 4.0 * eps * tnorm + pivmin;
   hi += 4.0 * eps * tnorm + pivmin;
+  double wprev = INFINITY;
   for (int it = 0; it < 40; ++it) {
     const double w = hi - lo;
-    if (w <= 4.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    // Sturm counts resolve an eigenvalue to about eps ||T|| (absolute)
+    if (w <= 4.0 * eps * tnorm + pivmin) break;
+    if (it > 0 && !(w < wprev)) break;   // rounding no longer separates the trial points
+    wprev = w;
     const double x = lo + w * (double)(lane + 1) / 33.0;
     const unsigned above = __ballot_sync(0xffffffffu, fd_sturm_count(d, e, n, x, pivmin) > k);
     const int j = above ? __ffs(above) - 1 : 32;
@@ -313,24 +320,33 @@ __global__ void fd_invit_kernel(const double* __restrict__ d, const double* __re
     }
     if (ai == 0.0) ai = tiny;
     WA(0, n - 1) = 1.0 / ai;
+    WA(1, n - 1) = 0.0;   // the last row has no super-diagonals
+    WA(2, n - 1) = 0.0;
     // ---- start vector (fixed, different per k), then three solves
     for (int i = 0; i < n; ++i) ZC(i) = 1.0 + 0.5 * sin(0.7 * i + 1.3 * k);
     for (int it = 0; it < 3; ++it) {
-      for (int i = 0; i + 1 < n; ++i) {   // forward: row swaps and multipliers
-        double yi = ZC(i), yn = ZC(i + 1);
+      // forward: row swaps and multipliers (the running entry stays in a register)
+      double yi = ZC(0);
+#pragma unroll 8
+      for (int i = 0; i + 1 < n; ++i) {
+        double yn = ZC(i + 1);
         if (WA(4, i) != 0.0) {
           const double t = yi;
           yi = yn;
           yn = t;
         }
         ZC(i) = yi;
-        ZC(i + 1) = yn - WA(3, i) * yi;
+        yi = yn - WA(3, i) * yi;
       }
-      for (int i = n - 1; i >= 0; --i) {   // backward with the two super-diagonals
-        double sacc = ZC(i);
-        if (i + 1 < n) sacc -= WA(1, i) * ZC(i + 1);
-        if (i + 2 < n) sacc -= WA(2, i) * ZC(i + 2);
-        ZC(i) = sacc * WA(0, i);
+      ZC(n - 1) = yi;
+      // backward with the two super-diagonals (z_{i+1}, z_{i+2} in registers)
+      double z1 = 0.0, z2 = 0.0;
+#pragma unroll 8
+      for (int i = n - 1; i >= 0; --i) {
+        const double zi = (ZC(i) - WA(1, i) * z1 - WA(2, i) * z2) * WA(0, i);
+        ZC(i) = zi;
+        z2 = z1;
+        z1 = zi;
       }
       for (int j = k0; j < k; ++j) {   // against the cluster's earlier members
         double dot = 0.0;
@@ -901,7 +917,8 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
       fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, tmp, bt, dd, ee, n);
       // eigenvalues (warp each), eigenvectors (thread each), back-transform (warp each),
       // all into A, which the tridiagonalisation no longer needs
-      fd_bisect_kernel<<<(unsigned)((32LL * n + 255) / 256), 256, 0, s>>>(dd, ee, n, lam);
+      // two warps per CTA: the warps' FP64 chains spread over the SMs' sub-partitions
+      fd_bisect_kernel<<<(unsigned)((32LL * n + 63) / 64), 64, 0, s>>>(dd, ee, n, lam);
       fd_invit_kernel<<<(n + 127) / 128, 128, 0, s>>>(dd, ee, lam, n, A, W);
       // symmetric orthogonalisation: E in W, the corrected vectors back into A
       const unsigned gnn = (unsigned)((nn + 255) / 256);
