@@ -21,6 +21,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "taps_internal.cuh"
 
 #define FD_THREADS 1024
@@ -194,6 +196,105 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
     for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) beta[k] = 0.0;
   }
 #undef AT
+}
+
+// The same tridiagonalisation with S held in the cluster's distributed shared memory
+// (n small enough that ceil(n / TD_CTAS) rows of n doubles fit one CTA's shared memory):
+// CTA r keeps rows i = r, r + TD_CTAS, ...  Step k: every CTA gathers column k from the
+// rows' owners (remote shared-memory loads), forms the reflector, computes p_i for its
+// own rows and stores each p_i into every CTA's copy of p; after a cluster barrier
+// every CTA forms w and updates its own rows; a second barrier ends the step.  S never
+// leaves shared memory.
+__global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
+    fd_tridiag_dsmem_kernel(const double* __restrict__ A, double* __restrict__ V, double* __restrict__ beta,
+                            double* __restrict__ d, double* __restrict__ e, int n) {
+  extern __shared__ double tsm[];   // vs [n] | ps [n] | ws [n] | own rows [nr][n]
+  __shared__ double red[32];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = TD_THREADS / 32;
+  double* vs = tsm;
+  double* ps = tsm + n;
+  double* ws = tsm + 2 * n;
+  double* rows = tsm + 3 * n;
+  const int nr = (n - rank + TD_CTAS - 1) / TD_CTAS;   // rows i = rank + TD_CTAS * l, l < nr
+  for (long long idx = tid; idx < (long long)nr * n; idx += TD_THREADS) {
+    const int l = (int)(idx / n), j = (int)(idx % n);
+    rows[(size_t)l * n + j] = A[(size_t)(rank + TD_CTAS * l) * n + j];
+  }
+  cluster.sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int len = n - k - 1;
+    // column k below the diagonal, from the owners of its rows
+    double s2 = 0.0;
+    for (int t = tid; t < len; t += TD_THREADS) {
+      const int i = k + 1 + t;
+      const double* owner_rows = cluster.map_shared_rank(rows, i % TD_CTAS);
+      const double x = owner_rows[(size_t)(i / TD_CTAS) * n + k];
+      vs[t] = x;
+      s2 += x * x;
+    }
+    s2 = block_sum(s2, red);
+    if (s2 == 0.0) {   // the same in every CTA
+      if (k % TD_CTAS == rank && tid == 0) d[k] = rows[(size_t)(k / TD_CTAS) * n + k];
+      if (rank == 0 && tid == 0) {
+        beta[k] = 0.0;
+        e[k] = 0.0;
+      }
+      cluster.sync();
+      continue;
+    }
+    const double x0 = vs[0];
+    const double alpha = -copysign(sqrt(s2), x0);
+    const double v0 = x0 - alpha;
+    const double bk = 2.0 / (s2 - x0 * x0 + v0 * v0);
+    __syncthreads();
+    if (tid == 0) vs[0] = v0;
+    __syncthreads();
+    // p_i for own rows i >= k + 1, pushed into every CTA's ps
+    const int l0 = (k + 1 - rank + TD_CTAS - 1) / TD_CTAS;   // first own row >= k + 1
+    for (int l = l0 + warp; l < nr; l += nwarps) {
+      const int i = rank + TD_CTAS * l;
+      const double* row = rows + (size_t)l * n + (k + 1);
+      double acc = 0.0;
+      for (int t = lane; t < len; t += 32) acc += row[t] * vs[t];
+      acc = warp_sum(acc) * bk;
+      if (lane < TD_CTAS) cluster.map_shared_rank(ps, lane)[i - k - 1] = acc;
+    }
+    cluster.sync();
+    double pv = 0.0;
+    for (int t = tid; t < len; t += TD_THREADS) pv += ps[t] * vs[t];
+    pv = block_sum(pv, red);
+    const double Kc = 0.5 * bk * pv;
+    for (int t = tid; t < len; t += TD_THREADS) ws[t] = ps[t] - Kc * vs[t];
+    __syncthreads();
+    for (int l = l0 + warp; l < nr; l += nwarps) {
+      const int i = rank + TD_CTAS * l - (k + 1);   // index within the trailing block
+      double* row = rows + (size_t)l * n + (k + 1);
+      const double vi = vs[i], wi = ws[i];
+      for (int t = lane; t < len; t += 32) row[t] -= vi * ws[t] + wi * vs[t];
+    }
+    if (rank == 0) {
+      for (int t = tid; t < len; t += TD_THREADS) V[(size_t)k * n + k + 1 + t] = vs[t];
+      if (tid == 0) {
+        beta[k] = bk;
+        e[k] = alpha;
+      }
+    }
+    if (k % TD_CTAS == rank && tid == 0) d[k] = rows[(size_t)(k / TD_CTAS) * n + k];
+    cluster.sync();
+  }
+  if (tid == 0) {
+    for (int i = (n >= 2 ? n - 2 : 0); i < n; ++i)
+      if (i % TD_CTAS == rank) d[i] = rows[(size_t)(i / TD_CTAS) * n + i];
+    if (n >= 2 && (n - 1) % TD_CTAS == rank) e[n - 2] = rows[(size_t)((n - 1) / TD_CTAS) * n + (n - 2)];
+    if (rank == 0) {
+      e[n - 1] = 0.0;
+      for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) beta[k] = 0.0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -885,12 +986,15 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
     // the back-transform keeps one column per warp in shared memory (n <= 6144); the
     // tridiagonalisation stages three vectors (3n doubles)
     if (sizeof(double) * (size_t)n > 48 * 1024) { st = TAPS_ERR_INVALID_ARG; break; }
-    if (sizeof(double) * 3 * (size_t)n > 48 * 1024) {
-      int dev = 0, maxsm = 0;
+    int maxsm_optin = 0;
+    {
+      int dev = 0;
       cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if ((st = taps_allow_dyn_smem((const void*)fd_tridiag_kernel, maxsm)) != TAPS_OK) break;
+      cudaDeviceGetAttribute(&maxsm_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
+    if (sizeof(double) * 3 * (size_t)n > 48 * 1024 &&
+        (st = taps_allow_dyn_smem((const void*)fd_tridiag_kernel, maxsm_optin)) != TAPS_OK)
+      break;
     if ((st = taps_alloc((void**)&E.Phi, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.PhiT, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.mu, sizeof(double) * n)) != TAPS_OK) break;
@@ -914,7 +1018,13 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
     // banded Cholesky and S (one CTA), then the tridiagonalisation (one cluster)
     fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(A, B, V, n, dm->hb, hasA, P->d_status);
     if (hasA) {
-      fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, tmp, bt, dd, ee, n);
+      const size_t dsm = sizeof(double) * ((size_t)((n + TD_CTAS - 1) / TD_CTAS) * n + 3 * (size_t)n);
+      if (dsm + 1024 <= (size_t)maxsm_optin) {   // S fits the cluster's shared memory
+        if ((st = taps_allow_dyn_smem((const void*)fd_tridiag_dsmem_kernel, maxsm_optin)) != TAPS_OK) break;
+        fd_tridiag_dsmem_kernel<<<TD_CTAS, TD_THREADS, dsm, s>>>(A, V, bt, dd, ee, n);
+      } else {
+        fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, tmp, bt, dd, ee, n);
+      }
       // eigenvalues (warp each), eigenvectors (thread each), back-transform (warp each),
       // all into A, which the tridiagonalisation no longer needs
       // two warps per CTA: the warps' FP64 chains spread over the SMs' sub-partitions
