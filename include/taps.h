@@ -158,9 +158,14 @@ typedef struct {
   int init;            /* TAPS_INIT_* for the columns added by the schedule */
   unsigned seed;       /* seed of TAPS_INIT_RANDOM */
   int history_cap;     /* capacity of the report's history arrays (0: none) */
-  int graphs;          /* 1: replay each sweep + residual as a captured CUDA graph
-                          (captured on first use per factors / M / precision / solver;
-                          falls back to direct launches if capture is unavailable) */
+  int graphs;          /* 0: direct launches.  1: replay each sweep + residual as a
+                          captured CUDA graph (captured on first use per factors / M /
+                          precision / solver; falls back to direct launches if capture
+                          is unavailable).  2: run the whole sweep loop of each M on the
+                          device, one graph whose conditional WHILE node repeats sweep,
+                          residual and the stopping test (FP64 / MIXED with the Eq. 42
+                          residual and profiling events off; otherwise as 1); the same
+                          sweeps and factors as 1, without a host round trip per sweep */
 } taps_solve_opts;
 
 typedef struct {

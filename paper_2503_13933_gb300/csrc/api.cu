@@ -1,3 +1,4 @@
+#include <stdlib.h>
 // C ABI: problem and factor objects, sweeps, greedy solve (Algorithm 1 with a growing
 // mode count), residuals and grid reconstruction (Eq. 13).
 #include <string.h>
@@ -164,6 +165,220 @@ static int graph_build(taps_problem* P, taps_factors* U, int prec, int solver, i
   return st;
 }
 
+// ---------------------------------------------------------------------------------
+// Device-side solve loop: one CUDA graph whose conditional WHILE node repeats
+// {sweep, Eq. 42 residual, decision} without returning to the host.  The decision
+// kernel forms the factor change and rho_42 from the device partial sums in the order
+// the host's finish functions use (so the stopping sweep and the factors are those of
+// the host loop), records them and sets the loop condition.
+// ---------------------------------------------------------------------------------
+struct LoopRanges {
+  int cta0[TAPS_MAX_DIMS + 1];
+};
+
+__global__ void solve_decide_kernel(cudaGraphConditionalHandle h, const double* __restrict__ scal, int M, int D,
+                                    const double* __restrict__ part, LoopRanges rg, double res_tol,
+                                    double als_tol, int max_sweeps, int* __restrict__ state,
+                                    double* __restrict__ hist, int cap, const int* __restrict__ status) {
+  if (threadIdx.x != 0) return;
+  double change = 0.0;
+  for (int d = 0; d < D; ++d) {
+    double dif = 0.0, n2 = 0.0;
+    for (int m = 0; m < M; ++m) {
+      dif += scal[(size_t)d * 2 * M + 2 * m];
+      n2 += scal[(size_t)d * 2 * M + 2 * m + 1];
+    }
+    change = fmax(change, n2 > 0.0 ? sqrt(dif / n2) : INFINITY);
+  }
+  double rho = 0.0;
+  for (int d = 0; d < D; ++d) {
+    double r2 = 0.0, f2 = 0.0;
+    for (int b = rg.cta0[d]; b < rg.cta0[d + 1]; ++b) {
+      r2 += part[2 * b];
+      f2 += part[2 * b + 1];
+    }
+    rho = fmax(rho, f2 > 0.0 ? sqrt(r2 / f2) : INFINITY);
+  }
+  const int it = state[0];
+  if (it < cap) {
+    hist[2 * it] = rho;
+    hist[2 * it + 1] = change;
+  }
+  state[0] = it + 1;
+  const int st = *status;
+  const bool finite = isfinite(rho) && isfinite(change);
+  state[1] = st;
+  state[2] = finite ? 1 : 0;
+  const bool more = st == 0 && finite && !(rho <= res_tol) && !(change <= als_tol) && it + 1 < max_sweeps;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+struct LoopGraph {
+  const taps_factors* U;
+  int M, precision, solver, ws_M, max_sweeps;
+  double res_tol, als_tol;
+  bool failed;
+  cudaGraph_t g;
+  cudaGraphExec_t exec;
+  cudaGraphConditionalHandle h;
+  int* d_state;       // [iterations, status, finite]
+  double* d_hist;     // [max_sweeps][rho, change]
+  int* h_state;       // pinned mirrors
+  double* h_hist;
+  long long dl[TAPS_PROF_NUM];   // per-iteration profiling increments
+  double dfl[TAPS_PROF_NUM], dby[TAPS_PROF_NUM];
+};
+
+static void loop_destroy(taps_problem* P) {
+  LoopGraph* L = (LoopGraph*)P->loop_graph;
+  if (!L) return;
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->g) cudaGraphDestroy(L->g);
+  cudaFree(L->d_state);
+  cudaFree(L->d_hist);
+  if (L->h_state) cudaFreeHost(L->h_state);
+  if (L->h_hist) cudaFreeHost(L->h_hist);
+  delete L;
+  P->loop_graph = nullptr;
+}
+
+static int loop_build(taps_problem* P, taps_factors* U, int prec, int solver, double res_tol, double als_tol,
+                      int max_sweeps) {
+  loop_destroy(P);
+  LoopGraph* L = new LoopGraph();
+  memset((void*)L, 0, sizeof(LoopGraph));
+  L->U = U;
+  L->M = U->M;
+  L->precision = prec;
+  L->solver = solver;
+  L->ws_M = P->ws_M;
+  L->max_sweeps = max_sweeps;
+  L->res_tol = res_tol;
+  L->als_tol = als_tol;
+  P->loop_graph = L;
+  int st = TAPS_OK;
+  do {
+    if ((st = taps_alloc((void**)&L->d_state, sizeof(int) * 4)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&L->d_hist, sizeof(double) * 2 * (size_t)max_sweeps)) != TAPS_OK) break;
+    if (cudaMallocHost((void**)&L->h_state, sizeof(int) * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&L->h_hist, sizeof(double) * 2 * (size_t)max_sweeps) != cudaSuccess) {
+      st = TAPS_ERR_OOM;
+      break;
+    }
+    if (cudaGraphCreate(&L->g, 0) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&L->h, L->g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      st = TAPS_ERR_CUDA;
+      break;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = L->h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, L->g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+      st = TAPS_ERR_CUDA;
+      break;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    LoopRanges rg;
+    memset(&rg, 0, sizeof(rg));
+    taps_als_partial_ranges(P, rg.cta0);
+    ProfState* S = P->prof;
+    long long l0[TAPS_PROF_NUM];
+    double f0[TAPS_PROF_NUM], b0[TAPS_PROF_NUM];
+    for (int c = 0; c < TAPS_PROF_NUM; ++c) { l0[c] = S->launches[c]; f0[c] = S->flops[c]; b0[c] = S->bytes[c]; }
+    cudaStream_t saved = P->stream;
+    P->stream = P->cap_stream;
+    S->capturing = true;
+    if (cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) {
+      st = TAPS_ERR_CUDA;
+    } else {
+      st = taps_sweep_enqueue(P, U, prec, solver, 1, 0);
+      if (st == TAPS_OK) st = taps_residual_enqueue(P, U, TAPS_RES_ALS, prec != TAPS_FP32, 0);
+      if (st == TAPS_OK) {
+        solve_decide_kernel<<<1, 32, 0, P->stream>>>(L->h, P->d_scal, U->M, P->D, P->d_partial, rg, res_tol, als_tol,
+                                                     max_sweeps, L->d_state, L->d_hist, max_sweeps, P->d_status);
+        if (cudaGetLastError() != cudaSuccess) st = TAPS_ERR_CUDA;
+      }
+      cudaGraph_t out = nullptr;
+      if (cudaStreamEndCapture(P->cap_stream, &out) != cudaSuccess) st = (st == TAPS_OK) ? TAPS_ERR_CUDA : st;
+    }
+    P->stream = saved;
+    S->capturing = false;
+    cudaGetLastError();
+    for (int c = 0; c < TAPS_PROF_NUM; ++c) {
+      L->dl[c] = S->launches[c] - l0[c];
+      L->dfl[c] = S->flops[c] - f0[c];
+      L->dby[c] = S->bytes[c] - b0[c];
+      S->launches[c] = l0[c];
+      S->flops[c] = f0[c];
+      S->bytes[c] = b0[c];
+    }
+    S->npending = 0;
+    if (st == TAPS_OK && cudaGraphInstantiate(&L->exec, L->g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      st = TAPS_ERR_CUDA;
+    }
+  } while (0);
+  if (st != TAPS_OK) L->failed = true;
+  return st;
+}
+
+// Runs up to max_sweeps sweeps on the device.  Returns TAPS_ERR_CUDA with *fallback = 1
+// when the loop graph is unavailable (the caller runs the host loop).  On return,
+// *done sweeps ran, hist_rho / hist_change (device order) hold their values.
+static int loop_solve(taps_problem* P, taps_factors* U, int prec, int solver, double res_tol, double als_tol,
+                      int max_sweeps, int* done, const double** hist, int* fallback) {
+  *fallback = 0;
+  *done = 0;
+  LoopGraph* L = (LoopGraph*)P->loop_graph;
+  bool match = L && L->U == U && L->M == U->M && L->precision == prec && L->solver == solver &&
+               L->ws_M == P->ws_M && L->max_sweeps == max_sweeps && L->res_tol == res_tol &&
+               L->als_tol == als_tol;
+  if (match && L->failed) {
+    *fallback = 1;
+    return TAPS_ERR_CUDA;
+  }
+  if (!match) {
+    if (taps_lu_needs_tuning(P, solver, U->M)) {   // the block-elimination tuner runs eagerly
+      *fallback = 1;
+      return TAPS_ERR_CUDA;
+    }
+    TAPS_TRY(taps_fd_prepare_all(P, solver));
+    if (loop_build(P, U, prec, solver, res_tol, als_tol, max_sweeps) != TAPS_OK) {
+      *fallback = 1;
+      return TAPS_ERR_CUDA;
+    }
+    L = (LoopGraph*)P->loop_graph;
+  }
+  cudaStream_t s = P->stream;
+  TAPS_CUDA(cudaMemsetAsync(L->d_state, 0, sizeof(int) * 4, s));
+  TAPS_CUDA(cudaGraphLaunch(L->exec, s));
+  TAPS_CUDA(cudaMemcpyAsync(L->h_state, L->d_state, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+  TAPS_CUDA(cudaMemcpyAsync(L->h_hist, L->d_hist, sizeof(double) * 2 * (size_t)max_sweeps, cudaMemcpyDeviceToHost,
+                            s));
+  TAPS_CUDA(cudaStreamSynchronize(s));
+  const int n = std::min(L->h_state[0], max_sweeps);
+  ProfState* S = P->prof;
+  for (int c = 0; c < TAPS_PROF_NUM; ++c) {
+    S->launches[c] += L->dl[c] * n;
+    S->flops[c] += L->dfl[c] * n;
+    S->bytes[c] += L->dby[c] * n;
+  }
+  *done = n;
+  *hist = L->h_hist;
+  if (L->h_state[1] != TAPS_DEV_OK) {
+    const int dev = L->h_state[1];
+    TAPS_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), s));
+    TAPS_CUDA(cudaStreamSynchronize(s));
+    return taps_status_from_device(dev);
+  }
+  if (!L->h_state[2]) return TAPS_ERR_NONFINITE;
+  return TAPS_OK;
+}
+
 // One sweep + residual through the cached graph (built on first use).  Returns
 // TAPS_ERR_CUDA with *fallback = 1 if capture is unavailable (caller runs eagerly).
 static int graph_sweep(taps_problem* P, taps_factors* U, int prec, int solver, int res_kind,
@@ -245,6 +460,7 @@ static void free_ws(taps_problem* P) {
     cudaFree(P->d_Usnap[d]);
     P->d_Usnap[d] = nullptr;
   }
+  loop_destroy(P);
   cudaFree(P->d_C);
   cudaFree(P->d_c);
   cudaFree(P->d_Call);
@@ -594,6 +810,34 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
   while (true) {
     double prev_rho = INFINITY;
     int prec = precision;
+    // FP64 / MIXED with graphs and the Eq. 42 residual: the whole sweep loop of this M
+    // on the device (no host round trip per sweep)
+    if (o->graphs == 2 && prec != TAPS_FP32 && o->res_kind == TAPS_RES_ALS && !P->prof->events) {
+      int done = 0, fallback = 0;
+      const double* dh = nullptr;
+      const int lst = loop_solve(P, U, prec, o->solver, o->res_tol, o->als_tol, o->max_sweeps, &done, &dh, &fallback);
+      if (!fallback) {
+        for (int j = 0; j < done; ++j) {
+          ++sweeps;
+          if (prec == TAPS_FP64) ++fp64_sweeps;
+          rho = dh[2 * j];
+          change = dh[2 * j + 1];
+          if (o->history_cap > 0 && rep && hist < o->history_cap) {
+            if (rep->hist_M) rep->hist_M[hist] = M;
+            if (rep->hist_change) rep->hist_change[hist] = change;
+            if (rep->hist_rho) rep->hist_rho[hist] = rho;
+            ++hist;
+          }
+        }
+        TAPS_TRY(lst);
+        if (rho <= o->res_tol) converged = true;
+        if (converged || M >= o->M_max) break;
+        TAPS_TRY(init_columns(P, U, M, M + 1, add_kind, o->seed));
+        U->M = ++M;
+        TAPS_TRY(taps_refresh_grams(P, U, precision));
+        continue;
+      }
+    }
     for (int it = 0; it < o->max_sweeps; ++it) {
       if (prec == TAPS_FP32) {
         for (int d = 0; d < P->D; ++d)

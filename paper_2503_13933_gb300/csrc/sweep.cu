@@ -672,7 +672,8 @@ static int coefficients(taps_problem* P, int d, int M) {
 // Kernels of one sweep (no host synchronisation: capturable in a CUDA graph).  The
 // per-column change / norm partials and the status word are copied to pinned host
 // memory at the end; taps_sweep_finish reads them after the stream has drained.
-int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize) {
+int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
+                       int host_copies) {
   int M = U->M;
   if (M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
@@ -697,6 +698,7 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
     TAPS_CUDA(cudaGetLastError());
     TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, d + 1 < P->D ? d + 1 : -1));
   }
+  if (!host_copies) return TAPS_OK;
   TAPS_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, sizeof(double) * 2 * M * P->D,
                             cudaMemcpyDeviceToHost, s));
   TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -937,7 +939,8 @@ __global__ void full_residual_combine_kernel(TermTable tt, BigGramPtrs bg, int M
 
 // Residual kernels (no host synchronisation); the partial sums land in pinned host
 // memory (P->h_part) for taps_residual_finish.  Returns the number of partials.
-int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current) {
+int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current,
+                          int host_copies) {
   int M = U->M;
   if (M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
@@ -977,6 +980,7 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     prof_end(P, TAPS_PROF_RESIDUAL, tk, fl, by);
     TAPS_CUDA(cudaGetLastError());
     size_t off = 2 * (size_t)rd.cta0[P->D];
+    if (!host_copies) return TAPS_OK;
     TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, off * sizeof(double), cudaMemcpyDeviceToHost, s));
     TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     return TAPS_OK;
@@ -1010,6 +1014,12 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
   TAPS_CUDA(cudaGetLastError());
   TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, 3 * nblk * sizeof(double), cudaMemcpyDeviceToHost, s));
   TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return TAPS_OK;
+}
+
+int taps_als_partial_ranges(const taps_problem* P, int* cta0) {
+  cta0[0] = 0;
+  for (int d = 0; d < P->D; ++d) cta0[d + 1] = cta0[d] + (P->dims[d]->nf + RR - 1) / RR;
   return TAPS_OK;
 }
 

@@ -146,6 +146,7 @@ struct taps_problem {
   int* h_status;      // pinned host mirror of the device status word
   cudaStream_t cap_stream;  // private stream used to capture sweep graphs
   void* graph;        // cached sweep graph (SweepGraph, api.cu)
+  void* loop_graph;   // cached device-side solve loop (LoopGraph, api.cu)
   double* d_Usnap[TAPS_MAX_DIMS];  // factor snapshot for the FP32 -> FP64 retry
   void* d_evalbuf;    // grow-only gathered rows of taps_eval_grid
   size_t evalbuf_len;
@@ -320,11 +321,17 @@ int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver,
                     double* change_out);
 int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double* rho_out,
                        int grams_current = 0);
-int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize);
+// host_copies = 0 leaves the change partials and the status word on the device (the
+// device-side solve loop reads them there).
+int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
+                       int host_copies = 1);
 int taps_sweep_finish(taps_problem* P, taps_factors* U, double* change_out);
 // grams_current: the FP64 Grams and source projections of every dim already belong to
 // U (true right after an FP64 or MIXED sweep), so the ALS residual does not refresh them.
-int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current = 0);
+int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current = 0,
+                          int host_copies = 1);
+// Per-dim ranges of the ALS residual's partial sums (CTA indices [cta0[d], cta0[d+1])).
+int taps_als_partial_ranges(const taps_problem* P, int* cta0);
 int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
 int taps_fd_prepare_all(taps_problem* P, int solver);
 int taps_lu_needs_tuning(const taps_problem* P, int solver, int M);

@@ -178,6 +178,29 @@ def test_graph_replay_matches_direct_launches(T, solver):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision,res_tol", [("fp64", 1e-7), ("fp64", -1.0), ("mixed", 1e-7)])
+def test_device_solve_loop_matches_host_loop(T, precision, res_tol):
+    """The solve loop run on the device (graphs = 2: a conditional WHILE graph node
+    repeating sweep, residual and decision) stops at the same sweep, with the same
+    history and the same factors bit for bit, as the host loop over per-sweep graphs
+    (graphs = 1); with mode growth M = 2 -> 4, stopping on the residual target or on
+    the sweep cap."""
+    desc = W.poisson_k(n_space=18, n_k=9, seed=2007)
+    prec = T.FP64 if precision == "fp64" else T.MIXED
+    out = []
+    for graphs in (2, 1):
+        P = T.Problem(desc)
+        U = P.factors(4)
+        r = P.solve(U, M0=2, M_max=4, res_tol=res_tol, als_tol=0.0, max_sweeps=12, precision=prec,
+                    init=T.INIT_RANDOM, seed=5, solver=T.SOLVER_FASTDIAG, graphs=graphs)
+        out.append((r, U.get()))
+    (ra, Ua), (rb, Ub) = out
+    assert ra["sweeps"] == rb["sweeps"] and ra["M"] == rb["M"] and ra["converged"] == rb["converged"]
+    assert ra["history"] == rb["history"]
+    for a, b in zip(Ua, Ub):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("name,M,nsw", [("poisson3d_n12", 3, 3), ("poisson_k_7x9", 4, 2),
                                         ("heat2d_robin", 5, 3)])
 def test_mixed_refined_small_solves_parity(T, name, M, nsw):
