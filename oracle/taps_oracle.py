@@ -438,6 +438,42 @@ def solve_fast_diag(prob: Problem, d, C, F):
     return Phi @ Y
 
 
+def mode_diag_pair(prob: Problem, d, C):
+    """Operator pair of dim d for diagonalisation on the mode side (Sec. 2.6: the
+    Sylvester form of the reduced system, cost M^3 + M^2 n_d + the banded solves):
+    returns (opX, opY), opX mass-like when the pair has one, if dim d has exactly two
+    operators and every other dim's operators are symmetric (then every Gram of the
+    other dims, and so every C_op of dim d, is symmetric); None otherwise."""
+    ops = list(C.keys())
+    if len(ops) != 2:
+        return None
+    for alpha, opk in prob.terms:
+        for e in range(prob.D):
+            if e != d and opk[e] == OP_G:
+                return None
+    mass = [o for o in ops if o in (OP_M, OP_W)]
+    x = mass[0] if mass else ops[0]
+    return x, [o for o in ops if o != x][0]
+
+
+def solve_mode_diag(prob: Problem, d, C, F):
+    """Diagonalisation on the mode side of Op_X U C_X + Op_Y U C_Y = F (C symmetric):
+    with the generalised eigenpairs C_Y w = lam C_X w (W^T C_X W = I, W^T C_Y W =
+    diag(lam); library symmetric-definite eigensolver), U = Z W^T where each column
+    solves the banded n_d x n_d system (Op_X + lam_j Op_Y) z_j = (F W)_j (library
+    dense solve)."""
+    import scipy.linalg
+    opX, opY = mode_diag_pair(prob, d, C)
+    CX = 0.5 * (C[opX] + C[opX].T)
+    CY = 0.5 * (C[opY] + C[opY].T)
+    lam, Wm = scipy.linalg.eigh(CY, CX)
+    G = F @ Wm
+    Z = np.zeros_like(G)
+    for j in range(G.shape[1]):
+        Z[:, j] = np.linalg.solve(prob.ops[d][opX] + lam[j] * prob.ops[d][opY], G[:, j])
+    return Z @ Wm.T
+
+
 def normalise_columns(Ud):
     """Unit 2-norm columns; sign makes the largest-magnitude entry positive.
     (Scale normalisation is not stated by the paper; the next dimension's solve
@@ -460,6 +496,10 @@ def sweep(prob: Problem, U, solver="banded"):
     For d = 1..D in order, with the other factors at their latest values
     (Gauss-Seidel), solve sum_op Op_d U_d C_op^T = F_d for U_d; normalise U_d for
     d < D.  Returns the new factors and max_d ||dU_d||_F / ||U_d||_F.
+
+    solver: "banded" (block elimination), "dense", "fastdiag" (node-side pencil where
+    the dim's operators allow, else mode-side where the coefficients allow, else
+    banded) or "modediag" (mode-side where allowed, else banded).
     """
     U = [u.copy() for u in U]
     change = 0.0
@@ -469,6 +509,8 @@ def sweep(prob: Problem, U, solver="banded"):
             Ud = solve_dense(reduced_matrix_dense(prob, d, C), F)
         elif solver == "fastdiag" and fast_diag_pencil(prob, d, C) is not None:
             Ud = solve_fast_diag(prob, d, C, F)
+        elif solver in ("fastdiag", "modediag") and mode_diag_pair(prob, d, C) is not None:
+            Ud = solve_mode_diag(prob, d, C, F)
         else:
             Ud = solve_block_banded(prob, d, C, F)
         if d < prob.D - 1:

@@ -43,6 +43,49 @@ def test_fast_diagonalisation_agrees_with_dense():
         assert used >= 2
 
 
+def test_mode_side_diagonalisation_agrees_with_dense():
+    """Diagonalisation on the mode side (the Sylvester form of Sec. 2.6, M x M
+    generalised eigenproblem + banded n_d x n_d solves) solves the same reduced system
+    as the dense Kronecker-assembled solve: transient time dims (G, M with symmetric
+    coefficients), also with convection faces on the space dims, and Poisson space dims
+    (K, M)."""
+    cases = (W.heat_transient(n_space=9, n_t=8, D_space=2, seed=3010),
+             W.heat_transient(n_space=8, n_t=7, D_space=2, h_conv=2.0, seed=3011),
+             W.poisson_sin(9, D=3))
+    used = {}
+    for k, desc in enumerate(cases):
+        P = O.problem_from_description(desc)
+        U = O.init_factors(P, 4, "random", 21 + k)
+        for d in range(P.D):
+            C, F = O.coefficients(P, U, d)
+            pair = O.mode_diag_pair(P, d, C)
+            if pair is None:
+                continue
+            used[(k, d)] = pair
+            Xd = O.solve_dense(O.reduced_matrix_dense(P, d, C), F)
+            Xm = O.solve_mode_diag(P, d, C, F)
+            assert np.max(np.abs(Xd - Xm)) < 1e-10 * np.max(np.abs(Xd)), (k, d)
+    # every time dim (ops G, M: mass-like X = M) and every Poisson dim was covered
+    assert used[(0, 2)] == (O.OP_M, O.OP_G) and used[(1, 2)] == (O.OP_M, O.OP_G)
+    assert all((2, d) in used for d in range(3))
+    # space dims of a transient problem carry the nonsymmetric time Gram: not eligible
+    assert (0, 0) not in used and (1, 0) not in used
+
+
+def test_mode_side_sweeps_follow_block_elimination():
+    """Three sweeps with the mode-side solver where it applies give the factors of
+    three block-elimination sweeps from the same start."""
+    P = O.problem_from_description(W.heat_transient(n_space=8, n_t=9, D_space=2, seed=3012))
+    U0 = O.init_factors(P, 3, "random", 4)
+    Ua, Ub = [u.copy() for u in U0], [u.copy() for u in U0]
+    for _ in range(3):
+        Ua, ca = O.sweep(P, Ua, solver="modediag")
+        Ub, cb = O.sweep(P, Ub, solver="banded")
+    for a, b in zip(Ua, Ub):
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
+    assert abs(ca - cb) <= 1e-8 * max(cb, 1.0)
+
+
 def test_reduced_system_is_the_galerkin_condition():
     """The reduced solve makes the dim-d Galerkin residual of the FULL system vanish:
     for every test direction dU (x) prod_{e!=d} U_e[:,m], <dU-test, F - A u> = 0."""
