@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-space", type=int, default=WORKLOAD["n_space"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=32, help="instances of the batched measurement (0: off)")
-    ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp32gram_fastdiag,mixed_fastdiag,mixed_fastdiag_mlp",
+    ap.add_argument("--batch", type=int, default=256, help="instances of the batched measurement (0: off)")
+    ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,mixed_fastdiag,"
+                                       "mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
     return ap.parse_args()
 
@@ -249,6 +250,7 @@ def run_ours(args, rank, world, local):
     # plain FP64 path (block-banded elimination) and the fast paths
     paths = {"fp64": (taps.FP64, taps.SOLVER_BLOCK_LU),
              "fp64_fastdiag": (taps.FP64, taps.SOLVER_FASTDIAG),
+             "fp64_modediag": (taps.FP64, taps.SOLVER_MODEDIAG),
              "fp32gram_fastdiag": (taps.FP32, taps.SOLVER_FASTDIAG),
              "mixed_fastdiag": (taps.MIXED, taps.SOLVER_FASTDIAG),
              "mixed_fastdiag_mlp": (taps.MIXED, taps.SOLVER_FASTDIAG, "mlp")}
@@ -315,16 +317,21 @@ def run_ours(args, rank, world, local):
     # host description, seeded initial factors copied in, solve, factors copied out.
     U0 = W.random_factors(desc, M, seed=seed)
     h2d = sum(u.nbytes for u in U0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    P2 = taps.Problem(desc)
-    U2 = P2.factors(M)
-    U2.set(U0)
-    rep2 = P2.solve(U2, M_max=M, res_tol=WORKLOAD["res_tol"], res_kind=taps.RES_ALS,
-                    max_sweeps=60, precision=taps.FP64, init=taps.INIT_GIVEN, als_tol=0.0,
-                    solver=taps.SOLVER_FASTDIAG)
-    Uout = U2.get()
-    e2e_s = time.perf_counter() - t0
+
+    def end_to_end(solver):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P2 = taps.Problem(desc)
+        U2 = P2.factors(M)
+        U2.set(U0)
+        rep2 = P2.solve(U2, M_max=M, res_tol=WORKLOAD["res_tol"], res_kind=taps.RES_ALS,
+                        max_sweeps=60, precision=taps.FP64, init=taps.INIT_GIVEN, als_tol=0.0,
+                        solver=solver)
+        Uout = U2.get()
+        return time.perf_counter() - t0, rep2, Uout
+
+    e2e_s, rep2, Uout = end_to_end(taps.SOLVER_FASTDIAG)
+    e2e_md_s, rep_md, _ = end_to_end(taps.SOLVER_MODEDIAG)   # no n_d x n_d pencil set-up
     d2h = sum(u.nbytes for u in Uout) + 8
 
     best = headline if res[headline]["converged"] else \
@@ -371,11 +378,12 @@ def run_ours(args, rank, world, local):
 
     batched = None
     if args.batch > 0:
-        # independent seeded instances (D 3..6, n_d 32..128, M 4..16, Poisson/transient):
-        # 10 sweeps each, all instances as one graph per sweep vs one launch sequence
-        # per instance in turn
-        descs, Ms = W.batch_instances(count=args.batch, seed=4000 + 1000 * rank, n_lo=32, n_hi=128,
-                                      M_lo=4, M_hi=16)
+        # independent seeded instances (D 3..6, n_d 32..1024, M 4..32, Poisson/transient
+        # 50/50, 1..4 Gaussian sources): 10 fixed-M sweeps each, all instances as one CUDA
+        # graph per sweep (solver chosen by the batch's tuner) vs one launch sequence per
+        # instance in turn with the same kernels
+        descs, Ms = W.batch_instances(count=args.batch, seed=4000 + 1000 * rank, n_lo=32, n_hi=1024,
+                                      M_lo=4, M_hi=32)
         bp, bu, b0 = [], [], []
         for i, (dsc, Mi) in enumerate(zip(descs, Ms)):
             Pi = taps.Problem(dsc, stream=taps.ctypes.c_void_p(torch.cuda.Stream().cuda_stream))
@@ -385,25 +393,47 @@ def run_ours(args, rank, world, local):
             bp.append(Pi)
             bu.append(Ui)
             b0.append(U0i)
-        times = {}
-        for mode in ("graph", "per_instance"):
-            Bt = taps.Batch(bp, bu, solver=taps.SOLVER_FASTDIAG)
-            for _ in range(2):
-                for Ui, U0i in zip(bu, b0):
-                    Ui.set(U0i)
-                Bt.sweep(10, graphs=(mode == "graph"))
+
+        def reset():
             for Ui, U0i in zip(bu, b0):
                 Ui.set(U0i)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            Bt.sweep(10, graphs=(mode == "graph"))
-            torch.cuda.synchronize()
-            times[mode] = time.perf_counter() - t0
-        batched = dict(instances=args.batch, sweeps=10, dims=[len(d["dims"]) for d in descs][:8],
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Bt = taps.Batch(bp, bu, solver=taps.SOLVER_AUTO)
+        torch.cuda.synchronize()
+        create_s = time.perf_counter() - t0
+        times, failed = {}, {}
+        for mode in ("graph", "per_instance"):
+            reset()
+            Bt.sweep(1, graphs=(mode == "graph"), statuses=True)   # capture / tuning / warm-up
+            reps = 3 if mode == "graph" else 1
+            ts = []
+            for _ in range(reps):
+                reset()
+                t0 = time.perf_counter()
+                ch, st = Bt.sweep(10, graphs=(mode == "graph"), statuses=True)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            times[mode] = min(ts)
+            failed[mode] = int(np.sum(st != 0))
+        chosen, trial = Bt.info()
+        transient = sum(1 for d in descs if any(dm["kind"] == W.TIME for dm in d["dims"]))
+        batched = dict(instances=args.batch, sweeps=10, transient=transient,
+                       n_d="U[32,1024]", M="U[4,32]", D="U{3..6}", setup_s=create_s,
+                       solver={taps.SOLVER_FASTDIAG: "fastdiag", taps.SOLVER_MODEDIAG: "modediag"}.get(chosen),
+                       tuner_trial_ms=dict(fastdiag=trial[0], modediag=trial[1]),
                        graph_s=times["graph"], per_instance_s=times["per_instance"],
                        instances_per_s=args.batch / times["graph"],
+                       instance_sweeps_per_s=10 * args.batch / times["graph"],
                        instances_per_s_per_instance_launches=args.batch / times["per_instance"],
-                       speedup=times["per_instance"] / times["graph"])
+                       speedup=times["per_instance"] / times["graph"],
+                       numerically_singular=failed["graph"],
+                       note="fixed-M sweeps from random factors; instances whose factors become "
+                            "numerically rank deficient report TAPS_ERR_SINGULAR and still run "
+                            "every sweep in both launch styles")
+        del Bt
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -434,6 +464,8 @@ def run_ours(args, rank, world, local):
         cpu_baseline=cpu,
         e2e=dict(value=e2e_s, unit="s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                  converged=rep2["converged"]),
+        e2e_modediag=dict(value=allmax(e2e_md_s, world), unit="s", sweeps=rep_md["sweeps"],
+                          converged=rep_md["converged"]),
         gpu_launches=launches,
         warm_start=ws_info,
         batched=batched,

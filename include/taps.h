@@ -96,7 +96,20 @@ extern "C" {
 #define TAPS_SOLVER_BLOCK_LU 0   /* block-banded Gaussian elimination, FP64 */
 #define TAPS_SOLVER_FASTDIAG 1   /* fast diagonalisation (Sec. 2.6) for every dimension whose
                                     operators form a symmetric pencil with a mass-like partner
-                                    (K/M, W, ...); block LU for the others (e.g. time) */
+                                    (K/M, W, ...: n_d x n_d pencil, n_d small M x M solves);
+                                    else, for a dimension with two operators whose coefficient
+                                    matrices are symmetric (every other dimension's operators
+                                    symmetric, e.g. the time dimension of a transient problem)
+                                    and M <= 32, diagonalisation on the mode side (M x M
+                                    pencil, M banded n_d x n_d solves); block LU otherwise */
+#define TAPS_SOLVER_MODEDIAG 2   /* diagonalisation on the mode side wherever it applies (one or
+                                    two operators, symmetric coefficients, M <= 32, band
+                                    half-width <= 5): no n_d x n_d decomposition, cost
+                                    O(M^3 + M^2 n_d + banded solves) per dimension; else as
+                                    TAPS_SOLVER_FASTDIAG */
+#define TAPS_SOLVER_AUTO 3       /* batches only: the first graph sweep times one sweep of the
+                                    batch with FASTDIAG and with MODEDIAG (factors restored)
+                                    and keeps the faster */
 
 typedef struct taps_dim taps_dim;
 typedef struct taps_problem taps_problem;
@@ -301,13 +314,24 @@ int taps_eval_points(const taps_problem* prob, const taps_factors* U, int n_pts,
  * With graphs = 1, one sweep of every instance is captured once as one CUDA graph
  * (instances on their own streams, forked from and joined to the batch's stream)
  * and replayed n_sweeps times; otherwise each instance runs its own launch sequence
- * in turn.  changes_out (count values, optional) receives each instance's factor
- * change of its last sweep.  The pointers must outlive the batch.  Errors as
- * taps_sweep, TAPS_ERR_INVALID_ARG for a shared problem or empty factors. */
+ * in turn.  Every instance's Grams are first recomputed from its current factors.
+ * changes_out (count values, optional) receives each instance's factor change of its
+ * last sweep.  status_out (count values, optional) receives each instance's status
+ * (the first numerical error of its sweeps, e.g. TAPS_ERR_SINGULAR when fixed-M sweeps
+ * have made its factors numerically rank deficient); every instance runs all
+ * n_sweeps regardless, and with status_out given the call returns TAPS_OK unless a
+ * launch fails.  Without status_out the first instance error is returned.  The
+ * pointers must outlive the batch.  Errors as taps_sweep, TAPS_ERR_INVALID_ARG for a
+ * shared problem or empty factors.  Pencil decompositions are made at creation, in
+ * waves of instances whose kernels run concurrently on the instances' streams. */
 typedef struct taps_batch taps_batch;
 int taps_batch_create(taps_problem* const* probs, taps_factors* const* Us, int count, int precision,
                       int solver, taps_batch** out);
-int taps_batch_sweep(taps_batch* batch, int n_sweeps, int graphs, double* changes_out);
+int taps_batch_sweep(taps_batch* batch, int n_sweeps, int graphs, double* changes_out, int* status_out);
+/* The solver a batch's sweeps use (for TAPS_SOLVER_AUTO the tuner's choice, made by the
+ * first graph sweep) and the tuner's two trial times in ms (FASTDIAG, MODEDIAG; -1
+ * before tuning or without AUTO).  Either pointer may be NULL. */
+int taps_batch_info(const taps_batch* batch, int* solver_out, float* trial_ms_out);
 void taps_batch_destroy(taps_batch* batch);
 
 /* ---- learned warm start (the paper's Algorithm 1 starts from random values) ------
@@ -363,7 +387,9 @@ int taps_factors_from_profiles(const taps_problem* prob, taps_factors* U, int M,
 #define TAPS_PROF_OTHER 8         /* initialisation, pencil set-up, copies           */
 #define TAPS_PROF_FASTDIAG 9      /* fast diagonalisation: the n small M x M solves  */
 #define TAPS_PROF_FD_TRANSFORM 10 /* fast diagonalisation: back to the nodal basis   */
-#define TAPS_PROF_NUM 11
+#define TAPS_PROF_MODEDIAG 11     /* mode-side diagonalisation: M x M eigenproblem,
+                                     banded solves, transform                       */
+#define TAPS_PROF_NUM 12
 int taps_profile_reset(taps_problem* prob, int enable_events);
 int taps_profile_get(taps_problem* prob, int kernel_class, long long* launches, double* ms,
                      double* flops, double* bytes);

@@ -346,7 +346,7 @@ static int loop_solve(taps_problem* P, taps_factors* U, int prec, int solver, do
       *fallback = 1;
       return TAPS_ERR_CUDA;
     }
-    TAPS_TRY(taps_fd_prepare_all(P, solver));
+    TAPS_TRY(taps_fd_prepare_all(P, solver, U->M));
     if (loop_build(P, U, prec, solver, res_tol, als_tol, max_sweeps) != TAPS_OK) {
       *fallback = 1;
       return TAPS_ERR_CUDA;
@@ -396,7 +396,7 @@ static int graph_sweep(taps_problem* P, taps_factors* U, int prec, int solver, i
     return TAPS_ERR_CUDA;
   }
   if (!match) {
-    TAPS_TRY(taps_fd_prepare_all(P, solver));
+    TAPS_TRY(taps_fd_prepare_all(P, solver, U->M));
     if (graph_build(P, U, prec, solver, res_kind) != TAPS_OK) {
       *fallback = 1;
       return TAPS_ERR_CUDA;
@@ -473,6 +473,8 @@ static void free_ws(taps_problem* P) {
   cudaFree(P->d_lu);
   cudaFree(P->d_Y);
   cudaFree(P->d_Uold);
+  cudaFree(P->d_md);
+  P->d_md = nullptr;
   cudaFree(P->d_partial);
   cudaFree(P->d_scal);
   cudaFree(P->d_bigG);
@@ -546,6 +548,8 @@ int taps_ws_ensure(taps_problem* P, int M) {
   TAPS_TRY(taps_alloc((void**)&P->d_lu, sizeof(double) * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_Y, sizeof(double) * TAPS_NUM_OPS * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_Uold, sizeof(double) * nfm * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_md, sizeof(double) * taps_md_scratch_doubles(nfm, M, P->Rf)));
+  TAPS_CUDA(cudaMemsetAsync(P->d_md, 0, sizeof(double) * taps_md_scratch_doubles(nfm, M, P->Rf), P->stream));
   TAPS_TRY(taps_alloc((void**)&P->d_partial, sizeof(double) * part));
   TAPS_TRY(taps_alloc((void**)&P->d_scal, sizeof(double) * 2 * M * D + 64));
   TAPS_TRY(taps_alloc((void**)&P->d_bigG, sizeof(double) * bigG));
@@ -761,9 +765,10 @@ extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const 
   int solver = opts ? opts->solver : TAPS_SOLVER_BLOCK_LU;
   int normalize = opts ? opts->normalize : 1;
   if (precision != TAPS_FP64 && precision != TAPS_FP32 && precision != TAPS_MIXED) return TAPS_ERR_INVALID_ARG;
-  if (solver != TAPS_SOLVER_BLOCK_LU && solver != TAPS_SOLVER_FASTDIAG) return TAPS_ERR_INVALID_ARG;
+  if (solver < TAPS_SOLVER_BLOCK_LU || solver > TAPS_SOLVER_MODEDIAG) return TAPS_ERR_INVALID_ARG;
   double t0 = now_s();
   TAPS_TRY(taps_ws_ensure(P, U->M));
+  TAPS_TRY(taps_md_reset(P));
   TAPS_TRY(taps_refresh_grams(P, U, precision));
   double change = 0.0;
   for (int it = 0; it < n_sweeps; ++it) TAPS_TRY(taps_sweep_impl(P, U, precision, solver, normalize, &change));
@@ -789,7 +794,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       (o->precision != TAPS_FP64 && o->precision != TAPS_FP32 && o->precision != TAPS_MIXED) ||
       (o->res_kind != TAPS_RES_ALS && o->res_kind != TAPS_RES_FULL) ||
       o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO ||
-      (o->solver != TAPS_SOLVER_BLOCK_LU && o->solver != TAPS_SOLVER_FASTDIAG))
+      o->solver < TAPS_SOLVER_BLOCK_LU || o->solver > TAPS_SOLVER_MODEDIAG)
     return TAPS_ERR_INVALID_ARG;
   double t0 = now_s();
   if (o->init != TAPS_INIT_GIVEN) {
@@ -802,6 +807,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
   int add_kind = (o->init == TAPS_INIT_GIVEN) ? TAPS_INIT_RANDOM : o->init;
   int M = U->M;
   TAPS_TRY(taps_ws_ensure(P, o->M_max));
+  TAPS_TRY(taps_md_reset(P));
   int precision = o->precision;
   TAPS_TRY(taps_refresh_grams(P, U, precision));
   int sweeps = 0, fp64_sweeps = 0, polish_left = o->polish_sweeps, hist = 0;
@@ -1174,6 +1180,9 @@ extern "C" int taps_eval_grid(const taps_problem* Pc, const taps_factors* U, con
 // ---------------------------------------------------------------------------------
 struct taps_batch {
   int count, precision, solver;
+  int eff_solver;     // the solver the sweeps use (AUTO: the tuner's choice)
+  int tuned;
+  float trial_ms[2];  // AUTO: one graph sweep with FASTDIAG, with MODEDIAG
   taps_problem** P;
   taps_factors** U;
   cudaStream_t master;
@@ -1202,7 +1211,7 @@ extern "C" void taps_batch_destroy(taps_batch* B) {
 extern "C" int taps_batch_create(taps_problem* const* probs, taps_factors* const* Us, int count, int precision,
                                  int solver, taps_batch** out) {
   if (!probs || !Us || !out || count < 1 || (precision != TAPS_FP64 && precision != TAPS_MIXED) ||
-      (solver != TAPS_SOLVER_BLOCK_LU && solver != TAPS_SOLVER_FASTDIAG))
+      solver < TAPS_SOLVER_BLOCK_LU || solver > TAPS_SOLVER_AUTO)
     return TAPS_ERR_INVALID_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
@@ -1215,6 +1224,7 @@ extern "C" int taps_batch_create(taps_problem* const* probs, taps_factors* const
   B->count = count;
   B->precision = precision;
   B->solver = solver;
+  B->eff_solver = solver == TAPS_SOLVER_AUTO ? TAPS_SOLVER_FASTDIAG : solver;
   B->P = new taps_problem*[count];
   B->U = new taps_factors*[count];
   for (int i = 0; i < count; ++i) { B->P[i] = probs[i]; B->U[i] = Us[i]; }
@@ -1226,13 +1236,26 @@ extern "C" int taps_batch_create(taps_problem* const* probs, taps_factors* const
     memset(B->join, 0, sizeof(cudaEvent_t) * count);
     for (int i = 0; i < count && st == TAPS_OK; ++i)
       if (cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) != cudaSuccess) st = TAPS_ERR_CUDA;
+    // pencil decompositions in waves of instances, each instance on its own stream,
+    // so that the small-grid kernels of different instances share the GPU
+    const int wave = 32;
+    std::vector<FdPending> pend;
+    for (int i0 = 0; i0 < count && st == TAPS_OK; i0 += wave) {
+      const int i1 = std::min(count, i0 + wave);
+      for (int i = i0; i < i1 && st == TAPS_OK; ++i) {
+        if ((st = taps_ws_ensure(B->P[i], B->U[i]->M)) != TAPS_OK) break;
+        // FASTDIAG's pencils cover MODEDIAG's (the dims it cannot solve on the mode side)
+        st = taps_fd_prepare_enqueue(B->P[i], B->eff_solver, B->U[i]->M, &pend);
+      }
+      int s2 = taps_fd_prepare_finish(&pend);
+      if (st == TAPS_OK) st = s2;
+    }
     for (int i = 0; i < count && st == TAPS_OK; ++i) {
       taps_problem* P = B->P[i];
-      if ((st = taps_ws_ensure(P, B->U[i]->M)) != TAPS_OK) break;
-      if ((st = taps_fd_prepare_all(P, solver)) != TAPS_OK) break;
       if ((st = taps_refresh_grams(P, B->U[i], TAPS_FP64)) != TAPS_OK) break;
-      if (cudaStreamSynchronize(P->stream) != cudaSuccess) st = TAPS_ERR_CUDA;
     }
+    for (int i = 0; i < count && st == TAPS_OK; ++i)
+      if (cudaStreamSynchronize(B->P[i]->stream) != cudaSuccess) st = TAPS_ERR_CUDA;
   } while (0);
   if (st != TAPS_OK) {
     taps_batch_destroy(B);
@@ -1255,7 +1278,7 @@ static int batch_capture(taps_batch* B) {
     bool cap = P->prof->capturing;
     P->prof->capturing = true;    // no event-pool growth or synchronisation inside capture
     cudaStreamWaitEvent(P->cap_stream, B->fork, 0);
-    if (st == TAPS_OK) st = taps_sweep_enqueue(P, B->U[i], B->precision, B->solver, 1);
+    if (st == TAPS_OK) st = taps_sweep_enqueue(P, B->U[i], B->precision, B->eff_solver, 1);
     cudaEventRecord(B->join[i], P->cap_stream);
     cudaStreamWaitEvent(B->master, B->join[i], 0);
     P->prof->capturing = cap;
@@ -1281,24 +1304,137 @@ static int batch_capture(taps_batch* B) {
   return st;
 }
 
-extern "C" int taps_batch_sweep(taps_batch* B, int n_sweeps, int graphs, double* changes_out) {
+static void batch_drop_graph(taps_batch* B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->g) cudaGraphDestroy(B->g);
+  B->exec = nullptr;
+  B->g = nullptr;
+}
+
+// Joins every instance's stream into the batch's stream.
+static int batch_join(taps_batch* B) {
+  for (int i = 0; i < B->count; ++i) {
+    TAPS_CUDA(cudaEventRecord(B->join[i], B->P[i]->stream));
+    TAPS_CUDA(cudaStreamWaitEvent(B->master, B->join[i], 0));
+  }
+  return TAPS_OK;
+}
+
+// TAPS_SOLVER_AUTO: one graph sweep of the whole batch with each candidate solver,
+// timed with events on the batch's stream; every instance's factors, Grams and status
+// are restored after each trial.  The faster candidate is kept.
+static int batch_autotune(taps_batch* B) {
+  size_t tot = 0;
+  for (int i = 0; i < B->count; ++i)
+    for (int d = 0; d < B->P[i]->D; ++d) tot += (size_t)B->P[i]->dims[d]->nf * B->U[i]->M;
+  double* backup = nullptr;
+  TAPS_TRY(taps_alloc((void**)&backup, sizeof(double) * std::max(tot, (size_t)1)));
+  auto copy_all = [&](bool save) -> int {
+    size_t off = 0;
+    for (int i = 0; i < B->count; ++i)
+      for (int d = 0; d < B->P[i]->D; ++d) {
+        const size_t len = (size_t)B->P[i]->dims[d]->nf * B->U[i]->M;
+        double* dev = B->U[i]->d_U[d];
+        TAPS_CUDA(cudaMemcpyAsync(save ? backup + off : dev, save ? dev : backup + off, sizeof(double) * len,
+                                  cudaMemcpyDeviceToDevice, B->P[i]->stream));
+        off += len;
+      }
+    return TAPS_OK;
+  };
+  const int cands[2] = {TAPS_SOLVER_FASTDIAG, TAPS_SOLVER_MODEDIAG};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = TAPS_OK, best = TAPS_SOLVER_FASTDIAG;
+  float best_ms = 1e30f;
+  do {
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+    if ((st = copy_all(true)) != TAPS_OK) break;
+    for (int k = 0; k < 2 && st == TAPS_OK; ++k) {
+      batch_drop_graph(B);
+      B->eff_solver = cands[k];
+      if ((st = batch_capture(B)) != TAPS_OK) break;
+      if (cudaGraphUpload(B->exec, B->master) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+      if ((st = batch_join(B)) != TAPS_OK) break;
+      cudaEventRecord(e0, B->master);
+      if (cudaGraphLaunch(B->exec, B->master) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+      cudaEventRecord(e1, B->master);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      B->trial_ms[k] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cands[k];
+      }
+      for (int i = 0; i < B->count; ++i) {   // consume the trial's status words
+        double ch = 0.0;
+        if (taps_sweep_finish(B->P[i], B->U[i], &ch) == TAPS_ERR_CUDA) st = TAPS_ERR_CUDA;
+      }
+      if (st != TAPS_OK || (st = copy_all(false)) != TAPS_OK) break;
+      for (int i = 0; i < B->count && st == TAPS_OK; ++i) {
+        if ((st = taps_md_reset(B->P[i])) == TAPS_OK) st = taps_refresh_grams(B->P[i], B->U[i], TAPS_FP64);
+      }
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (int i = 0; i < B->count; ++i) cudaStreamSynchronize(B->P[i]->stream);
+  cudaFree(backup);
+  if (st != TAPS_OK) return st;
+  if (B->eff_solver != best) {
+    batch_drop_graph(B);
+    B->eff_solver = best;
+  }
+  B->tuned = 1;
+  return TAPS_OK;
+}
+
+extern "C" int taps_batch_info(const taps_batch* B, int* solver_out, float* trial_ms_out) {
+  if (!B) return TAPS_ERR_INVALID_ARG;
+  if (solver_out) *solver_out = B->eff_solver;
+  if (trial_ms_out) {
+    trial_ms_out[0] = B->tuned ? B->trial_ms[0] : -1.f;
+    trial_ms_out[1] = B->tuned ? B->trial_ms[1] : -1.f;
+  }
+  return TAPS_OK;
+}
+
+extern "C" int taps_batch_sweep(taps_batch* B, int n_sweeps, int graphs, double* changes_out, int* status_out) {
   if (!B || n_sweeps < 1) return TAPS_ERR_INVALID_ARG;
+  if (graphs && B->solver == TAPS_SOLVER_AUTO && !B->tuned) TAPS_TRY(batch_autotune(B));
+  // the factors may have been set since the last call: every instance's Grams are
+  // recomputed from its current factors first (as taps_sweep does)
+  for (int i = 0; i < B->count; ++i) {
+    TAPS_TRY(taps_md_reset(B->P[i]));
+    TAPS_TRY(taps_refresh_grams(B->P[i], B->U[i], TAPS_FP64));
+  }
+  int first = TAPS_OK;
+  auto note = [&](int i, int st, double ch) {
+    if (changes_out) changes_out[i] = ch;
+    if (status_out) status_out[i] = st;
+    if (first == TAPS_OK) first = st;
+  };
   if (graphs) {
     TAPS_TRY(batch_capture(B));
+    TAPS_TRY(batch_join(B));
     for (int it = 0; it < n_sweeps; ++it) TAPS_CUDA(cudaGraphLaunch(B->exec, B->master));
     TAPS_CUDA(cudaStreamSynchronize(B->master));
     for (int i = 0; i < B->count; ++i) {
       double ch = 0.0;
-      TAPS_TRY(taps_sweep_finish(B->P[i], B->U[i], &ch));
-      if (changes_out) changes_out[i] = ch;
+      const int st = taps_sweep_finish(B->P[i], B->U[i], &ch);
+      if (st == TAPS_ERR_CUDA) return st;
+      note(i, st, st == TAPS_OK ? ch : NAN);
     }
-    return TAPS_OK;
+  } else {
+    for (int i = 0; i < B->count; ++i) {
+      double ch = 0.0;
+      int sti = TAPS_OK;
+      for (int it = 0; it < n_sweeps; ++it) {   // all sweeps run, as in the graph
+        const int st = taps_sweep_impl(B->P[i], B->U[i], B->precision, B->eff_solver, 1, &ch);
+        if (st == TAPS_ERR_CUDA) return st;
+        if (sti == TAPS_OK) sti = st;
+      }
+      note(i, sti, sti == TAPS_OK ? ch : NAN);
+    }
   }
-  for (int i = 0; i < B->count; ++i) {
-    double ch = 0.0;
-    for (int it = 0; it < n_sweeps; ++it)
-      TAPS_TRY(taps_sweep_impl(B->P[i], B->U[i], B->precision, B->solver, 1, &ch));
-    if (changes_out) changes_out[i] = ch;
-  }
-  return TAPS_OK;
+  return status_out ? TAPS_OK : first;
 }

@@ -964,10 +964,29 @@ int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB) {
   return 1;
 }
 
-static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, FdEntry** out) {
+static void fd_pending_free(FdPending& T) {
+  cudaFree(T.A);
+  cudaFree(T.B);
+  cudaFree(T.V);
+  cudaFree(T.tmp);
+  cudaFree(T.bt);
+  cudaFree(T.dd);
+  cudaFree(T.ee);
+  cudaFree(T.lam);
+  cudaFree(T.W);
+  memset(&T, 0, sizeof(T));
+}
+
+// Enqueues the decomposition of the pencil (opA, opB) of dm on P's stream without
+// waiting for it: the entry is registered at once (pending, with an event recorded
+// after its last kernel) and the temporaries are returned in *T for fd_finish.  An
+// entry that already exists, pending on another stream, makes P's stream wait for it.
+static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry** out, FdPending* T) {
+  memset(T, 0, sizeof(*T));
   for (int k = 0; k < dm->nfd; ++k)
     if (dm->fd[k].opA == opA && dm->fd[k].opB == opB) {
       *out = &dm->fd[k];
+      if (dm->fd[k].pending && dm->fd[k].done) TAPS_CUDA(cudaStreamWaitEvent(P->stream, dm->fd[k].done, 0));
       return dm->fd[k].status;
     }
   if (dm->nfd >= 4) return TAPS_ERR_INVALID_ARG;
@@ -978,10 +997,10 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
   int n = dm->nf;
   size_t nn = (size_t)n * n;
   cudaStream_t s = P->stream;
-  double *A = nullptr, *B = nullptr, *V = nullptr, *tmp = nullptr, *bt = nullptr, *dd = nullptr, *ee = nullptr;
-  double *lam = nullptr, *W = nullptr;
   const int hasA = opA >= 0 ? 1 : 0;
   int st = TAPS_OK;
+  T->E = &E;
+  T->P = P;
   do {
     // the back-transform keeps one column per warp in shared memory (n <= 6144); the
     // tridiagonalisation stages three vectors (3n doubles)
@@ -998,17 +1017,18 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
     if ((st = taps_alloc((void**)&E.Phi, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.PhiT, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.mu, sizeof(double) * n)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&A, sizeof(double) * nn)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&B, sizeof(double) * nn)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&V, sizeof(double) * nn)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&tmp, sizeof(double) * 2 * n)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&bt, sizeof(double) * n)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&dd, sizeof(double) * n)) != TAPS_OK) break;
-    if ((st = taps_alloc((void**)&ee, sizeof(double) * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->A, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->B, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->V, sizeof(double) * nn)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->tmp, sizeof(double) * 2 * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->bt, sizeof(double) * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->dd, sizeof(double) * n)) != TAPS_OK) break;
+    if ((st = taps_alloc((void**)&T->ee, sizeof(double) * n)) != TAPS_OK) break;
     if (hasA) {
-      if ((st = taps_alloc((void**)&lam, sizeof(double) * n)) != TAPS_OK) break;
-      if ((st = taps_alloc((void**)&W, sizeof(double) * 5 * nn)) != TAPS_OK) break;
+      if ((st = taps_alloc((void**)&T->lam, sizeof(double) * n)) != TAPS_OK) break;
+      if ((st = taps_alloc((void**)&T->W, sizeof(double) * 5 * nn)) != TAPS_OK) break;
     }
+    double *A = T->A, *B = T->B, *V = T->V, *W = T->W, *lam = T->lam;
     const size_t bsz = (size_t)n * dm->nb;
     const double* bandA = hasA ? dm->d_band + (size_t)opA * bsz : nullptr;
     const double* bandB = dm->d_band + (size_t)opB * bsz;
@@ -1021,15 +1041,16 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
       const size_t dsm = sizeof(double) * ((size_t)((n + TD_CTAS - 1) / TD_CTAS) * n + 3 * (size_t)n);
       if (dsm + 1024 <= (size_t)maxsm_optin) {   // S fits the cluster's shared memory
         if ((st = taps_allow_dyn_smem((const void*)fd_tridiag_dsmem_kernel, maxsm_optin)) != TAPS_OK) break;
-        fd_tridiag_dsmem_kernel<<<TD_CTAS, TD_THREADS, dsm, s>>>(A, V, bt, dd, ee, n);
+        fd_tridiag_dsmem_kernel<<<TD_CTAS, TD_THREADS, dsm, s>>>(A, V, T->bt, T->dd, T->ee, n);
       } else {
-        fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, tmp, bt, dd, ee, n);
+        fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, T->tmp, T->bt,
+                                                                                      T->dd, T->ee, n);
       }
       // eigenvalues (warp each), eigenvectors (thread each), back-transform (warp each),
       // all into A, which the tridiagonalisation no longer needs
       // two warps per CTA: the warps' FP64 chains spread over the SMs' sub-partitions
-      fd_bisect_kernel<<<(unsigned)((32LL * n + 63) / 64), 64, 0, s>>>(dd, ee, n, lam);
-      fd_invit_kernel<<<(n + 127) / 128, 128, 0, s>>>(dd, ee, lam, n, A, W);
+      fd_bisect_kernel<<<(unsigned)((32LL * n + 63) / 64), 64, 0, s>>>(T->dd, T->ee, n, lam);
+      fd_invit_kernel<<<(n + 127) / 128, 128, 0, s>>>(T->dd, T->ee, lam, n, A, W);
       // symmetric orthogonalisation: E in W, the corrected vectors back into A
       const unsigned gnn = (unsigned)((nn + 255) / 256);
       fd_gram_minus_identity_kernel<<<gnn, 256, 0, s>>>(A, n, W);
@@ -1039,8 +1060,8 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
         break;
       }
       const int wpc = std::max(1, std::min(8, (int)(48 * 1024 / (sizeof(double) * (size_t)n))));
-      fd_backtransform_kernel<<<(n + wpc - 1) / wpc, 32 * wpc, sizeof(double) * (size_t)n * wpc, s>>>(V, bt, n,
-                                                                                                      A);
+      fd_backtransform_kernel<<<(n + wpc - 1) / wpc, 32 * wpc, sizeof(double) * (size_t)n * wpc, s>>>(
+          V, T->bt, n, A);
     }
     fd_phi_kernel<<<(n + 127) / 128, 128, 0, s>>>(B, hasA ? A : nullptr, hasA ? lam : nullptr, n, dm->hb, E.Phi,
                                                   E.PhiT, E.mu, P->d_status);
@@ -1051,21 +1072,41 @@ static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, Fd
       st = TAPS_ERR_CUDA;
       break;
     }
-    st = taps_check_status(P->d_status, s);
+    if (cudaEventCreateWithFlags(&E.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(E.done, s) != cudaSuccess) {
+      st = TAPS_ERR_CUDA;
+      break;
+    }
   } while (0);
-  cudaFree(A);
-  cudaFree(B);
-  cudaFree(V);
-  cudaFree(tmp);
-  cudaFree(bt);
-  cudaFree(dd);
-  cudaFree(ee);
-  cudaFree(lam);
-  cudaFree(W);
   E.status = st;
+  E.pending = (st == TAPS_OK) ? 1 : 0;
   dm->nfd++;
   *out = &E;
+  if (st != TAPS_OK) fd_pending_free(*T);
   return st;
+}
+
+// Waits for a decomposition enqueued by fd_enqueue, reads its problem's device status
+// into the entry and frees the temporaries.
+static int fd_finish(FdPending& T) {
+  if (!T.E) return TAPS_OK;
+  int st = taps_check_status(T.P->d_status, T.P->stream);
+  if (T.E->status == TAPS_OK) T.E->status = st;
+  T.E->pending = 0;
+  if (T.E->done) {
+    cudaEventDestroy(T.E->done);
+    T.E->done = nullptr;
+  }
+  fd_pending_free(T);
+  return st;
+}
+
+static int fd_prepare(taps_problem* P, int d, taps_dim* dm, int opA, int opB, FdEntry** out) {
+  (void)d;
+  FdPending T;
+  int st = fd_enqueue(P, dm, opA, opB, out, &T);
+  if (st != TAPS_OK) return st;
+  return fd_finish(T);
 }
 
 // Reduced solve of dim d by fast diagonalisation, coefficients in P->d_C / P->d_c.
@@ -1114,14 +1155,19 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
 }
 
 // Pencil decompositions of every eligible dim, done before any capture (they
-// allocate and synchronise).
-int taps_fd_prepare_all(taps_problem* P, int solver) {
-  if (solver != TAPS_SOLVER_FASTDIAG) return TAPS_OK;
+// allocate and synchronise).  The enqueue half launches them on P's stream and keeps
+// their temporaries in *pend; the finish half waits, checks and frees.  Batches
+// enqueue many problems (each on its own stream) before finishing any, so the
+// decompositions of different instances run concurrently.
+int taps_fd_prepare_enqueue(taps_problem* P, int solver, int M, std::vector<FdPending>* pend) {
+  if (solver != TAPS_SOLVER_FASTDIAG && solver != TAPS_SOLVER_MODEDIAG) return TAPS_OK;
   for (int d = 0; d < P->D; ++d) {
     int sa, sb;
-    if (!taps_fd_eligible(P, d, &sa, &sb)) continue;
+    if (taps_dim_route(P, d, solver, M) != TAPS_ROUTE_FD || !taps_fd_eligible(P, d, &sa, &sb)) continue;
     FdEntry* E = nullptr;
-    TAPS_TRY(fd_prepare(P, d, P->dims[d], sa >= 0 ? P->ops[d][sa] : -1, P->ops[d][sb], &E));
+    FdPending T;
+    TAPS_TRY(fd_enqueue(P, P->dims[d], sa >= 0 ? P->ops[d][sa] : -1, P->ops[d][sb], &E, &T));
+    if (T.E) pend->push_back(T);
     if (!P->d_pq[d]) {   // the problem's source vectors in the pencil's eigenbasis
       const int n = P->dims[d]->nf;
       const long long tot = (long long)n * P->Rf;
@@ -1135,11 +1181,29 @@ int taps_fd_prepare_all(taps_problem* P, int solver) {
   return TAPS_OK;
 }
 
+int taps_fd_prepare_finish(std::vector<FdPending>* pend) {
+  int st = TAPS_OK;
+  for (auto& T : *pend) {
+    int s2 = fd_finish(T);
+    if (st == TAPS_OK) st = s2;
+  }
+  pend->clear();
+  return st;
+}
+
+int taps_fd_prepare_all(taps_problem* P, int solver, int M) {
+  std::vector<FdPending> pend;
+  int st = taps_fd_prepare_enqueue(P, solver, M, &pend);
+  int s2 = taps_fd_prepare_finish(&pend);
+  return st != TAPS_OK ? st : s2;
+}
+
 void taps_fd_release(taps_dim* dm) {
   for (int k = 0; k < dm->nfd; ++k) {
     cudaFree(dm->fd[k].Phi);
     cudaFree(dm->fd[k].PhiT);
     cudaFree(dm->fd[k].mu);
+    if (dm->fd[k].done) cudaEventDestroy(dm->fd[k].done);
   }
   dm->nfd = 0;
 }

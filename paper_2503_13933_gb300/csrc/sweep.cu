@@ -578,7 +578,9 @@ int taps_lu_needs_tuning(const taps_problem* P, int solver, int M) {
   if (getenv("TAPS_NO_TUNE")) return 0;
   for (int d = 0; d < P->D; ++d) {
     int sa, sb;
-    if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb)) continue;
+    (void)sa;
+    (void)sb;
+    if (taps_dim_route(P, d, solver, M) != TAPS_ROUTE_LU) continue;
     bool found = false;
     for (int k = 0; k < P->n_lu_tuned; ++k)
       if (P->lu_tuned[k][0] == P->dims[d]->nf && P->lu_tuned[k][1] == M) found = true;
@@ -681,9 +683,11 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
     const taps_dim* dm = P->dims[d];
     // the coefficients of the later dims come with the previous dim's Gram refresh
     if (d == 0) TAPS_TRY(coefficients(P, 0, M));
-    int sa, sb;
-    if (solver == TAPS_SOLVER_FASTDIAG && taps_fd_eligible(P, d, &sa, &sb)) {
+    const int route = taps_dim_route(P, d, solver, M);
+    if (route == TAPS_ROUTE_FD) {
       TAPS_TRY(taps_fd_solve(P, U, d, precision));   // keeps the old factor in d_Uold
+    } else if (route == TAPS_ROUTE_MD) {
+      TAPS_TRY(taps_md_solve(P, U, d));              // keeps the old factor in d_Uold
     } else {
       TAPS_CUDA(cudaMemcpyAsync(P->d_Uold, U->d_U[d], sizeof(double) * dm->nf * M,
                                 cudaMemcpyDeviceToDevice, s));
@@ -737,7 +741,7 @@ int taps_sweep_impl(taps_problem* P, taps_factors* U, int precision, int solver,
   int M = U->M;
   if (M < 1) return TAPS_ERR_INVALID_ARG;
   TAPS_TRY(taps_ws_ensure(P, M));
-  TAPS_TRY(taps_fd_prepare_all(P, solver));
+  TAPS_TRY(taps_fd_prepare_all(P, solver, M));
   TAPS_TRY(taps_sweep_enqueue(P, U, precision, solver, normalize));
   TAPS_CUDA(cudaStreamSynchronize(P->stream));
   return taps_sweep_finish(P, U, change_out);

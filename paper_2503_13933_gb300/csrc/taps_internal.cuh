@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <vector>
 
 #include "taps.h"
 
@@ -43,6 +44,8 @@ int taps_status_from_device(int dev);
 struct FdEntry {
   int opA, opB;
   int status;
+  int pending;         // enqueued, not yet finished (done marks its last kernel)
+  cudaEvent_t done;
   double* Phi;   // [nf][nf] row-major
   double* PhiT;  // [nf][nf] row-major (transpose)
   double* mu;    // [nf]
@@ -134,6 +137,8 @@ struct taps_problem {
   double* d_lu;       // [M][M] LU of the current diagonal block
   double* d_Y;        // [TAPS_NUM_OPS][nf_max][M] SpMM products
   double* d_Uold;     // [nf_max][M]
+  double* d_md;       // mode-side solve: W [M][M], lam [M], W^T c [Rf][M], Z [nf_max][M],
+                      // eliminated rows [nf_max][6][M]
   double* d_partial;  // partial sums of the Gram and residual kernels
   size_t partial_len;
   double* d_scal;     // small scalar scratch
@@ -333,7 +338,26 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
 // Per-dim ranges of the ALS residual's partial sums (CTA indices [cta0[d], cta0[d+1])).
 int taps_als_partial_ranges(const taps_problem* P, int* cta0);
 int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
-int taps_fd_prepare_all(taps_problem* P, int solver);
+// How dim d is solved at M modes under `solver`.
+#define TAPS_ROUTE_LU 0
+#define TAPS_ROUTE_FD 1   // node-side pencil (fastdiag.cu)
+#define TAPS_ROUTE_MD 2   // mode-side pencil (modediag.cu)
+int taps_dim_route(const taps_problem* P, int d, int solver, int M);
+int taps_fd_prepare_all(taps_problem* P, int solver, int M);
+// Temporaries of one pencil decomposition in flight (fastdiag.cu).
+struct FdPending {
+  FdEntry* E;
+  taps_problem* P;
+  double *A, *B, *V, *tmp, *bt, *dd, *ee, *lam, *W;
+};
+// Mode-side diagonalisation (modediag.cu): eligibility of dim d at M modes (slots of
+// the mass-like operator X and the other Y), scratch size, and the solve.
+int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY);
+size_t taps_md_scratch_doubles(int nf_max, int M, int Rf);
+int taps_md_solve(taps_problem* P, taps_factors* U, int d);
+int taps_md_reset(taps_problem* P);
+int taps_fd_prepare_enqueue(taps_problem* P, int solver, int M, std::vector<FdPending>* pend);
+int taps_fd_prepare_finish(std::vector<FdPending>* pend);
 int taps_lu_needs_tuning(const taps_problem* P, int solver, int M);
 int taps_check_status(int* d_status, cudaStream_t s);
 int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB);

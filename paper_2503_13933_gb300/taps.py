@@ -28,7 +28,7 @@ SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4, "opvec": 5}
 FP64, FP32, MIXED = 0, 1, 2
 RES_ALS, RES_FULL = 0, 1
 INIT_GIVEN, INIT_RANDOM, INIT_ZERO = 0, 1, 2
-SOLVER_BLOCK_LU, SOLVER_FASTDIAG = 0, 1
+SOLVER_BLOCK_LU, SOLVER_FASTDIAG, SOLVER_MODEDIAG, SOLVER_AUTO = 0, 1, 2, 3
 
 
 class DimDesc(ctypes.Structure):
@@ -106,7 +106,8 @@ SIGNATURES = {
     "taps_eval_grid_noalloc": (_i, [_vp, _vp, _pi, _pi, _pi, _vp, _i]),
     "taps_profile_reset": (_i, [_vp, _i]),
     "taps_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_vp)]),
-    "taps_batch_sweep": (_i, [_vp, _i, _i, _pd]),
+    "taps_batch_sweep": (_i, [_vp, _i, _i, _pd, _pi]),
+    "taps_batch_info": (_i, [_vp, _pi, ctypes.POINTER(ctypes.c_float)]),
     "taps_batch_destroy": (None, [_vp]),
     "taps_mlp_create": (_i, [_i, _i, _i, _i, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
     "taps_mlp_num_params": (ctypes.c_longlong, [_vp]),
@@ -124,7 +125,7 @@ SIGNATURES = {
 }
 
 PROF_CLASSES = ["gram", "coeff", "block_assemble", "block_lu", "backsub", "normalize",
-                "residual", "eval", "other", "fastdiag", "fd_transform"]
+                "residual", "eval", "other", "fastdiag", "fd_transform", "modediag"]
 
 _LIB = None
 
@@ -367,11 +368,23 @@ class Batch:
         check(lib().taps_batch_create(ph, uh, n, precision, solver, ctypes.byref(h)), "taps_batch_create")
         self.handle = h
 
-    def sweep(self, n_sweeps, graphs=True):
+    def sweep(self, n_sweeps, graphs=True, statuses=False):
+        """Returns each instance's last factor change; with statuses=True also each
+        instance's status (the batch then runs to the end whatever the instances'
+        numerical errors)."""
         ch = np.zeros(len(self.problems))
-        check(lib().taps_batch_sweep(self.handle, n_sweeps, int(graphs), ch.ctypes.data_as(_pd)),
+        st = np.zeros(len(self.problems), dtype=np.int32) if statuses else None
+        check(lib().taps_batch_sweep(self.handle, n_sweeps, int(graphs), ch.ctypes.data_as(_pd),
+                                     st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if statuses else None),
               "taps_batch_sweep")
-        return ch
+        return (ch, st) if statuses else ch
+
+    def info(self):
+        """(solver used by the sweeps, [trial ms FASTDIAG, MODEDIAG] of the AUTO tuner)."""
+        sv = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        check(lib().taps_batch_info(self.handle, ctypes.byref(sv), ms), "taps_batch_info")
+        return sv.value, [ms[0], ms[1]]
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:

@@ -58,3 +58,52 @@ def test_batched_graph_equals_per_instance(T, solver):
         Uo, _ = O.sweep(Po, Uo, solver="fastdiag" if solver == "fastdiag" else "banded")
     a, b = O.cp_full(got[0]), O.cp_full(Uo)
     assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_batched_sweep_restarts_from_reset_factors(T, graphs):
+    """Factors set between two calls on the same batch: the second call starts from the
+    new factors (every instance's Grams are recomputed), so resetting to the initial
+    factors repeats the first call bit for bit."""
+    descs, probs, facs, inits = _instances(T, 5, 4200)
+    B = T.Batch(probs, facs, solver=T.SOLVER_FASTDIAG)
+    c1 = B.sweep(2, graphs=graphs)
+    first = [u.get() for u in facs]
+    for U, U0 in zip(facs, inits):
+        U.set(U0)
+    c2 = B.sweep(2, graphs=graphs)
+    again = [u.get() for u in facs]
+    for a, b in zip(first, again):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(c1, c2)
+
+
+def test_batched_auto_solver_choice_is_timed_and_kept(T):
+    """TAPS_SOLVER_AUTO: the first graph sweep times one batch sweep with each solver
+    (factors restored), keeps the faster, and gives exactly the factors of a batch made
+    with that solver."""
+    descs, probs, facs, inits = _instances(T, 6, 4300)
+    B = T.Batch(probs, facs, solver=T.SOLVER_AUTO)
+    c1 = B.sweep(2, graphs=True)
+    chosen, trial = B.info()
+    assert chosen in (T.SOLVER_FASTDIAG, T.SOLVER_MODEDIAG)
+    assert trial[0] > 0 and trial[1] > 0
+    assert (chosen == T.SOLVER_FASTDIAG) == (trial[0] <= trial[1])
+    got = [u.get() for u in facs]
+    for U, U0 in zip(facs, inits):
+        U.set(U0)
+    c2 = T.Batch(probs, facs, solver=chosen).sweep(2, graphs=True)
+    for a, b in zip(got, [u.get() for u in facs]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(c1, c2)
+
+
+def test_batched_statuses_report_per_instance(T):
+    """With statuses requested every instance runs all sweeps and reports its own
+    status (all well posed here: zeros)."""
+    descs, probs, facs, inits = _instances(T, 4, 4400)
+    B = T.Batch(probs, facs, solver=T.SOLVER_MODEDIAG)
+    ch, st = B.sweep(2, graphs=True, statuses=True)
+    assert st.tolist() == [0, 0, 0, 0] and np.all(np.isfinite(ch))

@@ -157,6 +157,78 @@ def test_fastdiag_sweep_parity(T, name, M, nsw):
     assert prof["fastdiag"]["launches"] > 0
 
 
+def _rich_transient(n_space, n_t, M, h_conv, seed):
+    """A 2D transient problem whose source has M random separable terms (nodal values
+    U(-1,1)): the right-hand side has rank M, so the ALS systems stay well conditioned
+    at M modes (a few Gaussians would make the modes nearly collinear)."""
+    desc = W.heat_transient(n_space=n_space, n_t=n_t, D_space=2, h_conv=h_conv, seed=seed)
+    rng = np.random.default_rng(seed)
+    desc["sources"] = [(1.0, [("nodal", rng.uniform(-1.0, 1.0, dm["n"])) for dm in desc["dims"]])
+                       for _ in range(M)]
+    return desc
+
+
+@pytest.mark.parametrize("n_space,n_t,M,h_conv", [(12, 9, 3, 0.0), (40, 130, 20, 2.0), (24, 300, 32, 0.0),
+                                                   (40, 200, 7, 0.0)])
+def test_mode_side_time_solve_matches_oracle(T, n_space, n_t, M, h_conv):
+    """Time dims (G, M: symmetric coefficients) solved on the mode side (Sec. 2.6: M x M
+    generalised eigenproblem, M banded eliminations): two sweeps give the oracle's
+    factors, with no block elimination anywhere (space dims by the node-side pencil,
+    or by block elimination when convection faces give them a third operator)."""
+    desc = _rich_transient(n_space, n_t, M, h_conv, seed=3030 + M)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=70 + M)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    P.profile_reset()
+    P.sweep(Ug, 2, solver=T.SOLVER_FASTDIAG)
+    Uo = [u.copy() for u in U0]
+    for _ in range(2):
+        Uo, _ = O.sweep(Po, Uo, solver="fastdiag")
+    got = Ug.get()
+    for d in range(Po.D):
+        assert rel(got[d], Uo[d]) < 1e-10, (d, rel(got[d], Uo[d]))
+    prof = P.profile()
+    assert prof["modediag"]["launches"] == 2 * 3   # eig + band + output, per sweep
+    if h_conv == 0.0:
+        assert prof["block_lu"]["launches"] == 0
+
+
+def _rich_poisson_k(n_space, n_k, M, seed):
+    """The space-parameter problem with an M-term random separable source (nodal values
+    U(-1,1)), well conditioned at M modes."""
+    desc = W.poisson_k(n_space=n_space, n_k=n_k, seed=seed)
+    rng = np.random.default_rng(seed)
+    desc["sources"] = [(1.0, [("nodal", rng.uniform(-1.0, 1.0, dm["n"])) for dm in desc["dims"]])
+                       for _ in range(M)]
+    return desc
+
+
+@pytest.mark.parametrize("n_space,n_k,M", [(10, 7, 3), (60, 16, 12), (200, 32, 30)])
+def test_modediag_poisson_matches_oracle(T, n_space, n_k, M):
+    """TAPS_SOLVER_MODEDIAG on the space-parameter problem: every dim (K, M pairs and
+    the W-only parameter dim) on the mode side, no pencil decomposition; two sweeps
+    give the oracle's mode-side factors."""
+    desc = _rich_poisson_k(n_space, n_k, M, seed=2040 + M)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=80 + M)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    P.profile_reset()
+    P.sweep(Ug, 2, solver=T.SOLVER_MODEDIAG)
+    Uo = [u.copy() for u in U0]
+    for _ in range(2):
+        Uo, _ = O.sweep(Po, Uo, solver="modediag")
+    got = Ug.get()
+    for d in range(Po.D):
+        assert rel(got[d], Uo[d]) < 1e-10, (d, rel(got[d], Uo[d]))
+    prof = P.profile()
+    assert prof["modediag"]["launches"] == 2 * 3 * Po.D
+    assert prof["fastdiag"]["launches"] == 0 and prof["block_lu"]["launches"] == 0
+
+
 @pytest.mark.parametrize("solver", ["fastdiag", "block_lu"])
 def test_graph_replay_matches_direct_launches(T, solver):
     """Sweeps replayed from a captured CUDA graph give the same history and factors as

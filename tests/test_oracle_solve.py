@@ -51,7 +51,8 @@ def test_mode_side_diagonalisation_agrees_with_dense():
     (K, M)."""
     cases = (W.heat_transient(n_space=9, n_t=8, D_space=2, seed=3010),
              W.heat_transient(n_space=8, n_t=7, D_space=2, h_conv=2.0, seed=3011),
-             W.poisson_sin(9, D=3))
+             W.poisson_sin(9, D=3),
+             W.poisson_k(n_space=8, n_k=6, seed=2012))
     used = {}
     for k, desc in enumerate(cases):
         P = O.problem_from_description(desc)
@@ -68,8 +69,23 @@ def test_mode_side_diagonalisation_agrees_with_dense():
     # every time dim (ops G, M: mass-like X = M) and every Poisson dim was covered
     assert used[(0, 2)] == (O.OP_M, O.OP_G) and used[(1, 2)] == (O.OP_M, O.OP_G)
     assert all((2, d) in used for d in range(3))
+    # the parameter dim (W alone): one operator, W = L^-T
+    assert used[(3, 3)] == (O.OP_W, None) and all((3, d) in used for d in range(3))
     # space dims of a transient problem carry the nonsymmetric time Gram: not eligible
     assert (0, 0) not in used and (1, 0) not in used
+
+
+def test_mode_side_poisson_sweeps_follow_block_elimination():
+    """The space-parameter problem swept on the mode side in every dim gives the
+    factors of block elimination."""
+    P = O.problem_from_description(W.poisson_k(n_space=9, n_k=7, seed=2013))
+    U0 = O.init_factors(P, 4, "random", 6)
+    Ua, Ub = [u.copy() for u in U0], [u.copy() for u in U0]
+    for _ in range(2):
+        Ua, ca = O.sweep(P, Ua, solver="modediag")
+        Ub, cb = O.sweep(P, Ub, solver="banded")
+    for a, b in zip(Ua, Ub):
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
 
 
 def test_mode_side_sweeps_follow_block_elimination():
