@@ -441,16 +441,19 @@ def solve_fast_diag(prob: Problem, d, C, F):
 def mode_diag_pair(prob: Problem, d, C):
     """Operator pair of dim d for diagonalisation on the mode side (Sec. 2.6: the
     Sylvester form of the reduced system, cost M^3 + M^2 n_d + the banded solves):
-    returns (opX, opY), opX mass-like when the pair has one, if dim d has exactly two
-    operators and every other dim's operators are symmetric (then every Gram of the
-    other dims, and so every C_op of dim d, is symmetric); None otherwise."""
+    returns (opX, opY), opX mass-like when the pair has one, if dim d has one or two
+    operators (opY None for one) and every other dim's operators are symmetric (then
+    every Gram of the other dims, and so every C_op of dim d, is symmetric); None
+    otherwise."""
     ops = list(C.keys())
-    if len(ops) != 2:
+    if not 1 <= len(ops) <= 2:
         return None
     for alpha, opk in prob.terms:
         for e in range(prob.D):
             if e != d and opk[e] == OP_G:
                 return None
+    if len(ops) == 1:
+        return ops[0], None
     mass = [o for o in ops if o in (OP_M, OP_W)]
     x = mass[0] if mass else ops[0]
     return x, [o for o in ops if o != x][0]
@@ -465,12 +468,18 @@ def solve_mode_diag(prob: Problem, d, C, F):
     import scipy.linalg
     opX, opY = mode_diag_pair(prob, d, C)
     CX = 0.5 * (C[opX] + C[opX].T)
-    CY = 0.5 * (C[opY] + C[opY].T)
-    lam, Wm = scipy.linalg.eigh(CY, CX)
+    if opY is None:    # Op_X U C_X = F: W = L^-T (C_X = L L^T), lam = 0
+        Wm = np.linalg.inv(np.linalg.cholesky(CX)).T
+        lam = np.zeros(CX.shape[0])
+        OpY = np.zeros_like(prob.ops[d][opX])
+    else:
+        CY = 0.5 * (C[opY] + C[opY].T)
+        lam, Wm = scipy.linalg.eigh(CY, CX)
+        OpY = prob.ops[d][opY]
     G = F @ Wm
     Z = np.zeros_like(G)
     for j in range(G.shape[1]):
-        Z[:, j] = np.linalg.solve(prob.ops[d][opX] + lam[j] * prob.ops[d][opY], G[:, j])
+        Z[:, j] = np.linalg.solve(prob.ops[d][opX] + lam[j] * OpY, G[:, j])
     return Z @ Wm.T
 
 
@@ -498,8 +507,9 @@ def sweep(prob: Problem, U, solver="banded"):
     d < D.  Returns the new factors and max_d ||dU_d||_F / ||U_d||_F.
 
     solver: "banded" (block elimination), "dense", "fastdiag" (node-side pencil where
-    the dim's operators allow, else mode-side where the coefficients allow, else
-    banded) or "modediag" (mode-side where allowed, else banded).
+    the dim's operators allow, else mode-side for two operators with symmetric
+    coefficients, else banded) or "modediag" (mode-side for one or two operators with
+    symmetric coefficients, else node-side, else banded).
     """
     U = [u.copy() for u in U]
     change = 0.0
@@ -507,9 +517,11 @@ def sweep(prob: Problem, U, solver="banded"):
         C, F = coefficients(prob, U, d)
         if solver == "dense":
             Ud = solve_dense(reduced_matrix_dense(prob, d, C), F)
-        elif solver == "fastdiag" and fast_diag_pencil(prob, d, C) is not None:
+        elif solver == "modediag" and mode_diag_pair(prob, d, C) is not None:
+            Ud = solve_mode_diag(prob, d, C, F)
+        elif solver in ("fastdiag", "modediag") and fast_diag_pencil(prob, d, C) is not None:
             Ud = solve_fast_diag(prob, d, C, F)
-        elif solver in ("fastdiag", "modediag") and mode_diag_pair(prob, d, C) is not None:
+        elif solver == "fastdiag" and len(C) == 2 and mode_diag_pair(prob, d, C) is not None:
             Ud = solve_mode_diag(prob, d, C, F)
         else:
             Ud = solve_block_banded(prob, d, C, F)
