@@ -16,9 +16,11 @@
 //                    Cholesky C_X = L L^T, S = L^-1 C_Y L^-T, cyclic Jacobi
 //                    S = Q diag(lam) Q^T, W = P L^-T Q, and Wc_r = W^T c_r for the
 //                    right-hand side F W = sum_r q_r (W^T c_r)^T.
+//   md_prep_kernel   every system's band rows Op_X + lam_j Op_Y and right-hand side,
+//                    in parallel over rows, band entries and systems.
 //   md_band_kernel   thread j: Gaussian elimination without pivoting of the banded
-//                    Op_X + lam_j Op_Y (half-bandwidth HB) with the active window in
-//                    registers, then back substitution; Z is n_d x M row-major.
+//                    system (half-bandwidth HB) with the active rows in a register
+//                    ring, then back substitution; Z is n_d x M row-major.
 //   md_out_kernel    U = Z W^T into the factor layout, the old factor into Save.
 //
 // The eliminations need no pivoting: with X the mass-like operator (symmetric
@@ -267,143 +269,133 @@ __global__ void __launch_bounds__(MD_THREADS) md_eig_kernel(const double* __rest
   if (tid == 0) *wM = failed ? 0 : M;
 }
 
-// Element (row, col) of Op_X + lam Op_Y from the [n][2HB+1] bands; zero outside.
-template <int HB>
-__device__ __forceinline__ double md_elem(const double* __restrict__ bx, const double* __restrict__ by,
-                                          double lam, int n, int row, int col) {
-  const int k = col - row + HB;
-  if (row >= n || col >= n || k < 0 || k > 2 * HB) return 0.0;
-  const size_t o = (size_t)row * (2 * HB + 1) + k;
-  return bx[o] + lam * by[o];
-}
+// Padding rows below the matrix (identity rows, zero right-hand side) let the
+// elimination run whole unrolled groups and read ahead without bounds tests.
+#define MD_PAD 24
 
-// Right-hand side entry (F W)[row][j] = sum_r q_r[row] Wc_r[j].
-__device__ __forceinline__ double md_rhs(const double* __restrict__ q, const double* __restrict__ cw, int Rf,
-                                         int n, int M, int row, int j) {
-  if (row >= n) return 0.0;
-  double s = 0.0;
-  for (int r = 0; r < Rf; ++r) s += q[(size_t)r * n + row] * cw[r * M + j];
-  return s;
-}
-
-// Thread j < M solves (Op_X + lam_j Op_Y) z_j = (F W)_j.  Forward elimination keeps
-// rows i .. i+HB of the active matrix in registers (row i+r holds columns i .. i+r+HB;
-// Gaussian elimination of a band matrix without pivoting creates no fill outside the
-// band) and stores, per step, the pivot row scaled by the pivot's reciprocal; back
-// substitution walks the stored rows upwards.  Stored rows: scratch[i][c][j],
-// c = 0 (scaled right-hand side), 1..HB (scaled superdiagonal entries).
-// Raw band row `row` of X and Y, columns c0 .. c0 + 2HB (zero outside the matrix),
-// and its right-hand side entry: loaded two elimination steps before the row enters
-// the window, so that the loads' latency stays off the pivot chain.
+// Ab[(i * (2HB+2) + k) * M + j]: row i of Op_X + lam_j Op_Y in band-relative form
+// (k = column - i + HB, zero outside the matrix) and, at k = 2HB+1, the right-hand side
+// (F W)[i][j] = sum_r q_r[i] Wc_r[j]; rows n .. n+MD_PAD-1 are identity rows.
 template <int HB>
-__device__ __forceinline__ void md_stage(const double* __restrict__ bx, const double* __restrict__ by,
-                                         const double* __restrict__ q, const double* __restrict__ cw, int Rf,
-                                         int n, int M, int j, int row, int c0, double* x, double* y, double& r) {
-  constexpr int W2 = 2 * HB + 1;
-  const bool in = row < n;
-  const size_t o = (size_t)(in ? row : 0) * W2;
-#pragma unroll
-  for (int c = 0; c < W2; ++c) {
-    const bool ok = in && (c0 + c) < n && (c0 + c) >= 0 && (c0 + c - row + HB) >= 0 && (c0 + c - row + HB) < W2;
-    const int k = c0 + c - row + HB;
-    x[c] = ok ? bx[o + k] : 0.0;
-    y[c] = ok ? by[o + k] : 0.0;
+__global__ void md_prep_kernel(const double* __restrict__ bx, const double* __restrict__ by,
+                               const double* __restrict__ lam, const double* __restrict__ q,
+                               const double* __restrict__ cw, int Rf, int n, int M, double* __restrict__ Ab) {
+  constexpr int W2 = 2 * HB + 1, RW = W2 + 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)(n + MD_PAD) * RW * M;
+  if (idx >= tot) return;
+  const int j = (int)(idx % M);
+  const int k = (int)((idx / M) % RW);
+  const int i = (int)(idx / ((long long)M * RW));
+  double v = 0.0;
+  if (i >= n) {
+    v = (k == HB) ? 1.0 : 0.0;
+  } else if (k < W2) {
+    const int col = i + k - HB;
+    if (col >= 0 && col < n) v = fma(lam[j], by[(size_t)i * W2 + k], bx[(size_t)i * W2 + k]);
+  } else {
+    for (int r = 0; r < Rf; ++r) v = fma(q[(size_t)r * n + i], cw[r * M + j], v);
   }
-  r = md_rhs(q, cw, Rf, n, M, row, j);
+  Ab[idx] = v;
 }
 
-// Thread j < M solves (Op_X + lam_j Op_Y) z_j = (F W)_j.  Forward elimination keeps
-// rows i .. i+HB of the active matrix in registers (row i+r holds columns i .. i+r+HB;
-// Gaussian elimination of a band matrix without pivoting creates no fill outside the
-// band) and stores, per step, the pivot row scaled by the pivot's reciprocal; back
-// substitution walks the stored rows upwards.  Stored rows: scratch[i][c][j],
-// c = 0 (scaled right-hand side), 1..HB (scaled superdiagonal entries).
+// Thread j < M solves (Op_X + lam_j Op_Y) z_j = (F W)_j by Gaussian elimination without
+// pivoting (no fill outside the band).  The active rows i .. i+HB live in a ring of
+// NS = HB+1 register rows in band-relative form, so a row keeps its storage while the
+// window moves: row i+r sits in slot (i+r) mod NS, its entry in column i + c at
+// HB + c - r.  The loop is unrolled by U = lcm(NS, 2) so that every slot index is a
+// compile-time constant; the row entering at step i (row i+HB+1, into the pivot's slot)
+// was loaded two steps earlier.  Stored per step: the pivot row scaled by the pivot's
+// reciprocal, scratch[(i * (HB+1) + c) * M + j] (c = 0: right-hand side, 1..HB:
+// superdiagonal); back substitution walks them upwards with the same ring.
 template <int HB>
-__global__ void __launch_bounds__(32) md_band_kernel(const double* __restrict__ bx, const double* __restrict__ by,
-                                                     const double* __restrict__ lam, const double* __restrict__ q,
-                                                     const double* __restrict__ cw, int Rf, int n, int M,
+__global__ void __launch_bounds__(32) md_band_kernel(const double* __restrict__ Ab, int n, int M,
                                                      double* __restrict__ scratch, double* __restrict__ Z,
                                                      int* status) {
+  constexpr int W2 = 2 * HB + 1, RW = W2 + 1, NS = HB + 1;
+  constexpr int U = (NS % 2 == 0) ? NS : 2 * NS;
   const int j = threadIdx.x;
   if (j >= M) return;
-  const double lj = lam[j];
-  constexpr int W2 = 2 * HB + 1;
-  double A[HB + 1][W2];
-  double b[HB + 1];
+  const int nsteps = ((n + U - 1) / U) * U;   // <= n + U - 1; rows read <= nsteps + HB + 2
+  double A[NS][W2];
+  double b[NS];
 #pragma unroll
-  for (int r = 0; r <= HB; ++r) {
+  for (int r = 0; r < NS; ++r) {
+    const double* row = Ab + (size_t)r * RW * M + j;
 #pragma unroll
-    for (int c = 0; c < W2; ++c) A[r][c] = (c <= r + HB) ? md_elem<HB>(bx, by, lj, n, r, c) : 0.0;
-    b[r] = md_rhs(q, cw, Rf, n, M, r, j);
+    for (int k = 0; k < W2; ++k) A[r][k] = row[(size_t)k * M];
+    b[r] = row[(size_t)W2 * M];
   }
-  // the rows entering at the ends of steps 0 and 1
-  double x1[W2], y1[W2], r1, x2[W2], y2[W2], r2;
-  md_stage<HB>(bx, by, q, cw, Rf, n, M, j, 1 + HB, 1, x1, y1, r1);
-  md_stage<HB>(bx, by, q, cw, Rf, n, M, j, 2 + HB, 2, x2, y2, r2);
+  double st[2][RW];   // staged rows: row i+HB+1 enters at step i from st[i & 1]
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const double* row = Ab + (size_t)(HB + 1 + t) * RW * M + j;
+#pragma unroll
+    for (int k = 0; k < RW; ++k) st[t][k] = row[(size_t)k * M];
+  }
   bool bad = false;
-  for (int i = 0; i < n; ++i) {
-    const double piv = A[0][0];
-    const bool ok = fabs(piv) > 0.0 && isfinite(piv);
-    bad |= !ok;
-    const double inv = ok ? taps_rcp(piv) : 0.0;
-    double l[HB + 1];
+  for (int i0 = 0; i0 < nsteps; i0 += U) {
 #pragma unroll
-    for (int r = 1; r <= HB; ++r) l[r] = A[r][0] * inv;
+    for (int ph = 0; ph < U; ++ph) {
+      const int i = i0 + ph;
+      const int P = ph % NS;
+      const double piv = A[P][HB];
+      const bool ok = fabs(piv) > 0.0 && isfinite(piv);
+      bad |= !ok;
+      const double inv = ok ? taps_rcp(piv) : 0.0;
 #pragma unroll
-    for (int r = 1; r <= HB; ++r) {
+      for (int r = 1; r <= HB; ++r) {
+        const int R = (ph + r) % NS;
+        const double l = A[R][HB - r] * inv;
 #pragma unroll
-      for (int c = 1; c <= HB; ++c) A[r][c] -= l[r] * A[0][c];
-      b[r] -= l[r] * b[0];
+        for (int c = 1; c <= HB; ++c) A[R][HB + c - r] -= l * A[P][HB + c];
+        b[R] -= l * b[P];
+      }
+      double* out = scratch + (size_t)i * NS * M + j;
+      out[0] = b[P] * inv;
+#pragma unroll
+      for (int c = 1; c <= HB; ++c) out[(size_t)c * M] = A[P][HB + c] * inv;
+      // row i+HB+1 takes the pivot's slot; row i+HB+3 is staged in its place
+      const int t = ph & 1;
+#pragma unroll
+      for (int k = 0; k < W2; ++k) A[P][k] = st[t][k];
+      b[P] = st[t][W2];
+      const double* row = Ab + (size_t)(i + HB + 3) * RW * M + j;
+#pragma unroll
+      for (int k = 0; k < RW; ++k) st[t][k] = row[(size_t)k * M];
     }
-    double* out = scratch + (size_t)i * (HB + 1) * M + j;
-    out[0] = b[0] * inv;
-#pragma unroll
-    for (int c = 1; c <= HB; ++c) out[(size_t)c * M] = A[0][c] * inv;
-    // slide the window down one row and one column; row i+HB+1 enters
-#pragma unroll
-    for (int r = 0; r < HB; ++r) {
-#pragma unroll
-      for (int c = 0; c < W2 - 1; ++c) A[r][c] = A[r + 1][c + 1];
-      A[r][W2 - 1] = 0.0;
-      b[r] = b[r + 1];
-    }
-#pragma unroll
-    for (int c = 0; c < W2; ++c) {
-      A[HB][c] = fma(lj, y1[c], x1[c]);
-      x1[c] = x2[c];
-      y1[c] = y2[c];
-    }
-    b[HB] = r1;
-    r1 = r2;
-    md_stage<HB>(bx, by, q, cw, Rf, n, M, j, i + 3 + HB, i + 3, x2, y2, r2);
   }
   if (bad) taps_flag(status, TAPS_DEV_SINGULAR);
-  // back substitution: z_i = y_i - sum_c u_ic z_{i+c}; zr[c] = z_{i+c}; the stored
-  // rows are loaded two steps ahead
-  double zr[HB + 1];
+  // back substitution over the padded rows (their solution is zero): z_i = y_i -
+  // sum_c u_ic z_{i+c}, z in a ring of NS slots, stored rows loaded two steps ahead
+  double z[NS];
 #pragma unroll
-  for (int c = 0; c <= HB; ++c) zr[c] = 0.0;
-  double u1[HB + 1], u2[HB + 1];
+  for (int r = 0; r < NS; ++r) z[r] = 0.0;
+  double sr[2][NS];
 #pragma unroll
-  for (int c = 0; c <= HB; ++c) {
-    u1[c] = n - 1 >= 0 ? scratch[(size_t)(n - 1) * (HB + 1) * M + (size_t)c * M + j] : 0.0;
-    u2[c] = n - 2 >= 0 ? scratch[(size_t)(n - 2) * (HB + 1) * M + (size_t)c * M + j] : 0.0;
+  for (int t = 0; t < 2; ++t) {
+    const double* u = scratch + (size_t)(nsteps - 1 - t) * NS * M + j;
+#pragma unroll
+    for (int c = 0; c < NS; ++c) sr[t][c] = u[(size_t)c * M];
   }
-  for (int i = n - 1; i >= 0; --i) {
-    // the terms of z_{i+2} .. z_{i+HB} first: only the last FMA waits for z_{i+1}
-    double s = u1[0];
+  for (int i0 = nsteps - U; i0 >= 0; i0 -= U) {
 #pragma unroll
-    for (int c = HB; c >= 2; --c) s -= u1[c] * zr[c];
-    s -= u1[1] * zr[1];
+    for (int ph = U - 1; ph >= 0; --ph) {
+      const int i = i0 + ph;
+      const int t = (U - 1 - ph) & 1;   // rows nsteps-1, nsteps-2, ... alternate buffers
+      // the terms of z_{i+2} .. z_{i+HB} first: only the last FMA waits for z_{i+1}
+      double s = sr[t][0];
 #pragma unroll
-    for (int c = HB; c >= 2; --c) zr[c] = zr[c - 1];
-    zr[1] = s;
-    Z[(size_t)i * M + j] = s;
-    const int nx = i - 2;
+      for (int c = HB; c >= 2; --c) s -= sr[t][c] * z[(ph + c) % NS];
+      s -= sr[t][1] * z[(ph + 1) % NS];
+      z[ph % NS] = s;
+      if (i < n) Z[(size_t)i * M + j] = s;
+      const int nx = i - 2;
+      if (nx >= 0) {
+        const double* u = scratch + (size_t)nx * NS * M + j;
 #pragma unroll
-    for (int c = 0; c <= HB; ++c) {
-      u1[c] = u2[c];
-      u2[c] = nx >= 0 ? scratch[(size_t)nx * (HB + 1) * M + (size_t)c * M + j] : 0.0;
+        for (int c = 0; c < NS; ++c) sr[t][c] = u[(size_t)c * M];
+      }
     }
   }
 }
@@ -465,11 +457,11 @@ int taps_dim_route(const taps_problem* P, int d, int solver, int M) {
 }
 
 // [TAPS_MAX_DIMS][M][M] bases, TAPS_MAX_DIMS ints (one double each), lam [M], W^T c
-// [Rf][M], Z [nf_max][M], eliminated rows [nf_max][MD_MAX_HB + 1][M].  The caller
-// zeroes it (no valid basis).
+// [Rf][M], Z [nf_max][M], eliminated rows [nf_max + MD_PAD][MD_MAX_HB + 1][M], band
+// rows [nf_max + MD_PAD][2 MD_MAX_HB + 2][M].  The caller zeroes it (no valid basis).
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf) {
   return (size_t)TAPS_MAX_DIMS * M * M + TAPS_MAX_DIMS + M + (size_t)Rf * M + (size_t)nf_max * M +
-         (size_t)nf_max * (MD_MAX_HB + 1) * M;
+         (size_t)(nf_max + MD_PAD) * (MD_MAX_HB + 1) * M + (size_t)(nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M;
 }
 
 // Forgets every dim's stored basis (the next solves start cold).  Called when a sweep
@@ -483,9 +475,11 @@ int taps_md_reset(taps_problem* P) {
 
 template <int HB>
 static cudaError_t md_band_launch(const double* bx, const double* by, const double* lam, const double* q,
-                                  const double* cw, int Rf, int n, int M, double* scratch, double* Z, int* status,
-                                  cudaStream_t s) {
-  md_band_kernel<HB><<<1, 32, 0, s>>>(bx, by, lam, q, cw, Rf, n, M, scratch, Z, status);
+                                  const double* cw, int Rf, int n, int M, double* Ab, double* scratch, double* Z,
+                                  int* status, cudaStream_t s) {
+  const long long tot = (long long)(n + MD_PAD) * (2 * HB + 2) * M;
+  md_prep_kernel<HB><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(bx, by, lam, q, cw, Rf, n, M, Ab);
+  md_band_kernel<HB><<<1, 32, 0, s>>>(Ab, n, M, scratch, Z, status);
   return cudaGetLastError();
 }
 
@@ -506,6 +500,7 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
   double* cw = lam + M;
   double* Z = cw + (size_t)Rf * M;
   double* scratch = Z + (size_t)P->nf_max * M;
+  double* Ab = scratch + (size_t)(P->nf_max + MD_PAD) * (MD_MAX_HB + 1) * M;
   const size_t bsz = (size_t)n * dm->nb;
   const double* bx = dm->d_band + (size_t)P->ops[d][sx] * bsz;
   const double* by = sy >= 0 ? dm->d_band + (size_t)P->ops[d][sy] * bsz : bx;   // lam = 0 without Y
@@ -514,16 +509,16 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
                                           P->d_c, Rf, M, Wm, wM, lam, cw, P->d_status);
   cudaError_t ce = cudaSuccess;
   switch (hb) {
-    case 1: ce = md_band_launch<1>(bx, by, lam, P->d_q[d], cw, Rf, n, M, scratch, Z, P->d_status, s); break;
-    case 2: ce = md_band_launch<2>(bx, by, lam, P->d_q[d], cw, Rf, n, M, scratch, Z, P->d_status, s); break;
-    case 3: ce = md_band_launch<3>(bx, by, lam, P->d_q[d], cw, Rf, n, M, scratch, Z, P->d_status, s); break;
-    case 4: ce = md_band_launch<4>(bx, by, lam, P->d_q[d], cw, Rf, n, M, scratch, Z, P->d_status, s); break;
-    default: ce = md_band_launch<5>(bx, by, lam, P->d_q[d], cw, Rf, n, M, scratch, Z, P->d_status, s); break;
+    case 1: ce = md_band_launch<1>(bx, by, lam, P->d_q[d], cw, Rf, n, M, Ab, scratch, Z, P->d_status, s); break;
+    case 2: ce = md_band_launch<2>(bx, by, lam, P->d_q[d], cw, Rf, n, M, Ab, scratch, Z, P->d_status, s); break;
+    case 3: ce = md_band_launch<3>(bx, by, lam, P->d_q[d], cw, Rf, n, M, Ab, scratch, Z, P->d_status, s); break;
+    case 4: ce = md_band_launch<4>(bx, by, lam, P->d_q[d], cw, Rf, n, M, Ab, scratch, Z, P->d_status, s); break;
+    default: ce = md_band_launch<5>(bx, by, lam, P->d_q[d], cw, Rf, n, M, Ab, scratch, Z, P->d_status, s); break;
   }
   TAPS_CUDA(ce);
   const long long nM = (long long)n * M;
   md_out_kernel<<<(unsigned)((nM + 255) / 256), 256, 0, s>>>(Z, Wm, n, M, U->d_U[d], P->d_Uold);
-  P->prof->launches[TAPS_PROF_MODEDIAG] += 2;
+  P->prof->launches[TAPS_PROF_MODEDIAG] += 3;
   // algorithmic flops: ~10 M^3 for the generalised eigenproblem, the eliminations and
   // substitutions (2 HB^2 + 6 HB per row and system), the right-hand sides and the
   // output transform

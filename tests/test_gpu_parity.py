@@ -190,7 +190,7 @@ def test_mode_side_time_solve_matches_oracle(T, n_space, n_t, M, h_conv):
     for d in range(Po.D):
         assert rel(got[d], Uo[d]) < 1e-10, (d, rel(got[d], Uo[d]))
     prof = P.profile()
-    assert prof["modediag"]["launches"] == 2 * 3   # eig + band + output, per sweep
+    assert prof["modediag"]["launches"] == 2 * 4   # eig, band rows, elimination, output; per sweep
     if h_conv == 0.0:
         assert prof["block_lu"]["launches"] == 0
 
@@ -225,7 +225,7 @@ def test_modediag_poisson_matches_oracle(T, n_space, n_k, M):
     for d in range(Po.D):
         assert rel(got[d], Uo[d]) < 1e-10, (d, rel(got[d], Uo[d]))
     prof = P.profile()
-    assert prof["modediag"]["launches"] == 2 * 3 * Po.D
+    assert prof["modediag"]["launches"] == 2 * 4 * Po.D
     assert prof["fastdiag"]["launches"] == 0 and prof["block_lu"]["launches"] == 0
 
 
