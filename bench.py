@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--n-space", type=int, default=WORKLOAD["n_space"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched measurement (0: off)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1536^3 reconstruction measurement")
     ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,mixed_fastdiag,"
                                        "mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
@@ -451,6 +452,37 @@ def run_ours(args, rank, world, local):
                             "numerically rank deficient report TAPS_ERR_SINGULAR and still run "
                             "every sweep in both launch styles")
 
+    large = None
+    if not args.no_large:
+        # the large configuration's reconstruction: the 1536^3 space slice at fixed
+        # (t, P, r) of a 1536^3 x 256 x 16 x 16 CP field, M = 32, seeded factors
+        # (14.5 GB of FP32 output, well above L2)
+        dl = W.large_space_time_parameter()
+        PL = taps.Problem(dl)
+        UL = PL.factors(32)
+        UL.set(W.random_factors(dl, 32, seed=51))
+        cnt, st0 = [1536, 1536, 1536, 1, 1, 1], [0, 0, 0, 100, 7, 11]
+        outl = torch.empty(int(np.prod(cnt)), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            PL.eval_grid(UL, st0, cnt, [1] * 6, outl, dtype=taps.FP32)
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            PL.eval_grid(UL, st0, cnt, [1] * 6, outl, dtype=taps.FP32)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        lb = 4.0 * outl.numel()
+        lms = float(np.mean(ts))
+        large = dict(grid="1536^3 space slice at fixed (t, P, r) of 1536^3 x 256 x 16 x 16", M=32,
+                     dtype="f32 out (split-TF32 tensor cores)", ms=lms, bytes=lb,
+                     gb_s=lb / (lms * 1e-3) / 1e9, frac=lb / (lms * 1e-3) / 1e9 / hbm_peak,
+                     peak_source="measured (MEASURED_PEAKS.json hbm_gbs)",
+                     note="whole taps_eval_grid call: row gathers, operand images, tensor-core product")
+        del outl, UL, PL
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nsw = res[best]["sweeps"]
@@ -486,6 +518,7 @@ def run_ours(args, rank, world, local):
         gpu_launches=launches,
         warm_start=ws_info,
         batched=batched,
+        reconstruction_large=large,
         clocks=res[headline]["clocks"],
     )
     print(json.dumps(line))

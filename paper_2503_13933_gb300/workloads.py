@@ -98,6 +98,29 @@ def heat_transient(n_space=32, n_t=16, D_space=3, T=1.0, rho_cp=1.0, k=1.0, seed
                 terms=terms, sources=sources, params=g)
 
 
+def large_space_time_parameter(n_space=1536, n_t=256, n_p=16, n_r=16, seed=5000):
+    """The large configuration's separated operator on a 3D space (n_space nodes per
+    dim, widths 15.35 x 15.35 x 7.675 mm), one time slab (n_t nodes) and two parameter
+    dims (n_p laser powers in [100, 400] W, n_r radii in [30, 80] um): diffusion and
+    time-derivative terms, a Gaussian source in space, linear in P, constant in r and
+    a ramp in time.  Used for the full-size reconstruction of a space slice at fixed
+    (t, P, r)."""
+    rng = np.random.default_rng(seed)
+    Lx, Lz = 15.35e-3, 7.675e-3
+    dims = [dim(n_space, 0.0, Lx), dim(n_space, 0.0, Lx), dim(n_space, 0.0, Lz),
+            dim(n_t, 0.0, 2e-3, kind=TIME, dirichlet_lo=True, dirichlet_hi=False),
+            dim(n_p, 100.0, 400.0, kind=PARAM, dirichlet_lo=False, dirichlet_hi=False),
+            dim(n_r, 30e-6, 80e-6, kind=PARAM, dirichlet_lo=False, dirichlet_hi=False)]
+    terms = [(1.0, ["M", "M", "M", "G", "M", "M"])]
+    for e in range(3):
+        terms.append((1.0, ["K" if d == e else "M" for d in range(3)] + ["M", "M", "M"]))
+    c = rng.uniform(0.3, 0.7, size=3)
+    sources = [(1.0, [("gauss", (c[0] * Lx, 0.05 * Lx)), ("gauss", (c[1] * Lx, 0.05 * Lx)),
+                      ("gauss", (c[2] * Lz, 0.05 * Lz)), ("poly", (0.0, 1.0)),
+                      ("poly", (0.0, 1.0)), ("const", (1.0,))])]
+    return dict(name=f"large_{n_space}^3_t{n_t}_P{n_p}_r{n_r}", dims=dims, terms=terms, sources=sources)
+
+
 def batch_instances(count=256, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32):
     """Independent instances: D in {3..6}, n_d uniform in [n_lo, n_hi], a mode count
     in [M_lo, M_hi], Poisson or transient (last dim time) 50/50, 1..4 separable

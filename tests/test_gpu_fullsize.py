@@ -150,3 +150,42 @@ def test_plain_poisson_64cubed_matches_oracle_and_exact_solution(T):
     err_o = np.linalg.norm(uo - exact) / np.linalg.norm(exact)
     assert err_o < 1e-5
     assert abs(err_g - err_o) <= 1e-9 * max(1.0, err_o)
+
+
+def test_large_slice_reconstruction_1536cubed(T):
+    """The large configuration's reconstruction: the 1536^3 space slice of a
+    1536^3 x 256 x 16 x 16 space-time-parameter CP field at fixed (t, P, r), M = 32:
+    3.6e9 FP32 values (14.5 GB) on the tensor cores, 4096 seeded sample points against
+    FP64 sums of the same factors."""
+    desc = W.large_space_time_parameter()
+    P = T.Problem(desc)
+    M = 32
+    U0 = W.random_factors(desc, M, seed=51)
+    U = P.factors(M)
+    U.set(U0)
+    fixed = [100, 7, 11]   # time node (free index + 1), power node, radius node
+    start = [0, 0, 0] + fixed
+    count = [1536, 1536, 1536, 1, 1, 1]
+    field = torch.empty(int(np.prod(count)), dtype=torch.float32, device="cuda")
+    P.eval_grid(U, start, count, [1] * 6, field, dtype=T.FP32)
+    torch.cuda.synchronize()
+    dims = [O.dim_from_description(dm) for dm in desc["dims"]]
+    rows = [O.to_all_nodes(dims[d], u) for d, u in enumerate(U.get())]
+    rng = np.random.default_rng(8)
+    idx = np.stack([rng.integers(0, 1536, 4096) for _ in range(3)], axis=1)
+    terms = np.ones((4096, M))
+    for d in range(3):
+        terms *= rows[d][idx[:, d]]
+    for d, node in zip(range(3, 6), fixed):
+        terms *= rows[d][node][None, :]
+    ref = terms.sum(axis=1)
+    flat = np.ravel_multi_index(idx.T, count[:3])
+    got = field[torch.as_tensor(flat, device="cuda")].double().cpu().numpy()
+    bound = 2e-6 * np.abs(terms).sum(axis=1)
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+    # the last element of the slice (the end of the 14.5 GB buffer)
+    last = float(field[-1].item())
+    t_last = np.prod([rows[d][1535] for d in range(3)], axis=0)
+    for d, node in zip(range(3, 6), fixed):
+        t_last = t_last * rows[d][node]
+    assert abs(last - t_last.sum()) <= 2e-6 * np.abs(t_last).sum()
