@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched measurement (0: off)")
     ap.add_argument("--no-large", action="store_true", help="skip the 1536^3 reconstruction measurement")
+    ap.add_argument("--no-lpbf", action="store_true", help="skip the powder-bed-fusion slab measurement")
     ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,mixed_fastdiag,"
                                        "mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
@@ -483,6 +484,37 @@ def run_ours(args, rank, world, local):
                      note="whole taps_eval_grid call: row gathers, operand images, tensor-core product")
         del outl, UL, PL
 
+    lpbf = None
+    if not args.no_lpbf:
+        # the powder-bed-fusion slab at full size (512 x 512 x 128 space, 128 time nodes,
+        # 16 nodes each of laser power, spot radius and conductivity; moving source with
+        # R_f = 483 CP terms), M = 20 from seeded factors: set-up and sweep time
+        dl = W.lpbf_slab()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        PLB = taps.Problem(dl)
+        torch.cuda.synchronize()
+        lb_setup = time.perf_counter() - t0
+        Ml = 20
+        V0 = W.random_factors(dl, Ml, seed=6)
+        UL = PLB.factors(Ml)
+        UL.set(V0)
+        PLB.sweep(UL, 1, solver=taps.SOLVER_FASTDIAG)     # pencils, elimination tuning
+        UL.set(V0)
+        PLB.profile_reset(events=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nsw = 5
+        PLB.sweep(UL, nsw, solver=taps.SOLVER_FASTDIAG)
+        torch.cuda.synchronize()
+        lsw = (time.perf_counter() - t0) / nsw
+        lprof = PLB.profile()
+        lpbf = dict(grid="512 x 512 x 128 space x 128 time x 16 P x 16 r x 16 k", M=Ml,
+                    sources=len(dl["sources"]), setup_s=lb_setup, ms_per_sweep=lsw * 1e3,
+                    rho42_after=PLB.residual(UL, taps.RES_ALS), sweeps=nsw,
+                    classes_ms_per_sweep={k: v["ms"] / nsw for k, v in lprof.items() if v["launches"]})
+        del UL, PLB
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nsw = res[best]["sweeps"]
@@ -519,6 +551,7 @@ def run_ours(args, rank, world, local):
         warm_start=ws_info,
         batched=batched,
         reconstruction_large=large,
+        lpbf_slab=lpbf,
         clocks=res[headline]["clocks"],
     )
     print(json.dumps(line))

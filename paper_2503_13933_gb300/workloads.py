@@ -121,6 +121,64 @@ def large_space_time_parameter(n_space=1536, n_t=256, n_p=16, n_r=16, seed=5000)
     return dict(name=f"large_{n_space}^3_t{n_t}_P{n_p}_r{n_r}", dims=dims, terms=terms, sources=sources)
 
 
+def lpbf_slab(n_xy=512, n_z=128, n_t=128, n_par=16, slab=0, n_slabs=8, svd_tol=1e-10, s=2, a=20.0, p=2):
+    """Single-track laser powder-bed fusion in space-parameter-time (Sec. 3.4 setting):
+    rho c_p du/dt - div(k grad u) = f on x, y in [0, 2.555 mm] (n_xy nodes), z in
+    [0, 0.635 mm] (n_z), one time slab of n_t nodes, and three parameter dims of n_par
+    nodes: laser power P in [100, 400] W, spot radius r in [30, 80] um, conductivity k in
+    [10, 30] W/m/K.  Ti-6Al-4V: rho = 4270 kg/m^3, c_p = 745 J/kg/K; absorptivity 0.25,
+    penetration depth d_v = 50 um, scan speed 0.5 m/s; the track runs along x at
+    y0 = W/2 from x = 0.3 mm to 2.25 mm over n_slabs slabs.  u = T - T0: zero initial
+    condition, Dirichlet at the bottom face, free convection h = 14.73 W/m^2/K on the
+    other five faces.
+
+    The moving source (2 eta P / (pi r^2 d_v)) exp(-2((x - x0(t))^2 + (y - y0)^2) / r^2)
+    1(z >= H - d_v) is separable in P, y (at fixed r) and z; in (x, t) it is not.  Its CP
+    form is built as input data, the same for every solver: one group of terms per
+    r node r_j (the C-HiDeNN shape functions are Kronecker deltas at the nodes), whose
+    (x, t) part is the SVD of the nodal matrix exp(-2 (x_a - x0(t_b))^2 / r_j^2)
+    truncated at svd_tol relative to its largest singular value."""
+    Lxy, H = 2.555e-3, 0.635e-3
+    rho_cp, h_conv, eta, d_v, V = 4270.0 * 745.0, 14.73, 0.25, 50e-6, 0.5
+    x_start, x_end = 0.3e-3, 2.25e-3
+    T_slab = (x_end - x_start) / V / n_slabs
+    t0, t1 = slab * T_slab, (slab + 1) * T_slab
+    free = dict(dirichlet_lo=False, dirichlet_hi=False)
+    dims = [dim(n_xy, 0.0, Lxy, s=s, a=a, p=p, **free), dim(n_xy, 0.0, Lxy, s=s, a=a, p=p, **free),
+            dim(n_z, 0.0, H, s=s, a=a, p=p, dirichlet_lo=True, dirichlet_hi=False),
+            dim(n_t, t0, t1, kind=TIME, s=s, a=a, p=p, dirichlet_lo=True, dirichlet_hi=False),
+            dim(n_par, 100.0, 400.0, kind=PARAM, s=s, a=a, p=p, **free),
+            dim(n_par, 30e-6, 80e-6, kind=PARAM, s=s, a=a, p=p, **free),
+            dim(n_par, 10.0, 30.0, kind=PARAM, s=s, a=a, p=p, weight_poly=(0.0, 1.0), **free)]
+    terms = [(rho_cp, ["M", "M", "M", "G", "M", "M", "M"])]
+    for e in range(3):
+        terms.append((1.0, ["K" if d == e else "M" for d in range(3)] + ["M", "M", "M", "W"]))
+    for face in (["Blo", "M", "M"], ["Bhi", "M", "M"], ["M", "Blo", "M"], ["M", "Bhi", "M"],
+                 ["M", "M", "Bhi"]):
+        terms.append((h_conv, face + ["M", "M", "M", "M"]))
+    x = np.linspace(0.0, Lxy, n_xy)
+    z = np.linspace(0.0, H, n_z)
+    t = np.linspace(t0, t1, n_t)
+    x0 = x_start + V * t
+    y0 = 0.5 * Lxy
+    z_ind = (z >= H - d_v).astype(float)
+    r_nodes = np.linspace(30e-6, 80e-6, n_par)
+    sources = []
+    for j, rj in enumerate(r_nodes):
+        E = np.exp(-2.0 * (x[:, None] - x0[None, :]) ** 2 / rj ** 2)
+        Uu, sv, Vt = np.linalg.svd(E, full_matrices=False)
+        rank = max(1, int(np.sum(sv > svd_tol * sv[0])))
+        yj = np.exp(-2.0 * (x - y0) ** 2 / rj ** 2)
+        ej = np.zeros(n_par)
+        ej[j] = 2.0 * eta / (np.pi * rj ** 2 * d_v)
+        for q in range(rank):
+            sources.append((1.0, [("nodal", sv[q] * Uu[:, q]), ("nodal", yj), ("nodal", z_ind),
+                                  ("nodal", Vt[q]), ("poly", (0.0, 1.0)), ("nodal", ej),
+                                  ("const", (1.0,))]))
+    return dict(name=f"lpbf_{n_xy}x{n_xy}x{n_z}_t{n_t}_par{n_par}_slab{slab}", dims=dims, terms=terms,
+                sources=sources)
+
+
 def batch_instances(count=256, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32):
     """Independent instances: D in {3..6}, n_d uniform in [n_lo, n_hi], a mode count
     in [M_lo, M_hi], Poisson or transient (last dim time) 50/50, 1..4 separable
