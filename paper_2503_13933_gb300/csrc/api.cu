@@ -475,6 +475,8 @@ static void free_ws(taps_problem* P) {
   cudaFree(P->d_Uold);
   cudaFree(P->d_md);
   P->d_md = nullptr;
+  cudaFree(P->d_fdw);
+  P->d_fdw = nullptr;
   cudaFree(P->d_partial);
   cudaFree(P->d_scal);
   cudaFree(P->d_bigG);
@@ -548,6 +550,7 @@ int taps_ws_ensure(taps_problem* P, int M) {
   TAPS_TRY(taps_alloc((void**)&P->d_lu, sizeof(double) * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_Y, sizeof(double) * TAPS_NUM_OPS * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_Uold, sizeof(double) * nfm * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_fdw, sizeof(double) * taps_fdw_scratch_doubles(nfm, M)));
   TAPS_TRY(taps_alloc((void**)&P->d_md, sizeof(double) * taps_md_scratch_doubles(nfm, M, P->Rf)));
   TAPS_CUDA(cudaMemsetAsync(P->d_md, 0, sizeof(double) * taps_md_scratch_doubles(nfm, M, P->Rf), P->stream));
   TAPS_TRY(taps_alloc((void**)&P->d_partial, sizeof(double) * part));

@@ -1154,6 +1154,24 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
   return TAPS_OK;
 }
 
+// The cached (or newly made) decomposition of the pencil (opA, opB) of dim d.
+int taps_fd_lookup(taps_problem* P, int d, int opA, int opB, const FdEntry** out) {
+  FdEntry* E = nullptr;
+  TAPS_TRY(fd_prepare(P, d, P->dims[d], opA, opB, &E));
+  *out = E;
+  return TAPS_OK;
+}
+
+// Out = Phi Y in the factor layout (Y n x M row-major), the previous factor into Save.
+int taps_fd_to_nodal(taps_problem* P, const FdEntry* E, const double* Y, int n, int M, double* Out, double* Save) {
+  int tk = prof_begin(P, TAPS_PROF_FD_TRANSFORM);
+  TAPS_CUDA(taps_launch_pdl(fd_rowgemm_kernel, dim3(n), dim3(RG_WARPS * 32), 0, P->stream, (const double*)E->Phi,
+                            Y, n, M, Out, 1, Save));
+  prof_end(P, TAPS_PROF_FD_TRANSFORM, tk, 2.0 * (double)n * n * M, 8.0 * ((double)n * n + 3.0 * (double)n * M));
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
 // Pencil decompositions of every eligible dim, done before any capture (they
 // allocate and synchronise).  The enqueue half launches them on P's stream and keeps
 // their temporaries in *pend; the finish half waits, checks and frees.  Batches
@@ -1163,7 +1181,13 @@ int taps_fd_prepare_enqueue(taps_problem* P, int solver, int M, std::vector<FdPe
   if (solver != TAPS_SOLVER_FASTDIAG && solver != TAPS_SOLVER_MODEDIAG) return TAPS_OK;
   for (int d = 0; d < P->D; ++d) {
     int sa, sb;
-    if (taps_dim_route(P, d, solver, M) != TAPS_ROUTE_FD || !taps_fd_eligible(P, d, &sa, &sb)) continue;
+    const int route = taps_dim_route(P, d, solver, M);
+    if (route == TAPS_ROUTE_FDW) {
+      int s0, s1, nb;
+      taps_fdw_eligible(P, d, M, &sa, &sb, &s0, &s1, &nb);
+    } else if (route != TAPS_ROUTE_FD || !taps_fd_eligible(P, d, &sa, &sb)) {
+      continue;
+    }
     FdEntry* E = nullptr;
     FdPending T;
     TAPS_TRY(fd_enqueue(P, P->dims[d], sa >= 0 ? P->ops[d][sa] : -1, P->ops[d][sb], &E, &T));

@@ -444,14 +444,17 @@ int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY
 
 int taps_dim_route(const taps_problem* P, int d, int solver, int M) {
   int a, b;
+  int c0, c1, nb;
   if (solver == TAPS_SOLVER_MODEDIAG) {
     if (taps_md_eligible(P, d, M, &a, &b)) return TAPS_ROUTE_MD;
     if (taps_fd_eligible(P, d, &a, &b)) return TAPS_ROUTE_FD;
+    if (taps_fdw_eligible(P, d, M, &a, &b, &c0, &c1, &nb)) return TAPS_ROUTE_FDW;
     return TAPS_ROUTE_LU;
   }
   if (solver == TAPS_SOLVER_FASTDIAG) {
     if (taps_fd_eligible(P, d, &a, &b)) return TAPS_ROUTE_FD;
     if (taps_md_eligible(P, d, M, &a, &b) && P->tt.nops[d] == 2) return TAPS_ROUTE_MD;
+    if (taps_fdw_eligible(P, d, M, &a, &b, &c0, &c1, &nb)) return TAPS_ROUTE_FDW;
   }
   return TAPS_ROUTE_LU;
 }

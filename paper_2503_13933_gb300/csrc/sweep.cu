@@ -688,6 +688,8 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
       TAPS_TRY(taps_fd_solve(P, U, d, precision));   // keeps the old factor in d_Uold
     } else if (route == TAPS_ROUTE_MD) {
       TAPS_TRY(taps_md_solve(P, U, d));              // keeps the old factor in d_Uold
+    } else if (route == TAPS_ROUTE_FDW) {
+      TAPS_TRY(taps_fdw_solve(P, U, d));             // keeps the old factor in d_Uold
     } else {
       TAPS_CUDA(cudaMemcpyAsync(P->d_Uold, U->d_U[d], sizeof(double) * dm->nf * M,
                                 cudaMemcpyDeviceToDevice, s));

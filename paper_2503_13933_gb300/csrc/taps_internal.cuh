@@ -137,6 +137,7 @@ struct taps_problem {
   double* d_lu;       // [M][M] LU of the current diagonal block
   double* d_Y;        // [TAPS_NUM_OPS][nf_max][M] SpMM products
   double* d_Uold;     // [nf_max][M]
+  double* d_fdw;      // convection-face corrections: X [nf_max][2][M][M], w [nf_max][M], small parts
   double* d_md;       // mode-side solve: W [M][M], lam [M], W^T c [Rf][M], Z [nf_max][M],
                       // eliminated rows [nf_max][6][M]
   double* d_partial;  // partial sums of the Gram and residual kernels
@@ -342,6 +343,7 @@ int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, doubl
 #define TAPS_ROUTE_LU 0
 #define TAPS_ROUTE_FD 1   // node-side pencil (fastdiag.cu)
 #define TAPS_ROUTE_MD 2   // mode-side pencil (modediag.cu)
+#define TAPS_ROUTE_FDW 3  // node-side pencil with convection-face corrections (fdbound.cu)
 int taps_dim_route(const taps_problem* P, int d, int solver, int M);
 int taps_fd_prepare_all(taps_problem* P, int solver, int M);
 // Temporaries of one pencil decomposition in flight (fastdiag.cu).
@@ -356,6 +358,13 @@ int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf);
 int taps_md_solve(taps_problem* P, taps_factors* U, int d);
 int taps_md_reset(taps_problem* P);
+// Node-side diagonalisation with convection-face corrections (fdbound.cu).
+int taps_fdw_eligible(const taps_problem* P, int d, int M, int* slotA, int* slotB, int* slotC0, int* slotC1,
+                      int* nbnd);
+size_t taps_fdw_scratch_doubles(int nf_max, int M);
+int taps_fdw_solve(taps_problem* P, taps_factors* U, int d);
+int taps_fd_lookup(taps_problem* P, int d, int opA, int opB, const FdEntry** out);
+int taps_fd_to_nodal(taps_problem* P, const FdEntry* E, const double* Y, int n, int M, double* Out, double* Save);
 int taps_fd_prepare_enqueue(taps_problem* P, int solver, int M, std::vector<FdPending>* pend);
 int taps_fd_prepare_finish(std::vector<FdPending>* pend);
 int taps_lu_needs_tuning(const taps_problem* P, int solver, int M);
