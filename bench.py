@@ -486,34 +486,48 @@ def run_ours(args, rank, world, local):
 
     lpbf = None
     if not args.no_lpbf:
-        # the powder-bed-fusion slab at full size (512 x 512 x 128 space, 128 time nodes,
-        # 16 nodes each of laser power, spot radius and conductivity; moving source with
-        # R_f = 483 CP terms), M = 20 from seeded factors: set-up and sweep time
-        dl = W.lpbf_slab()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        PLB = taps.Problem(dl)
-        torch.cuda.synchronize()
-        lb_setup = time.perf_counter() - t0
-        Ml = 20
-        V0 = W.random_factors(dl, Ml, seed=6)
-        UL = PLB.factors(Ml)
-        UL.set(V0)
-        PLB.sweep(UL, 1, solver=taps.SOLVER_FASTDIAG)     # pencils, elimination tuning
-        UL.set(V0)
-        PLB.profile_reset(events=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        nsw = 5
-        PLB.sweep(UL, nsw, solver=taps.SOLVER_FASTDIAG)
-        torch.cuda.synchronize()
-        lsw = (time.perf_counter() - t0) / nsw
-        lprof = PLB.profile()
-        lpbf = dict(grid="512 x 512 x 128 space x 128 time x 16 P x 16 r x 16 k", M=Ml,
-                    sources=len(dl["sources"]), setup_s=lb_setup, ms_per_sweep=lsw * 1e3,
-                    rho42_after=PLB.residual(UL, taps.RES_ALS), sweeps=nsw,
-                    classes_ms_per_sweep={k: v["ms"] / nsw for k, v in lprof.items() if v["launches"]})
-        del UL, PLB
+        # the powder-bed-fusion configuration at full size (512 x 512 x 128 space, 8 slabs
+        # of 128 time nodes, 16 nodes each of laser power, spot radius and conductivity;
+        # moving source with R_f = 483 CP terms per slab): per slab M = 20 from seeded
+        # factors, 8 sweeps, then the end state is lifted into the next slab and
+        # compressed to 20 modes (App. B, 6 sweeps).  Timed: problem set-up, sweeps,
+        # residual, end state and compression of every slab (the source SVDs are input
+        # data, built before).
+        from paper_2503_13933_gb300 import slabs as S
+        Ml, nsw, Mc = 20, 8, 20
+        descs_l = [W.lpbf_slab(slab=k) for k in range(8)]
+        state, per_slab = None, []
+        t_all = 0.0
+        dim_cache = {}   # the space and parameter dims (and their pencils) are shared by all slabs
+        lprof = None
+        for k, dk in enumerate(descs_l):
+            if state is not None:
+                dk = S.next_slab(dk, state, 0.0)
+            V0 = W.random_factors(dk, Ml, seed=60 + k)
+            C0 = W.random_factors(dict(dims=[dm for j, dm in enumerate(dk["dims"]) if j != 3]), Mc,
+                                  seed=80 + k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            PLB = taps.Problem(dk, dim_cache=dim_cache)
+            UL = PLB.factors(Ml)
+            UL.set(V0)
+            if k == 0:
+                PLB.profile_reset(events=True)
+            PLB.sweep(UL, nsw, solver=taps.SOLVER_FASTDIAG)
+            rho = PLB.residual(UL, taps.RES_ALS)
+            if k == 0:
+                lprof = PLB.profile()
+            state = S.compress(dk, S.end_state(UL.get(), 3, state), C0, sweeps=6, dim_cache=dim_cache)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            t_all += dt
+            per_slab.append(dict(ms=dt * 1e3, sources=len(dk["sources"]), rho42=rho))
+            del UL, PLB
+        del dim_cache
+        lpbf = dict(grid="512 x 512 x 128 space x 8 slabs x 128 time x 16 P x 16 r x 16 k", M=Ml,
+                    sweeps_per_slab=nsw, compressed_modes=Mc, total_s=t_all, slabs=per_slab,
+                    slab0_classes_ms_per_sweep={c: v["ms"] / nsw for c, v in lprof.items() if v["launches"]},
+                    note="fixed sweeps per slab (a throughput run, not converged to a tolerance)")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

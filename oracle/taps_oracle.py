@@ -844,3 +844,25 @@ def slab_next_description(desc, state, time_dim, t_shift):
                            for d in range(len(ops))]))
     nd["sources"] = list(desc["sources"]) + extra
     return nd
+
+
+def slab_compress(desc, state, time_dim, U0, sweeps):
+    """Mode compression of a slab end state (App. B): the L2 projection of
+    u_end = sum_m w_m (x)_d U_d[:, m] onto the modes of U0 (fewer), i.e. the weighted
+    residual equation (x)_d M_d u_F = (x)_d M_d u_end over the dims other than time,
+    solved by Algorithm 1 sweeps (block elimination) from the given factors.  Returns
+    the compressed state (weights 1: the normalisation puts the scale in the last dim)."""
+    facs, wts = state
+    keep = [d for d in range(len(desc["dims"])) if d != time_dim]
+    cdesc = dict(name="compress", dims=[desc["dims"][d] for d in keep],
+                 terms=[(1.0, ["M"] * len(keep))],
+                 sources=[(float(wts[m]), [("opvec", ("M", facs[d][:, m])) for d in keep])
+                          for m in range(len(wts))])
+    P = problem_from_description(cdesc)
+    U = [u.copy() for u in U0]
+    for _ in range(sweeps):
+        U, _ = sweep(P, U, solver="banded")
+    out = [None] * len(desc["dims"])
+    for j, d in enumerate(keep):
+        out[d] = U[j]
+    return out, np.ones(U[0].shape[1])

@@ -7,7 +7,8 @@ derivative and every mode m of u_end, the separable term
     -alpha_t * tau_m * (x)_{d != t} (Op_{t,d} U_d[:, m]) (x) (M_t 1),
 where tau_m is mode m's time factor at t_max (the time derivative of the constant-in-
 time lifting vanishes).  The end state of slab T+1 is u_end + w(., t_max): the modes
-of both, concatenated (no mode compression).
+of both, concatenated; `compress` reduces them again (App. B: the L2 projection of the
+end state onto fewer modes, solved by the same subspace iteration).
 """
 from __future__ import annotations
 
@@ -65,3 +66,34 @@ def next_slab(desc, state, t_shift):
     nd["dims"] = dims
     nd["sources"] = list(desc["sources"]) + lifting_sources(desc, state)
     return nd
+
+
+def compression_description(desc, state):
+    """The mode-compression problem of an end state (App. B): over the dims other than
+    time, the operator (x)_d M_d and one source term per mode, w_m (x)_d M_d U_d[:, m]
+    (the projection of u_end)."""
+    t = state.time_dim
+    keep = [d for d in range(len(desc["dims"])) if d != t]
+    return dict(name="compress", dims=[desc["dims"][d] for d in keep], terms=[(1.0, ["M"] * len(keep))],
+                sources=[(float(state.weight[m]), [("opvec", ("M", state.U[d][:, m])) for d in keep])
+                         for m in range(state.M)])
+
+
+def compress(desc, state, U0, sweeps, stream=None, dim_cache=None):
+    """Compressed end state: `sweeps` subspace-iteration sweeps of the compression
+    problem on the GPU from the initial factors U0 (one array per kept dim, M_new
+    columns).  Weights are 1: the normalisation puts each mode's scale in the last dim.
+    dim_cache: shared assembled dims (see taps.Problem)."""
+    from . import taps
+    cdesc = compression_description(desc, state)
+    P = taps.Problem(cdesc, stream=stream, dim_cache=dim_cache)
+    M_new = U0[0].shape[1]
+    U = P.factors(M_new)
+    U.set(U0)
+    P.sweep(U, sweeps, solver=taps.SOLVER_FASTDIAG)
+    got = U.get()
+    keep = [d for d in range(len(desc["dims"])) if d != state.time_dim]
+    out = [None] * len(desc["dims"])
+    for j, d in enumerate(keep):
+        out[d] = got[j]
+    return EndState(out, np.ones(M_new), state.time_dim)

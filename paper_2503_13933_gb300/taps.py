@@ -219,12 +219,15 @@ class Dim:
 class Problem:
     """A separated problem (taps_problem_create) built from a workload description."""
 
-    def __init__(self, desc, stream=None):
+    def __init__(self, desc, stream=None, dim_cache=None):
+        """dim_cache: an optional dict shared by problems on the same stream (slabs of a
+        chain, their compression problems): identical dimension descriptions then share
+        one assembled dimension and its cached pencil decompositions across problems."""
         self.desc = desc
         self.stream = stream if stream is not None else current_stream()
         # identical dimension descriptions share one assembled dimension (and its
         # cached pencil decomposition)
-        uniq = {}
+        uniq = dim_cache if dim_cache is not None else {}
         self.dims = []
         for dm in desc["dims"]:
             key = tuple(sorted((k, tuple(v) if isinstance(v, (list, tuple)) else v)

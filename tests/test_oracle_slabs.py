@@ -64,3 +64,34 @@ def test_lifting_continues_the_full_grid_solution():
     rhs = F[idx_in] - A[np.ix_(idx_in, idx_ic)] @ u_end
     direct = np.linalg.solve(ub, rhs).reshape(5, 5)
     assert np.linalg.norm(u2 - direct) < 1e-9 * np.linalg.norm(direct)
+
+
+def test_mode_compression_recovers_a_low_rank_end_state():
+    """An end state of 8 modes whose field has rank 2 (two modes split into weighted
+    copies, plus pairs that cancel) is compressed to 2 modes: the compressed field
+    equals the end state's (App. B's projection reproduces a field it can represent)."""
+    desc = W.heat_transient(n_space=9, n_t=5, D_space=2, seed=3033)
+    rng = np.random.default_rng(5)
+    n = 7
+    a = [rng.uniform(-1, 1, (n, 2)) for _ in range(2)]
+    cols = [[], []]
+    w = []
+    for m in range(2):                  # mode m as 0.3 + 0.7 of itself
+        for f in (0.3, 0.7):
+            for d in range(2):
+                cols[d].append(a[d][:, m])
+            w.append(f)
+    b = [rng.uniform(-1, 1, n) for _ in range(2)]
+    for sgn in (1.0, -1.0):             # two cancelling pairs
+        for _ in range(2):
+            for d in range(2):
+                cols[d].append(b[d])
+            w.append(sgn)
+    facs = [np.stack(cols[0], axis=1), np.stack(cols[1], axis=1), None]
+    state = (facs, np.array(w))
+    u_end = np.einsum("im,jm,m->ij", facs[0], facs[1], np.array(w))
+    U0 = W.random_factors(dict(dims=[desc["dims"][0], desc["dims"][1]]), 2, seed=6)
+    cf, cw = O.slab_compress(desc, state, 2, U0, sweeps=60)
+    u_c = np.einsum("im,jm,m->ij", cf[0], cf[1], cw)
+    assert np.linalg.norm(u_c - u_end) <= 1e-9 * np.linalg.norm(u_end)
+    assert cf[2] is None and len(cw) == 2
