@@ -58,33 +58,68 @@ __device__ __forceinline__ size_t tc_img_offset(int rows, int ksteps, int row, i
 }
 
 // Image of X[x][m] = prod_{d in [d0, d1)} G_d[i_d(x)][m] (x in C order over d0..d1-1),
-// rows padded to a multiple of `rows`, m padded with zeros to 8 * ksteps.
+// rows padded to a multiple of `rows`, m padded with zeros to 8 * ksteps.  One thread
+// per (row, 4 consecutive m): the row's indices are decomposed once (32-bit when the
+// row count allows) and the 4 hi and 4 lo values go out as two 16-byte stores, which
+// for 8 consecutive rows fill one 128-byte core-matrix row group.
 __global__ void tc_image_kernel(const float* __restrict__ G, GridSpec gs, int d0, int d1, int M, int ksteps,
                                 long long nx, int rows, float* __restrict__ img) {
-  const int kp = ksteps * TC_KSTEP;
+  const int kq = ksteps * TC_KSTEP / 4;
   const long long nblk = (nx + rows - 1) / rows;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nblk * rows * kp) return;
-  const long long x = idx / kp;
-  const int m = (int)(idx - x * kp);
-  float v = 0.f;
-  if (x < nx && m < M) {
-    v = 1.f;
-    long long y = x;
-    for (int d = d1 - 1; d >= d0; --d) {
-      const long long q = y / gs.count[d];
-      const int id = (int)(y - q * gs.count[d]);
-      y = q;
-      v *= G[gs.goff[d] + (long long)id * M + m];
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nblk * rows * kq) return;
+  // consecutive threads take consecutive rows (coalesced 16-byte stores)
+  const long long padded = nblk * rows;
+  const int q = (int)(idx / padded);
+  const long long x = idx - (long long)q * padded;
+  long long off[TAPS_MAX_DIMS];
+  bool in = x < nx;
+  if (in) {
+    if (nx < (1ll << 31)) {
+      unsigned y = (unsigned)x;
+#pragma unroll
+      for (int d = TAPS_MAX_DIMS - 1; d >= 0; --d) {
+        off[d] = 0;
+        if (d >= d0 && d < d1) {
+          const unsigned c = (unsigned)gs.count[d], qq = y / c;
+          off[d] = gs.goff[d] + (long long)(y - qq * c) * M;
+          y = qq;
+        }
+      }
+    } else {
+      long long y = x;
+#pragma unroll
+      for (int d = TAPS_MAX_DIMS - 1; d >= 0; --d) {
+        off[d] = 0;
+        if (d >= d0 && d < d1) {
+          const long long qq = y / gs.count[d];
+          off[d] = gs.goff[d] + (y - qq * gs.count[d]) * M;
+          y = qq;
+        }
+      }
     }
   }
-  const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-  const float lo = v - hi;
+  float hi[4], lo[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int m = 4 * q + j;
+    float v = 0.f;
+    if (in && m < M) {
+      v = 1.f;
+#pragma unroll
+      for (int d = 0; d < TAPS_MAX_DIMS; ++d)
+        if (d >= d0 && d < d1) v *= G[off[d] + m];
+    }
+    hi[j] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    lo[j] = v - hi[j];
+  }
   const long long blk = x / rows;
   const int row = (int)(x - blk * rows);
   float* base = img + (size_t)blk * 2 * ksteps * rows * TC_KSTEP;
-  base[tc_img_offset(rows, ksteps, row, m, 0)] = hi;
-  base[tc_img_offset(rows, ksteps, row, m, 1)] = lo;
+  *reinterpret_cast<float4*>(base + tc_img_offset(rows, ksteps, row, 4 * q, 0)) =
+      make_float4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<float4*>(base + tc_img_offset(rows, ksteps, row, 4 * q, 1)) =
+      make_float4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 // ---------------------------------------------------------------------------------
@@ -385,7 +420,7 @@ int taps_eval_tc(taps_problem* P, const float* G, const GridSpec& gs, int split,
   float* Aimg = (float*)scratch;
   float* Bimg = Aimg + 2 * (size_t)ksteps * TC_KSTEP * nrb * TC_BM;
   cudaStream_t s = P->stream;
-  const long long na = nrb * TC_BM * ksteps * TC_KSTEP, nb = ncb * TC_BN * ksteps * TC_KSTEP;
+  const long long na = nrb * TC_BM * ksteps * TC_KSTEP / 4, nb = ncb * TC_BN * ksteps * TC_KSTEP / 4;
   tc_image_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(G, gs, 0, split, M, ksteps, rows, TC_BM, Aimg);
   tc_image_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(G, gs, split, gs.D, M, ksteps, cols, TC_BN,
                                                               Bimg);
