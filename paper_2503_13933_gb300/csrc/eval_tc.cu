@@ -216,13 +216,15 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
 
 // ---------------------------------------------------------------------------------
 // The persistent kernel.  Tile t covers rows 128 (t % nrb) .. and columns 256 (t / nrb)
-// .. (column-block-major, so that consecutive tiles share the B block in L2).
+// .. (column-block-major, so that consecutive tiles share the B block in L2), or, with
+// rowmajor (an A image too large for L2), rows 128 (t / ncb) .. and columns
+// 256 (t % ncb) .., so that the column blocks of one row block run together.
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __restrict__ Aimg,
                                                                  const float* __restrict__ Bimg,
                                                                  long long R, int C, int ksteps,
                                                                  float* __restrict__ out, int vec_ok,
-                                                                 int* status) {
+                                                                 int rowmajor, int* status) {
   extern __shared__ __align__(1024) unsigned char tc_sm[];
   __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
   __shared__ __align__(8) uint64_t acc_full[TC_ACC], acc_empty[TC_ACC], drain_bar;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
           taps_flag(status, TAPS_DEV_TIMEOUT);
           break;
         }
-        const long long rb = t % nrb, cb = t / nrb;
+        const long long rb = rowmajor ? t / ncb : t % nrb, cb = rowmajor ? t % ncb : t / nrb;
         unsigned char* st = base + (size_t)s * stage_bytes;
         tc_mbar_expect_tx(&full_bar[s], stage_bytes);
         const unsigned char* asrc = (const unsigned char*)Aimg + (size_t)rb * a_bytes;
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
         break;
       }
       tc_fence_after();
-      const long long rb = t % nrb, cb = t / nrb;
+      const long long rb = rowmajor ? t / ncb : t % nrb, cb = rowmajor ? t % ncb : t / nrb;
       const long long row0 = rb * TC_BM + 32 * q;
       const int c0 = (int)(cb * TC_BN) + half * (TC_BN / 2);
       const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * TC_BN + half * (TC_BN / 2));
@@ -429,7 +431,10 @@ int taps_eval_tc(taps_problem* P, const float* G, const GridSpec& gs, int split,
   const long long ntiles = nrb * ncb;
   const int grid = (int)std::min<long long>(ntiles, P->num_sms);
   const int vec_ok = ((cols & 3) == 0 && (((uintptr_t)out) & 15) == 0) ? 1 : 0;
-  eval_tc_kernel<<<grid, TC_THREADS, smem, s>>>(Aimg, Bimg, rows, (int)cols, ksteps, out, vec_ok,
+  // the larger operand image is walked in the outer order, so that each of its blocks
+  // is read from HBM once and its neighbours' tiles find it in L2
+  const int rowmajor = (nrb * TC_BM > ncb * TC_BN) && nrb * TC_BM * 2ll * ksteps * TC_KSTEP * 4 > (32ll << 20);
+  eval_tc_kernel<<<grid, TC_THREADS, smem, s>>>(Aimg, Bimg, rows, (int)cols, ksteps, out, vec_ok, rowmajor,
                                                  P->d_status);
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
