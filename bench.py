@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched measurement (0: off)")
     ap.add_argument("--no-large", action="store_true", help="skip the 1536^3 reconstruction measurement")
     ap.add_argument("--no-lpbf", action="store_true", help="skip the powder-bed-fusion slab measurement")
-    ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,mixed_fastdiag,"
-                                       "mixed_fastdiag_mlp",
+    ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,bf16gram_fastdiag,"
+                                       "mixed_fastdiag,mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
     return ap.parse_args()
 
@@ -254,6 +254,7 @@ def run_ours(args, rank, world, local):
              "fp64_fastdiag": (taps.FP64, taps.SOLVER_FASTDIAG),
              "fp64_modediag": (taps.FP64, taps.SOLVER_MODEDIAG),
              "fp32gram_fastdiag": (taps.FP32, taps.SOLVER_FASTDIAG),
+             "bf16gram_fastdiag": (taps.BF16, taps.SOLVER_FASTDIAG),
              "mixed_fastdiag": (taps.MIXED, taps.SOLVER_FASTDIAG),
              "mixed_fastdiag_mlp": (taps.MIXED, taps.SOLVER_FASTDIAG, "mlp")}
     paths = {k: v for k, v in paths.items() if k in args.paths.split(",")}

@@ -82,6 +82,9 @@ extern "C" {
 #define TAPS_MIXED 2  /* FP64 Grams; the n small M x M systems of the fast-diagonalisation
                          solve factorised in FP32 and refined in FP64 to FP64 backward
                          accuracy (FP64 LU fallback per system) */
+#define TAPS_BF16 3   /* Gram / SpMM contractions on BF16-rounded operands (factors, bands,
+                         source vectors) with FP32 accumulation; FP64 solves and residuals;
+                         handled by taps_solve like TAPS_FP32 (guard, FP64 polish) */
 
 /* ---- residual kinds ----------------------------------------------------------- */
 #define TAPS_RES_ALS 0   /* max_d ||K^[d] U_d - Q^[d]|| / ||Q^[d]|| of Eq. 42           */

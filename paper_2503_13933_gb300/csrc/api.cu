@@ -138,7 +138,7 @@ static int graph_build(taps_problem* P, taps_factors* U, int prec, int solver, i
     st = TAPS_ERR_CUDA;
   } else {
     st = taps_sweep_enqueue(P, U, prec, solver, 1);
-    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind, prec != TAPS_FP32);
+    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind, !taps_low_prec(prec));
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
     if (ce != cudaSuccess || g == nullptr) st = (st == TAPS_OK) ? TAPS_ERR_CUDA : st;
@@ -296,7 +296,7 @@ static int loop_build(taps_problem* P, taps_factors* U, int prec, int solver, do
       st = TAPS_ERR_CUDA;
     } else {
       st = taps_sweep_enqueue(P, U, prec, solver, 1, 0);
-      if (st == TAPS_OK) st = taps_residual_enqueue(P, U, TAPS_RES_ALS, prec != TAPS_FP32, 0);
+      if (st == TAPS_OK) st = taps_residual_enqueue(P, U, TAPS_RES_ALS, !taps_low_prec(prec), 0);
       if (st == TAPS_OK) {
         solve_decide_kernel<<<1, 32, 0, P->stream>>>(L->h, P->d_scal, U->M, P->D, P->d_partial, rg, res_tol, als_tol,
                                                      max_sweeps, L->d_state, L->d_hist, max_sweeps, P->d_status);
@@ -767,7 +767,7 @@ extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const 
   int precision = opts ? opts->precision : TAPS_FP64;
   int solver = opts ? opts->solver : TAPS_SOLVER_BLOCK_LU;
   int normalize = opts ? opts->normalize : 1;
-  if (precision != TAPS_FP64 && precision != TAPS_FP32 && precision != TAPS_MIXED) return TAPS_ERR_INVALID_ARG;
+  if (precision < TAPS_FP64 || precision > TAPS_BF16) return TAPS_ERR_INVALID_ARG;
   if (solver < TAPS_SOLVER_BLOCK_LU || solver > TAPS_SOLVER_MODEDIAG) return TAPS_ERR_INVALID_ARG;
   double t0 = now_s();
   TAPS_TRY(taps_ws_ensure(P, U->M));
@@ -794,7 +794,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
                           taps_solve_report* rep) {
   if (!P || !U || !o || U->prob != P) return TAPS_ERR_INVALID_ARG;
   if (o->M_max < 1 || o->M_max > U->M_cap || o->max_sweeps < 1 ||
-      (o->precision != TAPS_FP64 && o->precision != TAPS_FP32 && o->precision != TAPS_MIXED) ||
+      o->precision < TAPS_FP64 || o->precision > TAPS_BF16 ||
       (o->res_kind != TAPS_RES_ALS && o->res_kind != TAPS_RES_FULL) ||
       o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO ||
       o->solver < TAPS_SOLVER_BLOCK_LU || o->solver > TAPS_SOLVER_MODEDIAG)
@@ -821,7 +821,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
     int prec = precision;
     // FP64 / MIXED with graphs and the Eq. 42 residual: the whole sweep loop of this M
     // on the device (no host round trip per sweep)
-    if (o->graphs == 2 && prec != TAPS_FP32 && o->res_kind == TAPS_RES_ALS && !P->prof->events) {
+    if (o->graphs == 2 && !taps_low_prec(prec) && o->res_kind == TAPS_RES_ALS && !P->prof->events) {
       int done = 0, fallback = 0;
       const double* dh = nullptr;
       const int lst = loop_solve(P, U, prec, o->solver, o->res_tol, o->als_tol, o->max_sweeps, &done, &dh, &fallback);
@@ -848,7 +848,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       }
     }
     for (int it = 0; it < o->max_sweeps; ++it) {
-      if (prec == TAPS_FP32) {
+      if (taps_low_prec(prec)) {
         for (int d = 0; d < P->D; ++d)
           TAPS_CUDA(cudaMemcpyAsync(P->d_Usnap[d], U->d_U[d], sizeof(double) * P->dims[d]->nf * M,
                                     cudaMemcpyDeviceToDevice, P->stream));
@@ -860,7 +860,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
         rho_done = (sst == TAPS_OK);
       }
       if (fallback) sst = taps_sweep_impl(P, U, prec, o->solver, 1, &change);
-      if (prec == TAPS_FP32 && (sst == TAPS_ERR_SINGULAR || sst == TAPS_ERR_NONFINITE)) {
+      if (taps_low_prec(prec) && (sst == TAPS_ERR_SINGULAR || sst == TAPS_ERR_NONFINITE)) {
         // FP32 Grams cannot separate modes that agree to ~1e-8 (a Gram entry rounds to
         // an exact duplicate): restore the factors and redo the sweep in FP64.
         for (int d = 0; d < P->D; ++d)
@@ -874,7 +874,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       TAPS_TRY(sst);
       ++sweeps;
       if (prec == TAPS_FP64) ++fp64_sweeps;
-      if (!rho_done) TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho, prec != TAPS_FP32));
+      if (!rho_done) TAPS_TRY(taps_residual_impl(P, U, o->res_kind, &rho, !taps_low_prec(prec)));
       if (o->history_cap > 0 && rep && hist < o->history_cap) {
         if (rep->hist_M) rep->hist_M[hist] = M;
         if (rep->hist_change) rep->hist_change[hist] = change;
@@ -883,8 +883,8 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       }
       if (rho <= o->res_tol) { converged = true; break; }
       if (change <= o->als_tol) break;
-      if (prec == TAPS_FP32) {
-        // FP32 Grams stop helping once the residual no longer falls: refine in FP64.
+      if (taps_low_prec(prec)) {
+        // FP32 / BF16 Grams stop helping once the residual no longer falls: refine in FP64.
         // If the FP32 sweep made the residual grow (an ill-conditioned factor set
         // amplifies single-precision Gram errors), go back to the pre-sweep factors.
         if (rho > 0.5 * prev_rho) {
@@ -898,7 +898,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
           if (polish_left <= 0) break;
           prec = TAPS_FP64;
         }
-      } else if (precision == TAPS_FP32) {
+      } else if (taps_low_prec(precision)) {
         if (--polish_left <= 0) break;
       }
       prev_rho = rho;

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "taps_internal.cuh"
 
 // ---------------------------------------------------------------------------------
@@ -85,7 +87,15 @@ __global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call,
 #define GR 8
 #define GMT 8
 
-template <typename T>
+// Operand as the contraction sees it: with BF16IN rounded to bfloat16 (round to
+// nearest even) and widened to the accumulation type.
+template <typename T, bool BF16IN>
+__device__ __forceinline__ T gram_in(double x) {
+  if (BF16IN) return (T)__bfloat162float(__float2bfloat16_rn((float)x));
+  return (T)x;
+}
+
+template <typename T, bool BF16IN>
 __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M, int hb,
                                     const double* __restrict__ opband, int nops,
                                     const double* __restrict__ q, int Rf,
@@ -105,7 +115,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
   for (int idx = threadIdx.x; idx < rows_h * M; idx += blockDim.x) {
     int m = idx / rows_h, rr = idx % rows_h;
     int gi = r0 - hb + rr;
-    Us[rr * M + m] = (gi >= 0 && gi < nf) ? (T)U[(size_t)m * nf + gi] : (T)0;
+    Us[rr * M + m] = (gi >= 0 && gi < nf) ? gram_in<T, BF16IN>(U[(size_t)m * nf + gi]) : (T)0;
   }
   __syncthreads();
   double* out = partial + ((size_t)blockIdx.x) * stride;
@@ -117,7 +127,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
       T acc = 0;
       if (gi < nf) {
         const double* brow = band + (size_t)gi * nb;
-        for (int k = 0; k < nb; ++k) acc += (T)brow[k] * Us[(i + k) * M + n];
+        for (int k = 0; k < nb; ++k) acc += gram_in<T, BF16IN>(brow[k]) * Us[(i + k) * M + n];
       }
       Ys[i * M + n] = acc;
     }
@@ -135,7 +145,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
     T acc = 0;
     for (int i = 0; i < GR; ++i) {
       int gi = r0 + i;
-      if (gi < nf) acc += (T)q[(size_t)r * nf + gi] * Us[(i + hb) * M + m];
+      if (gi < nf) acc += gram_in<T, BF16IN>(q[(size_t)r * nf + gi]) * Us[(i + hb) * M + m];
     }
     out[(size_t)nops * M * M + (size_t)r * M + m] = (double)acc;
   }
@@ -205,12 +215,17 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
   GramPtrs gp = gram_ptrs(P);
   int tk = prof_begin(P, TAPS_PROF_GRAM);
   if (precision == TAPS_FP32) {   // TAPS_MIXED keeps FP64 Grams
-    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float>, grid, dim3(256), elems * sizeof(float), P->stream,
-                              (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
+    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, false>, grid, dim3(256), elems * sizeof(float),
+                              P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
+                              (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
+                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
+  } else if (precision == TAPS_BF16) {
+    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, true>, grid, dim3(256), elems * sizeof(float),
+                              P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
                               (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
                               P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
   } else {
-    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<double>, grid, dim3(256), elems * sizeof(double),
+    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<double, false>, grid, dim3(256), elems * sizeof(double),
                               P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d],
                               nops, (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
                               P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
@@ -651,8 +666,9 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
   int maxsm = 0;
   TAPS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   TAPS_TRY(taps_allow_dyn_smem((const void*)block_lu_kernel, maxsm));
-  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<double>, maxsm));
-  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float>, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<double, false>, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, false>, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, true>, maxsm));
   TAPS_TRY(residual_setup(maxsm));
   int bps = 0;
   size_t smem_max = sizeof(double) * TAPS_MAX_M * (TAPS_MAX_M + 1);

@@ -339,6 +339,9 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
 // Per-dim ranges of the ALS residual's partial sums (CTA indices [cta0[d], cta0[d+1])).
 int taps_als_partial_ranges(const taps_problem* P, int* cta0);
 int taps_residual_finish(taps_problem* P, const taps_factors* U, int kind, double* rho_out);
+// Reduced-precision Gram contractions (FP32 or BF16-rounded inputs, FP32 accumulation).
+static inline bool taps_low_prec(int precision) { return precision == TAPS_FP32 || precision == TAPS_BF16; }
+
 // How dim d is solved at M modes under `solver`.
 #define TAPS_ROUTE_LU 0
 #define TAPS_ROUTE_FD 1   // node-side pencil (fastdiag.cu)

@@ -25,7 +25,7 @@ SPACE, PARAM, TIME = 0, 1, 2
 OP = {"K": 0, "M": 1, "G": 2, "W": 3, "Blo": 4, "Bhi": 5}
 NUM_OPS = 6
 SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4, "opvec": 5}
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, BF16 = 0, 1, 2, 3
 RES_ALS, RES_FULL = 0, 1
 INIT_GIVEN, INIT_RANDOM, INIT_ZERO = 0, 1, 2
 SOLVER_BLOCK_LU, SOLVER_FASTDIAG, SOLVER_MODEDIAG, SOLVER_AUTO = 0, 1, 2, 3

@@ -482,6 +482,26 @@ def test_fp32_grams_then_fp64_polish(T):
     assert e < 1e-6, (e, r["rho"])
 
 
+def test_bf16_grams_then_fp64_polish(T):
+    """BF16-rounded Gram operands with FP32 accumulation (TAPS_BF16): the BF16 sweeps
+    carry BF16-level error, the solve hands over to FP64 and polishing restores the
+    mixed-path bound 1e-6 against the full-rank solution."""
+    desc = _full_rank_2d(20, 20, seed=23)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    u_full = O.solve_full(Po)
+    U = P.factors(18)
+    U.set(W.random_factors(desc, 18, seed=7))
+    P.sweep(U, 2, precision=T.BF16)
+    e16 = np.linalg.norm(O.cp_full(U.get()) - u_full) / np.linalg.norm(u_full)
+    assert 1e-6 < e16 < 1.0
+    r = P.solve(U, M_max=18, res_tol=1e-30, max_sweeps=8, init=T.INIT_GIVEN, precision=T.BF16,
+                polish_sweeps=3)
+    assert r["fp64_sweeps"] >= 1, r
+    e = np.linalg.norm(O.cp_full(U.get()) - u_full) / np.linalg.norm(u_full)
+    assert e < 1e-6, (e, r["rho"])
+
+
 def test_fp32_solve_poisson_matches_fp64(T):
     """3D Poisson, greedy to a full-residual target: the mixed-precision solve and the
     FP64 solve reconstruct the same field within the mixed-path bound 1e-6."""
