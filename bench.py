@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched measurement (0: off)")
     ap.add_argument("--no-large", action="store_true", help="skip the 1536^3 reconstruction measurement")
     ap.add_argument("--no-lpbf", action="store_true", help="skip the powder-bed-fusion slab measurement")
+    ap.add_argument("--no-e2e-modediag", action="store_true", help="skip the mode-side end-to-end solve")
     ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,bf16gram_fastdiag,"
                                        "mixed_fastdiag,mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
@@ -334,7 +335,9 @@ def run_ours(args, rank, world, local):
         return time.perf_counter() - t0, rep2, Uout
 
     e2e_s, rep2, Uout = end_to_end(taps.SOLVER_FASTDIAG)
-    e2e_md_s, rep_md, _ = end_to_end(taps.SOLVER_MODEDIAG)   # no n_d x n_d pencil set-up
+    e2e_md_s, rep_md = None, None
+    if not args.no_e2e_modediag:
+        e2e_md_s, rep_md, _ = end_to_end(taps.SOLVER_MODEDIAG)   # no n_d x n_d pencil set-up
     d2h = sum(u.nbytes for u in Uout) + 8
 
     best = headline if res[headline]["converged"] else \
@@ -561,7 +564,7 @@ def run_ours(args, rank, world, local):
         e2e=dict(value=e2e_s, unit="s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                  converged=rep2["converged"]),
         e2e_modediag=dict(value=allmax(e2e_md_s, world), unit="s", sweeps=rep_md["sweeps"],
-                          converged=rep_md["converged"]),
+                          converged=rep_md["converged"]) if rep_md is not None else None,
         gpu_launches=launches,
         warm_start=ws_info,
         batched=batched,
