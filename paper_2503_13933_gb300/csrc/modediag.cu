@@ -165,7 +165,15 @@ __global__ void __launch_bounds__(MD_THREADS) md_eig_kernel(const double* __rest
   __syncthreads();
   // cyclic Jacobi, round-robin pairing: N = M rounded up to even players, N - 1
   // rounds of N / 2 disjoint pairs per sweep; a pair with the padding player idles
+  // (its rotation is the identity; the padding row and column of S are zero)
   const int N = M + (M & 1), half = N / 2;
+  if (N > M) {
+    for (int j = tid; j < N; j += nt) {
+      S[M][j] = 0.0;
+      S[j][M] = 0.0;
+    }
+    __syncthreads();
+  }
   for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
     if (tid == 0) rotated = 0;
     __syncthreads();
@@ -204,32 +212,48 @@ __global__ void __launch_bounds__(MD_THREADS) md_eig_kernel(const double* __rest
         rq[tid] = q;
       }
       __syncthreads();
-      // columns p, q of S and V: S <- S J, V <- V J
-      for (int idx = tid; idx < half * M; idx += nt) {
-        const int k = idx / M, i = idx % M;
-        const double sn = rs[k];
-        if (sn != 0.0) {
-          const double cs = rc[k];
-          const int p = rp[k], q = rq[k];
-          const double sp = S[i][p], sq = S[i][q];
-          S[i][p] = cs * sp - sn * sq;
-          S[i][q] = sn * sp + cs * sq;
-          const double vp = V[i][p], vq = V[i][q];
-          V[i][p] = cs * vp - sn * vq;
-          V[i][q] = sn * vp + cs * vq;
+      // S <- J^T S J by 2 x 2 blocks of the round's pairs (k <= l; the lower block is
+      // the transpose, the annihilated entry of a diagonal block is set to zero), and
+      // V <- V J by row pairs, in one pass: the blocks and the row pairs are disjoint
+      for (int idx = tid; idx < half * half; idx += nt) {
+        const int k = idx / half, l = idx % half;
+        if (k > l) continue;
+        const double sk = rs[k], sl = rs[l];
+        if (sk == 0.0 && sl == 0.0) continue;
+        const double ck = rc[k], cl = rc[l];
+        const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
+        // B J_l
+        const double b00 = S[pk][pl], b01 = S[pk][ql], b10 = S[qk][pl], b11 = S[qk][ql];
+        const double t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+        const double t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+        // J_k^T (B J_l)
+        const double n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+        const double n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+        if (k == l) {
+          S[pk][pk] = n00;
+          S[qk][qk] = n11;
+          S[pk][qk] = 0.0;
+          S[qk][pk] = 0.0;
+        } else {
+          S[pk][pl] = n00;
+          S[pk][ql] = n01;
+          S[qk][pl] = n10;
+          S[qk][ql] = n11;
+          S[pl][pk] = n00;
+          S[ql][pk] = n01;
+          S[pl][qk] = n10;
+          S[ql][qk] = n11;
         }
       }
-      __syncthreads();
-      // rows p, q of S: S <- J^T S
       for (int idx = tid; idx < half * M; idx += nt) {
-        const int k = idx / M, j = idx % M;
-        const double sn = rs[k];
-        if (sn != 0.0) {
-          const double cs = rc[k];
-          const int p = rp[k], q = rq[k];
-          const double sp = S[p][j], sq = S[q][j];
-          S[p][j] = cs * sp - sn * sq;
-          S[q][j] = sn * sp + cs * sq;
+        const int l = idx / M, i = idx % M;
+        const double sl = rs[l];
+        if (sl != 0.0) {
+          const double cl = rc[l];
+          const int pl = rp[l], ql = rq[l];
+          const double vp = V[i][pl], vq = V[i][ql];
+          V[i][pl] = cl * vp - sl * vq;
+          V[i][ql] = sl * vp + cl * vq;
         }
       }
       __syncthreads();
