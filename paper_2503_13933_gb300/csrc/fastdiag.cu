@@ -37,9 +37,9 @@ __global__ void fd_dense_kernel(const double* __restrict__ bandA, const double* 
   B[idx] = in ? bandB[(size_t)i * nb + k] : 0.0;
 }
 
-// Single-CTA part of the pencil decomposition.  On exit B holds the banded Cholesky
-// factor L (lower) and, when the pencil has an A, A holds S = L^{-1} A L^{-T}
-// (symmetrised); V is n x n scratch.
+// Single-CTA part of the pencil decomposition: on exit B holds the banded Cholesky
+// factor L (lower).  S = L^{-1} A L^{-T} follows in fd_lsolve_kernel (twice) and
+// fd_symmetrize_kernel, column-parallel over many CTAs.
 __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double* B, double* V, int n, int hb,
                                                               int hasA, int* status) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -68,32 +68,33 @@ __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double*
     __syncthreads();
   }
 
-  if (hasA) {
-    // ---- 2. X = L^{-1} A (column by column), then S = L^{-1} X^T (A symmetric)
-    for (int c = tid; c < n; c += nt) {
-      for (int i = 0; i < n; ++i) {
-        double s = AT(A, i, c);
-        for (int j = max(0, i - hb); j < i; ++j) s -= AT(B, i, j) * AT(A, j, c);
-        AT(A, i, c) = s / AT(B, i, i);
-      }
-    }
-    __syncthreads();
-    for (int r = tid; r < n; r += nt) {   // column r of S into V (row-major V[i][r])
-      for (int i = 0; i < n; ++i) {
-        double s = AT(A, r, i);
-        for (int j = max(0, i - hb); j < i; ++j) s -= AT(B, i, j) * AT(V, j, r);
-        AT(V, i, r) = s / AT(B, i, i);
-      }
-    }
-    __syncthreads();
-    for (long long idx = tid; idx < (long long)n * n; idx += nt) {
-      int i = idx / n, j = idx % n;
-      A[idx] = 0.5 * (AT(V, i, j) + AT(V, j, i));
-    }
-    __syncthreads();
-
-  }
+  (void)A;
+  (void)V;
+  (void)hasA;
 #undef AT
+}
+
+// Out[:, c] = L^{-1} (In[:, c] or, with transposed input, In[c, :]^T) for the banded
+// lower factor L (half-bandwidth hb): one thread per column c, the chain of n
+// substitutions with the diagonal's reciprocal; 32-thread CTAs spread the columns over
+// the SMs (each chain is FP64-latency bound).
+__global__ void __launch_bounds__(32) fd_lsolve_kernel(const double* __restrict__ L, const double* __restrict__ In,
+                                                       int n, int hb, int trans_in, double* __restrict__ Out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = 0; i < n; ++i) {
+    double s = trans_in ? In[(size_t)c * n + i] : In[(size_t)i * n + c];
+    for (int j = max(0, i - hb); j < i; ++j) s -= L[(size_t)i * n + j] * Out[(size_t)j * n + c];
+    Out[(size_t)i * n + c] = s * taps_rcp(L[(size_t)i * n + i]);
+  }
+}
+
+// A = (V + V^T) / 2
+__global__ void fd_symmetrize_kernel(const double* __restrict__ V, int n, double* __restrict__ A) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  A[idx] = 0.5 * (V[(size_t)i * n + j] + V[(size_t)j * n + i]);
 }
 
 // ---------------------------------------------------------------------------------
@@ -544,7 +545,7 @@ __global__ void fd_phi_kernel(const double* __restrict__ L, const double* __rest
   for (int i = n - 1; i >= 0; --i) {
     double sacc = Z ? Z[(size_t)i * n + c] : (i == c ? 1.0 : 0.0);
     for (int j = i + 1; j <= min(n - 1, i + hb); ++j) sacc -= L[(size_t)j * n + i] * Phi[(size_t)j * n + c];
-    const double v = sacc / L[(size_t)i * n + i];
+    const double v = sacc * taps_rcp(L[(size_t)i * n + i]);
     Phi[(size_t)i * n + c] = v;
     PhiT[(size_t)c * n + i] = v;
   }
@@ -1038,6 +1039,11 @@ static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry**
     // banded Cholesky and S (one CTA), then the tridiagonalisation (one cluster)
     fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(A, B, V, n, dm->hb, hasA, P->d_status);
     if (hasA) {
+      // S = L^{-1} A L^{-T}: X = L^{-1} A into V, S^T = L^{-1} X^T into W, symmetrised into A
+      fd_lsolve_kernel<<<(n + 31) / 32, 32, 0, s>>>(B, A, n, dm->hb, 0, V);
+      fd_lsolve_kernel<<<(n + 31) / 32, 32, 0, s>>>(B, V, n, dm->hb, 1, W);
+      fd_symmetrize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(W, n, A);
+      if (cudaMemsetAsync(V, 0, sizeof(double) * nn, s) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
       const size_t dsm = sizeof(double) * ((size_t)((n + TD_CTAS - 1) / TD_CTAS) * n + 3 * (size_t)n);
       if (dsm + 1024 <= (size_t)maxsm_optin) {   // S fits the cluster's shared memory
         if ((st = taps_allow_dyn_smem((const void*)fd_tridiag_dsmem_kernel, maxsm_optin)) != TAPS_OK) break;
@@ -1050,7 +1056,8 @@ static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry**
       // all into A, which the tridiagonalisation no longer needs
       // two warps per CTA: the warps' FP64 chains spread over the SMs' sub-partitions
       fd_bisect_kernel<<<(unsigned)((32LL * n + 63) / 64), 64, 0, s>>>(T->dd, T->ee, n, lam);
-      fd_invit_kernel<<<(n + 127) / 128, 128, 0, s>>>(T->dd, T->ee, lam, n, A, W);
+      // one thread per eigenvector in 32-thread CTAs: the chains spread over the SMs
+      fd_invit_kernel<<<(n + 31) / 32, 32, 0, s>>>(T->dd, T->ee, lam, n, A, W);
       // symmetric orthogonalisation: E in W, the corrected vectors back into A
       const unsigned gnn = (unsigned)((nn + 255) / 256);
       fd_gram_minus_identity_kernel<<<gnn, 256, 0, s>>>(A, n, W);
@@ -1063,7 +1070,7 @@ static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry**
       fd_backtransform_kernel<<<(n + wpc - 1) / wpc, 32 * wpc, sizeof(double) * (size_t)n * wpc, s>>>(
           V, T->bt, n, A);
     }
-    fd_phi_kernel<<<(n + 127) / 128, 128, 0, s>>>(B, hasA ? A : nullptr, hasA ? lam : nullptr, n, dm->hb, E.Phi,
+    fd_phi_kernel<<<(n + 31) / 32, 32, 0, s>>>(B, hasA ? A : nullptr, hasA ? lam : nullptr, n, dm->hb, E.Phi,
                                                   E.PhiT, E.mu, P->d_status);
     prof_end(P, TAPS_PROF_OTHER, tk, (10.0 / 3.0) * (double)nn * n, 8.0 * 4.0 * nn);
     cudaError_t ce = cudaGetLastError();
