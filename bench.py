@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local):
                           solver=solver)
         else:
             rep = P.solve(U, M0=M, M_max=M, res_tol=WORKLOAD["res_tol"], res_kind=taps.RES_ALS,
-                          max_sweeps=60, precision=precision, polish_sweeps=30,
+                          max_sweeps=60, precision=precision, polish_sweeps=60,
                           init=taps.INIT_RANDOM, seed=seed, als_tol=0.0, solver=solver)
         e1.record(stream)
         P.eval_grid(U, [0, 0, 0, 0], count, [1, 1, 1, 1], field, dtype=taps.FP32)
