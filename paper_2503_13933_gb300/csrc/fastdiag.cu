@@ -99,7 +99,8 @@ __global__ void fd_symmetrize_kernel(const double* __restrict__ V, int n, double
 
 // ---------------------------------------------------------------------------------
 // Householder tridiagonalisation S = Q T Q^T of the symmetric S held in A (n x n,
-// row-major), on one cluster of TD_CTAS CTAs with hardware cluster barriers between
+// row-major), on one cluster of NC CTAs (16 where the GPU can place a 16-CTA cluster,
+// else 8; the arithmetic is the same for both) with hardware cluster barriers between
 // the phases of a step.  Step k: every CTA stages column k below the diagonal in
 // shared memory and forms the same reflector v (beta = 2 / v.v); one warp per row of
 // the cluster computes p = beta S22 v; after a cluster barrier every CTA forms
@@ -108,7 +109,6 @@ __global__ void fd_symmetrize_kernel(const double* __restrict__ V, int n, double
 // On exit (d, e) hold T (e[i] couples i and i+1), the rows of V the reflectors
 // (row k: entries k+1 .. n-1) and beta their factors.
 // ---------------------------------------------------------------------------------
-#define TD_CTAS 8
 #define TD_THREADS 1024
 __device__ __forceinline__ void td_cluster_sync() {
   asm volatile(
@@ -116,7 +116,8 @@ __device__ __forceinline__ void td_cluster_sync() {
       "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
+template <int NC>
+__global__ void __launch_bounds__(TD_THREADS)
     fd_tridiag_kernel(double* __restrict__ A, double* __restrict__ V, double* __restrict__ p,
                       double* __restrict__ beta, double* __restrict__ d, double* __restrict__ e, int n) {
   extern __shared__ double tds[];   // v [n], p [n], w [n]
@@ -127,7 +128,7 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
   const int rank = blockIdx.x;   // the grid is one cluster
   const int tid = threadIdx.x, lane = tid & 31;
   const int gwarp = rank * (TD_THREADS / 32) + (tid >> 5);
-  const int nwarps = TD_CTAS * (TD_THREADS / 32);
+  const int nwarps = NC * (TD_THREADS / 32);
 #define AT(i, j) A[(size_t)(i) * n + (j)]
   for (int k = 0; k + 2 < n; ++k) {
     const int len = n - k - 1;
@@ -200,13 +201,14 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
 }
 
 // The same tridiagonalisation with S held in the cluster's distributed shared memory
-// (n small enough that ceil(n / TD_CTAS) rows of n doubles fit one CTA's shared memory):
-// CTA r keeps rows i = r, r + TD_CTAS, ...  Step k: every CTA gathers column k from the
+// (n small enough that ceil(n / NC) rows of n doubles fit one CTA's shared memory):
+// CTA r keeps rows i = r, r + NC, ...  Step k: every CTA gathers column k from the
 // rows' owners (remote shared-memory loads), forms the reflector, computes p_i for its
 // own rows and stores each p_i into every CTA's copy of p; after a cluster barrier
 // every CTA forms w and updates its own rows; a second barrier ends the step.  S never
 // leaves shared memory.
-__global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
+template <int NC>
+__global__ void __launch_bounds__(TD_THREADS)
     fd_tridiag_dsmem_kernel(const double* __restrict__ A, double* __restrict__ V, double* __restrict__ beta,
                             double* __restrict__ d, double* __restrict__ e, int n) {
   extern __shared__ double tsm[];   // vs [n] | ps [n] | ws [n] | own rows [nr][n]
@@ -220,10 +222,10 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
   double* ps = tsm + n;
   double* ws = tsm + 2 * n;
   double* rows = tsm + 3 * n;
-  const int nr = (n - rank + TD_CTAS - 1) / TD_CTAS;   // rows i = rank + TD_CTAS * l, l < nr
+  const int nr = (n - rank + NC - 1) / NC;   // rows i = rank + NC * l, l < nr
   for (long long idx = tid; idx < (long long)nr * n; idx += TD_THREADS) {
     const int l = (int)(idx / n), j = (int)(idx % n);
-    rows[(size_t)l * n + j] = A[(size_t)(rank + TD_CTAS * l) * n + j];
+    rows[(size_t)l * n + j] = A[(size_t)(rank + NC * l) * n + j];
   }
   cluster.sync();
   for (int k = 0; k + 2 < n; ++k) {
@@ -232,14 +234,14 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
     double s2 = 0.0;
     for (int t = tid; t < len; t += TD_THREADS) {
       const int i = k + 1 + t;
-      const double* owner_rows = cluster.map_shared_rank(rows, i % TD_CTAS);
-      const double x = owner_rows[(size_t)(i / TD_CTAS) * n + k];
+      const double* owner_rows = cluster.map_shared_rank(rows, i % NC);
+      const double x = owner_rows[(size_t)(i / NC) * n + k];
       vs[t] = x;
       s2 += x * x;
     }
     s2 = block_sum(s2, red);
     if (s2 == 0.0) {   // the same in every CTA
-      if (k % TD_CTAS == rank && tid == 0) d[k] = rows[(size_t)(k / TD_CTAS) * n + k];
+      if (k % NC == rank && tid == 0) d[k] = rows[(size_t)(k / NC) * n + k];
       if (rank == 0 && tid == 0) {
         beta[k] = 0.0;
         e[k] = 0.0;
@@ -255,14 +257,14 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
     if (tid == 0) vs[0] = v0;
     __syncthreads();
     // p_i for own rows i >= k + 1, pushed into every CTA's ps
-    const int l0 = (k + 1 - rank + TD_CTAS - 1) / TD_CTAS;   // first own row >= k + 1
+    const int l0 = (k + 1 - rank + NC - 1) / NC;   // first own row >= k + 1
     for (int l = l0 + warp; l < nr; l += nwarps) {
-      const int i = rank + TD_CTAS * l;
+      const int i = rank + NC * l;
       const double* row = rows + (size_t)l * n + (k + 1);
       double acc = 0.0;
       for (int t = lane; t < len; t += 32) acc += row[t] * vs[t];
       acc = warp_sum(acc) * bk;
-      if (lane < TD_CTAS) cluster.map_shared_rank(ps, lane)[i - k - 1] = acc;
+      if (lane < NC) cluster.map_shared_rank(ps, lane)[i - k - 1] = acc;
     }
     cluster.sync();
     double pv = 0.0;
@@ -272,7 +274,7 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
     for (int t = tid; t < len; t += TD_THREADS) ws[t] = ps[t] - Kc * vs[t];
     __syncthreads();
     for (int l = l0 + warp; l < nr; l += nwarps) {
-      const int i = rank + TD_CTAS * l - (k + 1);   // index within the trailing block
+      const int i = rank + NC * l - (k + 1);   // index within the trailing block
       double* row = rows + (size_t)l * n + (k + 1);
       const double vi = vs[i], wi = ws[i];
       for (int t = lane; t < len; t += 32) row[t] -= vi * ws[t] + wi * vs[t];
@@ -284,13 +286,13 @@ __global__ void __cluster_dims__(TD_CTAS, 1, 1) __launch_bounds__(TD_THREADS)
         e[k] = alpha;
       }
     }
-    if (k % TD_CTAS == rank && tid == 0) d[k] = rows[(size_t)(k / TD_CTAS) * n + k];
+    if (k % NC == rank && tid == 0) d[k] = rows[(size_t)(k / NC) * n + k];
     cluster.sync();
   }
   if (tid == 0) {
     for (int i = (n >= 2 ? n - 2 : 0); i < n; ++i)
-      if (i % TD_CTAS == rank) d[i] = rows[(size_t)(i / TD_CTAS) * n + i];
-    if (n >= 2 && (n - 1) % TD_CTAS == rank) e[n - 2] = rows[(size_t)((n - 1) / TD_CTAS) * n + (n - 2)];
+      if (i % NC == rank) d[i] = rows[(size_t)(i / NC) * n + i];
+    if (n >= 2 && (n - 1) % NC == rank) e[n - 2] = rows[(size_t)((n - 1) / NC) * n + (n - 2)];
     if (rank == 0) {
       e[n - 1] = 0.0;
       for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) beta[k] = 0.0;
@@ -978,6 +980,83 @@ static void fd_pending_free(FdPending& T) {
   memset(&T, 0, sizeof(T));
 }
 
+// Cluster size of the tridiagonalisation: 16 CTAs when the device can run a 16-CTA
+// cluster of the kernel (non-portable size), else the portable 8.  Both variants do the
+// same arithmetic per row and per reduction, so the result does not depend on it.
+template <int NC>
+static bool td_cluster_ok(const void* fn, size_t smem) {
+  if (NC > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int maxsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (taps_allow_dyn_smem(fn, maxsm) != TAPS_OK) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC);
+  cfg.blockDim = dim3(TD_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters > 0;
+}
+
+template <int NC, typename... Args>
+static cudaError_t td_launch(void (*fn)(Args...), size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC);
+  cfg.blockDim = dim3(TD_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, args...);
+}
+
+// The tridiagonalisation of S (n x n in A) on one cluster: S in distributed shared
+// memory when its rows fit, else in global memory.
+static int td_run(double* A, double* V, double* tmp, double* bt, double* dd, double* ee, int n, int maxsm,
+                  cudaStream_t s) {
+  const size_t dsm16 = sizeof(double) * ((size_t)((n + 15) / 16) * n + 3 * (size_t)n);
+  const size_t dsm8 = sizeof(double) * ((size_t)((n + 7) / 8) * n + 3 * (size_t)n);
+  const size_t gsm = sizeof(double) * 3 * (size_t)n;
+  cudaError_t ce;
+  if (dsm16 + 1024 <= (size_t)maxsm && td_cluster_ok<16>((const void*)fd_tridiag_dsmem_kernel<16>, dsm16)) {
+    ce = td_launch<16>(fd_tridiag_dsmem_kernel<16>, dsm16, s, (const double*)A, V, bt, dd, ee, n);
+  } else if (dsm8 + 1024 <= (size_t)maxsm && td_cluster_ok<8>((const void*)fd_tridiag_dsmem_kernel<8>, dsm8)) {
+    ce = td_launch<8>(fd_tridiag_dsmem_kernel<8>, dsm8, s, (const double*)A, V, bt, dd, ee, n);
+  } else if (td_cluster_ok<16>((const void*)fd_tridiag_kernel<16>, gsm)) {
+    ce = td_launch<16>(fd_tridiag_kernel<16>, gsm, s, A, V, tmp, bt, dd, ee, n);
+  } else {
+    if (!td_cluster_ok<8>((const void*)fd_tridiag_kernel<8>, gsm)) return TAPS_ERR_CUDA;
+    ce = td_launch<8>(fd_tridiag_kernel<8>, gsm, s, A, V, tmp, bt, dd, ee, n);
+  }
+  if (ce != cudaSuccess) {
+    taps_note_cuda_error(ce, "tridiagonalisation launch", __FILE__, __LINE__);
+    return TAPS_ERR_CUDA;
+  }
+  return TAPS_OK;
+}
+
 // Enqueues the decomposition of the pencil (opA, opB) of dm on P's stream without
 // waiting for it: the entry is registered at once (pending, with an event recorded
 // after its last kernel) and the temporaries are returned in *T for fd_finish.  An
@@ -1012,9 +1091,6 @@ static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry**
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&maxsm_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
-    if (sizeof(double) * 3 * (size_t)n > 48 * 1024 &&
-        (st = taps_allow_dyn_smem((const void*)fd_tridiag_kernel, maxsm_optin)) != TAPS_OK)
-      break;
     if ((st = taps_alloc((void**)&E.Phi, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.PhiT, sizeof(double) * nn)) != TAPS_OK) break;
     if ((st = taps_alloc((void**)&E.mu, sizeof(double) * n)) != TAPS_OK) break;
@@ -1044,14 +1120,7 @@ static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry**
       fd_lsolve_kernel<<<(n + 31) / 32, 32, 0, s>>>(B, V, n, dm->hb, 1, W);
       fd_symmetrize_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(W, n, A);
       if (cudaMemsetAsync(V, 0, sizeof(double) * nn, s) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
-      const size_t dsm = sizeof(double) * ((size_t)((n + TD_CTAS - 1) / TD_CTAS) * n + 3 * (size_t)n);
-      if (dsm + 1024 <= (size_t)maxsm_optin) {   // S fits the cluster's shared memory
-        if ((st = taps_allow_dyn_smem((const void*)fd_tridiag_dsmem_kernel, maxsm_optin)) != TAPS_OK) break;
-        fd_tridiag_dsmem_kernel<<<TD_CTAS, TD_THREADS, dsm, s>>>(A, V, T->bt, T->dd, T->ee, n);
-      } else {
-        fd_tridiag_kernel<<<TD_CTAS, TD_THREADS, sizeof(double) * 3 * (size_t)n, s>>>(A, V, T->tmp, T->bt,
-                                                                                      T->dd, T->ee, n);
-      }
+      if ((st = td_run(A, V, T->tmp, T->bt, T->dd, T->ee, n, maxsm_optin, s)) != TAPS_OK) break;
       // eigenvalues (warp each), eigenvectors (thread each), back-transform (warp each),
       // all into A, which the tridiagonalisation no longer needs
       // two warps per CTA: the warps' FP64 chains spread over the SMs' sub-partitions
