@@ -397,6 +397,14 @@ int taps_profile_reset(taps_problem* prob, int enable_events);
 int taps_profile_get(taps_problem* prob, int kernel_class, long long* launches, double* ms,
                      double* flops, double* bytes);
 
+/* The library's bounded device-side grid barrier, for testing failure detection
+ * without a GPU fault: `ctas` CTAs (1..64) meet twice at a barrier that expects
+ * ctas + missing arrivals (missing 0..64), each wait bounded by poll_limit polls
+ * (1..2^26).  Returns TAPS_OK when missing = 0; with missing > 0 every wait runs out,
+ * the kernel records the timeout and returns, and the call returns TAPS_ERR_TIMEOUT
+ * with the CUDA context intact.  `stream` is a cudaStream_t (NULL: legacy stream). */
+int taps_util_barrier_test(int ctas, int missing, long long poll_limit, void* stream);
+
 /* ---- the FP64 reciprocal of the small reduced solves (no counterpart in the method;
  * exposed so that its accuracy can be checked against IEEE division) ---------------
  * y[i] = 1 / x[i] for n device doubles, from the hardware's approximate reciprocal

@@ -1324,3 +1324,40 @@ extern "C" int taps_util_rcp(const double* x_dev, double* y_dev, long long n, vo
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// The library's bounded grid barrier with a short poll limit, for its failure test:
+// `ctas` CTAs meet at a barrier that expects ctas + missing arrivals, twice.  With
+// missing > 0 every wait runs out after `limit` polls, records TAPS_DEV_TIMEOUT and the
+// kernel returns; the host reads the status.  Nothing waits without a bound.
+// ---------------------------------------------------------------------------------
+__global__ void barrier_test_kernel(unsigned* bar, int* status, unsigned expected, long long limit) {
+  grid_barrier(bar, status, expected, limit);
+  grid_barrier(bar, status, expected, limit);
+}
+
+extern "C" int taps_util_barrier_test(int ctas, int missing, long long poll_limit, void* stream) {
+  if (ctas < 1 || ctas > 64 || missing < 0 || missing > 64 || poll_limit < 1 || poll_limit > (1ll << 26))
+    return TAPS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* bar = nullptr;
+  int* status = nullptr;
+  TAPS_TRY(taps_alloc((void**)&bar, 2 * sizeof(unsigned)));
+  if (taps_alloc((void**)&status, sizeof(int)) != TAPS_OK) {
+    cudaFree(bar);
+    return TAPS_ERR_OOM;
+  }
+  int st = TAPS_OK;
+  if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) {
+    st = TAPS_ERR_CUDA;
+  } else {
+    barrier_test_kernel<<<ctas, 32, 0, s>>>(bar, status, (unsigned)(ctas + missing), poll_limit);
+    if (cudaGetLastError() != cudaSuccess) st = TAPS_ERR_CUDA;
+    else st = taps_check_status(status, s);
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(bar);
+  cudaFree(status);
+  return st;
+}

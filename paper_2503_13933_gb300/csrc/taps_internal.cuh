@@ -250,7 +250,8 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // a generation counter; every wait is bounded: after `limit` polls the barrier
 // records TAPS_DEV_TIMEOUT and stops waiting, and later barriers return at once, so
 // the kernel always runs to its end and the host reads the status.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status, unsigned nblocks) {
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status, unsigned nblocks,
+                                             long long limit = (1ll << 26)) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = bar + 1;
@@ -266,7 +267,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status, unsigne
       } else {
         long long polls = 0;
         while (*vgen == gen) {
-          if (++polls > (1ll << 26)) {  // ~seconds: far above any legitimate wait
+          if (++polls > limit) {  // default ~seconds: far above any legitimate wait
             taps_flag(status, TAPS_DEV_TIMEOUT);
             break;
           }

@@ -108,6 +108,7 @@ SIGNATURES = {
     "taps_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_vp)]),
     "taps_batch_sweep": (_i, [_vp, _i, _i, _pd, _pi]),
     "taps_batch_info": (_i, [_vp, _pi, ctypes.POINTER(ctypes.c_float)]),
+    "taps_util_barrier_test": (_i, [_i, _i, ctypes.c_longlong, _vp]),
     "taps_batch_destroy": (None, [_vp]),
     "taps_mlp_create": (_i, [_i, _i, _i, _i, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
     "taps_mlp_num_params": (ctypes.c_longlong, [_vp]),
@@ -486,3 +487,10 @@ class Factors:
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.taps_factors_destroy(self.handle)
             self.handle = None
+
+
+def barrier_test(ctas, missing, poll_limit, stream=None):
+    """Status of the library's bounded grid barrier test (taps_util_barrier_test):
+    OK with every CTA present, ERR_TIMEOUT with `missing` CTAs that never arrive."""
+    return lib().taps_util_barrier_test(ctas, missing, poll_limit,
+                                        stream if stream is not None else current_stream())
