@@ -40,8 +40,7 @@ __global__ void fd_dense_kernel(const double* __restrict__ bandA, const double* 
 // Single-CTA part of the pencil decomposition: on exit B holds the banded Cholesky
 // factor L (lower).  S = L^{-1} A L^{-T} follows in fd_lsolve_kernel (twice) and
 // fd_symmetrize_kernel, column-parallel over many CTAs.
-__global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double* B, double* V, int n, int hb,
-                                                              int hasA, int* status) {
+__global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* B, int n, int hb, int* status) {
   const int tid = threadIdx.x, nt = blockDim.x;
 #define AT(M_, i, j) M_[(size_t)(i) * n + (j)]
 
@@ -68,9 +67,6 @@ __global__ void __launch_bounds__(FD_THREADS) fd_setup_kernel(double* A, double*
     __syncthreads();
   }
 
-  (void)A;
-  (void)V;
-  (void)hasA;
 #undef AT
 }
 
@@ -1113,7 +1109,7 @@ static int fd_enqueue(taps_problem* P, taps_dim* dm, int opA, int opB, FdEntry**
     fd_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(bandA, bandB, n, dm->hb, A, B);
     if (cudaMemsetAsync(V, 0, sizeof(double) * nn, s) != cudaSuccess) { st = TAPS_ERR_CUDA; break; }
     // banded Cholesky and S (one CTA), then the tridiagonalisation (one cluster)
-    fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(A, B, V, n, dm->hb, hasA, P->d_status);
+    fd_setup_kernel<<<1, FD_THREADS, 0, s>>>(B, n, dm->hb, P->d_status);
     if (hasA) {
       // S = L^{-1} A L^{-T}: X = L^{-1} A into V, S^T = L^{-1} X^T into W, symmetrised into A
       fd_lsolve_kernel<<<(n + 31) / 32, 32, 0, s>>>(B, A, n, dm->hb, 0, V);
