@@ -229,6 +229,28 @@ def test_modediag_poisson_matches_oracle(T, n_space, n_k, M):
     assert prof["fastdiag"]["launches"] == 0 and prof["block_lu"]["launches"] == 0
 
 
+@pytest.mark.parametrize("s,p,M", [(1, 1, 3), (0, 0, 3), (2, 1, 4)])
+def test_modediag_narrow_bands_match_oracle(T, s, p, M):
+    """The mode-side eliminations for band half-widths 3 (s = 1) and 1 (s = 0, linear
+    hats): 3D Poisson with rich separable sources, two sweeps against the oracle."""
+    desc = W.poisson_sin(14, D=3, s=s, p=p)
+    rng = np.random.default_rng(40 + s)
+    desc["sources"] = [(1.0, [("nodal", rng.uniform(-1.0, 1.0, dm["n"])) for dm in desc["dims"]])
+                       for _ in range(M)]
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, M, seed=90 + s)
+    Ug = P.factors(M)
+    Ug.set(U0)
+    P.sweep(Ug, 2, solver=T.SOLVER_MODEDIAG)
+    Uo = [u.copy() for u in U0]
+    for _ in range(2):
+        Uo, _ = O.sweep(Po, Uo, solver="modediag")
+    got = Ug.get()
+    for d in range(3):
+        assert rel(got[d], Uo[d]) < 1e-10, (d, rel(got[d], Uo[d]))
+
+
 @pytest.mark.parametrize("solver", ["fastdiag", "block_lu"])
 def test_graph_replay_matches_direct_launches(T, solver):
     """Sweeps replayed from a captured CUDA graph give the same history and factors as
