@@ -9,6 +9,8 @@
 
 #include "taps_internal.cuh"
 
+int taps_project_sources_dim(const taps_dim* d, const taps_source* sources, int Rf, int dimIndex, double* d_q,
+                             cudaStream_t s);
 int taps_project_source(const taps_dim* d, int kind, const double* par, const double* nodal_host,
                         double* d_q_free, cudaStream_t s);
 
@@ -644,9 +646,7 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
           st = TAPS_ERR_CUDA;
       if (st != TAPS_OK) break;
       if ((st = taps_alloc((void**)&P->d_q[d], sizeof(double) * Rf * dm->nf)) != TAPS_OK) break;
-      for (int r = 0; r < Rf && st == TAPS_OK; ++r)
-        st = taps_project_source(dm, sources[r].kind[d], sources[r].par[d], sources[r].nodal[d],
-                                 P->d_q[d] + (size_t)r * dm->nf, P->stream);
+      st = taps_project_sources_dim(dm, sources, Rf, d, P->d_q[d], P->stream);
     }
     if (st != TAPS_OK) break;
     if ((st = taps_sweep_setup(dev, P->num_sms, &P->coop_blocks)) != TAPS_OK) break;

@@ -311,11 +311,10 @@ __device__ __forceinline__ double source_factor(int kind, const double* par, dou
 
 // q_i = int N~_i g (Gauss sums over the elements touching node i), or for nodal
 // data q = M_full g; written for the free nodes only.
-__global__ void source_kernel(DimParams P, const double* Nt, const double* xq,
-                              const double* band_full, const double* band_free, int kind, double p0,
-                              double p1, double p2, double p3, const double* nodal, double* q_free) {
-  int fi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (fi >= P.nf) return;
+__device__ __forceinline__ void source_entry(const DimParams& P, const double* Nt, const double* xq,
+                                             const double* band_full, const double* band_free, int kind,
+                                             double p0, double p1, double p2, double p3, const double* nodal,
+                                             double* q_free, int fi) {
   int i = fi + P.off;
   double par[4] = {p0, p1, p2, p3};
   double v = 0.0;
@@ -343,6 +342,28 @@ __global__ void source_kernel(DimParams P, const double* Nt, const double* xq,
     }
   }
   q_free[fi] = v;
+}
+
+__global__ void source_kernel(DimParams P, const double* Nt, const double* xq,
+                              const double* band_full, const double* band_free, int kind, double p0,
+                              double p1, double p2, double p3, const double* nodal, double* q_free) {
+  int fi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fi >= P.nf) return;
+  source_entry(P, Nt, xq, band_full, band_free, kind, p0, p1, p2, p3, nodal, q_free, fi);
+}
+
+// Every source factor of one dim at once (blockIdx.y = source r): the same entry
+// arithmetic as source_kernel; kinds, parameters and the offsets of the nodal data in
+// one packed device buffer.
+__global__ void source_all_kernel(DimParams P, const double* Nt, const double* xq, const double* band_full,
+                                  const double* band_free, const int* kinds, const double* pars,
+                                  const long long* offs, const double* nodal, double* q) {
+  const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (fi >= P.nf) return;
+  const double* pr = pars + 4 * (size_t)r;
+  source_entry(P, Nt, xq, band_full, band_free, kinds[r], pr[0], pr[1], pr[2], pr[3],
+               offs[r] >= 0 ? nodal + offs[r] : nullptr, q + (size_t)r * P.nf, fi);
 }
 
 // ---------------------------------------------------------------------------------
@@ -500,6 +521,58 @@ int taps_project_source(const taps_dim* d, int kind, const double* par, const do
   }
   TAPS_CUDA(e);
   return TAPS_OK;
+}
+
+// Projections of every source factor of dim `dimIndex` onto the free nodes, into
+// d_q [Rf][nf]: the nodal data of all sources travel in one host-to-device copy
+// and one launch projects them all.
+int taps_project_sources_dim(const taps_dim* d, const taps_source* sources, int Rf, int dimIndex, double* d_q,
+                             cudaStream_t s) {
+  DimParams P = make_params(d);
+  std::vector<int> kinds(Rf);
+  std::vector<long long> offs(Rf, -1);
+  size_t tot = 0;
+  for (int r = 0; r < Rf; ++r) {
+    const int k = sources[r].kind[dimIndex];
+    if (k < TAPS_SRC_CONST || k > TAPS_SRC_OPVEC) return TAPS_ERR_INVALID_ARG;
+    kinds[r] = k;
+    if (k == TAPS_SRC_NODAL || k == TAPS_SRC_OPVEC) {
+      if (!sources[r].nodal[dimIndex]) return TAPS_ERR_INVALID_ARG;
+      offs[r] = (long long)tot;
+      tot += k == TAPS_SRC_NODAL ? d->n : d->nf;
+    }
+  }
+  // packed: pars [Rf][4] | nodal data | offsets | kinds
+  const size_t npar = 4 * (size_t)Rf;
+  const size_t bytes = sizeof(double) * (npar + tot) + sizeof(long long) * Rf + sizeof(int) * Rf;
+  std::vector<unsigned char> host(bytes);
+  double* hp = reinterpret_cast<double*>(host.data());
+  for (int r = 0; r < Rf; ++r)
+    for (int j = 0; j < 4; ++j) hp[4 * (size_t)r + j] = sources[r].par[dimIndex][j];
+  for (int r = 0; r < Rf; ++r)
+    if (offs[r] >= 0) {
+      const size_t len = kinds[r] == TAPS_SRC_NODAL ? d->n : d->nf;
+      memcpy(hp + npar + offs[r], sources[r].nodal[dimIndex], sizeof(double) * len);
+    }
+  memcpy(host.data() + sizeof(double) * (npar + tot), offs.data(), sizeof(long long) * Rf);
+  memcpy(host.data() + sizeof(double) * (npar + tot) + sizeof(long long) * Rf, kinds.data(), sizeof(int) * Rf);
+  unsigned char* dev = nullptr;
+  TAPS_TRY(taps_alloc((void**)&dev, bytes));
+  int st = TAPS_OK;
+  if (cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    st = TAPS_ERR_CUDA;
+  } else {
+    const double* dpars = reinterpret_cast<const double*>(dev);
+    const double* dnodal = dpars + npar;
+    const long long* doffs = reinterpret_cast<const long long*>(dev + sizeof(double) * (npar + tot));
+    const int* dkinds = reinterpret_cast<const int*>(dev + sizeof(double) * (npar + tot) + sizeof(long long) * Rf);
+    source_all_kernel<<<dim3((d->nf + 127) / 128, Rf), 128, 0, s>>>(P, d->d_N, d->d_xq, d->d_band_full, d->d_band,
+                                                                    dkinds, dpars, doffs, dnodal, d_q);
+    if (cudaGetLastError() != cudaSuccess) st = TAPS_ERR_CUDA;
+  }
+  cudaStreamSynchronize(s);   // the host staging buffer is released on return
+  cudaFree(dev);
+  return st;
 }
 
 // Device-side evaluation of all shape functions of element e at x (point evaluation,
