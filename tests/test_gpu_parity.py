@@ -295,6 +295,28 @@ def test_device_solve_loop_matches_host_loop(T, precision, res_tol):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("solver", ["fastdiag", "modediag"])
+def test_device_solve_loop_transient_routes(T, solver):
+    """The device-side solve loop on a transient problem with a convection face: the
+    time dim on the mode side (its stored basis carried across the loop's sweeps), the
+    convection dim by the face-corrected route, the other by the node-side pencil; same
+    sweeps, history and factors as the host loop."""
+    desc = _rich_transient(16, 24, 5, 2.0, seed=3060)
+    sv = T.SOLVER_FASTDIAG if solver == "fastdiag" else T.SOLVER_MODEDIAG
+    out = []
+    for graphs in (2, 1):
+        P = T.Problem(desc)
+        U = P.factors(5)
+        r = P.solve(U, M0=5, M_max=5, res_tol=1e-30, als_tol=0.0, max_sweeps=6, init=T.INIT_RANDOM, seed=7,
+                    solver=sv, graphs=graphs)
+        out.append((r, U.get()))
+    (ra, Ua), (rb, Ub) = out
+    assert ra["sweeps"] == rb["sweeps"] == 6
+    assert ra["history"] == rb["history"]
+    for a, b in zip(Ua, Ub):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("name,M,nsw", [("poisson3d_n12", 3, 3), ("poisson_k_7x9", 4, 2),
                                         ("heat2d_robin", 5, 3)])
 def test_mixed_refined_small_solves_parity(T, name, M, nsw):
