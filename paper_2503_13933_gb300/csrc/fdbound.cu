@@ -9,15 +9,17 @@
 // with T_i = mu_i C_A + C_B, g_i = (Phi^T F)[i], phi_b = Phi^T e_b (row b of Phi) and
 // C_b the coefficient matrix of face b's operator.  The face terms couple the nodes
 // only through the nb M-vectors z_b, so (Sherman-Morrison-Woodbury)
-//     y_i = w_i - sum_b beta_b phi_b[i] X_ib z_b,   w_i = T_i^-1 g_i,  X_ib = T_i^-1 C_b,
+//     y_i = w_i - T_i^-1 sum_b beta_b phi_b[i] C_b z_b,   w_i = T_i^-1 g_i,
 // and the z_b solve the (nb M) x (nb M) capacitance system
-//     z_b' + sum_b beta_b (sum_i phi_b'[i] phi_b[i] X_ib) z_b = sum_i phi_b'[i] w_i.
+//     z_b' + sum_b beta_b (sum_i phi_b'[i] phi_b[i] T_i^-1) C_b z_b = sum_i phi_b'[i] w_i.
 //
-//   fdw_node_kernel    warp per node: LU of T_i without pivoting, w_i and X_ib (1 + nb M
-//                      right-hand sides, lane = row).
-//   fdw_reduce_kernel  the sums over the nodes (capacitance blocks and right-hand side).
+//   fdw_node_kernel    warp per node: LU of T_i without pivoting, w_i and T_i^-1
+//                      (1 + M right-hand sides, lane = row).
+//   fdw_reduce_kernel  the sums over the nodes: Z_b'b = sum_i phi_b' phi_b T_i^-1 and
+//                      the capacitance right-hand side.
+//   fdw_zc_kernel      the capacitance blocks Z_b'b C_b.
 //   fdw_cap_kernel     one CTA: the capacitance system by Gaussian elimination with
-//                      partial pivoting.
+//                      partial pivoting, then u_b = C_b z_b.
 //   fdw_final_kernel   y_i; then the node-side transform U = Phi Y (fd_rowgemm_kernel).
 #include <string.h>
 
@@ -61,9 +63,8 @@ __device__ __forceinline__ void fdw_warp_solve(const double row[33], double invd
 }
 
 __global__ void __launch_bounds__(32) fdw_node_kernel(const double* __restrict__ CA, const double* __restrict__ CB,
-                                                      const double* __restrict__ C0, const double* __restrict__ C1,
                                                       const double* __restrict__ mu, const double* __restrict__ pq,
-                                                      const double* __restrict__ c, int Rf, int n, int M, int nbnd,
+                                                      const double* __restrict__ c, int Rf, int n, int M,
                                                       double* __restrict__ X, double* __restrict__ w,
                                                       int* status) {
   const int i = blockIdx.x, lane = threadIdx.x;
@@ -109,15 +110,14 @@ __global__ void __launch_bounds__(32) fdw_node_kernel(const double* __restrict__
     for (int r = 0; r < Rf; ++r) g[0] = fma(pq[(size_t)r * n + i], c[r * M + lane], g[0]);
   fdw_warp_solve<1>(row, invd, g, lane, M, 1);
   if (act) w[(size_t)i * M + lane] = g[0];
-  // X_ib = T_i^-1 C_b
-  for (int b = 0; b < nbnd; ++b) {
-    const double* Cb = b == 0 ? C0 : C1;
+  // T_i^-1 (row `lane`, all columns)
+  {
     double rhs[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) rhs[k] = (act && k < M) ? Cb[lane * M + k] : 0.0;
+    for (int k = 0; k < 32; ++k) rhs[k] = (act && k == lane) ? 1.0 : 0.0;
     fdw_warp_solve<32>(row, invd, rhs, lane, M, M);
     if (act) {
-      double* out = X + (((size_t)i * nbnd + b) * M + lane) * M;
+      double* out = X + ((size_t)i * M + lane) * M;
 #pragma unroll
       for (int k = 0; k < 32; ++k)
         if (k < M) out[k] = rhs[k];
@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(32) fdw_node_kernel(const double* __restrict__
   }
 }
 
-// SC[b'][b][r][c] = sum_i phi_b'[i] phi_b[i] X_ib[r][c];  rr[b'][r] = sum_i phi_b'[i] w_i[r].
-// phi_b[i] = Phi[corner_b][i] (row corner_b of Phi: Phi^T e_b).
+// Z[b'][b][r][c] = sum_i phi_b'[i] phi_b[i] T_i^-1[r][c];  rr[b'][r] = sum_i phi_b'[i] w_i[r].
+// phi_b[i] = Phi[corner_b][i] (row corner_b of Phi: Phi^T e_b).  X holds T_i^-1.
 __global__ void fdw_reduce_kernel(const double* __restrict__ X, const double* __restrict__ w,
                                   const double* __restrict__ Phi, int c0, int c1, int n, int M, int nbnd,
-                                  double* __restrict__ SC, double* __restrict__ rr) {
+                                  double* __restrict__ Z, double* __restrict__ rr) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int nsc = nbnd * nbnd * M * M;
   if (idx < nsc) {
@@ -137,8 +137,8 @@ __global__ void fdw_reduce_kernel(const double* __restrict__ X, const double* __
     const double* pb = Phi + (size_t)(b == 0 ? c0 : c1) * n;
     const double* pbp = Phi + (size_t)(bp == 0 ? c0 : c1) * n;
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s = fma(pbp[i] * pb[i], X[(((size_t)i * nbnd + b) * M + r) * M + cc], s);
-    SC[idx] = s;
+    for (int i = 0; i < n; ++i) s = fma(pbp[i] * pb[i], X[((size_t)i * M + r) * M + cc], s);
+    Z[idx] = s;
   } else if (idx < nsc + nbnd * M) {
     const int k = idx - nsc, r = k % M, bp = k / M;
     const double* pbp = Phi + (size_t)(bp == 0 ? c0 : c1) * n;
@@ -148,14 +148,29 @@ __global__ void fdw_reduce_kernel(const double* __restrict__ X, const double* __
   }
 }
 
+// SC[b'][b] = Z[b'][b] C_b (M x M products).
+__global__ void fdw_zc_kernel(const double* __restrict__ Z, const double* __restrict__ C0,
+                              const double* __restrict__ C1, int M, int nbnd, double* __restrict__ SC) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nbnd * nbnd * M * M) return;
+  const int cc = idx % M, r = (idx / M) % M, b = (idx / (M * M)) % nbnd;
+  const double* Cb = b == 0 ? C0 : C1;
+  const double* zr = Z + (size_t)(idx - cc);   // row r of Z[b'][b]
+  double s = 0.0;
+  for (int k = 0; k < M; ++k) s = fma(zr[k], Cb[(size_t)k * M + cc], s);
+  (void)r;
+  SC[idx] = s;
+}
+
 // (I + [beta_b SC[b'][b]]) z = rr, N2 = nbnd M <= 64 unknowns, partial pivoting; beta_b
-// is the corner entry of face b's point-mass band.  beta is written out for the final
-// kernel.
+// is the corner entry of face b's point-mass band.  Writes u_b = C_b z_b and beta for the
+// final kernel.
 #define FDW_MAXN 64
 __global__ void __launch_bounds__(64) fdw_cap_kernel(const double* __restrict__ SC, const double* __restrict__ rr,
                                                      const double* __restrict__ band0,
                                                      const double* __restrict__ band1, int corner0, int corner1,
-                                                     int hb, int M, int nbnd, double* __restrict__ z,
+                                                     int hb, int M, int nbnd, const double* __restrict__ C0,
+                                                     const double* __restrict__ C1, double* __restrict__ z,
                                                      double* __restrict__ beta, int* status) {
   __shared__ double A[FDW_MAXN][FDW_MAXN + 1];
   __shared__ double bet[2];
@@ -213,26 +228,33 @@ __global__ void __launch_bounds__(64) fdw_cap_kernel(const double* __restrict__ 
     }
   }
   __syncthreads();
-  for (int rI = tid; rI < N2; rI += blockDim.x) z[rI] = A[rI][N2];
+  // u_b = C_b z_b, stored in z's place (the final kernel needs only u)
+  for (int rI = tid; rI < N2; rI += blockDim.x) {
+    const int b = rI / M, r = rI % M;
+    const double* Cb = b == 0 ? C0 : C1;
+    double u = 0.0;
+    for (int k = 0; k < M; ++k) u = fma(Cb[(size_t)r * M + k], A[b * M + k][N2], u);
+    z[rI] = u;
+  }
 }
 
-// Y[i][r] = w_i[r] - sum_b beta_b phi_b[i] (X_ib z_b)[r]   (row-major n x M)
+// Y[i][r] = w_i[r] - (T_i^-1 v_i)[r],  v_i = sum_b beta_b phi_b[i] u_b   (row-major n x M)
 __global__ void fdw_final_kernel(const double* __restrict__ X, const double* __restrict__ w,
-                                 const double* __restrict__ z, const double* __restrict__ beta,
+                                 const double* __restrict__ u, const double* __restrict__ beta,
                                  const double* __restrict__ Phi, int c0, int c1, int n, int M, int nbnd,
                                  double* __restrict__ Y) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * M) return;
   const int r = (int)(idx % M), i = (int)(idx / M);
-  double y = w[idx];
-  for (int b = 0; b < nbnd; ++b) {
-    const double f = beta[b] * Phi[(size_t)(b == 0 ? c0 : c1) * n + i];
-    const double* x = X + (((size_t)i * nbnd + b) * M + r) * M;
-    double s = 0.0;
-    for (int k = 0; k < M; ++k) s = fma(x[k], z[b * M + k], s);
-    y -= f * s;
+  const double f0 = beta[0] * Phi[(size_t)c0 * n + i];
+  const double f1 = nbnd > 1 ? beta[1] * Phi[(size_t)c1 * n + i] : 0.0;
+  const double* x = X + ((size_t)i * M + r) * M;
+  double s = 0.0;
+  for (int k = 0; k < M; ++k) {
+    const double v = nbnd > 1 ? fma(f1, u[M + k], f0 * u[k]) : f0 * u[k];
+    s = fma(x[k], v, s);
   }
-  Y[idx] = y;
+  Y[idx] = w[idx] - s;
 }
 
 // ---------------------------------------------------------------------------------
@@ -271,8 +293,9 @@ int taps_fdw_eligible(const taps_problem* P, int d, int M, int* slotA, int* slot
   return 1;
 }
 
+// T_i^-1 [nf_max][M][M], w [nf_max][M], Z and SC [4][M][M] each, rr, z / u, beta.
 size_t taps_fdw_scratch_doubles(int nf_max, int M) {
-  return (size_t)nf_max * (2 * (size_t)M * M + M) + 4 * (size_t)M * M + 4 * (size_t)M + 2 * (size_t)M + 8;
+  return (size_t)nf_max * ((size_t)M * M + M) + 8 * (size_t)M * M + 4 * (size_t)M + 8;
 }
 
 // Reduced solve of dim d (coefficients in P->d_C / P->d_c) through the pencil of its
@@ -288,9 +311,10 @@ int taps_fdw_solve(taps_problem* P, taps_factors* U, int d) {
   const int n = dm->nf, hb = dm->hb;
   const size_t MM = (size_t)M * M;
   cudaStream_t s = P->stream;
-  double* X = P->d_fdw;
-  double* w = X + (size_t)P->nf_max * 2 * MM;
-  double* SC = w + (size_t)P->nf_max * M;
+  double* X = P->d_fdw;                        // T_i^-1
+  double* w = X + (size_t)P->nf_max * MM;
+  double* Z = w + (size_t)P->nf_max * M;
+  double* SC = Z + 4 * MM;
   double* rr = SC + 4 * MM;
   double* z = rr + 2 * (size_t)M;
   double* beta = z + 2 * (size_t)M;
@@ -298,24 +322,27 @@ int taps_fdw_solve(taps_problem* P, taps_factors* U, int d) {
   const int k0 = P->ops[d][s0], k1 = s1 >= 0 ? P->ops[d][s1] : k0;
   const int corner0 = k0 == TAPS_OP_BLO ? 0 : n - 1, corner1 = k1 == TAPS_OP_BLO ? 0 : n - 1;
   const size_t bsz = (size_t)n * dm->nb;
+  const double* C0 = P->d_C + (size_t)s0 * MM;
+  const double* C1 = s1 >= 0 ? P->d_C + (size_t)s1 * MM : C0;
   int tk = prof_begin(P, TAPS_PROF_FASTDIAG);
-  fdw_node_kernel<<<n, 32, 0, s>>>(P->d_C + (size_t)sa * MM, P->d_C + (size_t)sb * MM, P->d_C + (size_t)s0 * MM,
-                                   s1 >= 0 ? P->d_C + (size_t)s1 * MM : nullptr, E->mu, P->d_pq[d], P->d_c,
-                                   P->Rf, n, M, nbnd, X, w, P->d_status);
+  fdw_node_kernel<<<n, 32, 0, s>>>(P->d_C + (size_t)sa * MM, P->d_C + (size_t)sb * MM, E->mu, P->d_pq[d], P->d_c,
+                                   P->Rf, n, M, X, w, P->d_status);
   const int nred = nbnd * nbnd * M * M + nbnd * M;
-  fdw_reduce_kernel<<<(nred + 127) / 128, 128, 0, s>>>(X, w, E->Phi, corner0, corner1, n, M, nbnd, SC, rr);
+  fdw_reduce_kernel<<<(nred + 127) / 128, 128, 0, s>>>(X, w, E->Phi, corner0, corner1, n, M, nbnd, Z, rr);
+  const int nzc = nbnd * nbnd * M * M;
+  fdw_zc_kernel<<<(nzc + 127) / 128, 128, 0, s>>>(Z, C0, C1, M, nbnd, SC);
   fdw_cap_kernel<<<1, 64, 0, s>>>(SC, rr, dm->d_band + (size_t)k0 * bsz, dm->d_band + (size_t)k1 * bsz, corner0,
-                                  corner1, hb, M, nbnd, z, beta, P->d_status);
+                                  corner1, hb, M, nbnd, C0, C1, z, beta, P->d_status);
   const long long nM = (long long)n * M;
   fdw_final_kernel<<<(unsigned)((nM + 255) / 256), 256, 0, s>>>(X, w, z, beta, E->Phi, corner0, corner1, n, M,
                                                                  nbnd, Y);
-  P->prof->launches[TAPS_PROF_FASTDIAG] += 3;
+  P->prof->launches[TAPS_PROF_FASTDIAG] += 4;
   const double Md = M;
   prof_end(P, TAPS_PROF_FASTDIAG, tk,
-           n * ((2.0 / 3.0) * Md * Md * Md + (1.0 + nbnd * Md) * 2.0 * Md * Md + 2.0 * P->Rf * Md) +
-               2.0 * n * (nbnd * nbnd * (double)MM + nbnd * Md) + (2.0 / 3.0) * pow(nbnd * Md, 3) +
-               2.0 * (double)nM * nbnd * Md,
-           8.0 * ((double)n * nbnd * MM * 2.0 + 4.0 * nM));
+           n * ((2.0 / 3.0) * Md * Md * Md + (1.0 + Md) * 2.0 * Md * Md + 2.0 * P->Rf * Md) +
+               2.0 * n * (nbnd * nbnd * (double)MM + nbnd * Md) + 2.0 * nbnd * nbnd * (double)MM * Md +
+               (2.0 / 3.0) * pow(nbnd * Md, 3) + 2.0 * (double)nM * (Md + nbnd),
+           8.0 * ((double)n * MM * 2.0 + 4.0 * nM));
   TAPS_CUDA(cudaGetLastError());
   // back to the nodal basis; the previous factor goes to d_Uold
   return taps_fd_to_nodal(P, E, Y, n, M, U->d_U[d], P->d_Uold);

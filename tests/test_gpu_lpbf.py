@@ -50,7 +50,7 @@ def test_lpbf_slab_sweeps_match_oracle(T):
     prof = P.profile()
     assert prof["block_lu"]["launches"] == 0
     assert prof["modediag"]["launches"] == 2 * 4
-    assert prof["fastdiag"]["launches"] == 2 * (3 * 1 + 3 * 4)   # parameter dims; space dims
+    assert prof["fastdiag"]["launches"] == 2 * (3 * 1 + 3 * 5)   # parameter dims; space dims
     # the Eq. 42 residual of the GPU's factors, recomputed by the oracle
     r_gpu = P.residual(U, T.RES_ALS)
     r_o = O.als_residual(Po, got)
