@@ -288,7 +288,8 @@ class Problem:
 
 def build_problem(dims, terms, sources):
     """dims: list of Dim; terms: list of (alpha, [op per dim]); sources: list of
-    (beta, [(kind, par) or ('nodal', values) per dim])."""
+    (beta, [(kind, par) or ('nodal', values) per dim]); kinds 'opvec' (free-node vector)
+    and 'opvecfull' (all-node vector) give par = (operator name, vector)."""
     tabs = [shape_tables(dm) for dm in dims]
     ops = [assemble_free(dm, tb) for dm, tb in zip(dims, tabs)]
     src = []
@@ -300,6 +301,11 @@ def build_problem(dims, terms, sources):
             elif kind == "opvec":
                 # the projection of a field already in the C-HiDeNN space: q = Op v
                 qs.append(ops[d][OP_BY_NAME[par[0]]] @ np.asarray(par[1], dtype=float))
+            elif kind == "opvecfull":
+                # a field given at all nodes, constrained ones included (the lifting of
+                # non-homogeneous Dirichlet data): q = (Op_all v)[free nodes]
+                full = assemble_full(dm, tb)[OP_BY_NAME[par[0]]] @ np.asarray(par[1], dtype=float)
+                qs.append(full[dm.free])
             else:
                 qs.append(project_source(dm, kind, par, tab=tb))
         src.append((float(beta), qs))
@@ -866,3 +872,19 @@ def slab_compress(desc, state, time_dim, U0, sweeps):
     for j, d in enumerate(keep):
         out[d] = U[j]
     return out, np.ones(U[0].shape[1])
+
+
+def dirichlet_lifting_sources(desc, lift):
+    """Non-homogeneous Dirichlet data by lifting (Sec. 2.5 weak form with u = u_D + w,
+    w = 0 on the constrained nodes): for a lifting u_D = sum_m w_m (x)_d v_{d,m} given at
+    all nodes (only its values at constrained nodes matter for the final field), the
+    problem for w gains, per operator term t and lifting mode m, the separable source
+    -alpha_t w_m (x)_d (Op_{t,d} v_{d,m})[free nodes]."""
+    vecs, wts = lift
+    out = []
+    for alpha, ops in desc["terms"]:
+        for m in range(len(wts)):
+            out.append((-float(alpha) * float(wts[m]),
+                        [("opvecfull", (ops[d], np.asarray(vecs[d][:, m], dtype=float)))
+                         for d in range(len(ops))]))
+    return out
