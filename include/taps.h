@@ -75,6 +75,9 @@ extern "C" {
 #define TAPS_SRC_OPVEC 5  /* q = Op v over the free nodes: par[0] = operator kind, nodal = v
                              (n_free values); the projection of a field already in the
                              C-HiDeNN space, e.g. the end state of a previous time slab */
+#define TAPS_SRC_OPVEC_FULL 6 /* q = (Op v)[free nodes] with v given at ALL nodes (constrained
+                                 ones included): the lifting of non-homogeneous Dirichlet
+                                 data; par[0] = operator kind, nodal = v (n values) */
 
 /* ---- precisions of the Gram / SpMM contractions (reduced solves stay FP64) --- */
 #define TAPS_FP64 0
@@ -147,7 +150,8 @@ typedef struct {
   int kind[TAPS_MAX_DIMS];
   double par[TAPS_MAX_DIMS][4];
   const double* nodal[TAPS_MAX_DIMS]; /* TAPS_SRC_NODAL: host array of n values;
-                                         TAPS_SRC_OPVEC: host array of n_free values */
+                                         TAPS_SRC_OPVEC: host array of n_free values;
+                                         TAPS_SRC_OPVEC_FULL: host array of n values */
 } taps_source;
 
 typedef struct {

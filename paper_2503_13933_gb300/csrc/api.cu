@@ -582,9 +582,11 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   for (int r = 0; r < Rf; ++r)
     for (int d = 0; d < D; ++d) {
       int k = sources[r].kind[d];
-      if (k < TAPS_SRC_CONST || k > TAPS_SRC_OPVEC) return TAPS_ERR_INVALID_ARG;
-      if ((k == TAPS_SRC_NODAL || k == TAPS_SRC_OPVEC) && !sources[r].nodal[d]) return TAPS_ERR_INVALID_ARG;
-      if (k == TAPS_SRC_OPVEC && (sources[r].par[d][0] < 0 || sources[r].par[d][0] >= TAPS_NUM_OPS))
+      if (k < TAPS_SRC_CONST || k > TAPS_SRC_OPVEC_FULL) return TAPS_ERR_INVALID_ARG;
+      if ((k == TAPS_SRC_NODAL || k == TAPS_SRC_OPVEC || k == TAPS_SRC_OPVEC_FULL) && !sources[r].nodal[d])
+        return TAPS_ERR_INVALID_ARG;
+      if ((k == TAPS_SRC_OPVEC || k == TAPS_SRC_OPVEC_FULL) &&
+          (sources[r].par[d][0] < 0 || sources[r].par[d][0] >= TAPS_NUM_OPS))
         return TAPS_ERR_INVALID_ARG;
     }
   taps_problem* P = new taps_problem();

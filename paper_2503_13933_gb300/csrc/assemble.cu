@@ -318,7 +318,13 @@ __device__ __forceinline__ void source_entry(const DimParams& P, const double* N
   int i = fi + P.off;
   double par[4] = {p0, p1, p2, p3};
   double v = 0.0;
-  if (kind == TAPS_SRC_OPVEC) {   // q = Op v on the free nodes
+  if (kind == TAPS_SRC_OPVEC_FULL) {   // q = (Op v)[free] for v at all nodes
+    const double* row = band_full + ((size_t)(int)p0 * P.n + i) * P.nb;
+    for (int k = 0; k < P.nb; ++k) {
+      int j = i + k - P.hb;
+      if (j >= 0 && j < P.n) v += row[k] * nodal[j];
+    }
+  } else if (kind == TAPS_SRC_OPVEC) {   // q = Op v on the free nodes
     const double* row = band_free + ((size_t)(int)p0 * P.nf + fi) * P.nb;
     for (int k = 0; k < P.nb; ++k) {
       int fj = fi + k - P.hb;
@@ -503,12 +509,12 @@ extern "C" int taps_dim_copy_shape(const taps_dim* d, double* N_out, double* B_o
 // Source projection of one factor onto the free nodes of an assembled dimension.
 int taps_project_source(const taps_dim* d, int kind, const double* par, const double* nodal_host,
                         double* d_q_free, cudaStream_t s) {
-  if (kind < TAPS_SRC_CONST || kind > TAPS_SRC_OPVEC) return TAPS_ERR_INVALID_ARG;
+  if (kind < TAPS_SRC_CONST || kind > TAPS_SRC_OPVEC_FULL) return TAPS_ERR_INVALID_ARG;
   DimParams P = make_params(d);
   double* d_nodal = nullptr;
-  if (kind == TAPS_SRC_NODAL || kind == TAPS_SRC_OPVEC) {
+  if (kind == TAPS_SRC_NODAL || kind == TAPS_SRC_OPVEC || kind == TAPS_SRC_OPVEC_FULL) {
     if (!nodal_host) return TAPS_ERR_INVALID_ARG;
-    size_t len = kind == TAPS_SRC_NODAL ? d->n : d->nf;
+    size_t len = kind == TAPS_SRC_OPVEC ? d->nf : d->n;
     TAPS_TRY(taps_alloc((void**)&d_nodal, sizeof(double) * len));
     TAPS_CUDA(cudaMemcpyAsync(d_nodal, nodal_host, sizeof(double) * len, cudaMemcpyHostToDevice, s));
   }
@@ -534,12 +540,12 @@ int taps_project_sources_dim(const taps_dim* d, const taps_source* sources, int 
   size_t tot = 0;
   for (int r = 0; r < Rf; ++r) {
     const int k = sources[r].kind[dimIndex];
-    if (k < TAPS_SRC_CONST || k > TAPS_SRC_OPVEC) return TAPS_ERR_INVALID_ARG;
+    if (k < TAPS_SRC_CONST || k > TAPS_SRC_OPVEC_FULL) return TAPS_ERR_INVALID_ARG;
     kinds[r] = k;
-    if (k == TAPS_SRC_NODAL || k == TAPS_SRC_OPVEC) {
+    if (k == TAPS_SRC_NODAL || k == TAPS_SRC_OPVEC || k == TAPS_SRC_OPVEC_FULL) {
       if (!sources[r].nodal[dimIndex]) return TAPS_ERR_INVALID_ARG;
       offs[r] = (long long)tot;
-      tot += k == TAPS_SRC_NODAL ? d->n : d->nf;
+      tot += k == TAPS_SRC_OPVEC ? d->nf : d->n;
     }
   }
   // packed: pars [Rf][4] | nodal data | offsets | kinds
@@ -551,7 +557,7 @@ int taps_project_sources_dim(const taps_dim* d, const taps_source* sources, int 
     for (int j = 0; j < 4; ++j) hp[4 * (size_t)r + j] = sources[r].par[dimIndex][j];
   for (int r = 0; r < Rf; ++r)
     if (offs[r] >= 0) {
-      const size_t len = kinds[r] == TAPS_SRC_NODAL ? d->n : d->nf;
+      const size_t len = kinds[r] == TAPS_SRC_OPVEC ? d->nf : d->n;
       memcpy(hp + npar + offs[r], sources[r].nodal[dimIndex], sizeof(double) * len);
     }
   memcpy(host.data() + sizeof(double) * (npar + tot), offs.data(), sizeof(long long) * Rf);

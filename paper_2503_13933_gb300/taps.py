@@ -24,7 +24,7 @@ NOALLOC_SCRATCH_BYTES = 4 << 20
 SPACE, PARAM, TIME = 0, 1, 2
 OP = {"K": 0, "M": 1, "G": 2, "W": 3, "Blo": 4, "Bhi": 5}
 NUM_OPS = 6
-SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4, "opvec": 5}
+SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4, "opvec": 5, "opvecfull": 6}
 FP64, FP32, MIXED, BF16 = 0, 1, 2, 3
 RES_ALS, RES_FULL = 0, 1
 INIT_GIVEN, INIT_RANDOM, INIT_ZERO = 0, 1, 2
@@ -253,7 +253,7 @@ class Problem:
                     arr = np.ascontiguousarray(par, dtype=np.float64)
                     self._keep.append(arr)
                     srcs[r].nodal[d] = arr.ctypes.data_as(_pd)
-                elif kind == "opvec":        # (operator name, free-node vector)
+                elif kind in ("opvec", "opvecfull"):   # (operator name, free- / all-node vector)
                     arr = np.ascontiguousarray(par[1], dtype=np.float64)
                     self._keep.append(arr)
                     srcs[r].nodal[d] = arr.ctypes.data_as(_pd)

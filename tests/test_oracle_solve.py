@@ -309,3 +309,23 @@ def test_dirichlet_lifting_equals_direct_boundary_solve():
     ub = uD.reshape(-1)
     uI = np.linalg.solve(A[np.ix_(inner, inner)], F[inner] - A[np.ix_(inner, ~inner)] @ ub[~inner])
     assert np.max(np.abs(u_taps.reshape(-1) - uI)) < 1e-9 * np.max(np.abs(uI))
+
+
+def test_product_lifting_helper_matches_oracle_reading():
+    """The library's lifting helper builds the same source terms (coefficients, operator
+    names, all-node vectors) as the oracle's reading of the lifted weak form."""
+    from paper_2503_13933_gb300 import boundary as B
+    rng = np.random.default_rng(5)
+    desc = W.heat_transient(n_space=9, n_t=7, D_space=2, h_conv=1.0)
+    vecs = [rng.uniform(-1, 1, (dm["n"], 2)) for dm in desc["dims"]]
+    wts = np.array([0.4, -2.0])
+    a = B.lifting_sources(desc, vecs, wts)
+    b = O.dirichlet_lifting_sources(desc, (vecs, wts))
+    assert len(a) == len(b) == 2 * len(desc["terms"])
+    for (ba, fa), (bb, fb) in zip(a, b):
+        assert ba == bb
+        for (ka, (oa, va)), (kb, (ob, vb)) in zip(fa, fb):
+            assert ka == kb == "opvecfull" and oa == ob
+            assert np.array_equal(va, vb)
+    with pytest.raises(ValueError):
+        B.lifting_sources(desc, [v[1:-1] for v in vecs], wts)   # free nodes only: rejected
