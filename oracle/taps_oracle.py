@@ -888,3 +888,62 @@ def dirichlet_lifting_sources(desc, lift):
                         [("opvecfull", (ops[d], np.asarray(vecs[d][:, m], dtype=float)))
                          for d in range(len(ops))]))
     return out
+
+
+# ---------------------------------------------------------------------------------
+# Accuracy against an exact solution (the relative L2 error of Sec. 3)
+# ---------------------------------------------------------------------------------
+def _quadrature_values(dim: Dim, V, tab=None):
+    """Gauss points, weights and the C-HiDeNN interpolants of the columns of V (all
+    nodes) at those points, over the whole dim (every element's rule)."""
+    if tab is None:
+        tab = shape_tables(dim)
+    xs, ws, F = [], [], []
+    for pts in tab:
+        for xe, wj, ids, N, B in pts:
+            xs.append(xe)
+            ws.append(wj)
+            F.append(np.asarray(N) @ V[np.array(ids)])
+    return np.array(xs), np.array(ws), np.array(F)
+
+
+def relative_l2_error(dims, V, c, sep, pair=None, pair_fn=None):
+    """Relative L2 error (Sec. 3) of u = sum_m c_m prod_d (sum_i N~_i(x_d) V[d][i, m])
+    against u_ex = prod_{d not in pair} sep[d](x_d) * pair_fn(x_a, x_b), (a, b) = pair,
+    over the tensor domain, each 1D integral by the dims' own Gauss rules.  Through
+    |u - u_ex|^2 = |u|^2 - 2 (u, u_ex) + |u_ex|^2, the first a Hadamard product of
+    per-dim Gram matrices, so the computed error has an absolute floor near
+    sqrt(eps) * |u_ex| (the rounding limit of the paper's S-P-T study).
+    sep[d] is a source factor (kind, params) of source_factor_values."""
+    D = len(dims)
+    c = np.asarray(c, dtype=float)
+    q = [_quadrature_values(dims[d], np.asarray(V[d], dtype=float)) for d in range(D)]
+    pd = set(pair) if pair is not None else set()
+    G = np.ones((len(c), len(c)))
+    cross = np.ones(len(c))
+    ex2 = 1.0
+    for d in range(D):
+        xs, ws, F = q[d]
+        G *= F.T @ (ws[:, None] * F)
+        if d in pd:
+            continue
+        g = source_factor_values(sep[d][0], sep[d][1], xs)
+        cross *= F.T @ (ws * g)
+        ex2 *= float(np.sum(ws * g * g))
+    if pair is not None:
+        (xa, wa, Fa), (xb, wb, Fb) = q[pair[0]], q[pair[1]]
+        E = pair_fn(xa[:, None], xb[None, :]) * np.outer(wa, wb)
+        cross *= np.einsum("am,ab,bm->m", Fa, E, Fb)
+        ex2 *= float(np.sum(pair_fn(xa[:, None], xb[None, :]) ** 2 * np.outer(wa, wb)))
+    err2 = float(c @ G @ c - 2.0 * c @ cross + ex2)
+    return math.sqrt(max(err2, 0.0) / ex2)
+
+
+def lifted_field_factors(dims, U, lift):
+    """The CP factors (all nodes) and weights of u = u_D + w: the solved w (free-node
+    factors, zero at the constrained nodes) and the lifting's modes."""
+    vecs, wts = lift
+    M = U[0].shape[1]
+    V = [np.concatenate([to_all_nodes(dims[d], U[d]), np.asarray(vecs[d], dtype=float)], axis=1)
+         for d in range(len(dims))]
+    return V, np.concatenate([np.ones(M), np.asarray(wts, dtype=float)])

@@ -223,3 +223,102 @@ def random_factors(desc, M, seed):
 
 def n_free(dm):
     return dm["n"] - int(dm["dirichlet_lo"]) - int(dm["dirichlet_hi"])
+
+
+SPT_RANGES = dict(x=(-0.5, 0.5), y=(-0.5, 0.5), z=(-0.5, 0.5), k=(1.0, 2.0), P=(1.0, 2.0),
+                  rho=(1.0, 2.0), cp=(1.0, 2.0), t=(0.0, 0.2))
+
+
+def _svd_modes(E, tol):
+    Uu, sv, Vt = np.linalg.svd(E, full_matrices=False)
+    rank = max(1, int(np.sum(sv > tol * sv[0])))
+    return [(float(sv[q]), Uu[:, q].copy(), Vt[q].copy()) for q in range(rank)]
+
+
+def spt_manufactured(n=16, s=2, a=20.0, p=2, n_quad=6, svd_tol=1e-12, ranges=None):
+    """The eight-dimensional space-parameter-time heat problem of Sec. 3.2 (Eq. 1 with the
+    source of that section): rho c_p du/dt - k Laplace u = f in x, y, z, the parameters
+    k, P, rho, c_p, and t, n nodes per dim, with the non-separable exact solution
+        u_ex = rho c_p P (1 - exp(-15 k t)) exp(-25 x^2 - 25 y^2),
+    zero initial condition and u = u_ex on every spatial face.
+
+    Domain (not stated in the paper; this reading): x, y, z in [-0.5, 0.5], k, P, rho,
+    c_p in [1, 2], t in [0, 0.2].  Dims in the order x, y, z, k, P, rho, c_p, t.
+
+    Input construction: exp(-25 x^2) enters as the Gaussian source kind (sigma^2 = 1/50);
+    (1 - 50 x^2) exp(-25 x^2) and the (k, t)-coupled factors k exp(-15 k t) and
+    k (1 - exp(-15 k t)) enter through their C-HiDeNN nodal interpolants, the coupled
+    ones as the SVD of their nodal matrices truncated at svd_tol relative to the largest
+    singular value.  The boundary data is a lifting (all-node factors) equal to u_ex's
+    nodal values on the spatial boundary nodes and zero at interior nodes:
+        u_D = u_ex * (1 - prod_{d in x,y,z} (1 - chi_d)),  chi_d = end-node indicator,
+    expanded into its 7 separable sign terms times the SVD of 1 - exp(-15 k t).
+
+    Returns (desc, lift, exact): lift = (vecs, weights) over all nodes; exact =
+    (separable factors per dim as (kind, params) or None for the coupled pair,
+    the coupled pair's dims, its function name)."""
+    R = dict(SPT_RANGES, **(ranges or {}))
+    names = ["x", "y", "z", "k", "P", "rho", "cp", "t"]
+    kinds = [SPACE] * 3 + [PARAM] * 4 + [TIME]
+    dims = []
+    for nm, kd in zip(names, kinds):
+        lo, hi = R[nm]
+        if kd == SPACE:
+            dims.append(dim(n, lo, hi, s=s, a=a, p=p, n_quad=n_quad))
+        elif kd == PARAM:
+            dims.append(dim(n, lo, hi, kind=PARAM, s=s, a=a, p=p, n_quad=n_quad, dirichlet_lo=False,
+                            dirichlet_hi=False, weight_poly=(0.0, 1.0)))
+        else:
+            dims.append(dim(n, lo, hi, kind=TIME, s=s, a=a, p=p, n_quad=n_quad, dirichlet_lo=True,
+                            dirichlet_hi=False))
+    X = {nm: np.linspace(*R[nm], n) for nm in names}
+    # rho c_p du/dt: W (weight = the coordinate) on rho and c_p, G in time
+    terms = [(1.0, ["M"] * 5 + ["W", "W", "G"])]
+    # -k Laplace u: K in one spatial dim, W on k
+    for e in range(3):
+        terms.append((1.0, ["K" if d == e else "M" for d in range(3)] + ["W", "M", "M", "M", "M"]))
+    sig = math.sqrt(1.0 / 50.0)
+    g = ("gauss", (0.0, sig))
+    hx = (1.0 - 50.0 * X["x"] ** 2) * np.exp(-25.0 * X["x"] ** 2)
+    hy = (1.0 - 50.0 * X["y"] ** 2) * np.exp(-25.0 * X["y"] ** 2)
+    kk, tt = np.meshgrid(X["k"], X["t"], indexing="ij")
+    one = ("const", (1.0,))
+    lin = ("poly", (0.0, 1.0))
+    sq = ("poly", (0.0, 0.0, 1.0))
+    sources = []
+    # 15 rho^2 c_p^2 k P exp(-15 k t) G(x) G(y)
+    for sv, uk, vt in _svd_modes(kk * np.exp(-15.0 * kk * tt), svd_tol):
+        sources.append((15.0 * sv, [g, g, one, ("nodal", uk), lin, sq, sq, ("nodal", vt)]))
+    # 50 rho c_p k P (1 - exp(-15 k t)) G(x) G(y) [(1 - 50 x^2) + (1 - 50 y^2)]
+    for sv, uk, vt in _svd_modes(kk * (1.0 - np.exp(-15.0 * kk * tt)), svd_tol):
+        sources.append((50.0 * sv, [("nodal", hx), g, one, ("nodal", uk), lin, lin, lin, ("nodal", vt)]))
+        sources.append((50.0 * sv, [g, ("nodal", hy), one, ("nodal", uk), lin, lin, lin, ("nodal", vt)]))
+    # lifting of the boundary data
+    gx, gy, onez = np.exp(-25.0 * X["x"] ** 2), np.exp(-25.0 * X["y"] ** 2), np.ones(n)
+    chi = np.zeros(n)
+    chi[[0, -1]] = 1.0
+    modes_E = _svd_modes(1.0 - np.exp(-15.0 * kk * tt), svd_tol)
+    cols = [[] for _ in range(8)]
+    wts = []
+    for mask in range(1, 8):
+        sign = -1.0 if bin(mask).count("1") % 2 == 0 else 1.0
+        base = [gx, gy, onez]
+        sp = [base[d] * chi if mask >> d & 1 else base[d] for d in range(3)]
+        for sv, uk, vt in modes_E:
+            for d in range(3):
+                cols[d].append(sp[d])
+            cols[3].append(uk)
+            cols[4].append(X["P"])
+            cols[5].append(X["rho"])
+            cols[6].append(X["cp"])
+            cols[7].append(vt)
+            wts.append(sign * sv)
+    vecs = [np.stack(c, axis=1) for c in cols]
+    exact = dict(sep=[g, g, one, None, lin, lin, lin, None], pair=(3, 7), pair_fn="1-exp(-15kt)")
+    desc = dict(name=f"spt_manufactured_n{n}_s{s}p{p}", dims=dims, terms=terms, sources=sources)
+    return desc, (vecs, np.array(wts)), exact
+
+
+def spt_exact_pair(k, t):
+    """The (k, t)-coupled factor of the Sec. 3.2 exact solution."""
+    return 1.0 - np.exp(-15.0 * k * t)
