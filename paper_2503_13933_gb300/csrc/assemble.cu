@@ -242,18 +242,24 @@ __global__ void shape_kernel(DimParams P, const double* ginv, double* Nt, double
   xq[(size_t)e * P.nq + g] = x;
 }
 
-// One thread per (op in K, M, G, W; node i; band offset k): element-by-element
-// Gauss sums of Eqs. 33-35 over the elements shared by nodes i and j = i + k - hb.
+// One thread per (op; node i; band offset k): for K, M, G, W element-by-element Gauss
+// sums of Eqs. 33-35 over the elements shared by nodes i and j = i + k - hb; for Blo,
+// Bhi the point mass at the end node (a face integral through the Kronecker delta).
 __global__ void band_kernel(DimParams P, const double* Nt, const double* Bt, const double* xq,
                             double* band_full) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long total = 4ll * P.n * P.nb;
+  long long total = (long long)TAPS_NUM_OPS * P.n * P.nb;
   if (idx >= total) return;
   int k = idx % P.nb;
   int i = (idx / P.nb) % P.n;
   int op = idx / ((long long)P.nb * P.n);
   int j = i + k - P.hb;
   double v = 0.0;
+  if (op == TAPS_OP_BLO || op == TAPS_OP_BHI) {
+    const int end = op == TAPS_OP_BLO ? 0 : P.n - 1;
+    band_full[idx] = (i == end && j == end) ? 1.0 : 0.0;
+    return;
+  }
   if (j >= 0 && j < P.n) {
     int e_lo = max(max(i, j) - P.s - 1, 0);
     int e_hi = min(min(i, j) + P.s, P.n - 2);
@@ -279,7 +285,7 @@ __global__ void band_kernel(DimParams P, const double* Nt, const double* Bt, con
   band_full[((size_t)op * P.n + i) * P.nb + k] = v;
 }
 
-// Boundary point masses (Blo, Bhi) and restriction of every band to the free nodes.
+// Restriction of every band to the free nodes.
 __global__ void restrict_kernel(DimParams P, const double* band_full, double* band) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)TAPS_NUM_OPS * P.nf * P.nb;
@@ -288,10 +294,7 @@ __global__ void restrict_kernel(DimParams P, const double* band_full, double* ba
   int fi = (idx / P.nb) % P.nf;
   int op = idx / ((long long)P.nb * P.nf);
   int i = fi + P.off, j = i + k - P.hb;
-  double v;
-  if (op == TAPS_OP_BLO) v = (i == 0 && j == 0) ? 1.0 : 0.0;
-  else if (op == TAPS_OP_BHI) v = (i == P.n - 1 && j == P.n - 1) ? 1.0 : 0.0;
-  else v = band_full[((size_t)op * P.n + i) * P.nb + k];
+  double v = band_full[((size_t)op * P.n + i) * P.nb + k];
   bool jfree = (j >= P.off) && (j < P.off + P.nf);
   band[idx] = jfree ? v : 0.0;
 }
@@ -429,7 +432,7 @@ static int assemble_impl(taps_dim* d) {
   TAPS_CUDA(cudaGetLastError());
   shape_kernel<<<n - 1, 32, 0, s>>>(P, d->d_ginv, d->d_N, d->d_B, d->d_xq);
   TAPS_CUDA(cudaGetLastError());
-  long long tot = 4ll * n * d->nb;
+  long long tot = (long long)TAPS_NUM_OPS * n * d->nb;
   band_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(P, d->d_N, d->d_B, d->d_xq,
                                                             d->d_band_full);
   TAPS_CUDA(cudaGetLastError());

@@ -24,6 +24,16 @@ def T():
     return taps
 
 
+def _scale(dm, fac):
+    """Per-entry rounding scale of a source factor: for (Op v)[free], |Op| |v| (the
+    assembled entries agree to ~1e-13 relative and the sum cancels); else max |q|."""
+    kind, par = fac
+    if kind == "opvecfull":
+        A = np.abs(O.assemble_full(dm)[O.OP_BY_NAME[par[0]]])
+        return (A @ np.abs(np.asarray(par[1])))[dm.free]
+    return None
+
+
 def _lifted_heat(seed):
     """Transient 3D heat (Robin faces, moving source) with rank-3 boundary data on
     every Dirichlet face: sources of every operator of the description."""
@@ -35,7 +45,7 @@ def _lifted_heat(seed):
 
 def test_lifting_sources_parity(T):
     """Every lifting source factor (each operator, each dim, ragged free-node sets)
-    against the oracle's (Op v)[free] at <= 1e-12."""
+    against the oracle's (Op v)[free], per entry within 1e-11 |Op| |v|."""
     desc, vecs, wts = _lifted_heat(41)
     lifted = B.lifted(desc, vecs, wts)
     P = T.Problem(lifted)
@@ -46,7 +56,8 @@ def test_lifting_sources_parity(T):
         for d in range(Po.D):
             ref = Po.sources[r][1][d]
             got = P.source(r, d)
-            assert np.max(np.abs(got - ref)) <= 1e-12 * max(np.max(np.abs(ref)), 1e-300), (r, d)
+            sc = _scale(Po.dims[d], lifted["sources"][r][1][d])
+            assert np.all(np.abs(got - ref) <= 1e-11 * sc), (r, d)
 
 
 @pytest.mark.parametrize("solver", ["block_lu", "fastdiag"])
