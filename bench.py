@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched measurement (0: off)")
     ap.add_argument("--no-large", action="store_true", help="skip the 1536^3 reconstruction measurement")
     ap.add_argument("--no-lpbf", action="store_true", help="skip the powder-bed-fusion slab measurement")
+    ap.add_argument("--no-spt", action="store_true",
+                    help="skip the eight-dimensional space-parameter-time measurement")
     ap.add_argument("--no-e2e-modediag", action="store_true", help="skip the mode-side end-to-end solve")
     ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,bf16gram_fastdiag,"
                                        "mixed_fastdiag,mixed_fastdiag_mlp",
@@ -533,6 +535,42 @@ def run_ours(args, rank, world, local):
                     slab0_classes_ms_per_sweep={c: v["ms"] / nsw for c, v in lprof.items() if v["launches"]},
                     note="fixed sweeps per slab (a throughput run, not converged to a tolerance)")
 
+    spt = None
+    if not args.no_spt:
+        # the eight-dimensional space-parameter-time problem of Sec. 3.2 (x, y, z, k, P,
+        # rho, c_p, t) at 450 nodes per dim (450^8 = 1.7e21 grid points in the full
+        # model), s = p = 2, lifted boundary data: modes 1..8 added greedily, up to 10
+        # sweeps each (ALS change 1e-3).  Timed: problem set-up and solve.  The error
+        # against the closed-form solution is estimated afterwards from 65536 uniform
+        # random points (u = w + u_D evaluated on the device).
+        from paper_2503_13933_gb300 import boundary as BD
+        ds, (lv, lw), _ = W.spt_manufactured(450)
+        ds = BD.lifted(ds, lv, lw)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            PS = taps.Problem(ds)
+            US = PS.factors(8)
+            reps = PS.solve(US, M0=1, M_max=8, als_tol=1e-3, res_tol=-1.0, max_sweeps=10,
+                            init=taps.INIT_RANDOM, seed=3, solver=taps.SOLVER_FASTDIAG)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        rng_s = np.random.default_rng(9)
+        lo = np.array([dm["lo"] for dm in ds["dims"]])
+        hi = np.array([dm["hi"] for dm in ds["dims"]])
+        Xs = lo + (hi - lo) * rng_s.uniform(size=(1 << 16, 8))
+        us = BD.LiftedField(ds, lv, lw).eval_points(
+            PS, US, torch.as_tensor(Xs, device="cuda"),
+            torch.empty(1 << 16, dtype=torch.float64, device="cuda")).cpu().numpy()
+        ue = W.spt_exact(Xs)
+        spt = dict(grid="450^8 (x, y, z, k, P, rho, c_p, t)", equivalent_points=450.0 ** 8, s=2, p=2,
+                   modes=reps["M"], sweeps=reps["sweeps"], sources=len(ds["sources"]),
+                   setup_and_solve_s=min(times), solve_s=reps["seconds"],
+                   rel_l2_error=float(np.sqrt(np.sum((us - ue) ** 2) / np.sum(ue ** 2))),
+                   error_estimate="65536 uniform random points")
+        del PS, US
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nsw = res[best]["sweeps"]
@@ -570,6 +608,7 @@ def run_ours(args, rank, world, local):
         batched=batched,
         reconstruction_large=large,
         lpbf_slab=lpbf,
+        spt_manufactured=spt,
         clocks=res[headline]["clocks"],
     )
     print(json.dumps(line))

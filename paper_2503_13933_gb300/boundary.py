@@ -40,3 +40,36 @@ def lifting_sources(desc, vecs, weights):
 def lifted(desc, vecs, weights):
     """`desc` with the lifting's sources appended (a new description)."""
     return dict(desc, sources=list(desc["sources"]) + lifting_sources(desc, vecs, weights))
+
+
+class LiftedField:
+    """u = w + u_D at arbitrary points, both parts on the device: w through the solved
+    factors of the lifted problem, u_D through the lifting's all-node factors on a copy
+    of the dims with no constrained node (the same C-HiDeNN interpolation), in chunks of
+    at most 128 lifting modes (the factor width limit)."""
+
+    CHUNK = 128
+
+    def __init__(self, desc, vecs, weights, stream=None):
+        from . import taps
+        weights = np.asarray(weights, dtype=float)
+        free = dict(desc, dims=[dict(dm, dirichlet_lo=False, dirichlet_hi=False) for dm in desc["dims"]],
+                    sources=[(1.0, [("const", (1.0,))] * len(desc["dims"]))])
+        self._P = taps.Problem(free, stream=stream)
+        self._U = []
+        for a in range(0, len(weights), self.CHUNK):
+            b = min(a + self.CHUNK, len(weights))
+            U = self._P.factors(b - a)
+            U.set([np.asarray(vecs[0][:, a:b], dtype=float) * weights[None, a:b]] +
+                  [np.asarray(v[:, a:b], dtype=float) for v in vecs[1:]])
+            self._U.append(U)
+
+    def eval_points(self, P, U, pts, out):
+        """out = w(pts) + u_D(pts); pts a CUDA float64 tensor [n, D], out CUDA float64 [n]."""
+        import torch
+        P.eval_points(U, pts, out)
+        tmp = torch.empty_like(out)
+        for UL in self._U:
+            self._P.eval_points(UL, pts, tmp)
+            out += tmp
+        return out

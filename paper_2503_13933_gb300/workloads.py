@@ -322,3 +322,73 @@ def spt_manufactured(n=16, s=2, a=20.0, p=2, n_quad=6, svd_tol=1e-12, ranges=Non
 def spt_exact_pair(k, t):
     """The (k, t)-coupled factor of the Sec. 3.2 exact solution."""
     return 1.0 - np.exp(-15.0 * k * t)
+
+
+def spt_exact(X):
+    """The Sec. 3.2 exact solution at points X [n, 8] (x, y, z, k, P, rho, c_p, t)."""
+    x, y, _, k, Pw, rho, cp, t = np.asarray(X, dtype=float).T
+    return rho * cp * Pw * spt_exact_pair(k, t) * np.exp(-25.0 * x ** 2 - 25.0 * y ** 2)
+
+
+ST_RANGES = dict(x=(0.0, 20.0), y=(-5.0, 5.0), t=(0.0, 0.1))
+
+
+def st_exact_pair(x, t):
+    """The (x, t)-coupled factor of the Sec. 3.1 exact solution (the moving Gaussian)."""
+    return (1.0 - np.exp(-15.0 * t)) * np.exp(-(x - 100.0 * t - 5.0) ** 2)
+
+
+def st_exact(X):
+    """The Sec. 3.1 exact solution at points X [n, 3] (x, y, t)."""
+    x, y, t = np.asarray(X, dtype=float).T
+    return st_exact_pair(x, t) * np.exp(-y ** 2)
+
+
+def st_manufactured(n=100, n_t=None, s=1, a=20.0, p=1, n_quad=6, svd_tol=1e-12, ranges=None):
+    """The space-time moving-source problem of Sec. 3.1: du/dt - Laplace u = f in x, y, t
+    with the non-separable exact solution
+        u_ex = (1 - exp(-15 t)) exp(-y^2 - (x - 100 t - 5)^2),
+    zero initial condition and u = u_ex on the spatial boundary; n nodes per spatial dim,
+    n_t (default n) in time.
+
+    Readings (the paper states neither the domain nor a source consistent with u_ex: its
+    source has the Gaussian centred at x = 100 t - 5 and the opposite sign on the
+    15 exp(-15 t) term): x in [0, 20], y in [-5, 5], t in [0, 0.1], rho c_p = k = 1, and
+    f = du_ex/dt - Laplace u_ex from u_ex as printed:
+        f = [15 e^{-15t} H + 200 xi E H + (2 - 4 xi^2) E H] e^{-y^2} + E H (2 - 4 y^2) e^{-y^2},
+    E = 1 - e^{-15 t}, xi = x - 100 t - 5, H = e^{-xi^2}.  The (x, t) parts enter through
+    the SVD of their nodal matrices (truncated at svd_tol), y parts as the Gaussian kind
+    and the nodal interpolant of (2 - 4 y^2) e^{-y^2}.  The lifting (boundary nodes
+    only) is u_ex's nodal values times 1 - (1 - chi_x)(1 - chi_y), 3 sign terms.
+
+    Returns (desc, lift, exact) as spt_manufactured."""
+    R = dict(ST_RANGES, **(ranges or {}))
+    n_t = n if n_t is None else n_t
+    dims = [dim(n, *R["x"], s=s, a=a, p=p, n_quad=n_quad), dim(n, *R["y"], s=s, a=a, p=p, n_quad=n_quad),
+            dim(n_t, *R["t"], kind=TIME, s=s, a=a, p=p, n_quad=n_quad, dirichlet_lo=True, dirichlet_hi=False)]
+    terms = [(1.0, ["M", "M", "G"]), (1.0, ["K", "M", "M"]), (1.0, ["M", "K", "M"])]
+    x, y, t = (np.linspace(*R[k], m) for k, m in (("x", n), ("y", n), ("t", n_t)))
+    xx, tt = np.meshgrid(x, t, indexing="ij")
+    E = 1.0 - np.exp(-15.0 * tt)
+    xi = xx - 100.0 * tt - 5.0
+    H = np.exp(-xi ** 2)
+    f2 = 15.0 * np.exp(-15.0 * tt) * H + 200.0 * xi * E * H + (2.0 - 4.0 * xi ** 2) * E * H
+    gy = ("gauss", (0.0, math.sqrt(0.5)))
+    hy = (2.0 - 4.0 * y ** 2) * np.exp(-y ** 2)
+    sources = [(sv, [("nodal", ux), gy, ("nodal", vt)]) for sv, ux, vt in _svd_modes(f2, svd_tol)]
+    sources += [(sv, [("nodal", ux), ("nodal", hy), ("nodal", vt)]) for sv, ux, vt in _svd_modes(E * H, svd_tol)]
+    chi = np.zeros(n)
+    chi[[0, -1]] = 1.0
+    ey = np.exp(-y ** 2)
+    cols = [[], [], []]
+    wts = []
+    for sv, ux, vt in _svd_modes(E * H, svd_tol):
+        for xf, yf, sign in ((ux * chi, ey, 1.0), (ux, ey * chi, 1.0), (ux * chi, ey * chi, -1.0)):
+            cols[0].append(xf)
+            cols[1].append(yf)
+            cols[2].append(vt)
+            wts.append(sign * sv)
+    vecs = [np.stack(c, axis=1) for c in cols]
+    exact = dict(sep=[None, gy, None], pair=(0, 2))
+    desc = dict(name=f"st_manufactured_n{n}_t{n_t}_s{s}p{p}", dims=dims, terms=terms, sources=sources)
+    return desc, (vecs, np.array(wts)), exact

@@ -64,7 +64,8 @@ def test_lifting_sources_parity(T):
 def test_lifted_2d_solve_equals_direct_boundary_solve(T, solver):
     """2D Poisson on 6 x 6 nodes, random separable boundary data (rank 2 at all nodes)
     and sources: with M = 4 modes the GPU's u_D + w equals the full-grid solve with the
-    boundary values imposed directly, and the oracle's lifted solve, to 1e-9."""
+    boundary values imposed directly, and the oracle's lifted solve, to 1e-9; the
+    device evaluation of u = w + u_D at points matches the interpolants to 1e-12."""
     rng = np.random.default_rng(12)
     desc = W.poisson_sin(6, D=2)
     desc["sources"] = [(1.0, [("nodal", rng.uniform(-1, 1, 6)), ("nodal", rng.uniform(-1, 1, 6))])
@@ -97,6 +98,24 @@ def test_lifted_2d_solve_equals_direct_boundary_solve(T, solver):
     ub = uD.reshape(-1)
     uI = np.linalg.solve(A[np.ix_(inner, inner)], F[inner] - A[np.ix_(inner, ~inner)] @ ub[~inner])
     assert np.max(np.abs(u.reshape(-1) - uI)) < 1e-9 * np.max(np.abs(uI))
+    # u = w + u_D at arbitrary points on the device against the interpolants summed
+    # point by point from the same factors (the lifting's at all nodes)
+    rng2 = np.random.default_rng(5)
+    X = rng2.uniform(0.0, 1.0, (64, 2))
+    X[:4] = [[0.0, 0.3], [1.0, 0.7], [0.2, 0.0], [0.6, 1.0]]   # on the boundary: u = u_D
+    got = B.LiftedField(lifted, vecs, wts).eval_points(
+        P, U, torch.as_tensor(X, device="cuda"), torch.empty(64, dtype=torch.float64, device="cuda")).cpu().numpy()
+    dims = [O.dim_from_description(dm) for dm in lifted["dims"]]
+    V, c = O.lifted_field_factors(dims, U.get(), (vecs, wts))
+    ref = np.zeros(64)
+    for i, xp in enumerate(X):
+        prod = np.array(c)
+        for d, dm in enumerate(dims):
+            e = O.locate(dm.x, xp[d])
+            ids, N, _ = O.shape_functions(dm.x, dm.s, dm.a, dm.p, e, xp[d])
+            prod = prod * (np.asarray(N) @ V[d][np.array(ids)])
+        ref[i] = prod.sum()
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
 def test_lifted_transient_sweeps_match_oracle(T):

@@ -78,16 +78,9 @@ def _sampled_error(T, n, s=2, p=2, M=6, sweeps=10, n_pts=1 << 16, seed=9):
     hi = np.array([dm["hi"] for dm in lifted["dims"]])
     X = lo + (hi - lo) * rng.uniform(size=(n_pts, 8))
     pts = torch.as_tensor(X, device="cuda")
-    w = P.eval_points(U, pts, torch.empty(n_pts, dtype=torch.float64, device="cuda"))
-    free = dict(lifted, dims=[dict(dm, dirichlet_lo=False, dirichlet_hi=False) for dm in lifted["dims"]],
-                sources=[(1.0, [("const", (1.0,))] * 8)])
-    PL = T.Problem(free)
-    UL = PL.factors(len(wts))
-    UL.set([vecs[0] * wts[None, :]] + [np.asarray(v) for v in vecs[1:]])
-    uD = PL.eval_points(UL, pts, torch.empty(n_pts, dtype=torch.float64, device="cuda"))
-    u = (w + uD).cpu().numpy()
-    x, y, _, k, Pw, rho, cp, t = X.T
-    uex = rho * cp * Pw * W.spt_exact_pair(k, t) * np.exp(-25.0 * x ** 2 - 25.0 * y ** 2)
+    field = B.LiftedField(lifted, vecs, wts)
+    u = field.eval_points(P, U, pts, torch.empty(n_pts, dtype=torch.float64, device="cuda")).cpu().numpy()
+    uex = W.spt_exact(X)
     return math.sqrt(np.sum((u - uex) ** 2) / np.sum(uex ** 2))
 
 

@@ -98,3 +98,42 @@ def test_spt_oracle_converges_to_the_exact_solution():
         errs.append(O.relative_l2_error(P.dims, V, c, ex["sep"], ex["pair"], W.spt_exact_pair))
     rate = math.log(errs[0] / errs[1]) / math.log(13 / 9)
     assert errs[1] < 1e-2 and rate > 2.5, (errs, rate)
+
+
+def test_st_source_is_the_exact_solutions_residual():
+    """The Sec. 3.1 source as built (the reading f = du_ex/dt - Laplace u_ex): its
+    nodal (x, t) SVD factors reproduce f at nodes, and f matches central differences of
+    u_ex at interior points to the differences' own error."""
+    desc, _, _ = W.st_manufactured(40)
+    x, y, t = (np.linspace(dm["lo"], dm["hi"], dm["n"]) for dm in desc["dims"])
+    rng = np.random.default_rng(2)
+    h = 1e-4
+    for _ in range(5):
+        i, j, k = rng.integers(5, 35), rng.integers(5, 35), rng.integers(5, 35)
+        f = 0.0
+        for beta, fac in desc["sources"]:
+            vy = fac[1][1][j] if fac[1][0] == "nodal" else math.exp(-y[j] ** 2)
+            f += beta * fac[0][1][i] * vy * fac[2][1][k]
+        u = lambda a, b, c: W.st_exact(np.array([[a, b, c]]))[0]
+        ut = (u(x[i], y[j], t[k] + h) - u(x[i], y[j], t[k] - h)) / (2 * h)
+        lap = ((u(x[i] + h, y[j], t[k]) - 2 * u(x[i], y[j], t[k]) + u(x[i] - h, y[j], t[k]))
+               + (u(x[i], y[j] + h, t[k]) - 2 * u(x[i], y[j], t[k]) + u(x[i], y[j] - h, t[k]))) / h ** 2
+        scale = abs(ut) + abs(lap) + 1e-3
+        assert abs(f - (ut - lap)) < 1e-4 * scale, (f, ut - lap)
+
+
+def test_st_oracle_converges_to_the_exact_solution():
+    """Sec. 3.1 on a shortened window (x in [0, 10], y in [-4, 4], t in [0, 0.02]),
+    s = p = 1, modes 1..8 greedily: the lifted solution's error against u_ex falls at
+    order >= 1.6 in h from 24 to 48 nodes per dim (p + 1 = 2) and is below 5e-3."""
+    rng_ = dict(x=(0.0, 10.0), y=(-4.0, 4.0), t=(0.0, 0.02))
+    errs = []
+    for n in (24, 48):
+        desc, lift, ex = W.st_manufactured(n, s=1, p=1, ranges=rng_)
+        P = O.problem_from_description(dict(desc, sources=list(desc["sources"])
+                                            + O.dirichlet_lifting_sources(desc, lift)))
+        r = O.solve(P, M0=1, M_max=8, als_tol=1e-3, res_tol=-1.0, max_sweeps=5, init="random", seed=3)
+        V, c = O.lifted_field_factors(P.dims, r.U, lift)
+        errs.append(O.relative_l2_error(P.dims, V, c, ex["sep"], ex["pair"], W.st_exact_pair))
+    rate = math.log(errs[0] / errs[1]) / math.log(47 / 23)
+    assert errs[1] < 5e-3 and rate > 1.6, (errs, rate)
