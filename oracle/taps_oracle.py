@@ -286,12 +286,48 @@ class Problem:
         return [len(dm.free) for dm in self.dims]
 
 
-def build_problem(dims, terms, sources):
+OP_WEIGHTED = 16   # op code OP_WEIGHTED + j: weighted operator j of the dim
+
+
+def assemble_weighted(dim: Dim, base, w, tab=None):
+    """A weighted 1D operator over all nodes, the weight a C-HiDeNN field
+    w(x) = sum_k N~_k(x) w_k of nodal values w (App. A: rho c_p(u) and k(u) kept in the
+    separated form, so each of their modes weights the 1D integrals of Eqs. 33-35):
+        'K': int w B~_i B~_j,   'M': int w N~_i N~_j,
+        'G': int N~_i d/dt (w N~_j) = int N~_i (w' N~_j + w B~_j)   (the time derivative
+             of the product rho c_p(u) u in the weak form of App. A).
+    Element-by-element Gauss sums, as assemble_full."""
+    if tab is None:
+        tab = shape_tables(dim)
+    w = np.asarray(w, dtype=float)
+    A = np.zeros((dim.n, dim.n))
+    for pts in tab:
+        for xe, wj, ids, N, B in pts:
+            ids = np.array(ids)
+            N, B = np.asarray(N), np.asarray(B)
+            wv, dwv = N @ w[ids], B @ w[ids]
+            if base == "K":
+                A[np.ix_(ids, ids)] += wj * wv * np.outer(B, B)
+            elif base == "M":
+                A[np.ix_(ids, ids)] += wj * wv * np.outer(N, N)
+            elif base == "G":
+                A[np.ix_(ids, ids)] += wj * (dwv * np.outer(N, N) + wv * np.outer(N, B))
+            else:
+                raise ValueError(base)
+    return A
+
+
+def build_problem(dims, terms, sources, weighted=None):
     """dims: list of Dim; terms: list of (alpha, [op per dim]); sources: list of
     (beta, [(kind, par) or ('nodal', values) per dim]); kinds 'opvec' (free-node vector)
-    and 'opvecfull' (all-node vector) give par = (operator name, vector)."""
+    and 'opvecfull' (all-node vector) give par = (operator name, vector).
+    weighted[d]: list of (base 'K'|'M'|'G', all-node weights), op OP_WEIGHTED + j."""
     tabs = [shape_tables(dm) for dm in dims]
     ops = [assemble_free(dm, tb) for dm, tb in zip(dims, tabs)]
+    for d, wl in enumerate(weighted or []):
+        for j, (base, w) in enumerate(wl or []):
+            f = dims[d].free
+            ops[d][OP_WEIGHTED + j] = assemble_weighted(dims[d], base, w, tabs[d])[np.ix_(f, f)]
     src = []
     for beta, facs in sources:
         qs = []
@@ -741,10 +777,15 @@ def dim_from_description(dm):
                dirichlet_hi=dm["dirichlet_hi"], weight_poly=tuple(dm["weight_poly"]))
 
 
+def op_code(name):
+    """'K', 'M', ... or 'w<j>' (the dim's weighted operator j)."""
+    return OP_WEIGHTED + int(name[1:]) if name.startswith("w") else OP_BY_NAME[name]
+
+
 def problem_from_description(desc):
     dims = [dim_from_description(dm) for dm in desc["dims"]]
-    terms = [(a, [OP_BY_NAME[o] for o in ops]) for a, ops in desc["terms"]]
-    return build_problem(dims, terms, desc["sources"])
+    terms = [(a, [op_code(o) for o in ops]) for a, ops in desc["terms"]]
+    return build_problem(dims, terms, desc["sources"], desc.get("weighted"))
 
 
 def als_residual(prob: Problem, U):
@@ -947,3 +988,86 @@ def lifted_field_factors(dims, U, lift):
     V = [np.concatenate([to_all_nodes(dims[d], U[d]), np.asarray(vecs[d], dtype=float)], axis=1)
          for d in range(len(dims))]
     return V, np.concatenate([np.ones(M), np.asarray(wts, dtype=float)])
+
+
+# ---------------------------------------------------------------------------------
+# Nonlinear problems: global-local iteration (App. A, Algorithm 2)
+# ---------------------------------------------------------------------------------
+def cp_factors_all_nodes(dims, U):
+    """The factors of u over all nodes (constrained nodes 0)."""
+    return [to_all_nodes(dm, u) for dm, u in zip(dims, U)]
+
+
+def nonlinear_global_description(desc, law, V):
+    """The linear global stage of Algorithm 2 for rho c_p(u) du/dt-type problems on
+    space dims 0..D-2 and time dim D-1: with rho c_p = m_c u + n_c and k = m_k u + n_k
+    linear in u (Sec. 3.3), both are separated fields with the modes of the current u
+    (all-node factors V) plus a constant mode, and the weak form of App. A,
+        int du d/dt[c u] + int grad du . k grad u = int du f,
+    becomes, per mode j of c (coefficient m_c, or n_c for the constant), the term
+    (x)_{d<D-1} M[V_d,j] (x) G[V_t,j], and per mode j of k and space direction e the
+    term K[V_e,j] in dim e, M[V_d,j] in the other space dims and M[V_t,j] in time
+    (X[v] the operator weighted by the interpolant of v; the constant mode uses the
+    unweighted K, M, G).  desc: the problem's dims and sources (its terms are
+    replaced); law = (m_c, n_c, m_k, n_k)."""
+    m_c, n_c, m_k, n_k = law
+    D = len(desc["dims"])
+    Ds = D - 1
+    M = V[0].shape[1] if V is not None else 0
+    weighted = [[] for _ in range(D)]
+    names = [dict() for _ in range(D)]
+
+    def wop(d, base, j):
+        key = (base, j)
+        if key not in names[d]:
+            names[d][key] = f"w{len(weighted[d])}"
+            weighted[d].append((base, np.asarray(V[d][:, j], dtype=float)))
+        return names[d][key]
+
+    terms = [(n_c, ["M"] * Ds + ["G"])]
+    terms += [(n_k, ["K" if d == e else "M" for d in range(Ds)] + ["M"]) for e in range(Ds)]
+    for j in range(M):
+        if m_c != 0.0:
+            terms.append((m_c, [wop(d, "M", j) for d in range(Ds)] + [wop(Ds, "G", j)]))
+        if m_k != 0.0:
+            for e in range(Ds):
+                terms.append((m_k, [wop(d, "K" if d == e else "M", j) for d in range(Ds)]
+                              + [wop(Ds, "M", j)]))
+    return dict(desc, terms=terms, weighted=weighted)
+
+
+def cp_change(U_new, U_old):
+    """|u_new - u_old| / |u_new| in the Euclidean norm of the nodal tensors, by Gram
+    products of the factors."""
+    A = [np.concatenate([a, b], axis=1) for a, b in zip(U_new, U_old)]
+    G = np.ones((A[0].shape[1],) * 2)
+    for a in A:
+        G *= a.T @ a
+    m = U_new[0].shape[1]
+    c = np.concatenate([np.ones(m), -np.ones(U_old[0].shape[1])])
+    nn = float(np.sum(G[:m, :m]))
+    return math.sqrt(max(float(c @ G @ c), 0.0) / nn) if nn > 0 else 0.0
+
+
+def nonlinear_solve(desc, law, M, sweeps, max_iters=50, tol=1e-10, seed=0, solver="banded"):
+    """Algorithm 2: start from u = 0 (rho c_p = n_c, k = n_k), then repeat the global
+    stage (the linear problem of nonlinear_global_description, Algorithm 1 with M modes
+    and `sweeps` subspace iterations from the previous factors; random factors the first
+    time) and the local update of rho c_p(u), k(u) (here exact: the fields are linear in
+    u, so the update is the new factors), until the relative change of u <= tol.
+    Returns (factors, history of changes)."""
+    dims = [dim_from_description(dm) for dm in desc["dims"]]
+    U, V, hist = None, None, []
+    for it in range(max_iters):
+        P = problem_from_description(nonlinear_global_description(desc, law, V))
+        if U is None:
+            U = init_factors(P, M, "random", seed)
+        U_old = [u.copy() for u in U]
+        for _ in range(sweeps):
+            U, _ = sweep(P, U, solver)
+        ch = cp_change(U, U_old) if it > 0 else float("inf")
+        hist.append(ch)
+        V = cp_factors_all_nodes(dims, U)
+        if ch <= tol:
+            break
+    return U, hist

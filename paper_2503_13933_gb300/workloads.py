@@ -392,3 +392,88 @@ def st_manufactured(n=100, n_t=None, s=1, a=20.0, p=1, n_quad=6, svd_tol=1e-12, 
     exact = dict(sep=[None, gy, None], pair=(0, 2))
     desc = dict(name=f"st_manufactured_n{n}_t{n_t}_s{s}p{p}", dims=dims, terms=terms, sources=sources)
     return desc, (vecs, np.array(wts)), exact
+
+
+NONLINEAR_LAW = (0.5, 1.0, 0.3, 1.0)   # (m_c, n_c, m_k, n_k) of the manufactured case
+NONLINEAR_MODES = ((1.0, 1.0, 1), (0.5, 2.0, 2), (0.25, 3.0, 3))   # (amplitude, omega, k)
+
+
+def _harm_mul(a, b):
+    """Product of two harmonics ('s'|'c', k) as a list of (coef, harmonic):
+    sin a sin b = (cos(a-b) - cos(a+b))/2, cos a cos b = (cos(a-b) + cos(a+b))/2,
+    sin a cos b = (sin(a+b) + sin(a-b))/2, with sin(-k) = -sin k, cos(-k) = cos k."""
+    (ta, ka), (tb, kb) = a, b
+    def s_(k):
+        return [(1.0 if k > 0 else -1.0, ("s", abs(k)))] if k != 0 else []
+    def c_(k):
+        return [(1.0, ("c", abs(k)))]
+    if ta == "s" and tb == "s":
+        return [(0.5 * c, h) for c, h in c_(ka - kb)] + [(-0.5 * c, h) for c, h in c_(ka + kb)]
+    if ta == "c" and tb == "c":
+        return [(0.5 * c, h) for c, h in c_(ka - kb)] + [(0.5 * c, h) for c, h in c_(ka + kb)]
+    if ta == "c":
+        (ta, ka), (tb, kb) = b, a
+    return [(0.5 * c, h) for c, h in s_(ka + kb)] + [(0.5 * c, h) for c, h in s_(ka - kb)]
+
+
+def nonlinear_manufactured(n=32, n_t=None, s=2, a=20.0, p=2, law=NONLINEAR_LAW, modes=NONLINEAR_MODES):
+    """A manufactured nonlinear space-time problem for the global-local solver of
+    App. A: d/dt[c(u) u] - d/dx (k(u) du/dx) = f on x in [0, 1], t in [0, 1], with the
+    linear laws c = m_c u + n_c, k = m_k u + n_k (as in Sec. 3.3), u = 0 at x = 0, 1
+    and at t = 0, and the exact solution of CP rank 3
+        u = sum_a A_a sin(omega_a t) sin(k_a pi x).
+    f = (2 m_c u + n_c) du/dt - m_k (du/dx)^2 - (m_k u + n_k) d2u/dx2, expanded into
+    separable harmonics by the product-to-sum identities: every factor is a sine or a
+    cosine (the sine kind with phase pi/2; cos 0 = 1 the constant kind).
+    Returns the description (dims, sources; the terms are the solver's)."""
+    m_c, n_c, m_k, n_k = law
+    n_t = n if n_t is None else n_t
+    dims = [dim(n, 0.0, 1.0, s=s, a=a, p=p),
+            dim(n_t, 0.0, 1.0, kind=TIME, s=s, a=a, p=p, dirichlet_lo=True, dirichlet_hi=False)]
+    pi = math.pi
+    # u, du/dt, du/dx, d2u/dx2 as lists of (coef, x-harmonic in units of pi, t-harmonic)
+    U = [(A, ("s", k), ("s", w)) for A, w, k in modes]
+    Ut = [(A * w, ("s", k), ("c", w)) for A, w, k in modes]
+    Ux = [(A * k * pi, ("c", k), ("s", w)) for A, w, k in modes]
+    Uxx = [(-A * (k * pi) ** 2, ("s", k), ("s", w)) for A, w, k in modes]
+    acc = {}
+
+    def add(coef, hx, ht):
+        key = (hx, ht)
+        acc[key] = acc.get(key, 0.0) + coef
+
+    def prod(coef, P, Q):
+        for ca, xa, ta in P:
+            for cb, xb, tb in Q:
+                for cx, hx in _harm_mul(xa, xb):
+                    for ct, ht in _harm_mul(ta, tb):
+                        add(coef * ca * cb * cx * ct, hx, ht)
+
+    prod(2.0 * m_c, U, Ut)
+    for c, hx, ht in Ut:
+        add(n_c * c, hx, ht)
+    prod(-m_k, Ux, Ux)
+    prod(-m_k, U, Uxx)
+    for c, hx, ht in Uxx:
+        add(-n_k * c, hx, ht)
+
+    def factor(h, scale):
+        t, k = h
+        if t == "c" and k == 0:
+            return ("const", (1.0,))
+        return ("sin", (k * scale, 0.0 if t == "s" else 0.5 * pi))
+
+    sources = [(c, [factor(hx, pi), factor(ht, 1.0)]) for (hx, ht), c in sorted(acc.items())
+               if abs(c) > 1e-14 and not (hx[0] == "s" and hx[1] == 0) and not (ht[0] == "s" and ht[1] == 0)]
+    return dict(name=f"nonlinear_manufactured_n{n}_t{n_t}", dims=dims, terms=[], sources=sources)
+
+
+def nonlinear_exact(X, modes=NONLINEAR_MODES):
+    """The manufactured solution at points X [n, 2] (x, t)."""
+    x, t = np.asarray(X, dtype=float).T
+    return sum(A * np.sin(w * t) * np.sin(k * math.pi * x) for A, w, k in modes)
+
+
+def nonlinear_exact_factors(modes=NONLINEAR_MODES):
+    """Its separable form: per mode (amplitude, x-function, t-function)."""
+    return [(A, (lambda x, k=k: np.sin(k * math.pi * x)), (lambda t, w=w: np.sin(w * t))) for A, w, k in modes]
