@@ -65,6 +65,16 @@ extern "C" {
 #define TAPS_OP_BLO 4  /* point mass at the low end  (convection face, Eqs. 21/25)     */
 #define TAPS_OP_BHI 5  /* point mass at the high end                                   */
 #define TAPS_NUM_OPS 6
+/* Weighted operators (App. A: coefficients that depend on the solution, kept in the
+ * separated form, weight every 1D integral by one mode's C-HiDeNN field
+ * w(x) = sum_k N~_k(x) w_k): op code TAPS_OP_WEIGHTED + j in a term names weighted
+ * operator j of that dim, defined by taps_problem_set_weighted_ops.  Bases:
+ *   TAPS_OP_K:  int w B~_i B~_j      TAPS_OP_M:  int w N~_i N~_j
+ *   TAPS_OP_G:  int N~_i d/dt (w N~_j) = int N~_i (w' N~_j + w B~_j)
+ * A dim with weighted operators is solved by block elimination. */
+#define TAPS_OP_WEIGHTED 16
+#define TAPS_MAX_WEIGHTED 64   /* weighted operators per dim */
+#define TAPS_MAX_SLOTS 40      /* distinct operators (plain and weighted) per dim */
 
 /* ---- source factor kinds g(x) of a separable source term -------------------- */
 #define TAPS_SRC_CONST 0  /* par[0]                                       */
@@ -231,10 +241,27 @@ void taps_dim_destroy(taps_dim* dim);
  * dimensions (the problem keeps pointers: they must outlive it).  Source projections
  * q_{r,d} are computed on the device.  Errors: TAPS_ERR_INVALID_ARG for D outside
  * [1, TAPS_MAX_DIMS], R outside [1, TAPS_MAX_TERMS], Rf outside [1, TAPS_MAX_SOURCES], an operator or source kind
- * out of range, or a NULL nodal array. */
+ * out of range (operators: the plain kinds and TAPS_OP_WEIGHTED + j, j < TAPS_MAX_WEIGHTED;
+ * at most TAPS_MAX_SLOTS distinct ones per dim), or a NULL nodal array. */
 int taps_problem_create(taps_dim* const* dims, int D, const taps_term* terms, int R,
                         const taps_source* sources, int Rf, void* stream,
                         taps_problem** out);
+/* Define or update weighted operators 0..count-1 of dim `dim` (op codes
+ * TAPS_OP_WEIGHTED + j): base[j] is TAPS_OP_K, TAPS_OP_M or TAPS_OP_G and
+ * weights + j * n_d holds the nodal values of its weight at ALL n_d nodes of the dim
+ * (host memory, FP64, row j per operator).  The bands of those operators that the
+ * problem's terms use are assembled on the device (restricted to the free nodes);
+ * the next sweep or solve refreshes the Gram matrices.  Every weighted operator a
+ * term uses must be defined before the first sweep (else TAPS_ERR_INVALID_ARG).
+ * Errors: TAPS_ERR_INVALID_ARG for a bad dim, count outside [1, TAPS_MAX_WEIGHTED],
+ * a NULL array or a base other than K, M, G. */
+int taps_problem_set_weighted_ops(taps_problem* prob, int dim, int count, const int* base,
+                                  const double* weights);
+/* Copy the band of operator `op` (a plain kind or TAPS_OP_WEIGHTED + j) of dim `dim`
+ * as the problem's terms use it: [n_free][2 hb + 1] FP64 values, row i holding
+ * entries (i, i + k - hb) over the free nodes, to host memory.  TAPS_ERR_INVALID_ARG if
+ * no term uses `op` in that dim. */
+int taps_problem_copy_op(const taps_problem* prob, int dim, int op, double* host_out);
 /* Copy q_{r,d} (n_free(d) FP64 values) to host memory. */
 int taps_problem_copy_source(const taps_problem* prob, int r, int d, double* host_out);
 void taps_problem_destroy(taps_problem* prob);

@@ -1049,15 +1049,16 @@ def cp_change(U_new, U_old):
     return math.sqrt(max(float(c @ G @ c), 0.0) / nn) if nn > 0 else 0.0
 
 
-def nonlinear_solve(desc, law, M, sweeps, max_iters=50, tol=1e-10, seed=0, solver="banded"):
+def nonlinear_solve(desc, law, M, sweeps, max_iters=50, tol=1e-10, seed=0, solver="banded", U0=None):
     """Algorithm 2: start from u = 0 (rho c_p = n_c, k = n_k), then repeat the global
     stage (the linear problem of nonlinear_global_description, Algorithm 1 with M modes
-    and `sweeps` subspace iterations from the previous factors; random factors the first
-    time) and the local update of rho c_p(u), k(u) (here exact: the fields are linear in
+    and `sweeps` subspace iterations from the previous factors; U0 or random factors the
+    first time) and the local update of rho c_p(u), k(u) (here exact: the fields are linear in
     u, so the update is the new factors), until the relative change of u <= tol.
     Returns (factors, history of changes)."""
     dims = [dim_from_description(dm) for dm in desc["dims"]]
-    U, V, hist = None, None, []
+    U = [np.array(u, dtype=float) for u in U0] if U0 is not None else None
+    V, hist = None, []
     for it in range(max_iters):
         P = problem_from_description(nonlinear_global_description(desc, law, V))
         if U is None:

@@ -9,6 +9,7 @@
 
 #include "taps_internal.cuh"
 
+int taps_weighted_ready(const taps_problem* P);
 int taps_project_sources_dim(const taps_dim* d, const taps_source* sources, int Rf, int dimIndex, double* d_q,
                              cudaStream_t s);
 int taps_project_source(const taps_dim* d, int kind, const double* par, const double* nodal_host,
@@ -504,6 +505,7 @@ extern "C" void taps_problem_destroy(taps_problem* P) {
   cudaFree(P->d_bar);
   cudaFree(P->d_beta);
   cudaFree(P->d_evalbuf);
+  cudaFree(P->d_wbuf);
   if (P->h_status) cudaFreeHost(P->h_status);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->prof) {
@@ -541,16 +543,17 @@ int taps_ws_ensure(taps_problem* P, int M) {
   part = std::max(part, (size_t)3 * 64);
   size_t MM = (size_t)M * M;
   int nfm = P->nf_max;
-  TAPS_TRY(taps_alloc((void**)&P->d_C, sizeof(double) * TAPS_NUM_OPS * MM));
+  const size_t cs = (size_t)P->tt.cs;   // TAPS_NUM_OPS unless weighted operators add slots
+  TAPS_TRY(taps_alloc((void**)&P->d_C, sizeof(double) * cs * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_c, sizeof(double) * P->Rf * M));
-  TAPS_TRY(taps_alloc((void**)&P->d_Call, sizeof(double) * D * TAPS_NUM_OPS * MM));
+  TAPS_TRY(taps_alloc((void**)&P->d_Call, sizeof(double) * D * cs * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_call, sizeof(double) * D * P->Rf * M));
   TAPS_TRY(taps_alloc((void**)&P->d_ticket, sizeof(unsigned) * 64));   // >= M / 8 + 1
   TAPS_CUDA(cudaMemsetAsync(P->d_ticket, 0, sizeof(unsigned) * 64, P->stream));
   TAPS_TRY(taps_alloc((void**)&P->d_F, sizeof(double) * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_blocks, sizeof(double) * nfm * nbmax * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_lu, sizeof(double) * MM));
-  TAPS_TRY(taps_alloc((void**)&P->d_Y, sizeof(double) * TAPS_NUM_OPS * nfm * M));
+  TAPS_TRY(taps_alloc((void**)&P->d_Y, sizeof(double) * cs * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_Uold, sizeof(double) * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_fdw, sizeof(double) * taps_fdw_scratch_doubles(nfm, M)));
   TAPS_TRY(taps_alloc((void**)&P->d_md, sizeof(double) * taps_md_scratch_doubles(nfm, M, P->Rf)));
@@ -577,8 +580,21 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   for (int d = 0; d < D; ++d)
     if (!dims[d]) return TAPS_ERR_INVALID_ARG;
   for (int t = 0; t < R; ++t)
-    for (int d = 0; d < D; ++d)
-      if (terms[t].op[d] < 0 || terms[t].op[d] >= TAPS_NUM_OPS) return TAPS_ERR_INVALID_ARG;
+    for (int d = 0; d < D; ++d) {
+      const int op = terms[t].op[d];
+      const bool plain = op >= 0 && op < TAPS_NUM_OPS;
+      const bool weighted = op >= TAPS_OP_WEIGHTED && op < TAPS_OP_WEIGHTED + TAPS_MAX_WEIGHTED;
+      if (!plain && !weighted) return TAPS_ERR_INVALID_ARG;
+    }
+  for (int d = 0; d < D; ++d) {   // distinct operators per dim
+    int distinct = 0;
+    for (int t = 0; t < R; ++t) {
+      bool seen = false;
+      for (int u = 0; u < t; ++u) seen = seen || terms[u].op[d] == terms[t].op[d];
+      distinct += seen ? 0 : 1;
+    }
+    if (distinct > TAPS_MAX_SLOTS) return TAPS_ERR_INVALID_ARG;
+  }
   for (int r = 0; r < Rf; ++r)
     for (int d = 0; d < D; ++d) {
       int k = sources[r].kind[d];
@@ -614,9 +630,15 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
         P->ops[d][n++] = op;
       }
       P->tt.oi[t][d] = (signed char)slot;
+      if (op >= TAPS_OP_WEIGHTED) {
+        P->has_weighted = true;
+        P->wuse[d] |= 1ull << (op - TAPS_OP_WEIGHTED);
+      }
     }
     P->tt.nops[d] = n;
+    P->tt.cs = std::max(P->tt.cs, n);
   }
+  P->tt.cs = std::max(P->tt.cs, TAPS_NUM_OPS);
   for (int t = 0; t < R; ++t) P->tt.alpha[t] = terms[t].alpha;
   std::vector<double> hbeta(Rf);
   for (int r = 0; r < Rf; ++r) hbeta[r] = sources[r].beta;
@@ -642,10 +664,13 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
       int nops = P->tt.nops[d];
       size_t bandsz = (size_t)dm->nf * dm->nb;
       if ((st = taps_alloc((void**)&P->d_opband[d], sizeof(double) * nops * bandsz)) != TAPS_OK) break;
-      for (int j = 0; j < nops; ++j)
-        if (cudaMemcpyAsync(P->d_opband[d] + j * bandsz, dm->d_band + (size_t)P->ops[d][j] * bandsz,
-                            sizeof(double) * bandsz, cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess)
-          st = TAPS_ERR_CUDA;
+      for (int j = 0; j < nops; ++j) {
+        cudaError_t ce = P->ops[d][j] < TAPS_NUM_OPS
+                             ? cudaMemcpyAsync(P->d_opband[d] + j * bandsz, dm->d_band + (size_t)P->ops[d][j] * bandsz,
+                                               sizeof(double) * bandsz, cudaMemcpyDeviceToDevice, P->stream)
+                             : cudaMemsetAsync(P->d_opband[d] + j * bandsz, 0, sizeof(double) * bandsz, P->stream);
+        if (ce != cudaSuccess) st = TAPS_ERR_CUDA;
+      }
       if (st != TAPS_OK) break;
       if ((st = taps_alloc((void**)&P->d_q[d], sizeof(double) * Rf * dm->nf)) != TAPS_OK) break;
       st = taps_project_sources_dim(dm, sources, Rf, d, P->d_q[d], P->stream);
@@ -659,6 +684,58 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
     return st;
   }
   *out = P;
+  return TAPS_OK;
+}
+
+int taps_dim_weighted_band(const taps_dim* d, int base, const double* d_w, double* band_out, cudaStream_t stream);
+
+extern "C" int taps_problem_set_weighted_ops(taps_problem* P, int d, int count, const int* base,
+                                             const double* weights) {
+  if (!P || !base || !weights || d < 0 || d >= P->D || count < 1 || count > TAPS_MAX_WEIGHTED)
+    return TAPS_ERR_INVALID_ARG;
+  for (int j = 0; j < count; ++j)
+    if (base[j] != TAPS_OP_K && base[j] != TAPS_OP_M && base[j] != TAPS_OP_G) return TAPS_ERR_INVALID_ARG;
+  const taps_dim* dm = P->dims[d];
+  const size_t n = (size_t)dm->n, need = (size_t)count * n;
+  if (need > P->wbuf_cap) {
+    if (P->stream) TAPS_CUDA(cudaStreamSynchronize(P->stream));
+    cudaFree(P->d_wbuf);
+    P->d_wbuf = nullptr;
+    P->wbuf_cap = 0;
+    TAPS_TRY(taps_alloc((void**)&P->d_wbuf, sizeof(double) * need));
+    P->wbuf_cap = need;
+  }
+  TAPS_CUDA(cudaMemcpyAsync(P->d_wbuf, weights, sizeof(double) * need, cudaMemcpyHostToDevice, P->stream));
+  const size_t bandsz = (size_t)dm->nf * dm->nb;
+  for (int s = 0; s < P->tt.nops[d]; ++s) {
+    const int j = P->ops[d][s] - TAPS_OP_WEIGHTED;
+    if (j < 0 || j >= count) continue;
+    TAPS_TRY(taps_dim_weighted_band(dm, base[j], P->d_wbuf + (size_t)j * n, P->d_opband[d] + s * bandsz,
+                                    P->stream));
+  }
+  P->wdef[d] |= (count >= 64) ? ~0ull : ((1ull << count) - 1ull);
+  // the staging buffer is reused by the next call: the copies above must be done
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  return TAPS_OK;
+}
+
+// Every weighted operator the terms use has been defined.
+int taps_weighted_ready(const taps_problem* P) {
+  for (int d = 0; d < P->D; ++d)
+    if (P->wuse[d] & ~P->wdef[d]) return TAPS_ERR_INVALID_ARG;
+  return TAPS_OK;
+}
+
+extern "C" int taps_problem_copy_op(const taps_problem* P, int d, int op, double* host_out) {
+  if (!P || !host_out || d < 0 || d >= P->D) return TAPS_ERR_INVALID_ARG;
+  int slot = -1;
+  for (int s = 0; s < P->tt.nops[d]; ++s)
+    if (P->ops[d][s] == op) slot = s;
+  if (slot < 0) return TAPS_ERR_INVALID_ARG;
+  const size_t bandsz = (size_t)P->dims[d]->nf * P->dims[d]->nb;
+  TAPS_CUDA(cudaMemcpyAsync(host_out, P->d_opband[d] + slot * bandsz, sizeof(double) * bandsz,
+                            cudaMemcpyDeviceToHost, P->stream));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
   return TAPS_OK;
 }
 
@@ -771,6 +848,7 @@ extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const 
   int normalize = opts ? opts->normalize : 1;
   if (precision < TAPS_FP64 || precision > TAPS_BF16) return TAPS_ERR_INVALID_ARG;
   if (solver < TAPS_SOLVER_BLOCK_LU || solver > TAPS_SOLVER_MODEDIAG) return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_weighted_ready(P));
   double t0 = now_s();
   TAPS_TRY(taps_ws_ensure(P, U->M));
   TAPS_TRY(taps_md_reset(P));
@@ -789,6 +867,7 @@ extern "C" int taps_sweep(taps_problem* P, taps_factors* U, int n_sweeps, const 
 
 extern "C" int taps_residual(taps_problem* P, const taps_factors* U, int kind, double* rho_out) {
   if (!P || !U || !rho_out || U->prob != P || U->M < 1) return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_weighted_ready(P));
   return taps_residual_impl(P, U, kind, rho_out);
 }
 
@@ -801,6 +880,7 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       o->init < TAPS_INIT_GIVEN || o->init > TAPS_INIT_ZERO ||
       o->solver < TAPS_SOLVER_BLOCK_LU || o->solver > TAPS_SOLVER_MODEDIAG)
     return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_weighted_ready(P));
   double t0 = now_s();
   if (o->init != TAPS_INIT_GIVEN) {
     if (o->M0 < 1 || o->M0 > o->M_max) return TAPS_ERR_INVALID_ARG;
@@ -1221,6 +1301,7 @@ extern "C" int taps_batch_create(taps_problem* const* probs, taps_factors* const
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     if (!probs[i] || !Us[i] || Us[i]->prob != probs[i] || Us[i]->M < 1) return TAPS_ERR_INVALID_ARG;
+    if (taps_weighted_ready(probs[i]) != TAPS_OK) return TAPS_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
       if (probs[j] == probs[i]) return TAPS_ERR_INVALID_ARG;   // instances must not share workspaces
   }

@@ -285,6 +285,47 @@ __global__ void band_kernel(DimParams P, const double* Nt, const double* Bt, con
   band_full[((size_t)op * P.n + i) * P.nb + k] = v;
 }
 
+// Weighted operator over the free nodes (App. A): one thread per (free row fi, band
+// offset k), Gauss sums over the elements shared by nodes i and j = i + k - hb of
+//   K: w B~_i B~_j,   M: w N~_i N~_j,   G: N~_i (w' N~_j + w B~_j),
+// with w and w' the C-HiDeNN interpolant of the nodal weights (all nodes) and its
+// derivative at the Gauss point, summed over the element's patch nodes.  Entries
+// whose column is a constrained node are 0 (the restriction of restrict_kernel).
+__global__ void weighted_band_kernel(DimParams P, const double* Nt, const double* Bt, int base,
+                                     const double* __restrict__ w, double* __restrict__ band) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)P.nf * P.nb) return;
+  const int k = (int)(idx % P.nb);
+  const int fi = (int)(idx / P.nb);
+  const int i = fi + P.off, j = i + k - P.hb;
+  double v = 0.0;
+  if (j >= P.off && j < P.off + P.nf) {
+    const int e_lo = max(max(i, j) - P.s - 1, 0);
+    const int e_hi = min(min(i, j) + P.s, P.n - 2);
+    for (int e = e_lo; e <= e_hi; ++e) {
+      const double he = node_x(P, e + 1) - node_x(P, e);
+      const int li = i - (e - P.s), lj = j - (e - P.s);
+      for (int g = 0; g < P.nq; ++g) {
+        const size_t base_idx = ((size_t)e * P.nq + g) * P.nloc;
+        double wv = 0.0, dw = 0.0;
+        for (int l = 0; l < P.nloc; ++l) {
+          const int node = e - P.s + l;
+          if (node >= 0 && node < P.n) {
+            wv += Nt[base_idx + l] * w[node];
+            dw += Bt[base_idx + l] * w[node];
+          }
+        }
+        double term;
+        if (base == TAPS_OP_K) term = wv * Bt[base_idx + li] * Bt[base_idx + lj];
+        else if (base == TAPS_OP_M) term = wv * Nt[base_idx + li] * Nt[base_idx + lj];
+        else term = Nt[base_idx + li] * (dw * Nt[base_idx + lj] + wv * Bt[base_idx + lj]);
+        v += P.gq_w[g] * he * term;
+      }
+    }
+  }
+  band[idx] = v;
+}
+
 // Restriction of every band to the free nodes.
 __global__ void restrict_kernel(DimParams P, const double* band_full, double* band) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -659,6 +700,19 @@ extern "C" int taps_eval_points(const taps_problem* prob, const taps_factors* U,
   }
   eval_points_kernel<<<(n_pts + 127) / 128, 128, 0, prob->stream>>>(PD, prob->D, U->M, n_pts,
                                                                      pts_dev, out_dev);
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+// Weighted operator `base` (K, M or G) of dim d with nodal weights d_w (device, all
+// nodes) into band_out [nf][nb] (device), on `stream`.
+int taps_dim_weighted_band(const taps_dim* d, int base, const double* d_w, double* band_out, cudaStream_t stream) {
+  if (!d || !d_w || !band_out) return TAPS_ERR_INVALID_ARG;
+  if (base != TAPS_OP_K && base != TAPS_OP_M && base != TAPS_OP_G) return TAPS_ERR_INVALID_ARG;
+  DimParams P = make_params(d);
+  const long long tot = (long long)d->nf * d->nb;
+  if (tot == 0) return TAPS_OK;
+  weighted_band_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, stream>>>(P, d->d_N, d->d_B, base, d_w, band_out);
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }

@@ -950,6 +950,8 @@ int taps_fd_eligible(const taps_problem* P, int d, int* slotA, int* slotB) {
   int n = P->tt.nops[d];
   if (n < 1 || n > 2) return 0;
   for (int s = 0; s < n; ++s)
+    if (P->ops[d][s] >= TAPS_NUM_OPS) return 0;   // weighted operators: block elimination
+  for (int s = 0; s < n; ++s)
     if (!op_symmetric(P->ops[d][s])) return 0;
   if (n == 1) {
     *slotA = -1;

@@ -448,6 +448,7 @@ static bool md_op_mass_like(int op) { return op == TAPS_OP_M || op == TAPS_OP_W;
 int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY) {
   const int nops = P->tt.nops[d];
   if (nops < 1 || nops > 2 || M < 1 || M > 32) return 0;
+  if (P->has_weighted) return 0;   // symmetry of weighted operators is not tracked
   const int hb = P->dims[d]->hb;
   if (hb < 1 || hb > MD_MAX_HB) return 0;
   for (int e = 0; e < P->D; ++e) {

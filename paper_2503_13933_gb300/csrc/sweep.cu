@@ -18,6 +18,24 @@
 // ---------------------------------------------------------------------------------
 // The loads of one product are issued together (unrolled over TAPS_MAX_DIMS with a
 // factor 1 for the skipped dims, an exact no-op) so that their latencies overlap.
+// More distinct operators than TAPS_NUM_OPS (weighted operators): one slot at a time,
+// the terms in the same order, so each slot's sum is the one the register version forms.
+__device__ __forceinline__ void coeff_C_slots(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
+                                           double* C) {
+  const int MM = M * M;
+  for (int o = 0; o < tt.nops[d]; ++o) {
+    double acc = 0.0;
+    for (int t = 0; t < tt.R; ++t) {
+      if (tt.oi[t][d] != o) continue;
+      double prod = tt.alpha[t];
+      for (int e = 0; e < tt.D; ++e)
+        if (e != d) prod *= __ldcg(gp.gram[e] + (size_t)tt.oi[t][e] * MM + idx);
+      acc += prod;
+    }
+    C[(size_t)o * MM + idx] = acc;
+  }
+}
+
 __device__ __forceinline__ void coeff_C(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
                                         double* C) {
   const int MM = M * M;
@@ -74,6 +92,27 @@ __global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call,
   const int d = blockIdx.y;
   coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x,
               Call + (size_t)d * TAPS_NUM_OPS * M * M, call + (size_t)d * tt.Rf * M);
+}
+
+// The same with more distinct operators than TAPS_NUM_OPS in some dim (weighted
+// operators): coefficient arrays with slot stride tt.cs.
+__device__ __forceinline__ void coeff_entry_slots(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
+                                                  double* C, double* c) {
+  if (idx < M * M) coeff_C_slots(tt, gp, d, M, idx, C);
+  if (idx < M)
+    for (int r = 0; r < tt.Rf; ++r) coeff_c(tt, gp, d, M, r, idx, c);
+}
+
+__global__ void coeff_slots_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
+  taps_pdl_wait_then_release();
+  coeff_entry_slots(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x, C, c);
+}
+
+__global__ void coeff_all_slots_kernel(TermTable tt, GramPtrs gp, int M, double* Call, double* call) {
+  taps_pdl_wait_then_release();
+  const int d = blockIdx.y;
+  coeff_entry_slots(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x,
+                    Call + (size_t)d * tt.cs * M * M, call + (size_t)d * tt.Rf * M);
 }
 
 // ---------------------------------------------------------------------------------
@@ -197,6 +236,16 @@ static GramPtrs gram_ptrs(const taps_problem* P) {
 }
 
 int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision, int coeff_dim) {
+  if (P->tt.cs > TAPS_NUM_OPS && coeff_dim >= 0) {
+    // weighted operators: the Gram refresh, then the coefficients in their own launch
+    TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, -1));
+    const int M = U->M;
+    int tk = prof_begin(P, TAPS_PROF_COEFF);
+    TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+                              gram_ptrs(P), coeff_dim, M, P->d_C, P->d_c));
+    prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D, 8.0 * ((double)P->R * M * M * P->D));
+    return TAPS_OK;
+  }
   const taps_dim* dm = P->dims[d];
   int M = U->M, nf = dm->nf, hb = dm->hb, nops = P->tt.nops[d], Rf = P->Rf;
   if (M == 0) return TAPS_OK;
@@ -679,8 +728,12 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
 
 static int coefficients(taps_problem* P, int d, int M) {
   int tk = prof_begin(P, TAPS_PROF_COEFF);
-  TAPS_CUDA(taps_launch_pdl(coeff_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
-                            gram_ptrs(P), d, M, P->d_C, P->d_c));
+  if (P->tt.cs > TAPS_NUM_OPS)
+    TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+                              gram_ptrs(P), d, M, P->d_C, P->d_c));
+  else
+    TAPS_CUDA(taps_launch_pdl(coeff_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+                              gram_ptrs(P), d, M, P->d_C, P->d_c));
   prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D + (double)P->Rf * M * P->D,
            8.0 * ((double)P->R * M * M * P->D));
   TAPS_CUDA(cudaGetLastError());
@@ -801,6 +854,7 @@ struct ResDims {
   int nf[TAPS_MAX_DIMS], hb[TAPS_MAX_DIMS], nops[TAPS_MAX_DIMS];
   int cta0[TAPS_MAX_DIMS + 1];
   int D;
+  int cs;   // slot stride of Call
 };
 
 __global__ void __launch_bounds__(256) als_residual_all_kernel(ResDims rd, int M, int Rf,
@@ -839,7 +893,7 @@ __global__ void __launch_bounds__(256) als_residual_all_kernel(ResDims rd, int M
     }
   }
   __syncthreads();
-  const double* C = Call + (size_t)d * TAPS_NUM_OPS * M * M;
+  const double* C = Call + (size_t)d * rd.cs * M * M;
   const double* c = call + (size_t)d * Rf * M;
   const double* q = rd.q[d];
   double r2 = 0.0, f2 = 0.0;
@@ -971,14 +1025,19 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     // then every dim's residual in one launch.
     if (!grams_current) TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
     int tk = prof_begin(P, TAPS_PROF_COEFF);
-    TAPS_CUDA(taps_launch_pdl(coeff_all_kernel, dim3((M * M + 127) / 128, P->D), dim3(128), 0, s, P->tt,
-                              gram_ptrs(P), M, P->d_Call, P->d_call));
+    if (P->tt.cs > TAPS_NUM_OPS)
+      TAPS_CUDA(taps_launch_pdl(coeff_all_slots_kernel, dim3((M * M + 127) / 128, P->D), dim3(128), 0, s,
+                                P->tt, gram_ptrs(P), M, P->d_Call, P->d_call));
+    else
+      TAPS_CUDA(taps_launch_pdl(coeff_all_kernel, dim3((M * M + 127) / 128, P->D), dim3(128), 0, s, P->tt,
+                                gram_ptrs(P), M, P->d_Call, P->d_call));
     prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D * P->D,
              8.0 * ((double)P->R * M * M * P->D * P->D));
     TAPS_CUDA(cudaGetLastError());
     ResDims rd;
     memset(&rd, 0, sizeof(rd));
     rd.D = P->D;
+    rd.cs = P->tt.cs;
     double fl = 0.0, by = 0.0;
     int rows_max = 0;
     for (int d = 0; d < P->D; ++d) {

@@ -87,6 +87,7 @@ struct TermTable {
   const double* beta;   // device array [Rf] (source amplitudes)
   signed char oi[TAPS_MAX_TERMS][TAPS_MAX_DIMS];  // distinct-op index of term t in dim d
   int nops[TAPS_MAX_DIMS];
+  int cs;   // slot stride of the coefficient arrays: max(TAPS_NUM_OPS, max_d nops[d])
 };
 
 struct GramPtrs {
@@ -117,7 +118,12 @@ struct taps_problem {
   taps_dim* dims[TAPS_MAX_DIMS];
   cudaStream_t stream;
   TermTable tt;
-  int ops[TAPS_MAX_DIMS][TAPS_NUM_OPS];  // op kind of each distinct-op slot
+  int ops[TAPS_MAX_DIMS][TAPS_MAX_SLOTS];  // op code of each distinct-op slot
+  bool has_weighted;                       // some term uses a weighted operator
+  unsigned long long wdef[TAPS_MAX_DIMS];  // weighted operators defined (bit j)
+  unsigned long long wuse[TAPS_MAX_DIMS];  // weighted operators the terms use (bit j)
+  double* d_wbuf;                          // nodal weights staged for assembly
+  size_t wbuf_cap;
   int nf_max;
   double* d_q[TAPS_MAX_DIMS];            // [Rf][nf_d] source projections
   double* d_pq[TAPS_MAX_DIMS];           // [Rf][nf_d] Phi_d^T q_r (fast diagonalisation)
@@ -127,15 +133,15 @@ struct taps_problem {
   int ws_M;
   double* d_gram[TAPS_MAX_DIMS];  // [nops_d][M][M]
   double* d_h[TAPS_MAX_DIMS];     // [Rf][M]
-  double* d_C;        // [TAPS_NUM_OPS][M][M] coefficient matrices of the current dim
+  double* d_C;        // [tt.cs][M][M] coefficient matrices of the current dim
   double* d_c;        // [Rf][M]
-  double* d_Call;     // [D][TAPS_NUM_OPS][M][M] coefficients of every dim (residual)
+  double* d_Call;     // [D][tt.cs][M][M] coefficients of every dim (residual)
   double* d_call;     // [D][Rf][M]
   unsigned* d_ticket; // CTA tickets of the kernels whose last CTA finishes a reduction
   double* d_F;        // [nf_max][M] reduced right-hand side (node-major)
   double* d_blocks;   // [nf_max][nb][M][M] block band of the reduced matrix
   double* d_lu;       // [M][M] LU of the current diagonal block
-  double* d_Y;        // [TAPS_NUM_OPS][nf_max][M] SpMM products
+  double* d_Y;        // [tt.cs][nf_max][M] SpMM products
   double* d_Uold;     // [nf_max][M]
   double* d_fdw;      // convection-face corrections: X [nf_max][2][M][M], w [nf_max][M], small parts
   double* d_md;       // mode-side solve: W [M][M], lam [M], W^T c [Rf][M], Z [nf_max][M],

@@ -23,6 +23,12 @@ ERR_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SCRATCH_LIMIT = -5, -6, -7, -8
 NOALLOC_SCRATCH_BYTES = 4 << 20
 SPACE, PARAM, TIME = 0, 1, 2
 OP = {"K": 0, "M": 1, "G": 2, "W": 3, "Blo": 4, "Bhi": 5}
+OP_WEIGHTED = 16   # 'w<j>' in a term: weighted operator j of that dim
+
+
+def op_code(name):
+    """'K', 'M', 'G', 'W', 'Blo', 'Bhi' or 'w<j>' (the dim's weighted operator j)."""
+    return OP_WEIGHTED + int(name[1:]) if name.startswith("w") else OP[name]
 NUM_OPS = 6
 SRC = {"const": 0, "sin": 1, "gauss": 2, "poly": 3, "nodal": 4, "opvec": 5, "opvecfull": 6}
 FP64, FP32, MIXED, BF16 = 0, 1, 2, 3
@@ -91,6 +97,8 @@ SIGNATURES = {
     "taps_problem_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(Term), _i,
                                  ctypes.POINTER(Source), _i, _vp, ctypes.POINTER(_vp)]),
     "taps_problem_copy_source": (_i, [_vp, _i, _i, _pd]),
+    "taps_problem_set_weighted_ops": (_i, [_vp, _i, _i, ctypes.POINTER(_i), _pd]),
+    "taps_problem_copy_op": (_i, [_vp, _i, _i, _pd]),
     "taps_problem_destroy": (None, [_vp]),
     "taps_factors_create": (_i, [_vp, _i, ctypes.POINTER(_vp)]),
     "taps_factors_set": (_i, [_vp, _i, ctypes.POINTER(_pd)]),
@@ -242,7 +250,7 @@ class Problem:
         for t, (alpha, ops) in enumerate(desc["terms"]):
             terms[t].alpha = float(alpha)
             for d, o in enumerate(ops):
-                terms[t].op[d] = OP[o]
+                terms[t].op[d] = op_code(o)
         srcs = (Source * len(desc["sources"]))()
         self._keep = []
         for r, (beta, facs) in enumerate(desc["sources"]):
@@ -269,6 +277,24 @@ class Problem:
               "taps_problem_create")
         self.handle = h
         self.n_free = [dm.n_free for dm in self.dims]
+        for d, wl in enumerate(desc.get("weighted") or []):
+            if wl:
+                self.set_weighted(d, wl)
+
+    def set_weighted(self, d, ops):
+        """Define / update dim d's weighted operators: ops[j] = (base 'K'|'M'|'G',
+        nodal weights at all nodes) is operator 'w<j>' (taps_problem_set_weighted_ops)."""
+        base = (ctypes.c_int * len(ops))(*[OP[b] for b, _ in ops])
+        w = np.ascontiguousarray(np.stack([np.asarray(v, dtype=np.float64) for _, v in ops]))
+        check(lib().taps_problem_set_weighted_ops(self.handle, int(d), len(ops), base, w.ctypes.data_as(_pd)),
+              "taps_problem_set_weighted_ops")
+
+    def op_band(self, d, op):
+        """The band [n_free][2 hb + 1] of operator `op` ('K', ..., 'w<j>') of dim d."""
+        out = np.zeros((self.n_free[d], 2 * self.dims[d].hb + 1))
+        check(lib().taps_problem_copy_op(self.handle, int(d), op_code(op), out.ctypes.data_as(_pd)),
+              "taps_problem_copy_op")
+        return out
 
     def source(self, r, d):
         out = np.zeros(self.n_free[d])
