@@ -477,3 +477,40 @@ def nonlinear_exact(X, modes=NONLINEAR_MODES):
 def nonlinear_exact_factors(modes=NONLINEAR_MODES):
     """Its separable form: per mode (amplitude, x-function, t-function)."""
     return [(A, (lambda x, k=k: np.sin(k * math.pi * x)), (lambda t, w=w: np.sin(w * t))) for A, w, k in modes]
+
+
+# Sec. 3.3 (Inconel 718): rho c_p = m_cp u + n_cp, k = m_k u + n_k in mm, s, W, K
+INCONEL_LAW = (6.11e-7, 3.25e-3, 1.52e-5, 5.29e-3)   # (m_c, n_c, m_k, n_k)
+
+
+def nonlinear_track(n_xy=101, n_z=11, n_t=113, P=200.0, eta=0.25, d_v=0.1, r=0.5, V=500.0,
+                    svd_tol=1e-10, s=2, a=20.0, p=2):
+    """The moving-source problem with temperature-dependent coefficients of Sec. 3.3:
+    a 10 mm x 10 mm x 1 mm plate (n_xy x n_xy x n_z nodes; 10 elements across the
+    source diameter at the default 101 nodes), homogeneous Dirichlet on the left and
+    right faces (x = 0, 10 mm), insulated elsewhere, zero initial temperature rise, time
+    step 1.6e-4 s (n_t = 113: the source crosses x = 0.5 .. 9.5 mm at V = 500 mm/s), and
+    the linear laws INCONEL_LAW for rho c_p(u) and k(u).
+
+    Readings (the paper gives no power, absorptivity or penetration depth for this
+    case): the moving source of Sec. 2.4, 2 eta P / (pi r^2 d_v) exp(-2((x - x0(t))^2 +
+    (y - y0)^2) / r^2) on the top layer z >= H - d_v, with P = 200 W, eta = 0.25,
+    d_v = 0.1 mm, r = 0.5 mm, y0 = 5 mm, x0(t) = 0.5 mm + V t.  The (x, t) part enters as
+    the SVD of its nodal matrix truncated at svd_tol; y as the Gaussian kind
+    (sigma = r / 2); z as the nodal top-layer indicator.  Returns the description
+    (dims with time last, sources; the terms are the solver's)."""
+    Lx, H = 10.0, 1.0
+    T_end = 1.6e-4 * (n_t - 1)
+    dims = [dim(n_xy, 0.0, Lx, s=s, a=a, p=p),
+            dim(n_xy, 0.0, Lx, s=s, a=a, p=p, dirichlet_lo=False, dirichlet_hi=False),
+            dim(n_z, 0.0, H, s=s, a=a, p=p, dirichlet_lo=False, dirichlet_hi=False),
+            dim(n_t, 0.0, T_end, kind=TIME, s=s, a=a, p=p, dirichlet_lo=True, dirichlet_hi=False)]
+    x = np.linspace(0.0, Lx, n_xy)
+    z = np.linspace(0.0, H, n_z)
+    t = np.linspace(0.0, T_end, n_t)
+    E = np.exp(-2.0 * (x[:, None] - (0.5 + V * t[None, :])) ** 2 / r ** 2)
+    amp = 2.0 * eta * P / (math.pi * r ** 2 * d_v)
+    top = (z >= H - d_v - 1e-12).astype(float)
+    sources = [(amp * sv, [("nodal", ux), ("gauss", (5.0, 0.5 * r)), ("nodal", top), ("nodal", vt)])
+               for sv, ux, vt in _svd_modes(E, svd_tol)]
+    return dict(name=f"nonlinear_track_{n_xy}x{n_xy}x{n_z}_t{n_t}", dims=dims, terms=[], sources=sources)
