@@ -1211,9 +1211,19 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
     if (M <= 32)
       fd_small_solve_warp_kernel<<<n, 32, 0, s>>>(CA, CB, slotA >= 0 ? E->mu : nullptr, G, n, M, Y,
                                                   P->d_status, 1);
-    else
+    else {
+      // M (M + 1) doubles exceed the default 48 KB from M = 78 on: allow up to M = 128
+      static bool smem_ok = false;
+      if (!smem_ok) {
+        int dev = 0, maxsm = 0;
+        TAPS_CUDA(cudaGetDevice(&dev));
+        TAPS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        TAPS_TRY(taps_allow_dyn_smem((const void*)fd_small_solve_kernel, maxsm));
+        smem_ok = true;
+      }
       fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
           CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
+    }
     ++launches;
   }
   P->prof->launches[TAPS_PROF_FASTDIAG] += launches - 2;
