@@ -272,6 +272,15 @@ int taps_factors_create(const taps_problem* prob, int M_cap, taps_factors** out)
 int taps_factors_set(taps_factors* U, int M, const double* const* host_U);
 /* Copy the current factors to host_U[d] (n_free(d) x M column-major each). */
 int taps_factors_get(const taps_factors* U, double* const* host_U);
+/* Copy the factors of src into dst (same problem, on the device); dst takes src's mode
+ * count.  TAPS_ERR_INVALID_ARG if the problems differ or src's modes exceed dst's
+ * capacity. */
+int taps_factors_copy(taps_factors* dst, const taps_factors* src);
+/* |u_A - u_B| / |u_A| for the CP tensors of two factor sets of the same problem (the
+ * Euclidean norm of the nodal values on the free nodes), through the Gram matrices of
+ * the concatenated factors, dim by dim, on the device: the convergence check of the
+ * global-local iteration (App. A).  0 when u_A = 0. */
+int taps_factors_rel_change(const taps_factors* A, const taps_factors* B, double* out);
 int taps_factors_M(const taps_factors* U);
 /* Device pointer of U_d (n_free(d) x M_cap storage, leading dimension n_free(d)). */
 const double* taps_factors_device_ptr(const taps_factors* U, int d);

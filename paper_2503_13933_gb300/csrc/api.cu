@@ -802,6 +802,101 @@ extern "C" int taps_factors_get(const taps_factors* U, double* const* host_U) {
 
 extern "C" int taps_factors_M(const taps_factors* U) { return U ? U->M : -1; }
 
+extern "C" int taps_factors_copy(taps_factors* dst, const taps_factors* src) {
+  if (!dst || !src || dst->prob != src->prob || src->M > dst->M_cap) return TAPS_ERR_INVALID_ARG;
+  const taps_problem* P = src->prob;
+  for (int d = 0; d < P->D && src->M > 0; ++d)
+    TAPS_CUDA(cudaMemcpyAsync(dst->d_U[d], src->d_U[d], sizeof(double) * P->dims[d]->nf * src->M,
+                              cudaMemcpyDeviceToDevice, P->stream));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  dst->M = src->M;
+  return TAPS_OK;
+}
+
+// G[a][b] = x_a . x_b over the K = MA + MB columns of [UA | UB] of one dim (one CTA per
+// entry, a fixed reduction order).
+__global__ void pair_gram_kernel(const double* __restrict__ UA, const double* __restrict__ UB, int nf, int MA,
+                                 int K, double* __restrict__ G) {
+  __shared__ double red[32];
+  const int a = blockIdx.x / K, b = blockIdx.x % K;
+  const double* xa = a < MA ? UA + (size_t)a * nf : UB + (size_t)(a - MA) * nf;
+  const double* xb = b < MA ? UA + (size_t)b * nf : UB + (size_t)(b - MA) * nf;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) acc += xa[i] * xb[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) G[blockIdx.x] = acc;
+  }
+}
+
+// out = (sum_ab c_a c_b prod_d G_d[a][b], sum_{a,b < MA} prod_d G_d[a][b]) with
+// c = (1 .. 1, -1 .. -1): |u_A - u_B|^2 and |u_A|^2 of the CP tensors (one CTA).
+__global__ void pair_change_kernel(const double* __restrict__ G, int D, int K, int MA, double* __restrict__ out) {
+  __shared__ double rn[32], rd[32];
+  double num = 0.0, den = 0.0;
+  const int KK = K * K;
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
+    double prod = 1.0;
+    for (int d = 0; d < D; ++d) prod *= G[(size_t)d * KK + e];
+    const int a = e / K, b = e % K;
+    const double ca = a < MA ? 1.0 : -1.0, cb = b < MA ? 1.0 : -1.0;
+    num += ca * cb * prod;
+    if (a < MA && b < MA) den += prod;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_down_sync(0xffffffffu, num, o);
+    den += __shfl_down_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rn[threadIdx.x >> 5] = num;
+    rd[threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    num = threadIdx.x < (blockDim.x >> 5) ? rn[threadIdx.x] : 0.0;
+    den = threadIdx.x < (blockDim.x >> 5) ? rd[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_down_sync(0xffffffffu, num, o);
+      den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (threadIdx.x == 0) {
+      out[0] = num;
+      out[1] = den;
+    }
+  }
+}
+
+extern "C" int taps_factors_rel_change(const taps_factors* A, const taps_factors* B, double* out) {
+  if (!A || !B || !out || A->prob != B->prob || A->M < 1 || B->M < 1) return TAPS_ERR_INVALID_ARG;
+  const taps_problem* P = A->prob;
+  const int K = A->M + B->M, D = P->D;
+  const size_t KK = (size_t)K * K;
+  double* buf = nullptr;
+  TAPS_TRY(taps_alloc((void**)&buf, sizeof(double) * (D * KK + 2)));
+  int st = TAPS_OK;
+  for (int d = 0; d < D && st == TAPS_OK; ++d) {
+    pair_gram_kernel<<<(unsigned)KK, 128, 0, P->stream>>>(A->d_U[d], B->d_U[d], P->dims[d]->nf, A->M, K,
+                                                           buf + (size_t)d * KK);
+    if (cudaGetLastError() != cudaSuccess) st = TAPS_ERR_CUDA;
+  }
+  double h[2] = {0.0, 0.0};
+  if (st == TAPS_OK) {
+    pair_change_kernel<<<1, 256, 0, P->stream>>>(buf, D, K, A->M, buf + (size_t)D * KK);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h, buf + (size_t)D * KK, sizeof(h), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess)
+      st = TAPS_ERR_CUDA;
+  }
+  cudaFree(buf);
+  if (st != TAPS_OK) return st;
+  *out = h[1] > 0.0 ? sqrt(std::max(h[0], 0.0) / h[1]) : 0.0;
+  return TAPS_OK;
+}
+
 extern "C" const double* taps_factors_device_ptr(const taps_factors* U, int d) {
   if (!U || d < 0 || d >= U->prob->D) return nullptr;
   return U->d_U[d];

@@ -11,12 +11,11 @@ in time, X[v] the 1D operator weighted by the C-HiDeNN interpolant of the mode's
 factor v (TAPS_OP_WEIGHTED operators, assembled on the device).  The local stage
 updates c and k from the new u; with linear laws that is exact in the separated form
 (the weights become the new factors).  The iteration stops when the relative change of
-u falls below the tolerance.  The problem and its term structure are built once; each
-global stage re-assembles the weighted operators and runs Algorithm 1.
+u falls below the tolerance (taps_factors_rel_change, on the device).  The problem and
+its term structure are built once; each global stage re-assembles the weighted
+operators and runs Algorithm 1.
 """
 from __future__ import annotations
-
-import math
 
 import numpy as np
 
@@ -54,18 +53,6 @@ def global_terms(D, M, law):
     return terms, wops
 
 
-def relative_change(U_new, U_old):
-    """|u_new - u_old| / |u_new| (Euclidean norm of the nodal tensors) by Gram products."""
-    A = [np.concatenate([a, b], axis=1) for a, b in zip(U_new, U_old)]
-    G = np.ones((A[0].shape[1],) * 2)
-    for a in A:
-        G *= a.T @ a
-    m = U_new[0].shape[1]
-    c = np.concatenate([np.ones(m), -np.ones(U_old[0].shape[1])])
-    nn = float(np.sum(G[:m, :m]))
-    return math.sqrt(max(float(c @ G @ c), 0.0) / nn) if nn > 0 else 0.0
-
-
 class GlobalLocal:
     """Algorithm 2 for a description `desc` (dims with time last, sources; its terms
     are replaced) and law = (m_c, n_c, m_k, n_k)."""
@@ -79,6 +66,7 @@ class GlobalLocal:
         self.dims = desc["dims"]
         self.P = taps.Problem(self.desc, stream=stream)
         self.U = self.P.factors(M)
+        self.U_old = self.P.factors(M)
         self._set_weights(None)
 
     def _set_weights(self, U):
@@ -109,11 +97,11 @@ class GlobalLocal:
         self._set_weights(None)
         hist, U = [], None
         for it in range(max_iters):
-            U_old = self.U.get()
+            self.U_old.copy_from(self.U)
             self.P.sweep(self.U, sweeps, solver=solver)
-            U = self.U.get()
-            ch = relative_change(U, U_old) if it > 0 else float("inf")
+            ch = self.U.rel_change(self.U_old) if it > 0 else float("inf")
             hist.append(ch)
+            U = self.U.get()   # the new weights (host copies for the weighted-operator call)
             self._set_weights(U)
             if ch <= tol:
                 break

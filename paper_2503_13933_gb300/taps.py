@@ -99,6 +99,8 @@ SIGNATURES = {
     "taps_problem_copy_source": (_i, [_vp, _i, _i, _pd]),
     "taps_problem_set_weighted_ops": (_i, [_vp, _i, _i, ctypes.POINTER(_i), _pd]),
     "taps_problem_copy_op": (_i, [_vp, _i, _i, _pd]),
+    "taps_factors_copy": (_i, [_vp, _vp]),
+    "taps_factors_rel_change": (_i, [_vp, _vp, _pd]),
     "taps_problem_destroy": (None, [_vp]),
     "taps_factors_create": (_i, [_vp, _i, ctypes.POINTER(_vp)]),
     "taps_factors_set": (_i, [_vp, _i, ctypes.POINTER(_pd)]),
@@ -501,6 +503,17 @@ class Factors:
                                                ctypes.c_void_p(prof.data_ptr()), n_ref,
                                                float(weight_scale)),
               "taps_factors_from_profiles")
+
+    def copy_from(self, other):
+        """These factors := other's (same problem; a device copy)."""
+        check(lib().taps_factors_copy(self.handle, other.handle), "taps_factors_copy")
+
+    def rel_change(self, other):
+        """|u_self - u_other| / |u_self| of the CP tensors, on the device."""
+        out = ctypes.c_double()
+        check(lib().taps_factors_rel_change(self.handle, other.handle, ctypes.byref(out)),
+              "taps_factors_rel_change")
+        return out.value
 
     def get(self):
         M = self.M

@@ -156,3 +156,22 @@ def test_moving_source_track_matches_oracle(T):
     ug, uo = O.cp_full(U), O.cp_full(Uo)
     assert np.max(np.abs(ug - uo)) <= 1e-8 * np.max(np.abs(uo))
     assert np.allclose(hist[1:], ho[1:], rtol=1e-6)
+
+
+def test_factor_copy_and_relative_change_match_oracle(T):
+    """taps_factors_copy (device copy) and taps_factors_rel_change (Gram products on the
+    device) against the oracle's |u_A - u_B| / |u_A| of random factor sets with
+    different mode counts, and 0 for identical sets."""
+    desc = _global(19, 3, seed=8)
+    P = T.Problem(desc)
+    A0 = W.random_factors(desc, 5, seed=9)
+    B0 = [a[:, :3] + 0.1 * b for a, b in zip(A0, W.random_factors(desc, 3, seed=10))]
+    A, B, C = P.factors(5), P.factors(5), P.factors(5)
+    A.set(A0)
+    B.set(B0)
+    got = A.rel_change(B)
+    ref = O.cp_change(A0, B0)
+    assert abs(got - ref) <= 1e-9 * ref
+    C.copy_from(A)
+    assert C.M == 5 and all(np.array_equal(x, y) for x, y in zip(C.get(), A0))
+    assert C.rel_change(A) <= 1e-7   # the expansion's rounding floor
