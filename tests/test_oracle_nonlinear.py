@@ -102,3 +102,21 @@ def test_linear_laws_with_zero_slope_reduce_to_one_linear_solve():
     assert all(not wl for wl in g["weighted"]) and len(g["terms"]) == 2
     U, hist = O.nonlinear_solve(desc, law, M=3, sweeps=40, max_iters=5, tol=1e-9, seed=1)
     assert len(hist) <= 3
+
+
+@pytest.mark.parametrize("D,M,law", [(2, 3, W.NONLINEAR_LAW), (4, 5, W.INCONEL_LAW), (3, 1, (0.0, 1.0, 0.2, 1.0)),
+                                     (4, 2, (0.3, 1.0, 0.0, 2.0))])
+def test_library_global_stage_terms_match_the_oracle_reading(D, M, law):
+    """The library's global-stage term structure (host logic of nonlinear.py) equals the
+    oracle's reading of Algorithm 2's weak form: the same terms in the same order and,
+    per dim, the same weighted operators (base and mode) behind each 'w<j>' name."""
+    from paper_2503_13933_gb300 import nonlinear as NL
+    terms, wops = NL.global_terms(D, M, law)
+    dims = [dict(n=6, dirichlet_lo=True, dirichlet_hi=True)] * D
+    V = [np.tile(np.arange(1.0, M + 1.0), (6, 1)) * (d + 1) for d in range(D)]
+    g = O.nonlinear_global_description(dict(dims=dims, sources=[]), law, V)
+    assert g["terms"] == terms
+    for d in range(D):
+        assert [b for b, _ in g["weighted"][d]] == [b for b, _ in wops[d]]
+        for (b, w), (b2, j) in zip(g["weighted"][d], wops[d]):
+            assert np.array_equal(w, V[d][:, j])
