@@ -10,6 +10,8 @@ convection : a powder-bed-fusion slab at 128^2 x 32 space, M = 20, two sweeps
 images     : the FP32 tensor-core reconstruction of poisson_k 160^3 x 32, M = 30
 pencil     : poisson_k 256^3 x 32, M = 30, one node-side sweep (the pencil
              decomposition of the 254-node space dims runs first)
+nonlinear  : the temperature-dependent moving-source plate at full size (101^2 x 11
+             space, 113 time, M = 10): two global stages of two subspace iterations
 """
 from __future__ import annotations
 
@@ -50,7 +52,13 @@ def _pencil(taps, W):
     P.sweep(U, 1, solver=taps.SOLVER_FASTDIAG)
 
 
-CASES = dict(modediag=_modediag, convection=_convection, images=_images, pencil=_pencil)
+def _nonlinear(taps, W):
+    from . import nonlinear as NL
+    gl = NL.GlobalLocal(W.nonlinear_track(), W.INCONEL_LAW, 10)
+    gl.solve(2, max_iters=2, tol=0.0, seed=5)
+
+
+CASES = dict(modediag=_modediag, convection=_convection, images=_images, pencil=_pencil, nonlinear=_nonlinear)
 
 
 def main(argv=None):
