@@ -687,7 +687,8 @@ extern "C" int taps_problem_create(taps_dim* const* dims, int D, const taps_term
   return TAPS_OK;
 }
 
-int taps_dim_weighted_band(const taps_dim* d, int base, const double* d_w, double* band_out, cudaStream_t stream);
+int taps_dim_weighted_bands(const taps_dim* d, int count, const int* base, const int* slot, const double* d_w,
+                            double* bands, cudaStream_t stream);
 
 extern "C" int taps_problem_set_weighted_ops(taps_problem* P, int d, int count, const int* base,
                                              const double* weights) {
@@ -706,13 +707,13 @@ extern "C" int taps_problem_set_weighted_ops(taps_problem* P, int d, int count, 
     P->wbuf_cap = need;
   }
   TAPS_CUDA(cudaMemcpyAsync(P->d_wbuf, weights, sizeof(double) * need, cudaMemcpyHostToDevice, P->stream));
-  const size_t bandsz = (size_t)dm->nf * dm->nb;
+  int slot[TAPS_MAX_WEIGHTED];
+  for (int j = 0; j < count; ++j) slot[j] = -1;
   for (int s = 0; s < P->tt.nops[d]; ++s) {
     const int j = P->ops[d][s] - TAPS_OP_WEIGHTED;
-    if (j < 0 || j >= count) continue;
-    TAPS_TRY(taps_dim_weighted_band(dm, base[j], P->d_wbuf + (size_t)j * n, P->d_opband[d] + s * bandsz,
-                                    P->stream));
+    if (j >= 0 && j < count) slot[j] = s;
   }
+  TAPS_TRY(taps_dim_weighted_bands(dm, count, base, slot, P->d_wbuf, P->d_opband[d], P->stream));
   P->wdef[d] |= (count >= 64) ? ~0ull : ((1ull << count) - 1ull);
   // the staging buffer is reused by the next call: the copies above must be done
   TAPS_CUDA(cudaStreamSynchronize(P->stream));

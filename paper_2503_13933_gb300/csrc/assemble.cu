@@ -291,8 +291,21 @@ __global__ void band_kernel(DimParams P, const double* Nt, const double* Bt, con
 // with w and w' the C-HiDeNN interpolant of the nodal weights (all nodes) and its
 // derivative at the Gauss point, summed over the element's patch nodes.  Entries
 // whose column is a constrained node are 0 (the restriction of restrict_kernel).
-__global__ void weighted_band_kernel(DimParams P, const double* Nt, const double* Bt, int base,
-                                     const double* __restrict__ w, double* __restrict__ band) {
+// Every weighted operator of one dim in one launch: blockIdx.y = operator, its base,
+// weight row and output band from the table.
+struct WeightedOps {
+  int count;
+  int base[TAPS_MAX_SLOTS];
+  int wrow[TAPS_MAX_SLOTS];   // row of the weights array
+  int slot[TAPS_MAX_SLOTS];   // band slot in the output
+};
+
+__global__ void weighted_band_kernel(DimParams P, const double* Nt, const double* Bt, WeightedOps ops,
+                                     const double* __restrict__ wall, double* __restrict__ bands) {
+  const int o = blockIdx.y;
+  const int base = ops.base[o];
+  const double* __restrict__ w = wall + (size_t)ops.wrow[o] * P.n;
+  double* __restrict__ band = bands + (size_t)ops.slot[o] * P.nf * P.nb;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)P.nf * P.nb) return;
   const int k = (int)(idx % P.nb);
@@ -704,15 +717,28 @@ extern "C" int taps_eval_points(const taps_problem* prob, const taps_factors* U,
   return TAPS_OK;
 }
 
-// Weighted operator `base` (K, M or G) of dim d with nodal weights d_w (device, all
-// nodes) into band_out [nf][nb] (device), on `stream`.
-int taps_dim_weighted_band(const taps_dim* d, int base, const double* d_w, double* band_out, cudaStream_t stream) {
-  if (!d || !d_w || !band_out) return TAPS_ERR_INVALID_ARG;
-  if (base != TAPS_OP_K && base != TAPS_OP_M && base != TAPS_OP_G) return TAPS_ERR_INVALID_ARG;
-  DimParams P = make_params(d);
+// Weighted operators of dim d: for each j < count with slot[j] >= 0, base[j] (K, M or
+// G) weighted by row j of d_w (device, [count][n] all-node values) into band slot
+// slot[j] of bands ([slots][nf][nb], device), in one launch on `stream`.
+int taps_dim_weighted_bands(const taps_dim* d, int count, const int* base, const int* slot, const double* d_w,
+                            double* bands, cudaStream_t stream) {
+  if (!d || !d_w || !bands || count < 0) return TAPS_ERR_INVALID_ARG;
+  WeightedOps ops;
+  memset(&ops, 0, sizeof(ops));
+  for (int j = 0; j < count; ++j) {
+    if (slot[j] < 0) continue;
+    if (ops.count >= TAPS_MAX_SLOTS) return TAPS_ERR_INVALID_ARG;
+    if (base[j] != TAPS_OP_K && base[j] != TAPS_OP_M && base[j] != TAPS_OP_G) return TAPS_ERR_INVALID_ARG;
+    ops.base[ops.count] = base[j];
+    ops.wrow[ops.count] = j;
+    ops.slot[ops.count] = slot[j];
+    ++ops.count;
+  }
   const long long tot = (long long)d->nf * d->nb;
-  if (tot == 0) return TAPS_OK;
-  weighted_band_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, stream>>>(P, d->d_N, d->d_B, base, d_w, band_out);
+  if (tot == 0 || ops.count == 0) return TAPS_OK;
+  DimParams P = make_params(d);
+  weighted_band_kernel<<<dim3((unsigned)((tot + 127) / 128), ops.count), 128, 0, stream>>>(P, d->d_N, d->d_B, ops,
+                                                                                        d_w, bands);
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }
