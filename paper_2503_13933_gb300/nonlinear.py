@@ -62,6 +62,8 @@ class GlobalLocal:
         self.M = M
         D = len(desc["dims"])
         terms, self.wops = global_terms(D, M, law)
+        if len(terms) > taps.MAX_TERMS:
+            raise ValueError(f"{len(terms)} operator terms for M = {M} exceed the library's {taps.MAX_TERMS}")
         self.desc = dict(desc, terms=terms)
         self.dims = desc["dims"]
         self.P = taps.Problem(self.desc, stream=stream)
