@@ -137,3 +137,22 @@ def test_st_oracle_converges_to_the_exact_solution():
         errs.append(O.relative_l2_error(P.dims, V, c, ex["sep"], ex["pair"], W.st_exact_pair))
     rate = math.log(errs[0] / errs[1]) / math.log(47 / 23)
     assert errs[1] < 5e-3 and rate > 1.6, (errs, rate)
+
+
+def test_relative_l2_error_separable_exact_matches_brute_force():
+    """No coupled pair: exact solution sin(3x) (x) poly, random CP field; the Gram
+    expansion equals the direct tensor sum point by point."""
+    rng = np.random.default_rng(11)
+    dims = [O.Dim(n=8, lo=0.0, hi=1.0, s=2, p=2, n_quad=4), O.Dim(n=6, lo=-1.0, hi=1.0, s=1, p=1, n_quad=4)]
+    V = [rng.uniform(-1, 1, (d.n, 2)) for d in dims]
+    c = np.array([1.5, -0.4])
+    sep = [("sin", (3.0, 0.0)), ("poly", (0.5, -1.0, 0.25))]
+    got = O.relative_l2_error(dims, V, c, sep)
+    rules = [_tensor_rule(d) for d in dims]
+    F = [_interp_at(d, v, r[0]) for d, v, r in zip(dims, V, rules)]
+    u = np.einsum("am,bm,m->ab", F[0], F[1], c)
+    xa, xb = rules[0][0], rules[1][0]
+    ex = np.sin(3.0 * xa)[:, None] * (0.5 - xb + 0.25 * xb ** 2)[None, :]
+    w = np.outer(rules[0][1], rules[1][1])
+    ref = math.sqrt(np.sum(w * (u - ex) ** 2) / np.sum(w * ex ** 2))
+    assert abs(got - ref) <= 1e-9 * ref
