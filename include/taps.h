@@ -277,9 +277,13 @@ int taps_factors_get(const taps_factors* U, double* const* host_U);
  * capacity. */
 int taps_factors_copy(taps_factors* dst, const taps_factors* src);
 /* |u_A - u_B| / |u_A| for the CP tensors of two factor sets of the same problem (the
- * Euclidean norm of the nodal values on the free nodes), through the Gram matrices of
- * the concatenated factors, dim by dim, on the device: the convergence check of the
- * global-local iteration (App. A).  0 when u_A = 0. */
+ * Euclidean norm of the nodal values on the free nodes), on the device: the
+ * convergence check of the global-local iteration (App. A).  The difference is
+ * evaluated as a CP tensor of D * max(M_A, M_B) telescoped terms (per mode,
+ * prod a_d - prod b_d = sum_k prod_{d<k} b_d (a_k - b_k) prod_{d>k} a_d, the shorter set
+ * padded with zero columns) through 1D Gram products, so small changes keep their
+ * relative accuracy (no |a|^2 + |b|^2 - 2<a, b> cancellation).  0 when u_A = 0 and for
+ * identical factor sets. */
 int taps_factors_rel_change(const taps_factors* A, const taps_factors* B, double* out);
 int taps_factors_M(const taps_factors* U);
 /* Device pointer of U_d (n_free(d) x M_cap storage, leading dimension n_free(d)). */
@@ -335,9 +339,10 @@ int taps_eval_grid(const taps_problem* prob, const taps_factors* U, const int* s
  * output type) lives in one fixed array of TAPS_NOALLOC_SCRATCH_BYTES in device
  * global memory, which every GPU that loads this library holds until the process
  * exits.  Requests that need more return TAPS_ERR_SCRATCH_LIMIT and touch nothing.
- * The first call on a device looks up that array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call on a device shares the one array and it keeps the last
+ * Every call looks up that array's device address with the calling device current
+ * (no allocation; nothing cached, so a reset primary context is safe); the first
+ * lookup on a device may load the library's device code, so make the first call on
+ * each device before any stream capture.  Every call on a device shares the one array and it keeps the last
  * call's contents (each call overwrites all it reads, so nothing needs clearing);
  * calls whose kernels overlap on the GPU -- on different streams, or different
  * problems launched concurrently -- race on it and must be serialised by the

@@ -1037,16 +1037,39 @@ def nonlinear_global_description(desc, law, V):
 
 
 def cp_change(U_new, U_old):
-    """|u_new - u_old| / |u_new| in the Euclidean norm of the nodal tensors, by Gram
-    products of the factors."""
-    A = [np.concatenate([a, b], axis=1) for a, b in zip(U_new, U_old)]
-    G = np.ones((A[0].shape[1],) * 2)
-    for a in A:
-        G *= a.T @ a
-    m = U_new[0].shape[1]
-    c = np.concatenate([np.ones(m), -np.ones(U_old[0].shape[1])])
-    nn = float(np.sum(G[:m, :m]))
-    return math.sqrt(max(float(c @ G @ c), 0.0) / nn) if nn > 0 else 0.0
+    """|u_new - u_old| / |u_new| in the Euclidean norm of the nodal tensors (the
+    convergence check of Algorithm 2, App. A), by Gram products of the factors.
+
+    Expanding |a|^2 + |b|^2 - 2 <a, b> cancels to ~sqrt(eps) relative, far above the
+    changes a converging iteration reaches.  So the difference itself is written as a
+    CP tensor whose terms are all small, by telescoping each mode's product
+    (the shorter factor set padded with zero columns):
+        prod_d a_d - prod_d b_d = sum_k (prod_{d<k} b_d) (a_k - b_k) (prod_{d>k} a_d),
+    and its squared norm is the sum over pairs of those D*M terms of the products of
+    their 1D inner products."""
+    D = len(U_new)
+    Mx = max(U_new[0].shape[1], U_old[0].shape[1])
+
+    def pad(u):
+        return np.concatenate([u, np.zeros((u.shape[0], Mx - u.shape[1]))], axis=1)
+
+    A = [pad(u) for u in U_new]
+    B = [pad(u) for u in U_old]
+    terms = []     # per telescoped term (k, m): its factor in every dim
+    for k in range(D):
+        for m in range(Mx):
+            terms.append([B[d][:, m] if d < k else (A[d][:, m] - B[d][:, m] if d == k else A[d][:, m])
+                          for d in range(D)])
+    T = len(terms)
+    G = np.ones((T, T))
+    for d in range(D):
+        F = np.stack([t[d] for t in terms], axis=1)
+        G *= F.T @ F
+    GA = np.ones((U_new[0].shape[1],) * 2)
+    for a in U_new:
+        GA *= a.T @ a
+    nn = float(np.sum(GA))
+    return math.sqrt(max(float(np.sum(G)), 0.0) / nn) if nn > 0 else 0.0
 
 
 def nonlinear_solve(desc, law, M, sweeps, max_iters=50, tol=1e-10, seed=0, solver="banded", U0=None):

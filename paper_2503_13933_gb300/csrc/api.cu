@@ -814,16 +814,25 @@ extern "C" int taps_factors_copy(taps_factors* dst, const taps_factors* src) {
   return TAPS_OK;
 }
 
-// G[a][b] = x_a . x_b over the K = MA + MB columns of [UA | UB] of one dim (one CTA per
-// entry, a fixed reduction order).
+// Gram matrix of the 3 Mx columns [A | B | A - B] of one dim (A and B padded with zero
+// columns to Mx = max(MA, MB)); one CTA per entry.  The difference columns are formed
+// here, exactly as the telescoped change below needs them.
+__device__ __forceinline__ double pair_col(const double* UA, const double* UB, int MA, int MB, int Mx,
+                                           int nf, int c, int i) {
+  const int blk = c / Mx, m = c % Mx;
+  const double a = m < MA ? UA[(size_t)m * nf + i] : 0.0;
+  const double b = m < MB ? UB[(size_t)m * nf + i] : 0.0;
+  return blk == 0 ? a : (blk == 1 ? b : a - b);
+}
+
 __global__ void pair_gram_kernel(const double* __restrict__ UA, const double* __restrict__ UB, int nf, int MA,
-                                 int K, double* __restrict__ G) {
+                                 int MB, int Mx, double* __restrict__ G) {
   __shared__ double red[32];
+  const int K = 3 * Mx;
   const int a = blockIdx.x / K, b = blockIdx.x % K;
-  const double* xa = a < MA ? UA + (size_t)a * nf : UB + (size_t)(a - MA) * nf;
-  const double* xb = b < MA ? UA + (size_t)b * nf : UB + (size_t)(b - MA) * nf;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < nf; i += blockDim.x) acc += xa[i] * xb[i];
+  for (int i = threadIdx.x; i < nf; i += blockDim.x)
+    acc += pair_col(UA, UB, MA, MB, Mx, nf, a, i) * pair_col(UA, UB, MA, MB, Mx, nf, b, i);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -834,19 +843,34 @@ __global__ void pair_gram_kernel(const double* __restrict__ UA, const double* __
   }
 }
 
-// out = (sum_ab c_a c_b prod_d G_d[a][b], sum_{a,b < MA} prod_d G_d[a][b]) with
-// c = (1 .. 1, -1 .. -1): |u_A - u_B|^2 and |u_A|^2 of the CP tensors (one CTA).
-__global__ void pair_change_kernel(const double* __restrict__ G, int D, int K, int MA, double* __restrict__ out) {
+// |u_A - u_B|^2 and |u_A|^2 (one CTA).  The difference of the two CP tensors is written
+// as D * Mx terms whose factors are all small where the factor sets are close: per mode
+// m, prod_d a_d - prod_d b_d = sum_k (prod_{d<k} b_d)(a_k - b_k)(prod_{d>k} a_d), so its
+// squared norm, the sum over pairs of those terms of the products of their 1D inner
+// products, keeps relative accuracy down to changes near the rounding of the factors
+// (the expansion |a|^2 + |b|^2 - 2<a, b> cancels to ~sqrt(eps)).
+__global__ void pair_change_kernel(const double* __restrict__ G, int D, int Mx, int MA, double* __restrict__ out) {
   __shared__ double rn[32], rd[32];
   double num = 0.0, den = 0.0;
-  const int KK = K * K;
-  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
+  const int K = 3 * Mx, T = D * Mx;
+  const size_t KK = (size_t)K * K;
+  const long long TT = (long long)T * T;
+  for (long long e = threadIdx.x; e < TT; e += blockDim.x) {
+    const int p = (int)(e / T), q = (int)(e % T);
+    const int kp = p / Mx, mp = p % Mx, kq = q / Mx, mq = q % Mx;
     double prod = 1.0;
-    for (int d = 0; d < D; ++d) prod *= G[(size_t)d * KK + e];
-    const int a = e / K, b = e % K;
-    const double ca = a < MA ? 1.0 : -1.0, cb = b < MA ? 1.0 : -1.0;
-    num += ca * cb * prod;
-    if (a < MA && b < MA) den += prod;
+    for (int d = 0; d < D; ++d) {
+      const int cp = (d < kp ? Mx : (d == kp ? 2 * Mx : 0)) + mp;
+      const int cq = (d < kq ? Mx : (d == kq ? 2 * Mx : 0)) + mq;
+      prod *= G[(size_t)d * KK + (size_t)cp * K + cq];
+    }
+    num += prod;
+  }
+  for (int e = threadIdx.x; e < MA * MA; e += blockDim.x) {
+    const int a = e / MA, b = e % MA;
+    double prod = 1.0;
+    for (int d = 0; d < D; ++d) prod *= G[(size_t)d * KK + (size_t)a * K + b];
+    den += prod;
   }
   for (int o = 16; o > 0; o >>= 1) {
     num += __shfl_down_sync(0xffffffffu, num, o);
@@ -874,19 +898,19 @@ __global__ void pair_change_kernel(const double* __restrict__ G, int D, int K, i
 extern "C" int taps_factors_rel_change(const taps_factors* A, const taps_factors* B, double* out) {
   if (!A || !B || !out || A->prob != B->prob || A->M < 1 || B->M < 1) return TAPS_ERR_INVALID_ARG;
   const taps_problem* P = A->prob;
-  const int K = A->M + B->M, D = P->D;
+  const int Mx = std::max(A->M, B->M), K = 3 * Mx, D = P->D;
   const size_t KK = (size_t)K * K;
   double* buf = nullptr;
   TAPS_TRY(taps_alloc((void**)&buf, sizeof(double) * (D * KK + 2)));
   int st = TAPS_OK;
   for (int d = 0; d < D && st == TAPS_OK; ++d) {
-    pair_gram_kernel<<<(unsigned)KK, 128, 0, P->stream>>>(A->d_U[d], B->d_U[d], P->dims[d]->nf, A->M, K,
+    pair_gram_kernel<<<(unsigned)KK, 128, 0, P->stream>>>(A->d_U[d], B->d_U[d], P->dims[d]->nf, A->M, B->M, Mx,
                                                            buf + (size_t)d * KK);
     if (cudaGetLastError() != cudaSuccess) st = TAPS_ERR_CUDA;
   }
   double h[2] = {0.0, 0.0};
   if (st == TAPS_OK) {
-    pair_change_kernel<<<1, 256, 0, P->stream>>>(buf, D, K, A->M, buf + (size_t)D * KK);
+    pair_change_kernel<<<1, 1024, 0, P->stream>>>(buf, D, Mx, A->M, buf + (size_t)D * KK);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(h, buf + (size_t)D * KK, sizeof(h), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
         cudaStreamSynchronize(P->stream) != cudaSuccess)

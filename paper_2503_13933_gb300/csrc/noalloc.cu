@@ -7,8 +7,6 @@
 // allocation can cause.  This entry point computes the same values as
 // taps_eval_grid but takes its working memory from one fixed array in device global
 // memory that the library reserves when it is loaded.
-#include <mutex>
-
 #include "taps_internal.cuh"
 
 // Fixed scratch: the gathered factor rows, sum_d count[d] * M values of the output
@@ -16,27 +14,20 @@
 static __device__ __align__(256) unsigned char taps_noalloc_scratch[TAPS_NOALLOC_SCRATCH_BYTES];
 
 // Host code must not pass `taps_noalloc_scratch` itself to a kernel: in host code
-// that name is a host-side shadow, not a device address.  The device address is
-// looked up once per device (with that device current) and cached here.
-#define TAPS_NOALLOC_MAX_DEVICES 64
-static void* g_scratch_addr[TAPS_NOALLOC_MAX_DEVICES];
-static std::mutex g_scratch_mutex;
-
+// that name is a host-side shadow, not a device address.  The device address is looked
+// up on every call, with the calling device current: the lookup allocates nothing and
+// costs far less than the launches, and a cached address could go stale once the
+// device's primary context is reset (cudaDeviceReset) or the module is reloaded.  The
+// first lookup on a device may load the library's device code into the context, which
+// is why the first call on a device should come before any stream capture.
 static int noalloc_scratch_address(void** out) {
-  int dev = 0;
-  TAPS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= TAPS_NOALLOC_MAX_DEVICES) return TAPS_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, taps_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      taps_note_cuda_error(e, "cudaGetSymbolAddress(taps_noalloc_scratch)", __FILE__, __LINE__);
-      return TAPS_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, taps_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    taps_note_cuda_error(e, "cudaGetSymbolAddress(taps_noalloc_scratch)", __FILE__, __LINE__);
+    return TAPS_ERR_CUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return TAPS_OK;
 }
 
@@ -60,6 +51,7 @@ __global__ void noalloc_gather_kernel(const double* U, int nf, int off, int star
 // entries of the last dim: the rows' factor products are formed in shared memory,
 // then every output is one length-M dot product against a last-dim factor row.
 #define NR 8
+static_assert(NR * TAPS_MAX_M * sizeof(double) <= 48 * 1024, "noalloc eval rows exceed the default shared memory");
 template <typename T>
 __global__ void __launch_bounds__(256) noalloc_eval_kernel(const T* __restrict__ G, NoallocGrid g, int M,
                                                            long long rows, T* __restrict__ out) {
@@ -113,6 +105,10 @@ extern "C" int taps_eval_grid_noalloc(const taps_problem* P, const taps_factors*
     total *= count[d];
   }
   if ((size_t)goff * esz > (size_t)TAPS_NOALLOC_SCRATCH_BYTES) return TAPS_ERR_SCRATCH_LIMIT;
+  // the eval kernel's shared rows: at most NR * TAPS_MAX_M doubles (8 KB), inside the
+  // 48 KB every launch may use without an opt-in; checked before anything is launched
+  const size_t smem = (size_t)NR * M * esz;
+  if (M > TAPS_MAX_M || smem > 48u * 1024u) return TAPS_ERR_INVALID_ARG;
   void* scratch = nullptr;
   TAPS_TRY(noalloc_scratch_address(&scratch));
   cudaStream_t s = P->stream;
@@ -129,7 +125,6 @@ extern "C" int taps_eval_grid_noalloc(const taps_problem* P, const taps_factors*
   }
   long long rows = total / count[P->D - 1];
   unsigned blocks = (unsigned)((rows + NR - 1) / NR);
-  size_t smem = (size_t)NR * M * esz;
   if (out_dtype == TAPS_FP64)
     noalloc_eval_kernel<double><<<blocks, 256, smem, s>>>((const double*)scratch, g, M, rows, (double*)out_dev);
   else

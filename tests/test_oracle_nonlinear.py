@@ -120,3 +120,38 @@ def test_library_global_stage_terms_match_the_oracle_reading(D, M, law):
         assert [b for b, _ in g["weighted"][d]] == [b for b, _ in wops[d]]
         for (b, w), (b2, j) in zip(g["weighted"][d], wops[d]):
             assert np.array_equal(w, V[d][:, j])
+
+
+def _expanded_change(U_new, U_old):
+    """|a|^2 + |b|^2 - 2 <a, b> from Gram products (the form that cancels)."""
+    A = [np.concatenate([a, b], axis=1) for a, b in zip(U_new, U_old)]
+    G = np.ones((A[0].shape[1],) * 2)
+    for a in A:
+        G *= a.T @ a
+    m = U_new[0].shape[1]
+    c = np.concatenate([np.ones(m), -np.ones(U_old[0].shape[1])])
+    return math.sqrt(max(float(c @ G @ c), 0.0) / float(np.sum(G[:m, :m])))
+
+
+@pytest.mark.parametrize("rel", [1e-1, 1e-4, 1e-9])
+def test_cp_change_equals_explicit_tensor_difference(rel):
+    """The convergence check of Algorithm 2 against its plain definition: the norm of
+    the difference of the two full nodal tensors (3 dims of 7, 6 and 5 nodes; 4 modes
+    against 3, then a perturbation of relative size `rel` of the same 4 modes).  The
+    telescoped form keeps ~1e-6 relative accuracy down to changes of 1e-9, where the
+    expanded Gram form has lost every digit."""
+    rng = np.random.default_rng(17)
+    A = [rng.uniform(-1, 1, (n, 4)) for n in (7, 6, 5)]
+    B3 = [a[:, :3] + 0.3 * rng.uniform(-1, 1, (a.shape[0], 3)) for a in A]
+    a_full = O.cp_full(A)
+    got = O.cp_change(A, B3)
+    ref = np.linalg.norm(a_full - O.cp_full(B3)) / np.linalg.norm(a_full)
+    assert abs(got - ref) <= 1e-12 * ref
+    B = [a + rel * rng.uniform(-1, 1, a.shape) for a in A]
+    got = O.cp_change(A, B)
+    ref = np.linalg.norm(a_full - O.cp_full(B)) / np.linalg.norm(a_full)
+    # the explicit difference itself carries ~eps / rel relative rounding
+    assert abs(got - ref) <= max(1e-12, 1e-6 * 1e-9 / rel) * ref + 1e-15, (got, ref)
+    assert O.cp_change(A, A) == 0.0
+    if rel == 1e-9:   # the expanded form cannot resolve this change
+        assert abs(_expanded_change(A, B) - ref) > 0.5 * ref

@@ -9,6 +9,7 @@ This file is collected last so that a failure here cannot hide other results."""
 import numpy as np
 import pytest
 
+from oracle import taps_oracle as O
 from paper_2503_13933_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +50,35 @@ def test_noalloc_matches_eval_grid_twice(T, dtype):
         r, g = ref.double().cpu().numpy(), got.double().cpu().numpy()
         assert np.all(np.isfinite(g)), call
         assert np.max(np.abs(g - r)) <= tol * np.max(np.abs(r)), call
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_noalloc_matches_oracle_eval_grid(T, dtype):
+    """Against the FP64 oracle's reconstruction (Eq. 13 at the nodes: the factor
+    entries, zero at constrained nodes) on a strided slice with a ragged last dim,
+    two calls in a row with different factors and grids."""
+    desc = W.poisson_k(n_space=23, n_k=9, seed=2009)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    code = T.FP32 if dtype == "f32" else T.FP64
+    # FP32: the factors rounded to float and M = 7 products of D = 4 of them summed in
+    # float, a few units of 2^-24 times the magnitude of the terms
+    tol = 1e-5 if dtype == "f32" else 1e-13
+    for seed, (start, count, step) in ((43, ([0, 2, 1, 0], [23, 7, 11, 9], [1, 3, 2, 1])),
+                                       (44, ([22, 0, 5, 3], [1, 23, 6, 5], [1, 1, 3, 1]))):
+        U0 = W.random_factors(desc, 7, seed=seed)
+        U = P.factors(7)
+        U.set(U0)
+        n = int(np.prod(count))
+        got = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+        P.eval_grid_noalloc(U, start, count, step, got, dtype=code)
+        torch.cuda.synchronize()
+        ref = O.eval_grid(Po, U0, [range(a, a + b * c, c) for a, b, c in zip(start, count, step)])
+        g = got.double().cpu().numpy().reshape(ref.shape)
+        err = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+        print(f"noalloc vs oracle ({dtype}): max rel. diff {err:.2e}")
+        assert err <= tol, err
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(T):
