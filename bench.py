@@ -97,6 +97,25 @@ def allmax(v, world):
     return float(t.item())
 
 
+def partition(count, rank, world):
+    """Instance indices of a fixed set of `count` independent instances owned by `rank`:
+    round robin, so every rank gets a mix of the set's sizes and each index belongs to
+    exactly one rank."""
+    return list(range(rank, count, world))
+
+
+def gather_reports(reports, world):
+    """Per-instance reports (index, status, change) of every rank, gathered on the host
+    (no data-path collective: the instances are independent).  Returns the reports of
+    all ranks sorted by index on every rank."""
+    if world == 1:
+        return sorted(reports)
+    import torch.distributed as td
+    out = [None] * world
+    td.all_gather_object(out, list(reports))
+    return sorted(r for part in out for r in part)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -394,10 +413,14 @@ def run_ours(args, rank, world, local):
         # 50/50, 1..4 Gaussian sources): 10 fixed-M sweeps each, all instances as one CUDA
         # graph per sweep (solver chosen by the batch's tuner) vs one launch sequence per
         # instance in turn with the same kernels
-        descs, Ms = W.batch_instances(count=args.batch, seed=4000 + 1000 * rank, n_lo=32, n_hi=1024,
-                                      M_lo=4, M_hi=32)
+        # one fixed seeded set of args.batch instances, partitioned over the ranks (each
+        # rank sweeps its share; per-instance reports gathered on the host)
+        descs_all, Ms_all = W.batch_instances(count=args.batch, seed=4000, n_lo=32, n_hi=1024,
+                                              M_lo=4, M_hi=32)
+        mine = partition(args.batch, rank, world)
+        descs, Ms = [descs_all[i] for i in mine], [Ms_all[i] for i in mine]
         bp, bu, b0 = [], [], []
-        for i, (dsc, Mi) in enumerate(zip(descs, Ms)):
+        for i, dsc, Mi in zip(mine, descs, Ms):
             Pi = taps.Problem(dsc, stream=taps.ctypes.c_void_p(torch.cuda.Stream().cuda_stream))
             Ui = Pi.factors(Mi)
             U0i = W.random_factors(dsc, Mi, seed=100 + i)
@@ -428,8 +451,10 @@ def run_ours(args, rank, world, local):
                 ch, st = Bt.sweep(10, graphs=(mode == "graph"), statuses=True)
                 torch.cuda.synchronize()
                 ts.append(time.perf_counter() - t0)
-            times[mode] = min(ts)
+            times[mode] = allmax(min(ts), world)
             failed[mode] = int(np.sum(st != 0))
+            if mode == "graph":
+                reports = gather_reports([(i, int(a), float(b)) for i, a, b in zip(mine, st, ch)], world)
         chosen, trial = Bt.info()
         del Bt
         # per-instance launches with the other route too (the faster one per instance
@@ -442,7 +467,7 @@ def run_ours(args, rank, world, local):
         t0 = time.perf_counter()
         Bo.sweep(10, graphs=False, statuses=True)
         torch.cuda.synchronize()
-        per_other = time.perf_counter() - t0
+        per_other = allmax(time.perf_counter() - t0, world)
         del Bo
         names = {taps.SOLVER_FASTDIAG: "fastdiag", taps.SOLVER_MODEDIAG: "modediag"}
         per_best = min(times["per_instance"], per_other)
@@ -458,10 +483,14 @@ def run_ours(args, rank, world, local):
                        instances_per_s_per_instance_launches=args.batch / per_best,
                        speedup=times["per_instance"] / times["graph"],
                        speedup_vs_best_per_instance=per_best / times["graph"],
-                       numerically_singular=failed["graph"],
-                       note="fixed-M sweeps from random factors; instances whose factors become "
-                            "numerically rank deficient report TAPS_ERR_SINGULAR and still run "
-                            "every sweep in both launch styles")
+                       ranks=world, gathered=len(reports),
+                       completed=sum(1 for r in reports if r[1] == 0),
+                       completed_instances_per_s=sum(1 for r in reports if r[1] == 0) / times["graph"],
+                       numerically_singular=[r[0] for r in reports if r[1] != 0],
+                       note="one fixed seeded set partitioned over the ranks (times: max over ranks); "
+                            "fixed-M sweeps from random factors; instances whose factors become "
+                            "numerically rank deficient report TAPS_ERR_SINGULAR, still run every "
+                            "sweep, and are excluded from completed_instances_per_s")
 
     large = None
     if not args.no_large:

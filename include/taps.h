@@ -38,8 +38,8 @@ extern "C" {
 #define TAPS_MAX_P 3       /* reproducing order p <= 3 */
 #define TAPS_MAX_QUAD 12   /* Gauss points per element */
 #define TAPS_MAX_M 128     /* modes per factor */
-#define TAPS_MAX_TERMS 64     /* operator terms R */
-#define TAPS_MAX_SOURCES 1024 /* source terms R_f (slab chaining adds M per term and slab) */
+#define TAPS_MAX_TERMS 128    /* operator terms R */
+#define TAPS_MAX_SOURCES 4096 /* source terms R_f (slab chaining adds M per term and slab) */
 
 /* ---- status codes ---------------------------------------------------------- */
 #define TAPS_OK 0

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtaps.so")
 
 MAX_DIMS = 8
-MAX_TERMS = 64
-MAX_SOURCES = 1024
+MAX_TERMS = 128
+MAX_SOURCES = 4096
 OK, ERR_INVALID_ARG, ERR_SINGULAR, ERR_NONFINITE, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4
 ERR_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SCRATCH_LIMIT = -5, -6, -7, -8
 NOALLOC_SCRATCH_BYTES = 4 << 20

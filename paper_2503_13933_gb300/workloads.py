@@ -179,6 +179,55 @@ def lpbf_slab(n_xy=512, n_z=128, n_t=128, n_par=16, slab=0, n_slabs=8, svd_tol=1
                 sources=sources)
 
 
+def lpbf_large(n_xy=1536, n_z=1536, n_t=256, n_par=16, h_xy=10e-6, h_z=5e-6, T_slab=2e-3, k=22.0,
+               svd_tol=1e-8, track=1e-3, x_start=None, y0=None, s=2, a=20.0, p=2):
+    """The large space-parameter-time configuration: a moving Gaussian laser source over
+    a 3D block of n_xy x n_xy x n_z nodes at h = (10, 10, 5) um (15.35 x 15.35 x 7.675 mm
+    at full size, 3.6e9 spatial nodes), one time slab of n_t nodes over T_slab, and the
+    laser power P in [100, 400] W and spot radius r in [30, 80] um as parameter dims of
+    n_par nodes each; conductivity k fixed (22 W/m/K), Ti-6Al-4V rho c_p, absorptivity
+    0.25, penetration depth d_v = 50 um, scan speed 0.5 m/s along x through the centre
+    of the block (track of length `track`, centred), y0 = W/2.
+
+    u = T - T0 with a zero initial condition and u = 0 on the bottom and the four side
+    faces (the block is ~15 x the heat-affected zone wide: the far field stays at T0);
+    the top face is insulated (convection at h = 14.73 W/m^2/K carries ~1e-6 of the
+    laser's flux density and is left out).  The source, as in lpbf_slab, is one group
+    of CP terms per r node (Kronecker delta in r): the SVD of the nodal (x, t) matrix
+    exp(-2 (x - x0(t))^2 / r_j^2) truncated at svd_tol, times the y Gaussian, the
+    top-layer indicator, P and 2 eta / (pi r_j^2 d_v).  With the defaults R_f = 1301."""
+    Lxy, H = (n_xy - 1) * h_xy, (n_z - 1) * h_z
+    rho_cp, eta, d_v, V = 4270.0 * 745.0, 0.25, 50e-6, 0.5
+    x_start = 0.5 * Lxy - 0.5 * track if x_start is None else x_start
+    y0 = 0.5 * Lxy if y0 is None else y0
+    free = dict(dirichlet_lo=False, dirichlet_hi=False)
+    dims = [dim(n_xy, 0.0, Lxy, s=s, a=a, p=p), dim(n_xy, 0.0, Lxy, s=s, a=a, p=p),
+            dim(n_z, 0.0, H, s=s, a=a, p=p, dirichlet_lo=True, dirichlet_hi=False),
+            dim(n_t, 0.0, T_slab, kind=TIME, s=s, a=a, p=p, dirichlet_lo=True, dirichlet_hi=False),
+            dim(n_par, 100.0, 400.0, kind=PARAM, s=s, a=a, p=p, **free),
+            dim(n_par, 30e-6, 80e-6, kind=PARAM, s=s, a=a, p=p, **free)]
+    terms = [(rho_cp, ["M", "M", "M", "G", "M", "M"])]
+    for e in range(3):
+        terms.append((k, ["K" if d == e else "M" for d in range(3)] + ["M", "M", "M"]))
+    x = np.linspace(0.0, Lxy, n_xy)
+    z = np.linspace(0.0, H, n_z)
+    t = np.linspace(0.0, T_slab, n_t)
+    x0 = x_start + V * t
+    z_ind = (z >= H - d_v - 1e-12).astype(float)
+    r_nodes = np.linspace(30e-6, 80e-6, n_par)
+    sources = []
+    for j, rj in enumerate(r_nodes):
+        E = np.exp(-2.0 * (x[:, None] - x0[None, :]) ** 2 / rj ** 2)
+        yj = np.exp(-2.0 * (x - y0) ** 2 / rj ** 2)
+        ej = np.zeros(n_par)
+        ej[j] = 2.0 * eta / (np.pi * rj ** 2 * d_v)
+        for sv, ux, vt in _svd_modes(E, svd_tol):
+            sources.append((1.0, [("nodal", sv * ux), ("nodal", yj), ("nodal", z_ind), ("nodal", vt),
+                                  ("poly", (0.0, 1.0)), ("nodal", ej)]))
+    return dict(name=f"lpbf_large_{n_xy}x{n_xy}x{n_z}_t{n_t}_P{n_par}_r{n_par}", dims=dims, terms=terms,
+                sources=sources, params=dict(k=k, x_start=x_start, y0=y0, V=V))
+
+
 def batch_instances(count=256, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32):
     """Independent instances: D in {3..6}, n_d uniform in [n_lo, n_hi], a mode count
     in [M_lo, M_hi], Poisson or transient (last dim time) 50/50, 1..4 separable

@@ -50,24 +50,30 @@ def test_full_size_solve_reaches_target_and_residual_matches_oracle(T, full):
 
 
 def test_full_size_sweep_matches_oracle(T, full):
-    """One fast-diagonalisation sweep on the GPU and in the oracle from the same
-    converged factors: same normalised factors."""
+    """One fast-diagonalisation sweep on the GPU and in the oracle from the same factors,
+    whole fields compared through the telescoped CP difference (no grid is formed).
+
+    From the seeded random start the reduced systems are well conditioned and the bar is
+    the FP64 one: field and factors within 1e-10.  From the converged 30 modes they are
+    not: the modes are nearly dependent, and the oracle's own two FP64 solvers (fast
+    diagonalisation, banded elimination) give fields 3.9e-7 apart (factors 1e-4) from
+    those factors; the GPU must stay within 2e-6 of the oracle there, about five times
+    that spread."""
     desc, P, U, _ = full
     Po = O.problem_from_description(desc)
-    U0 = U.get()
-    V = P.factors(30)
-    V.set(U0)
-    P.sweep(V, 1, solver=T.SOLVER_FASTDIAG)
-    Uo, _ = O.sweep(Po, [u.copy() for u in U0], solver="fastdiag")
-    Ub, _ = O.sweep(Po, [u.copy() for u in U0], solver="banded")
-    got = V.get()
-    for d in range(Po.D):
-        # converged M = 30 modes make the reduced systems ill-conditioned; the spread
-        # between the oracle's two FP64 solvers (fast diagonalisation, banded LU)
-        # measures kappa * eps of this case and sets the bound
-        spread = np.linalg.norm(Ub[d] - Uo[d]) / np.linalg.norm(Uo[d])
-        err = np.linalg.norm(got[d] - Uo[d]) / np.linalg.norm(Uo[d])
-        assert err < max(1e-10, 10 * spread), (d, err, spread)
+    U_rand = O.init_factors(Po, 30, "random", 2000)
+    for name, U0, tol in (("random start", U_rand, 1e-10), ("converged", U.get(), 2e-6)):
+        V = P.factors(30)
+        V.set(U0)
+        P.sweep(V, 1, solver=T.SOLVER_FASTDIAG)
+        Uo, _ = O.sweep(Po, [u.copy() for u in U0], solver="fastdiag")
+        got = V.get()
+        field = O.cp_change(Uo, got)
+        fac = max(np.linalg.norm(g - o) / np.linalg.norm(o) for g, o in zip(got, Uo))
+        print(f"{name}: field rel. diff {field:.2e}, factors {fac:.2e} (bound {tol:.0e})")
+        assert field <= tol, (name, field)
+        if name == "random start":
+            assert fac <= 1e-10, fac
 
 
 def test_full_size_reconstruction_sampled(T, full):

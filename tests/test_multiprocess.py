@@ -1,8 +1,9 @@
 """The bench's multi-rank path (one process per GPU, launched by torch.distributed.run)
 exercised on the CPU with the gloo backend and two ranks: the rendezvous, the barrier,
 the max over ranks of the timed values, the per-rank workload seeds (independent
-instances, weak scaling, no data-path collective) and the reference arm's rank-0-only
-output."""
+instances, weak scaling, no data-path collective), the partition of a fixed set of batched
+instances over the ranks with the host gather of their reports, and the reference arm's
+rank-0-only output."""
 import contextlib
 import io
 import os
@@ -36,10 +37,14 @@ def _rank_main(rank, world, port, out_dir):
     bench.barrier(w)
     # every rank reports the max over ranks of its own timing
     got = bench.allmax(1.5 + rank, w)
-    # per-rank workloads: the single-instance seed and the batched instances differ by rank
+    # per-rank workloads: the single-instance seed differs by rank (replicas)
     seed = bench.WORKLOAD["seed"] + rank
     desc = W.poisson_k(8, 4, seed=seed)
-    descs, Ms = W.batch_instances(count=3, seed=4000 + 1000 * rank, n_lo=8, n_hi=12, M_lo=2, M_hi=3)
+    # a fixed set of batched instances partitioned over the ranks; per-instance reports
+    # (index, status, change) gathered on the host
+    count = 11
+    mine = bench.partition(count, rank, w)
+    gathered = bench.gather_reports([(i, -2 if i == 7 else 0, 0.1 * i) for i in mine], w)
     # the reference arm: ranks other than 0 return at once without output
     buf = io.StringIO()
     if rank != 0:
@@ -47,7 +52,8 @@ def _rank_main(rank, world, port, out_dir):
             bench.run_reference(None, rank, w)
     with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
         f.write(repr(dict(max=got, seed=seed, src=desc["sources"][0][0],
-                          batch=[len(d["dims"]) for d in descs] + Ms, ref_out=buf.getvalue())))
+                          ref_out=buf.getvalue(),
+                          mine=mine, gathered=gathered)))
     bench.barrier(w)
     dist.destroy_process_group()
 
@@ -58,5 +64,13 @@ def test_two_gloo_ranks(tmp_path):
     res = [eval(open(tmp_path / f"rank{r}.txt").read()) for r in range(2)]
     assert res[0]["max"] == res[1]["max"] == 2.5
     assert res[0]["seed"] != res[1]["seed"]
-    assert res[0]["src"] != res[1]["src"] or res[0]["batch"] != res[1]["batch"]
+    assert res[0]["src"] != res[1]["src"]
     assert res[1]["ref_out"] == ""
+    # the partition covers the fixed set exactly once; every rank holds the complete,
+    # ordered gather of all ranks' reports
+    assert sorted(res[0]["mine"] + res[1]["mine"]) == list(range(11))
+    assert not set(res[0]["mine"]) & set(res[1]["mine"])
+    for r in res:
+        assert [g[0] for g in r["gathered"]] == list(range(11))
+        assert [g[1] for g in r["gathered"]] == [-2 if i == 7 else 0 for i in range(11)]
+        assert r["gathered"] == res[0]["gathered"]
