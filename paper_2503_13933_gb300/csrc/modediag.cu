@@ -293,6 +293,274 @@ __global__ void __launch_bounds__(MD_THREADS) md_eig_kernel(const double* __rest
   if (tid == 0) *wM = failed ? 0 : M;
 }
 
+// The same generalised eigenproblem for M in (32, TAPS_MAX_M]: the M x M matrices no
+// longer fit in shared memory together, so only S (the matrix the Jacobi rounds rotate,
+// Np x (Np + 1) with Np = M rounded up to even) stays in shared memory; L, the rotated
+// basis V (column-major, so that a round's row-pair updates are coalesced), T and the
+// previous basis P live in a global workspace gw of 4 M^2 doubles (L2-resident).  The
+// steps and their arithmetic are those of md_eig_kernel; W^T c_r is left to
+// md_cw_kernel, spread over many CTAs.
+#define MDB_THREADS 512
+__global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* __restrict__ CX,
+                                                                 const double* __restrict__ CY, int M,
+                                                                 double* __restrict__ Wio, int* __restrict__ wM,
+                                                                 double* __restrict__ lam, double* __restrict__ gw,
+                                                                 int* status) {
+  extern __shared__ __align__(16) double Ssh[];
+  __shared__ double linv[TAPS_MAX_M];
+  __shared__ double rc[TAPS_MAX_M / 2], rs[TAPS_MAX_M / 2];
+  __shared__ int rp[TAPS_MAX_M / 2], rq[TAPS_MAX_M / 2];
+  __shared__ int rotated, failed;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int Np = M + (M & 1), ld = Np + 1;
+  const size_t MM = (size_t)M * M;
+  double* L = gw;            // row-major [M][M], lower triangle used
+  double* Vt = gw + MM;      // column-major basis: Vt[c * M + r] = V[r][c]
+  double* T = gw + 2 * MM;   // row-major temporary
+  double* Pw = gw + 3 * MM;  // row-major previous basis (identity when cold)
+#define SB(i, j) Ssh[(size_t)(i) * ld + (j)]
+  const bool warm = (*wM == M);
+  if (tid == 0) failed = 0;
+  for (int idx = tid; idx < M * M; idx += nt) {
+    const int i = idx / M, j = idx % M;
+    L[idx] = 0.5 * (CX[i * M + j] + CX[j * M + i]);
+    SB(i, j) = CY ? 0.5 * (CY[i * M + j] + CY[j * M + i]) : 0.0;
+    Pw[idx] = warm ? Wio[idx] : (i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (warm) {   // L <- P^T C_X P, S <- P^T C_Y P (through T)
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx % M;
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) s += L[i * M + k] * Pw[k * M + j];
+      T[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx % M;
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) s += Pw[k * M + i] * T[k * M + j];
+      L[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx % M;
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) s += SB(i, k) * Pw[k * M + j];
+      T[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx % M;
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) s += Pw[k * M + i] * T[k * M + j];
+      SB(i, j) = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx % M;
+      if (i < j) {
+        const double a = 0.5 * (L[i * M + j] + L[j * M + i]), b = 0.5 * (SB(i, j) + SB(j, i));
+        L[i * M + j] = a;
+        L[j * M + i] = a;
+        SB(i, j) = b;
+        SB(j, i) = b;
+      }
+    }
+    __syncthreads();
+  }
+  // Cholesky with the same pivot floor as md_eig_kernel
+  double dmax = 0.0;
+  for (int k = 0; k < M; ++k) dmax = fmax(dmax, fabs(L[k * M + k]));
+  const double floor_piv = 64.0 * 1.1102230246251565e-16 * dmax;
+  for (int k = 0; k < M; ++k) {
+    if (tid == 0) {
+      double piv = L[k * M + k];
+      if (!isfinite(piv) || !(dmax > 0.0) || !isfinite(dmax) || piv < -1e-8 * dmax) {
+        taps_flag(status, TAPS_DEV_SINGULAR);
+        failed = 1;
+        piv = 1.0;
+      } else if (piv < floor_piv) {
+        piv = floor_piv;
+      }
+      const double r = sqrt(piv);
+      L[k * M + k] = r;
+      linv[k] = taps_rcp(r);
+    }
+    __syncthreads();
+    const double il = linv[k];
+    for (int i = k + 1 + tid; i < M; i += nt) L[i * M + k] *= il;
+    __syncthreads();
+    const int w = M - k - 1;
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+      if (j <= i) L[i * M + j] -= L[i * M + k] * L[j * M + k];
+    }
+    __syncthreads();
+  }
+  // X = L^-1 C_Y into T (thread per column), then S = L^-1 X^T (thread per column)
+  if (tid < M) {
+    const int col = tid;
+    for (int i = 0; i < M; ++i) {
+      double s = SB(i, col);
+      for (int j = 0; j < i; ++j) s -= L[i * M + j] * T[j * M + col];
+      T[i * M + col] = s * linv[i];
+    }
+  }
+  __syncthreads();
+  if (tid < M) {
+    const int col = tid;
+    for (int i = 0; i < M; ++i) {
+      double s = T[col * M + i];
+      for (int j = 0; j < i; ++j) s -= L[i * M + j] * SB(j, col);
+      SB(i, col) = s * linv[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < M * M; idx += nt) {
+    const int i = idx / M, j = idx % M;
+    if (i < j) {
+      const double a = 0.5 * (SB(i, j) + SB(j, i));
+      SB(i, j) = a;
+      SB(j, i) = a;
+    }
+    Vt[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int N = Np, half = N / 2;
+  if (N > M) {
+    for (int j = tid; j < N; j += nt) {
+      SB(M, j) = 0.0;
+      SB(j, M) = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      if (tid < half) {
+        int a, b;
+        if (tid == 0) {
+          a = r;
+          b = N - 1;
+        } else {
+          a = (r + tid) % (N - 1);
+          b = (r - tid + N - 1) % (N - 1);
+        }
+        const int p = min(a, b), q = max(a, b);
+        double cs = 1.0, sn = 0.0;
+        if (q < M) {
+          const double apq = SB(p, q), app = SB(p, p), aqq = SB(q, q);
+          if (fabs(apq) > 1.1102230246251565e-16 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+            const double th = (aqq - app) * taps_rcp(2.0 * apq);
+            double t;
+            if (fabs(th) > 1e150) {
+              t = 0.5 * taps_rcp(th);
+            } else {
+              t = taps_rcp(fabs(th) + sqrt(th * th + 1.0));
+              if (th < 0.0) t = -t;
+            }
+            cs = taps_rcp(sqrt(t * t + 1.0));
+            sn = t * cs;
+            rotated = 1;
+          }
+        }
+        rc[tid] = cs;
+        rs[tid] = sn;
+        rp[tid] = p;
+        rq[tid] = q;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * half; idx += nt) {
+        const int k = idx / half, l = idx % half;
+        if (k > l) continue;
+        const double sk = rs[k], sl = rs[l];
+        if (sk == 0.0 && sl == 0.0) continue;
+        const double ck = rc[k], cl = rc[l];
+        const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
+        const double b00 = SB(pk, pl), b01 = SB(pk, ql), b10 = SB(qk, pl), b11 = SB(qk, ql);
+        const double t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+        const double t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+        const double n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+        const double n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+        if (k == l) {
+          SB(pk, pk) = n00;
+          SB(qk, qk) = n11;
+          SB(pk, qk) = 0.0;
+          SB(qk, pk) = 0.0;
+        } else {
+          SB(pk, pl) = n00;
+          SB(pk, ql) = n01;
+          SB(qk, pl) = n10;
+          SB(qk, ql) = n11;
+          SB(pl, pk) = n00;
+          SB(ql, pk) = n01;
+          SB(pl, qk) = n10;
+          SB(ql, qk) = n11;
+        }
+      }
+      // V <- V J: columns p_l, q_l of V are rows p_l, q_l of Vt (coalesced over i)
+      for (int idx = tid; idx < half * M; idx += nt) {
+        const int l = idx / M, i = idx % M;
+        const double sl = rs[l];
+        if (sl != 0.0) {
+          const double cl = rc[l];
+          const int pl = rp[l], ql = rq[l];
+          if (ql < M) {
+            const double vp = Vt[(size_t)pl * M + i], vq = Vt[(size_t)ql * M + i];
+            Vt[(size_t)pl * M + i] = cl * vp - sl * vq;
+            Vt[(size_t)ql * M + i] = sl * vp + cl * vq;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // W_inner = L^-T Q in place of V (thread per column, bottom row first)
+  if (tid < M) {
+    const int col = tid;
+    double* v = Vt + (size_t)col * M;
+    for (int i = M - 1; i >= 0; --i) {
+      double s = v[i];
+      for (int j = i + 1; j < M; ++j) s -= L[j * M + i] * v[j];
+      v[i] = s * linv[i];
+    }
+  }
+  __syncthreads();
+  // W = P W_inner
+  bool finite = true;
+  for (int idx = tid; idx < M * M; idx += nt) {
+    const int i = idx / M, j = idx % M;
+    double s = 0.0;
+    for (int k = 0; k < M; ++k) s += Pw[i * M + k] * Vt[(size_t)j * M + k];
+    finite &= isfinite(s);
+    T[idx] = s;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < M * M; idx += nt) Wio[idx] = T[idx];
+  if (!finite) failed = 1;
+  for (int j = tid; j < M; j += nt) lam[j] = SB(j, j);
+  __syncthreads();
+  if (tid == 0) *wM = failed ? 0 : M;
+#undef SB
+}
+
+// cw[r][j] = sum_m c[r][m] W[m][j] (the right-hand side's mode-side coefficients), one
+// thread per entry over many CTAs.
+__global__ void md_cw_kernel(const double* __restrict__ c, const double* __restrict__ Wm, int Rf, int M,
+                             double* __restrict__ cw) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Rf * M) return;
+  const int r = (int)(idx / M), j = (int)(idx % M);
+  const double* cr = c + (size_t)r * M;
+  double s = 0.0;
+  for (int m = 0; m < M; ++m) s += cr[m] * Wm[(size_t)m * M + j];
+  cw[idx] = s;
+}
+
 // Padding rows below the matrix (identity rows, zero right-hand side) let the
 // elimination run whole unrolled groups and read ahead without bounds tests.
 #define MD_PAD 24
@@ -338,7 +606,7 @@ __global__ void __launch_bounds__(32) md_band_kernel(const double* __restrict__ 
                                                      int* status) {
   constexpr int W2 = 2 * HB + 1, RW = W2 + 1, NS = HB + 1;
   constexpr int U = (NS % 2 == 0) ? NS : 2 * NS;
-  const int j = threadIdx.x;
+  const int j = blockIdx.x * 32 + threadIdx.x;   // system index (one warp per 32 systems)
   if (j >= M) return;
   const int nsteps = ((n + U - 1) / U) * U;   // <= n + U - 1; rows read <= nsteps + HB + 2
   double A[NS][W2];
@@ -447,7 +715,7 @@ static bool md_op_mass_like(int op) { return op == TAPS_OP_M || op == TAPS_OP_W;
 
 int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY) {
   const int nops = P->tt.nops[d];
-  if (nops < 1 || nops > 2 || M < 1 || M > 32) return 0;
+  if (nops < 1 || nops > 2 || M < 1 || M > TAPS_MAX_M) return 0;
   if (P->has_weighted) return 0;   // symmetry of weighted operators is not tracked
   const int hb = P->dims[d]->hb;
   if (hb < 1 || hb > MD_MAX_HB) return 0;
@@ -489,7 +757,8 @@ int taps_dim_route(const taps_problem* P, int d, int solver, int M) {
 // rows [nf_max + MD_PAD][2 MD_MAX_HB + 2][M].  The caller zeroes it (no valid basis).
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf) {
   return (size_t)TAPS_MAX_DIMS * M * M + TAPS_MAX_DIMS + M + (size_t)Rf * M + (size_t)nf_max * M +
-         (size_t)(nf_max + MD_PAD) * (MD_MAX_HB + 1) * M + (size_t)(nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M;
+         (size_t)(nf_max + MD_PAD) * (MD_MAX_HB + 1) * M + (size_t)(nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M +
+         (M > 32 ? (size_t)4 * M * M : 0);
 }
 
 // Forgets every dim's stored basis (the next solves start cold).  Called when a sweep
@@ -501,13 +770,24 @@ int taps_md_reset(taps_problem* P) {
   return TAPS_OK;
 }
 
+// Shared-memory opt-in of the large-M eigen-solve (S of up to TAPS_MAX_M rows, padded);
+// made with the problem's device current when its first problem is created.
+int taps_md_setup(int maxsm) {
+  const int need = (int)(sizeof(double) * (TAPS_MAX_M + 1) * (TAPS_MAX_M + 2));
+  cudaFuncAttributes fa;
+  TAPS_CUDA(cudaFuncGetAttributes(&fa, md_eig_big_kernel));
+  TAPS_CUDA(cudaFuncSetAttribute(md_eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 std::min(need, maxsm - (int)fa.sharedSizeBytes)));
+  return TAPS_OK;
+}
+
 template <int HB>
 static cudaError_t md_band_launch(const double* bx, const double* by, const double* lam, const double* q,
                                   const double* cw, int Rf, int n, int M, double* Ab, double* scratch, double* Z,
                                   int* status, cudaStream_t s) {
   const long long tot = (long long)(n + MD_PAD) * (2 * HB + 2) * M;
   md_prep_kernel<HB><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(bx, by, lam, q, cw, Rf, n, M, Ab);
-  md_band_kernel<HB><<<1, 32, 0, s>>>(Ab, n, M, scratch, Z, status);
+  md_band_kernel<HB><<<(unsigned)((M + 31) / 32), 32, 0, s>>>(Ab, n, M, scratch, Z, status);
   return cudaGetLastError();
 }
 
@@ -533,8 +813,20 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
   const double* bx = dm->d_band + (size_t)P->ops[d][sx] * bsz;
   const double* by = sy >= 0 ? dm->d_band + (size_t)P->ops[d][sy] * bsz : bx;   // lam = 0 without Y
   int tk = prof_begin(P, TAPS_PROF_MODEDIAG);
-  md_eig_kernel<<<1, MD_THREADS, 0, s>>>(P->d_C + (size_t)sx * MM, sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr,
-                                          P->d_c, Rf, M, Wm, wM, lam, cw, P->d_status);
+  if (M <= 32) {
+    md_eig_kernel<<<1, MD_THREADS, 0, s>>>(P->d_C + (size_t)sx * MM, sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr,
+                                            P->d_c, Rf, M, Wm, wM, lam, cw, P->d_status);
+  } else {
+    // the eigen-solve's workspace follows the band rows (sized for M > 32 only)
+    double* gw = Ab + (size_t)(P->nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M;
+    const int Np = M + (M & 1);
+    const size_t smem = sizeof(double) * (size_t)Np * (Np + 1);   // opted in by taps_md_setup
+    md_eig_big_kernel<<<1, MDB_THREADS, smem, s>>>(P->d_C + (size_t)sx * MM,
+                                                   sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm, wM, lam,
+                                                   gw, P->d_status);
+    const long long rm = (long long)Rf * M;
+    md_cw_kernel<<<(unsigned)((rm + 255) / 256), 256, 0, s>>>(P->d_c, Wm, Rf, M, cw);
+  }
   cudaError_t ce = cudaSuccess;
   switch (hb) {
     case 1: ce = md_band_launch<1>(bx, by, lam, P->d_q[d], cw, Rf, n, M, Ab, scratch, Z, P->d_status, s); break;

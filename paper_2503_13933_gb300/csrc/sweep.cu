@@ -719,6 +719,7 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
   TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, false>, maxsm));
   TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, true>, maxsm));
   TAPS_TRY(residual_setup(maxsm));
+  TAPS_TRY(taps_md_setup(maxsm));
   int bps = 0;
   size_t smem_max = sizeof(double) * TAPS_MAX_M * (TAPS_MAX_M + 1);
   TAPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, block_lu_kernel, 256, smem_max));

@@ -366,6 +366,7 @@ struct FdPending {
 // the mass-like operator X and the other Y), scratch size, and the solve.
 int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY);
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf);
+int taps_md_setup(int maxsm);
 int taps_md_solve(taps_problem* P, taps_factors* U, int d);
 int taps_md_reset(taps_problem* P);
 // Node-side diagonalisation with convection-face corrections (fdbound.cu).

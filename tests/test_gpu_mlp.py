@@ -94,30 +94,60 @@ def test_factors_from_profiles(T):
 
 
 def test_warm_start_gain_over_random_init(T):
-    """What the trained network gains over the method without it.  Trained on the
-    converged factors of 8 seeded space-parameter instances (48^3 x 16, M = 24), it
-    initialises 3 held-out instances.  After the first sweep the warm start's Eq. 42
-    residual is more than 3x below the random start's, and at no later sweep of the
-    first three is it more than 2x above it.  (From the second sweep on both starts
-    are in the slow, oscillating phase of the subspace iteration, where the order of
-    two nearby residuals is set by rounding; sweeps-to-target are reported by the
-    benchmark, not asserted here.)"""
+    """What the trained network gains over the method without it, on the space-parameter
+    workload at full size (256^3 x 32, M = 30).  Trained on the converged factors of 16
+    seeded instances (2001-2016), it initialises 8 held-out instances (2017-2024), each
+    also solved from the seeded random start:
+      - first sweep: the Eq. 42 residual is >= 10x lower on average and >= 3x lower on
+        every instance;
+      - after two sweeps the full residual rho_full (the accuracy of the field) is lower on
+        every instance, >= 2x on average;
+      - sweeps to rho_42 <= 1e-6 (60 at most): summed over the instances where both
+        starts reach the target, the warm start needs no more sweeps than the random one.
+    The gain is confined to the early sweeps: from the third sweep on both starts are in
+    the slow final approach of the ill-conditioned M = 30 iteration (the sweep counts to
+    1e-6 then move by +-1 with rounding-level changes), so the sweep counts are a sum
+    over instances, not a per-instance bound.  All numbers are printed."""
     from paper_2503_13933_gb300 import warmstart as WS
-    M = 24
-    X, Tt, _ = WS.training_set(range(2101, 2109), n_space=48, n_k=16, M=M, res_tol=1e-8, max_sweeps=40)
+    M = 30
+    X, Tt, _ = WS.training_set(range(2001, 2017), n_space=256, n_k=32, M=M, res_tol=1e-8, max_sweeps=80)
     ws = WS.WarmStart(M=M)
-    ws.fit(X, Tt, steps=3000, lr=5e-4)
-    for sd in (2200, 2201, 2202):
-        desc = W.poisson_k(48, 16, seed=sd)
+    ws.fit(X, Tt, steps=6000, lr=5e-4)
+    rows = []
+    for sd in range(2017, 2025):
+        desc = W.poisson_k(256, 32, seed=sd)
         P = T.Problem(desc)
-        Ur, Um = P.factors(M), P.factors(M)
-        rr = P.solve(Ur, M0=M, M_max=M, res_tol=-1.0, max_sweeps=3, init=T.INIT_RANDOM, seed=sd,
-                     als_tol=0.0, solver=T.SOLVER_FASTDIAG)
-        ws.init_factors(P, Um, desc)
-        rm = P.solve(Um, M_max=M, res_tol=-1.0, max_sweeps=3, init=T.INIT_GIVEN, als_tol=0.0,
-                     solver=T.SOLVER_FASTDIAG)
-        hr = [h[2] for h in rr["history"]]
-        hm = [h[2] for h in rm["history"]]
-        print(f"seed {sd}: residual per sweep random {hr} vs warm {hm}")
-        assert hm[0] * 3.0 < hr[0]
-        assert all(a <= 2.0 * b for a, b in zip(hm, hr)), (hm, hr)
+        out = {}
+        for kind in ("random", "warm"):
+            U = P.factors(M)
+            if kind == "random":
+                r = P.solve(U, M0=M, M_max=M, res_tol=1e-6, max_sweeps=60, init=T.INIT_RANDOM, seed=sd,
+                            als_tol=0.0, solver=T.SOLVER_FASTDIAG)
+            else:
+                ws.init_factors(P, U, desc)
+                r = P.solve(U, M_max=M, res_tol=1e-6, max_sweeps=60, init=T.INIT_GIVEN, als_tol=0.0,
+                            solver=T.SOLVER_FASTDIAG)
+            V = P.factors(M)
+            if kind == "random":
+                P.solve(V, M0=M, M_max=M, res_tol=-1.0, max_sweeps=2, init=T.INIT_RANDOM, seed=sd, als_tol=0.0,
+                        solver=T.SOLVER_FASTDIAG)
+            else:
+                ws.init_factors(P, V, desc)
+                P.sweep(V, 2, solver=T.SOLVER_FASTDIAG)
+            out[kind] = dict(sweeps=r["sweeps"], converged=r["converged"], rho1=r["history"][0][2],
+                             rho_full2=P.residual(V, T.RES_FULL))
+        rows.append(out)
+        print(f"seed {sd}: sweeps to 1e-6 random {out['random']['sweeps']} warm {out['warm']['sweeps']}; "
+              f"first-sweep rho_42 {out['random']['rho1']:.2e} / {out['warm']['rho1']:.2e}; "
+              f"rho_full after 2 sweeps {out['random']['rho_full2']:.2e} / {out['warm']['rho_full2']:.2e}")
+    g1 = [o["random"]["rho1"] / o["warm"]["rho1"] for o in rows]
+    g2 = [o["random"]["rho_full2"] / o["warm"]["rho_full2"] for o in rows]
+    both = [o for o in rows if o["random"]["converged"] and o["warm"]["converged"]]
+    sr = [o["random"]["sweeps"] for o in both]
+    sw = [o["warm"]["sweeps"] for o in both]
+    print(f"first-sweep gain mean {np.mean(g1):.1f}x worst {min(g1):.1f}x; rho_full(2) gain mean "
+          f"{np.mean(g2):.1f}x worst {min(g2):.1f}x; sweeps to 1e-6 on {len(both)} instances: random "
+          f"mean {np.mean(sr):.1f} worst {max(sr)}, warm mean {np.mean(sw):.1f} worst {max(sw)}")
+    assert np.mean(g1) >= 10.0 and min(g1) >= 3.0, g1
+    assert np.mean(g2) >= 2.0 and min(g2) > 1.0, g2
+    assert len(both) >= 4 and sum(sw) <= sum(sr), (sr, sw)
