@@ -324,6 +324,7 @@ def build_problem(dims, terms, sources, weighted=None):
     weighted[d]: list of (base 'K'|'M'|'G', all-node weights), op OP_WEIGHTED + j."""
     tabs = [shape_tables(dm) for dm in dims]
     ops = [assemble_free(dm, tb) for dm, tb in zip(dims, tabs)]
+    full_mass = {}     # all-node mass matrix of a dim, assembled once for its nodal sources
     for d, wl in enumerate(weighted or []):
         for j, (base, w) in enumerate(wl or []):
             f = dims[d].free
@@ -333,7 +334,10 @@ def build_problem(dims, terms, sources, weighted=None):
         qs = []
         for d, (dm, tb, (kind, par)) in enumerate(zip(dims, tabs, facs)):
             if kind == "nodal":
-                qs.append(project_source(dm, kind, None, nodal=par, tab=tb))
+                # q = M_full g restricted to the free nodes (project_source's 'nodal' case)
+                if d not in full_mass:
+                    full_mass[d] = assemble_full(dm, tb)[OP_M]
+                qs.append((full_mass[d] @ np.asarray(par, dtype=float))[dm.free])
             elif kind == "opvec":
                 # the projection of a field already in the C-HiDeNN space: q = Op v
                 qs.append(ops[d][OP_BY_NAME[par[0]]] @ np.asarray(par[1], dtype=float))

@@ -179,15 +179,15 @@ def lpbf_slab(n_xy=512, n_z=128, n_t=128, n_par=16, slab=0, n_slabs=8, svd_tol=1
                 sources=sources)
 
 
-def lpbf_large(n_xy=1536, n_z=1536, n_t=256, n_par=16, h_xy=10e-6, h_z=5e-6, T_slab=2e-3, k=22.0,
-               svd_tol=1e-8, track=1e-3, x_start=None, y0=None, s=2, a=20.0, p=2):
+def lpbf_large(n_xy=1536, n_z=1536, n_t=256, n_par=16, h_xy=10e-6, h_z=5e-6, T_slab=0.2e-3, k=22.0,
+               svd_tol=1e-8, x_start=None, y0=None, s=2, a=20.0, p=2):
     """The large space-parameter-time configuration: a moving Gaussian laser source over
     a 3D block of n_xy x n_xy x n_z nodes at h = (10, 10, 5) um (15.35 x 15.35 x 7.675 mm
     at full size, 3.6e9 spatial nodes), one time slab of n_t nodes over T_slab, and the
     laser power P in [100, 400] W and spot radius r in [30, 80] um as parameter dims of
     n_par nodes each; conductivity k fixed (22 W/m/K), Ti-6Al-4V rho c_p, absorptivity
-    0.25, penetration depth d_v = 50 um, scan speed 0.5 m/s along x through the centre
-    of the block (track of length `track`, centred), y0 = W/2.
+    0.25, penetration depth d_v = 50 um, scan speed 0.5 m/s along x, the slab's path
+    (V T_slab long: 0.1 mm at the default 0.2 ms) centred in the block, y0 = W/2.
 
     u = T - T0 with a zero initial condition and u = 0 on the bottom and the four side
     faces (the block is ~15 x the heat-affected zone wide: the far field stays at T0);
@@ -195,10 +195,11 @@ def lpbf_large(n_xy=1536, n_z=1536, n_t=256, n_par=16, h_xy=10e-6, h_z=5e-6, T_s
     laser's flux density and is left out).  The source, as in lpbf_slab, is one group
     of CP terms per r node (Kronecker delta in r): the SVD of the nodal (x, t) matrix
     exp(-2 (x - x0(t))^2 / r_j^2) truncated at svd_tol, times the y Gaussian, the
-    top-layer indicator, P and 2 eta / (pi r_j^2 d_v).  With the defaults R_f = 1301."""
+    top-layer indicator, P and 2 eta / (pi r_j^2 d_v).  With the defaults R_f = 239
+    (1301 for a 2 ms slab, whose 1 mm path the modes of one slab cannot follow)."""
     Lxy, H = (n_xy - 1) * h_xy, (n_z - 1) * h_z
     rho_cp, eta, d_v, V = 4270.0 * 745.0, 0.25, 50e-6, 0.5
-    x_start = 0.5 * Lxy - 0.5 * track if x_start is None else x_start
+    x_start = 0.5 * Lxy - 0.5 * V * T_slab if x_start is None else x_start
     y0 = 0.5 * Lxy if y0 is None else y0
     free = dict(dirichlet_lo=False, dirichlet_hi=False)
     dims = [dim(n_xy, 0.0, Lxy, s=s, a=a, p=p), dim(n_xy, 0.0, Lxy, s=s, a=a, p=p),
@@ -225,7 +226,7 @@ def lpbf_large(n_xy=1536, n_z=1536, n_t=256, n_par=16, h_xy=10e-6, h_z=5e-6, T_s
             sources.append((1.0, [("nodal", sv * ux), ("nodal", yj), ("nodal", z_ind), ("nodal", vt),
                                   ("poly", (0.0, 1.0)), ("nodal", ej)]))
     return dict(name=f"lpbf_large_{n_xy}x{n_xy}x{n_z}_t{n_t}_P{n_par}_r{n_par}", dims=dims, terms=terms,
-                sources=sources, params=dict(k=k, x_start=x_start, y0=y0, V=V))
+                sources=sources, params=dict(k=k, x_start=x_start, y0=y0, V=V, T_slab=T_slab))
 
 
 def batch_instances(count=256, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32):
