@@ -264,6 +264,17 @@ int taps_problem_set_weighted_ops(taps_problem* prob, int dim, int count, const 
 int taps_problem_copy_op(const taps_problem* prob, int dim, int op, double* host_out);
 /* Copy q_{r,d} (n_free(d) FP64 values) to host memory. */
 int taps_problem_copy_source(const taps_problem* prob, int r, int d, double* host_out);
+/* Recompute every dim's Gram matrices (Eq. 34) from the factors U at `precision`
+ * (TAPS_FP64, TAPS_FP32: CUDA cores; TAPS_BF16: tensor cores where the dim allows, see
+ * taps_batch_refresh_grams).  Synchronous. */
+int taps_problem_refresh_grams(taps_problem* prob, const taps_factors* U, int precision);
+/* Copy the current Grams of dim d for mode count M: gram_out [nops][M][M] row-major,
+ * Gamma_o[m][n] = U[:, m]^T Op_o U[:, n], one per distinct operator of the dim in slot
+ * order (ops_out receives their op codes, nops_out their count); h_out [R_f][M].  Any
+ * output pointer may be NULL.  M must not exceed the problem's workspace (the largest M
+ * swept or refreshed). */
+int taps_problem_copy_grams(const taps_problem* prob, int d, int M, double* gram_out, double* h_out, int* ops_out,
+                            int* nops_out);
 void taps_problem_destroy(taps_problem* prob);
 
 /* ---- factors: D device matrices U_d (n_free(d) x M, column-major, FP64; Eq. 7) --- */
@@ -380,6 +391,27 @@ int taps_batch_sweep(taps_batch* batch, int n_sweeps, int graphs, double* change
  * first graph sweep) and the tuner's two trial times in ms (FASTDIAG, MODEDIAG; -1
  * before tuning or without AUTO).  Either pointer may be NULL. */
 int taps_batch_info(const taps_batch* batch, int* solver_out, float* trial_ms_out);
+/* Recompute the Gram matrices Gamma_{o,d} = U_d^T Op_{o,d} U_d and h_{r,d} = U_d^T q_{r,d}
+ * (Eq. 34) of every dim of every instance from the current factors, all instances at
+ * once (the SpMM + Gram refresh of Algorithm 1, batched).  precision TAPS_BF16: one
+ * persistent launch on the tensor cores (tcgen05, factors, bands and source vectors
+ * rounded to bfloat16, the banded product kept to ~16 bits as two bfloat16 parts, FP32
+ * accumulation in tensor memory); CTAs pull (instance, dim) items from a device queue,
+ * largest first.  The first such call times the chunk height (64 or 128 nodes) and the
+ * CTAs per SM (1 or 2) on the batch and keeps the fastest (taps_batch_gram_info).
+ * Every item needs M <= 64, R_f <= 64 and at most 4 distinct operators, else
+ * TAPS_ERR_INVALID_ARG.  precision TAPS_FP64: each instance's FP64 refresh on its own
+ * stream.  The batch's sweeps keep their own precision; this call replaces the
+ * instances' Grams until the next sweep recomputes them.  ms_out (optional): device time
+ * of the refresh (CUDA events on the batch's stream, the queue set-up excluded);
+ * bytes_out (optional): its algorithmic bytes (FP64 factors, bands and source vectors
+ * read once, Grams written).  Synchronous. */
+int taps_batch_refresh_grams(taps_batch* batch, int precision, float* ms_out, double* bytes_out);
+/* The tuner's choice of taps_batch_refresh_grams (chunk rows, CTAs per SM; 0 before the
+ * first BF16 call) and its trial times in ms for (64, 1), (64, 2), (128, 1), (128, 2)
+ * (-1 where the shared memory or TMEM does not allow the occupancy).  Pointers may be
+ * NULL. */
+int taps_batch_gram_info(const taps_batch* batch, int* rows_out, int* ctas_per_sm_out, float* table_ms_out);
 void taps_batch_destroy(taps_batch* batch);
 
 /* ---- learned warm start (the paper's Algorithm 1 starts from random values) ------

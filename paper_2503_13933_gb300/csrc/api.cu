@@ -1395,11 +1395,21 @@ struct taps_batch {
   cudaEvent_t* join;
   cudaGraph_t g;
   cudaGraphExec_t exec;
+  // batched tensor-core Gram refresh: queue buffer, per-item tickets, the tile choice
+  // (chunk rows, CTAs per SM) of the tuner and its trial times
+  void* gt_buf;
+  size_t gt_buf_bytes;
+  unsigned* gt_tickets;
+  int gt_items_cap;
+  int gt_rows, gt_cps, gt_tuned;
+  float gt_table[4];
 };
 
 extern "C" void taps_batch_destroy(taps_batch* B) {
   if (!B) return;
   if (B->master) cudaStreamSynchronize(B->master);
+  if (B->gt_buf) cudaFree(B->gt_buf);
+  if (B->gt_tickets) cudaFree(B->gt_tickets);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->g) cudaGraphDestroy(B->g);
   if (B->join) {
@@ -1643,4 +1653,173 @@ extern "C" int taps_batch_sweep(taps_batch* B, int n_sweeps, int graphs, double*
     }
   }
   return status_out ? TAPS_OK : first;
+}
+
+// ---------------------------------------------------------------------------------
+// Gram refresh of every dim of every instance of a batch in one persistent launch
+// (tensor cores, BF16 operands) or instance by instance (FP64, CUDA cores).
+// ---------------------------------------------------------------------------------
+static const int kGtRows[4] = {64, 64, 128, 128};
+static const int kGtCps[4] = {1, 2, 1, 2};
+
+extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_out, double* bytes_out) {
+  if (!B || (precision != TAPS_FP64 && precision != TAPS_BF16)) return TAPS_ERR_INVALID_ARG;
+  std::vector<GtHostItem> items;
+  int maxN = 16, maxNH = 16, maxops = 1;
+  size_t chunks64 = 0;
+  double bytes = 0.0;
+  for (int i = 0; i < B->count; ++i) {
+    taps_problem* P = B->P[i];
+    taps_factors* U = B->U[i];
+    for (int d = 0; d < P->D; ++d) {
+      const taps_dim* dm = P->dims[d];
+      GtHostItem h;
+      h.U = U->d_U[d];
+      h.band = P->d_opband[d];
+      h.q = P->d_q[d];
+      h.gram = P->d_gram[d];
+      h.h = P->d_h[d];
+      h.n = dm->nf;
+      h.M = U->M;
+      h.hb = dm->hb;
+      h.nops = P->tt.nops[d];
+      h.Rf = P->Rf;
+      if (precision == TAPS_BF16 && !taps_gram_tc_eligible(h.M, h.nops, h.Rf, h.hb)) return TAPS_ERR_INVALID_ARG;
+      items.push_back(h);
+      maxN = std::max(maxN, (h.M + 15) & ~15);
+      maxNH = std::max(maxNH, (h.Rf + 15) & ~15);
+      maxops = std::max(maxops, h.nops);
+      chunks64 += (size_t)(h.n + 63) / 64;
+      const int nb = 2 * h.hb + 1;
+      bytes += 8.0 * ((double)h.n * h.M + (double)h.nops * h.n * nb + (double)h.Rf * h.n +
+                      (double)h.nops * h.M * h.M + (double)h.Rf * h.M);
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TAPS_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return TAPS_ERR_CUDA;
+  }
+  int st = TAPS_OK;
+  float ms = 0.f;
+  do {
+    if ((st = batch_join(B)) != TAPS_OK) break;
+    if (precision == TAPS_FP64) {
+      // instance by instance on their own streams, forked from and joined to the batch's
+      if (cudaEventRecord(e0, B->master) != cudaSuccess || cudaEventRecord(B->fork, B->master) != cudaSuccess) {
+        st = TAPS_ERR_CUDA;
+        break;
+      }
+      for (int i = 0; i < B->count && st == TAPS_OK; ++i) {
+        if (cudaStreamWaitEvent(B->P[i]->stream, B->fork, 0) != cudaSuccess) st = TAPS_ERR_CUDA;
+        else st = taps_refresh_grams(B->P[i], B->U[i], TAPS_FP64);
+      }
+      if (st != TAPS_OK || (st = batch_join(B)) != TAPS_OK) break;
+      if (cudaEventRecord(e1, B->master) != cudaSuccess) st = TAPS_ERR_CUDA;
+    } else {
+      const int dev_sms = B->P[0]->num_sms;
+      const size_t need = taps_gram_tc_queue_bytes((int)items.size(), (int)chunks64);
+      if (need > B->gt_buf_bytes) {
+        if (B->gt_buf) cudaFree(B->gt_buf);
+        B->gt_buf = nullptr;
+        B->gt_buf_bytes = 0;
+        if ((st = taps_alloc(&B->gt_buf, need)) != TAPS_OK) break;
+        B->gt_buf_bytes = need;
+      }
+      if ((int)items.size() > B->gt_items_cap) {
+        if (B->gt_tickets) cudaFree(B->gt_tickets);
+        B->gt_tickets = nullptr;
+        B->gt_items_cap = 0;
+        if ((st = taps_alloc((void**)&B->gt_tickets, sizeof(unsigned) * items.size())) != TAPS_OK) break;
+        if (cudaMemsetAsync(B->gt_tickets, 0, sizeof(unsigned) * items.size(), B->master) != cudaSuccess) {
+          st = TAPS_ERR_CUDA;
+          break;
+        }
+        B->gt_items_cap = (int)items.size();
+      }
+      int* status = B->P[0]->d_status;
+      // one task per item (the whole dim in one CTA): no partials; the tuner times the
+      // chunk height and the CTAs per SM the shared memory and TMEM allow
+      if (!B->gt_tuned) {
+        int maxsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        float best = 1e30f;
+        for (int k = 0; k < 4 && st == TAPS_OK; ++k) {
+          size_t smem = 0;
+          int ncols = 0;
+          taps_gram_tc_footprint(kGtRows[k], maxN, maxNH, maxops, &smem, &ncols);
+          B->gt_table[k] = -1.f;
+          if ((size_t)kGtCps[k] * (smem + 1024) > (size_t)maxsm || kGtCps[k] * ncols > 512) continue;
+          st = taps_gram_tc_queue(items, kGtRows[k], 1 << 20, dev_sms * kGtCps[k], B->gt_buf, B->gt_buf_bytes,
+                                  nullptr, 0, B->gt_tickets, B->master, status, nullptr, nullptr, e0, e1);
+          if (st != TAPS_OK) break;
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          B->gt_table[k] = t;
+          if (t < best) {
+            best = t;
+            B->gt_rows = kGtRows[k];
+            B->gt_cps = kGtCps[k];
+          }
+        }
+        if (st != TAPS_OK) break;
+        B->gt_tuned = 1;
+      }
+      st = taps_gram_tc_queue(items, B->gt_rows, 1 << 20, dev_sms * B->gt_cps, B->gt_buf, B->gt_buf_bytes, nullptr,
+                              0, B->gt_tickets, B->master, status, nullptr, nullptr, e0, e1);
+      if (st != TAPS_OK) break;
+    }
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = TAPS_ERR_CUDA;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    // the instances' next work sees the new Grams
+    if (cudaEventRecord(B->fork, B->master) != cudaSuccess) st = TAPS_ERR_CUDA;
+    for (int i = 0; i < B->count && st == TAPS_OK; ++i)
+      if (cudaStreamWaitEvent(B->P[i]->stream, B->fork, 0) != cudaSuccess) st = TAPS_ERR_CUDA;
+    if (st == TAPS_OK) st = taps_check_status(B->P[0]->d_status, B->master);
+  } while (0);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TAPS_OK) return st;
+  if (ms_out) *ms_out = ms;
+  if (bytes_out) *bytes_out = bytes;
+  return TAPS_OK;
+}
+
+extern "C" int taps_batch_gram_info(const taps_batch* B, int* rows_out, int* ctas_per_sm_out, float* table_ms_out) {
+  if (!B) return TAPS_ERR_INVALID_ARG;
+  if (rows_out) *rows_out = B->gt_tuned ? B->gt_rows : 0;
+  if (ctas_per_sm_out) *ctas_per_sm_out = B->gt_tuned ? B->gt_cps : 0;
+  if (table_ms_out)
+    for (int k = 0; k < 4; ++k) table_ms_out[k] = B->gt_tuned ? B->gt_table[k] : -1.f;
+  return TAPS_OK;
+}
+
+extern "C" int taps_problem_refresh_grams(taps_problem* P, const taps_factors* U, int precision) {
+  if (!P || !U || U->prob != P || U->M < 1 ||
+      (precision != TAPS_FP64 && precision != TAPS_FP32 && precision != TAPS_BF16))
+    return TAPS_ERR_INVALID_ARG;
+  TAPS_TRY(taps_ws_ensure(P, U->M));
+  TAPS_TRY(taps_refresh_grams(P, U, precision));
+  return taps_check_status(P->d_status, P->stream);
+}
+
+extern "C" int taps_problem_copy_grams(const taps_problem* P, int d, int M, double* gram_out, double* h_out,
+                                       int* ops_out, int* nops_out) {
+  if (!P || d < 0 || d >= P->D || M < 1 || M > P->ws_M) return TAPS_ERR_INVALID_ARG;
+  const int nops = P->tt.nops[d];
+  if (nops_out) *nops_out = nops;
+  if (ops_out)
+    for (int o = 0; o < nops; ++o) ops_out[o] = P->ops[d][o];
+  if (gram_out)
+    TAPS_CUDA(cudaMemcpyAsync(gram_out, P->d_gram[d], sizeof(double) * nops * M * M, cudaMemcpyDeviceToHost,
+                              P->stream));
+  if (h_out)
+    TAPS_CUDA(cudaMemcpyAsync(h_out, P->d_h[d], sizeof(double) * P->Rf * M, cudaMemcpyDeviceToHost, P->stream));
+  TAPS_CUDA(cudaStreamSynchronize(P->stream));
+  return TAPS_OK;
 }

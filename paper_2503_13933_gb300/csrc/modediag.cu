@@ -301,6 +301,11 @@ __global__ void __launch_bounds__(MD_THREADS) md_eig_kernel(const double* __rest
 // steps and their arithmetic are those of md_eig_kernel; W^T c_r is left to
 // md_cw_kernel, spread over many CTAs.
 #define MDB_THREADS 512
+#define MDB_SMEM_SV_MAX (220 * 1024)   // S and V together in dynamic shared memory up to this size
+// VSH: the basis V also lives in shared memory, after S (when both fit: Np <= 116);
+// its round-by-round row-pair updates are then shared-memory traffic instead of L2
+// round trips, which bound the global variant.
+template <bool VSH>
 __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* __restrict__ CX,
                                                                  const double* __restrict__ CY, int M,
                                                                  double* __restrict__ Wio, int* __restrict__ wM,
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
   const int Np = M + (M & 1), ld = Np + 1;
   const size_t MM = (size_t)M * M;
   double* L = gw;            // row-major [M][M], lower triangle used
-  double* Vt = gw + MM;      // column-major basis: Vt[c * M + r] = V[r][c]
+  double* Vt = VSH ? Ssh + (size_t)Np * ld : gw + MM;   // column-major basis: Vt[c * M + r] = V[r][c]
   double* T = gw + 2 * MM;   // row-major temporary
   double* Pw = gw + 3 * MM;  // row-major previous basis (identity when cold)
 #define SB(i, j) Ssh[(size_t)(i) * ld + (j)]
@@ -775,9 +780,12 @@ int taps_md_reset(taps_problem* P) {
 int taps_md_setup(int maxsm) {
   const int need = (int)(sizeof(double) * (TAPS_MAX_M + 1) * (TAPS_MAX_M + 2));
   cudaFuncAttributes fa;
-  TAPS_CUDA(cudaFuncGetAttributes(&fa, md_eig_big_kernel));
-  TAPS_CUDA(cudaFuncSetAttribute(md_eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TAPS_CUDA(cudaFuncGetAttributes(&fa, md_eig_big_kernel<false>));
+  TAPS_CUDA(cudaFuncSetAttribute(md_eig_big_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  std::min(need, maxsm - (int)fa.sharedSizeBytes)));
+  TAPS_CUDA(cudaFuncGetAttributes(&fa, md_eig_big_kernel<true>));
+  TAPS_CUDA(cudaFuncSetAttribute(md_eig_big_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 std::min(MDB_SMEM_SV_MAX, maxsm - (int)fa.sharedSizeBytes)));
   return TAPS_OK;
 }
 
@@ -820,10 +828,16 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
     // the eigen-solve's workspace follows the band rows (sized for M > 32 only)
     double* gw = Ab + (size_t)(P->nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M;
     const int Np = M + (M & 1);
-    const size_t smem = sizeof(double) * (size_t)Np * (Np + 1);   // opted in by taps_md_setup
-    md_eig_big_kernel<<<1, MDB_THREADS, smem, s>>>(P->d_C + (size_t)sx * MM,
-                                                   sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm, wM, lam,
-                                                   gw, P->d_status);
+    const size_t smem_s = sizeof(double) * (size_t)Np * (Np + 1);   // opted in by taps_md_setup
+    const size_t smem_sv = smem_s + sizeof(double) * (size_t)M * M;
+    if (smem_sv <= (size_t)MDB_SMEM_SV_MAX)
+      md_eig_big_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(P->d_C + (size_t)sx * MM,
+                                                              sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm,
+                                                              wM, lam, gw, P->d_status);
+    else
+      md_eig_big_kernel<false><<<1, MDB_THREADS, smem_s, s>>>(P->d_C + (size_t)sx * MM,
+                                                              sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm,
+                                                              wM, lam, gw, P->d_status);
     const long long rm = (long long)Rf * M;
     md_cw_kernel<<<(unsigned)((rm + 255) / 256), 256, 0, s>>>(P->d_c, Wm, Rf, M, cw);
   }

@@ -235,6 +235,8 @@ static GramPtrs gram_ptrs(const taps_problem* P) {
   return gp;
 }
 
+static int coefficients(taps_problem* P, int d, int M);
+
 int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision, int coeff_dim) {
   if (P->tt.cs > TAPS_NUM_OPS && coeff_dim >= 0) {
     // weighted operators: the Gram refresh, then the coefficients in their own launch
@@ -262,6 +264,19 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
     gbytes += 8.0 * ((double)P->R * M * M * P->D);
   }
   GramPtrs gp = gram_ptrs(P);
+  if (precision == TAPS_BF16 && taps_gram_tc_eligible(M, nops, Rf, hb)) {
+    // BF16 operands on the tensor cores (chunks of 64 nodes, one CTA each), then the
+    // next dim's coefficients in their own launch
+    int tk = prof_begin(P, TAPS_PROF_GRAM);
+    TAPS_TRY(taps_gram_tc_single(U->d_U[d], P->d_opband[d], P->d_q[d], P->d_gram[d], P->d_h[d], nf, M, hb, nops,
+                                 Rf, P->d_partial, P->d_ticket + 48, 64, P->stream, P->d_status));
+    prof_end(P, TAPS_PROF_GRAM, tk, nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M,
+             8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf + (double)nops * M * M +
+                    (double)Rf * M));
+    TAPS_CUDA(cudaGetLastError());
+    if (coeff_dim >= 0) TAPS_TRY(coefficients(P, coeff_dim, M));
+    return TAPS_OK;
+  }
   int tk = prof_begin(P, TAPS_PROF_GRAM);
   if (precision == TAPS_FP32) {   // TAPS_MIXED keeps FP64 Grams
     TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, false>, grid, dim3(256), elems * sizeof(float),
@@ -720,6 +735,7 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
   TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, true>, maxsm));
   TAPS_TRY(residual_setup(maxsm));
   TAPS_TRY(taps_md_setup(maxsm));
+  TAPS_TRY(taps_gram_tc_setup(maxsm));
   int bps = 0;
   size_t smem_max = sizeof(double) * TAPS_MAX_M * (TAPS_MAX_M + 1);
   TAPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, block_lu_kernel, 256, smem_max));

@@ -367,6 +367,24 @@ struct FdPending {
 int taps_md_eligible(const taps_problem* P, int d, int M, int* slotX, int* slotY);
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf);
 int taps_md_setup(int maxsm);
+
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation) Gram refresh (gram_tc.cu).
+int taps_gram_tc_eligible(int M, int nops, int Rf, int hb);
+int taps_gram_tc_setup(int maxsm);
+int taps_gram_tc_single(const double* U, const double* band, const double* q, double* gram, double* h, int n,
+                        int M, int hb, int nops, int Rf, double* partial, unsigned* ticket, int rows,
+                        cudaStream_t s, int* status);
+struct GtHostItem {
+  const double *U, *band, *q;
+  double *gram, *h;
+  int n, M, hb, nops, Rf;
+};
+size_t taps_gram_tc_queue_bytes(int nitems, int max_tasks);
+int taps_gram_tc_queue(const std::vector<GtHostItem>& hitems, int rows, int cpt, int ctas, void* dev_buf,
+                       size_t dev_buf_bytes, double* partial, size_t partial_doubles, unsigned* tickets,
+                       cudaStream_t s, int* status, double* flops_out, double* bytes_out, cudaEvent_t ev0,
+                       cudaEvent_t ev1);
+int taps_gram_tc_footprint(int rows, int maxN, int maxNH, int maxops, size_t* smem, int* ncols);
 int taps_md_solve(taps_problem* P, taps_factors* U, int d);
 int taps_md_reset(taps_problem* P);
 // Node-side diagonalisation with convection-face corrections (fdbound.cu).

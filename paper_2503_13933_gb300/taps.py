@@ -118,6 +118,10 @@ SIGNATURES = {
     "taps_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _i, ctypes.POINTER(_vp)]),
     "taps_batch_sweep": (_i, [_vp, _i, _i, _pd, _pi]),
     "taps_batch_info": (_i, [_vp, _pi, ctypes.POINTER(ctypes.c_float)]),
+    "taps_batch_refresh_grams": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_float), _pd]),
+    "taps_batch_gram_info": (_i, [_vp, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
+    "taps_problem_refresh_grams": (_i, [_vp, _vp, _i]),
+    "taps_problem_copy_grams": (_i, [_vp, _i, _i, _pd, _pd, _pi, _pi]),
     "taps_util_barrier_test": (_i, [_i, _i, ctypes.c_longlong, _vp]),
     "taps_batch_destroy": (None, [_vp]),
     "taps_mlp_create": (_i, [_i, _i, _i, _i, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
@@ -307,6 +311,22 @@ class Problem:
     def factors(self, M_cap):
         return Factors(self, M_cap)
 
+    def refresh_grams(self, U, precision=FP64):
+        """Recompute every dim's Grams from U at `precision` (taps_problem_refresh_grams)."""
+        check(lib().taps_problem_refresh_grams(self.handle, U.handle, precision), "taps_problem_refresh_grams")
+
+    def grams(self, d, M):
+        """(Gamma [nops][M][M], h [R_f][M], op codes) of dim d (taps_problem_copy_grams)."""
+        nops = ctypes.c_int()
+        ops = (ctypes.c_int * 64)()
+        check(lib().taps_problem_copy_grams(self.handle, d, M, None, None, ops, ctypes.byref(nops)),
+              "taps_problem_copy_grams")
+        g = np.zeros((nops.value, M, M))
+        h = np.zeros((len(self.desc["sources"]), M))
+        check(lib().taps_problem_copy_grams(self.handle, d, M, g.ctypes.data_as(_pd), h.ctypes.data_as(_pd),
+                                            None, None), "taps_problem_copy_grams")
+        return g, h, [ops[k] for k in range(nops.value)]
+
     def sweep(self, U, n=1, precision=FP64, normalize=True, solver=SOLVER_BLOCK_LU):
         """Run n sweeps (Algorithm 1 inner loop)."""
         o = SweepOpts(precision=precision, solver=solver, normalize=int(normalize))
@@ -417,6 +437,22 @@ class Batch:
         ms = (ctypes.c_float * 2)()
         check(lib().taps_batch_info(self.handle, ctypes.byref(sv), ms), "taps_batch_info")
         return sv.value, [ms[0], ms[1]]
+
+    def refresh_grams(self, precision=BF16):
+        """Every instance's Grams from its current factors (taps_batch_refresh_grams);
+        returns (device ms, algorithmic bytes)."""
+        ms = ctypes.c_float()
+        by = ctypes.c_double()
+        check(lib().taps_batch_refresh_grams(self.handle, precision, ctypes.byref(ms), ctypes.byref(by)),
+              "taps_batch_refresh_grams")
+        return ms.value, by.value
+
+    def gram_info(self):
+        """(chunk rows, CTAs per SM, trial ms of (64,1), (64,2), (128,1), (128,2))."""
+        r, c = ctypes.c_int(), ctypes.c_int()
+        t = (ctypes.c_float * 4)()
+        check(lib().taps_batch_gram_info(self.handle, ctypes.byref(r), ctypes.byref(c), t), "taps_batch_gram_info")
+        return r.value, c.value, [t[k] for k in range(4)]
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
