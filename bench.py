@@ -43,6 +43,102 @@ TRAFFIC_BYTES = {
 }
 
 
+# Small seeded cases for kernel profiles (ncu captures that end on their own):
+# `python bench.py --profile-case NAME [NAME ...]` runs them in order and exits.
+#   modediag   : poisson_k 256^3 x 32, M = 30, two sweeps on the mode-side route
+#   convection : a powder-bed-fusion slab at 128^2 x 32 space, M = 20, two sweeps
+#                (convection-face route on the space dims)
+#   images     : the FP32 tensor-core reconstruction of poisson_k 160^3 x 32, M = 30
+#   pencil     : poisson_k 256^3 x 32, M = 30, one node-side sweep (the pencil
+#                decomposition of the 254-node space dims runs first)
+#   nonlinear  : the temperature-dependent moving-source plate at full size (101^2 x 11
+#                space, 113 time, M = 10): two global stages of two subspace iterations
+#   gram_tc    : 64 instances of the batched family (n_d 32..1024, M 4..32): the batched
+#                tensor-core Gram refresh, tuned, then three refreshes
+#   large_time : the large moving-source configuration at a 256^2 x 128 block, M = 100,
+#                two node-side / mode-side sweeps (the 100-mode time-dim eigen-solve)
+def _case_modediag(taps, W):
+    d = W.poisson_k(256, 32, seed=2000)
+    P = taps.Problem(d)
+    U = P.factors(30)
+    U.set(W.random_factors(d, 30, seed=1))
+    P.sweep(U, 2, solver=taps.SOLVER_MODEDIAG)
+
+
+def _case_convection(taps, W):
+    d = W.lpbf_slab(n_xy=128, n_z=32, n_t=32, n_par=8)
+    P = taps.Problem(d)
+    U = P.factors(20)
+    U.set(W.random_factors(d, 20, seed=2))
+    P.sweep(U, 2, solver=taps.SOLVER_FASTDIAG)
+
+
+def _case_images(taps, W):
+    import torch
+    d = W.poisson_k(160, 32, seed=2000)
+    P = taps.Problem(d)
+    U = P.factors(30)
+    U.set(W.random_factors(d, 30, seed=3))
+    out = torch.empty(160 ** 3 * 32, dtype=torch.float32, device="cuda")
+    P.eval_grid(U, [0, 0, 0, 0], [160, 160, 160, 32], [1, 1, 1, 1], out)
+
+
+def _case_pencil(taps, W):
+    d = W.poisson_k(256, 32, seed=2000)
+    P = taps.Problem(d)
+    U = P.factors(30)
+    U.set(W.random_factors(d, 30, seed=1))
+    P.sweep(U, 1, solver=taps.SOLVER_FASTDIAG)
+
+
+def _case_nonlinear(taps, W):
+    from paper_2503_13933_gb300 import nonlinear as NL
+    gl = NL.GlobalLocal(W.nonlinear_track(), W.INCONEL_LAW, 10)
+    gl.solve(2, max_iters=2, tol=0.0, seed=5)
+
+
+def _case_gram_tc(taps, W):
+    import torch
+    descs, Ms = W.batch_instances(count=64, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32)
+    probs, facs = [], []
+    for i, (dsc, M) in enumerate(zip(descs, Ms)):
+        P = taps.Problem(dsc, stream=taps.ctypes.c_void_p(torch.cuda.Stream().cuda_stream))
+        U = P.factors(M)
+        U.set(W.random_factors(dsc, M, seed=100 + i))
+        probs.append(P)
+        facs.append(U)
+    B = taps.Batch(probs, facs, solver=taps.SOLVER_FASTDIAG)
+    for _ in range(4):
+        B.refresh_grams(taps.BF16)
+
+
+def _case_large_time(taps, W):
+    d = W.lpbf_large(n_xy=256, n_z=128)
+    P = taps.Problem(d)
+    U = P.factors(100)
+    P.solve(U, M0=100, M_max=100, res_tol=-1.0, max_sweeps=2, init=taps.INIT_RANDOM, seed=5001, als_tol=0.0,
+            solver=taps.SOLVER_FASTDIAG)
+
+
+PROFILE_CASES = dict(modediag=_case_modediag, convection=_case_convection, images=_case_images,
+                     pencil=_case_pencil, nonlinear=_case_nonlinear, gram_tc=_case_gram_tc,
+                     large_time=_case_large_time)
+
+
+def run_profile_cases(names):
+    import torch
+    from paper_2503_13933_gb300 import taps
+    from paper_2503_13933_gb300 import workloads as W
+    for nm in names:
+        if nm not in PROFILE_CASES:
+            raise SystemExit(f"unknown case {nm!r}; cases: {', '.join(PROFILE_CASES)}")
+    taps.lib()
+    for nm in names:
+        PROFILE_CASES[nm](taps, W)
+    torch.cuda.synchronize()
+    print("ok")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -65,6 +161,9 @@ def parse():
     ap.add_argument("--no-spt", action="store_true",
                     help="skip the eight-dimensional space-parameter-time measurement")
     ap.add_argument("--no-e2e-modediag", action="store_true", help="skip the mode-side end-to-end solve")
+    ap.add_argument("--profile-case", nargs="+", default=None,
+                    help="run small seeded profiling cases by name and exit: " + ", ".join(
+                        ["modediag", "convection", "images", "pencil", "nonlinear", "gram_tc", "large_time"]))
     ap.add_argument("--paths", default="fp64,fp64_fastdiag,fp64_modediag,fp32gram_fastdiag,bf16gram_fastdiag,"
                                        "mixed_fastdiag,mixed_fastdiag_mlp",
                     help="comma list of solver paths to time")
@@ -834,6 +933,9 @@ def run_ours(args, rank, world, local):
 
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_cases(args.profile_case)
+        return
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
