@@ -683,8 +683,7 @@ def run_ours(args, rank, world, local):
                             hbm_frac=gby / (np.mean(gms) * 1e-3) / 1e9 / hbm_peak,
                             peak_source="measured (MEASURED_PEAKS.json hbm_gbs)",
                             tile_rows=g_rows, ctas_per_sm=g_cps,
-                            tuner_ms={"64x1": g_table[0], "64x2": g_table[1], "128x1": g_table[2],
-                                      "128x2": g_table[3]},
+                            tuner_ms={f"{r}x{c}": t for (r, c), t in zip(taps.Batch.GRAM_TILES, g_table)},
                             fp64_cuda_cores_ms=ms64,
                             kernel="gram_tc_kernel (tcgen05 kind::f16, persistent, device work queue)")
         times, failed = {}, {}

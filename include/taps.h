@@ -398,7 +398,7 @@ int taps_batch_info(const taps_batch* batch, int* solver_out, float* trial_ms_ou
  * rounded to bfloat16, the banded product kept to ~16 bits as two bfloat16 parts, FP32
  * accumulation in tensor memory); CTAs pull (instance, dim) items from a device queue,
  * largest first.  The first such call times the chunk height (64 or 128 nodes) and the
- * CTAs per SM (1 or 2) on the batch and keeps the fastest (taps_batch_gram_info).
+ * CTAs per SM (1 to 4) on the batch and keeps the fastest (taps_batch_gram_info).
  * Every item needs M <= 64, R_f <= 64 and at most 4 distinct operators, else
  * TAPS_ERR_INVALID_ARG.  precision TAPS_FP64: each instance's FP64 refresh on its own
  * stream.  The batch's sweeps keep their own precision; this call replaces the
@@ -408,9 +408,9 @@ int taps_batch_info(const taps_batch* batch, int* solver_out, float* trial_ms_ou
  * read once, Grams written).  Synchronous. */
 int taps_batch_refresh_grams(taps_batch* batch, int precision, float* ms_out, double* bytes_out);
 /* The tuner's choice of taps_batch_refresh_grams (chunk rows, CTAs per SM; 0 before the
- * first BF16 call) and its trial times in ms for (64, 1), (64, 2), (128, 1), (128, 2)
- * (-1 where the shared memory or TMEM does not allow the occupancy).  Pointers may be
- * NULL. */
+ * first BF16 call) and its 6 trial times in ms for (rows, CTAs per SM) = (64, 1), (64, 2),
+ * (64, 3), (64, 4), (128, 1), (128, 2) (-1 where the shared memory or TMEM does not allow
+ * the occupancy).  Pointers may be NULL. */
 int taps_batch_gram_info(const taps_batch* batch, int* rows_out, int* ctas_per_sm_out, float* table_ms_out);
 void taps_batch_destroy(taps_batch* batch);
 

@@ -1402,7 +1402,7 @@ struct taps_batch {
   unsigned* gt_tickets;
   int gt_items_cap;
   int gt_rows, gt_cps, gt_tuned;
-  float gt_table[4];
+  float gt_table[6];
 };
 
 extern "C" void taps_batch_destroy(taps_batch* B) {
@@ -1659,8 +1659,9 @@ extern "C" int taps_batch_sweep(taps_batch* B, int n_sweeps, int graphs, double*
 // Gram refresh of every dim of every instance of a batch in one persistent launch
 // (tensor cores, BF16 operands) or instance by instance (FP64, CUDA cores).
 // ---------------------------------------------------------------------------------
-static const int kGtRows[4] = {64, 64, 128, 128};
-static const int kGtCps[4] = {1, 2, 1, 2};
+#define GT_CAND 6
+static const int kGtRows[GT_CAND] = {64, 64, 64, 64, 128, 128};
+static const int kGtCps[GT_CAND] = {1, 2, 3, 4, 1, 2};
 
 extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_out, double* bytes_out) {
   if (!B || (precision != TAPS_FP64 && precision != TAPS_BF16)) return TAPS_ERR_INVALID_ARG;
@@ -1746,7 +1747,7 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         float best = 1e30f;
-        for (int k = 0; k < 4 && st == TAPS_OK; ++k) {
+        for (int k = 0; k < GT_CAND && st == TAPS_OK; ++k) {
           size_t smem = 0;
           int ncols = 0;
           taps_gram_tc_footprint(kGtRows[k], maxN, maxNH, maxops, &smem, &ncols);
@@ -1795,7 +1796,7 @@ extern "C" int taps_batch_gram_info(const taps_batch* B, int* rows_out, int* cta
   if (rows_out) *rows_out = B->gt_tuned ? B->gt_rows : 0;
   if (ctas_per_sm_out) *ctas_per_sm_out = B->gt_tuned ? B->gt_cps : 0;
   if (table_ms_out)
-    for (int k = 0; k < 4; ++k) table_ms_out[k] = B->gt_tuned ? B->gt_table[k] : -1.f;
+    for (int k = 0; k < GT_CAND; ++k) table_ms_out[k] = B->gt_tuned ? B->gt_table[k] : -1.f;
   return TAPS_OK;
 }
 

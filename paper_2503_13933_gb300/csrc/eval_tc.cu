@@ -20,9 +20,11 @@
 //   warps 2 - 9  : epilogue; warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 and
 //                  the column half (w - 2) / 4 of the tile
 // Two TMEM accumulators (256 columns each, 512 in all) let the operand copy and the
-// MMAs of the next tile run while the previous tile streams out; the copy and the
-// MMAs are short next to a tile's 128 KB output, so one operand stage suffices and
-// the shared memory goes to the epilogue's staging blocks.  Every wait on an mbarrier is bounded;
+// MMAs of the next tile run while the previous tile streams out.  Up to K = 32 the copy
+// and the MMAs are short next to a tile's 128 KB output, so a tile's operands travel in
+// one stage and the rest of the shared memory goes to the epilogue's staging blocks;
+// beyond (up to K = 128) the operands of a tile travel in chunks of 16 K through three
+// stages, the accumulator collecting the chunks' MMAs.  Every wait on an mbarrier is bounded;
 // a wait that runs out sets TAPS_DEV_TIMEOUT, the other roles see the abort flag, the
 // MMA issuer waits (bounded) for its outstanding MMAs, and TMEM is freed on exit.
 #include <stdint.h>
@@ -34,10 +36,11 @@
 #define TC_BM 128                    // output rows per tile (TMEM lanes)
 #define TC_BN 256                    // output columns per tile (TMEM columns)
 #define TC_KSTEP 8                   // K of one kind::tf32 MMA
-#define TC_MAXK 32                   // largest padded K handled here (M <= 32)
+#define TC_MAXK 128                  // largest padded K handled here (M <= 128)
 #define TC_A_KBLK (TC_BM * TC_KSTEP) // floats of one A K-step block (4 KB)
 #define TC_B_KBLK (TC_BN * TC_KSTEP) // floats of one B K-step block (8 KB)
-#define TC_STAGES 1                  // operand stages (the output stream dominates)
+#define TC_MAXSTAGES 3               // operand stages: 1 for K <= 32 (a tile's operands in one
+                                     // stage), 3 stages of 16 K each beyond
 #define TC_ACC 2                     // TMEM accumulators
 #define TC_EPI_WARPS 8               // two per TMEM lane quarter, one per column half
 #define TC_THREADS (64 + 32 * TC_EPI_WARPS)
@@ -222,11 +225,11 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __restrict__ Aimg,
                                                                  const float* __restrict__ Bimg,
-                                                                 long long R, int C, int ksteps,
+                                                                 long long R, int C, int ksteps, int kc, int nst,
                                                                  float* __restrict__ out, int vec_ok,
                                                                  int rowmajor, int* status) {
   extern __shared__ __align__(1024) unsigned char tc_sm[];
-  __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t full_bar[TC_MAXSTAGES], empty_bar[TC_MAXSTAGES];
   __shared__ __align__(8) uint64_t acc_full[TC_ACC], acc_empty[TC_ACC], drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -234,15 +237,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
   const long long nrb = (R + TC_BM - 1) / TC_BM;
   const long long ncb = (C + TC_BN - 1) / TC_BN;
   const long long ntiles = nrb * ncb;
+  // an operand block in global memory: [hi | lo][ksteps][rows x 8 floats]; a stage
+  // holds one K chunk of kc steps of both operands: [A hi][A lo][B hi][B lo], each part
+  // kc steps long (with kc = ksteps, one chunk: a tile's whole operands)
   const uint32_t a_bytes = 2u * ksteps * TC_A_KBLK * 4u;
   const uint32_t b_bytes = 2u * ksteps * TC_B_KBLK * 4u;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint32_t stage_bytes = 2u * kc * (TC_A_KBLK + TC_B_KBLK) * 4u;
+  const int nchunks = (ksteps + kc - 1) / kc;
   // 1024-byte aligned stages
   unsigned char* base = tc_sm + ((1024u - (tc_smem(tc_sm) & 1023u)) & 1023u);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       tc_mbar_init(&full_bar[s], 1);
       tc_mbar_init(&empty_bar[s], 1);
     }
@@ -266,70 +273,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {   // ---- producer
-      long long i = 0;
-      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int s = (int)(i % TC_STAGES);
-        const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
-        if (!tc_mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
-          abort_flag = 1;
-          taps_flag(status, TAPS_DEV_TIMEOUT);
-          break;
-        }
+    if (lane == 0) {   // ---- producer: one stage per K chunk of a tile
+      long long i = 0;   // chunks issued
+      bool stop = false;
+      for (long long t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         const long long rb = rowmajor ? t / ncb : t % nrb, cb = rowmajor ? t % ncb : t / nrb;
-        unsigned char* st = base + (size_t)s * stage_bytes;
-        tc_mbar_expect_tx(&full_bar[s], stage_bytes);
         const unsigned char* asrc = (const unsigned char*)Aimg + (size_t)rb * a_bytes;
         const unsigned char* bsrc = (const unsigned char*)Bimg + (size_t)cb * b_bytes;
-        for (uint32_t o = 0; o < a_bytes; o += 8192u)
-          tc_bulk_g2s(st + o, asrc + o, min(8192u, a_bytes - o), &full_bar[s]);
-        for (uint32_t o = 0; o < b_bytes; o += 8192u)
-          tc_bulk_g2s(st + a_bytes + o, bsrc + o, min(8192u, b_bytes - o), &full_bar[s]);
+        for (int c = 0; c < nchunks; ++c, ++i) {
+          const int s = (int)(i % nst);
+          const uint32_t ph = (uint32_t)((i / nst) & 1);
+          if (!tc_mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
+            abort_flag = 1;
+            taps_flag(status, TAPS_DEV_TIMEOUT);
+            stop = true;
+            break;
+          }
+          const int k0 = c * kc, kcc = min(kc, ksteps - k0);
+          unsigned char* st = base + (size_t)s * stage_bytes;
+          tc_mbar_expect_tx(&full_bar[s], 2u * kcc * (TC_A_KBLK + TC_B_KBLK) * 4u);
+          // (part, source offset, stage offset, bytes) of the chunk's four parts
+          const uint32_t abk = TC_A_KBLK * 4u, bbk = TC_B_KBLK * 4u;
+          const unsigned char* src[4] = {asrc + (size_t)k0 * abk, asrc + (size_t)(ksteps + k0) * abk,
+                                         bsrc + (size_t)k0 * bbk, bsrc + (size_t)(ksteps + k0) * bbk};
+          const uint32_t dst[4] = {0u, (uint32_t)kc * abk, 2u * kc * abk, 2u * kc * abk + (uint32_t)kc * bbk};
+          const uint32_t len[4] = {(uint32_t)kcc * abk, (uint32_t)kcc * abk, (uint32_t)kcc * bbk,
+                                   (uint32_t)kcc * bbk};
+          for (int part = 0; part < 4; ++part)
+            for (uint32_t o = 0; o < len[part]; o += 8192u)
+              tc_bulk_g2s(st + dst[part] + o, src[part] + o, min(8192u, len[part] - o), &full_bar[s]);
+        }
       }
       // copies still in flight land before the CTA leaves: wait for the stages issued
       // but not consumed (bounded)
       if (abort_flag) {
         const long long issued = i;
-        for (long long j = (issued > TC_STAGES ? issued - TC_STAGES : 0); j < issued; ++j) {
+        for (long long j = (issued > nst ? issued - nst : 0); j < issued; ++j) {
           volatile int never = 0;
-          tc_mbar_wait(&full_bar[j % TC_STAGES], (uint32_t)((j / TC_STAGES) & 1), (volatile int*)&never);
+          tc_mbar_wait(&full_bar[j % nst], (uint32_t)((j / nst) & 1), (volatile int*)&never);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {   // ---- MMA issuer
-      long long i = 0;
-      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int s = (int)(i % TC_STAGES);
-        const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
-        const int b = (int)(i % TC_ACC);
-        const uint32_t pb = (uint32_t)((i / TC_ACC) & 1);
-        if (!tc_mbar_wait(&acc_empty[b], pb ^ 1u, &abort_flag) || !tc_mbar_wait(&full_bar[s], ph, &abort_flag)) {
+      long long i = 0, tile = 0;   // chunks consumed, tiles started
+      bool stop = false;
+      for (long long t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++tile) {
+        const int b = (int)(tile % TC_ACC);
+        const uint32_t pb = (uint32_t)((tile / TC_ACC) & 1);
+        if (!tc_mbar_wait(&acc_empty[b], pb ^ 1u, &abort_flag)) {
           abort_flag = 1;
           taps_flag(status, TAPS_DEV_TIMEOUT);
           break;
         }
-        tc_fence_after();
-        const uint32_t sa = tc_smem(base + (size_t)s * stage_bytes);
-        const uint32_t sb = sa + a_bytes;
         const uint32_t d = tmem + (uint32_t)(b * TC_BN);
         uint32_t acc = 0;
-        // lo * hi, hi * lo, then hi * hi: the small terms first
-        for (int k = 0; k < ksteps; ++k) {
-          const uint32_t a_hi = sa + (uint32_t)k * TC_A_KBLK * 4u;
-          const uint32_t a_lo = a_hi + (uint32_t)ksteps * TC_A_KBLK * 4u;
-          const uint32_t b_hi = sb + (uint32_t)k * TC_B_KBLK * 4u;
-          const uint32_t b_lo = b_hi + (uint32_t)ksteps * TC_B_KBLK * 4u;
-          tc_mma(d, tc_desc(a_lo, 128, 256), tc_desc(b_hi, 128, 256), acc);
-          acc = 1;
-          tc_mma(d, tc_desc(a_hi, 128, 256), tc_desc(b_lo, 128, 256), acc);
+        for (int c = 0; c < nchunks; ++c, ++i) {
+          const int s = (int)(i % nst);
+          const uint32_t ph = (uint32_t)((i / nst) & 1);
+          if (!tc_mbar_wait(&full_bar[s], ph, &abort_flag)) {
+            abort_flag = 1;
+            taps_flag(status, TAPS_DEV_TIMEOUT);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const int kcc = min(kc, ksteps - c * kc);
+          const uint32_t sa = tc_smem(base + (size_t)s * stage_bytes);
+          const uint32_t sb = sa + 2u * kc * TC_A_KBLK * 4u;
+          // lo * hi, hi * lo, then hi * hi: the small terms first (within the chunk)
+          for (int k = 0; k < kcc; ++k) {
+            const uint32_t a_hi = sa + (uint32_t)k * TC_A_KBLK * 4u;
+            const uint32_t a_lo = a_hi + (uint32_t)kc * TC_A_KBLK * 4u;
+            const uint32_t b_hi = sb + (uint32_t)k * TC_B_KBLK * 4u;
+            const uint32_t b_lo = b_hi + (uint32_t)kc * TC_B_KBLK * 4u;
+            tc_mma(d, tc_desc(a_lo, 128, 256), tc_desc(b_hi, 128, 256), acc);
+            acc = 1;
+            tc_mma(d, tc_desc(a_hi, 128, 256), tc_desc(b_lo, 128, 256), acc);
+          }
+          for (int k = 0; k < kcc; ++k) {
+            const uint32_t a_hi = sa + (uint32_t)k * TC_A_KBLK * 4u;
+            const uint32_t b_hi = sb + (uint32_t)k * TC_B_KBLK * 4u;
+            tc_mma(d, tc_desc(a_hi, 128, 256), tc_desc(b_hi, 128, 256), 1u);
+          }
+          tc_commit(&empty_bar[s]);   // operands free once these MMAs have read them
         }
-        for (int k = 0; k < ksteps; ++k) {
-          const uint32_t a_hi = sa + (uint32_t)k * TC_A_KBLK * 4u;
-          const uint32_t b_hi = sb + (uint32_t)k * TC_B_KBLK * 4u;
-          tc_mma(d, tc_desc(a_hi, 128, 256), tc_desc(b_hi, 128, 256), 1u);
-        }
-        tc_commit(&empty_bar[s]);   // operands free once these MMAs have read them
+        if (stop) break;
         tc_commit(&acc_full[b]);    // accumulator ready for the epilogue
       }
       // every MMA issued by this thread has completed before TMEM is released
@@ -342,7 +371,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) eval_tc_kernel(const float* __r
     const int half = (warp - 2) >> 2;   // column half of the tile
     // 32 x 32 block of this warp, row stride 36 floats: the row-wise float4 writes and
     // the column-wise float4 reads of 8 lanes at a time fall in distinct banks
-    float* tb = reinterpret_cast<float*>(base + (size_t)TC_STAGES * stage_bytes) + (warp - 2) * (32 * 36);
+    float* tb = reinterpret_cast<float*>(base + (size_t)nst * stage_bytes) + (warp - 2) * (32 * 36);
     const int rr = lane >> 3, c4 = (lane & 7) * 4;   // store pattern: 4 rows x 8 float4
     long long i = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
@@ -426,16 +455,18 @@ int taps_eval_tc(taps_problem* P, const float* G, const GridSpec& gs, int split,
   tc_image_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(G, gs, 0, split, M, ksteps, rows, TC_BM, Aimg);
   tc_image_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(G, gs, split, gs.D, M, ksteps, cols, TC_BN,
                                                               Bimg);
-  const size_t stage = (size_t)2 * ksteps * (TC_A_KBLK + TC_B_KBLK) * sizeof(float);
-  const size_t smem = TC_STAGES * stage + TC_EPI_WARPS * 32 * 36 * sizeof(float) + 1024;
+  // K <= 32: a tile's operands in one stage; beyond, three stages of 2 K steps (16 K)
+  const int kc = ksteps <= 4 ? ksteps : 2, nst = ksteps <= 4 ? 1 : TC_MAXSTAGES;
+  const size_t stage = (size_t)2 * kc * (TC_A_KBLK + TC_B_KBLK) * sizeof(float);
+  const size_t smem = nst * stage + TC_EPI_WARPS * 32 * 36 * sizeof(float) + 1024;
   const long long ntiles = nrb * ncb;
   const int grid = (int)std::min<long long>(ntiles, P->num_sms);
   const int vec_ok = ((cols & 3) == 0 && (((uintptr_t)out) & 15) == 0) ? 1 : 0;
   // the larger operand image is walked in the outer order, so that each of its blocks
   // is read from HBM once and its neighbours' tiles find it in L2
   const int rowmajor = (nrb * TC_BM > ncb * TC_BN) && nrb * TC_BM * 2ll * ksteps * TC_KSTEP * 4 > (32ll << 20);
-  eval_tc_kernel<<<grid, TC_THREADS, smem, s>>>(Aimg, Bimg, rows, (int)cols, ksteps, out, vec_ok, rowmajor,
-                                                 P->d_status);
+  eval_tc_kernel<<<grid, TC_THREADS, smem, s>>>(Aimg, Bimg, rows, (int)cols, ksteps, kc, nst, out, vec_ok,
+                                                 rowmajor, P->d_status);
   TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }

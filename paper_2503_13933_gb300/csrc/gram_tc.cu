@@ -37,6 +37,7 @@
 #define GT_MAXN 64     // modes and source terms of an item (each rounded up to 16)
 #define GT_MAXOPS 4    // distinct operators of a dim
 #define GT_SPIN (1u << 24)
+#define GT_UNR 8       // loads in flight per thread
 
 struct GtItem {
   const double* U;      // n x M, column-major (FP64 master)
@@ -145,26 +146,50 @@ __device__ bool gt_task(const GtItem& it, int c0, int c1, const GtLayout& L, uns
   float* Us = reinterpret_cast<float*>(Bq + L.NH * ROWS);
   float* Bd = Us + (ROWS + 2 * TAPS_MAX_S * 2 + 2) * (L.N + 1);
   const int ld = M + 1;
+  // one index space over the chunk's loads: factor rows r0 - hb .. r0 + ROWS + hb (all
+  // modes), band rows r0 .. r0 + ROWS (all operators), source rows (all terms); each
+  // thread issues GT_UNR loads before it converts and stores any, so that a chunk's
+  // ~60 KB are in flight together
+  const int nU = RW * M, nBd = nops * ROWS * nb, nQ = NH * ROWS, nAll = nU + nBd + nQ;
   for (int c = c0; c < c1; ++c) {
     const int r0 = c * ROWS;
-    // factor rows r0 - hb .. r0 + ROWS + hb (zero outside the dim) as FP32 values of
-    // their bfloat16 rounding, and the chunk's rows as the A operand (U^T)
-    for (int idx = tid; idx < RW * M; idx += nt) {
-      const int m = idx / RW, j = idx - m * RW;
-      const int g = r0 - hb + j;
-      const __nv_bfloat16 v = (g >= 0 && g < n) ? gt_bf(__ldg(it.U + (size_t)m * n + g)) : __float2bfloat16_rn(0.f);
-      Us[j * ld + m] = __bfloat162float(v);
-      if (j >= hb && j < hb + ROWS) A[gt_off(128, m, j - hb)] = v;
-    }
-    for (int idx = tid; idx < nops * ROWS * nb; idx += nt) {
-      const int o = idx / (ROWS * nb), rem = idx - o * (ROWS * nb);
-      const int g = r0 + rem / nb;
-      Bd[idx] = g < n ? __bfloat162float(gt_bf(__ldg(it.band + ((size_t)o * n + r0) * nb + rem))) : 0.f;
-    }
-    for (int idx = tid; idx < NH * ROWS; idx += nt) {
-      const int r = idx / ROWS, i = idx - r * ROWS;
-      const int g = r0 + i;
-      Bq[gt_off(NH, r, i)] = (r < Rf && g < n) ? gt_bf(__ldg(it.q + (size_t)r * n + g)) : __float2bfloat16_rn(0.f);
+    for (int base = 0; base < nAll; base += nt * GT_UNR) {
+      double v[GT_UNR];
+#pragma unroll
+      for (int u = 0; u < GT_UNR; ++u) {
+        const int idx = base + u * nt + tid;
+        double x = 0.0;
+        if (idx < nU) {
+          const int m = idx / RW, j = idx - m * RW;
+          const int g = r0 - hb + j;
+          if (g >= 0 && g < n) x = __ldg(it.U + (size_t)m * n + g);
+        } else if (idx < nU + nBd) {
+          const int e = idx - nU;
+          const int o = e / (ROWS * nb), rem = e - o * (ROWS * nb);
+          if (r0 + rem / nb < n) x = __ldg(it.band + ((size_t)o * n + r0) * nb + rem);
+        } else if (idx < nAll) {
+          const int e = idx - nU - nBd;
+          const int r = e / ROWS, i = e - r * ROWS;
+          if (r < Rf && r0 + i < n) x = __ldg(it.q + (size_t)r * n + r0 + i);
+        }
+        v[u] = x;
+      }
+#pragma unroll
+      for (int u = 0; u < GT_UNR; ++u) {
+        const int idx = base + u * nt + tid;
+        const __nv_bfloat16 b = gt_bf(v[u]);
+        if (idx < nU) {
+          const int m = idx / RW, j = idx - m * RW;
+          Us[j * ld + m] = __bfloat162float(b);
+          if (j >= hb && j < hb + ROWS) A[gt_off(128, m, j - hb)] = b;
+        } else if (idx < nU + nBd) {
+          Bd[idx - nU] = __bfloat162float(b);
+        } else if (idx < nAll) {
+          const int e = idx - nU - nBd;
+          const int r = e / ROWS, i = e - r * ROWS;
+          Bq[gt_off(NH, r, i)] = b;
+        }
+      }
     }
     __syncthreads();
     // Y_o = Op_o U for the chunk's rows (FP32), split into two bfloat16 parts

@@ -447,12 +447,14 @@ class Batch:
               "taps_batch_refresh_grams")
         return ms.value, by.value
 
+    GRAM_TILES = [(64, 1), (64, 2), (64, 3), (64, 4), (128, 1), (128, 2)]
+
     def gram_info(self):
-        """(chunk rows, CTAs per SM, trial ms of (64,1), (64,2), (128,1), (128,2))."""
+        """(chunk rows, CTAs per SM, trial ms of each (rows, CTAs per SM) in GRAM_TILES)."""
         r, c = ctypes.c_int(), ctypes.c_int()
-        t = (ctypes.c_float * 4)()
+        t = (ctypes.c_float * 6)()
         check(lib().taps_batch_gram_info(self.handle, ctypes.byref(r), ctypes.byref(c), t), "taps_batch_gram_info")
-        return r.value, c.value, [t[k] for k in range(4)]
+        return r.value, c.value, [t[k] for k in range(6)]
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:

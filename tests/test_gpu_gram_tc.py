@@ -115,7 +115,7 @@ def test_batched_tensor_core_refresh(T):
     print(f"batched BF16 refresh: {ms:.3f} ms, {by / 1e6:.1f} MB, tile rows {rows}, CTAs/SM {cps}, table {table}")
     assert rows in (64, 128) and cps in (1, 2) and ms > 0 and by > 0
     timed = [t for t in table if t > 0]
-    assert timed and min(timed) == table[[64, 64, 128, 128].index(rows) + (cps - 1)]
+    assert timed and min(timed) == table[T.Batch.GRAM_TILES.index((rows, cps))]
     for P, U0, M in zip(probs, inits, Ms):
         for d in range(P.D):
             check_dim(T, P, U0, d, M, NAMES)
