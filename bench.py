@@ -388,6 +388,30 @@ def run_config5(args, taps, W, torch, stream, hbm_peak):
                                   ms_per_sweep=float(np.mean(ts)) / max(rep["sweeps"], 1),
                                   rho42=rep["rho"], rho_full=rho_full, converged=rep["converged"],
                                   rho42_history=[h[2] for h in rep["history"]])
+    # the Eq. 42 residual over 40 fixed-M sweeps from the same start: where it levels off
+    # (the reason the target here is 1e-3, not 1e-6), with the full residual at the end
+    flush.zero_()
+    r40 = P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=40, init=taps.INIT_RANDOM, seed=C5["seed"],
+                  als_tol=0.0, solver=taps.SOLVER_FASTDIAG)
+    out["fixed_M_40_sweeps"] = dict(rho42_history=[h[2] for h in r40["history"]], rho_full=r40["rho_full"],
+                                    seconds=r40["seconds"])
+    # the greedy schedule on the full residual: 4 modes per growth step from 4, up to 3
+    # sweeps per mode count, stopping at M = 100 or once rho_full improves by less than
+    # 1% over two mode counts
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rg = P.solve(U, M0=4, M_max=M, res_tol=1e-6, res_kind=taps.RES_FULL, max_sweeps=3, init=taps.INIT_RANDOM,
+                 seed=C5["seed"], als_tol=1e-2, solver=taps.SOLVER_FASTDIAG, res_stall=0.01, M_step=4)
+    torch.cuda.synchronize()
+    ends = {}
+    for Mh, ch, rho in rg["history"]:
+        ends[Mh] = rho
+    out["greedy_rho_full"] = dict(seconds=time.perf_counter() - t0, M=rg["M"], sweeps=rg["sweeps"],
+                                  rho_full=rg["rho_full"], rho_full_per_M={int(k): v for k, v in ends.items()},
+                                  rho42=P.residual(U, taps.RES_ALS),
+                                  rule="modes +4 per step, <= 3 sweeps each, stop at M = 100 or on < 1% "
+                                       "improvement of rho_full over two mode counts")
     # per-class breakdown of the timed path (events around every class, separate runs)
     run(taps.FP64, taps.INIT_RANDOM)
     P.profile_reset(events=True)

@@ -196,6 +196,11 @@ typedef struct {
                           residual and the stopping test (FP64 / MIXED with the Eq. 42
                           residual and profiling events off; otherwise as 1); the same
                           sweeps and factors as 1, without a host round trip per sweep */
+  double res_stall;    /* greedy stop on stagnation: growth ends once the residual (kind
+                          res_kind) at the end of a mode count exceeds (1 - res_stall) times
+                          its value at the end of the previous mode count, two mode counts
+                          in a row (0: off) */
+  int M_step;          /* modes appended per growth step of the greedy schedule (0 or 1: one) */
 } taps_solve_opts;
 
 typedef struct {
@@ -321,8 +326,9 @@ int taps_residual(taps_problem* prob, const taps_factors* U, int kind, double* r
 
 /* ---- solve: greedy mode schedule M0..M_max with sweeps to tolerance ----------------
  * For each M: sweep until rho (kind res_kind) <= res_tol or the factor change <=
- * als_tol or max_sweeps; then stop if rho <= res_tol, else append one column per
- * factor (init rule) and continue.  With precision TAPS_FP32 the sweeps use FP32
+ * als_tol or max_sweeps; then stop if rho <= res_tol (or, with res_stall > 0, once rho
+ * has stagnated over two mode counts), else append M_step columns per factor (init
+ * rule, at most up to M_max) and continue.  With precision TAPS_FP32 the sweeps use FP32
  * Grams; once the FP32 sweeps stop improving, up to polish_sweeps FP64 sweeps
  * refine the result to FP64 accuracy.  U must have M_cap >= M_max; with init
  * TAPS_INIT_GIVEN its current M columns are the start (M0 is then ignored), else it

@@ -705,16 +705,20 @@ class SolveResult:
 
 
 def solve(prob: Problem, M0=1, M_max=8, als_tol=1e-10, res_tol=1e-6, max_sweeps=200,
-          init="zero", seed=0, solver="banded", U0=None):
-    """Run Algorithm 1 for M = M0..M_max modes, adding one column per step.
+          init="zero", seed=0, solver="banded", U0=None, res_stall=0.0, M_step=1):
+    """Run Algorithm 1 for M = M0..M_max modes, adding M_step columns per step.
     At each M, sweep until the factor change <= als_tol or rho <= res_tol (or
-    max_sweeps); stop growing M once rho <= res_tol."""
+    max_sweeps); stop growing M once rho <= res_tol, or (res_stall > 0) once rho at the
+    end of a mode count has been above (1 - res_stall) times its value at the end of the
+    previous mode count for two mode counts in a row (the greedy schedule's stop on
+    stagnation, reading O6)."""
     if U0 is not None:
         U = [u.copy() for u in U0]
     else:
         U = init_factors(prob, M0, init, seed)
     res = SolveResult(U=U)
     M = U[0].shape[1]
+    rho_prev, stalls = math.inf, 0
     while True:
         for it in range(max_sweeps):
             U, change = sweep(prob, U, solver)
@@ -728,9 +732,15 @@ def solve(prob: Problem, M0=1, M_max=8, als_tol=1e-10, res_tol=1e-6, max_sweeps=
             return res
         if M >= M_max:
             return res
-        U = [np.concatenate([U[d], init_column(prob, d, M, init, seed)[:, None]], axis=1)
+        if res_stall > 0.0:
+            stalls = stalls + 1 if not rho <= (1.0 - res_stall) * rho_prev else 0
+            rho_prev = rho
+            if stalls >= 2:
+                return res
+        Mn = min(M_max, M + max(1, M_step))
+        U = [np.concatenate([U[d]] + [init_column(prob, d, m, init, seed)[:, None] for m in range(M, Mn)], axis=1)
              for d in range(prob.D)]
-        M += 1
+        M = Mn
 
 
 # ---------------------------------------------------------------------------------

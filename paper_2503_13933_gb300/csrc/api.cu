@@ -1018,6 +1018,17 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
   int sweeps = 0, fp64_sweeps = 0, polish_left = o->polish_sweeps, hist = 0;
   double rho = INFINITY, change = INFINITY;
   bool converged = false;
+  const int step = o->M_step > 0 ? o->M_step : 1;
+  double rho_prev_M = INFINITY;   // residual at the end of the previous mode count
+  int stalls = 0;
+  // end of a mode count: true when the greedy growth stops on stagnation
+  auto stalled = [&]() {
+    if (!(o->res_stall > 0.0)) return false;
+    const bool st = !(rho <= (1.0 - o->res_stall) * rho_prev_M);
+    stalls = st ? stalls + 1 : 0;
+    rho_prev_M = rho;
+    return stalls >= 2;
+  };
   while (true) {
     double prev_rho = INFINITY;
     int prec = precision;
@@ -1042,9 +1053,10 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
         }
         TAPS_TRY(lst);
         if (rho <= o->res_tol) converged = true;
-        if (converged || M >= o->M_max) break;
-        TAPS_TRY(init_columns(P, U, M, M + 1, add_kind, o->seed));
-        U->M = ++M;
+        if (converged || M >= o->M_max || stalled()) break;
+        const int Mn = std::min(o->M_max, M + step);
+        TAPS_TRY(init_columns(P, U, M, Mn, add_kind, o->seed));
+        U->M = M = Mn;
         TAPS_TRY(taps_refresh_grams(P, U, precision));
         continue;
       }
@@ -1105,9 +1117,10 @@ extern "C" int taps_solve(taps_problem* P, taps_factors* U, const taps_solve_opt
       }
       prev_rho = rho;
     }
-    if (converged || M >= o->M_max) break;
-    TAPS_TRY(init_columns(P, U, M, M + 1, add_kind, o->seed));
-    U->M = ++M;
+    if (converged || M >= o->M_max || stalled()) break;
+    const int Mn = std::min(o->M_max, M + step);
+    TAPS_TRY(init_columns(P, U, M, Mn, add_kind, o->seed));
+    U->M = M = Mn;
     TAPS_TRY(taps_refresh_grams(P, U, precision));
   }
   double rho_full = rho;

@@ -67,7 +67,8 @@ class SolveOpts(ctypes.Structure):
                 ("res_tol", ctypes.c_double), ("res_kind", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("precision", ctypes.c_int),
                 ("polish_sweeps", ctypes.c_int), ("solver", ctypes.c_int), ("init", ctypes.c_int),
-                ("seed", ctypes.c_uint), ("history_cap", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("seed", ctypes.c_uint), ("history_cap", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("res_stall", ctypes.c_double), ("M_step", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -342,11 +343,12 @@ class Problem:
 
     def solve(self, U, M0=1, M_max=8, als_tol=1e-10, res_tol=1e-6, res_kind=RES_ALS,
               max_sweeps=200, precision=FP64, polish_sweeps=20, init=INIT_ZERO, seed=0,
-              history_cap=4096, raise_not_converged=False, solver=SOLVER_BLOCK_LU, graphs=True):
+              history_cap=4096, raise_not_converged=False, solver=SOLVER_BLOCK_LU, graphs=True,
+              res_stall=0.0, M_step=1):
         o = SolveOpts(M0=M0, M_max=M_max, als_tol=als_tol, res_tol=res_tol, res_kind=res_kind,
                       max_sweeps=max_sweeps, precision=precision, polish_sweeps=polish_sweeps,
                       solver=solver, init=init, seed=seed, history_cap=history_cap,
-                      graphs=int(graphs))
+                      graphs=int(graphs), res_stall=res_stall, M_step=M_step)
         hM = (ctypes.c_int * max(history_cap, 1))()
         hc = (ctypes.c_double * max(history_cap, 1))()
         hr = (ctypes.c_double * max(history_cap, 1))()

@@ -596,3 +596,26 @@ def test_small_solve_reciprocal_within_one_ulp(T):
     assert np.all(np.abs(y - r) <= ulp)
     pow2 = np.isin(x, 2.0 ** np.arange(-1000, 1001, 7))
     assert np.array_equal(y[pow2], r[pow2])
+
+
+def test_greedy_full_residual_schedule_matches_oracle(T):
+    """The greedy schedule on the full residual with two modes per growth step and the
+    stagnation rule armed (space-parameter problem, 12^3 x 8): the GPU's mode counts,
+    the residual at the end of each of them, and the final field equal the oracle's."""
+    desc = W.poisson_k(n_space=12, n_k=8, seed=2060)
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U = P.factors(20)
+    rep = P.solve(U, M0=1, M_max=11, als_tol=1e-6, res_tol=1e-12, res_kind=T.RES_FULL, max_sweeps=30,
+                  init=T.INIT_RANDOM, seed=3, solver=T.SOLVER_FASTDIAG, res_stall=0.01, M_step=2)
+    ro = O.solve(Po, M0=1, M_max=11, als_tol=1e-6, res_tol=1e-12, max_sweeps=30, init="random", seed=3,
+                 solver="fastdiag", res_stall=0.01, M_step=2)
+    ends_g, ends_o = {}, {}
+    for M, ch, rho in rep["history"]:
+        ends_g[M] = rho
+    for M, it, ch, rho in ro.history:
+        ends_o[M] = rho
+    assert list(ends_g) == list(ends_o) == [1, 3, 5, 7, 9, 11]
+    for M in ends_o:
+        assert abs(ends_g[M] - ends_o[M]) <= 1e-6 * ends_o[M], (M, ends_g[M], ends_o[M])
+    assert O.cp_change(ro.U, U.get()) <= 1e-8

@@ -329,3 +329,24 @@ def test_product_lifting_helper_matches_oracle_reading():
             assert np.array_equal(va, vb)
     with pytest.raises(ValueError):
         B.lifting_sources(desc, [v[1:-1] for v in vecs], wts)   # free nodes only: rejected
+
+
+def test_greedy_stops_on_stagnation(monkeypatch):
+    """The greedy schedule's stop on stagnation (res_stall): with the residual at the end
+    of the mode counts 1, 2, 3, ... forced to 0.5, 0.3, 0.2995, 0.299, 0.1, ... growth
+    stops after the second mode count in a row that improved it by less than 1% (M = 4),
+    and M_step appends that many columns per growth step."""
+    desc = W.poisson_sin(14, D=2)
+    rng = np.random.default_rng(3)
+    desc["sources"] = [(1.0, [("nodal", rng.uniform(-1, 1, 14)) for _ in range(2)]) for _ in range(10)]
+    P = O.problem_from_description(desc)
+    seq = iter([0.5, 0.3, 0.2995, 0.299, 0.1, 0.05])
+    monkeypatch.setattr(O, "residual", lambda prob, U: (next(seq), 0.0, 0.0, 0.0))
+    r = O.solve(P, M0=1, M_max=8, als_tol=1.0, res_tol=0.0, max_sweeps=1, init="random", seed=2,
+                res_stall=0.01)
+    assert [h[0] for h in r.history] == [1, 2, 3, 4] and not r.converged
+    seq = iter([0.5, 0.3, 0.2995, 0.299, 0.1, 0.05])
+    r = O.solve(P, M0=1, M_max=8, als_tol=1.0, res_tol=0.0, max_sweeps=1, init="random", seed=2,
+                res_stall=0.01, M_step=3)
+    assert [h[0] for h in r.history] == [1, 4, 7, 8]
+    assert r.U[0].shape[1] == 8
