@@ -132,10 +132,19 @@ struct GtLayout {   // shared-memory carve-up of one launch (element offsets, bf
 
 // One task: chunks [c0, c1) of item `it` accumulated into TMEM at `tmem`.  Returns false
 // after a timeout (the status word is set).
+//
+// Operand build of a chunk, division-free: warp w loads the factor rows of modes
+// w, w + 8, ... (lane = row, coalesced along the column; 4 modes per pass), every
+// thread loads its share
+// of the chunk's band rows (one contiguous run per operator) and source rows, all loads
+// of a thread issued before any is converted; the banded product is formed by thread
+// (operator, row, slice of modes) with the row's band entries in registers.
+#define GT_RPL(ROWS) (((ROWS) + 2 * (2 * TAPS_MAX_S + 1) + 31) / 32)   // factor rows per lane
 template <int ROWS>
 __device__ bool gt_task(const GtItem& it, int c0, int c1, const GtLayout& L, unsigned char* sm, uint32_t tmem,
                         uint64_t* mma_bar, uint32_t& phase, int* status) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  constexpr int RPL = GT_RPL(ROWS);
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
   const int M = it.M, n = it.n, hb = it.hb, nb = 2 * hb + 1, nops = it.nops, Rf = it.Rf;
   const int N = (M + 15) & ~15, NH = (Rf + 15) & ~15;
   const int RW = ROWS + 2 * hb;
@@ -146,66 +155,98 @@ __device__ bool gt_task(const GtItem& it, int c0, int c1, const GtLayout& L, uns
   float* Us = reinterpret_cast<float*>(Bq + L.NH * ROWS);
   float* Bd = Us + (ROWS + 2 * TAPS_MAX_S * 2 + 2) * (L.N + 1);
   const int ld = M + 1;
-  // one index space over the chunk's loads: factor rows r0 - hb .. r0 + ROWS + hb (all
-  // modes), band rows r0 .. r0 + ROWS (all operators), source rows (all terms); each
-  // thread issues GT_UNR loads before it converts and stores any, so that a chunk's
-  // ~60 KB are in flight together
-  const int nU = RW * M, nBd = nops * ROWS * nb, nQ = NH * ROWS, nAll = nU + nBd + nQ;
+  const int nBd = nops * ROWS * nb;       // band entries of the chunk (all operators)
+  const int nQ = NH * ROWS;               // source entries (padded terms)
+  // mode slices of the banded product: thread (operator, row, slice)
+  const int pairs = nops * ROWS;
+  const int slices = pairs >= nt ? 1 : nt / pairs;
+  const int per = (M + slices - 1) / slices;
   for (int c = c0; c < c1; ++c) {
     const int r0 = c * ROWS;
-    for (int base = 0; base < nAll; base += nt * GT_UNR) {
-      double v[GT_UNR];
+    const int rows_left = n - r0;          // rows of the chunk inside the dim
+    // ---- loads: factor rows (8 modes per pass), band runs, source rows
+    for (int m0 = warp; m0 < M; m0 += 8 * 4) {
+      double v[4][RPL];
 #pragma unroll
-      for (int u = 0; u < GT_UNR; ++u) {
-        const int idx = base + u * nt + tid;
-        double x = 0.0;
-        if (idx < nU) {
-          const int m = idx / RW, j = idx - m * RW;
+      for (int a = 0; a < 4; ++a) {
+        const int m = m0 + 8 * a;
+#pragma unroll
+        for (int b = 0; b < RPL; ++b) {
+          const int j = lane + 32 * b;
           const int g = r0 - hb + j;
-          if (g >= 0 && g < n) x = __ldg(it.U + (size_t)m * n + g);
-        } else if (idx < nU + nBd) {
-          const int e = idx - nU;
-          const int o = e / (ROWS * nb), rem = e - o * (ROWS * nb);
-          if (r0 + rem / nb < n) x = __ldg(it.band + ((size_t)o * n + r0) * nb + rem);
-        } else if (idx < nAll) {
-          const int e = idx - nU - nBd;
-          const int r = e / ROWS, i = e - r * ROWS;
-          if (r < Rf && r0 + i < n) x = __ldg(it.q + (size_t)r * n + r0 + i);
+          v[a][b] = (m < M && j < RW && g >= 0 && g < n) ? __ldg(it.U + (size_t)m * n + g) : 0.0;
         }
-        v[u] = x;
       }
 #pragma unroll
-      for (int u = 0; u < GT_UNR; ++u) {
-        const int idx = base + u * nt + tid;
-        const __nv_bfloat16 b = gt_bf(v[u]);
-        if (idx < nU) {
-          const int m = idx / RW, j = idx - m * RW;
-          Us[j * ld + m] = __bfloat162float(b);
-          if (j >= hb && j < hb + ROWS) A[gt_off(128, m, j - hb)] = b;
-        } else if (idx < nU + nBd) {
-          Bd[idx - nU] = __bfloat162float(b);
-        } else if (idx < nAll) {
-          const int e = idx - nU - nBd;
-          const int r = e / ROWS, i = e - r * ROWS;
-          Bq[gt_off(NH, r, i)] = b;
+      for (int a = 0; a < 4; ++a) {
+        const int m = m0 + 8 * a;
+        if (m >= M) continue;
+#pragma unroll
+        for (int b = 0; b < RPL; ++b) {
+          const int j = lane + 32 * b;
+          if (j >= RW) continue;
+          const __nv_bfloat16 x = gt_bf(v[a][b]);
+          Us[j * ld + m] = __bfloat162float(x);
+          const int i = j - hb;
+          if (i >= 0 && i < ROWS) A[gt_off(128, m, i)] = x;
+        }
+      }
+    }
+    {
+      constexpr int PB = 8;
+      for (int e0 = tid; e0 < nBd + nQ; e0 += nt * PB) {
+        double v[PB];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          const int e = e0 + u * nt;
+          double x = 0.0;
+          if (e < nBd) {
+            const int o = e / (ROWS * nb), rem = e - o * (ROWS * nb);   // once per entry
+            if (rem < rows_left * nb) x = __ldg(it.band + ((size_t)o * n + r0) * nb + rem);
+          } else if (e < nBd + nQ) {
+            const int f = e - nBd, r = f / ROWS, i = f - r * ROWS;        // ROWS: a power of 2
+            if (r < Rf && i < rows_left) x = __ldg(it.q + (size_t)r * n + r0 + i);
+          }
+          v[u] = x;
+        }
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          const int e = e0 + u * nt;
+          if (e < nBd) {
+            Bd[e] = __bfloat162float(gt_bf(v[u]));
+          } else if (e < nBd + nQ) {
+            const int f = e - nBd, r = f / ROWS, i = f - r * ROWS;
+            Bq[gt_off(NH, r, i)] = gt_bf(v[u]);
+          }
         }
       }
     }
     __syncthreads();
-    // Y_o = Op_o U for the chunk's rows (FP32), split into two bfloat16 parts
-    for (int idx = tid; idx < nops * N * ROWS; idx += nt) {
-      const int o = idx / (N * ROWS), rem = idx - o * (N * ROWS);
-      const int nn = rem / ROWS, i = rem - nn * ROWS;
-      float y = 0.f;
-      if (nn < M) {
-        const float* brow = Bd + (o * ROWS + i) * nb;
-        const float* ucol = Us + i * ld + nn;
-        for (int k = 0; k < nb; ++k) y = fmaf(brow[k], ucol[k * ld], y);
+    // ---- Y_o = Op_o U for the chunk's rows (FP32), split into two bfloat16 parts
+    for (int t = tid; t < pairs * slices; t += nt) {
+      const int i = t % ROWS, rest = t / ROWS;
+      const int o = rest % nops, sl = rest / nops;
+      float br[2 * (2 * TAPS_MAX_S + 1) + 1];
+      const float* brow = Bd + (o * ROWS + i) * nb;
+#pragma unroll
+      for (int k = 0; k < 2 * (2 * TAPS_MAX_S + 1) + 1; ++k) br[k] = k < nb ? brow[k] : 0.f;
+      const int n0 = sl * per, n1 = min(N, n0 + per + (sl == slices - 1 ? N : 0));
+      __nv_bfloat16* bh = B + (2 * o) * N * ROWS;
+      __nv_bfloat16* bl = B + (2 * o + 1) * N * ROWS;
+      for (int nn = n0; nn < n1; ++nn) {
+        float y = 0.f;
+        if (nn < M) {
+          const float* ucol = Us + i * ld + nn;
+#pragma unroll
+          for (int k = 0; k < 2 * (2 * TAPS_MAX_S + 1) + 1; ++k)
+            if (k < nb) y = fmaf(br[k], ucol[k * ld], y);
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(y - __bfloat162float(hi));
+        const int off = gt_off(N, nn, i);
+        bh[off] = hi;
+        bl[off] = lo;
       }
-      const __nv_bfloat16 hi = __float2bfloat16_rn(y);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(y - __bfloat162float(hi));
-      B[(2 * o) * N * ROWS + gt_off(N, nn, i)] = hi;
-      B[(2 * o + 1) * N * ROWS + gt_off(N, nn, i)] = lo;
     }
     // the generic-proxy writes above become visible to the tensor cores' async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
