@@ -74,7 +74,7 @@ extern "C" {
  * A dim with weighted operators is solved by block elimination. */
 #define TAPS_OP_WEIGHTED 16
 #define TAPS_MAX_WEIGHTED 64   /* weighted operators per dim */
-#define TAPS_MAX_SLOTS 40      /* distinct operators (plain and weighted) per dim */
+#define TAPS_MAX_SLOTS 72      /* distinct operators (plain and weighted) per dim */
 
 /* ---- source factor kinds g(x) of a separable source term -------------------- */
 #define TAPS_SRC_CONST 0  /* par[0]                                       */

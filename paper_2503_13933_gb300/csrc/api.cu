@@ -1412,6 +1412,8 @@ struct taps_batch {
   // (chunk rows, CTAs per SM) of the tuner and its trial times
   void* gt_buf;
   size_t gt_buf_bytes;
+  double* gt_partial;
+  size_t gt_partial_len;
   unsigned* gt_tickets;
   int gt_items_cap;
   int gt_rows, gt_cps, gt_tuned;
@@ -1422,6 +1424,7 @@ extern "C" void taps_batch_destroy(taps_batch* B) {
   if (!B) return;
   if (B->master) cudaStreamSynchronize(B->master);
   if (B->gt_buf) cudaFree(B->gt_buf);
+  if (B->gt_partial) cudaFree(B->gt_partial);
   if (B->gt_tickets) cudaFree(B->gt_tickets);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->g) cudaGraphDestroy(B->g);
@@ -1673,6 +1676,7 @@ extern "C" int taps_batch_sweep(taps_batch* B, int n_sweeps, int graphs, double*
 // (tensor cores, BF16 operands) or instance by instance (FP64, CUDA cores).
 // ---------------------------------------------------------------------------------
 #define GT_CAND 6
+#define GT_CPT 8   // chunks per task of the batched Gram refresh
 static const int kGtRows[GT_CAND] = {64, 64, 64, 64, 128, 128};
 static const int kGtCps[GT_CAND] = {1, 2, 3, 4, 1, 2};
 
@@ -1680,7 +1684,7 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
   if (!B || (precision != TAPS_FP64 && precision != TAPS_BF16)) return TAPS_ERR_INVALID_ARG;
   std::vector<GtHostItem> items;
   int maxN = 16, maxNH = 16, maxops = 1;
-  size_t chunks64 = 0;
+  size_t chunks64 = 0, partial_need = 0;
   double bytes = 0.0;
   for (int i = 0; i < B->count; ++i) {
     taps_problem* P = B->P[i];
@@ -1704,6 +1708,9 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
       maxNH = std::max(maxNH, (h.Rf + 15) & ~15);
       maxops = std::max(maxops, h.nops);
       chunks64 += (size_t)(h.n + 63) / 64;
+      // partial sums of an item split over tasks of GT_CPT chunks (64-node chunks: the most tasks)
+      const size_t tasks64 = ((size_t)(h.n + 63) / 64 + GT_CPT - 1) / GT_CPT;
+      if (tasks64 > 1) partial_need += tasks64 * ((size_t)h.nops * h.M * h.M + (size_t)h.Rf * h.M);
       const int nb = 2 * h.hb + 1;
       bytes += 8.0 * ((double)h.n * h.M + (double)h.nops * h.n * nb + (double)h.Rf * h.n +
                       (double)h.nops * h.M * h.M + (double)h.Rf * h.M);
@@ -1741,6 +1748,13 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
         if ((st = taps_alloc(&B->gt_buf, need)) != TAPS_OK) break;
         B->gt_buf_bytes = need;
       }
+      if (partial_need > B->gt_partial_len) {
+        if (B->gt_partial) cudaFree(B->gt_partial);
+        B->gt_partial = nullptr;
+        B->gt_partial_len = 0;
+        if ((st = taps_alloc((void**)&B->gt_partial, sizeof(double) * partial_need)) != TAPS_OK) break;
+        B->gt_partial_len = partial_need;
+      }
       if ((int)items.size() > B->gt_items_cap) {
         if (B->gt_tickets) cudaFree(B->gt_tickets);
         B->gt_tickets = nullptr;
@@ -1753,8 +1767,9 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
         B->gt_items_cap = (int)items.size();
       }
       int* status = B->P[0]->d_status;
-      // one task per item (the whole dim in one CTA): no partials; the tuner times the
-      // chunk height and the CTAs per SM the shared memory and TMEM allow
+      // tasks of GT_CPT chunks (a dim of more than GT_CPT chunks is split, its partial
+      // sums added in task order by its last task); the tuner times the chunk height and
+      // the CTAs per SM the shared memory and TMEM allow
       if (!B->gt_tuned) {
         int maxsm = 0, dev = 0;
         cudaGetDevice(&dev);
@@ -1766,8 +1781,9 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
           taps_gram_tc_footprint(kGtRows[k], maxN, maxNH, maxops, &smem, &ncols);
           B->gt_table[k] = -1.f;
           if ((size_t)kGtCps[k] * (smem + 1024) > (size_t)maxsm || kGtCps[k] * ncols > 512) continue;
-          st = taps_gram_tc_queue(items, kGtRows[k], 1 << 20, dev_sms * kGtCps[k], B->gt_buf, B->gt_buf_bytes,
-                                  nullptr, 0, B->gt_tickets, B->master, status, nullptr, nullptr, e0, e1);
+          st = taps_gram_tc_queue(items, kGtRows[k], GT_CPT, dev_sms * kGtCps[k], B->gt_buf, B->gt_buf_bytes,
+                                  B->gt_partial, B->gt_partial_len, B->gt_tickets, B->master, status, nullptr,
+                                  nullptr, e0, e1);
           if (st != TAPS_OK) break;
           float t = 0.f;
           cudaEventElapsedTime(&t, e0, e1);
@@ -1781,8 +1797,9 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
         if (st != TAPS_OK) break;
         B->gt_tuned = 1;
       }
-      st = taps_gram_tc_queue(items, B->gt_rows, 1 << 20, dev_sms * B->gt_cps, B->gt_buf, B->gt_buf_bytes, nullptr,
-                              0, B->gt_tickets, B->master, status, nullptr, nullptr, e0, e1);
+      st = taps_gram_tc_queue(items, B->gt_rows, GT_CPT, dev_sms * B->gt_cps, B->gt_buf, B->gt_buf_bytes,
+                              B->gt_partial, B->gt_partial_len, B->gt_tickets, B->master, status, nullptr, nullptr,
+                              e0, e1);
       if (st != TAPS_OK) break;
     }
     if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -155,7 +155,6 @@ __device__ bool gt_task(const GtItem& it, int c0, int c1, const GtLayout& L, uns
   float* Us = reinterpret_cast<float*>(Bq + L.NH * ROWS);
   float* Bd = Us + (ROWS + 2 * TAPS_MAX_S * 2 + 2) * (L.N + 1);
   const int ld = M + 1;
-  const int nBd = nops * ROWS * nb;       // band entries of the chunk (all operators)
   const int nQ = NH * ROWS;               // source entries (padded terms)
   // mode slices of the banded product: thread (operator, row, slice)
   const int pairs = nops * ROWS;
@@ -193,31 +192,37 @@ __device__ bool gt_task(const GtItem& it, int c0, int c1, const GtLayout& L, uns
       }
     }
     {
-      constexpr int PB = 8;
-      for (int e0 = tid; e0 < nBd + nQ; e0 += nt * PB) {
-        double v[PB];
+      // band rows: one contiguous run of ROWS * nb entries per operator (the chunk's
+      // rows inside the dim loaded, the rest zero); source rows: NH x ROWS
+      constexpr int BPT = (ROWS * (2 * (2 * TAPS_MAX_S + 1) + 1) + GT_THREADS - 1) / GT_THREADS;
+      const int run = ROWS * nb, runv = min(rows_left, ROWS) * nb;
+      for (int o = 0; o < nops; ++o) {
+        const double* src = it.band + ((size_t)o * n + r0) * nb;
+        double v[BPT];
 #pragma unroll
-        for (int u = 0; u < PB; ++u) {
-          const int e = e0 + u * nt;
-          double x = 0.0;
-          if (e < nBd) {
-            const int o = e / (ROWS * nb), rem = e - o * (ROWS * nb);   // once per entry
-            if (rem < rows_left * nb) x = __ldg(it.band + ((size_t)o * n + r0) * nb + rem);
-          } else if (e < nBd + nQ) {
-            const int f = e - nBd, r = f / ROWS, i = f - r * ROWS;        // ROWS: a power of 2
-            if (r < Rf && i < rows_left) x = __ldg(it.q + (size_t)r * n + r0 + i);
-          }
-          v[u] = x;
+        for (int u = 0; u < BPT; ++u) {
+          const int e = tid + u * GT_THREADS;
+          v[u] = e < runv ? __ldg(src + e) : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < PB; ++u) {
-          const int e = e0 + u * nt;
-          if (e < nBd) {
-            Bd[e] = __bfloat162float(gt_bf(v[u]));
-          } else if (e < nBd + nQ) {
-            const int f = e - nBd, r = f / ROWS, i = f - r * ROWS;
-            Bq[gt_off(NH, r, i)] = gt_bf(v[u]);
-          }
+        for (int u = 0; u < BPT; ++u) {
+          const int e = tid + u * GT_THREADS;
+          if (e < run) Bd[o * run + e] = __bfloat162float(gt_bf(v[u]));
+        }
+      }
+      constexpr int QPT = 4;
+      for (int f0 = tid; f0 < nQ; f0 += GT_THREADS * QPT) {
+        double v[QPT];
+#pragma unroll
+        for (int u = 0; u < QPT; ++u) {
+          const int f = f0 + u * GT_THREADS;
+          const int r = f / ROWS, i = f % ROWS;
+          v[u] = (f < nQ && r < Rf && i < rows_left) ? __ldg(it.q + (size_t)r * n + r0 + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < QPT; ++u) {
+          const int f = f0 + u * GT_THREADS;
+          if (f < nQ) Bq[gt_off(NH, f / ROWS, f % ROWS)] = gt_bf(v[u]);
         }
       }
     }

@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
   __shared__ double linv[TAPS_MAX_M];
   __shared__ double rc[TAPS_MAX_M / 2], rs[TAPS_MAX_M / 2];
   __shared__ int rp[TAPS_MAX_M / 2], rq[TAPS_MAX_M / 2];
+  __shared__ float rcf[TAPS_MAX_M / 2], rsf[TAPS_MAX_M / 2];
   __shared__ int rotated, failed;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int Np = M + (M & 1), ld = Np + 1;
@@ -324,13 +325,22 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
   double* T = gw + 2 * MM;   // row-major temporary
   double* Pw = gw + 3 * MM;  // row-major previous basis (identity when cold)
 #define SB(i, j) Ssh[(size_t)(i) * ld + (j)]
-  const bool warm = (*wM == M);
+  const bool warm0 = (*wM == M);
   if (tid == 0) failed = 0;
+  // With V in shared memory a first pass of FP32 rotations (the FP64 pipe of one SM
+  // bounds FP64 rounds: ~4 flop per cycle) finds the basis P <- P L^-T V_32 of the
+  // (previous-basis-transformed, when warm) pencil; the FP64 pass then starts from that
+  // basis, and its rotations finish in two or three sweeps.  The result is the FP64
+  // pass's, to FP64 accuracy.
+  const int npass = VSH ? 2 : 1;
+  for (int pass = 0; pass < npass; ++pass) {
+  const bool warm = warm0 || pass == 1;
+  const bool f32 = npass == 2 && pass == 0;
   for (int idx = tid; idx < M * M; idx += nt) {
     const int i = idx / M, j = idx % M;
     L[idx] = 0.5 * (CX[i * M + j] + CX[j * M + i]);
     SB(i, j) = CY ? 0.5 * (CY[i * M + j] + CY[j * M + i]) : 0.0;
-    Pw[idx] = warm ? Wio[idx] : (i == j ? 1.0 : 0.0);
+    if (pass == 0) Pw[idx] = warm ? Wio[idx] : (i == j ? 1.0 : 0.0);
   }
   __syncthreads();
   if (warm) {   // L <- P^T C_X P, S <- P^T C_Y P (through T)
@@ -433,6 +443,123 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
   }
   __syncthreads();
   const int N = Np, half = N / 2;
+  if (f32) {
+    // S in FP32 in V's region, the FP32 basis (column-major) in S's region
+    float* S32 = reinterpret_cast<float*>(Vt);
+    float* V32 = reinterpret_cast<float*>(Ssh);
+    for (int idx = tid; idx < Np * ld; idx += nt) {
+      const int i = idx / ld, j = idx - i * ld;
+      S32[idx] = (i < M && j < M) ? (float)SB(i, j) : 0.f;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) V32[idx] = (idx / M == idx % M) ? 1.f : 0.f;
+    __syncthreads();
+    for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
+      if (tid == 0) rotated = 0;
+      __syncthreads();
+      for (int r = 0; r < N - 1; ++r) {
+        if (tid < half) {
+          int a, b;
+          if (tid == 0) {
+            a = r;
+            b = N - 1;
+          } else {
+            a = (r + tid) % (N - 1);
+            b = (r - tid + N - 1) % (N - 1);
+          }
+          const int p = min(a, b), q = max(a, b);
+          float cs = 1.f, sn = 0.f;
+          if (q < M) {
+            const float apq = S32[p * ld + q], app = S32[p * ld + p], aqq = S32[q * ld + q];
+            if (fabsf(apq) > 6.0e-8f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-30f) {
+              const float th = (aqq - app) / (2.f * apq);
+              float t;
+              if (fabsf(th) > 1e18f) {
+                t = 0.5f / th;
+              } else {
+                t = 1.f / (fabsf(th) + sqrtf(th * th + 1.f));
+                if (th < 0.f) t = -t;
+              }
+              cs = 1.f / sqrtf(t * t + 1.f);
+              sn = t * cs;
+              rotated = 1;
+            }
+          }
+          rcf[tid] = cs;
+          rsf[tid] = sn;
+          rp[tid] = p;
+          rq[tid] = q;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < half * half; idx += nt) {
+          const int k = idx / half, l = idx % half;
+          if (k > l) continue;
+          const float sk = rsf[k], sl = rsf[l];
+          if (sk == 0.f && sl == 0.f) continue;
+          const float ck = rcf[k], cl = rcf[l];
+          const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
+          const float b00 = S32[pk * ld + pl], b01 = S32[pk * ld + ql], b10 = S32[qk * ld + pl],
+                      b11 = S32[qk * ld + ql];
+          const float t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+          const float t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+          const float n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+          const float n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+          if (k == l) {
+            S32[pk * ld + pk] = n00;
+            S32[qk * ld + qk] = n11;
+            S32[pk * ld + qk] = 0.f;
+            S32[qk * ld + pk] = 0.f;
+          } else {
+            S32[pk * ld + pl] = n00;
+            S32[pk * ld + ql] = n01;
+            S32[qk * ld + pl] = n10;
+            S32[qk * ld + ql] = n11;
+            S32[pl * ld + pk] = n00;
+            S32[ql * ld + pk] = n01;
+            S32[pl * ld + qk] = n10;
+            S32[ql * ld + qk] = n11;
+          }
+        }
+        for (int idx = tid; idx < half * M; idx += nt) {
+          const int l = idx / M, i = idx % M;
+          const float sl = rsf[l];
+          if (sl != 0.f) {
+            const float cl = rcf[l];
+            const int pl = rp[l], ql = rq[l];
+            if (ql < M) {
+              const float vp = V32[pl * M + i], vq = V32[ql * M + i];
+              V32[pl * M + i] = cl * vp - sl * vq;
+              V32[ql * M + i] = sl * vp + cl * vq;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (!rotated) break;
+      __syncthreads();
+    }
+    // X = L^-T V_32 (FP64; thread per column, bottom row first) into T, then
+    // P <- P X (through L, free until the FP64 pass reloads it): the FP64 pass's start
+    if (tid < M) {
+      const int col = tid;
+      for (int i = M - 1; i >= 0; --i) {
+        double s = (double)V32[col * M + i];
+        for (int j = i + 1; j < M; ++j) s -= L[j * M + i] * T[j * M + col];
+        T[i * M + col] = s * linv[i];
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx % M;
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) s += Pw[i * M + k] * T[k * M + j];
+      L[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) Pw[idx] = L[idx];
+    __syncthreads();
+    continue;
+  }
   if (N > M) {
     for (int j = tid; j < N; j += nt) {
       SB(M, j) = 0.0;
@@ -550,6 +677,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
   for (int j = tid; j < M; j += nt) lam[j] = SB(j, j);
   __syncthreads();
   if (tid == 0) *wM = failed ? 0 : M;
+  }   // pass
 #undef SB
 }
 
