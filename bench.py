@@ -314,6 +314,149 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+C5 = dict(M=100, res_tol=1e-3, max_sweeps=40, seed=5001)
+
+
+def run_config5(args, taps, W, torch, stream, hbm_peak):
+    """The large configuration at full size: a moving Gaussian laser source over a
+    1536^3 block (h = 10, 10, 5 um), one 0.2 ms slab of 256 time nodes, 16 laser powers
+    and 16 spot radii as parameter dims, M = 100 modes (the paper's rule of ~5 modes per
+    time point of a ~20-point slab), Algorithm 1 from seeded random factors.  On this
+    source the subspace iteration's Eq. 42 residual does not reach 1e-6 in any bounded
+    number of sweeps (it levels off near 1e-4 after tens of sweeps), so the target here
+    is 1e-3, where the field is settled to the accuracy the 100 modes allow (rho_full is
+    reported beside it).  Paths: FP64 node-side/mode-side diagonalisation (the timed
+    path), FP32-factorised small systems with FP64 refinement, BF16-input Grams with the
+    FP64 polish, and one sampled sweep of block elimination everywhere (the plain FP64 path, whose time
+    to target is that sweep's time times the timed path's sweep count, labelled as
+    such).  Timed with CUDA events on the library's stream, pencil decompositions made
+    once before (reported separately); L2 flushed before every run."""
+    M = C5["M"]
+    t0 = time.perf_counter()
+    desc = W.lpbf_large()
+    build_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P = taps.Problem(desc)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = dict(workload="lpbf_large 1536^3 x 256 (0.2 ms slab) x 16 P x 16 r, moving source, M = 100",
+               sources=len(desc["sources"]), res_kind="Eq. 42", res_tol=C5["res_tol"],
+               build_source_s=build_s, problem_setup_s=setup_s, paths={})
+    U = P.factors(M)
+    # first solve: makes the pencil decompositions of the 1534-node space dims
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=1, init=taps.INIT_RANDOM, seed=C5["seed"], als_tol=0.0,
+            solver=taps.SOLVER_FASTDIAG)
+    torch.cuda.synchronize()
+    out["first_sweep_with_pencils_s"] = time.perf_counter() - t0
+
+    def run(precision, init, solver=taps.SOLVER_FASTDIAG, max_sweeps=C5["max_sweeps"]):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = P.solve(U, M0=M, M_max=M, res_tol=C5["res_tol"], res_kind=taps.RES_ALS, max_sweeps=max_sweeps,
+                    precision=precision, polish_sweeps=max_sweeps, init=init, seed=C5["seed"], als_tol=0.0,
+                    solver=solver)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), r
+
+    for name, prec, init, nrun in (("fp64_fastdiag", taps.FP64, taps.INIT_RANDOM, args.config5_runs),
+                                   ("mixed_fastdiag", taps.MIXED, taps.INIT_RANDOM, args.config5_runs),
+                                   ("bf16gram_fastdiag", taps.BF16, taps.INIT_RANDOM, 1)):
+        run(prec, init)   # warm-up (graph capture)
+        ts, rep = [], None
+        P.profile_reset(events=False)
+        for _ in range(nrun):
+            ms, rep = run(prec, init)
+            ts.append(ms)
+        rho_full = P.residual(U, taps.RES_FULL)
+        out["paths"][name] = dict(ms=float(np.mean(ts)), ms_runs=ts, sweeps=rep["sweeps"],
+                                  ms_per_sweep=float(np.mean(ts)) / max(rep["sweeps"], 1),
+                                  rho42=rep["rho"], rho_full=rho_full, converged=rep["converged"],
+                                  rho42_history=[h[2] for h in rep["history"]])
+    # the Eq. 42 residual over 40 fixed-M sweeps from the same start: where it levels off
+    # (the reason the target here is 1e-3, not 1e-6), with the full residual at the end
+    flush.zero_()
+    r40 = P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=40, init=taps.INIT_RANDOM, seed=C5["seed"],
+                  als_tol=0.0, solver=taps.SOLVER_FASTDIAG)
+    out["fixed_M_40_sweeps"] = dict(rho42_history=[h[2] for h in r40["history"]], rho_full=r40["rho_full"],
+                                    seconds=r40["seconds"])
+    # the greedy schedule on the full residual: 4 modes per growth step from 4, up to 3
+    # sweeps per mode count, stopping at M = 100 or once rho_full improves by less than
+    # 1% over two mode counts
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rg = P.solve(U, M0=4, M_max=M, res_tol=1e-6, res_kind=taps.RES_FULL, max_sweeps=3, init=taps.INIT_RANDOM,
+                 seed=C5["seed"], als_tol=1e-2, solver=taps.SOLVER_FASTDIAG, res_stall=0.01, M_step=4)
+    torch.cuda.synchronize()
+    ends = {}
+    for Mh, ch, rho in rg["history"]:
+        ends[Mh] = rho
+    out["greedy_rho_full"] = dict(seconds=time.perf_counter() - t0, M=rg["M"], sweeps=rg["sweeps"],
+                                  rho_full=rg["rho_full"], rho_full_per_M={int(k): v for k, v in ends.items()},
+                                  rho42=P.residual(U, taps.RES_ALS),
+                                  rule="modes +4 per step, <= 3 sweeps each, stop at M = 100 or on < 1% "
+                                       "improvement of rho_full over two mode counts")
+    # per-class breakdown of the timed path (events around every class, separate runs)
+    run(taps.FP64, taps.INIT_RANDOM)
+    P.profile_reset(events=True)
+    run(taps.FP64, taps.INIT_RANDOM)
+    prof = P.profile()
+    nsw = max(out["paths"]["fp64_fastdiag"]["sweeps"], 1)
+    out["classes_ms_per_sweep"] = {c: v["ms"] / nsw for c, v in prof.items() if v["launches"]}
+    out["classes_gflops"] = {c: v["flops"] / (v["ms"] * 1e-3) / 1e9 for c, v in prof.items()
+                             if v["launches"] and v["ms"] > 0}
+    # reconstruction of the solved field: the 1536^3 space slice at the slab's last time
+    # node, P = 400 W, r = 30 um (14.5 GB of FP32)
+    cnt, st0 = [1536, 1536, 1536, 1, 1, 1], [0, 0, 0, 255, 15, 0]
+    field = torch.empty(int(np.prod(cnt)), dtype=torch.float32, device="cuda")
+    P.eval_grid(U, st0, cnt, [1] * 6, field, dtype=taps.FP32)
+    ts = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        P.eval_grid(U, st0, cnt, [1] * 6, field, dtype=taps.FP32)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    peak = float(field.max().item())
+    del field
+    rb = 4.0 * float(np.prod(cnt))
+    out["reconstruction"] = dict(grid="1536^3 slice at (t = 0.2 ms, P = 400 W, r = 30 um)", M=M,
+                                 ms=float(np.mean(ts)), gb_s=rb / (np.mean(ts) * 1e-3) / 1e9,
+                                 frac=rb / (np.mean(ts) * 1e-3) / 1e9 / hbm_peak, peak_rise_K=peak)
+    if not args.no_config5_plain:
+        # the plain FP64 path: one block-elimination sweep from the same seeded factors
+        flush.zero_()
+        P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=1, init=taps.INIT_RANDOM, seed=C5["seed"],
+                als_tol=0.0, solver=taps.SOLVER_BLOCK_LU)
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.sweep(U, 1, solver=taps.SOLVER_BLOCK_LU)
+        b.record(stream)
+        b.synchronize()
+        sw_ms = a.elapsed_time(b)
+        fd = out["paths"]["fp64_fastdiag"]
+        out["paths"]["fp64_block_lu"] = dict(ms_per_sweep=sw_ms, sampled_sweeps=1,
+                                             ms_extrapolated=sw_ms * fd["sweeps"],
+                                             note="one sweep timed; time to target = that sweep x the "
+                                                  "timed path's sweep count (extrapolated)")
+        out["speedup_vs_block_lu"] = sw_ms * fd["sweeps"] / fd["ms"]
+    out["mixed_vs_fp64_fastdiag"] = out["paths"]["fp64_fastdiag"]["ms"] / out["paths"]["mixed_fastdiag"]["ms"]
+    del U, P, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2503_13933_gb300 import taps
@@ -743,25 +886,24 @@ def run_ours(args, rank, world, local):
     if not args.no_nonlinear:
         # the moving-source plate with temperature-dependent coefficients of Sec. 3.3
         # (10 x 10 x 1 mm, 101 x 101 x 11 space nodes, 113 time nodes at 1.6e-4 s,
-        # Inconel 718 linear laws for rho c_p(u) and k(u)): Algorithm 2 with M = 10
-        # modes, 10 global stages of 4 subspace iterations (a throughput run: on this
-        # moving source the linear stage's own subspace iteration still moves the field
-        # by a few percent per 4 sweeps at M <= 20, so the stage-to-stage change levels
-        # off there).  Timed: problem set-up and every global stage (weighted-operator
-        # assembly on the device, sweeps, the change from the factors).
+        # Inconel 718 linear laws for rho c_p(u) and k(u)): Algorithm 2 with M = 20
+        # modes (84 operator terms), up to 20 global stages of 4 subspace iterations,
+        # stopping at a stage-to-stage change of 1e-3.  Timed: problem set-up and every
+        # global stage (weighted-operator assembly on the device, sweeps, the change from
+        # the factors).
         from paper_2503_13933_gb300 import nonlinear as NLM
         dn = W.nonlinear_track()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        gl = NLM.GlobalLocal(dn, W.INCONEL_LAW, 10)
-        Un, hn = gl.solve(4, max_iters=10, tol=0.0, seed=5)
+        gl = NLM.GlobalLocal(dn, W.INCONEL_LAW, 20)
+        Un, hn = gl.solve(4, max_iters=20, tol=1e-3, seed=5)
         torch.cuda.synchronize()
         tn = time.perf_counter() - t0
         peak = float(np.max(np.abs(gl.P.eval_points(
             gl.U, torch.as_tensor(np.array([[x0, 5.0, 1.0, 0.0155] for x0 in np.linspace(7.0, 8.5, 61)]),
                                   device="cuda"),
             torch.empty(61, dtype=torch.float64, device="cuda")).cpu().numpy())))
-        nonlin = dict(grid="101 x 101 x 11 space x 113 time", modes=10, sweeps_per_stage=4,
+        nonlin = dict(grid="101 x 101 x 11 space x 113 time", modes=20, sweeps_per_stage=4,
                       stages=len(hn), changes=[float(c) for c in hn[1:]], total_s=tn, s_per_stage=tn / len(hn),
                       terms=len(gl.desc["terms"]), sources=len(dn["sources"]),
                       operators_per_dim=[len(w) + 2 for w in gl.wops],
@@ -792,6 +934,14 @@ def run_ours(args, rank, world, local):
                        fp64_sweeps=v["fp64_sweeps"], rho=v["rho"], rho_full=v["rho_full"],
                        converged=v["converged"]) for k, v in res.items()},
         speedup_vs_fp64=(res["fp64"]["solve_ms"] / res[best]["solve_ms"]) if "fp64" in res else None,
+        speedup_vs_plain={
+            "block_elimination": (res["fp64"]["solve_ms"] / res[best]["solve_ms"]) if "fp64" in res else None,
+            "mode_side_diagonalisation_sec2_6": (res["fp64_modediag"]["solve_ms"] / res[best]["solve_ms"])
+            if "fp64_modediag" in res else None,
+            "mixed_fastdiag": (res["mixed_fastdiag"]["solve_ms"] / res[best]["solve_ms"])
+            if "mixed_fastdiag" in res else None,
+            "note": "time of the named FP64 path (seeded random factors, no warm start) over the headline "
+                    "path's time to the same target; mixed_fastdiag is the reduced-precision path"},
         roofline=roof,
         roofline_eval=roof_all.get("eval"),
         roofline_classes=roof_all,
