@@ -23,6 +23,16 @@ from . import taps
 N_REF = 64
 
 
+def features_conductivity(desc, M):
+    """Features of an instance of the large moving-source family: its conductivity k
+    (scaled to [-1, 1] over [10, 30] W/m/K) and the mode index scaled to [-1, 1]."""
+    k = float(desc["params"]["k"])
+    X = np.zeros((M, 2), dtype=np.float32)
+    X[:, 0] = (k - 20.0) / 10.0
+    X[:, 1] = np.array([2.0 * m / max(M - 1, 1) - 1.0 for m in range(M)], dtype=np.float32)
+    return X
+
+
 def features(desc, M):
     g = sorted(desc["params"], key=lambda t: -t[0])
     base = []
@@ -42,15 +52,15 @@ def _all_nodes(dm, col):
     return full
 
 
-def targets(desc, Us):
-    """Converged factors -> (targets [M, D*N_REF + 1], raw weights [M])."""
+def targets(desc, Us, n_ref=N_REF):
+    """Converged factors -> (targets [M, D*n_ref + 1], raw weights [M])."""
     dims = desc["dims"]
     D, M = len(Us), Us[0].shape[1]
-    prof = np.zeros((M, D, N_REF))
+    prof = np.zeros((M, D, n_ref))
     w = np.ones(M)
     for d, dm in enumerate(dims):
         xs = np.linspace(0.0, 1.0, dm["n"])
-        xr = np.linspace(0.0, 1.0, N_REF)
+        xr = np.linspace(0.0, 1.0, n_ref)
         for m in range(M):
             col = _all_nodes(dm, Us[d][:, m])
             k = int(np.argmax(np.abs(col)))
@@ -61,16 +71,17 @@ def targets(desc, Us):
             prof[m, d] = np.interp(xr, xs, col / abs(peak))
             w[m] *= abs(peak) if d < D - 1 else peak
     order = np.argsort(-np.abs(w), kind="stable")
-    T = np.concatenate([prof[order].reshape(M, D * N_REF), w[order, None]], axis=1)
+    T = np.concatenate([prof[order].reshape(M, D * n_ref), w[order, None]], axis=1)
     return T.astype(np.float64), w[order]
 
 
 class WarmStart:
-    """A taps.MLP plus the weight scale of its training set."""
+    """A taps.MLP plus the weight scale of its training set.  `features(desc, M)` maps an
+    instance to the network's inputs; profiles live on n_ref points per dim."""
 
-    def __init__(self, n_in=21, M=30, D=4, hidden=256, layers=3, seed=7):
-        self.M, self.D = M, D
-        self.net = taps.MLP(n_in, hidden, layers, D * N_REF + 1, seed=seed)
+    def __init__(self, n_in=21, M=30, D=4, hidden=256, layers=3, seed=7, n_ref=N_REF, features=features):
+        self.M, self.D, self.n_ref, self.features = M, D, n_ref, features
+        self.net = taps.MLP(n_in, hidden, layers, D * n_ref + 1, seed=seed)
         self.weight_scale = 1.0
 
     def fit(self, X, T, steps=3000, lr=1e-3):
@@ -86,10 +97,10 @@ class WarmStart:
     def init_factors(self, P, U, desc):
         """Predict profiles for every mode of `desc` and write them into U (device)."""
         import torch
-        X = torch.tensor(features(desc, self.M), device="cuda")
-        prof = torch.empty((self.M, self.D * N_REF + 1), dtype=torch.float32, device="cuda")
+        X = torch.tensor(self.features(desc, self.M), device="cuda")
+        prof = torch.empty((self.M, self.D * self.n_ref + 1), dtype=torch.float32, device="cuda")
         self.net.forward(X, prof)
-        U.from_profiles(prof, self.M, N_REF, self.weight_scale)
+        U.from_profiles(prof, self.M, self.n_ref, self.weight_scale)
         return U
 
 
@@ -109,3 +120,24 @@ def training_set(seeds, n_space=256, n_k=32, M=30, res_tol=1e-8, max_sweeps=80):
         Xs.append(features(desc, M))
         Ts.append(T)
     return np.concatenate(Xs), np.concatenate(Ts), sweeps
+
+
+def training_set_conductivity(base, ks, M=100, sweeps=12, n_ref=1536, dim_cache=None, seed=0):
+    """Factors of the large moving-source family at the conductivities `ks` (the base
+    description's other data shared), M modes after `sweeps` FP64 sweeps from the same
+    seeded random factors -> stacked (X, T)."""
+    from . import workloads as W
+    Xs, Ts = [], []
+    for j, k in enumerate(ks):
+        desc = W.with_conductivity(base, k)
+        P = taps.Problem(desc, dim_cache=dim_cache)
+        U = P.factors(M)
+        # one seed for every conductivity: the iterations of neighbouring k follow each
+        # other, so their modes are comparable targets
+        P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=sweeps, init=taps.INIT_RANDOM, seed=seed,
+                als_tol=0.0, solver=taps.SOLVER_FASTDIAG)
+        T, _ = targets(desc, U.get(), n_ref)
+        Xs.append(features_conductivity(desc, M))
+        Ts.append(T)
+        del U, P
+    return np.concatenate(Xs), np.concatenate(Ts)

@@ -229,6 +229,14 @@ def lpbf_large(n_xy=1536, n_z=1536, n_t=256, n_par=16, h_xy=10e-6, h_z=5e-6, T_s
                 sources=sources, params=dict(k=k, x_start=x_start, y0=y0, V=V, T_slab=T_slab))
 
 
+def with_conductivity(desc, k):
+    """A copy of a lpbf_large description with conductivity k (the coefficient of its
+    three diffusion terms; the source and the dims are shared)."""
+    terms = [desc["terms"][0]] + [(float(k), ops) for _, ops in desc["terms"][1:]]
+    return dict(desc, terms=terms, params=dict(desc["params"], k=float(k)),
+                name=desc["name"] + f"_k{k:g}")
+
+
 def batch_instances(count=256, seed=4000, n_lo=32, n_hi=1024, M_lo=4, M_hi=32):
     """Independent instances: D in {3..6}, n_d uniform in [n_lo, n_hi], a mode count
     in [M_lo, M_hi], Poisson or transient (last dim time) 50/50, 1..4 separable
