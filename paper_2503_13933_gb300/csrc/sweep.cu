@@ -515,63 +515,63 @@ __global__ void __launch_bounds__(256) block_backsub_kernel(const double* __rest
   }
 }
 
-// Column normalisation (unit 2-norm for d < D, largest-magnitude entry positive) and the
-// factor change sum ||dU||^2, ||U||^2 per column against the saved old factor, one warp
-// per column (four columns per CTA): shuffle reductions only, no block barriers.
-__global__ void __launch_bounds__(128) normalize_change_warp_kernel(double* U, const double* Uold, int nf, int M,
-                                                                   int normalize, double* out, int* status) {
+// ---------------------------------------------------------------------------------
+// Column normalisation (unit 2-norm, largest-magnitude entry positive) and the
+// squared change / norm of every column against the pre-solve copy.
+// ---------------------------------------------------------------------------------
+__global__ void normalize_change_kernel(double* U, const double* Uold, int nf, int M, int normalize,
+                                        double* out, int* status) {
   taps_pdl_wait_then_release();
-  const int lane = threadIdx.x & 31;
-  const int m = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (m >= M) return;
+  __shared__ double red[32];
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  int m = blockIdx.x;
   double* col = U + (size_t)m * nf;
   const double* old = Uold + (size_t)m * nf;
   double s2 = 0.0, best = -1.0;
   int bi = 0x7fffffff;
-  for (int i = lane; i < nf; i += 32) {
-    const double v = col[i];
-    s2 = fma(v, v, s2);
-    const double a = fabs(v);
-    if (a > best) {
-      best = a;
-      bi = i;
-    }
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    double v = col[i];
+    s2 += v * v;
+    double a = fabs(v);
+    if (a > best) { best = a; bi = i; }
   }
+  s2 = block_sum(s2, red);
+  // argmax with ties to the smallest index
   for (int o = 16; o > 0; o >>= 1) {
-    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) {   // argmax, ties to the smallest index
-      best = ob;
-      bi = oi;
-    }
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
-  const double nrm = sqrt(s2);
-  if (!isfinite(nrm) && lane == 0) taps_flag(status, TAPS_DEV_NONFINITE);
-  double dif = 0.0, n2 = 0.0;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { redv[w] = best; redi[w] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int j = 1; j < nw; ++j)
+      if (redv[j] > redv[0] || (redv[j] == redv[0] && redi[j] < redi[0])) { redv[0] = redv[j]; redi[0] = redi[j]; }
+  }
+  __syncthreads();
+  int imax = redi[0];
+  double nrm = sqrt(s2);
+  if (!isfinite(nrm)) taps_flag(status, TAPS_DEV_NONFINITE);
   if (normalize && nrm > 0.0) {
-    const double den = (col[bi] >= 0.0 ? 1.0 : -1.0) * nrm;
-    __syncwarp();
-    for (int i = lane; i < nf; i += 32) {
-      const double v = col[i] / den;
-      col[i] = v;
-      const double dv = v - old[i];
-      dif = fma(dv, dv, dif);
-      n2 = fma(v, v, n2);
-    }
-  } else {
-    for (int i = lane; i < nf; i += 32) {
-      const double v = col[i];
-      const double dv = v - old[i];
-      dif = fma(dv, dv, dif);
-      n2 = fma(v, v, n2);
-    }
+    double sgn = (col[imax] >= 0.0) ? 1.0 : -1.0;
+    double den = sgn * nrm;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) col[i] = col[i] / den;
+    __syncthreads();
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    dif += __shfl_xor_sync(0xffffffffu, dif, o);
-    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  double dif = 0.0, n2 = 0.0;
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    double v = col[i];
+    double dv = v - old[i];
+    dif += dv * dv;
+    n2 += v * v;
   }
-  if (lane == 0) {
+  dif = block_sum(dif, red);
+  n2 = block_sum(n2, red);
+  if (threadIdx.x == 0) {
     out[2 * m] = dif;
     out[2 * m + 1] = n2;
   }
@@ -783,7 +783,7 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
     }
     int norm_d = (normalize && d < P->D - 1) ? 1 : 0;
     int tk = prof_begin(P, TAPS_PROF_NORMALIZE);
-    TAPS_CUDA(taps_launch_pdl(normalize_change_warp_kernel, dim3((M + 3) / 4), dim3(128), 0, s, U->d_U[d],
+    TAPS_CUDA(taps_launch_pdl(normalize_change_kernel, dim3(M), dim3(256), 0, s, U->d_U[d],
                               (const double*)P->d_Uold, dm->nf, M, norm_d, P->d_scal + (size_t)d * 2 * M,
                               P->d_status));
     prof_end(P, TAPS_PROF_NORMALIZE, tk, 7.0 * dm->nf * M, 8.0 * 3.0 * dm->nf * M);
