@@ -681,6 +681,346 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
 #undef SB
 }
 
+// The mode-side eigen-solve split across launches (32 < M, S and V together in shared
+// memory): the pencil transforms and basis products are FP64 GEMMs on many CTAs
+// (md_gemm_kernel), and one CTA per pass does only what is sequential -- the Cholesky
+// factorisation, S = L^-1 C_Y L^-T and the rotations.  md_core_kernel takes the
+// (transformed) pencil (C_X, C_Y) and writes X = L^-T V: with F32 the rotations run in
+// FP32 (the FP64 pipe of one SM bounds FP64 rounds) and X only seeds the FP64 pass;
+// without, they run in FP64 to convergence and X, diag(S) are the pass's basis and
+// eigenvalues.
+template <bool F32>
+__global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __restrict__ CX,
+                                                              const double* __restrict__ CY, int M,
+                                                              double* __restrict__ Xout, int* __restrict__ wM,
+                                                              double* __restrict__ lam, double* __restrict__ gw,
+                                                              int* status) {
+  extern __shared__ __align__(16) double Ssh[];
+  __shared__ double linv[TAPS_MAX_M];
+  __shared__ double rc[TAPS_MAX_M / 2], rs[TAPS_MAX_M / 2];
+  __shared__ int rp[TAPS_MAX_M / 2], rq[TAPS_MAX_M / 2];
+  __shared__ float rcf[TAPS_MAX_M / 2], rsf[TAPS_MAX_M / 2];
+  __shared__ int rotated, failed;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int Np = M + (M & 1), ld = Np + 1;
+  const size_t MM = (size_t)M * M;
+  double* L = gw;                        // row-major [M][M], lower triangle used
+  double* Vt = Ssh + (size_t)Np * ld;    // column-major basis: Vt[c * M + r] = V[r][c]
+  double* T = gw + 2 * MM;               // row-major temporary
+#define SB(i, j) Ssh[(size_t)(i) * ld + (j)]
+  if (tid == 0) failed = 0;
+  for (int idx = tid; idx < M * M; idx += nt) {
+    const int i = idx / M, j = idx % M;
+    L[idx] = 0.5 * (CX[i * M + j] + CX[j * M + i]);
+    SB(i, j) = CY ? 0.5 * (CY[i * M + j] + CY[j * M + i]) : 0.0;
+  }
+  __syncthreads();
+  // Cholesky with the same pivot floor as md_eig_kernel
+  double dmax = 0.0;
+  for (int k = 0; k < M; ++k) dmax = fmax(dmax, fabs(L[k * M + k]));
+  const double floor_piv = 64.0 * 1.1102230246251565e-16 * dmax;
+  for (int k = 0; k < M; ++k) {
+    if (tid == 0) {
+      double piv = L[k * M + k];
+      if (!isfinite(piv) || !(dmax > 0.0) || !isfinite(dmax) || piv < -1e-8 * dmax) {
+        taps_flag(status, TAPS_DEV_SINGULAR);
+        failed = 1;
+        piv = 1.0;
+      } else if (piv < floor_piv) {
+        piv = floor_piv;
+      }
+      const double r = sqrt(piv);
+      L[k * M + k] = r;
+      linv[k] = taps_rcp(r);
+    }
+    __syncthreads();
+    const double il = linv[k];
+    for (int i = k + 1 + tid; i < M; i += nt) L[i * M + k] *= il;
+    __syncthreads();
+    const int w = M - k - 1;
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+      if (j <= i) L[i * M + j] -= L[i * M + k] * L[j * M + k];
+    }
+    __syncthreads();
+  }
+  // X = L^-1 C_Y into T (thread per column), then S = L^-1 X^T (thread per column)
+  if (tid < M) {
+    const int col = tid;
+    for (int i = 0; i < M; ++i) {
+      double s = SB(i, col);
+      for (int j = 0; j < i; ++j) s -= L[i * M + j] * T[j * M + col];
+      T[i * M + col] = s * linv[i];
+    }
+  }
+  __syncthreads();
+  if (tid < M) {
+    const int col = tid;
+    for (int i = 0; i < M; ++i) {
+      double s = T[col * M + i];
+      for (int j = 0; j < i; ++j) s -= L[i * M + j] * SB(j, col);
+      SB(i, col) = s * linv[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < M * M; idx += nt) {
+    const int i = idx / M, j = idx % M;
+    if (i < j) {
+      const double a = 0.5 * (SB(i, j) + SB(j, i));
+      SB(i, j) = a;
+      SB(j, i) = a;
+    }
+    Vt[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int N = Np, half = N / 2;
+  if (F32) {
+    // S in FP32 in V's region, the FP32 basis (column-major) in S's region
+    float* S32 = reinterpret_cast<float*>(Vt);
+    float* V32 = reinterpret_cast<float*>(Ssh);
+    for (int idx = tid; idx < Np * ld; idx += nt) {
+      const int i = idx / ld, j = idx - i * ld;
+      S32[idx] = (i < M && j < M) ? (float)SB(i, j) : 0.f;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) V32[idx] = (idx / M == idx % M) ? 1.f : 0.f;
+    __syncthreads();
+    for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
+      if (tid == 0) rotated = 0;
+      __syncthreads();
+      for (int r = 0; r < N - 1; ++r) {
+        if (tid < half) {
+          int a, b;
+          if (tid == 0) {
+            a = r;
+            b = N - 1;
+          } else {
+            a = (r + tid) % (N - 1);
+            b = (r - tid + N - 1) % (N - 1);
+          }
+          const int p = min(a, b), q = max(a, b);
+          float cs = 1.f, sn = 0.f;
+          if (q < M) {
+            const float apq = S32[p * ld + q], app = S32[p * ld + p], aqq = S32[q * ld + q];
+            if (fabsf(apq) > 6.0e-8f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-30f) {
+              const float th = (aqq - app) / (2.f * apq);
+              float t;
+              if (fabsf(th) > 1e18f) {
+                t = 0.5f / th;
+              } else {
+                t = 1.f / (fabsf(th) + sqrtf(th * th + 1.f));
+                if (th < 0.f) t = -t;
+              }
+              cs = 1.f / sqrtf(t * t + 1.f);
+              sn = t * cs;
+              rotated = 1;
+            }
+          }
+          rcf[tid] = cs;
+          rsf[tid] = sn;
+          rp[tid] = p;
+          rq[tid] = q;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < half * half; idx += nt) {
+          const int k = idx / half, l = idx % half;
+          if (k > l) continue;
+          const float sk = rsf[k], sl = rsf[l];
+          if (sk == 0.f && sl == 0.f) continue;
+          const float ck = rcf[k], cl = rcf[l];
+          const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
+          const float b00 = S32[pk * ld + pl], b01 = S32[pk * ld + ql], b10 = S32[qk * ld + pl],
+                      b11 = S32[qk * ld + ql];
+          const float t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+          const float t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+          const float n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+          const float n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+          if (k == l) {
+            S32[pk * ld + pk] = n00;
+            S32[qk * ld + qk] = n11;
+            S32[pk * ld + qk] = 0.f;
+            S32[qk * ld + pk] = 0.f;
+          } else {
+            S32[pk * ld + pl] = n00;
+            S32[pk * ld + ql] = n01;
+            S32[qk * ld + pl] = n10;
+            S32[qk * ld + ql] = n11;
+            S32[pl * ld + pk] = n00;
+            S32[ql * ld + pk] = n01;
+            S32[pl * ld + qk] = n10;
+            S32[ql * ld + qk] = n11;
+          }
+        }
+        for (int idx = tid; idx < half * M; idx += nt) {
+          const int l = idx / M, i = idx % M;
+          const float sl = rsf[l];
+          if (sl != 0.f) {
+            const float cl = rcf[l];
+            const int pl = rp[l], ql = rq[l];
+            if (ql < M) {
+              const float vp = V32[pl * M + i], vq = V32[ql * M + i];
+              V32[pl * M + i] = cl * vp - sl * vq;
+              V32[ql * M + i] = sl * vp + cl * vq;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (!rotated) break;
+      __syncthreads();
+    }
+    // X = L^-T V_32 (thread per column, bottom row first)
+    if (tid < M) {
+      const int col = tid;
+      for (int i = M - 1; i >= 0; --i) {
+        double s = (double)V32[col * M + i];
+        for (int j = i + 1; j < M; ++j) s -= L[j * M + i] * Xout[j * M + col];
+        Xout[i * M + col] = s * linv[i];
+      }
+    }
+    return;
+  }
+  if (N > M) {
+    for (int j = tid; j < N; j += nt) {
+      SB(M, j) = 0.0;
+      SB(j, M) = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      if (tid < half) {
+        int a, b;
+        if (tid == 0) {
+          a = r;
+          b = N - 1;
+        } else {
+          a = (r + tid) % (N - 1);
+          b = (r - tid + N - 1) % (N - 1);
+        }
+        const int p = min(a, b), q = max(a, b);
+        double cs = 1.0, sn = 0.0;
+        if (q < M) {
+          const double apq = SB(p, q), app = SB(p, p), aqq = SB(q, q);
+          if (fabs(apq) > 1.1102230246251565e-16 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+            const double th = (aqq - app) * taps_rcp(2.0 * apq);
+            double t;
+            if (fabs(th) > 1e150) {
+              t = 0.5 * taps_rcp(th);
+            } else {
+              t = taps_rcp(fabs(th) + sqrt(th * th + 1.0));
+              if (th < 0.0) t = -t;
+            }
+            cs = taps_rcp(sqrt(t * t + 1.0));
+            sn = t * cs;
+            rotated = 1;
+          }
+        }
+        rc[tid] = cs;
+        rs[tid] = sn;
+        rp[tid] = p;
+        rq[tid] = q;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * half; idx += nt) {
+        const int k = idx / half, l = idx % half;
+        if (k > l) continue;
+        const double sk = rs[k], sl = rs[l];
+        if (sk == 0.0 && sl == 0.0) continue;
+        const double ck = rc[k], cl = rc[l];
+        const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
+        const double b00 = SB(pk, pl), b01 = SB(pk, ql), b10 = SB(qk, pl), b11 = SB(qk, ql);
+        const double t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+        const double t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+        const double n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+        const double n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+        if (k == l) {
+          SB(pk, pk) = n00;
+          SB(qk, qk) = n11;
+          SB(pk, qk) = 0.0;
+          SB(qk, pk) = 0.0;
+        } else {
+          SB(pk, pl) = n00;
+          SB(pk, ql) = n01;
+          SB(qk, pl) = n10;
+          SB(qk, ql) = n11;
+          SB(pl, pk) = n00;
+          SB(ql, pk) = n01;
+          SB(pl, qk) = n10;
+          SB(ql, qk) = n11;
+        }
+      }
+      // V <- V J: columns p_l, q_l of V are rows p_l, q_l of Vt (coalesced over i)
+      for (int idx = tid; idx < half * M; idx += nt) {
+        const int l = idx / M, i = idx % M;
+        const double sl = rs[l];
+        if (sl != 0.0) {
+          const double cl = rc[l];
+          const int pl = rp[l], ql = rq[l];
+          if (ql < M) {
+            const double vp = Vt[(size_t)pl * M + i], vq = Vt[(size_t)ql * M + i];
+            Vt[(size_t)pl * M + i] = cl * vp - sl * vq;
+            Vt[(size_t)ql * M + i] = sl * vp + cl * vq;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // W_inner = L^-T Q in place of V (thread per column, bottom row first)
+  if (tid < M) {
+    const int col = tid;
+    double* v = Vt + (size_t)col * M;
+    for (int i = M - 1; i >= 0; --i) {
+      double s = v[i];
+      for (int j = i + 1; j < M; ++j) s -= L[j * M + i] * v[j];
+      v[i] = s * linv[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < M * M; idx += nt) {
+    const int i = idx / M, j = idx % M;
+    Xout[idx] = Vt[(size_t)j * M + i];
+    if (!isfinite(Xout[idx])) failed = 1;
+  }
+  for (int j = tid; j < M; j += nt) lam[j] = SB(j, j);
+  __syncthreads();
+  if (tid == 0) *wM = failed ? 0 : M;
+#undef SB
+}
+
+// C = op(A) B for M x M row-major FP64 matrices, a 16 x 16 output tile per CTA.  With a
+// basis flag (P_mode != 0) the operand P is the dim's previous basis when it is sound
+// (*wM == M) and the identity otherwise: P_mode 1: C = A P (A when cold); 2: C = P^T B
+// (B when cold); 3: C = P B (B when cold).
+__global__ void __launch_bounds__(256) md_gemm_kernel(const double* __restrict__ A, int transA,
+                                                      const double* __restrict__ B, double* __restrict__ C, int M,
+                                                      const int* __restrict__ wM, int P_mode) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  const bool cold = P_mode != 0 && *wM != M;
+  if (cold) {   // a product with the identity
+    if (row < M && col < M) C[row * M + col] = (P_mode == 1) ? A[row * M + col] : B[row * M + col];
+    return;
+  }
+  double acc = 0.0;
+  for (int k0 = 0; k0 < M; k0 += 16) {
+    const int ka = k0 + tx, kb = k0 + ty;
+    As[ty][tx] = (row < M && ka < M) ? (transA ? A[ka * M + row] : A[row * M + ka]) : 0.0;
+    Bs[ty][tx] = (kb < M && col < M) ? B[kb * M + col] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+    __syncthreads();
+  }
+  if (row < M && col < M) C[row * M + col] = acc;
+}
+
 // cw[r][j] = sum_m c[r][m] W[m][j] (the right-hand side's mode-side coefficients), one
 // thread per entry over many CTAs.
 __global__ void md_cw_kernel(const double* __restrict__ c, const double* __restrict__ Wm, int Rf, int M,
@@ -891,7 +1231,7 @@ int taps_dim_route(const taps_problem* P, int d, int solver, int M) {
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf) {
   return (size_t)TAPS_MAX_DIMS * M * M + TAPS_MAX_DIMS + M + (size_t)Rf * M + (size_t)nf_max * M +
          (size_t)(nf_max + MD_PAD) * (MD_MAX_HB + 1) * M + (size_t)(nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M +
-         (M > 32 ? (size_t)4 * M * M : 0);
+         (M > 32 ? (size_t)7 * M * M : 0);
 }
 
 // Forgets every dim's stored basis (the next solves start cold).  Called when a sweep
@@ -913,6 +1253,12 @@ int taps_md_setup(int maxsm) {
                                  std::min(need, maxsm - (int)fa.sharedSizeBytes)));
   TAPS_CUDA(cudaFuncGetAttributes(&fa, md_eig_big_kernel<true>));
   TAPS_CUDA(cudaFuncSetAttribute(md_eig_big_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 std::min(MDB_SMEM_SV_MAX, maxsm - (int)fa.sharedSizeBytes)));
+  TAPS_CUDA(cudaFuncGetAttributes(&fa, md_core_kernel<true>));
+  TAPS_CUDA(cudaFuncSetAttribute(md_core_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 std::min(MDB_SMEM_SV_MAX, maxsm - (int)fa.sharedSizeBytes)));
+  TAPS_CUDA(cudaFuncGetAttributes(&fa, md_core_kernel<false>));
+  TAPS_CUDA(cudaFuncSetAttribute(md_core_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  std::min(MDB_SMEM_SV_MAX, maxsm - (int)fa.sharedSizeBytes)));
   return TAPS_OK;
 }
@@ -958,14 +1304,44 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
     const int Np = M + (M & 1);
     const size_t smem_s = sizeof(double) * (size_t)Np * (Np + 1);   // opted in by taps_md_setup
     const size_t smem_sv = smem_s + sizeof(double) * (size_t)M * M;
-    if (smem_sv <= (size_t)MDB_SMEM_SV_MAX)
-      md_eig_big_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(P->d_C + (size_t)sx * MM,
-                                                              sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm,
-                                                              wM, lam, gw, P->d_status);
-    else
+    if (smem_sv <= (size_t)MDB_SMEM_SV_MAX) {
+      // transforms and basis products on many CTAs, the sequential part on one
+      const double* CX = P->d_C + (size_t)sx * MM;
+      const double* CY = sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr;
+      double* T = gw + 2 * MM;
+      double* P1 = gw + 3 * MM;
+      double* CXw = gw + 4 * MM;
+      double* CYw = gw + 5 * MM;
+      double* X = gw + 6 * MM;
+      const dim3 gg((M + 15) / 16, (M + 15) / 16);
+      // the previous basis P (identity when cold): CXw = P^T C_X P, CYw = P^T C_Y P
+      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, Wm, T, M, wM, 1);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CXw, M, wM, 2);
+      if (CY) {
+        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, Wm, T, M, wM, 1);
+        md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CYw, M, wM, 2);
+      }
+      // FP32 rotations: X, then P1 = P X
+      md_core_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
+                                                           P->d_status);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 0, X, P1, M, wM, 3);
+      // FP64 pass on (P1^T C_X P1, P1^T C_Y P1): X = W_inner, lam; W = P1 W_inner
+      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, P1, T, M, wM, 0);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CXw, M, wM, 0);
+      if (CY) {
+        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, P1, T, M, wM, 0);
+        md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CYw, M, wM, 0);
+      }
+      md_core_kernel<false><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
+                                                            P->d_status);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 0, X, Wm, M, wM, 0);
+      P->prof->launches[TAPS_PROF_MODEDIAG] += CY ? 11 : 7;
+    } else {
       md_eig_big_kernel<false><<<1, MDB_THREADS, smem_s, s>>>(P->d_C + (size_t)sx * MM,
                                                               sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm,
                                                               wM, lam, gw, P->d_status);
+    }
+    ++P->prof->launches[TAPS_PROF_MODEDIAG];   // W^T c
     const long long rm = (long long)Rf * M;
     md_cw_kernel<<<(unsigned)((rm + 255) / 256), 256, 0, s>>>(P->d_c, Wm, Rf, M, cw);
   }
