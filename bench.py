@@ -408,26 +408,45 @@ def run_config5(args, taps, W, torch, stream, hbm_peak):
             b.synchronize()
             return a.elapsed_time(b), r
 
-        for name, prec in (("fp64_fastdiag_mlp", taps.FP64), ("mixed_fastdiag_mlp", taps.MIXED)):
-            run_ws(prec)
-            ts, rep = [], None
-            for _ in range(args.config5_runs):
-                ms, rep = run_ws(prec)
-                ts.append(ms)
-            out["paths"][name] = dict(ms=float(np.mean(ts)), ms_runs=ts, sweeps=rep["sweeps"],
-                                      ms_per_sweep=float(np.mean(ts)) / max(rep["sweeps"], 1),
-                                      rho42=rep["rho"], rho_full=P.residual(U, taps.RES_FULL),
-                                      converged=rep["converged"], rho42_history=[h[2] for h in rep["history"]])
-        # the first sweep from each start: the residuals after it
-        ws.init_factors(P, U, desc)
-        P.sweep(U, 1, solver=taps.SOLVER_FASTDIAG)
-        w1 = (P.residual(U, taps.RES_ALS), P.residual(U, taps.RES_FULL))
-        P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=1, init=taps.INIT_RANDOM, seed=C5["seed"],
-                als_tol=0.0, solver=taps.SOLVER_FASTDIAG)
-        r1 = (P.residual(U, taps.RES_ALS), P.residual(U, taps.RES_FULL))
-        out["warm_start"].update(first_sweep_rho42=dict(random=r1[0], warm=w1[0]),
-                                 first_sweep_rho_full=dict(random=r1[1], warm=w1[1]))
-        out["mlp_mixed_vs_fp64_fastdiag"] = out["paths"]["fp64_fastdiag"]["ms"] / out["paths"]["mixed_fastdiag_mlp"]["ms"]
+        # a predicted start can be numerically rank deficient (the 16-node parameter dims
+        # hold at most 16 independent modes of 100): a solve that reports it is recorded,
+        # not retried
+        try:
+            for name, prec in (("fp64_fastdiag_mlp", taps.FP64), ("mixed_fastdiag_mlp", taps.MIXED)):
+                run_ws(prec)
+                ts, rep = [], None
+                for _ in range(args.config5_runs):
+                    ms, rep = run_ws(prec)
+                    ts.append(ms)
+                out["paths"][name] = dict(ms=float(np.mean(ts)), ms_runs=ts, sweeps=rep["sweeps"],
+                                          ms_per_sweep=float(np.mean(ts)) / max(rep["sweeps"], 1),
+                                          rho42=rep["rho"], rho_full=P.residual(U, taps.RES_FULL),
+                                          converged=rep["converged"],
+                                          rho42_history=[h[2] for h in rep["history"]])
+            # the prediction alone (network forward pass and factors from the profiles)
+            ti = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                ws.init_factors(P, U, desc)
+                b.record(stream)
+                b.synchronize()
+                ti.append(a.elapsed_time(b))
+            out["warm_start"]["init_ms"] = float(np.mean(ti))
+            # the first sweep from each start: the residuals after it
+            ws.init_factors(P, U, desc)
+            P.sweep(U, 1, solver=taps.SOLVER_FASTDIAG)
+            w1 = (P.residual(U, taps.RES_ALS), P.residual(U, taps.RES_FULL))
+            P.solve(U, M0=M, M_max=M, res_tol=-1.0, max_sweeps=1, init=taps.INIT_RANDOM, seed=C5["seed"],
+                    als_tol=0.0, solver=taps.SOLVER_FASTDIAG)
+            r1 = (P.residual(U, taps.RES_ALS), P.residual(U, taps.RES_FULL))
+            out["warm_start"].update(first_sweep_rho42=dict(random=r1[0], warm=w1[0]),
+                                     first_sweep_rho_full=dict(random=r1[1], warm=w1[1]))
+            out["mlp_mixed_vs_fp64_fastdiag"] = (out["paths"]["fp64_fastdiag"]["ms"] /
+                                                 out["paths"]["mixed_fastdiag_mlp"]["ms"])
+        except taps.TapsError as e:
+            out["warm_start"]["error"] = str(e)
         del ws
     # the Eq. 42 residual over 40 fixed-M sweeps from the same start: where it levels off
     # (the reason the target here is 1e-3, not 1e-6), with the full residual at the end

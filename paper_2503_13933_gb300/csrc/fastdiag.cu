@@ -868,15 +868,26 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
 }
 
 // One CTA per node i (M > 32): solve (mu_i C_A + C_B) y = g_i by LU with partial
-// pivoting in shared memory.
-__global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __restrict__ CA,
+// pivoting in shared memory, the right-hand side carried along as column M.  Per
+// step p, warp 0 finds the pivot row (largest magnitude, ties to the smaller row),
+// swaps it into place and takes the pivot's reciprocal; then warp w updates the rows
+// r = p+1+w, p+5+w, ... (lanes over the columns c > p, coalesced) with one FMA per
+// entry, T[r][c] -= l_r T[p][c], l_r = T[r][p] / T[p][p] (as a product with the
+// reciprocal, seed plus refinement).  The trailing update is FP64 FMA issue on all
+// four SM sub-partitions (eight warps, so that two CTAs per SM keep four warps on each
+// sub-partition); two barriers per step.  Back substitution column by column: x_r = b_r / U_rr, then
+// every thread removes x_r from its rows' right-hand sides.  A zero or non-finite
+// pivot is reported as TAPS_DEV_SINGULAR.
+__global__ void __launch_bounds__(256) fd_small_solve_kernel(const double* __restrict__ CA,
                                                              const double* __restrict__ CB,
                                                              const double* __restrict__ mu,
                                                              const double* __restrict__ G, int M,
                                                              double* __restrict__ Y, int* status) {
   extern __shared__ double T[];   // [M][M+1]: matrix | rhs
-  __shared__ int piv_row;
+  __shared__ double pinv;
+  __shared__ int bad;
   const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int ld = M + 1;
   const double mi = mu ? mu[i] : 0.0;
   for (int idx = tid; idx < M * M; idx += nt) {
@@ -884,12 +895,13 @@ __global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __res
     T[r * ld + c] = (CA ? mi * CA[idx] : 0.0) + CB[idx];
   }
   for (int r = tid; r < M; r += nt) T[r * ld + M] = G[(size_t)i * M + r];
+  if (tid == 0) bad = 0;
   __syncthreads();
   for (int p = 0; p < M; ++p) {
-    if (tid < 32) {   // argmax |T[r][p]|, r >= p (ties to the smaller r)
+    if (warp == 0) {   // argmax |T[r][p]|, r >= p (ties to the smaller r), swap, reciprocal
       double best = -1.0;
       int br = p;
-      for (int r = p + tid; r < M; r += 32) {
+      for (int r = p + lane; r < M; r += 32) {
         double a = fabs(T[r * ld + p]);
         if (a > best) { best = a; br = r; }
       }
@@ -898,43 +910,40 @@ __global__ void __launch_bounds__(128) fd_small_solve_kernel(const double* __res
         int orr = __shfl_xor_sync(0xffffffffu, br, o);
         if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
       }
-      if (tid == 0) {
-        piv_row = br;
-        if (!(best > 0.0) || !isfinite(best)) taps_flag(status, TAPS_DEV_SINGULAR);
-      }
-    }
-    __syncthreads();
-    int pr = piv_row;
-    if (pr != p)
-      for (int c = tid; c <= M; c += nt) {
-        double t = T[p * ld + c];
-        T[p * ld + c] = T[pr * ld + c];
-        T[pr * ld + c] = t;
-      }
-    __syncthreads();
-    double pv = T[p * ld + p];
-    double inv = (pv != 0.0 && isfinite(pv)) ? 1.0 / pv : 0.0;
-    int w = M - p - 1;
-    for (int idx = tid; idx < w * (w + 1); idx += nt) {
-      int r = p + 1 + idx / (w + 1), c = p + 1 + idx % (w + 1);
-      T[r * ld + c] -= T[r * ld + p] * inv * T[p * ld + c];
-    }
-    __syncthreads();
-  }
-  if (tid < 32) {   // back substitution (one warp)
-    for (int r = M - 1; r >= 0; --r) {
-      double s = 0.0;
-      for (int c = r + 1 + tid; c < M; c += 32) s += T[r * ld + c] * T[c * ld + M];
-      s = warp_sum(s);
-      if (tid == 0) {
-        double pv = T[r * ld + r];
-        T[r * ld + M] = (pv != 0.0) ? (T[r * ld + M] - s) / pv : 0.0;
-      }
+      if (br != p)
+        for (int c = p + lane; c <= M; c += 32) {
+          const double t = T[p * ld + c];
+          T[p * ld + c] = T[br * ld + c];
+          T[br * ld + c] = t;
+        }
       __syncwarp();
+      if (lane == 0) {
+        const double pv = T[p * ld + p];
+        const bool ok = pv != 0.0 && isfinite(pv);
+        pinv = ok ? taps_rcp(pv) : 0.0;
+        if (!ok) bad = 1;
+      }
     }
+    __syncthreads();
+    const double inv = pinv;
+    for (int r = p + 1 + warp; r < M; r += nw) {
+      const double l = T[r * ld + p] * inv;
+      for (int c = p + 1 + lane; c <= M; c += 32) T[r * ld + c] = fma(-l, T[p * ld + c], T[r * ld + c]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  for (int r = M - 1; r >= 0; --r) {
+    if (tid == 0) {
+      const double pv = T[r * ld + r];
+      T[r * ld + M] = (pv != 0.0) ? T[r * ld + M] / pv : 0.0;
+    }
+    __syncthreads();
+    const double xr = T[r * ld + M];
+    for (int k = tid; k < r; k += nt) T[k * ld + M] = fma(-T[k * ld + r], xr, T[k * ld + M]);
+    __syncthreads();
+  }
   for (int r = tid; r < M; r += nt) Y[(size_t)i * M + r] = T[r * ld + M];
+  if (tid == 0 && bad) taps_flag(status, TAPS_DEV_SINGULAR);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1221,7 +1230,7 @@ int taps_fd_solve(taps_problem* P, taps_factors* U, int d, int precision) {
         TAPS_TRY(taps_allow_dyn_smem((const void*)fd_small_solve_kernel, maxsm));
         smem_ok = true;
       }
-      fd_small_solve_kernel<<<n, 128, sizeof(double) * (size_t)M * (M + 1), s>>>(
+      fd_small_solve_kernel<<<n, 256, sizeof(double) * (size_t)M * (M + 1), s>>>(
           CA, CB, slotA >= 0 ? E->mu : nullptr, G, M, Y, P->d_status);
     }
     ++launches;

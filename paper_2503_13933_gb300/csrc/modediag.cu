@@ -694,13 +694,15 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
                                                               const double* __restrict__ CY, int M,
                                                               double* __restrict__ Xout, int* __restrict__ wM,
                                                               double* __restrict__ lam, double* __restrict__ gw,
-                                                              int* status) {
+                                                              int* status, const int* __restrict__ skip,
+                                                              int* __restrict__ floored_out) {
   extern __shared__ __align__(16) double Ssh[];
   __shared__ double linv[TAPS_MAX_M];
   __shared__ double rc[TAPS_MAX_M / 2], rs[TAPS_MAX_M / 2];
   __shared__ int rp[TAPS_MAX_M / 2], rq[TAPS_MAX_M / 2];
   __shared__ float rcf[TAPS_MAX_M / 2], rsf[TAPS_MAX_M / 2];
-  __shared__ int rotated, failed;
+  __shared__ int rotated, failed, floored;
+  if (skip && *skip) return;   // the refinement already delivered the basis
   const int tid = threadIdx.x, nt = blockDim.x;
   const int Np = M + (M & 1), ld = Np + 1;
   const size_t MM = (size_t)M * M;
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
   double* Vt = Ssh + (size_t)Np * ld;    // column-major basis: Vt[c * M + r] = V[r][c]
   double* T = gw + 2 * MM;               // row-major temporary
 #define SB(i, j) Ssh[(size_t)(i) * ld + (j)]
-  if (tid == 0) failed = 0;
+  if (tid == 0) failed = floored = 0;
   for (int idx = tid; idx < M * M; idx += nt) {
     const int i = idx / M, j = idx % M;
     L[idx] = 0.5 * (CX[i * M + j] + CX[j * M + i]);
@@ -728,6 +730,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
         piv = 1.0;
       } else if (piv < floor_piv) {
         piv = floor_piv;
+        floored = 1;
       }
       const double r = sqrt(piv);
       L[k * M + k] = r;
@@ -785,6 +788,10 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
     __syncthreads();
     for (int idx = tid; idx < M * M; idx += nt) V32[idx] = (idx / M == idx % M) ? 1.f : 0.f;
     __syncthreads();
+    // half is even or odd: with odd half the middle row pairs with itself, so the
+    // folded count is half (half + 1) / 2 either way
+    const int ntri = half * (half + 1) / 2;
+    const int vi = tid & 127, vl0 = tid >> 7;
     for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
       if (tid == 0) rotated = 0;
       __syncthreads();
@@ -822,9 +829,18 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
           rq[tid] = q;
         }
         __syncthreads();
-        for (int idx = tid; idx < half * half; idx += nt) {
-          const int k = idx / half, l = idx % half;
-          if (k > l) continue;
+        // pair blocks (k, l), k <= l, enumerated without the lower half: rows k and
+        // half-1-k of the triangle together hold half+1 blocks
+        for (int idx = tid; idx < ntri; idx += nt) {
+          int k, l;
+          const int q = idx / (half + 1), rr = idx - q * (half + 1);
+          if (rr < half - q) {
+            k = q;
+            l = q + rr;
+          } else {
+            k = half - 1 - q;
+            l = k + rr - (half - q);
+          }
           const float sk = rsf[k], sl = rsf[l];
           if (sk == 0.f && sl == 0.f) continue;
           const float ck = rcf[k], cl = rcf[l];
@@ -851,19 +867,20 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
             S32[ql * ld + qk] = n11;
           }
         }
-        for (int idx = tid; idx < half * M; idx += nt) {
-          const int l = idx / M, i = idx % M;
-          const float sl = rsf[l];
-          if (sl != 0.f) {
-            const float cl = rcf[l];
-            const int pl = rp[l], ql = rq[l];
-            if (ql < M) {
-              const float vp = V32[pl * M + i], vq = V32[ql * M + i];
-              V32[pl * M + i] = cl * vp - sl * vq;
-              V32[ql * M + i] = sl * vp + cl * vq;
+        // V <- V J: thread (row i = tid mod 128, pairs l = tid / 128 + 4 j)
+        if (vi < M)
+          for (int l = vl0; l < half; l += nt >> 7) {
+            const float sl = rsf[l];
+            if (sl != 0.f) {
+              const float cl = rcf[l];
+              const int pl = rp[l], ql = rq[l];
+              if (ql < M) {
+                const float vp = V32[pl * M + vi], vq = V32[ql * M + vi];
+                V32[pl * M + vi] = cl * vp - sl * vq;
+                V32[ql * M + vi] = sl * vp + cl * vq;
+              }
             }
           }
-        }
         __syncthreads();
       }
       if (!rotated) break;
@@ -878,6 +895,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
         Xout[i * M + col] = s * linv[i];
       }
     }
+    if (tid == 0 && floored_out) *floored_out = floored | failed;
     return;
   }
   if (N > M) {
@@ -999,8 +1017,10 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
 // (B when cold); 3: C = P B (B when cold).
 __global__ void __launch_bounds__(256) md_gemm_kernel(const double* __restrict__ A, int transA,
                                                       const double* __restrict__ B, double* __restrict__ C, int M,
-                                                      const int* __restrict__ wM, int P_mode) {
+                                                      const int* __restrict__ wM, int P_mode,
+                                                      const int* __restrict__ skip) {
   __shared__ double As[16][17], Bs[16][17];
+  if (skip && *skip) return;   // the refinement already delivered the basis
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
   const bool cold = P_mode != 0 && *wM != M;
@@ -1019,6 +1039,143 @@ __global__ void __launch_bounds__(256) md_gemm_kernel(const double* __restrict__
     __syncthreads();
   }
   if (row < M && col < M) C[row * M + col] = acc;
+}
+
+// Refinement of an approximate eigenbasis X of the symmetric-definite pencil
+// (C_Y, C_X) in FP64 by matrix products only (first-order correction, repeated):
+// with R = I - X^T C_X X and S = X^T C_Y X, the exact basis is X (I + F) where, to first
+// order, F + F^T = R (C_X-orthonormality) and S + F^T D + D F is diagonal (D = diag of
+// the Rayleigh quotients lam_i = S_ii / (1 - R_ii)), i.e. F_ii = R_ii / 2 and
+// F_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for i != j.  Each correction is about
+// the square of the previous one while the error is small against the gaps of lam
+// (the FP32 rotations deliver ~1e-4; three corrections reach the FP64 rounding
+// floor).  A step whose largest |F| exceeds MR_FAIL (no quadratic regime: a cluster
+// or a poor start) ends the refinement unaccepted, and so does a non-finite entry;
+// once max |F| <= MR_DONE the corrected basis goes to Wout, lam to lam_out and *acc
+// = 1 (the FP64 rotation pass is then skipped).  Not attempted when the FP32 pass
+// raised a Cholesky pivot of C_X to its floor (the rotation pass's regularised
+// pencil, not the exact one, is then the solve's).  One cooperative launch; phases
+// are separated by bounded grid barriers, and every CTA takes the same decisions from
+// the same global maximum.
+#define MR_THREADS 256
+#define MR_MAX_STEPS 4
+#define MR_FAIL 0.1
+#define MR_DONE 1e-9
+struct MrBufs {
+  double *Xa, *Xb, *T1, *T2, *A, *B, *F;
+  unsigned long long* maxbits;   // [MR_MAX_STEPS] bit patterns of non-negative doubles
+  unsigned* bar;                 // grid barrier (zeroed before the launch)
+};
+
+// C[tile] = op(P) Q for one 16 x 16 output tile; sym: P is the symmetric part of a
+// coefficient matrix (0.5 (P + P^T)); transP: P^T.  Accumulation over k in order.
+__device__ __forceinline__ void mr_tile(const double* __restrict__ Pm, int sym, int transP,
+                                        const double* __restrict__ Q, double* __restrict__ C, int M, int ti,
+                                        int tj, double (*Ps)[17], double (*Qs)[17], const double* __restrict__ Add) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row = ti * 16 + ty, col = tj * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < M; k0 += 16) {
+    const int ka = k0 + tx, kb = k0 + ty;
+    double pv = 0.0;
+    if (row < M && ka < M) {
+      if (sym) pv = 0.5 * (Pm[row * M + ka] + Pm[ka * M + row]);
+      else pv = transP ? Pm[ka * M + row] : Pm[row * M + ka];
+    }
+    Ps[ty][tx] = pv;
+    Qs[ty][tx] = (kb < M && col < M) ? Q[kb * M + col] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(Ps[ty][k], Qs[k][tx], acc);
+    __syncthreads();
+  }
+  if (row < M && col < M) C[row * M + col] = Add ? Add[row * M + col] + acc : acc;
+}
+
+__device__ __forceinline__ double mr_max_read(const unsigned long long* p) {
+  return __longlong_as_double((long long)*(volatile const unsigned long long*)p);
+}
+
+__global__ void __launch_bounds__(MR_THREADS) md_refine_kernel(const double* __restrict__ CX,
+                                                              const double* __restrict__ CY, int M,
+                                                              const double* __restrict__ X0, MrBufs b,
+                                                              double* __restrict__ Wout, double* __restrict__ lam_out,
+                                                              int* wM, int* acc, const int* __restrict__ floored,
+                                                              int* status) {
+  __shared__ double Ps[16][17], Qs[16][17];
+  __shared__ double red[MR_THREADS / 32];
+  const int nt = (M + 15) / 16, ntt = nt * nt;
+  const unsigned nb = gridDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *acc = 0;
+    for (int k = 0; k < MR_MAX_STEPS; ++k) b.maxbits[k] = 0ull;
+  }
+  // a Cholesky pivot of the FP32 pass raised to the floor: C_X is numerically
+  // singular on the modes, and the FP64 rotation pass (with the same floor) decides
+  if (*floored) return;
+  const double* X = X0;
+  for (int step = 0; step < MR_MAX_STEPS; ++step) {
+    double* Xn = (step & 1) ? b.Xb : b.Xa;
+    // T1 = sym(C_X) X, T2 = sym(C_Y) X (C_Y absent: T2 unused)
+    for (int it = blockIdx.x; it < 2 * ntt; it += nb) {
+      const int mat = it / ntt, t = it % ntt;
+      if (mat == 1 && !CY) continue;
+      mr_tile(mat ? CY : CX, 1, 0, X, mat ? b.T2 : b.T1, M, t / nt, t % nt, Ps, Qs, nullptr);
+    }
+    grid_barrier(b.bar, status, nb);
+    // A = X^T T1, B = X^T T2
+    for (int it = blockIdx.x; it < 2 * ntt; it += nb) {
+      const int mat = it / ntt, t = it % ntt;
+      if (mat == 1 && !CY) continue;
+      mr_tile(X, 0, 1, mat ? b.T2 : b.T1, mat ? b.B : b.A, M, t / nt, t % nt, Ps, Qs, nullptr);
+    }
+    grid_barrier(b.bar, status, nb);
+    // F and its largest magnitude (non-finite entries count as infinite)
+    double fmx = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * M; e += nb * blockDim.x) {
+      const int i = e / M, j = e % M;
+      const double Rij = (i == j ? 1.0 : 0.0) - 0.5 * (b.A[i * M + j] + b.A[j * M + i]);
+      const double Rii = 1.0 - b.A[i * M + i], Rjj = 1.0 - b.A[j * M + j];
+      const double Sij = CY ? 0.5 * (b.B[i * M + j] + b.B[j * M + i]) : 0.0;
+      const double li = CY ? b.B[i * M + i] / (1.0 - Rii) : 0.0;
+      const double lj = CY ? b.B[j * M + j] / (1.0 - Rjj) : 0.0;
+      double f;
+      if (i == j) {
+        f = 0.5 * Rij;
+        lam_out[i] = li;   // final only when this step is accepted; else the FP64 pass rewrites it
+      } else {
+        f = (Sij + lj * Rij) / (lj - li);
+        if (!CY) f = 0.5 * Rij;
+      }
+      b.F[e] = f;
+      const double a = fabs(f);
+      fmx = isfinite(a) ? fmax(fmx, a) : INFINITY;
+    }
+    for (int o = 16; o > 0; o >>= 1) fmx = fmax(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fmx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < MR_THREADS / 32; ++w) m = fmax(m, red[w]);
+      atomicMax(b.maxbits + step, (unsigned long long)__double_as_longlong(m));
+    }
+    grid_barrier(b.bar, status, nb);
+    const double mx = mr_max_read(b.maxbits + step);
+    if (!(mx <= MR_FAIL)) return;   // not accepted: the FP64 rotation pass runs
+    const bool done = mx <= MR_DONE;
+    // X_next = X + X F (into the basis output once accepted)
+    double* dst = done ? Wout : Xn;
+    for (int t = blockIdx.x; t < ntt; t += nb) mr_tile(X, 0, 0, b.F, dst, M, t / nt, t % nt, Ps, Qs, X);
+    if (done) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *acc = 1;
+        *wM = M;
+      }
+      return;
+    }
+    grid_barrier(b.bar, status, nb);
+    X = Xn;
+  }
 }
 
 // cw[r][j] = sum_m c[r][m] W[m][j] (the right-hand side's mode-side coefficients), one
@@ -1231,7 +1388,7 @@ int taps_dim_route(const taps_problem* P, int d, int solver, int M) {
 size_t taps_md_scratch_doubles(int nf_max, int M, int Rf) {
   return (size_t)TAPS_MAX_DIMS * M * M + TAPS_MAX_DIMS + M + (size_t)Rf * M + (size_t)nf_max * M +
          (size_t)(nf_max + MD_PAD) * (MD_MAX_HB + 1) * M + (size_t)(nf_max + MD_PAD) * (2 * MD_MAX_HB + 2) * M +
-         (M > 32 ? (size_t)7 * M * M : 0);
+         (M > 32 ? (size_t)14 * M * M + 8 : 0);
 }
 
 // Forgets every dim's stored basis (the next solves start cold).  Called when a sweep
@@ -1314,28 +1471,53 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
       double* CYw = gw + 5 * MM;
       double* X = gw + 6 * MM;
       const dim3 gg((M + 15) / 16, (M + 15) / 16);
+      MrBufs rb;
+      rb.Xa = gw + 7 * MM;
+      rb.Xb = gw + 8 * MM;
+      rb.T1 = gw + 9 * MM;
+      rb.T2 = gw + 10 * MM;
+      rb.A = gw + 11 * MM;
+      rb.B = gw + 12 * MM;
+      rb.F = gw + 13 * MM;
+      rb.maxbits = (unsigned long long*)(gw + 14 * MM);
+      rb.bar = (unsigned*)(gw + 14 * MM + MR_MAX_STEPS);
+      int* acc = (int*)(gw + 14 * MM + MR_MAX_STEPS + 1);
+      int* floored = (int*)(gw + 14 * MM + MR_MAX_STEPS + 2);
+      const int* no_skip = nullptr;
       // the previous basis P (identity when cold): CXw = P^T C_X P, CYw = P^T C_Y P
-      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, Wm, T, M, wM, 1);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CXw, M, wM, 2);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, Wm, T, M, wM, 1, no_skip);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CXw, M, wM, 2, no_skip);
       if (CY) {
-        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, Wm, T, M, wM, 1);
-        md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CYw, M, wM, 2);
+        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, Wm, T, M, wM, 1, no_skip);
+        md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CYw, M, wM, 2, no_skip);
       }
       // FP32 rotations: X, then P1 = P X
       md_core_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
-                                                           P->d_status);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 0, X, P1, M, wM, 3);
-      // FP64 pass on (P1^T C_X P1, P1^T C_Y P1): X = W_inner, lam; W = P1 W_inner
-      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, P1, T, M, wM, 0);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CXw, M, wM, 0);
+                                                           P->d_status, no_skip, floored);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 0, X, P1, M, wM, 3, no_skip);
+      // FP64 corrections of P1 by matrix products (many CTAs); accepted, they give W
+      // and lam and the FP64 rotation pass below returns at once
+      {
+        const int ntt = ((M + 15) / 16) * ((M + 15) / 16);
+        const int grid = std::max(1, std::min(2 * ntt, P->num_sms));
+        TAPS_CUDA(cudaMemsetAsync(rb.bar, 0, 2 * sizeof(unsigned), s));
+        const double* X0 = P1;
+        void* args[] = {(void*)&CX, (void*)&CY, (void*)&M, (void*)&X0, (void*)&rb, (void*)&Wm,
+                        (void*)&lam, (void*)&wM, (void*)&acc, (void*)&floored, (void*)&P->d_status};
+        TAPS_CUDA(cudaLaunchCooperativeKernel((const void*)md_refine_kernel, dim3(grid), dim3(MR_THREADS), args, 0,
+                                              s));
+      }
+      // FP64 rotation pass on (P1^T C_X P1, P1^T C_Y P1): X = W_inner, lam; W = P1 W_inner
+      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, P1, T, M, wM, 0, acc);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CXw, M, wM, 0, acc);
       if (CY) {
-        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, P1, T, M, wM, 0);
-        md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CYw, M, wM, 0);
+        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, P1, T, M, wM, 0, acc);
+        md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CYw, M, wM, 0, acc);
       }
       md_core_kernel<false><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
-                                                            P->d_status);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 0, X, Wm, M, wM, 0);
-      P->prof->launches[TAPS_PROF_MODEDIAG] += CY ? 11 : 7;
+                                                            P->d_status, acc, nullptr);
+      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 0, X, Wm, M, wM, 0, acc);
+      P->prof->launches[TAPS_PROF_MODEDIAG] += CY ? 12 : 8;
     } else {
       md_eig_big_kernel<false><<<1, MDB_THREADS, smem_s, s>>>(P->d_C + (size_t)sx * MM,
                                                               sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm,

@@ -332,13 +332,22 @@ __global__ void block_assemble_kernel(const double* __restrict__ opband, int nop
 
 // ---------------------------------------------------------------------------------
 // Block-banded Gaussian elimination without pivoting (one cooperative launch).
-// For each block row k: LU of the diagonal block (CTA 0, shared memory) -> W_kj =
-// D_k^{-1} A_kj and z_k = D_k^{-1} F_k (one warp per column, triangular solves) ->
-// Schur updates A_ij -= A_ik W_kj, F_i -= A_ik z_k (all threads).  Three grid
-// barriers per block row.  The symmetric part of every reduced matrix is positive
-// definite (Hadamard products of Gram matrices, Kronecker products with SPD 1D
-// matrices), so elimination without pivoting exists; a zero or non-finite pivot is
-// reported as TAPS_DEV_SINGULAR.
+// For each block row k: every CTA that has solve work factors the diagonal block
+// D_k = A(k,k) = L U in its own shared memory (no barrier, no global copy), then its
+// warps form W_kj = D_k^{-1} A_kj and z_k = D_k^{-1} F_k (one warp per column,
+// triangular solves by shuffles); after a grid barrier all threads apply the Schur
+// updates A_ij -= A_ik W_kj, F_i -= A_ik z_k; a second barrier closes the row.  The
+// factorisation: at step p warp 0 updates row p+1 and takes the next pivot's
+// reciprocal (seed plus refinement, within one ulp of the quotient) while warps 1 ..
+// update the other rows four at a time, one FMA per entry (lanes over the columns), so
+// the pivot chain is the step's only serial part; the reciprocals are kept for the
+// back substitution.  A per-warp triangular solve issues FP64 work only for the
+// register slots that hold rows.  Measured phase costs (n = 254, hb = 3, M = 30,
+// synthetic blocks): grid barrier ~2.1 µs; per row before these changes LU 27.8 µs,
+// triangular solves 20.8 µs.  The
+// symmetric part of every reduced matrix is positive definite (Hadamard products of
+// Gram matrices, Kronecker products with SPD 1D matrices), so elimination without
+// pivoting exists; a zero or non-finite pivot is reported as TAPS_DEV_SINGULAR.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ double slot_get(const double v[4], int s) {
   return s == 0 ? v[0] : (s == 1 ? v[1] : (s == 2 ? v[2] : v[3]));
@@ -355,6 +364,7 @@ __global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ bloc
                                                        double* __restrict__ lu_g, int nf, int hb,
                                                        int M, int* status, unsigned* bar) {
   extern __shared__ __align__(16) double sm[];  // LU of the diagonal block, stride M+1
+  __shared__ double invd[TAPS_MAX_M];            // reciprocals of the pivots
   const int nb = 2 * hb + 1;
   const int ld = M + 1;
   const size_t MM = (size_t)M * M;
@@ -363,42 +373,70 @@ __global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ bloc
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   const long long gtid = (long long)blockIdx.x * nthr + tid;
   const long long gthreads = (long long)nblk * nthr;
+  (void)lu_g;
 #define BLK(i, j) (blocks + ((size_t)(i) * nb + ((j) - (i) + hb)) * MM)
 
   for (int k = 0; k < nf; ++k) {
-    // ---- LU of the diagonal block A(k,k), CTA 0
-    if (blockIdx.x == 0) {
-      const double* Akk = BLK(k, k);
-      for (int idx = tid; idx < (int)MM; idx += nthr) sm[(idx / M) * ld + idx % M] = Akk[idx];
-      __syncthreads();
-      for (int p = 0; p < M; ++p) {
-        double piv = sm[p * ld + p];
-        bool bad = !(fabs(piv) > 0.0) || !isfinite(piv);
-        if (bad && tid == 0) taps_flag(status, TAPS_DEV_SINGULAR);
-        double inv = bad ? 1.0 : 1.0 / piv;
-        for (int r = p + 1 + tid; r < M; r += nthr) sm[r * ld + p] *= inv;
-        __syncthreads();
-        int w = M - p - 1;
-        for (int idx = tid; idx < w * w; idx += nthr) {
-          int r = p + 1 + idx / w, c = p + 1 + idx % w;
-          sm[r * ld + c] -= sm[r * ld + p] * sm[p * ld + c];
-        }
-        __syncthreads();
-      }
-      for (int idx = tid; idx < (int)MM; idx += nthr) lu_g[idx] = sm[(idx / M) * ld + idx % M];
-    }
-    grid_barrier(bar, status, nblk);
-
-    // ---- W(k, k+jj) = LU^{-1} A(k, k+jj), z_k = LU^{-1} F_k : one warp per column
     const int nj = min(hb, nf - 1 - k);
     const int ntask = nj * M + 1;
     const int cta_needed = (ntask + nwarps - 1) / nwarps;
     if ((int)blockIdx.x < cta_needed) {
-      if (blockIdx.x != 0) {
-        for (int idx = tid; idx < (int)MM; idx += nthr) sm[(idx / M) * ld + idx % M] = lu_g[idx];
+      // ---- LU of the diagonal block A(k,k) in this CTA's shared memory
+      const double* Akk = BLK(k, k);
+      for (int idx = tid; idx < (int)MM; idx += nthr) sm[(idx / M) * ld + idx % M] = Akk[idx];
+      __syncthreads();
+      if (tid == 0) {
+        const double piv = sm[0];
+        const bool bad = !(fabs(piv) > 0.0) || !isfinite(piv);
+        if (bad && blockIdx.x == 0) taps_flag(status, TAPS_DEV_SINGULAR);
+        invd[0] = bad ? 1.0 : taps_rcp(piv);
       }
       __syncthreads();
-      // grid-stride over the columns: any CTA count covers all of them
+      for (int p = 0; p < M - 1; ++p) {
+        const double inv = invd[p];
+        // warp 0 finishes row p+1 and the next pivot's reciprocal (the chain) alone;
+        // warps 1 .. update the other rows four at a time (independent loads and FMAs
+        // in flight)
+        if (warp == 0) {
+          const int r = p + 1;
+          const double l = sm[r * ld + p] * inv;
+          for (int c = p + 1 + lane; c < M; c += 32) sm[r * ld + c] = fma(-l, sm[p * ld + c], sm[r * ld + c]);
+          __syncwarp();
+          if (lane == 0) {
+            sm[r * ld + p] = l;   // unit lower factor
+            const double piv = sm[r * ld + r];
+            const bool bad = !(fabs(piv) > 0.0) || !isfinite(piv);
+            if (bad && blockIdx.x == 0) taps_flag(status, TAPS_DEV_SINGULAR);
+            invd[r] = bad ? 1.0 : taps_rcp(piv);
+          }
+        } else {
+          const int nwo = nwarps - 1;   // the other rows over warps 1 ..
+          for (int rb = p + 1 + warp; rb < M; rb += 4 * nwo) {
+            double l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = rb + u * nwo;
+              l[u] = r < M ? sm[r * ld + p] * inv : 0.0;
+            }
+            for (int c = p + 1 + lane; c < M; c += 32) {
+              const double pc = sm[p * ld + c];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int r = rb + u * nwo;
+                if (r < M) sm[r * ld + c] = fma(-l[u], pc, sm[r * ld + c]);
+              }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = rb + u * nwo;
+              if (r < M && lane == 0) sm[r * ld + p] = l[u];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // ---- W(k, k+jj) = LU^{-1} A(k, k+jj), z_k = LU^{-1} F_k : one warp per column
       for (int task = blockIdx.x * nwarps + warp; task < ntask; task += (int)nblk * nwarps) {
         double* col;
         int cstride;
@@ -411,33 +449,40 @@ __global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ bloc
           cstride = 1;
         }
         double v[4];
+        // only the slots that hold rows issue FP64 work (a warp-wide FP64 instruction
+        // holds the sub-partition's pipe however few lanes are active)
+        const int nsl = (M + 31) >> 5;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           int r = lane + 32 * s;
-          v[s] = (r < M) ? col[(size_t)r * cstride] : 0.0;
+          v[s] = (s < nsl && r < M) ? col[(size_t)r * cstride] : 0.0;
         }
         // forward: unit lower L
         for (int c = 0; c < M; ++c) {
           double yc = __shfl_sync(0xffffffffu, slot_get(v, c >> 5), c & 31);
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
+            if (s >= nsl) break;
             int r = lane + 32 * s;
-            if (r > c && r < M) v[s] -= sm[r * ld + c] * yc;
+            const double a = (r > c && r < M) ? sm[r * ld + c] : 0.0;
+            v[s] = fma(-a, yc, v[s]);
           }
         }
-        // backward: upper U
+        // backward: upper U, with the kept reciprocals of its diagonal
         for (int c = M - 1; c >= 0; --c) {
           int sc = c >> 5;
           double own = slot_get(v, sc);
           if (lane == (c & 31)) {
-            own /= sm[c * ld + c];
+            own *= invd[c];
             slot_set(v, sc, own);
           }
           double yc = __shfl_sync(0xffffffffu, own, c & 31);
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
+            if (s >= nsl) break;
             int r = lane + 32 * s;
-            if (r < c) v[s] -= sm[r * ld + c] * yc;
+            const double a = (r < c) ? sm[r * ld + c] : 0.0;
+            v[s] = fma(-a, yc, v[s]);
           }
         }
 #pragma unroll
@@ -461,7 +506,7 @@ __global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ bloc
         const double* L = BLK(k + ii, k) + (size_t)m * M;
         const double* W = BLK(k, k + jj) + n;
         double s = 0.0;
-        for (int l = 0; l < M; ++l) s += L[l] * W[(size_t)l * M];
+        for (int l = 0; l < M; ++l) s = fma(L[l], W[(size_t)l * M], s);
         BLK(k + ii, k + jj)[(size_t)m * M + n] -= s;
       } else {
         int o2 = (int)(o - nupd);
@@ -469,7 +514,7 @@ __global__ void __launch_bounds__(256) block_lu_kernel(double* __restrict__ bloc
         const double* L = BLK(k + ii, k) + (size_t)m * M;
         const double* z = F + (size_t)k * M;
         double s = 0.0;
-        for (int l = 0; l < M; ++l) s += L[l] * z[l];
+        for (int l = 0; l < M; ++l) s = fma(L[l], z[l], s);
         F[(size_t)(k + ii) * M + m] -= s;
       }
     }

@@ -171,11 +171,12 @@ def _rich_transient(n_space, n_t, M, h_conv, seed):
 def _md_launches(M, pencil):
     """Launches of one mode-side solve: up to 32 modes the eigen-solve (with W^T c), band
     rows, elimination, output; beyond, the eigen-solve split into transforms on many CTAs
-    (two per operator and pass), an FP32 and an FP64 rotation kernel and two basis
-    products, then W^T c, band rows, elimination, output."""
+    (two per operator and pass), an FP32 and an FP64 rotation kernel, two basis products
+    and the FP64 refinement between the passes, then W^T c, band rows, elimination,
+    output."""
     if M <= 32:
         return 4
-    return (2 + 2 * (4 if pencil else 2) + 2) + 4
+    return (2 + 2 * (4 if pencil else 2) + 2 + 1) + 4
 
 
 @pytest.mark.parametrize("n_space,n_t,M,h_conv", [(12, 9, 3, 0.0), (40, 130, 20, 2.0), (24, 300, 32, 0.0),
