@@ -497,6 +497,22 @@ int taps_util_barrier_test(int ctas, int missing, long long poll_limit, void* st
  * Asynchronous; TAPS_ERR_INVALID_ARG for n < 0 or null pointers with n > 0. */
 int taps_util_rcp(const double* x_dev, double* y_dev, long long n, void* stream);
 
+/* ---- the eigen-solve of the mode-side diagonalisation (Sec. 2.6) on its own -------
+ * For the M x M pencil of a mode-side solve, C_X symmetric positive definite and C_Y
+ * symmetric (both row-major device arrays; only their symmetric parts are used; CY_dev
+ * may be NULL for a single operator, lam = 0 then): W (row-major device M x M, column j
+ * the generalised eigenvector of C_Y w = lam_j C_X w, W^T C_X W = I) and lam (device
+ * [M]), computed as the mode-side solve computes them for 32 < M from a cold start:
+ * FP32 Jacobi rotations, then FP64 first-order corrections of the basis by matrix
+ * products, and FP64 rotations when a correction is rejected.  *refined (host int,
+ * may be NULL) receives 1 when the corrections were accepted, 0 when the rotation pass
+ * ran.  Synchronous on `stream` (a cudaStream_t or NULL); allocates its workspace.
+ * TAPS_ERR_INVALID_ARG for M outside (32, TAPS_MAX_M], M > 116 (S and V must fit in
+ * shared memory) or null pointers; TAPS_ERR_SINGULAR when C_X is not positive definite
+ * (a Cholesky pivot below -1e-8 times the largest diagonal entry). */
+int taps_util_md_pencil(const double* CX_dev, const double* CY_dev, int M, double* W_dev, double* lam_dev,
+                        int* refined, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1430,6 +1430,71 @@ static cudaError_t md_band_launch(const double* bx, const double* by, const doub
   return cudaGetLastError();
 }
 
+// The eigen-solve of one mode-side solve, 32 < M with S and V in shared memory: the
+// pencil transforms with the previous basis (identity when *wM != M), FP32 rotations,
+// the FP64 refinement, and the FP64 rotation pass when the refinement is not accepted.
+// gw: 14 M^2 + 8 doubles of workspace; on return Wm, lam and *wM hold the new basis.
+static int md_eig_split(const double* CX, const double* CY, int M, double* Wm, int* wM, double* lam, double* gw,
+                        int* status, int num_sms, cudaStream_t s) {
+  const size_t MM = (size_t)M * M;
+  const int Np = M + (M & 1);
+  const size_t smem_sv = sizeof(double) * ((size_t)Np * (Np + 1) + (size_t)M * M);
+  double* T = gw + 2 * MM;
+  double* P1 = gw + 3 * MM;
+  double* CXw = gw + 4 * MM;
+  double* CYw = gw + 5 * MM;
+  double* X = gw + 6 * MM;
+  const dim3 gg((M + 15) / 16, (M + 15) / 16);
+  MrBufs rb;
+  rb.Xa = gw + 7 * MM;
+  rb.Xb = gw + 8 * MM;
+  rb.T1 = gw + 9 * MM;
+  rb.T2 = gw + 10 * MM;
+  rb.A = gw + 11 * MM;
+  rb.B = gw + 12 * MM;
+  rb.F = gw + 13 * MM;
+  rb.maxbits = (unsigned long long*)(gw + 14 * MM);
+  rb.bar = (unsigned*)(gw + 14 * MM + MR_MAX_STEPS);
+  int* acc = (int*)(gw + 14 * MM + MR_MAX_STEPS + 1);
+  int* floored = (int*)(gw + 14 * MM + MR_MAX_STEPS + 2);
+  const int* no_skip = nullptr;
+  // the previous basis P (identity when cold): CXw = P^T C_X P, CYw = P^T C_Y P
+  md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, Wm, T, M, wM, 1, no_skip);
+  md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CXw, M, wM, 2, no_skip);
+  if (CY) {
+    md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, Wm, T, M, wM, 1, no_skip);
+    md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CYw, M, wM, 2, no_skip);
+  }
+  // FP32 rotations: X, then P1 = P X
+  md_core_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
+                                                       status, no_skip, floored);
+  md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 0, X, P1, M, wM, 3, no_skip);
+  // FP64 corrections of P1 by matrix products (many CTAs); accepted, they give W
+  // and lam and the FP64 rotation pass below returns at once
+  {
+    const int ntt = ((M + 15) / 16) * ((M + 15) / 16);
+    const int grid = std::max(1, std::min(2 * ntt, num_sms));
+    TAPS_CUDA(cudaMemsetAsync(rb.bar, 0, 2 * sizeof(unsigned), s));
+    const double* X0 = P1;
+    void* args[] = {(void*)&CX, (void*)&CY, (void*)&M, (void*)&X0, (void*)&rb, (void*)&Wm,
+                    (void*)&lam, (void*)&wM, (void*)&acc, (void*)&floored, (void*)&status};
+    TAPS_CUDA(cudaLaunchCooperativeKernel((const void*)md_refine_kernel, dim3(grid), dim3(MR_THREADS), args, 0,
+                                          s));
+  }
+  // FP64 rotation pass on (P1^T C_X P1, P1^T C_Y P1): X = W_inner, lam; W = P1 W_inner
+  md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, P1, T, M, wM, 0, acc);
+  md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CXw, M, wM, 0, acc);
+  if (CY) {
+    md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, P1, T, M, wM, 0, acc);
+    md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CYw, M, wM, 0, acc);
+  }
+  md_core_kernel<false><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
+                                                        status, acc, nullptr);
+  md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 0, X, Wm, M, wM, 0, acc);
+  TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
 // Reduced solve of dim d on the mode side, coefficients in P->d_C / P->d_c; the
 // previous factor goes to P->d_Uold.
 int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
@@ -1463,61 +1528,9 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
     const size_t smem_sv = smem_s + sizeof(double) * (size_t)M * M;
     if (smem_sv <= (size_t)MDB_SMEM_SV_MAX) {
       // transforms and basis products on many CTAs, the sequential part on one
-      const double* CX = P->d_C + (size_t)sx * MM;
-      const double* CY = sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr;
-      double* T = gw + 2 * MM;
-      double* P1 = gw + 3 * MM;
-      double* CXw = gw + 4 * MM;
-      double* CYw = gw + 5 * MM;
-      double* X = gw + 6 * MM;
-      const dim3 gg((M + 15) / 16, (M + 15) / 16);
-      MrBufs rb;
-      rb.Xa = gw + 7 * MM;
-      rb.Xb = gw + 8 * MM;
-      rb.T1 = gw + 9 * MM;
-      rb.T2 = gw + 10 * MM;
-      rb.A = gw + 11 * MM;
-      rb.B = gw + 12 * MM;
-      rb.F = gw + 13 * MM;
-      rb.maxbits = (unsigned long long*)(gw + 14 * MM);
-      rb.bar = (unsigned*)(gw + 14 * MM + MR_MAX_STEPS);
-      int* acc = (int*)(gw + 14 * MM + MR_MAX_STEPS + 1);
-      int* floored = (int*)(gw + 14 * MM + MR_MAX_STEPS + 2);
-      const int* no_skip = nullptr;
-      // the previous basis P (identity when cold): CXw = P^T C_X P, CYw = P^T C_Y P
-      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, Wm, T, M, wM, 1, no_skip);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CXw, M, wM, 2, no_skip);
-      if (CY) {
-        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, Wm, T, M, wM, 1, no_skip);
-        md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CYw, M, wM, 2, no_skip);
-      }
-      // FP32 rotations: X, then P1 = P X
-      md_core_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
-                                                           P->d_status, no_skip, floored);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 0, X, P1, M, wM, 3, no_skip);
-      // FP64 corrections of P1 by matrix products (many CTAs); accepted, they give W
-      // and lam and the FP64 rotation pass below returns at once
-      {
-        const int ntt = ((M + 15) / 16) * ((M + 15) / 16);
-        const int grid = std::max(1, std::min(2 * ntt, P->num_sms));
-        TAPS_CUDA(cudaMemsetAsync(rb.bar, 0, 2 * sizeof(unsigned), s));
-        const double* X0 = P1;
-        void* args[] = {(void*)&CX, (void*)&CY, (void*)&M, (void*)&X0, (void*)&rb, (void*)&Wm,
-                        (void*)&lam, (void*)&wM, (void*)&acc, (void*)&floored, (void*)&P->d_status};
-        TAPS_CUDA(cudaLaunchCooperativeKernel((const void*)md_refine_kernel, dim3(grid), dim3(MR_THREADS), args, 0,
-                                              s));
-      }
-      // FP64 rotation pass on (P1^T C_X P1, P1^T C_Y P1): X = W_inner, lam; W = P1 W_inner
-      md_gemm_kernel<<<gg, 256, 0, s>>>(CX, 0, P1, T, M, wM, 0, acc);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CXw, M, wM, 0, acc);
-      if (CY) {
-        md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, P1, T, M, wM, 0, acc);
-        md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CYw, M, wM, 0, acc);
-      }
-      md_core_kernel<false><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
-                                                            P->d_status, acc, nullptr);
-      md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 0, X, Wm, M, wM, 0, acc);
-      P->prof->launches[TAPS_PROF_MODEDIAG] += CY ? 12 : 8;
+      TAPS_TRY(md_eig_split(P->d_C + (size_t)sx * MM, sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm, wM,
+                            lam, gw, P->d_status, P->num_sms, s));
+      P->prof->launches[TAPS_PROF_MODEDIAG] += sy >= 0 ? 12 : 8;
     } else {
       md_eig_big_kernel<false><<<1, MDB_THREADS, smem_s, s>>>(P->d_C + (size_t)sx * MM,
                                                               sy >= 0 ? P->d_C + (size_t)sy * MM : nullptr, M, Wm,
@@ -1547,5 +1560,46 @@ int taps_md_solve(taps_problem* P, taps_factors* U, int d) {
            10.0 * Md * Md * Md + Md * n * (2.0 * hb * hb + 6.0 * hb + 2.0 * Rf) + 2.0 * (double)nM * M,
            8.0 * (2.0 * bsz + (double)Rf * n + 3.0 * (double)nM + (double)n * (hb + 1) * M));
   TAPS_CUDA(cudaGetLastError());
+  return TAPS_OK;
+}
+
+// The eigen-solve of a mode-side solve on its own (exposed so that it can be tested
+// against a dense symmetric-definite eigensolver): cold start, 32 < M with S and V in
+// shared memory.  Synchronous on `stream`.
+extern "C" int taps_util_md_pencil(const double* CX, const double* CY, int M, double* W, double* lam, int* refined,
+                                   void* stream) {
+  if (!CX || !W || !lam || M <= 32 || M > TAPS_MAX_M) return TAPS_ERR_INVALID_ARG;
+  const int Np = M + (M & 1);
+  if (sizeof(double) * ((size_t)Np * (Np + 1) + (size_t)M * M) > (size_t)MDB_SMEM_SV_MAX) return TAPS_ERR_INVALID_ARG;
+  int dev = 0, maxsm = 0, num_sms = 0;
+  TAPS_CUDA(cudaGetDevice(&dev));
+  TAPS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  TAPS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  TAPS_TRY(taps_md_setup(maxsm));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t MM = (size_t)M * M;
+  double* gw = nullptr;
+  int* dint = nullptr;   // [0] basis mode count (0: cold), [1] status
+  TAPS_TRY(taps_alloc((void**)&gw, sizeof(double) * (14 * MM + 8)));
+  if (taps_alloc((void**)&dint, 2 * sizeof(int)) != TAPS_OK) {
+    cudaFree(gw);
+    return TAPS_ERR_CUDA;
+  }
+  int st = TAPS_OK;
+  int h[2] = {0, 0}, acc = 0;
+  if (cudaMemsetAsync(dint, 0, 2 * sizeof(int), s) != cudaSuccess) st = TAPS_ERR_CUDA;
+  if (st == TAPS_OK) st = md_eig_split(CX, CY, M, W, dint, lam, gw, dint + 1, num_sms, s);
+  if (st == TAPS_OK) {
+    if (cudaMemcpyAsync(h, dint, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&acc, gw + 14 * MM + MR_MAX_STEPS + 1, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = TAPS_ERR_CUDA;
+  }
+  cudaFree(gw);
+  cudaFree(dint);
+  if (st != TAPS_OK) return st;
+  if (h[1] != TAPS_DEV_OK) return taps_status_from_device(h[1]);
+  if (refined) *refined = acc;
   return TAPS_OK;
 }

@@ -138,6 +138,7 @@ SIGNATURES = {
     "taps_factors_from_profiles": (_i, [_vp, _vp, _i, _vp, _i, _d]),
     "taps_profile_get": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong), _pd, _pd, _pd]),
     "taps_util_rcp": (_i, [_vp, _vp, ctypes.c_longlong, _vp]),
+    "taps_util_md_pencil": (_i, [_vp, _vp, _i, _vp, _vp, _pi, _vp]),
 }
 
 PROF_CLASSES = ["gram", "coeff", "block_assemble", "block_lu", "backsub", "normalize",
@@ -186,6 +187,18 @@ def rcp(x, y):
     """y = 1 / x with the small solves' reciprocal (x, y: CUDA float64 tensors)."""
     check(lib().taps_util_rcp(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                               x.numel(), current_stream()), "taps_util_rcp")
+
+
+def md_pencil(CX, CY, W, lam):
+    """The mode-side eigen-solve on one pencil (taps_util_md_pencil): CX, CY (CY may be
+    None), W CUDA float64 M x M tensors, lam CUDA float64 [M]; returns 1 if the FP64
+    corrections were accepted, 0 if the FP64 rotation pass ran."""
+    ref = ctypes.c_int()
+    cy = ctypes.c_void_p(CY.data_ptr()) if CY is not None else ctypes.c_void_p(0)
+    check(lib().taps_util_md_pencil(ctypes.c_void_p(CX.data_ptr()), cy, CX.shape[0], ctypes.c_void_p(W.data_ptr()),
+                                    ctypes.c_void_p(lam.data_ptr()), ctypes.byref(ref), current_stream()),
+          "taps_util_md_pencil")
+    return ref.value
 
 
 def dim_desc(dm):
