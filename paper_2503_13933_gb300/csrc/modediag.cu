@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(MD_THREADS) md_eig_kernel(const double* __rest
 // steps and their arithmetic are those of md_eig_kernel; W^T c_r is left to
 // md_cw_kernel, spread over many CTAs.
 #define MDB_THREADS 512
+#define MDC_THREADS 1024   // md_core_kernel: more threads shorten each one's chain of pair updates per round
 #define MDB_SMEM_SV_MAX (220 * 1024)   // S and V together in dynamic shared memory up to this size
 // VSH: the basis V also lives in shared memory, after S (when both fit: Np <= 116);
 // its round-by-round row-pair updates are then shared-memory traffic instead of L2
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_eig_big_kernel(const double* _
 // without, they run in FP64 to convergence and X, diag(S) are the pass's basis and
 // eigenvalues.
 template <bool F32>
-__global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __restrict__ CX,
+__global__ void __launch_bounds__(MDC_THREADS) md_core_kernel(const double* __restrict__ CX,
                                                               const double* __restrict__ CY, int M,
                                                               double* __restrict__ Xout, int* __restrict__ wM,
                                                               double* __restrict__ lam, double* __restrict__ gw,
@@ -702,6 +703,7 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
   __shared__ int rp[TAPS_MAX_M / 2], rq[TAPS_MAX_M / 2];
   __shared__ float rcf[TAPS_MAX_M / 2], rsf[TAPS_MAX_M / 2];
   __shared__ int rotated, failed, floored;
+  __shared__ float smax32;
   if (skip && *skip) return;   // the refinement already delivered the basis
   const int tid = threadIdx.x, nt = blockDim.x;
   const int Np = M + (M & 1), ld = Np + 1;
@@ -747,6 +749,172 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
     }
     __syncthreads();
   }
+  const int N = Np, half = N / 2;
+  if (F32) {
+    // The seed is formed in FP32 throughout (FP32 dependent latency is a small fraction of
+    // FP64's): L and T = L^-1 C_Y in V's region, S = L^-1 T^T then in S's region (C_Y,
+    // read once, is dead by then), the basis V_32 (column-major) in V's region.  Its
+    // error, ~kappa(L) 2^-24 against the spectral gaps, is what the FP64 corrections
+    // remove.
+    float* L32 = reinterpret_cast<float*>(Vt);   // [M][M]
+    float* T32 = L32 + (size_t)M * M;             // [M][M]
+    float* S32 = reinterpret_cast<float*>(Ssh);   // [Np][ld]
+    float* V32 = reinterpret_cast<float*>(Vt);    // [M][M], after L32 and T32
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx - i * M;
+      L32[idx] = (j <= i) ? (float)L[idx] : 0.f;
+    }
+    __syncthreads();
+    if (tid < M) {   // T = L^-1 C_Y, thread per column
+      const int col = tid;
+      for (int i = 0; i < M; ++i) {
+        float a = (float)SB(i, col);
+        for (int j = 0; j < i; ++j) a = fmaf(-L32[i * M + j], T32[j * M + col], a);
+        T32[i * M + col] = a * (float)linv[i];
+      }
+    }
+    __syncthreads();
+    if (tid < M) {   // S = L^-1 T^T, thread per column, into S's region as FP32
+      const int col = tid;
+      for (int i = 0; i < M; ++i) {
+        float a = T32[col * M + i];
+        for (int j = 0; j < i; ++j) a = fmaf(-L32[i * M + j], S32[j * ld + col], a);
+        S32[i * ld + col] = a * (float)linv[i];
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < Np * ld; idx += nt) {   // symmetric part; zero padding
+      const int i = idx / ld, j = idx - i * ld;
+      if (i >= M || j >= M) S32[idx] = 0.f;
+      else if (i < j) {
+        const float a = 0.5f * (S32[idx] + S32[j * ld + i]);
+        S32[idx] = a;
+        S32[j * ld + i] = a;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) V32[idx] = (idx / M == idx % M) ? 1.f : 0.f;
+    if (tid < 32) {   // the largest diagonal magnitude: the absolute floor of the rotations
+      float m = 0.f;
+      for (int i = tid; i < M; i += 32) m = fmaxf(m, fabsf(S32[i * ld + i]));
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (tid == 0) smax32 = m;
+    }
+    __syncthreads();
+    // The FP32 basis only seeds the FP64 corrections, which converge from an error of
+    // ~1e-3 against the spectral gaps: a pair is rotated while its coupling exceeds
+    // 1e-5 of its diagonal entries (and 1e-7 of the largest one).  A tighter threshold
+    // would chase FP32 rounding noise (~6e-8 of a row's scale) and keep rotating.
+    const float abs_floor = 1e-7f * smax32;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
+      if (tid == 0) rotated = 0;
+      __syncthreads();
+      for (int r = 0; r < N - 1; ++r) {
+        if (tid < half) {
+          int a, b;
+          if (tid == 0) {
+            a = r;
+            b = N - 1;
+          } else {
+            a = (r + tid) % (N - 1);
+            b = (r - tid + N - 1) % (N - 1);
+          }
+          const int p = min(a, b), q = max(a, b);
+          float cs = 1.f, sn = 0.f;
+          if (q < M) {
+            const float apq = S32[p * ld + q], app = S32[p * ld + p], aqq = S32[q * ld + q];
+            if (fabsf(apq) > 1e-5f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > abs_floor && fabsf(apq) > 1e-30f) {
+              // the rotation's chain is the round's serial part: approximate quotient,
+              // square root and reciprocal square root (cs^2 + sn^2 = 1 to FP32 accuracy)
+              const float th = __fdividef(aqq - app, 2.f * apq);
+              float t;
+              if (fabsf(th) > 1e18f) {
+                t = __fdividef(0.5f, th);
+              } else {
+                t = __fdividef(1.f, fabsf(th) + __fsqrt_rn(fmaf(th, th, 1.f)));
+                if (th < 0.f) t = -t;
+              }
+              cs = rsqrtf(fmaf(t, t, 1.f));
+              sn = t * cs;
+              rotated = 1;
+            }
+          }
+          rcf[tid] = cs;
+          rsf[tid] = sn;
+          rp[tid] = p;
+          rq[tid] = q;
+        }
+        __syncthreads();
+        // the round's rotations applied as two passes over contiguous data (rows, then
+        // columns: S <- J^T S J), so that shared-memory accesses do not collide in
+        // banks (row stride ld is odd), with the basis rows of V^T in the row pass.
+        // Warp w takes the pairs w, w + 32, ... (its rotation read once), lanes the
+        // entries of the pair's rows or columns.
+        for (int l = wid; l < half; l += nw) {
+          const float sl = rsf[l];
+          if (sl == 0.f) continue;
+          const float cl = rcf[l];
+          const int pl = rp[l], ql = rq[l];
+          float* Sp = S32 + pl * ld;
+          float* Sq = S32 + ql * ld;
+#pragma unroll 4
+          for (int c = lane; c < N; c += 32) {
+            const float a = Sp[c], bq = Sq[c];
+            Sp[c] = cl * a - sl * bq;
+            Sq[c] = sl * a + cl * bq;
+          }
+          if (ql < M) {
+            float* Vp = V32 + pl * M;
+            float* Vq = V32 + ql * M;
+#pragma unroll 4
+            for (int c = lane; c < M; c += 32) {
+              const float vp = Vp[c], vq = Vq[c];
+              Vp[c] = cl * vp - sl * vq;
+              Vq[c] = sl * vp + cl * vq;
+            }
+          }
+        }
+        __syncthreads();
+        for (int l = wid; l < half; l += nw) {
+          const float sl = rsf[l];
+          if (sl == 0.f) continue;
+          const float cl = rcf[l];
+          const int pl = rp[l], ql = rq[l];
+#pragma unroll 4
+          for (int r2 = lane; r2 < N; r2 += 32) {
+            const float a = S32[r2 * ld + pl], bq = S32[r2 * ld + ql];
+            S32[r2 * ld + pl] = (r2 == ql) ? 0.f : cl * a - sl * bq;
+            S32[r2 * ld + ql] = (r2 == pl) ? 0.f : sl * a + cl * bq;
+          }
+        }
+        __syncthreads();
+      }
+      if (!rotated) break;
+      __syncthreads();
+    }
+    // X = L^-T V_32 (thread per column, bottom row first), in FP32 with L reloaded into
+    // S's region (dead now) and X beside it
+    float* Lb = S32;
+    float* X32 = S32 + (size_t)M * M;
+    for (int idx = tid; idx < M * M; idx += nt) {
+      const int i = idx / M, j = idx - i * M;
+      Lb[idx] = (j <= i) ? (float)L[idx] : 0.f;
+    }
+    __syncthreads();
+    if (tid < M) {
+      const int col = tid;
+      for (int i = M - 1; i >= 0; --i) {
+        float a = V32[col * M + i];
+        for (int j = i + 1; j < M; ++j) a = fmaf(-Lb[j * M + i], X32[j * M + col], a);
+        X32[i * M + col] = a * (float)linv[i];
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * M; idx += nt) Xout[idx] = (double)X32[idx];
+    if (tid == 0 && floored_out) *floored_out = floored | failed;
+    return;
+  }
   // X = L^-1 C_Y into T (thread per column), then S = L^-1 X^T (thread per column)
   if (tid < M) {
     const int col = tid;
@@ -776,128 +944,6 @@ __global__ void __launch_bounds__(MDB_THREADS) md_core_kernel(const double* __re
     Vt[idx] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  const int N = Np, half = N / 2;
-  if (F32) {
-    // S in FP32 in V's region, the FP32 basis (column-major) in S's region
-    float* S32 = reinterpret_cast<float*>(Vt);
-    float* V32 = reinterpret_cast<float*>(Ssh);
-    for (int idx = tid; idx < Np * ld; idx += nt) {
-      const int i = idx / ld, j = idx - i * ld;
-      S32[idx] = (i < M && j < M) ? (float)SB(i, j) : 0.f;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < M * M; idx += nt) V32[idx] = (idx / M == idx % M) ? 1.f : 0.f;
-    __syncthreads();
-    // half is even or odd: with odd half the middle row pairs with itself, so the
-    // folded count is half (half + 1) / 2 either way
-    const int ntri = half * (half + 1) / 2;
-    const int vi = tid & 127, vl0 = tid >> 7;
-    for (int sw = 0; sw < MD_MAX_SWEEPS && M > 1; ++sw) {
-      if (tid == 0) rotated = 0;
-      __syncthreads();
-      for (int r = 0; r < N - 1; ++r) {
-        if (tid < half) {
-          int a, b;
-          if (tid == 0) {
-            a = r;
-            b = N - 1;
-          } else {
-            a = (r + tid) % (N - 1);
-            b = (r - tid + N - 1) % (N - 1);
-          }
-          const int p = min(a, b), q = max(a, b);
-          float cs = 1.f, sn = 0.f;
-          if (q < M) {
-            const float apq = S32[p * ld + q], app = S32[p * ld + p], aqq = S32[q * ld + q];
-            if (fabsf(apq) > 6.0e-8f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-30f) {
-              const float th = (aqq - app) / (2.f * apq);
-              float t;
-              if (fabsf(th) > 1e18f) {
-                t = 0.5f / th;
-              } else {
-                t = 1.f / (fabsf(th) + sqrtf(th * th + 1.f));
-                if (th < 0.f) t = -t;
-              }
-              cs = 1.f / sqrtf(t * t + 1.f);
-              sn = t * cs;
-              rotated = 1;
-            }
-          }
-          rcf[tid] = cs;
-          rsf[tid] = sn;
-          rp[tid] = p;
-          rq[tid] = q;
-        }
-        __syncthreads();
-        // pair blocks (k, l), k <= l, enumerated without the lower half: rows k and
-        // half-1-k of the triangle together hold half+1 blocks
-        for (int idx = tid; idx < ntri; idx += nt) {
-          int k, l;
-          const int q = idx / (half + 1), rr = idx - q * (half + 1);
-          if (rr < half - q) {
-            k = q;
-            l = q + rr;
-          } else {
-            k = half - 1 - q;
-            l = k + rr - (half - q);
-          }
-          const float sk = rsf[k], sl = rsf[l];
-          if (sk == 0.f && sl == 0.f) continue;
-          const float ck = rcf[k], cl = rcf[l];
-          const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
-          const float b00 = S32[pk * ld + pl], b01 = S32[pk * ld + ql], b10 = S32[qk * ld + pl],
-                      b11 = S32[qk * ld + ql];
-          const float t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
-          const float t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
-          const float n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
-          const float n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
-          if (k == l) {
-            S32[pk * ld + pk] = n00;
-            S32[qk * ld + qk] = n11;
-            S32[pk * ld + qk] = 0.f;
-            S32[qk * ld + pk] = 0.f;
-          } else {
-            S32[pk * ld + pl] = n00;
-            S32[pk * ld + ql] = n01;
-            S32[qk * ld + pl] = n10;
-            S32[qk * ld + ql] = n11;
-            S32[pl * ld + pk] = n00;
-            S32[ql * ld + pk] = n01;
-            S32[pl * ld + qk] = n10;
-            S32[ql * ld + qk] = n11;
-          }
-        }
-        // V <- V J: thread (row i = tid mod 128, pairs l = tid / 128 + 4 j)
-        if (vi < M)
-          for (int l = vl0; l < half; l += nt >> 7) {
-            const float sl = rsf[l];
-            if (sl != 0.f) {
-              const float cl = rcf[l];
-              const int pl = rp[l], ql = rq[l];
-              if (ql < M) {
-                const float vp = V32[pl * M + vi], vq = V32[ql * M + vi];
-                V32[pl * M + vi] = cl * vp - sl * vq;
-                V32[ql * M + vi] = sl * vp + cl * vq;
-              }
-            }
-          }
-        __syncthreads();
-      }
-      if (!rotated) break;
-      __syncthreads();
-    }
-    // X = L^-T V_32 (thread per column, bottom row first)
-    if (tid < M) {
-      const int col = tid;
-      for (int i = M - 1; i >= 0; --i) {
-        double s = (double)V32[col * M + i];
-        for (int j = i + 1; j < M; ++j) s -= L[j * M + i] * Xout[j * M + col];
-        Xout[i * M + col] = s * linv[i];
-      }
-    }
-    if (tid == 0 && floored_out) *floored_out = floored | failed;
-    return;
-  }
   if (N > M) {
     for (int j = tid; j < N; j += nt) {
       SB(M, j) = 0.0;
@@ -1048,8 +1094,8 @@ __global__ void __launch_bounds__(256) md_gemm_kernel(const double* __restrict__
 // the Rayleigh quotients lam_i = S_ii / (1 - R_ii)), i.e. F_ii = R_ii / 2 and
 // F_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for i != j.  Each correction is about
 // the square of the previous one while the error is small against the gaps of lam
-// (the FP32 rotations deliver ~1e-4; three corrections reach the FP64 rounding
-// floor).  A step whose largest |F| exceeds MR_FAIL (no quadratic regime: a cluster
+// (the FP32 seed's error is ~kappa(L) 2^-24 against them; three or four corrections
+// reach the FP64 rounding floor, at most five are taken).  A step whose largest |F| exceeds MR_FAIL (no quadratic regime: a cluster
 // or a poor start) ends the refinement unaccepted, and so does a non-finite entry;
 // once max |F| <= MR_DONE the corrected basis goes to Wout, lam to lam_out and *acc
 // = 1 (the FP64 rotation pass is then skipped).  Not attempted when the FP32 pass
@@ -1058,7 +1104,7 @@ __global__ void __launch_bounds__(256) md_gemm_kernel(const double* __restrict__
 // are separated by bounded grid barriers, and every CTA takes the same decisions from
 // the same global maximum.
 #define MR_THREADS 256
-#define MR_MAX_STEPS 4
+#define MR_MAX_STEPS 5
 #define MR_FAIL 0.1
 #define MR_DONE 1e-9
 struct MrBufs {
@@ -1466,7 +1512,7 @@ static int md_eig_split(const double* CX, const double* CY, int M, double* Wm, i
     md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 1, T, CYw, M, wM, 2, no_skip);
   }
   // FP32 rotations: X, then P1 = P X
-  md_core_kernel<true><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
+  md_core_kernel<true><<<1, MDC_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
                                                        status, no_skip, floored);
   md_gemm_kernel<<<gg, 256, 0, s>>>(Wm, 0, X, P1, M, wM, 3, no_skip);
   // FP64 corrections of P1 by matrix products (many CTAs); accepted, they give W
@@ -1488,7 +1534,7 @@ static int md_eig_split(const double* CX, const double* CY, int M, double* Wm, i
     md_gemm_kernel<<<gg, 256, 0, s>>>(CY, 0, P1, T, M, wM, 0, acc);
     md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 1, T, CYw, M, wM, 0, acc);
   }
-  md_core_kernel<false><<<1, MDB_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
+  md_core_kernel<false><<<1, MDC_THREADS, smem_sv, s>>>(CXw, CY ? CYw : nullptr, M, X, wM, lam, gw,
                                                         status, acc, nullptr);
   md_gemm_kernel<<<gg, 256, 0, s>>>(P1, 0, X, Wm, M, wM, 0, acc);
   TAPS_CUDA(cudaGetLastError());
