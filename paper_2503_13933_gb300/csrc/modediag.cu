@@ -704,6 +704,7 @@ __global__ void __launch_bounds__(MDC_THREADS) md_core_kernel(const double* __re
   __shared__ float rcf[TAPS_MAX_M / 2], rsf[TAPS_MAX_M / 2];
   __shared__ int rotated, failed, floored;
   __shared__ float smax32;
+  __shared__ double rmin_s, rmax_s;
   if (skip && *skip) return;   // the refinement already delivered the basis
   const int tid = threadIdx.x, nt = blockDim.x;
   const int Np = M + (M & 1), ld = Np + 1;
@@ -712,7 +713,11 @@ __global__ void __launch_bounds__(MDC_THREADS) md_core_kernel(const double* __re
   double* Vt = Ssh + (size_t)Np * ld;    // column-major basis: Vt[c * M + r] = V[r][c]
   double* T = gw + 2 * MM;               // row-major temporary
 #define SB(i, j) Ssh[(size_t)(i) * ld + (j)]
-  if (tid == 0) failed = floored = 0;
+  if (tid == 0) {
+    failed = floored = 0;
+    rmin_s = INFINITY;
+    rmax_s = 0.0;
+  }
   for (int idx = tid; idx < M * M; idx += nt) {
     const int i = idx / M, j = idx % M;
     L[idx] = 0.5 * (CX[i * M + j] + CX[j * M + i]);
@@ -737,6 +742,8 @@ __global__ void __launch_bounds__(MDC_THREADS) md_core_kernel(const double* __re
       const double r = sqrt(piv);
       L[k * M + k] = r;
       linv[k] = taps_rcp(r);
+      rmin_s = fmin(rmin_s, r);
+      rmax_s = fmax(rmax_s, r);
     }
     __syncthreads();
     const double il = linv[k];
@@ -760,29 +767,70 @@ __global__ void __launch_bounds__(MDC_THREADS) md_core_kernel(const double* __re
     float* T32 = L32 + (size_t)M * M;             // [M][M]
     float* S32 = reinterpret_cast<float*>(Ssh);   // [Np][ld]
     float* V32 = reinterpret_cast<float*>(Vt);    // [M][M], after L32 and T32
-    for (int idx = tid; idx < M * M; idx += nt) {
-      const int i = idx / M, j = idx - i * M;
-      L32[idx] = (j <= i) ? (float)L[idx] : 0.f;
-    }
-    __syncthreads();
-    if (tid < M) {   // T = L^-1 C_Y, thread per column
-      const int col = tid;
-      for (int i = 0; i < M; ++i) {
-        float a = (float)SB(i, col);
-        for (int j = 0; j < i; ++j) a = fmaf(-L32[i * M + j], T32[j * M + col], a);
-        T32[i * M + col] = a * (float)linv[i];
+    // FP32 transforms only while L is well conditioned (its diagonal within a factor 64):
+    // their error grows with kappa(L); otherwise the FP64 transforms, then S to FP32
+    const bool tr32 = rmax_s <= 64.0 * rmin_s;
+    if (tr32) {
+      for (int idx = tid; idx < M * M; idx += nt) {
+        const int i = idx / M, j = idx - i * M;
+        L32[idx] = (j <= i) ? (float)L[idx] : 0.f;
       }
-    }
-    __syncthreads();
-    if (tid < M) {   // S = L^-1 T^T, thread per column, into S's region as FP32
-      const int col = tid;
-      for (int i = 0; i < M; ++i) {
-        float a = T32[col * M + i];
-        for (int j = 0; j < i; ++j) a = fmaf(-L32[i * M + j], S32[j * ld + col], a);
-        S32[i * ld + col] = a * (float)linv[i];
+      __syncthreads();
+      if (tid < M) {   // T = L^-1 C_Y, thread per column
+        const int col = tid;
+        for (int i = 0; i < M; ++i) {
+          float a = (float)SB(i, col);
+          for (int j = 0; j < i; ++j) a = fmaf(-L32[i * M + j], T32[j * M + col], a);
+          T32[i * M + col] = a * (float)linv[i];
+        }
       }
+      __syncthreads();
+      if (tid < M) {   // S = L^-1 T^T, thread per column, into S's region as FP32
+        const int col = tid;
+        for (int i = 0; i < M; ++i) {
+          float a = T32[col * M + i];
+          for (int j = 0; j < i; ++j) a = fmaf(-L32[i * M + j], S32[j * ld + col], a);
+          S32[i * ld + col] = a * (float)linv[i];
+        }
+      }
+      __syncthreads();
+    } else {
+      // X = L^-1 C_Y into T (thread per column), then S = L^-1 X^T (thread per column)
+      if (tid < M) {
+        const int col = tid;
+        for (int i = 0; i < M; ++i) {
+          double s = SB(i, col);
+          for (int j = 0; j < i; ++j) s -= L[i * M + j] * T[j * M + col];
+          T[i * M + col] = s * linv[i];
+        }
+      }
+      __syncthreads();
+      if (tid < M) {
+        const int col = tid;
+        for (int i = 0; i < M; ++i) {
+          double s = T[col * M + i];
+          for (int j = 0; j < i; ++j) s -= L[i * M + j] * SB(j, col);
+          SB(i, col) = s * linv[i];
+        }
+      }
+      __syncthreads();
+      // S (FP64) to FP32 in place: every thread reads its entries before any is written
+      // (16 per thread cover Np (Np + 1) <= 116 x 117 entries with the 1024 threads)
+      float sv[16];
+      const int per = (Np * ld + nt - 1) / nt;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int idx = tid + u * nt;
+        sv[u] = (u < per && idx < Np * ld) ? (float)Ssh[idx] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int idx = tid + u * nt;
+        if (u < per && idx < Np * ld) S32[idx] = sv[u];
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int idx = tid; idx < Np * ld; idx += nt) {   // symmetric part; zero padding
       const int i = idx / ld, j = idx - i * ld;
       if (i >= M || j >= M) S32[idx] = 0.f;
@@ -893,25 +941,36 @@ __global__ void __launch_bounds__(MDC_THREADS) md_core_kernel(const double* __re
       if (!rotated) break;
       __syncthreads();
     }
-    // X = L^-T V_32 (thread per column, bottom row first), in FP32 with L reloaded into
-    // S's region (dead now) and X beside it
-    float* Lb = S32;
-    float* X32 = S32 + (size_t)M * M;
-    for (int idx = tid; idx < M * M; idx += nt) {
-      const int i = idx / M, j = idx - i * M;
-      Lb[idx] = (j <= i) ? (float)L[idx] : 0.f;
-    }
-    __syncthreads();
-    if (tid < M) {
-      const int col = tid;
-      for (int i = M - 1; i >= 0; --i) {
-        float a = V32[col * M + i];
-        for (int j = i + 1; j < M; ++j) a = fmaf(-Lb[j * M + i], X32[j * M + col], a);
-        X32[i * M + col] = a * (float)linv[i];
+    if (tr32) {
+      // X = L^-T V_32 (thread per column, bottom row first), in FP32 with L reloaded into
+      // S's region (dead now) and X beside it
+      float* Lb = S32;
+      float* X32 = S32 + (size_t)M * M;
+      for (int idx = tid; idx < M * M; idx += nt) {
+        const int i = idx / M, j = idx - i * M;
+        Lb[idx] = (j <= i) ? (float)L[idx] : 0.f;
+      }
+      __syncthreads();
+      if (tid < M) {
+        const int col = tid;
+        for (int i = M - 1; i >= 0; --i) {
+          float a = V32[col * M + i];
+          for (int j = i + 1; j < M; ++j) a = fmaf(-Lb[j * M + i], X32[j * M + col], a);
+          X32[i * M + col] = a * (float)linv[i];
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < M * M; idx += nt) Xout[idx] = (double)X32[idx];
+    } else {   // X = L^-T V_32 in FP64 (thread per column, bottom row first)
+      if (tid < M) {
+        const int col = tid;
+        for (int i = M - 1; i >= 0; --i) {
+          double a = (double)V32[col * M + i];
+          for (int j = i + 1; j < M; ++j) a -= L[j * M + i] * Xout[j * M + col];
+          Xout[i * M + col] = a * linv[i];
+        }
       }
     }
-    __syncthreads();
-    for (int idx = tid; idx < M * M; idx += nt) Xout[idx] = (double)X32[idx];
     if (tid == 0 && floored_out) *floored_out = floored | failed;
     return;
   }
