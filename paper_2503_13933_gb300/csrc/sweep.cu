@@ -76,8 +76,7 @@ __device__ __forceinline__ void coeff_c(const TermTable& tt, const GramPtrs& gp,
 __device__ __forceinline__ void coeff_entry(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
                                             double* C, double* c) {
   if (idx < M * M) coeff_C(tt, gp, d, M, idx, C);
-  if (idx < M)
-    for (int r = 0; r < tt.Rf; ++r) coeff_c(tt, gp, d, M, r, idx, c);
+  if (idx < tt.Rf * M) coeff_c(tt, gp, d, M, idx / M, idx % M, c);   // one thread per (r, m)
 }
 
 __global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
@@ -99,8 +98,7 @@ __global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call,
 __device__ __forceinline__ void coeff_entry_slots(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
                                                   double* C, double* c) {
   if (idx < M * M) coeff_C_slots(tt, gp, d, M, idx, C);
-  if (idx < M)
-    for (int r = 0; r < tt.Rf; ++r) coeff_c(tt, gp, d, M, r, idx, c);
+  if (idx < tt.Rf * M) coeff_c(tt, gp, d, M, idx / M, idx % M, c);   // one thread per (r, m)
 }
 
 __global__ void coeff_slots_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
@@ -236,6 +234,93 @@ static GramPtrs gram_ptrs(const taps_problem* P) {
 }
 
 static int coefficients(taps_problem* P, int d, int M);
+// ---------------------------------------------------------------------------------
+// Gram refresh of a long dim with many modes (FP64; M > 32, n >= 256): the banded
+// products Y_o = Op_o U once for the whole dim (spmm_kernel), then W = U^T [Y_0 | ... |
+// Q] (Q the n x R_f source projections) as a tiled contraction over the nodes: CTA
+// (row chunk, 32 x 32 output tile) accumulates KC nodes of its tile (8 x 32 threads,
+// four outputs each, operands staged 32 nodes at a time), its partial goes to the
+// workspace, and gram_gemm_reduce_kernel adds the chunks' partials in chunk order.
+// Every mode tile no longer rebuilds the banded products, and the reduction is over
+// n / KC chunks instead of n / 8.
+// ---------------------------------------------------------------------------------
+#define GG_KC 256
+__global__ void spmm_kernel(const double* __restrict__ U, int nf, int M, int hb,
+                            const double* __restrict__ opband, int nops, double* __restrict__ Y);
+__global__ void __launch_bounds__(256) gram_gemm_kernel(const double* __restrict__ U, int nf, int M,
+                                                        const double* __restrict__ Y, int nops,
+                                                        const double* __restrict__ q, int Rf,
+                                                        double* __restrict__ partial) {
+  __shared__ double Us[32][33], Bs[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int ncol = nops * M + Rf;
+  const int ntc = (ncol + 31) / 32;
+  const int tm = blockIdx.y / ntc, tc = blockIdx.y % ntc;
+  const int m0 = tm * 32, c0 = tc * 32;
+  const int k0 = blockIdx.x * GG_KC, k1 = min(nf, k0 + GG_KC);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int kb = k0; kb < k1; kb += 32) {
+    // U rows kb.. (node index fastest: coalesced in the column-major factor)
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int mm = e >> 5, kk = e & 31;
+      const int i = kb + kk, m = m0 + mm;
+      Us[kk][mm] = (i < k1 && m < M) ? U[(size_t)m * nf + i] : 0.0;
+    }
+    // B columns c0..: Y_o (row-major, column fastest) or Q (node fastest)
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int kk = e >> 5, cc = e & 31;
+      const int i = kb + kk, c = c0 + cc;
+      if (c >= nops * M && c < ncol) continue;   // source columns: the loop below
+      double v = 0.0;
+      if (i < k1 && c < nops * M) {
+        const int o = c / M, n = c - o * M;
+        v = Y[((size_t)o * nf + i) * M + n];
+      }
+      Bs[kk][cc] = v;
+    }
+    if (c0 + 31 >= nops * M) {   // the tile reaches the source columns
+      for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        const int cc = e >> 5, kk = e & 31;
+        const int i = kb + kk, c = c0 + cc;
+        if (c >= nops * M && c < ncol) Bs[kk][cc] = (i < k1) ? q[(size_t)(c - nops * M) * nf + i] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double b = Bs[kk][tx];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fma(Us[kk][ty + 8 * j], b, acc[j]);
+    }
+    __syncthreads();
+  }
+  double* out = partial + (size_t)blockIdx.x * M * ncol;
+  const int c = c0 + tx;
+  if (c < ncol)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = m0 + ty + 8 * j;
+      if (m < M) out[(size_t)m * ncol + c] = acc[j];
+    }
+}
+
+// gram[o][m][n] and h[r][m] from the chunks' partials W[m][col], added in chunk order.
+__global__ void gram_gemm_reduce_kernel(const double* __restrict__ partial, int nchunk, int M, int nops, int Rf,
+                                        double* __restrict__ gram, double* __restrict__ h) {
+  const int ncol = nops * M + Rf;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)M * ncol) return;
+  const int m = (int)(e / ncol), c = (int)(e % ncol);
+  double s = 0.0;
+  for (int ch = 0; ch < nchunk; ++ch) s += partial[(size_t)ch * M * ncol + e];
+  if (c < nops * M) {
+    const int o = c / M, n = c - o * M;
+    gram[((size_t)o * M + m) * M + n] = s;
+  } else {
+    h[(size_t)(c - nops * M) * M + m] = s;
+  }
+}
+
 
 int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision, int coeff_dim) {
   if (P->tt.cs > TAPS_NUM_OPS && coeff_dim >= 0) {
@@ -243,7 +328,7 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
     TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, -1));
     const int M = U->M;
     int tk = prof_begin(P, TAPS_PROF_COEFF);
-    TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+    TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((std::max(M * M, P->Rf * M) + 127) / 128), dim3(128), 0, P->stream, P->tt,
                               gram_ptrs(P), coeff_dim, M, P->d_C, P->d_c));
     prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D, 8.0 * ((double)P->R * M * M * P->D));
     return TAPS_OK;
@@ -273,6 +358,27 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
     prof_end(P, TAPS_PROF_GRAM, tk, nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M,
              8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf + (double)nops * M * M +
                     (double)Rf * M));
+    TAPS_CUDA(cudaGetLastError());
+    if (coeff_dim >= 0) TAPS_TRY(coefficients(P, coeff_dim, M));
+    return TAPS_OK;
+  }
+  if (precision != TAPS_FP32 && precision != TAPS_BF16 && M > 32 && nf >= 256 &&
+      (size_t)((nf + GG_KC - 1) / GG_KC) * M * (nops * M + Rf) <= P->partial_len) {
+    // long dim, many modes: banded products once, then the tiled contraction
+    int tk = prof_begin(P, TAPS_PROF_GRAM);
+    const long long ny = (long long)nops * nf * M;
+    spmm_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, P->stream>>>(U->d_U[d], nf, M, hb, P->d_opband[d], nops,
+                                                                     P->d_Y);
+    const int ncol = nops * M + Rf;
+    const int nkc = (nf + GG_KC - 1) / GG_KC;
+    gram_gemm_kernel<<<dim3(nkc, ((M + 31) / 32) * ((ncol + 31) / 32)), 256, 0, P->stream>>>(
+        U->d_U[d], nf, M, P->d_Y, nops, P->d_q[d], Rf, P->d_partial);
+    const long long nout = (long long)M * ncol;
+    gram_gemm_reduce_kernel<<<(unsigned)((nout + 255) / 256), 256, 0, P->stream>>>(P->d_partial, nkc, M, nops, Rf,
+                                                                                   P->d_gram[d], P->d_h[d]);
+    P->prof->launches[TAPS_PROF_GRAM] += 2;
+    prof_end(P, TAPS_PROF_GRAM, tk, gflops - (coeff_dim >= 0 ? (double)P->R * M * M * P->D + (double)P->Rf * M * P->D : 0.0),
+             gbytes);
     TAPS_CUDA(cudaGetLastError());
     if (coeff_dim >= 0) TAPS_TRY(coefficients(P, coeff_dim, M));
     return TAPS_OK;
@@ -791,10 +897,10 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
 static int coefficients(taps_problem* P, int d, int M) {
   int tk = prof_begin(P, TAPS_PROF_COEFF);
   if (P->tt.cs > TAPS_NUM_OPS)
-    TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+    TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((std::max(M * M, P->Rf * M) + 127) / 128), dim3(128), 0, P->stream, P->tt,
                               gram_ptrs(P), d, M, P->d_C, P->d_c));
   else
-    TAPS_CUDA(taps_launch_pdl(coeff_kernel, dim3((M * M + 127) / 128), dim3(128), 0, P->stream, P->tt,
+    TAPS_CUDA(taps_launch_pdl(coeff_kernel, dim3((std::max(M * M, P->Rf * M) + 127) / 128), dim3(128), 0, P->stream, P->tt,
                               gram_ptrs(P), d, M, P->d_C, P->d_c));
   prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D + (double)P->Rf * M * P->D,
            8.0 * ((double)P->R * M * M * P->D));
@@ -1088,10 +1194,10 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     if (!grams_current) TAPS_TRY(taps_refresh_grams(P, U, TAPS_FP64));
     int tk = prof_begin(P, TAPS_PROF_COEFF);
     if (P->tt.cs > TAPS_NUM_OPS)
-      TAPS_CUDA(taps_launch_pdl(coeff_all_slots_kernel, dim3((M * M + 127) / 128, P->D), dim3(128), 0, s,
+      TAPS_CUDA(taps_launch_pdl(coeff_all_slots_kernel, dim3((std::max(M * M, P->Rf * M) + 127) / 128, P->D), dim3(128), 0, s,
                                 P->tt, gram_ptrs(P), M, P->d_Call, P->d_call));
     else
-      TAPS_CUDA(taps_launch_pdl(coeff_all_kernel, dim3((M * M + 127) / 128, P->D), dim3(128), 0, s, P->tt,
+      TAPS_CUDA(taps_launch_pdl(coeff_all_kernel, dim3((std::max(M * M, P->Rf * M) + 127) / 128, P->D), dim3(128), 0, s, P->tt,
                                 gram_ptrs(P), M, P->d_Call, P->d_call));
     prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D * P->D,
              8.0 * ((double)P->R * M * M * P->D * P->D));
