@@ -873,10 +873,11 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
 // swaps it into place and takes the pivot's reciprocal; then warp w updates the rows
 // r = p+1+w, p+5+w, ... (lanes over the columns c > p, coalesced) with one FMA per
 // entry, T[r][c] -= l_r T[p][c], l_r = T[r][p] / T[p][p] (as a product with the
-// reciprocal, seed plus refinement).  The trailing update is FP64 FMA issue on all
-// four SM sub-partitions (eight warps, so that two CTAs per SM keep four warps on each
-// sub-partition); two barriers per step.  Back substitution column by column: x_r = b_r / U_rr, then
-// every thread removes x_r from its rows' right-hand sides.  A zero or non-finite
+// reciprocal, seed plus refinement, formed by warp 0 for all rows at once).  The
+// trailing update is FP64 FMA issue on all four SM sub-partitions (eight warps, so that
+// two CTAs per SM keep four warps on each sub-partition); two barriers per step.  Back
+// substitution column by column: x_r = b_r U_rr^-1 (the kept reciprocal), then every
+// thread removes x_r from its rows' right-hand sides.  A zero or non-finite
 // pivot is reported as TAPS_DEV_SINGULAR.
 __global__ void __launch_bounds__(256) fd_small_solve_kernel(const double* __restrict__ CA,
                                                              const double* __restrict__ CB,
@@ -884,7 +885,8 @@ __global__ void __launch_bounds__(256) fd_small_solve_kernel(const double* __res
                                                              const double* __restrict__ G, int M,
                                                              double* __restrict__ Y, int* status) {
   extern __shared__ double T[];   // [M][M+1]: matrix | rhs
-  __shared__ double pinv;
+  __shared__ double invd[TAPS_MAX_M];   // reciprocals of the pivots
+  __shared__ double lmul[TAPS_MAX_M];   // the step's multipliers, by row
   __shared__ int bad;
   const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -917,26 +919,26 @@ __global__ void __launch_bounds__(256) fd_small_solve_kernel(const double* __res
           T[br * ld + c] = t;
         }
       __syncwarp();
+      const double pv = T[p * ld + p];
+      const bool ok = pv != 0.0 && isfinite(pv);
+      const double inv = ok ? taps_rcp(pv) : 0.0;
       if (lane == 0) {
-        const double pv = T[p * ld + p];
-        const bool ok = pv != 0.0 && isfinite(pv);
-        pinv = ok ? taps_rcp(pv) : 0.0;
+        invd[p] = inv;
         if (!ok) bad = 1;
       }
+      // the multipliers of every row below, lanes over rows: one FP64 instruction per
+      // 32 rows instead of one per row in the update warps
+      for (int r = p + 1 + lane; r < M; r += 32) lmul[r] = T[r * ld + p] * inv;
     }
     __syncthreads();
-    const double inv = pinv;
     for (int r = p + 1 + warp; r < M; r += nw) {
-      const double l = T[r * ld + p] * inv;
+      const double l = lmul[r];
       for (int c = p + 1 + lane; c <= M; c += 32) T[r * ld + c] = fma(-l, T[p * ld + c], T[r * ld + c]);
     }
     __syncthreads();
   }
   for (int r = M - 1; r >= 0; --r) {
-    if (tid == 0) {
-      const double pv = T[r * ld + r];
-      T[r * ld + M] = (pv != 0.0) ? T[r * ld + M] / pv : 0.0;
-    }
+    if (tid == 0) T[r * ld + M] *= invd[r];   // the kept reciprocal (0 for a bad pivot)
     __syncthreads();
     const double xr = T[r * ld + M];
     for (int k = tid; k < r; k += nt) T[k * ld + M] = fma(-T[k * ld + r], xr, T[k * ld + M]);
