@@ -434,6 +434,13 @@ def run_config5(args, taps, W, torch, stream, hbm_peak):
                 b.synchronize()
                 ti.append(a.elapsed_time(b))
             out["warm_start"]["init_ms"] = float(np.mean(ti))
+            # per-class time of the warm-started FP64 run (events around every class)
+            P.profile_reset(events=True)
+            _, rw = run_ws(taps.FP64)
+            prof = P.profile()
+            out["warm_start"]["classes_ms_per_sweep"] = {c: v["ms"] / max(rw["sweeps"], 1)
+                                                         for c, v in prof.items() if v["launches"]}
+            P.profile_reset(events=False)
             # the first sweep from each start: the residuals after it
             ws.init_factors(P, U, desc)
             P.sweep(U, 1, solver=taps.SOLVER_FASTDIAG)
