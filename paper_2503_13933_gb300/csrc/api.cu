@@ -89,6 +89,7 @@ struct SweepGraph {
   int M, precision, solver, res_kind, ws_M;
   bool events;                   // captured with timing-event nodes
   bool failed;
+  bool c0_skip;                  // its sweep reuses dim 0's coefficients from before the replay
   cudaGraph_t g;
   cudaGraphExec_t exec;
   long long dl[TAPS_PROF_NUM];   // per-replay profiling increments
@@ -137,16 +138,23 @@ static int graph_build(taps_problem* P, taps_factors* U, int prec, int solver, i
   P->stream = P->cap_stream;
   int st = TAPS_OK;
   S->capturing = true;
+  // capture runs nothing: the coefficient state is the pre-capture one until a replay
+  const int c0_before = P->c0_valid, c0_M_before = P->c0_M;
+  P->c0_skipped = 0;
   if (cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     st = TAPS_ERR_CUDA;
   } else {
-    st = taps_sweep_enqueue(P, U, prec, solver, 1);
-    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind, !taps_low_prec(prec));
+    st = taps_sweep_enqueue(P, U, prec, solver, 1, 0);
+    if (st == TAPS_OK) st = taps_residual_enqueue(P, U, res_kind, !taps_low_prec(prec), 0);
+    if (st == TAPS_OK) st = taps_results_to_host(P, 2 * U->M * P->D, taps_residual_npart(P, res_kind));
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
     if (ce != cudaSuccess || g == nullptr) st = (st == TAPS_OK) ? TAPS_ERR_CUDA : st;
     G->g = g;
   }
+  G->c0_skip = P->c0_skipped != 0;
+  P->c0_valid = c0_before;
+  P->c0_M = c0_M_before;
   P->stream = saved;
   S->capturing = false;
   cudaGetLastError();
@@ -221,6 +229,7 @@ struct LoopGraph {
   int M, precision, solver, ws_M, max_sweeps;
   double res_tol, als_tol;
   bool failed;
+  bool c0_skip;       // the body's sweep reuses dim 0's coefficients (see SweepGraph)
   cudaGraph_t g;
   cudaGraphExec_t exec;
   cudaGraphConditionalHandle h;
@@ -294,6 +303,8 @@ static int loop_build(taps_problem* P, taps_factors* U, int prec, int solver, do
     cudaStream_t saved = P->stream;
     P->stream = P->cap_stream;
     S->capturing = true;
+    const int c0_before = P->c0_valid, c0_M_before = P->c0_M;
+    P->c0_skipped = 0;
     if (cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess) {
       st = TAPS_ERR_CUDA;
@@ -308,6 +319,9 @@ static int loop_build(taps_problem* P, taps_factors* U, int prec, int solver, do
       cudaGraph_t out = nullptr;
       if (cudaStreamEndCapture(P->cap_stream, &out) != cudaSuccess) st = (st == TAPS_OK) ? TAPS_ERR_CUDA : st;
     }
+    L->c0_skip = P->c0_skipped != 0;
+    P->c0_valid = c0_before;
+    P->c0_M = c0_M_before;
     P->stream = saved;
     S->capturing = false;
     cudaGetLastError();
@@ -357,8 +371,11 @@ static int loop_solve(taps_problem* P, taps_factors* U, int prec, int solver, do
     L = (LoopGraph*)P->loop_graph;
   }
   cudaStream_t s = P->stream;
+  if (L->c0_skip && !(P->c0_valid && P->c0_M == U->M)) TAPS_TRY(taps_coefficients(P, 0, U->M));
   TAPS_CUDA(cudaMemsetAsync(L->d_state, 0, sizeof(int) * 4, s));
   TAPS_CUDA(cudaGraphLaunch(L->exec, s));
+  P->c0_valid = 1;   // every body ends with the last dim's refresh forming them
+  P->c0_M = U->M;
   TAPS_CUDA(cudaMemcpyAsync(L->h_state, L->d_state, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   TAPS_CUDA(cudaMemcpyAsync(L->h_hist, L->d_hist, sizeof(double) * 2 * (size_t)max_sweeps, cudaMemcpyDeviceToHost,
                             s));
@@ -406,7 +423,10 @@ static int graph_sweep(taps_problem* P, taps_factors* U, int prec, int solver, i
     }
     G = (SweepGraph*)P->graph;
   }
+  if (G->c0_skip && !(P->c0_valid && P->c0_M == U->M)) TAPS_TRY(taps_coefficients(P, 0, U->M));
   TAPS_CUDA(cudaGraphLaunch(G->exec, P->stream));
+  P->c0_valid = 1;   // the sweep's last dim formed them
+  P->c0_M = U->M;
   TAPS_CUDA(cudaStreamSynchronize(P->stream));
   ProfState* S = P->prof;
   for (int c = 0; c < TAPS_PROF_NUM; ++c) {
@@ -483,6 +503,10 @@ static void free_ws(taps_problem* P) {
   cudaFree(P->d_partial);
   cudaFree(P->d_scal);
   cudaFree(P->d_bigG);
+  cudaFree(P->d_Yres);
+  P->d_Yres = nullptr;
+  cudaFree(P->d_ticket_all);
+  P->d_ticket_all = nullptr;
   if (P->h_scal) cudaFreeHost(P->h_scal);
   if (P->h_part) cudaFreeHost(P->h_part);
   P->h_part = nullptr;
@@ -523,8 +547,9 @@ int taps_ws_ensure(taps_problem* P, int M) {
   if (M <= P->ws_M) return TAPS_OK;
   if (P->stream) TAPS_CUDA(cudaStreamSynchronize(P->stream));
   free_ws(P);
+  P->c0_valid = 0;
   int nbmax = 0, D = P->D;
-  size_t part = 0, bigG = 0;
+  size_t part = 0, bigG = 0, yres = 0, part_all = 0;
   for (int d = 0; d < D; ++d) {
     const taps_dim* dm = P->dims[d];
     int nops = P->tt.nops[d];
@@ -534,12 +559,17 @@ int taps_ws_ensure(taps_problem* P, int M) {
     TAPS_TRY(taps_alloc((void**)&P->d_Usnap[d], sizeof(double) * dm->nf * M));
     size_t gp = (size_t)((dm->nf + 7) / 8) * (nops * M * M + P->Rf * M);
     part = std::max(part, gp);
+    part_all += gp;
     size_t NC = (size_t)nops * M + P->Rf;
     bigG += NC * NC;
+    yres += (size_t)nops * dm->nf * M;
   }
   size_t als_part = 0;
   for (int d = 0; d < D; ++d) als_part += 2 * (((size_t)P->dims[d]->nf + 7) / 8);   // 8 rows per CTA
   part = std::max(part, als_part);
+  // the all-dims Gram refresh needs every dim's chunk partials at once: allowed up to 32 MB
+  P->gram_all_ok = part_all <= ((size_t)1 << 22);
+  if (P->gram_all_ok) part = std::max(part, part_all);
   part = std::max(part, (size_t)3 * 64);
   size_t MM = (size_t)M * M;
   int nfm = P->nf_max;
@@ -550,6 +580,8 @@ int taps_ws_ensure(taps_problem* P, int M) {
   TAPS_TRY(taps_alloc((void**)&P->d_call, sizeof(double) * D * P->Rf * M));
   TAPS_TRY(taps_alloc((void**)&P->d_ticket, sizeof(unsigned) * 64));   // >= M / 8 + 1
   TAPS_CUDA(cudaMemsetAsync(P->d_ticket, 0, sizeof(unsigned) * 64, P->stream));
+  TAPS_TRY(taps_alloc((void**)&P->d_ticket_all, sizeof(unsigned) * 32 * TAPS_MAX_DIMS));
+  TAPS_CUDA(cudaMemsetAsync(P->d_ticket_all, 0, sizeof(unsigned) * 32 * TAPS_MAX_DIMS, P->stream));
   TAPS_TRY(taps_alloc((void**)&P->d_F, sizeof(double) * nfm * M));
   TAPS_TRY(taps_alloc((void**)&P->d_blocks, sizeof(double) * nfm * nbmax * MM));
   TAPS_TRY(taps_alloc((void**)&P->d_lu, sizeof(double) * MM));
@@ -561,6 +593,7 @@ int taps_ws_ensure(taps_problem* P, int M) {
   TAPS_TRY(taps_alloc((void**)&P->d_partial, sizeof(double) * part));
   TAPS_TRY(taps_alloc((void**)&P->d_scal, sizeof(double) * 2 * M * D + 64));
   TAPS_TRY(taps_alloc((void**)&P->d_bigG, sizeof(double) * bigG));
+  TAPS_TRY(taps_alloc((void**)&P->d_Yres, sizeof(double) * yres));
   TAPS_CUDA(cudaMallocHost((void**)&P->h_scal, sizeof(double) * (2 * M * D + 64)));
   TAPS_CUDA(cudaMallocHost((void**)&P->h_part, sizeof(double) * part));
   P->partial_len = part;
@@ -928,28 +961,44 @@ extern "C" const double* taps_factors_device_ptr(const taps_factors* U, int d) {
 }
 
 // Columns [m0, m1) of U_d by the init rule (SplitMix64 draws or zero/one).
-__global__ void init_cols_kernel(double* U, int nf, int m0, int m1, int d, int kind, unsigned seed) {
+// Columns m0..m1-1 of every dim's factor in one launch (thread per entry; the dims'
+// entries one after another).
+struct InitCols {
+  double* U[TAPS_MAX_DIMS];
+  long long off[TAPS_MAX_DIMS + 1];   // prefix of nf_d (m1 - m0)
+  int nf[TAPS_MAX_DIMS];
+  int D;
+};
+
+__global__ void init_cols_kernel(InitCols ic, int m0, int m1, int kind, unsigned seed) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long tot = (long long)nf * (m1 - m0);
-  if (idx >= tot) return;
-  int i = idx % nf, m = m0 + (int)(idx / nf);
+  if (idx >= ic.off[ic.D]) return;
+  int d = 0;
+  while (d + 1 < ic.D && idx >= ic.off[d + 1]) ++d;
+  const long long loc = idx - ic.off[d];
+  const int nf = ic.nf[d];
+  int i = loc % nf, m = m0 + (int)(loc / nf);
   double v;
   if (kind == TAPS_INIT_RANDOM) v = taps_uniform_pm1(seed, d, i, m);
   else v = (d == 0) ? 0.0 : 1.0;
-  U[(size_t)m * nf + i] = v;
+  ic.U[d][(size_t)m * nf + i] = v;
 }
 
 static int init_columns(taps_problem* P, taps_factors* U, int m0, int m1, int kind, unsigned seed) {
   if (m1 <= m0) return TAPS_OK;
+  InitCols ic;
+  memset(&ic, 0, sizeof(ic));
+  ic.D = P->D;
   for (int d = 0; d < P->D; ++d) {
-    int nf = P->dims[d]->nf;
-    long long tot = (long long)nf * (m1 - m0);
-    int tk = prof_begin(P, TAPS_PROF_OTHER);
-    init_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, P->stream>>>(U->d_U[d], nf, m0, m1, d,
-                                                                           kind, seed);
-    prof_end(P, TAPS_PROF_OTHER, tk, 0.0, 8.0 * tot);
-    TAPS_CUDA(cudaGetLastError());
+    ic.U[d] = U->d_U[d];
+    ic.nf[d] = P->dims[d]->nf;
+    ic.off[d + 1] = ic.off[d] + (long long)ic.nf[d] * (m1 - m0);
   }
+  const long long tot = ic.off[P->D];
+  int tk = prof_begin(P, TAPS_PROF_OTHER);
+  init_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, P->stream>>>(ic, m0, m1, kind, seed);
+  prof_end(P, TAPS_PROF_OTHER, tk, 0.0, 8.0 * tot);
+  TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }
 
@@ -1510,7 +1559,14 @@ static int batch_capture(taps_batch* B) {
     bool cap = P->prof->capturing;
     P->prof->capturing = true;    // no event-pool growth or synchronisation inside capture
     cudaStreamWaitEvent(P->cap_stream, B->fork, 0);
+    // the batch graph replays after batched Gram refreshes too: it forms dim 0's
+    // coefficients itself
+    const int c0_before = P->c0_valid, c0_M_before = P->c0_M;
+    P->c0_forbid = 1;
     if (st == TAPS_OK) st = taps_sweep_enqueue(P, B->U[i], B->precision, B->eff_solver, 1);
+    P->c0_forbid = 0;
+    P->c0_valid = c0_before;
+    P->c0_M = c0_M_before;
     cudaEventRecord(B->join[i], P->cap_stream);
     cudaStreamWaitEvent(B->master, B->join[i], 0);
     P->prof->capturing = cap;
@@ -1740,6 +1796,7 @@ extern "C" int taps_batch_refresh_grams(taps_batch* B, int precision, float* ms_
       if (cudaEventRecord(e1, B->master) != cudaSuccess) st = TAPS_ERR_CUDA;
     } else {
       const int dev_sms = B->P[0]->num_sms;
+      for (int i = 0; i < B->count; ++i) B->P[i]->c0_valid = 0;   // Grams replaced, no coefficients formed
       const size_t need = taps_gram_tc_queue_bytes((int)items.size(), (int)chunks64);
       if (need > B->gt_buf_bytes) {
         if (B->gt_buf) cudaFree(B->gt_buf);

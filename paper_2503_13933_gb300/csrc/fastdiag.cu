@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(RG_WARPS * 32) fd_rowgemm_kernel(const double*
   __shared__ double part[RG_WARPS][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x;
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   if (colmajor && Save)   // the writes below come after a barrier
     for (int m = threadIdx.x; m < M; m += blockDim.x) Save[(size_t)m * n + i] = Out[(size_t)m * n + i];
   const double* row = Mat + (size_t)i * n;
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x;
   if (i >= n) return;
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   const double mi = (CA && mu) ? mu[i] : 0.0;
   double v[8];
 #pragma unroll

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(GT_THREADS) gram_tc_kernel(const GtItem* __res
   __shared__ uint32_t tmem_slot;
   __shared__ int s_task, s_last;
   const int tid = threadIdx.x, warp = tid >> 5;
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   unsigned char* sm = gt_sm + ((1024u - (gt_smem(gt_sm) & 1023u)) & 1023u);
   if (tid == 0) {
     gt_mbar_init(&mma_bar, 1);

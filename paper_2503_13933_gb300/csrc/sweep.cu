@@ -80,14 +80,14 @@ __device__ __forceinline__ void coeff_entry(const TermTable& tt, const GramPtrs&
 }
 
 __global__ void coeff_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x, C, c);
 }
 
 // Coefficients of every dim at once (blockIdx.y = dim), into [D][TAPS_NUM_OPS][M][M]
 // and [D][Rf][M].
 __global__ void coeff_all_kernel(TermTable tt, GramPtrs gp, int M, double* Call, double* call) {
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   const int d = blockIdx.y;
   coeff_entry(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x,
               Call + (size_t)d * TAPS_NUM_OPS * M * M, call + (size_t)d * tt.Rf * M);
@@ -102,12 +102,12 @@ __device__ __forceinline__ void coeff_entry_slots(const TermTable& tt, const Gra
 }
 
 __global__ void coeff_slots_kernel(TermTable tt, GramPtrs gp, int d, int M, double* C, double* c) {
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   coeff_entry_slots(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x, C, c);
 }
 
 __global__ void coeff_all_slots_kernel(TermTable tt, GramPtrs gp, int M, double* Call, double* call) {
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   const int d = blockIdx.y;
   coeff_entry_slots(tt, gp, d, M, blockIdx.x * blockDim.x + threadIdx.x,
                     Call + (size_t)d * tt.cs * M * M, call + (size_t)d * tt.Rf * M);
@@ -122,7 +122,6 @@ __global__ void coeff_all_slots_kernel(TermTable tt, GramPtrs gp, int M, double*
 // launch does all three steps.
 // ---------------------------------------------------------------------------------
 #define GR 8
-#define GMT 8
 
 // Operand as the contraction sees it: with BF16IN rounded to bfloat16 (round to
 // nearest even) and widened to the accumulation type.
@@ -133,29 +132,29 @@ __device__ __forceinline__ T gram_in(double x) {
 }
 
 template <typename T, bool BF16IN>
-__global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M, int hb,
-                                    const double* __restrict__ opband, int nops,
-                                    const double* __restrict__ q, int Rf,
-                                    double* __restrict__ partial, int stride, unsigned* ticket,
-                                    double* gram, double* h, TermTable tt, GramPtrs gp, int cd,
-                                    double* C, double* c) {
+__device__ __forceinline__ void gram_partial_body(int chunk, int tile, int nchunk, const double* __restrict__ U,
+                                                  int nf, int M, int hb, const double* __restrict__ opband,
+                                                  int nops, const double* __restrict__ q, int Rf,
+                                                  double* __restrict__ partial, int stride, unsigned* ticket,
+                                                  double* gram, double* h, const TermTable& tt,
+                                                  const GramPtrs& gp, int cd, double* C, double* c, int gmt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int is_last;
   const int nb = 2 * hb + 1;
   const int rows_h = GR + 2 * hb;
   T* Us = reinterpret_cast<T*>(smem_raw);  // [rows_h][M]
   T* Ys = Us + rows_h * M;                 // [GR][M]
-  const int r0 = blockIdx.x * GR;
-  const int m0 = blockIdx.y * GMT;
-  const int mt = min(GMT, M - m0);
-  taps_pdl_wait_then_release();
+  const int r0 = chunk * GR;
+  const int m0 = tile * gmt;
+  const int mt = min(gmt, M - m0);
+  taps_pdl_wait();
   for (int idx = threadIdx.x; idx < rows_h * M; idx += blockDim.x) {
     int m = idx / rows_h, rr = idx % rows_h;
     int gi = r0 - hb + rr;
     Us[rr * M + m] = (gi >= 0 && gi < nf) ? gram_in<T, BF16IN>(U[(size_t)m * nf + gi]) : (T)0;
   }
   __syncthreads();
-  double* out = partial + ((size_t)blockIdx.x) * stride;
+  double* out = partial + ((size_t)chunk) * stride;
   for (int o = 0; o < nops; ++o) {
     const double* band = opband + (size_t)o * nf * nb;
     for (int idx = threadIdx.x; idx < GR * M; idx += blockDim.x) {
@@ -191,12 +190,11 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
   // CTAs of tile y.
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(ticket + blockIdx.y, 1u) == gridDim.x - 1) ? 1 : 0;
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket + tile, 1u) == (unsigned)(nchunk - 1)) ? 1 : 0;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int nchunk = gridDim.x;
-  const int ng = nops * M * M;
+    const int ng = nops * M * M;
   const int nslice = nops * mt * M + Rf * mt;   // this tile's rows of every Gamma_o, then of h
   for (int e = threadIdx.x; e < nslice; e += blockDim.x) {
     int j;
@@ -213,7 +211,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
     if (j < ng) gram[j] = acc;
     else h[j - ng] = acc;
   }
-  if (threadIdx.x == 0) ticket[blockIdx.y] = 0u;   // ready for the next launch on this stream
+  if (threadIdx.x == 0) ticket[tile] = 0u;   // ready for the next launch on this stream
   if (cd < 0) return;
   // entry (m, n) of the coefficients needs entry (m, n) of each dim's Gram only, so
   // this CTA forms the rows m of its tile
@@ -222,6 +220,51 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
   for (int e = threadIdx.x; e < mt * M; e += blockDim.x) coeff_C(tt, gp, cd, M, m0 * M + e, C);
   for (int e = threadIdx.x; e < Rf * mt; e += blockDim.x) coeff_c(tt, gp, cd, M, e / mt, m0 + e % mt, c);
 }
+
+template <typename T, bool BF16IN>
+__global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M, int hb,
+                                    const double* __restrict__ opband, int nops,
+                                    const double* __restrict__ q, int Rf,
+                                    double* __restrict__ partial, int stride, unsigned* ticket,
+                                    double* gram, double* h, TermTable tt, GramPtrs gp, int cd,
+                                    double* C, double* c, int gmt) {
+  gram_partial_body<T, BF16IN>(blockIdx.x, blockIdx.y, gridDim.x, U, nf, M, hb, opband, nops, q, Rf, partial,
+                               stride, ticket, gram, h, tt, gp, cd, C, c, gmt);
+}
+
+// The Gram refresh of every dim in one launch (the refresh that starts a solve): CTA
+// blockIdx.x is (dim d, mode tile, row chunk) with the same work, partial layout, ticket
+// protocol and fixed-order tail sum as gram_partial_kernel's CTA (chunk, tile) of dim d,
+// each dim with its own partial region and tickets.
+struct GramAll {
+  const double* U[TAPS_MAX_DIMS];
+  const double* band[TAPS_MAX_DIMS];
+  const double* q[TAPS_MAX_DIMS];
+  double* partial[TAPS_MAX_DIMS];
+  unsigned* ticket[TAPS_MAX_DIMS];
+  double* gram[TAPS_MAX_DIMS];
+  double* h[TAPS_MAX_DIMS];
+  int nf[TAPS_MAX_DIMS], hb[TAPS_MAX_DIMS], nops[TAPS_MAX_DIMS], nchunk[TAPS_MAX_DIMS];
+  int cta0[TAPS_MAX_DIMS + 1];
+  int D;
+};
+
+__global__ void gram_partial_all_kernel(GramAll ga, int M, int Rf, TermTable tt, GramPtrs gp, int gmt) {
+  int d = 0;
+  while (d + 1 < ga.D && (int)blockIdx.x >= ga.cta0[d + 1]) ++d;
+  const int loc = blockIdx.x - ga.cta0[d];
+  const int nchunk = ga.nchunk[d];
+  const int nops = ga.nops[d];
+  gram_partial_body<double, false>(loc % nchunk, loc / nchunk, nchunk, ga.U[d], ga.nf[d], M, ga.hb[d], ga.band[d],
+                                   nops, ga.q[d], Rf, ga.partial[d], nops * M * M + Rf * M, ga.ticket[d],
+                                   ga.gram[d], ga.h[d], tt, gp, -1, nullptr, nullptr, gmt);
+}
+
+// Mode tiles of gmt rows: each tile's last CTA adds its rows' chunk partials, so smaller
+// tiles spread that FP64 work over more SMs while every CTA still forms the whole banded
+// product of its chunk; 4 rows measured fastest up to 32 modes (8 beyond).  The tile
+// height changes no sum's order.  At most 32 tiles (M <= 128).
+static int gram_tile_rows(int M) { return M <= 32 ? 4 : 8; }
 
 static GramPtrs gram_ptrs(const taps_problem* P) {
   GramPtrs gp;
@@ -323,6 +366,7 @@ __global__ void gram_gemm_reduce_kernel(const double* __restrict__ partial, int 
 
 
 int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int precision, int coeff_dim) {
+  P->c0_valid = 0;   // the Grams of dim d change; the routes below re-form coeff_dim's
   if (P->tt.cs > TAPS_NUM_OPS && coeff_dim >= 0) {
     // weighted operators: the Gram refresh, then the coefficients in their own launch
     TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, -1));
@@ -331,6 +375,8 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
     TAPS_CUDA(taps_launch_pdl(coeff_slots_kernel, dim3((std::max(M * M, P->Rf * M) + 127) / 128), dim3(128), 0, P->stream, P->tt,
                               gram_ptrs(P), coeff_dim, M, P->d_C, P->d_c));
     prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D, 8.0 * ((double)P->R * M * M * P->D));
+    P->c0_valid = (coeff_dim == 0);
+    P->c0_M = M;
     return TAPS_OK;
   }
   const taps_dim* dm = P->dims[d];
@@ -338,7 +384,8 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
   if (M == 0) return TAPS_OK;
   int nchunk = (nf + GR - 1) / GR;
   int stride = nops * M * M + Rf * M;
-  dim3 grid(nchunk, (M + GMT - 1) / GMT);
+  const int gmt = gram_tile_rows(M);
+  dim3 grid(nchunk, (M + gmt - 1) / gmt);
   size_t elems = (size_t)(GR + 2 * hb) * M + (size_t)GR * M;
   const int nb = 2 * hb + 1;
   double gflops = nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
@@ -388,26 +435,72 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
     TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, false>, grid, dim3(256), elems * sizeof(float),
                               P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
                               (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
-                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
+                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt));
   } else if (precision == TAPS_BF16) {
     TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, true>, grid, dim3(256), elems * sizeof(float),
                               P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
                               (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
-                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
+                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt));
   } else {
     TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<double, false>, grid, dim3(256), elems * sizeof(double),
                               P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d],
                               nops, (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
-                              P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c));
+                              P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt));
   }
   prof_end(P, TAPS_PROF_GRAM, tk, gflops, gbytes);
   TAPS_CUDA(cudaGetLastError());
+  P->c0_valid = (coeff_dim == 0);   // the last CTA of each mode tile formed them
+  P->c0_M = M;
   return TAPS_OK;
 }
 
+// Every dim's Grams; the last refresh also forms dim 0's coefficients for the next sweep.
+// In FP64 with every dim on the chunked route (and the partial regions of all dims in
+// the workspace), one launch refreshes all dims and a second forms dim 0's coefficients.
 int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision) {
-  for (int d = 0; d < P->D; ++d) TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, -1));
-  return TAPS_OK;
+  const int M = U->M;
+  bool all = P->gram_all_ok && M >= 1 && (precision == TAPS_FP64 || precision == TAPS_MIXED) &&
+             P->tt.cs <= TAPS_NUM_OPS;
+  for (int d = 0; d < P->D && all; ++d)
+    if (M > 32 && P->dims[d]->nf >= 256) all = false;   // the banded-product + contraction route
+  if (!all) {
+    for (int d = 0; d < P->D; ++d) TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, d == P->D - 1 ? 0 : -1));
+    return TAPS_OK;
+  }
+  P->c0_valid = 0;
+  const int gmt = gram_tile_rows(M), ntile = (M + gmt - 1) / gmt, Rf = P->Rf;
+  GramAll ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.D = P->D;
+  size_t off = 0, elems = 0;
+  double gflops = 0.0, gbytes = 0.0;
+  for (int d = 0; d < P->D; ++d) {
+    const taps_dim* dm = P->dims[d];
+    const int nf = dm->nf, hb = dm->hb, nops = P->tt.nops[d], nb = 2 * hb + 1;
+    ga.U[d] = U->d_U[d];
+    ga.band[d] = P->d_opband[d];
+    ga.q[d] = P->d_q[d];
+    ga.partial[d] = P->d_partial + off;
+    ga.ticket[d] = P->d_ticket_all + (size_t)d * 32;
+    ga.gram[d] = P->d_gram[d];
+    ga.h[d] = P->d_h[d];
+    ga.nf[d] = nf;
+    ga.hb[d] = hb;
+    ga.nops[d] = nops;
+    ga.nchunk[d] = (nf + GR - 1) / GR;
+    ga.cta0[d + 1] = ga.cta0[d] + ga.nchunk[d] * ntile;
+    off += (size_t)ga.nchunk[d] * (nops * M * M + Rf * M);
+    elems = std::max(elems, (size_t)(GR + 2 * hb) * M + (size_t)GR * M);
+    gflops += nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
+    gbytes += 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf + (double)nops * M * M +
+                     (double)Rf * M);
+  }
+  int tk = prof_begin(P, TAPS_PROF_GRAM);
+  TAPS_CUDA(taps_launch_pdl(gram_partial_all_kernel, dim3(ga.cta0[P->D]), dim3(256), elems * sizeof(double),
+                            P->stream, ga, M, Rf, P->tt, gram_ptrs(P), gmt));
+  prof_end(P, TAPS_PROF_GRAM, tk, gflops, gbytes);
+  TAPS_CUDA(cudaGetLastError());
+  return coefficients(P, 0, M);
 }
 
 // Block band of the reduced matrix (node-major, I = (i, m)):
@@ -672,7 +765,7 @@ __global__ void __launch_bounds__(256) block_backsub_kernel(const double* __rest
 // ---------------------------------------------------------------------------------
 __global__ void normalize_change_kernel(double* U, const double* Uold, int nf, int M, int normalize,
                                         double* out, int* status) {
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   __shared__ double red[32];
   __shared__ double redv[32];
   __shared__ int redi[32];
@@ -725,6 +818,93 @@ __global__ void normalize_change_kernel(double* U, const double* Uold, int nf, i
   if (threadIdx.x == 0) {
     out[2 * m] = dif;
     out[2 * m + 1] = n2;
+  }
+}
+
+// The same for columns of at most NC_PER * 256 entries, with the column and its old
+// values held in registers: one load of each, the sum of squares and the signed
+// largest entry in one pass of reductions, the scaled column written once, and the
+// change sums in a second pass: two barriers instead of a dozen, no re-reads.  Each
+// sum follows the block_sum tree (per-thread order, xor butterfly in the warp, then the
+// butterfly over the warps' sums, whose lanes all hold the same value), so the results
+// equal normalize_change_kernel's bit for bit.
+#define NC_PER 4
+__global__ void __launch_bounds__(256) normalize_change_reg_kernel(double* U, const double* Uold, int nf, int M,
+                                                                   int normalize, double* out, int* status) {
+  __shared__ double rs[8], rv[8], rsv[8], rd[8], rn[8];
+  __shared__ int ri[8];
+  taps_pdl_wait();
+  const int m = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* col = U + (size_t)m * nf;
+  const double* old = Uold + (size_t)m * nf;
+  double v[NC_PER], o[NC_PER];
+#pragma unroll
+  for (int k = 0; k < NC_PER; ++k) {
+    const int i = threadIdx.x + k * 256;
+    v[k] = i < nf ? col[i] : 0.0;
+    o[k] = i < nf ? old[i] : 0.0;
+  }
+  double s2 = 0.0, best = -1.0, bv = 0.0;
+  int bi = 0x7fffffff;
+#pragma unroll
+  for (int k = 0; k < NC_PER; ++k) {
+    const int i = threadIdx.x + k * 256;
+    if (i < nf) {
+      s2 += v[k] * v[k];
+      const double a = fabs(v[k]);
+      if (a > best) { best = a; bi = i; bv = v[k]; }
+    }
+  }
+  s2 = warp_sum(s2);
+  // largest magnitude with ties to the smallest index, carrying its signed value
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o2);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o2);
+    const double ov = __shfl_xor_sync(0xffffffffu, bv, o2);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
+  }
+  if (lane == 0) { rs[w] = s2; rv[w] = best; ri[w] = bi; rsv[w] = bv; }
+  __syncthreads();
+  const int nw = 8;
+  double tot = warp_sum(lane < nw ? rs[lane] : 0.0);
+  double gb = rv[0], gv = rsv[0];
+  int gi = ri[0];
+  for (int j = 1; j < nw; ++j)
+    if (rv[j] > gb || (rv[j] == gb && ri[j] < gi)) { gb = rv[j]; gi = ri[j]; gv = rsv[j]; }
+  const double nrm = sqrt(tot);
+  if (!isfinite(nrm) && threadIdx.x == 0) taps_flag(status, TAPS_DEV_NONFINITE);
+  if (normalize && nrm > 0.0) {
+    const double den = (gv >= 0.0 ? 1.0 : -1.0) * nrm;
+#pragma unroll
+    for (int k = 0; k < NC_PER; ++k) {
+      const int i = threadIdx.x + k * 256;
+      if (i < nf) {
+        v[k] = v[k] / den;
+        col[i] = v[k];
+      }
+    }
+  }
+  double dif = 0.0, n2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < NC_PER; ++k) {
+    const int i = threadIdx.x + k * 256;
+    if (i < nf) {
+      const double dv = v[k] - o[k];
+      dif += dv * dv;
+      n2 += v[k] * v[k];
+    }
+  }
+  dif = warp_sum(dif);
+  n2 = warp_sum(n2);
+  if (lane == 0) { rd[w] = dif; rn[w] = n2; }
+  __syncthreads();
+  if (w == 0) {
+    dif = warp_sum(lane < nw ? rd[lane] : 0.0);
+    n2 = warp_sum(lane < nw ? rn[lane] : 0.0);
+    if (lane == 0) {
+      out[2 * m] = dif;
+      out[2 * m + 1] = n2;
+    }
   }
 }
 
@@ -884,6 +1064,7 @@ int taps_sweep_setup(int dev, int num_sms, int* coop_blocks) {
   TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<double, false>, maxsm));
   TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, false>, maxsm));
   TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_kernel<float, true>, maxsm));
+  TAPS_TRY(taps_allow_dyn_smem((const void*)gram_partial_all_kernel, maxsm));
   TAPS_TRY(residual_setup(maxsm));
   TAPS_TRY(taps_md_setup(maxsm));
   TAPS_TRY(taps_gram_tc_setup(maxsm));
@@ -905,8 +1086,12 @@ static int coefficients(taps_problem* P, int d, int M) {
   prof_end(P, TAPS_PROF_COEFF, tk, (double)P->R * M * M * P->D + (double)P->Rf * M * P->D,
            8.0 * ((double)P->R * M * M * P->D));
   TAPS_CUDA(cudaGetLastError());
+  P->c0_valid = (d == 0);
+  P->c0_M = M;
   return TAPS_OK;
 }
+
+int taps_coefficients(taps_problem* P, int d, int M) { return coefficients(P, d, M); }
 
 // Kernels of one sweep (no host synchronisation: capturable in a CUDA graph).  The
 // per-column change / norm partials and the status word are copied to pinned host
@@ -918,8 +1103,12 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
   cudaStream_t s = P->stream;
   for (int d = 0; d < P->D; ++d) {
     const taps_dim* dm = P->dims[d];
-    // the coefficients of the later dims come with the previous dim's Gram refresh
-    if (d == 0) TAPS_TRY(coefficients(P, 0, M));
+    // the coefficients of the later dims come with the previous dim's Gram refresh, and
+    // dim 0's with the last dim's refresh of the previous sweep (or of taps_refresh_grams)
+    if (d == 0) {
+      if (P->c0_valid && P->c0_M == M && !P->c0_forbid) P->c0_skipped = 1;
+      else TAPS_TRY(coefficients(P, 0, M));
+    }
     const int route = taps_dim_route(P, d, solver, M);
     if (route == TAPS_ROUTE_FD) {
       TAPS_TRY(taps_fd_solve(P, U, d, precision));   // keeps the old factor in d_Uold
@@ -934,18 +1123,15 @@ int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solv
     }
     int norm_d = (normalize && d < P->D - 1) ? 1 : 0;
     int tk = prof_begin(P, TAPS_PROF_NORMALIZE);
-    TAPS_CUDA(taps_launch_pdl(normalize_change_kernel, dim3(M), dim3(256), 0, s, U->d_U[d],
-                              (const double*)P->d_Uold, dm->nf, M, norm_d, P->d_scal + (size_t)d * 2 * M,
-                              P->d_status));
+    TAPS_CUDA(taps_launch_pdl(dm->nf <= NC_PER * 256 ? normalize_change_reg_kernel : normalize_change_kernel,
+                              dim3(M), dim3(256), 0, s, U->d_U[d], (const double*)P->d_Uold, dm->nf, M, norm_d,
+                              P->d_scal + (size_t)d * 2 * M, P->d_status));
     prof_end(P, TAPS_PROF_NORMALIZE, tk, 7.0 * dm->nf * M, 8.0 * 3.0 * dm->nf * M);
     TAPS_CUDA(cudaGetLastError());
-    TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, d + 1 < P->D ? d + 1 : -1));
+    TAPS_TRY(taps_refresh_gram_dim(P, U, d, precision, d + 1 < P->D ? d + 1 : 0));
   }
   if (!host_copies) return TAPS_OK;
-  TAPS_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, sizeof(double) * 2 * M * P->D,
-                            cudaMemcpyDeviceToHost, s));
-  TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  return TAPS_OK;
+  return taps_results_to_host(P, 2 * M * P->D, 0);
 }
 
 // Reads the device status and the change partials copied by taps_sweep_enqueue (the
@@ -1032,7 +1218,7 @@ __global__ void __launch_bounds__(256) als_residual_all_kernel(ResDims rd, int M
   extern __shared__ __align__(16) double rsm[];
   __shared__ double red[32];
   const int b = blockIdx.x;
-  taps_pdl_wait_then_release();
+  taps_pdl_wait();
   int d = 0;
   while (d + 1 < rd.D && b >= rd.cta0[d + 1]) ++d;
   const int r0 = (b - rd.cta0[d]) * RR;
@@ -1106,32 +1292,83 @@ __device__ __forceinline__ double big_gram_col(const double* Y, const double* q,
   return (a < nops * M) ? Y[((size_t)(a / M) * nf + i) * M + (a % M)] : q[(size_t)(a - nops * M) * nf + i];
 }
 
-__global__ void __launch_bounds__(BG_COLS * BG_SPLIT) big_gram_kernel(const double* __restrict__ Y, int nops,
-                                                                       int nf, int M,
-                                                                       const double* __restrict__ q, int Rf,
-                                                                       double* __restrict__ G) {
+struct BigGramPtrs {
+  const double* G[TAPS_MAX_DIMS];
+  int NC[TAPS_MAX_DIMS];
+};
+
+// Every dim of the full residual in one launch each: the banded products Y_o = Op_o U
+// of all dims (thread per output, as spmm_kernel) and the big Grams of all dims (CTA per
+// row a of dim d's Gram of the columns [Y_0 .. Y_{nops-1} | Q]: BG_SPLIT row ranges, each
+// a sequential sum taking its operands eight rows at a time so that their loads are in
+// flight together, then the ranges' sums added pairwise).
+struct ResAll {
+  const double* U[TAPS_MAX_DIMS];
+  const double* band[TAPS_MAX_DIMS];
+  const double* q[TAPS_MAX_DIMS];
+  double* G[TAPS_MAX_DIMS];
+  long long yoff[TAPS_MAX_DIMS + 1];   // prefix of nops_d nf_d M (outputs of the banded products)
+  int aoff[TAPS_MAX_DIMS + 1];         // prefix of NC_d (rows of the big Grams)
+  int nf[TAPS_MAX_DIMS], hb[TAPS_MAX_DIMS], nops[TAPS_MAX_DIMS];
+  int D;
+};
+
+__global__ void spmm_all_kernel(ResAll ra, int M, double* __restrict__ Yall) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ra.yoff[ra.D]) return;
+  int d = 0;
+  while (d + 1 < ra.D && idx >= ra.yoff[d + 1]) ++d;
+  const long long loc = idx - ra.yoff[d];
+  const int nf = ra.nf[d], hb = ra.hb[d], nb = 2 * hb + 1;
+  const int m = loc % M;
+  const int i = (loc / M) % nf;
+  const int o = loc / ((long long)M * nf);
+  const double* brow = ra.band[d] + ((size_t)o * nf + i) * nb;
+  const double* U = ra.U[d];
+  double acc = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    int j = i + k - hb;
+    if (j >= 0 && j < nf) acc += brow[k] * U[(size_t)m * nf + j];
+  }
+  Yall[idx] = acc;
+}
+
+__global__ void __launch_bounds__(BG_COLS * BG_SPLIT) big_gram_all_kernel(ResAll ra, int M, int Rf,
+                                                                           const double* __restrict__ Yall) {
   __shared__ double part[BG_SPLIT][BG_COLS];
+  int d = 0;
+  while (d + 1 < ra.D && (int)blockIdx.x >= ra.aoff[d + 1]) ++d;
+  const int nops = ra.nops[d], nf = ra.nf[d];
   const int NC = nops * M + Rf;
-  const int a = blockIdx.x;
+  const int a = blockIdx.x - ra.aoff[d];
+  const double* Y = Yall + ra.yoff[d];
+  const double* q = ra.q[d];
   const int col = threadIdx.x % BG_COLS, sp = threadIdx.x / BG_COLS;
   const int i0 = (int)((long long)nf * sp / BG_SPLIT), i1 = (int)((long long)nf * (sp + 1) / BG_SPLIT);
   for (int b0 = 0; b0 < NC; b0 += BG_COLS) {
     const int b = b0 + col;
     double acc = 0.0;
-    if (b < NC)
-      for (int i = i0; i < i1; ++i)
-        acc += big_gram_col(Y, q, nops, nf, M, a, i) * big_gram_col(Y, q, nops, nf, M, b, i);
+    if (b < NC) {
+      int i = i0;
+      for (; i + 8 <= i1; i += 8) {
+        double x[8], y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          x[k] = big_gram_col(Y, q, nops, nf, M, a, i + k);
+          y[k] = big_gram_col(Y, q, nops, nf, M, b, i + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc += x[k] * y[k];
+      }
+      for (; i < i1; ++i) acc += big_gram_col(Y, q, nops, nf, M, a, i) * big_gram_col(Y, q, nops, nf, M, b, i);
+    }
     part[sp][col] = acc;
     __syncthreads();
-    if (sp == 0 && b < NC) G[(size_t)a * NC + b] = (part[0][col] + part[1][col]) + (part[2][col] + part[3][col]);
+    if (sp == 0 && b < NC)
+      ra.G[d][(size_t)a * NC + b] = (part[0][col] + part[1][col]) + (part[2][col] + part[3][col]);
     __syncthreads();
   }
 }
-
-struct BigGramPtrs {
-  const double* G[TAPS_MAX_DIMS];
-  int NC[TAPS_MAX_DIMS];
-};
 
 // Gram-identity combination: partial sums of ||F||^2, F^T A u and ||A u||^2.
 __global__ void full_residual_combine_kernel(TermTable tt, BigGramPtrs bg, int M, double* partial) {
@@ -1228,41 +1465,84 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
                               (const double*)P->d_Call, (const double*)P->d_call, P->d_partial));
     prof_end(P, TAPS_PROF_RESIDUAL, tk, fl, by);
     TAPS_CUDA(cudaGetLastError());
-    size_t off = 2 * (size_t)rd.cta0[P->D];
     if (!host_copies) return TAPS_OK;
-    TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, off * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    return TAPS_OK;
+    return taps_results_to_host(P, 0, taps_residual_npart(P, TAPS_RES_ALS));
   }
   if (kind != TAPS_RES_FULL) return TAPS_ERR_INVALID_ARG;
   BigGramPtrs bg;
   memset(&bg, 0, sizeof(bg));
+  ResAll ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.D = P->D;
   size_t goff = 0;
+  double fl = 0.0, by = 0.0;
   for (int d = 0; d < P->D; ++d) {
     const taps_dim* dm = P->dims[d];
     int nops = P->tt.nops[d];
     int NC = nops * M + P->Rf;
     long long ny = (long long)nops * dm->nf * M;
-    int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
-    spmm_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(U->d_U[d], dm->nf, M, dm->hb,
-                                                             P->d_opband[d], nops, P->d_Y);
-    TAPS_CUDA(cudaGetLastError());
-    P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
-    prof_end(P, TAPS_PROF_RESIDUAL, tk, 2.0 * ny * dm->nb + 2.0 * (double)NC * NC * dm->nf, 8.0 * 2.0 * ny);
-    big_gram_kernel<<<NC, BG_COLS * BG_SPLIT, 0, s>>>(P->d_Y, nops, dm->nf, M, P->d_q[d], P->Rf,
-                                                      P->d_bigG + goff);
-    TAPS_CUDA(cudaGetLastError());
+    ra.U[d] = U->d_U[d];
+    ra.band[d] = P->d_opband[d];
+    ra.q[d] = P->d_q[d];
+    ra.G[d] = P->d_bigG + goff;
+    ra.nf[d] = dm->nf;
+    ra.hb[d] = dm->hb;
+    ra.nops[d] = nops;
+    ra.yoff[d + 1] = ra.yoff[d] + ny;
+    ra.aoff[d + 1] = ra.aoff[d] + NC;
+    fl += 2.0 * ny * dm->nb + 2.0 * (double)NC * NC * dm->nf;
+    by += 8.0 * 2.0 * ny;
     bg.G[d] = P->d_bigG + goff;
     bg.NC[d] = NC;
     goff += (size_t)NC * NC;
+  }
+  {
+    int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
+    const long long ny = ra.yoff[P->D];
+    spmm_all_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(ra, M, P->d_Yres);
+    TAPS_CUDA(cudaGetLastError());
+    big_gram_all_kernel<<<ra.aoff[P->D], BG_COLS * BG_SPLIT, 0, s>>>(ra, M, P->Rf, (const double*)P->d_Yres);
+    TAPS_CUDA(cudaGetLastError());
+    P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
+    prof_end(P, TAPS_PROF_RESIDUAL, tk, fl, by);
   }
   const int nblk = 64;
   int tk = prof_begin(P, TAPS_PROF_RESIDUAL);
   full_residual_combine_kernel<<<nblk, 256, 0, s>>>(P->tt, bg, M, P->d_partial);
   prof_end(P, TAPS_PROF_RESIDUAL, tk, (double)P->R * M * P->R * M * (P->D + 1), 8.0 * (double)goff);
   TAPS_CUDA(cudaGetLastError());
-  TAPS_CUDA(cudaMemcpyAsync(P->h_part, P->d_partial, 3 * nblk * sizeof(double), cudaMemcpyDeviceToHost, s));
-  TAPS_CUDA(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (!host_copies) return TAPS_OK;
+  return taps_results_to_host(P, 0, taps_residual_npart(P, TAPS_RES_FULL));
+}
+
+// The change partials of a sweep (nscal), the partial sums of a residual (npart) and the
+// status word into the pinned host buffers (device-accessible under unified addressing)
+// by one kernel: it replaces device-to-host copies of a few hundred bytes each, whose
+// latency (several microseconds per copy) sat on the critical path of every sweep.
+__global__ void host_results_kernel(const double* __restrict__ scal, int nscal, const double* __restrict__ part,
+                                    int npart, const int* __restrict__ status, double* h_scal, double* h_part,
+                                    int* h_status) {
+  taps_pdl_wait();
+  for (int i = threadIdx.x; i < nscal; i += blockDim.x) h_scal[i] = scal[i];
+  for (int i = threadIdx.x; i < npart; i += blockDim.x) h_part[i] = part[i];
+  if (threadIdx.x == 0) *h_status = *status;
+  __threadfence_system();
+}
+
+int taps_residual_npart(const taps_problem* P, int kind) {
+  if (kind != TAPS_RES_ALS) return 3 * 64;
+  int cta0[TAPS_MAX_DIMS + 1];
+  taps_als_partial_ranges(P, cta0);
+  return 2 * cta0[P->D];
+}
+
+int taps_results_to_host(taps_problem* P, int nscal, int npart) {
+  int tk = prof_begin(P, TAPS_PROF_OTHER);
+  TAPS_CUDA(taps_launch_pdl(host_results_kernel, dim3(1), dim3(256), 0, P->stream, (const double*)P->d_scal,
+                            nscal, (const double*)P->d_partial, npart, (const int*)P->d_status, P->h_scal,
+                            P->h_part, P->h_status));
+  prof_end(P, TAPS_PROF_OTHER, tk, 0.0, 8.0 * ((double)nscal + npart));
+  TAPS_CUDA(cudaGetLastError());
   return TAPS_OK;
 }
 

@@ -151,6 +151,9 @@ struct taps_problem {
   double* d_scal;     // small scalar scratch
   double* d_bigG;     // [D][NC][NC] residual Grams
   size_t bigG_len;
+  double* d_Yres;     // [sum_d nops_d nf_d M] banded products of every dim (full residual)
+  unsigned* d_ticket_all;   // [D][32] tickets of the all-dims Gram refresh
+  int gram_all_ok;    // d_partial holds the chunk partials of every dim at once
   int* d_status;
   unsigned* d_bar;    // grid barrier words (count, generation)
   double* h_scal;     // pinned host mirror of d_scal
@@ -166,6 +169,12 @@ struct taps_problem {
   int lu_tuned[16][3];  // tuned block-elimination CTA counts: (n, M, CTAs)
   int n_lu_tuned;
   int coop_blocks;    // CTAs of the cooperative block solve
+  // d_C / d_c hold dim 0's coefficients for the current Grams (the last dim's Gram
+  // refresh of a sweep or of taps_refresh_grams forms them), so the next sweep need not
+  int c0_valid;
+  int c0_M;           // the mode count they were formed for (the layout of d_C)
+  int c0_forbid;      // set around captures whose replays cannot rely on c0_valid
+  int c0_skipped;     // a sweep enqueue reused them (read after a capture)
   int num_sms;
   ProfState* prof;
 };
@@ -198,11 +207,15 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Programmatic dependent launch.  A kernel launched by taps_launch_pdl may be
 // scheduled while its predecessor on the stream is still running; it calls
 // taps_pdl_wait() before its first global-memory access (the wait returns once the
-// predecessor has completed and its writes are visible) and then lets its own
-// successor be scheduled.  Launched without the attribute, the wait returns at once.
-__device__ __forceinline__ void taps_pdl_wait_then_release() {
+// predecessor has completed and its writes are visible).  Launched without the
+// attribute, the wait returns at once.  The kernels do not trigger their successor
+// early (griddepcontrol.launch_dependents at their start): a successor released that
+// way keeps all its CTAs resident and waiting beside the running kernel, which on this
+// GPU stretched the node-side small solves from ~19 to ~60 us per launch on some dims
+// (globaltimer traces of the whole sweep); released at exit, the successor's launch
+// still overlaps the predecessor's tail.
+__device__ __forceinline__ void taps_pdl_wait() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 template <typename... KArgs, typename... Args>
@@ -308,6 +321,8 @@ __host__ __device__ __forceinline__ double taps_uniform_pm1(unsigned seed, int d
 // ---------------------------------------------------------------------------------
 int taps_ws_ensure(taps_problem* P, int M);
 int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision);
+// Coefficients of dim d from the current Grams into P->d_C / P->d_c.
+int taps_coefficients(taps_problem* P, int d, int M);
 // Largest dynamic shared memory a launch of `fn` may ask for (opt-in limit less the
 // kernel's static shared memory).
 int taps_allow_dyn_smem(const void* fn, int maxsm);
@@ -339,6 +354,12 @@ int taps_residual_impl(taps_problem* P, const taps_factors* U, int kind, double*
 int taps_sweep_enqueue(taps_problem* P, taps_factors* U, int precision, int solver, int normalize,
                        int host_copies = 1);
 int taps_sweep_finish(taps_problem* P, taps_factors* U, double* change_out);
+// After a sweep and/or a residual enqueued without host copies: nscal change partials,
+// npart residual partials and the status word into the pinned host buffers that the
+// finish functions read.
+int taps_results_to_host(taps_problem* P, int nscal, int npart);
+// Number of partial sums a residual of this kind leaves in P->d_partial.
+int taps_residual_npart(const taps_problem* P, int kind);
 // grams_current: the FP64 Grams and source projections of every dim already belong to
 // U (true right after an FP64 or MIXED sweep), so the ALS residual does not refresh them.
 int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int grams_current = 0,
