@@ -16,8 +16,12 @@
 // Coefficients of dim d: C_o = sum_{t: op(t,d) = o} alpha_t prod_{e != d} Gamma_{op(t,e),e}
 // and c_r = beta_r prod_{e != d} h_{r,e} (Eq. 35), entry idx of the M x M matrices.
 // ---------------------------------------------------------------------------------
-// The loads of one product are issued together (unrolled over TAPS_MAX_DIMS with a
-// factor 1 for the skipped dims, an exact no-op) so that their latencies overlap.
+// The loads of one product are issued together (unrolled over TAPS_MAX_DIMS, predicated
+// off for the skipped dims) so that their latencies overlap; the product then multiplies
+// only the D - 1 real factors in increasing dim order (each FP64 instruction holds the
+// pipe ~64 cycles on this GPU, so the exact multiplications by 1 of unused dim slots
+// and an add per possible operator slot were most of the work).  Each operator slot's
+// sum takes its terms in increasing order.
 // More distinct operators than TAPS_NUM_OPS (weighted operators): one slot at a time,
 // the terms in the same order, so each slot's sum is the one the register version forms.
 __device__ __forceinline__ void coeff_C_slots(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
@@ -39,26 +43,22 @@ __device__ __forceinline__ void coeff_C_slots(const TermTable& tt, const GramPtr
 __device__ __forceinline__ void coeff_C(const TermTable& tt, const GramPtrs& gp, int d, int M, int idx,
                                         double* C) {
   const int MM = M * M;
-  double acc[TAPS_NUM_OPS];
+  for (int o = 0; o < tt.nops[d]; ++o) {
+    double acc = 0.0;
+    for (int t = 0; t < tt.R; ++t) {
+      if (tt.oi[t][d] != o) continue;
+      double f[TAPS_MAX_DIMS];
 #pragma unroll
-  for (int o = 0; o < TAPS_NUM_OPS; ++o) acc[o] = 0.0;
-#pragma unroll 4
-  for (int t = 0; t < tt.R; ++t) {
-    double f[TAPS_MAX_DIMS];
+      for (int e = 0; e < TAPS_MAX_DIMS; ++e)
+        f[e] = (e < tt.D && e != d) ? __ldcg(gp.gram[e] + (size_t)tt.oi[t][e] * MM + idx) : 1.0;
+      double prod = tt.alpha[t];
 #pragma unroll
-    for (int e = 0; e < TAPS_MAX_DIMS; ++e)
-      f[e] = (e < tt.D && e != d) ? __ldcg(gp.gram[e] + (size_t)tt.oi[t][e] * MM + idx) : 1.0;
-    double prod = tt.alpha[t];
-#pragma unroll
-    for (int e = 0; e < TAPS_MAX_DIMS; ++e) prod *= f[e];
-    const int od = tt.oi[t][d];
-#pragma unroll
-    for (int o = 0; o < TAPS_NUM_OPS; ++o)
-      if (o == od) acc[o] += prod;
+      for (int e = 0; e < TAPS_MAX_DIMS; ++e)
+        if (e < tt.D && e != d) prod *= f[e];
+      acc += prod;
+    }
+    C[(size_t)o * MM + idx] = acc;
   }
-#pragma unroll
-  for (int o = 0; o < TAPS_NUM_OPS; ++o)
-    if (o < tt.nops[d]) C[(size_t)o * MM + idx] = acc[o];
 }
 
 __device__ __forceinline__ void coeff_c(const TermTable& tt, const GramPtrs& gp, int d, int M, int r, int m,
@@ -69,7 +69,8 @@ __device__ __forceinline__ void coeff_c(const TermTable& tt, const GramPtrs& gp,
     f[e] = (e < tt.D && e != d) ? __ldcg(gp.h[e] + (size_t)r * M + m) : 1.0;
   double v = tt.beta[r];
 #pragma unroll
-  for (int e = 0; e < TAPS_MAX_DIMS; ++e) v *= f[e];
+  for (int e = 0; e < TAPS_MAX_DIMS; ++e)
+    if (e < tt.D && e != d) v *= f[e];
   c[(size_t)r * M + m] = v;
 }
 
@@ -137,33 +138,46 @@ __device__ __forceinline__ void gram_partial_body(int chunk, int tile, int nchun
                                                   int nops, const double* __restrict__ q, int Rf,
                                                   double* __restrict__ partial, int stride, unsigned* ticket,
                                                   double* gram, double* h, const TermTable& tt,
-                                                  const GramPtrs& gp, int cd, double* C, double* c, int gmt) {
+                                                  const GramPtrs& gp, int cd, double* C, double* c, int gmt,
+                                                  int tail) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int is_last;
   const int nb = 2 * hb + 1;
   const int rows_h = GR + 2 * hb;
   T* Us = reinterpret_cast<T*>(smem_raw);  // [rows_h][M]
   T* Ys = Us + rows_h * M;                 // [GR][M]
+  T* Bs = Ys + GR * M;                     // [nops][GR][nb] the chunk's band rows
+  T* Qs = Bs + nops * GR * nb;             // [Rf][GR] the chunk's source rows
   const int r0 = chunk * GR;
   const int m0 = tile * gmt;
   const int mt = min(gmt, M - m0);
   taps_pdl_wait();
+  // the factor rows, band rows and source rows of the chunk in one load phase, so that
+  // the products below read shared memory only
   for (int idx = threadIdx.x; idx < rows_h * M; idx += blockDim.x) {
     int m = idx / rows_h, rr = idx % rows_h;
     int gi = r0 - hb + rr;
     Us[rr * M + m] = (gi >= 0 && gi < nf) ? gram_in<T, BF16IN>(U[(size_t)m * nf + gi]) : (T)0;
   }
+  for (int idx = threadIdx.x; idx < nops * GR * nb; idx += blockDim.x) {
+    const int o = idx / (GR * nb), rem = idx % (GR * nb);
+    const int gi = r0 + rem / nb;
+    Bs[idx] = gi < nf ? gram_in<T, BF16IN>(opband[((size_t)o * nf + gi) * nb + rem % nb]) : (T)0;
+  }
+  for (int idx = threadIdx.x; idx < Rf * GR; idx += blockDim.x) {
+    const int r = idx / GR, gi = r0 + idx % GR;
+    Qs[idx] = gi < nf ? gram_in<T, BF16IN>(q[(size_t)r * nf + gi]) : (T)0;
+  }
   __syncthreads();
   double* out = partial + ((size_t)chunk) * stride;
   for (int o = 0; o < nops; ++o) {
-    const double* band = opband + (size_t)o * nf * nb;
     for (int idx = threadIdx.x; idx < GR * M; idx += blockDim.x) {
       int i = idx / M, n = idx % M;
       int gi = r0 + i;
       T acc = 0;
       if (gi < nf) {
-        const double* brow = band + (size_t)gi * nb;
-        for (int k = 0; k < nb; ++k) acc += gram_in<T, BF16IN>(brow[k]) * Us[(i + k) * M + n];
+        const T* brow = Bs + (o * GR + i) * nb;
+        for (int k = 0; k < nb; ++k) acc += brow[k] * Us[(i + k) * M + n];
       }
       Ys[i * M + n] = acc;
     }
@@ -181,10 +195,11 @@ __device__ __forceinline__ void gram_partial_body(int chunk, int tile, int nchun
     T acc = 0;
     for (int i = 0; i < GR; ++i) {
       int gi = r0 + i;
-      if (gi < nf) acc += gram_in<T, BF16IN>(q[(size_t)r * nf + gi]) * Us[(i + hb) * M + m];
+      if (gi < nf) acc += Qs[r * GR + i] * Us[(i + hb) * M + m];
     }
     out[(size_t)nops * M * M + (size_t)r * M + m] = (double)acc;
   }
+  if (!tail) return;   // gram_reduce_coeff_kernel adds the partials
   // ---- per mode tile, the last chunk CTA reduces the tile's slice of the partials
   // and forms the tile's rows of the coefficients of dim cd.  Ticket y counts the
   // CTAs of tile y.
@@ -205,20 +220,30 @@ __device__ __forceinline__ void gram_partial_body(int chunk, int tile, int nchun
       const int rem = e - nops * mt * M;
       j = ng + (rem / mt) * M + m0 + rem % mt;
     }
+    // chunk partials 32 at a time: the loads of a batch in flight together, then the
+    // sum in chunk order
     double acc = 0.0;
-#pragma unroll 16
-    for (int ch = 0; ch < nchunk; ++ch) acc += __ldcg(partial + (size_t)ch * stride + j);
+    for (int c0 = 0; c0 < nchunk; c0 += 32) {
+      double v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = (c0 + k < nchunk) ? __ldcg(partial + (size_t)(c0 + k) * stride + j) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (c0 + k < nchunk) acc += v[k];
+    }
     if (j < ng) gram[j] = acc;
     else h[j - ng] = acc;
   }
   if (threadIdx.x == 0) ticket[tile] = 0u;   // ready for the next launch on this stream
   if (cd < 0) return;
   // entry (m, n) of the coefficients needs entry (m, n) of each dim's Gram only, so
-  // this CTA forms the rows m of its tile
-  __threadfence();
+  // this CTA forms the rows m of its tile (the Gram rows it just wrote are visible to
+  // its threads after the barrier); the matrix and source entries in one pass
   __syncthreads();
-  for (int e = threadIdx.x; e < mt * M; e += blockDim.x) coeff_C(tt, gp, cd, M, m0 * M + e, C);
-  for (int e = threadIdx.x; e < Rf * mt; e += blockDim.x) coeff_c(tt, gp, cd, M, e / mt, m0 + e % mt, c);
+  for (int e = threadIdx.x; e < mt * M + Rf * mt; e += blockDim.x) {
+    if (e < mt * M) coeff_C(tt, gp, cd, M, m0 * M + e, C);
+    else coeff_c(tt, gp, cd, M, (e - mt * M) / mt, m0 + (e - mt * M) % mt, c);
+  }
 }
 
 template <typename T, bool BF16IN>
@@ -227,9 +252,49 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
                                     const double* __restrict__ q, int Rf,
                                     double* __restrict__ partial, int stride, unsigned* ticket,
                                     double* gram, double* h, TermTable tt, GramPtrs gp, int cd,
-                                    double* C, double* c, int gmt) {
+                                    double* C, double* c, int gmt, int tail) {
   gram_partial_body<T, BF16IN>(blockIdx.x, blockIdx.y, gridDim.x, U, nf, M, hb, opband, nops, q, Rf, partial,
-                               stride, ticket, gram, h, tt, gp, cd, C, c, gmt);
+                               stride, ticket, gram, h, tt, gp, cd, C, c, gmt, tail);
+}
+
+// The chunk partials of a dim's Grams added in chunk order and the next dim's
+// coefficients, spread over many small CTAs: CTA b < ceil(M^2 / 32) takes the 32 entries
+// (m, n) = 32b .. 32b+31, warp o adds entry (o, m, n) of Gamma_o over the chunks (32
+// partials in flight at a time), and after the block barrier warp 0 forms C(m, n) of dim
+// cd from them; the CTAs after those add the source projections h_r[m] and form c.  The
+// same sums and coefficient functions as the last-CTA tail of gram_partial_kernel, whose
+// FP64 work ran on one SM per mode tile.
+__global__ void gram_reduce_coeff_kernel(const double* __restrict__ partial, int stride, int nchunk, int M,
+                                         int nops, int Rf, double* gram, double* h, TermTable tt, GramPtrs gp,
+                                         int cd, double* C, double* c) {
+  taps_pdl_wait();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int MM = M * M, ng = nops * MM;
+  const int nCg = (MM + 31) / 32;
+  auto chunk_sum = [&](int j) {
+    double acc = 0.0;
+    for (int c0 = 0; c0 < nchunk; c0 += 32) {
+      double v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = (c0 + k < nchunk) ? __ldcg(partial + (size_t)(c0 + k) * stride + j) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (c0 + k < nchunk) acc += v[k];
+    }
+    return acc;
+  };
+  if ((int)blockIdx.x < nCg) {
+    const int idx = blockIdx.x * 32 + lane;
+    if (idx < MM && w < nops) gram[w * MM + idx] = chunk_sum(w * MM + idx);
+    __syncthreads();
+    if (cd >= 0 && w == 0 && idx < MM) coeff_C(tt, gp, cd, M, idx, C);
+  } else {
+    const int e = (blockIdx.x - nCg) * 32 + lane;
+    if (w == 0 && e < Rf * M) {
+      h[e] = chunk_sum(ng + e);
+      if (cd >= 0) coeff_c(tt, gp, cd, M, e / M, e % M, c);
+    }
+  }
 }
 
 // The Gram refresh of every dim in one launch (the refresh that starts a solve): CTA
@@ -257,7 +322,7 @@ __global__ void gram_partial_all_kernel(GramAll ga, int M, int Rf, TermTable tt,
   const int nops = ga.nops[d];
   gram_partial_body<double, false>(loc % nchunk, loc / nchunk, nchunk, ga.U[d], ga.nf[d], M, ga.hb[d], ga.band[d],
                                    nops, ga.q[d], Rf, ga.partial[d], nops * M * M + Rf * M, ga.ticket[d],
-                                   ga.gram[d], ga.h[d], tt, gp, -1, nullptr, nullptr, gmt);
+                                   ga.gram[d], ga.h[d], tt, gp, -1, nullptr, nullptr, gmt, 1);
 }
 
 // Mode tiles of gmt rows: each tile's last CTA adds its rows' chunk partials, so smaller
@@ -386,7 +451,7 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
   int stride = nops * M * M + Rf * M;
   const int gmt = gram_tile_rows(M);
   dim3 grid(nchunk, (M + gmt - 1) / gmt);
-  size_t elems = (size_t)(GR + 2 * hb) * M + (size_t)GR * M;
+  size_t elems = (size_t)(GR + 2 * hb) * M + (size_t)GR * M + (size_t)nops * GR * (2 * hb + 1) + (size_t)Rf * GR;
   const int nb = 2 * hb + 1;
   double gflops = nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
   double gbytes = 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf +
@@ -435,17 +500,26 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
     TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, false>, grid, dim3(256), elems * sizeof(float),
                               P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
                               (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
-                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt));
+                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt, 1));
   } else if (precision == TAPS_BF16) {
     TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<float, true>, grid, dim3(256), elems * sizeof(float),
                               P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d], nops,
                               (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket, P->d_gram[d],
-                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt));
+                              P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt, 1));
   } else {
-    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<double, false>, grid, dim3(256), elems * sizeof(double),
-                              P->stream, (const double*)U->d_U[d], nf, M, hb, (const double*)P->d_opband[d],
-                              nops, (const double*)P->d_q[d], Rf, P->d_partial, stride, P->d_ticket,
-                              P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt));
+    // FP64: the chunk partials (8-mode tiles: without the tail, fewer tiles recompute
+    // the banded products fewer times), then the chunk sums and coefficients spread over
+    // many CTAs
+    const int gmt8 = 8;
+    TAPS_CUDA(taps_launch_pdl(gram_partial_kernel<double, false>, dim3(nchunk, (M + gmt8 - 1) / gmt8), dim3(256),
+                              elems * sizeof(double), P->stream, (const double*)U->d_U[d], nf, M, hb,
+                              (const double*)P->d_opband[d], nops, (const double*)P->d_q[d], Rf, P->d_partial, stride,
+                              P->d_ticket, P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt8, 0));
+    const int nCg = (M * M + 31) / 32, nCh = (Rf * M + 31) / 32;
+    TAPS_CUDA(taps_launch_pdl(gram_reduce_coeff_kernel, dim3(nCg + nCh), dim3(32 * nops), 0, P->stream,
+                              (const double*)P->d_partial, stride, nchunk, M, nops, Rf, P->d_gram[d], P->d_h[d],
+                              P->tt, gp, coeff_dim, P->d_C, P->d_c));
+    P->prof->launches[TAPS_PROF_GRAM] += 1;
   }
   prof_end(P, TAPS_PROF_GRAM, tk, gflops, gbytes);
   TAPS_CUDA(cudaGetLastError());
@@ -490,7 +564,7 @@ int taps_refresh_grams(taps_problem* P, const taps_factors* U, int precision) {
     ga.nchunk[d] = (nf + GR - 1) / GR;
     ga.cta0[d + 1] = ga.cta0[d] + ga.nchunk[d] * ntile;
     off += (size_t)ga.nchunk[d] * (nops * M * M + Rf * M);
-    elems = std::max(elems, (size_t)(GR + 2 * hb) * M + (size_t)GR * M);
+    elems = std::max(elems, (size_t)(GR + 2 * hb) * M + (size_t)GR * M + (size_t)nops * GR * nb + (size_t)Rf * GR);
     gflops += nops * (2.0 * nb * nf * M + 2.0 * nf * (double)M * M) + 2.0 * Rf * nf * M;
     gbytes += 8.0 * ((double)nf * M + (double)nops * nf * nb + (double)Rf * nf + (double)nops * M * M +
                      (double)Rf * M);
@@ -824,15 +898,19 @@ __global__ void normalize_change_kernel(double* U, const double* Uold, int nf, i
 // The same for columns of at most NC_PER * 256 entries, with the column and its old
 // values held in registers: one load of each, the sum of squares and the signed
 // largest entry in one pass of reductions, the scaled column written once, and the
-// change sums in a second pass: two barriers instead of a dozen, no re-reads.  Each
-// sum follows the block_sum tree (per-thread order, xor butterfly in the warp, then the
-// butterfly over the warps' sums, whose lanes all hold the same value), so the results
-// equal normalize_change_kernel's bit for bit.
+// change sums in a second pass.  Each sum follows the block_sum tree (per-thread order,
+// xor butterfly in the warp, then the butterfly over the warps' sums in warp 0), so the
+// results equal normalize_change_kernel's bit for bit.  The largest magnitude is found
+// on the bit patterns of |v| (non-negative doubles order like their bits), the block
+// totals and the square root in warp 0 only: every warp-wide FP64 instruction holds the
+// pipe of its SM sub-partition for ~64 cycles on this GPU.
 #define NC_PER 4
 __global__ void __launch_bounds__(256) normalize_change_reg_kernel(double* U, const double* Uold, int nf, int M,
                                                                    int normalize, double* out, int* status) {
-  __shared__ double rs[8], rv[8], rsv[8], rd[8], rn[8];
+  __shared__ double rs[8], rsv[8], rd[8], rn[8];
+  __shared__ long long rk[8];
   __shared__ int ri[8];
+  __shared__ double den_s;
   taps_pdl_wait();
   const int m = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double* col = U + (size_t)m * nf;
@@ -844,37 +922,45 @@ __global__ void __launch_bounds__(256) normalize_change_reg_kernel(double* U, co
     v[k] = i < nf ? col[i] : 0.0;
     o[k] = i < nf ? old[i] : 0.0;
   }
-  double s2 = 0.0, best = -1.0, bv = 0.0;
+  double s2 = 0.0, bv = 0.0;
+  long long best = -1;   // bits of |v|; -1 below every entry
   int bi = 0x7fffffff;
 #pragma unroll
   for (int k = 0; k < NC_PER; ++k) {
     const int i = threadIdx.x + k * 256;
     if (i < nf) {
       s2 += v[k] * v[k];
-      const double a = fabs(v[k]);
+      const long long a = __double_as_longlong(fabs(v[k]));
       if (a > best) { best = a; bi = i; bv = v[k]; }
     }
   }
   s2 = warp_sum(s2);
   // largest magnitude with ties to the smallest index, carrying its signed value
   for (int o2 = 16; o2 > 0; o2 >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o2);
+    const long long ob = __shfl_xor_sync(0xffffffffu, best, o2);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o2);
     const double ov = __shfl_xor_sync(0xffffffffu, bv, o2);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
   }
-  if (lane == 0) { rs[w] = s2; rv[w] = best; ri[w] = bi; rsv[w] = bv; }
+  if (lane == 0) { rs[w] = s2; rk[w] = best; ri[w] = bi; rsv[w] = bv; }
   __syncthreads();
   const int nw = 8;
-  double tot = warp_sum(lane < nw ? rs[lane] : 0.0);
-  double gb = rv[0], gv = rsv[0];
-  int gi = ri[0];
-  for (int j = 1; j < nw; ++j)
-    if (rv[j] > gb || (rv[j] == gb && ri[j] < gi)) { gb = rv[j]; gi = ri[j]; gv = rsv[j]; }
-  const double nrm = sqrt(tot);
-  if (!isfinite(nrm) && threadIdx.x == 0) taps_flag(status, TAPS_DEV_NONFINITE);
-  if (normalize && nrm > 0.0) {
-    const double den = (gv >= 0.0 ? 1.0 : -1.0) * nrm;
+  if (w == 0) {
+    const double tot = warp_sum(lane < nw ? rs[lane] : 0.0);
+    if (lane == 0) {
+      long long gb = rk[0];
+      int gi = ri[0];
+      double gv = rsv[0];
+      for (int j = 1; j < nw; ++j)
+        if (rk[j] > gb || (rk[j] == gb && ri[j] < gi)) { gb = rk[j]; gi = ri[j]; gv = rsv[j]; }
+      const double nrm = sqrt(tot);
+      if (!isfinite(nrm)) taps_flag(status, TAPS_DEV_NONFINITE);
+      den_s = (normalize && nrm > 0.0) ? (gv >= 0.0 ? 1.0 : -1.0) * nrm : 0.0;
+    }
+  }
+  __syncthreads();
+  const double den = den_s;
+  if (den != 0.0) {
 #pragma unroll
     for (int k = 0; k < NC_PER; ++k) {
       const int i = threadIdx.x + k * 256;
