@@ -259,8 +259,9 @@ __global__ void gram_partial_kernel(const double* __restrict__ U, int nf, int M,
 
 // The chunk partials of a dim's Grams added in chunk order and the next dim's
 // coefficients, spread over many small CTAs: CTA b < ceil(M^2 / 32) takes the 32 entries
-// (m, n) = 32b .. 32b+31, warp o adds entry (o, m, n) of Gamma_o over the chunks (32
-// partials in flight at a time), and after the block barrier warp 0 forms C(m, n) of dim
+// (m, n) = 32b .. 32b+31, warp w adds entries (o, m, n) of Gamma_o, o = w, w + 8, ...,
+// over the chunks (32 partials in flight at a time; at most eight warps), and after
+// the block barrier warp 0 forms C(m, n) of dim
 // cd from them; the CTAs after those add the source projections h_r[m] and form c.  The
 // same sums and coefficient functions as the last-CTA tail of gram_partial_kernel, whose
 // FP64 work ran on one SM per mode tile.
@@ -285,7 +286,8 @@ __global__ void gram_reduce_coeff_kernel(const double* __restrict__ partial, int
   };
   if ((int)blockIdx.x < nCg) {
     const int idx = blockIdx.x * 32 + lane;
-    if (idx < MM && w < nops) gram[w * MM + idx] = chunk_sum(w * MM + idx);
+    if (idx < MM)
+      for (int o = w; o < nops; o += blockDim.x >> 5) gram[o * MM + idx] = chunk_sum(o * MM + idx);
     __syncthreads();
     if (cd >= 0 && w == 0 && idx < MM) coeff_C(tt, gp, cd, M, idx, C);
   } else {
@@ -516,7 +518,7 @@ int taps_refresh_gram_dim(taps_problem* P, const taps_factors* U, int d, int pre
                               (const double*)P->d_opband[d], nops, (const double*)P->d_q[d], Rf, P->d_partial, stride,
                               P->d_ticket, P->d_gram[d], P->d_h[d], P->tt, gp, coeff_dim, P->d_C, P->d_c, gmt8, 0));
     const int nCg = (M * M + 31) / 32, nCh = (Rf * M + 31) / 32;
-    TAPS_CUDA(taps_launch_pdl(gram_reduce_coeff_kernel, dim3(nCg + nCh), dim3(32 * nops), 0, P->stream,
+    TAPS_CUDA(taps_launch_pdl(gram_reduce_coeff_kernel, dim3(nCg + nCh), dim3(32 * std::min(nops, 8)), 0, P->stream,
                               (const double*)P->d_partial, stride, nchunk, M, nops, Rf, P->d_gram[d], P->d_h[d],
                               P->tt, gp, coeff_dim, P->d_C, P->d_c));
     P->prof->launches[TAPS_PROF_GRAM] += 1;

@@ -94,6 +94,28 @@ def test_global_stage_sweeps_match_oracle(T):
     assert abs(rho - O.als_residual(Po, U.get())) <= 1e-8 * max(rho, 1e-300)
 
 
+def test_global_stage_many_operators_sweeps_match_oracle(T):
+    """34 distinct operators per dim (2 plain + 32 weighted: a global stage at 16
+    weight modes), M = 3: more operators than one CTA of the Gram chunk sums has warps,
+    so each warp adds several operators' entries; three sweeps from the same factors give
+    the oracle's normalised factors to 1e-10 and the Eq. 42 residual matches."""
+    desc = _global(20, 16, seed=8)
+    assert all(len(w) + 2 > 32 for w in desc["weighted"])
+    P = T.Problem(desc)
+    Po = O.problem_from_description(desc)
+    U0 = W.random_factors(desc, 3, seed=9)
+    U = P.factors(3)
+    U.set(U0)
+    P.sweep(U, 3, solver=T.SOLVER_BLOCK_LU)
+    Uo = [u.copy() for u in U0]
+    for _ in range(3):
+        Uo, _ = O.sweep(Po, Uo)
+    for d, (g, o) in enumerate(zip(U.get(), Uo)):
+        assert np.max(np.abs(g - o)) < 1e-10 * np.max(np.abs(o)), d
+    rho = P.residual(U, T.RES_ALS)
+    assert abs(rho - O.als_residual(Po, U.get())) <= 1e-8 * max(rho, 1e-300)
+
+
 def test_weighted_ops_must_be_defined_before_a_sweep(T):
     from paper_2503_13933_gb300 import nonlinear as NL
     desc = W.nonlinear_manufactured(12)
