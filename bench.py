@@ -35,10 +35,10 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (recipe table); probe measured 1.
 # the kernel changed since its capture).  "eval" is per reconstruction: the
 # tensor-core kernel's bytes at 160^3 x 32 scaled by the output size to 256^3 x 32.
 TRAFFIC_BYTES = {
-    "fastdiag": (3 * 96.5e3 + 80.4e3) / 4,          # sweep_kernels_poisson_k_256x32_M30.md
-    "fd_transform": (3 * 651.8e3 + 37.1e3) / 4,
-    "normalize": (3 * 142.1e3 + 35.6e3) / 4,
-    "gram": 188.2e3,
+    "fastdiag": (3 * 97.2e3 + 80.4e3) / 4,          # sweep_kernels_poisson_k_256x32_M30.md
+    "fd_transform": (3 * 652.0e3 + 37.4e3) / 4,
+    "normalize": (3 * 143.1e3 + 36.6e3) / 4,
+    "gram": (3 * (144.6e3 + 545.4e3) + (42.0e3 + 91.4e3)) / 8,   # partial + chunk-sum launches
     "eval": (462.87e6 + 7.92e6) * (256 ** 3) / (160 ** 3),   # eval_tc_kernel_poisson_k_160x32_M30.md
 }
 
