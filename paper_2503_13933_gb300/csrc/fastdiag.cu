@@ -869,8 +869,9 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
 
 // One CTA per node i (M > 32): solve (mu_i C_A + C_B) y = g_i by LU with partial
 // pivoting in shared memory, the right-hand side carried along as column M.  Per
-// step p, warp 0 finds the pivot row (largest magnitude, ties to the smaller row),
-// swaps it into place and takes the pivot's reciprocal; then warp w updates the rows
+// step p, warp 0 finds the pivot row (largest magnitude, ties to the smaller row;
+// integer compares of the magnitudes' bit patterns), swaps it into place and takes the
+// pivot's reciprocal; then warp w updates the rows
 // r = p+1+w, p+5+w, ... (lanes over the columns c > p, coalesced) with one FMA per
 // entry, T[r][c] -= l_r T[p][c], l_r = T[r][p] / T[p][p] (as a product with the
 // reciprocal, seed plus refinement, formed by warp 0 for all rows at once).  The
@@ -901,15 +902,17 @@ __global__ void __launch_bounds__(256) fd_small_solve_kernel(const double* __res
   __syncthreads();
   for (int p = 0; p < M; ++p) {
     if (warp == 0) {   // argmax |T[r][p]|, r >= p (ties to the smaller r), swap, reciprocal
-      double best = -1.0;
+      // compared as the bit patterns of |T[r][p]| (non-negative doubles order like
+      // their bits): integer compares, off the FP64 pipe the update warps keep busy
+      long long best = -1;
       int br = p;
       for (int r = p + lane; r < M; r += 32) {
-        double a = fabs(T[r * ld + p]);
+        const long long a = __double_as_longlong(fabs(T[r * ld + p]));
         if (a > best) { best = a; br = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
         if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
       }
       if (br != p)
