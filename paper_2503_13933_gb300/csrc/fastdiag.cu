@@ -805,7 +805,7 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
   // multipliers of step 0 (column 0 belongs to warp 0)
   if (w == 0) {
     const double piv = __shfl_sync(0xffffffffu, v[0], 0);
-    bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
+    bad |= !taps_finite_nonzero(piv);
     const double inv = taps_rcp(piv);
     lbuf[0][lane] = (lane > 0 && lane < M) ? v[0] * inv : 0.0;
     if (lane == 0) invd[0] = inv;
@@ -830,7 +830,7 @@ __global__ void __launch_bounds__(128) fd_small_solve_quad_kernel(const double* 
         for (int k = (q >> 2) + 1; k < 8; ++k) v[k] -= l * __shfl_sync(0xffffffffu, v[k], p);
         lbuf[q & 1][lane] = (lane > q && lane < M) ? v[q >> 2] * inv : 0.0;
         if (lane == 0) invd[q] = inv;
-        bad |= !(fabs(piv) > 0.0) || !isfinite(piv);
+        bad |= !taps_finite_nonzero(piv);
       } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {   // this warp's columns c > p
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(256) fd_small_solve_kernel(const double* __res
         }
       __syncwarp();
       const double pv = T[p * ld + p];
-      const bool ok = pv != 0.0 && isfinite(pv);
+      const bool ok = taps_finite_nonzero(pv);
       const double inv = ok ? taps_rcp(pv) : 0.0;
       if (lane == 0) {
         invd[p] = inv;

@@ -247,6 +247,13 @@ __device__ __forceinline__ double taps_rcp(double x) {
   return fma(y0, fma(e, e, e), y0);
 }
 
+// A double that is neither zero nor infinite nor NaN, decided on its bits (integer
+// operations: no FP64 compare, which would hold an FP64 pipe on this GPU ~64 cycles).
+__device__ __forceinline__ bool taps_finite_nonzero(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  return u != 0ull && (u >> 52) != 0x7FFull;
+}
+
 // Block-wide sum for blockDim.x <= 1024; `red` holds >= 32 T in shared memory.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
