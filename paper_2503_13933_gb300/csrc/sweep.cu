@@ -1387,9 +1387,9 @@ struct BigGramPtrs {
 
 // Every dim of the full residual in one launch each: the banded products Y_o = Op_o U
 // of all dims (thread per output, as spmm_kernel) and the big Grams of all dims (CTA per
-// row a of dim d's Gram of the columns [Y_0 .. Y_{nops-1} | Q]: BG_SPLIT row ranges, each
-// a sequential sum taking its operands eight rows at a time so that their loads are in
-// flight together, then the ranges' sums added pairwise).
+// pair of rows of dim d's Gram of the columns [Y_0 .. Y_{nops-1} | Q]: per entry
+// BG_SPLIT row ranges, each a sequential sum taking its operands eight rows at a time so
+// that their loads are in flight together, then the ranges' sums added pairwise).
 struct ResAll {
   const double* U[TAPS_MAX_DIMS];
   const double* band[TAPS_MAX_DIMS];
@@ -1422,38 +1422,63 @@ __global__ void spmm_all_kernel(ResAll ra, int M, double* __restrict__ Yall) {
 }
 
 __global__ void __launch_bounds__(BG_COLS * BG_SPLIT) big_gram_all_kernel(ResAll ra, int M, int Rf,
-                                                                           const double* __restrict__ Yall) {
+                                                                           const double* __restrict__ Yall,
+                                                                           int stage) {
+  extern __shared__ double ysm[];   // [2][nf]: the columns of the CTA's two rows (stage)
   __shared__ double part[BG_SPLIT][BG_COLS];
   int d = 0;
   while (d + 1 < ra.D && (int)blockIdx.x >= ra.aoff[d + 1]) ++d;
   const int nops = ra.nops[d], nf = ra.nf[d];
   const int NC = nops * M + Rf;
-  const int a = blockIdx.x - ra.aoff[d];
+  // the Gram is symmetric and a product does not depend on its operands' order, so
+  // entry (a, b) is formed once for b >= a and written to both places; the CTA takes
+  // rows pr and NC-1-pr (NC + 1 columns between them, the middle row alone)
+  const int pr = blockIdx.x - ra.aoff[d];
+  const int r0 = pr, r1 = NC - 1 - pr;
+  const int len0 = NC - r0;
+  const int nv = (r1 == r0) ? len0 : len0 + (NC - r1);
   const double* Y = Yall + ra.yoff[d];
   const double* q = ra.q[d];
+  if (stage) {
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+      ysm[i] = big_gram_col(Y, q, nops, nf, M, r0, i);
+      ysm[nf + i] = big_gram_col(Y, q, nops, nf, M, r1, i);
+    }
+    __syncthreads();
+  }
   const int col = threadIdx.x % BG_COLS, sp = threadIdx.x / BG_COLS;
   const int i0 = (int)((long long)nf * sp / BG_SPLIT), i1 = (int)((long long)nf * (sp + 1) / BG_SPLIT);
-  for (int b0 = 0; b0 < NC; b0 += BG_COLS) {
-    const int b = b0 + col;
+  for (int v0 = 0; v0 < nv; v0 += BG_COLS) {
+    const int v = v0 + col;
+    int a = -1, b = 0;
+    if (v < nv) {
+      if (v < len0) { a = r0; b = r0 + v; }
+      else { a = r1; b = r1 + (v - len0); }
+    }
+    const double* xs = ysm + (a == r0 ? 0 : nf);
     double acc = 0.0;
-    if (b < NC) {
+    if (a >= 0) {
       int i = i0;
       for (; i + 8 <= i1; i += 8) {
         double x[8], y[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          x[k] = big_gram_col(Y, q, nops, nf, M, a, i + k);
+          x[k] = stage ? xs[i + k] : big_gram_col(Y, q, nops, nf, M, a, i + k);
           y[k] = big_gram_col(Y, q, nops, nf, M, b, i + k);
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc += x[k] * y[k];
       }
-      for (; i < i1; ++i) acc += big_gram_col(Y, q, nops, nf, M, a, i) * big_gram_col(Y, q, nops, nf, M, b, i);
+      for (; i < i1; ++i)
+        acc += (stage ? xs[i] : big_gram_col(Y, q, nops, nf, M, a, i)) * big_gram_col(Y, q, nops, nf, M, b, i);
     }
     part[sp][col] = acc;
     __syncthreads();
-    if (sp == 0 && b < NC)
-      ra.G[d][(size_t)a * NC + b] = (part[0][col] + part[1][col]) + (part[2][col] + part[3][col]);
+    if (sp == 0 && a >= 0) {
+      const double g = (part[0][col] + part[1][col]) + (part[2][col] + part[3][col]);
+      ra.G[d][(size_t)a * NC + b] = g;
+      ra.G[d][(size_t)b * NC + a] = g;
+    }
     __syncthreads();
   }
 }
@@ -1577,7 +1602,7 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     ra.hb[d] = dm->hb;
     ra.nops[d] = nops;
     ra.yoff[d + 1] = ra.yoff[d] + ny;
-    ra.aoff[d + 1] = ra.aoff[d] + NC;
+    ra.aoff[d + 1] = ra.aoff[d] + (NC + 1) / 2;   // row pairs of the symmetric big Gram
     fl += 2.0 * ny * dm->nb + 2.0 * (double)NC * NC * dm->nf;
     by += 8.0 * 2.0 * ny;
     bg.G[d] = P->d_bigG + goff;
@@ -1589,7 +1614,10 @@ int taps_residual_enqueue(taps_problem* P, const taps_factors* U, int kind, int 
     const long long ny = ra.yoff[P->D];
     spmm_all_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(ra, M, P->d_Yres);
     TAPS_CUDA(cudaGetLastError());
-    big_gram_all_kernel<<<ra.aoff[P->D], BG_COLS * BG_SPLIT, 0, s>>>(ra, M, P->Rf, (const double*)P->d_Yres);
+    // the two rows' columns in shared memory when they fit the default 48 KB
+    const int stage = (size_t)2 * P->nf_max * sizeof(double) <= 48 * 1024 ? 1 : 0;
+    big_gram_all_kernel<<<ra.aoff[P->D], BG_COLS * BG_SPLIT, stage ? 2 * P->nf_max * sizeof(double) : 0, s>>>(
+        ra, M, P->Rf, (const double*)P->d_Yres, stage);
     TAPS_CUDA(cudaGetLastError());
     P->prof->launches[TAPS_PROF_RESIDUAL] += 1;
     prof_end(P, TAPS_PROF_RESIDUAL, tk, fl, by);
